@@ -1,0 +1,159 @@
+/*
+ * scal3r_ttt.h -- C ABI of the GB300 (sm_103a) test-time-training layer of
+ * Scal3R (arXiv 2604.08542), the "Global Context Memory" hot path.
+ *
+ * What the layer computes (per sequence s and head h, a "chain"):
+ *   fast weights W = (W1 [F,D], W3 [F,D], W2 [D,F]) of the SwiGLU network
+ *       f_W(x) = W2 ( SiLU(W1 x) o (W3 x) )                (Supp. Sec. A)
+ *   start at w0; the sequence's tokens are cut into chunks (Sec. 4.1, 4.2);
+ *   for every chunk, in order:
+ *     1. one gradient step on the whole chunk at the pre-chunk weights,
+ *          W <- W - grad_W sum_i lr_i L(f_W(k_i), v_i)      (Eq. 8)
+ *        with the dot-product loss L = -f_W(k)^T v           (Eq. 9)
+ *        or the squared error 1/2 ||f_W(k) - v||^2;
+ *     2. every row of W1, W3, W2 is rescaled to a target L2 norm (its norm
+ *        in w0 by default) with the clamp max(||row||, eps);
+ *     3. the chunk's queries are transformed by the updated weights,
+ *          o_i = f_W(q_i)                                    (Eq. 4, Sec. 4.2)
+ *   The weights carry over from chunk to chunk of the same sequence (one GPU
+ *   processes the chunks sequentially, Sec. 4.4).
+ * The backward entry point differentiates sum(d_o * o) through the whole
+ * chain of updates (gradients to q, k, v, lr and w0).
+ *
+ * Conventions common to every entry point
+ *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
+ *  - q, k, v, o, d_o, dq, dk, dv: [T, H, D] contiguous, element type given by
+ *    the config's dtype (float32 or bfloat16), 16-byte aligned device memory.
+ *  - lr, dlr: [T, H] float32 device memory.
+ *  - Fast weights of one head are P = 3*F*D float32 values packed W1, W3, W2,
+ *    each row-major.  w0 is [H, P] shared by all sequences (w0_seq_stride = 0)
+ *    or one [H, P] block per sequence, w0_seq_stride floats apart.
+ *  - chunk_offsets [C+1] int64 and seq_chunk_ptr [S+1] int32 are HOST arrays:
+ *    chunk c covers tokens [chunk_offsets[c], chunk_offsets[c+1]) of the
+ *    concatenated sequences; the chunks of sequence s are
+ *    seq_chunk_ptr[s] .. seq_chunk_ptr[s+1]-1.  chunk_offsets[0] = 0, chunks
+ *    are non-empty, seq_chunk_ptr is non-decreasing from 0 to C.  A sequence
+ *    with no chunk is allowed (its w_final is its w0).
+ *  - Every tensor is caller-owned device memory; the library owns only the
+ *    handle and the schedule tables it builds for a chunk layout.  Scratch
+ *    memory comes from the caller's workspace (scal3r_ttt_workspace_size).
+ *  - All work is ordered on the caller's stream (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  One handle per stream at a time.
+ *  - Return value: SCAL3R_OK or an error code; no exception or abort crosses
+ *    the ABI.  Argument errors are found before any work is enqueued.
+ *  - The first call with a new chunk layout builds and uploads a schedule
+ *    (synchronous host work and one cudaMemcpy); make that call, or
+ *    scal3r_ttt_plan, before capturing the stream into a CUDA graph.
+ */
+#ifndef SCAL3R_TTT_H
+#define SCAL3R_TTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SCAL3R_OK                 0
+#define SCAL3R_ERR_INVALID_ARG    1  /* null pointer, bad offsets, bad config value */
+#define SCAL3R_ERR_UNSUPPORTED    2  /* shape/dtype/loss combination not built */
+#define SCAL3R_ERR_MISALIGNED     3  /* a tensor is not 16-byte aligned */
+#define SCAL3R_ERR_CUDA           4  /* a CUDA runtime/driver call failed */
+#define SCAL3R_ERR_TIMEOUT        5  /* a bounded device-side wait gave up */
+#define SCAL3R_ERR_WORKSPACE      6  /* workspace missing or too small */
+#define SCAL3R_ERR_NO_DEVICE      7  /* no sm_103 device current */
+
+/* config values */
+#define SCAL3R_FP32         0   /* q,k,v,o float32: plain SIMT path */
+#define SCAL3R_BF16         1   /* q,k,v,o bfloat16: tcgen05 tensor-core path */
+#define SCAL3R_LOSS_DOT     0   /* L = -f(k)^T v  (Eq. 9) */
+#define SCAL3R_LOSS_MSE     1   /* L = 1/2 ||f(k) - v||^2 */
+#define SCAL3R_NORM_ROW_W0  0   /* rescale rows to their norm in w0 */
+#define SCAL3R_NORM_NONE    1   /* no rescaling */
+#define SCAL3R_NORM_UNIT    2   /* rescale rows to unit norm */
+
+typedef struct scal3r_ttt_config {
+  int32_t num_heads;    /* H >= 1 */
+  int32_t head_dim;     /* D; the BF16 path needs 64, the FP32 path 1..128 */
+  int32_t hidden_dim;   /* F; the BF16 path needs 128, the FP32 path 1..256 */
+  int32_t dtype;        /* SCAL3R_FP32 | SCAL3R_BF16 */
+  int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 path) */
+  int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
+  float   norm_eps;     /* clamp of the row norm; <= 0 selects 1e-6 */
+  int32_t reserved;     /* must be 0 */
+} scal3r_ttt_config;
+
+typedef struct scal3r_ttt_handle scal3r_ttt_handle;
+
+/* Create a handle for one layer configuration on the current CUDA device.
+ * Fails with SCAL3R_ERR_NO_DEVICE unless the device is compute capability
+ * 10.3 (the library is built for sm_103a only). */
+int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out);
+
+/* Free the handle and its schedule tables.  NULL is ignored. */
+void scal3r_ttt_destroy(scal3r_ttt_handle* handle);
+
+/* Static string for a status code. */
+const char* scal3r_ttt_error_string(int status);
+
+/* Validate a chunk layout and build its schedule (work items per chunk step,
+ * token split per chain).  Forward/backward calls with the same layout reuse
+ * it.  Synchronous; not allowed during stream capture. */
+int scal3r_ttt_plan(scal3r_ttt_handle* handle,
+                    const int64_t* chunk_offsets, int32_t num_chunks,
+                    const int32_t* seq_chunk_ptr, int32_t num_seqs);
+
+/* Bytes of workspace the forward (with_backward = 0) or the backward
+ * (with_backward = 1) needs for this layout.  Plans the layout if needed. */
+int scal3r_ttt_workspace_size(scal3r_ttt_handle* handle,
+                              const int64_t* chunk_offsets, int32_t num_chunks,
+                              const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                              int32_t with_backward, size_t* bytes);
+
+/* Forward pass (Eq. 8, Eq. 9, Eq. 4 chunk by chunk; see the file comment).
+ *   o        [T,H,D] out, dtype of q.
+ *   w_ckpt   [C,H,P] float32 out or NULL: the weights after each chunk's
+ *            update (needed by the backward).
+ *   wnorm    [C,H,2F+D] float32 out or NULL: each row's L2 norm after the
+ *            gradient step and before rescaling (needed by the backward).
+ *   w_final  [S,H,P] float32 out or NULL: the weights after the last chunk
+ *            of each sequence (w0 for a sequence with no chunk); pass it as
+ *            the w0 of a following call to continue a stream.
+ *   workspace: device scratch of at least scal3r_ttt_workspace_size(.., 0) bytes. */
+int scal3r_ttt_forward(scal3r_ttt_handle* handle,
+                       const void* q, const void* k, const void* v,
+                       const float* lr, const float* w0, int64_t w0_seq_stride,
+                       const int64_t* chunk_offsets, int32_t num_chunks,
+                       const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                       void* o, float* w_ckpt, float* wnorm, float* w_final,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Backward pass: gradients of sum(d_o * o) through every chunk update.
+ *   d_o      [T,H,D] upstream gradient, dtype of q.
+ *   w_ckpt, wnorm: as written by the forward on the same inputs.
+ *   dq, dk, dv [T,H,D] out (dtype of q); dlr [T,H] float32 out.
+ *   dw0      float32 out with the shape of w0: [H,P] summed over sequences
+ *            when w0_seq_stride = 0, else one block per sequence at the same
+ *            stride.
+ *   workspace: at least scal3r_ttt_workspace_size(.., 1) bytes. */
+int scal3r_ttt_backward(scal3r_ttt_handle* handle,
+                        const void* q, const void* k, const void* v,
+                        const float* lr, const float* w0, int64_t w0_seq_stride,
+                        const int64_t* chunk_offsets, int32_t num_chunks,
+                        const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                        const void* d_o, const float* w_ckpt, const float* wnorm,
+                        void* dq, void* dk, void* dv, float* dlr, float* dw0,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* Synchronise the stream and return the device status word of the last
+ * calls on this handle (SCAL3R_ERR_TIMEOUT if a bounded device wait gave
+ * up), then clear it. */
+int scal3r_ttt_get_status(scal3r_ttt_handle* handle, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCAL3R_TTT_H */

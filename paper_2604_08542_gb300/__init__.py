@@ -1,0 +1,164 @@
+"""GB300 (sm_103a) test-time-training layer of Scal3R (arXiv 2604.08542).
+
+Thin Python binding over the C-ABI library ``libscal3r_ttt.so`` (built from
+``csrc/`` by ``build.py``).  Every step of the layer runs in the library's
+CUDA kernels; this package only marshals arguments (torch tensors provide
+device memory and the current stream).  There is no CPU fallback: if the
+library is missing, every call raises.
+
+Public names mirror the C ABI (``scal3r_ttt_init``, ``scal3r_ttt_forward``,
+``scal3r_ttt_backward``, ...), plus a convenience class :class:`TTT` and the
+``torch.autograd.Function`` :class:`TTTFunction`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libscal3r_ttt.so")
+
+SCAL3R_OK = 0
+SCAL3R_ERR_INVALID_ARG = 1
+SCAL3R_ERR_UNSUPPORTED = 2
+SCAL3R_ERR_MISALIGNED = 3
+SCAL3R_ERR_CUDA = 4
+SCAL3R_ERR_TIMEOUT = 5
+SCAL3R_ERR_WORKSPACE = 6
+SCAL3R_ERR_NO_DEVICE = 7
+
+SCAL3R_FP32 = 0
+SCAL3R_BF16 = 1
+SCAL3R_LOSS_DOT = 0
+SCAL3R_LOSS_MSE = 1
+SCAL3R_NORM_ROW_W0 = 0
+SCAL3R_NORM_NONE = 1
+SCAL3R_NORM_UNIT = 2
+
+EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", "scal3r_ttt_plan",
+            "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
+            "scal3r_ttt_get_status")
+
+
+class scal3r_ttt_config(ctypes.Structure):
+    _fields_ = [("num_heads", ctypes.c_int32), ("head_dim", ctypes.c_int32),
+                ("hidden_dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("loss", ctypes.c_int32), ("weight_norm", ctypes.c_int32),
+                ("norm_eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class Scal3rError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {error_string(status)} (status {status})")
+
+
+_lib_handle = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the C-ABI library (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2604_08542_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    lib.scal3r_ttt_init.argtypes = [ctypes.POINTER(scal3r_ttt_config), ctypes.POINTER(vp)]
+    lib.scal3r_ttt_init.restype = ctypes.c_int
+    lib.scal3r_ttt_destroy.argtypes = [vp]
+    lib.scal3r_ttt_destroy.restype = None
+    lib.scal3r_ttt_error_string.argtypes = [ctypes.c_int]
+    lib.scal3r_ttt_error_string.restype = ctypes.c_char_p
+    lib.scal3r_ttt_plan.argtypes = [vp, vp, i32, vp, i32]
+    lib.scal3r_ttt_plan.restype = ctypes.c_int
+    lib.scal3r_ttt_workspace_size.argtypes = [vp, vp, i32, vp, i32, i32, ctypes.POINTER(sz)]
+    lib.scal3r_ttt_workspace_size.restype = ctypes.c_int
+    lib.scal3r_ttt_forward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32,
+                                       vp, vp, vp, vp, vp, sz, vp]
+    lib.scal3r_ttt_forward.restype = ctypes.c_int
+    lib.scal3r_ttt_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32,
+                                        vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.scal3r_ttt_backward.restype = ctypes.c_int
+    lib.scal3r_ttt_get_status.argtypes = [vp, vp]
+    lib.scal3r_ttt_get_status.restype = ctypes.c_int
+    _lib_handle = lib
+    return lib
+
+
+def error_string(status: int) -> str:
+    try:
+        return load_library().scal3r_ttt_error_string(status).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def _check(status: int, what: str) -> None:
+    if status != SCAL3R_OK:
+        raise Scal3rError(status, what)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one wrapper per entry point (pointers are ints or None)
+# ---------------------------------------------------------------------------
+
+def scal3r_ttt_init(cfg: scal3r_ttt_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().scal3r_ttt_init(ctypes.byref(cfg), ctypes.byref(h)), "scal3r_ttt_init")
+    return h.value
+
+
+def scal3r_ttt_destroy(handle: int) -> None:
+    load_library().scal3r_ttt_destroy(handle)
+
+
+def scal3r_ttt_error_string(status: int) -> str:
+    return error_string(status)
+
+
+def _host_layout(chunk_offsets, seq_chunk_ptr):
+    off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+    ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+    return off, ptr
+
+
+def scal3r_ttt_plan(handle: int, chunk_offsets, seq_chunk_ptr) -> None:
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    _check(load_library().scal3r_ttt_plan(handle, off.ctypes.data, len(off) - 1, ptr.ctypes.data, len(ptr) - 1),
+           "scal3r_ttt_plan")
+
+
+def scal3r_ttt_workspace_size(handle: int, chunk_offsets, seq_chunk_ptr, with_backward: bool) -> int:
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    n = ctypes.c_size_t()
+    _check(load_library().scal3r_ttt_workspace_size(handle, off.ctypes.data, len(off) - 1, ptr.ctypes.data,
+                                                    len(ptr) - 1, int(bool(with_backward)), ctypes.byref(n)),
+           "scal3r_ttt_workspace_size")
+    return n.value
+
+
+def scal3r_ttt_forward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, seq_chunk_ptr,
+                       o, w_ckpt, wnorm, w_final, workspace, workspace_bytes, stream) -> int:
+    """Raw entry point: every tensor argument is a device pointer (int) or None."""
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    return load_library().scal3r_ttt_forward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
+                                             len(off) - 1, ptr.ctypes.data, len(ptr) - 1, o, w_ckpt, wnorm,
+                                             w_final, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, seq_chunk_ptr, d_o,
+                        w_ckpt, wnorm, dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream) -> int:
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    return load_library().scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
+                                              len(off) - 1, ptr.ctypes.data, len(ptr) - 1, d_o, w_ckpt, wnorm,
+                                              dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_get_status(handle: int, stream=None) -> int:
+    return load_library().scal3r_ttt_get_status(handle, stream)
+
+
+from .layer import TTT, TTTFunction  # noqa: E402,F401

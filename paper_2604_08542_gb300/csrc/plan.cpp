@@ -1,0 +1,249 @@
+// Host-side schedule of the chunk recurrence.
+//
+// A chain (sequence s, head h) carries its fast weights from chunk to chunk
+// (Sec. 4.4: one GPU processes the chunks sequentially).  Chunk step j of a
+// chain needs the weights W_j after j updates; at that step two independent
+// sweeps over tokens use W_j:
+//   - the gradient of chunk j at W_j (Eq. 8 is evaluated at the pre-chunk
+//     weights), whose update produces W_{j+1};
+//   - the apply of chunk j-1, whose queries see W_j, the weights after
+//     chunk j-1's own update (Sec. 4.2).
+// The planner lays every chain's step-j work side by side, cuts each token
+// range into pieces so that one step fills the GPU (longest pieces first),
+// and gives every gradient piece a slot for its partial sum; because the
+// chunk gradient is a plain sum over tokens (Eq. 8, Eq. 10), the pieces'
+// partial sums add up to it, in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ttt_internal.h"
+
+namespace scal3r {
+
+namespace {
+
+constexpr int64_t kAlign = 128;   // piece boundaries fall on 128-token tiles
+
+struct Task {
+  int32_t chain, seq, role, chunk;
+  int64_t t0, t1;
+  float cost;
+  int32_t wchunk;
+};
+
+// Cut [t0, t1) into n nearly equal pieces with boundaries on kAlign tokens
+// from t0.
+std::vector<std::pair<int64_t, int64_t>> split(int64_t t0, int64_t t1, int n) {
+  std::vector<std::pair<int64_t, int64_t>> out;
+  int64_t len = t1 - t0;
+  int64_t tiles = (len + kAlign - 1) / kAlign;
+  if (n > tiles) n = (int)std::max<int64_t>(1, tiles);
+  int64_t base = tiles / n, extra = tiles % n;
+  int64_t cur = t0;
+  for (int i = 0; i < n; ++i) {
+    int64_t nt = base + (i < extra ? 1 : 0);
+    int64_t end = std::min(t1, cur + nt * kAlign);
+    if (i == n - 1) end = t1;
+    out.push_back({cur, end});
+    cur = end;
+  }
+  return out;
+}
+
+void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_sms,
+                  bool backward, std::vector<WorkItem>& items, std::vector<UpdateItem>& upds,
+                  std::vector<Step>& steps, int32_t& max_slots,
+                  const std::vector<UpdateItem>& step_updates_template) {
+  Step st{};
+  st.item0 = (int32_t)items.size();
+  st.upd0 = (int32_t)upds.size();
+  double total = 0;
+  for (auto& t : tasks) total += t.cost;
+  int ctas = sch.ctas_per_wave > 0 ? sch.ctas_per_wave : num_sms;
+  double target = std::max(1, sch.waves * ctas);
+  double piece_cost = std::max((double)sch.min_tokens, total / target);
+  // pieces per task
+  std::vector<WorkItem> step_items;
+  // slots: per chain, slots are contiguous (key pieces, and in the backward
+  // also apply pieces, of the same chain).
+  std::vector<UpdateItem> upd = step_updates_template;
+  int32_t slot = 0;
+  for (auto& u : upd) {
+    u.slot0 = slot;
+    u.nslots = 0;
+    for (auto& t : tasks) {
+      if (t.chain != u.chain) continue;
+      bool reduces = backward || t.role == ROLE_KEY;
+      if (!reduces) continue;
+      int n = std::max(1, (int)std::lround(t.cost / piece_cost));
+      for (auto& pr : split(t.t0, t.t1, n)) {
+        WorkItem w{pr.first, pr.second, t.chain, t.role, slot++, t.seq, t.wchunk, 0};
+        step_items.push_back(w);
+        u.nslots++;
+      }
+    }
+  }
+  for (auto& t : tasks) {
+    bool reduces = backward || t.role == ROLE_KEY;
+    if (reduces) continue;
+    int n = std::max(1, (int)std::lround(t.cost / piece_cost));
+    for (auto& pr : split(t.t0, t.t1, n)) {
+      WorkItem w{pr.first, pr.second, t.chain, t.role, -1, t.seq, t.wchunk, 0};
+      step_items.push_back(w);
+    }
+  }
+  // longest (costliest) pieces first
+  auto cost_of = [&](const WorkItem& w) {
+    double c = (double)(w.t1 - w.t0);
+    if (w.role == ROLE_KEY) c *= sch.key_cost;
+    if (w.role == ROLE_BKEY) c *= sch.bkey_cost;
+    return c;
+  };
+  std::stable_sort(step_items.begin(), step_items.end(),
+                   [&](const WorkItem& a, const WorkItem& b) { return cost_of(a) > cost_of(b); });
+  items.insert(items.end(), step_items.begin(), step_items.end());
+  upds.insert(upds.end(), upd.begin(), upd.end());
+  st.nitems = (int32_t)step_items.size();
+  st.nupd = (int32_t)upd.size();
+  st.nslots = slot;
+  max_slots = std::max(max_slots, slot);
+  steps.push_back(st);
+}
+
+}  // namespace
+
+int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
+               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S) {
+  if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
+  if (off[0] != 0) return SCAL3R_ERR_INVALID_ARG;
+  for (int32_t c = 0; c < C; ++c)
+    if (off[c + 1] <= off[c]) return SCAL3R_ERR_INVALID_ARG;  // empty or decreasing chunk
+  if (ptr[0] != 0 || ptr[S] != C) return SCAL3R_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < S; ++i)
+    if (ptr[i + 1] < ptr[i]) return SCAL3R_ERR_INVALID_ARG;
+  if (C > 0 && off[C] > ((int64_t)1 << 40)) return SCAL3R_ERR_INVALID_ARG;
+
+  Plan p;
+  p.chunk_offsets.assign(off, off + C + 1);
+  p.seq_chunk_ptr.assign(ptr, ptr + S + 1);
+  p.H = s.H;
+  p.S = S;
+  p.C = C;
+  p.T = off[C];
+  int32_t maxn = 0;
+  for (int32_t i = 0; i < S; ++i) maxn = std::max(maxn, ptr[i + 1] - ptr[i]);
+  p.max_chunks = maxn;
+  const int32_t H = s.H;
+
+  // ---- forward: steps j = 0 .. maxn --------------------------------------
+  for (int32_t j = 0; j <= maxn; ++j) {
+    std::vector<Task> tasks;
+    std::vector<UpdateItem> upd;
+    for (int32_t q = 0; q < S; ++q) {
+      int32_t n = ptr[q + 1] - ptr[q];
+      if (j > n) continue;
+      for (int32_t h = 0; h < H; ++h) {
+        int32_t chain = q * H + h;
+        if (j < n) {
+          int32_t c = ptr[q] + j;
+          tasks.push_back({chain, q, ROLE_KEY, c, off[c], off[c + 1],
+                           (float)(off[c + 1] - off[c]) * sch.key_cost, -1});
+          UpdateItem u{};
+          u.chain = chain;
+          u.chunk = c;
+          u.last = (j == n - 1);
+          u.seq = q;
+          upd.push_back(u);
+        }
+        if (j >= 1) {
+          int32_t c = ptr[q] + j - 1;
+          tasks.push_back({chain, q, ROLE_APPLY, c, off[c], off[c + 1], (float)(off[c + 1] - off[c]), -1});
+        }
+        if (n == 0 && j == 0) {
+          UpdateItem u{};
+          u.chain = chain;
+          u.chunk = -1;   // no chunk: w_final = w0
+          u.last = 1;
+          u.seq = q;
+          upd.push_back(u);
+        }
+      }
+    }
+    lay_out_step(tasks, sch, num_sms, false, p.items, p.updates, p.steps, p.max_slots, upd);
+  }
+
+  // ---- backward: steps j = maxn .. 0 -------------------------------------
+  for (int32_t j = maxn; j >= 0; --j) {
+    std::vector<Task> tasks;
+    std::vector<UpdateItem> upd;
+    for (int32_t q = 0; q < S; ++q) {
+      int32_t n = ptr[q + 1] - ptr[q];
+      if (n == 0 || j > n) continue;
+      for (int32_t h = 0; h < H; ++h) {
+        int32_t chain = q * H + h;
+        if (j < n) {
+          int32_t c = ptr[q] + j;
+          tasks.push_back({chain, q, ROLE_BKEY, c, off[c], off[c + 1],
+                           (float)(off[c + 1] - off[c]) * sch.bkey_cost, j >= 1 ? c - 1 : -1});
+        }
+        if (j >= 1) {
+          int32_t c = ptr[q] + j - 1;
+          tasks.push_back({chain, q, ROLE_BAPPLY, c, off[c], off[c + 1], (float)(off[c + 1] - off[c]), c});
+        }
+        UpdateItem u{};
+        u.chain = chain;
+        u.chunk = (j >= 1) ? ptr[q] + j - 1 : -1;   // the update whose norm VJP follows
+        u.last = (j == n);                           // no adjoint from a later chunk yet
+        u.first = (j == 0);
+        u.seq = q;
+        upd.push_back(u);
+      }
+    }
+    lay_out_step(tasks, sch, num_sms, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
+  }
+  p.valid = true;
+  plan = std::move(p);
+  return SCAL3R_OK;
+}
+
+size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
+  const size_t chains = (size_t)p.S * s.H;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t b = 0;
+  b += al(2 * chains * s.P() * sizeof(float));                  // wm
+  b += al(chains * s.R() * sizeof(float));                      // rho
+  size_t slots = std::max(p.max_slots, with_backward ? p.bmax_slots : 0);
+  b += al(std::max<size_t>(slots, 1) * s.P() * sizeof(float));  // partials
+  if (with_backward) {
+    b += al(chains * s.P() * sizeof(float));                    // rbuf
+    b += al(chains * s.R() * sizeof(float));                    // drho
+    b += al(chains * s.P() * sizeof(float));                    // dw0 per chain
+  }
+  return b;
+}
+
+void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws, Params& prm) {
+  const size_t chains = (size_t)p.S * s.H;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* c = (char*)ws;
+  prm.wm = (float*)c;
+  c += al(2 * chains * s.P() * sizeof(float));
+  prm.rho = (float*)c;
+  c += al(chains * s.R() * sizeof(float));
+  prm.part = (float*)c;
+  size_t slots = std::max(p.max_slots, with_backward ? p.bmax_slots : 0);
+  c += al(std::max<size_t>(slots, 1) * s.P() * sizeof(float));
+  if (with_backward) {
+    prm.rbuf = (float*)c;
+    c += al(chains * s.P() * sizeof(float));
+    prm.drho = (float*)c;
+    c += al(chains * s.R() * sizeof(float));
+    prm.dw0_chain = (float*)c;
+    c += al(chains * s.P() * sizeof(float));
+  } else {
+    prm.rbuf = prm.drho = prm.dw0_chain = nullptr;
+  }
+}
+
+}  // namespace scal3r

@@ -1,0 +1,147 @@
+// Internal types shared by the host planner and the kernels of the
+// test-time-training layer.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/scal3r_ttt.h"
+
+namespace scal3r {
+
+// Roles of one CTA-sized piece of work inside a chunk step.
+enum Role : int32_t {
+  ROLE_KEY = 0,     // forward: gradient partial of chunk j at W_j (Eq. 8)
+  ROLE_APPLY = 1,   // forward: o = f_{W_j}(q) for chunk j-1 (Eq. 4)
+  ROLE_BKEY = 2,    // backward: VJP of chunk j's update at W_j
+  ROLE_BAPPLY = 3,  // backward: VJP of chunk j-1's apply at W_j
+};
+
+// One piece of a chunk step: a token range of one chain (sequence, head).
+struct WorkItem {
+  int64_t t0, t1;   // tokens [t0, t1) (global token index)
+  int32_t chain;    // s * H + h
+  int32_t role;
+  int32_t slot;     // partial-sum slot written by this piece (-1: none)
+  int32_t seq;
+  int32_t wchunk;   // backward: checkpoint holding the weights (-1: w0)
+  int32_t pad;
+};
+
+// The update of one chain that closes a chunk step: reduce the partial sums
+// of its pieces (fixed order), step, normalise, checkpoint.
+struct UpdateItem {
+  int32_t chain;
+  int32_t chunk;    // global index of the chunk whose update this is, or -1
+  int32_t slot0;    // first partial slot of this chain at this step
+  int32_t nslots;   // number of slots (0: no key pieces, e.g. an empty range)
+  int32_t last;     // forward: 1 if chunk is the last of its sequence
+  int32_t seq;
+  int32_t first;    // backward: 1 if this closes chunk 0 (produces dW0)
+  int32_t pad;
+};
+
+struct Step {
+  int32_t item0, nitems;  // sweep pieces
+  int32_t upd0, nupd;     // updates after the sweep
+  int32_t nslots;         // partial slots used in this step
+};
+
+struct Plan {
+  std::vector<int64_t> chunk_offsets;
+  std::vector<int32_t> seq_chunk_ptr;
+  int32_t H = 0, S = 0, C = 0;
+  int64_t T = 0;
+  int32_t max_chunks = 0;
+  // forward
+  std::vector<WorkItem> items;
+  std::vector<UpdateItem> updates;
+  std::vector<Step> steps;
+  int32_t max_slots = 0;
+  // backward
+  std::vector<WorkItem> bitems;
+  std::vector<UpdateItem> bupdates;
+  std::vector<Step> bsteps;
+  int32_t bmax_slots = 0;
+  // device copies (owned by the handle)
+  WorkItem* d_items = nullptr;
+  UpdateItem* d_updates = nullptr;
+  WorkItem* d_bitems = nullptr;
+  UpdateItem* d_bupdates = nullptr;
+  bool valid = false;
+};
+
+// Scheduling knobs (the autotuner's search space).
+struct Schedule {
+  int32_t ctas_per_wave = 0;   // 0: number of SMs
+  int32_t waves = 1;           // target CTAs per step = waves * ctas_per_wave
+  int32_t min_tokens = 256;    // smallest piece (tokens)
+  float key_cost = 2.0f;       // relative cost of a key token vs a query token
+  float bkey_cost = 2.0f;      // backward: key-side VJP vs apply-side VJP
+};
+
+struct Shape {
+  int32_t H, D, F;
+  int32_t P() const { return 3 * F * D; }
+  int32_t R() const { return 2 * F + D; }
+};
+
+// Device-side parameter block of one forward/backward call.
+struct Params {
+  // inputs
+  const void* q;
+  const void* k;
+  const void* v;
+  const float* lr;
+  const float* w0;
+  int64_t w0_seq_stride;
+  const void* d_o;
+  const float* w_ckpt_in;
+  const float* wnorm_in;
+  // outputs
+  void* o;
+  float* w_ckpt;
+  float* wnorm;
+  float* w_final;
+  void* dq;
+  void* dk;
+  void* dv;
+  float* dlr;
+  float* dw0;
+  // workspace regions
+  float* wm;        // [2][chains][P] master weights (double buffer by step parity)
+  float* rho;       // [chains][R] row-norm targets
+  float* part;      // [max_slots][P] partial sums
+  float* rbuf;      // backward: [chains][P] adjoint R of the next update
+  float* drho;      // backward: [chains][R]
+  float* dw0_chain; // backward: [chains][P] per-chain dW0 (shared w0 only)
+  int* status;      // handle-owned status word
+  // shape and options
+  int32_t H, D, F, S;
+  int64_t T;
+  int32_t loss, norm;
+  float eps;
+};
+
+size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward);
+void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws, Params& prm);
+int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
+               const int64_t* chunk_offsets, int32_t num_chunks,
+               const int32_t* seq_chunk_ptr, int32_t num_seqs);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st);
+cudaError_t launch_update(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st);
+cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st);
+cudaError_t launch_bfinal(const Params& prm, cudaStream_t st);
+cudaError_t launch_fp32_sweep(const Params& prm, const WorkItem* items, int nitems, int step, cudaStream_t st);
+cudaError_t launch_fp32_bsweep(const Params& prm, const WorkItem* items, int nitems, int step, cudaStream_t st);
+cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int nitems, int step,
+                              const void* tmaps, cudaStream_t st);
+cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int nitems, int step,
+                               const void* tmaps, cudaStream_t st);
+
+}  // namespace scal3r

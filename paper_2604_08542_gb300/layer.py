@@ -1,0 +1,157 @@
+"""torch-facing wrapper of the C ABI: tensors in, tensors out.
+
+Only argument marshalling happens here (shape/dtype checks, output and
+workspace allocation, the current CUDA stream); the computation is the
+library's.  Layouts follow the C header: q, k, v, o [T, H, D]; lr [T, H]
+float32; w0 [H, 3*F*D] (shared) or [S, H, 3*F*D] (per sequence) float32,
+packed W1 [F, D], W3 [F, D], W2 [D, F]; chunk_offsets [C+1] int64 and
+seq_chunk_ptr [S+1] int32 on the host.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3R_NORM_NONE,
+               SCAL3R_NORM_ROW_W0, SCAL3R_NORM_UNIT, Scal3rError, _check, scal3r_ttt_backward,
+               scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_status,
+               scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_workspace_size)
+
+NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
+LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class TTT:
+    """One configured layer (a C-ABI handle) on the current CUDA device."""
+
+    def __init__(self, num_heads: int, head_dim: int = 64, hidden_dim: int = 128,
+                 dtype: torch.dtype = torch.bfloat16, loss: str = "dot", weight_norm: str = "row_w0",
+                 norm_eps: float = 1e-6):
+        if dtype not in (torch.bfloat16, torch.float32):
+            raise ValueError("dtype must be torch.bfloat16 or torch.float32")
+        self.H, self.D, self.F = num_heads, head_dim, hidden_dim
+        self.dtype = dtype
+        self.cfg = scal3r_ttt_config(num_heads, head_dim, hidden_dim,
+                                     SCAL3R_BF16 if dtype == torch.bfloat16 else SCAL3R_FP32,
+                                     LOSSES[loss], NORMS[weight_norm], float(norm_eps), 0)
+        self.handle = scal3r_ttt_init(self.cfg)
+        self._ws = None
+
+    @property
+    def P(self) -> int:
+        return 3 * self.F * self.D
+
+    @property
+    def R(self) -> int:
+        return 2 * self.F + self.D
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            scal3r_ttt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers ---------------------------------------------------------
+    def plan(self, chunk_offsets, seq_chunk_ptr) -> None:
+        scal3r_ttt_plan(self.handle, chunk_offsets, seq_chunk_ptr)
+
+    def workspace(self, chunk_offsets, seq_chunk_ptr, with_backward: bool, device) -> torch.Tensor:
+        n = scal3r_ttt_workspace_size(self.handle, chunk_offsets, seq_chunk_ptr, with_backward)
+        if self._ws is None or self._ws.numel() < n or self._ws.device != torch.device(device):
+            self._ws = torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def _check_tokens(self, name, t, T):
+        if t.dtype != self.dtype or t.dim() != 3 or tuple(t.shape) != (T, self.H, self.D) or not t.is_cuda \
+                or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor of shape [T, H, D]")
+
+    def _w0_stride(self, w0, S):
+        if w0.dtype != torch.float32 or not w0.is_cuda or not w0.is_contiguous():
+            raise ValueError("w0 must be a contiguous CUDA float32 tensor")
+        if w0.dim() == 2 and tuple(w0.shape) == (self.H, self.P):
+            return 0
+        if w0.dim() == 3 and tuple(w0.shape) == (S, self.H, self.P):
+            return self.H * self.P
+        raise ValueError("w0 must be [H, 3*F*D] or [S, H, 3*F*D]")
+
+    # -- passes ------------------------------------------------------------
+    def forward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, *, save_for_backward=True,
+                want_final=False, workspace=None, o=None):
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        T, C, S = int(off[-1]), len(off) - 1, len(ptr) - 1
+        for n, t in (("q", q), ("k", k), ("v", v)):
+            self._check_tokens(n, t, T)
+        if lr.dtype != torch.float32 or tuple(lr.shape) != (T, self.H) or not lr.is_contiguous():
+            raise ValueError("lr must be a contiguous float32 tensor of shape [T, H]")
+        stride = self._w0_stride(w0, S)
+        dev = q.device
+        o = torch.empty_like(q) if o is None else o
+        w_ckpt = torch.empty((C, self.H, self.P), dtype=torch.float32, device=dev) if save_for_backward else None
+        wnorm = torch.empty((C, self.H, self.R), dtype=torch.float32, device=dev) if save_for_backward else None
+        w_final = torch.empty((S, self.H, self.P), dtype=torch.float32, device=dev) if want_final else None
+        ws = self.workspace(off, ptr, False, dev) if workspace is None else workspace
+        st = torch.cuda.current_stream(dev).cuda_stream
+        rc = scal3r_ttt_forward(self.handle, _ptr(q), _ptr(k), _ptr(v), _ptr(lr), _ptr(w0), stride, off, ptr,
+                                _ptr(o), _ptr(w_ckpt), _ptr(wnorm), _ptr(w_final), _ptr(ws), ws.numel(), st)
+        _check(rc, "scal3r_ttt_forward")
+        return o, w_ckpt, wnorm, w_final
+
+    def backward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, d_o, w_ckpt, wnorm, *, workspace=None):
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        T, S = int(off[-1]), len(ptr) - 1
+        for n, t in (("q", q), ("k", k), ("v", v), ("d_o", d_o)):
+            self._check_tokens(n, t, T)
+        stride = self._w0_stride(w0, S)
+        dq, dk, dv = torch.empty_like(q), torch.empty_like(k), torch.empty_like(v)
+        dlr = torch.empty_like(lr)
+        dw0 = torch.empty_like(w0)
+        ws = self.workspace(off, ptr, True, q.device) if workspace is None else workspace
+        st = torch.cuda.current_stream(q.device).cuda_stream
+        rc = scal3r_ttt_backward(self.handle, _ptr(q), _ptr(k), _ptr(v), _ptr(lr), _ptr(w0), stride, off, ptr,
+                                 _ptr(d_o), _ptr(w_ckpt), _ptr(wnorm), _ptr(dq), _ptr(dk), _ptr(dv), _ptr(dlr),
+                                 _ptr(dw0), _ptr(ws), ws.numel(), st)
+        _check(rc, "scal3r_ttt_backward")
+        return dq, dk, dv, dlr, dw0
+
+    def status(self) -> int:
+        return scal3r_ttt_get_status(self.handle, torch.cuda.current_stream().cuda_stream)
+
+
+class TTTFunction(torch.autograd.Function):
+    """o = TTT(q, k, v, lr, w0) with the library's hand-written backward.
+
+    ``TTTFunction.apply(q, k, v, lr, w0, layer, chunk_offsets, seq_chunk_ptr)``;
+    the fast weights are checkpointed at every chunk boundary in the forward
+    and the chunks in between are recomputed in the backward.
+    """
+
+    @staticmethod
+    def forward(ctx, q, k, v, lr, w0, layer: TTT, chunk_offsets, seq_chunk_ptr):
+        o, w_ckpt, wnorm, _ = layer.forward(q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, save_for_backward=True)
+        ctx.layer = layer
+        ctx.layout = (np.asarray(chunk_offsets, dtype=np.int64).copy(), np.asarray(seq_chunk_ptr, dtype=np.int32).copy())
+        ctx.save_for_backward(q, k, v, lr, w0, w_ckpt, wnorm)
+        return o
+
+    @staticmethod
+    def backward(ctx, d_o):
+        q, k, v, lr, w0, w_ckpt, wnorm = ctx.saved_tensors
+        off, ptr = ctx.layout
+        d_o = d_o.contiguous()
+        dq, dk, dv, dlr, dw0 = ctx.layer.backward(q, k, v, lr, w0, off, ptr, d_o, w_ckpt, wnorm)
+        return dq, dk, dv, dlr, dw0, None, None, None
+
+
+__all__ = ["TTT", "TTTFunction", "Scal3rError"]
