@@ -1,16 +1,521 @@
-// BF16 tensor-core path (tcgen05 + TMA) of the test-time-training layer.
+// BF16 tensor-core path of the test-time-training layer (sm_103a):
+// tcgen05.mma with TMEM accumulators, operands staged by TMA, warp-specialised
+// CTAs, one CTA per SM (all 512 TMEM columns).
+//
+// Work item roles (see plan.cpp for the chunk-step schedule):
+//
+// KEY  (gradient partial of a chunk at the pre-chunk weights, Eq. 8, Eq. 9).
+//   Lanes of TMEM = hidden unit f (F = 128 = the MMA's M), columns = tokens.
+//   The three weight matrices are A operands resident in TMEM (bf16, packed
+//   along the contraction dim D).  Per tile of 32 tokens:
+//     Z1t = W1 K^T, Z3t = W3 K^T, Pt = W2^T V^T       (M 128, N 32, K 64)
+//   the epilogue warps (thread = f) form, per token t with learning rate e,
+//     a = SiLU(z1), u~ = e a z3, p~ = e p, g1~ = p~ z3 SiLU'(z1), g3~ = p~ a
+//   and write them back to TMEM as bf16 over the columns they just read;
+//   then, with the raw K / V tiles as MN-major B operands,
+//     S1 += G1~^T K, S3 += G3~^T K, S2t += U~^T V      (M 128, N 64, K 16/step)
+//   accumulate in TMEM for the whole piece.  W1 += S1, W3 += S3, W2 += S2t^T
+//   after the fixed-order sum over pieces (update.cu).
+// APPLY (o = f_W(q), Eq. 4).  Lanes = token (M = 128 tokens per tile):
+//     Zq = Q [W1; W3]^T                                 (M 128, N 256, K 64)
+//   the epilogue (thread = token) forms h = SiLU(zq1) zq3 as bf16 into TMEM,
+//     O = H W2^T                                        (M 128, N 64, K 128)
+//   with H as the TMEM A operand, and stores O as bf16.
+//
+// Warp roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
+// MMAs (one thread), warps 2..9 are the epilogue (two warps per TMEM lane
+// quarter).  Every wait is an mbarrier wait bounded in time: on timeout the
+// CTA raises an abort flag, every role leaves its loop, the status word is set
+// to SCAL3R_ERR_TIMEOUT and TMEM is freed.
+#include <cudaTypedefs.h>
+
+#include "sm100.cuh"
 #include "ttt_internal.h"
 
 namespace scal3r {
+namespace {
 
-bool bf16_shape_supported(int D, int F) { return D == 64 && F == 128; }
+using namespace sm100;
 
-cudaError_t launch_bf16_sweep(const Params&, const WorkItem*, int, int, const void*, cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr int D = 64;
+constexpr int F = 128;
+constexpr int NTHREADS = 320;
+constexpr int KT = 32;        // key tile (tokens)
+constexpr int QT = 128;       // query tile (tokens)
+constexpr int KSTAGES = 6;    // K/V stages, 8 KB each
+constexpr int QSTAGES = 3;    // Q stages, 16 KB each
+
+// TMEM columns, key role
+constexpr uint32_t K_AW1 = 0, K_AW3 = 32, K_AW2T = 64;     // A operands (bf16 x2 per column)
+constexpr uint32_t K_S1 = 96, K_S3 = 160, K_S2T = 224;     // fp32 accumulators [f][d]
+constexpr uint32_t K_BUF = 288;                            // 2 x (z1 | z3 | p), 32 columns each
+// TMEM columns, apply role
+constexpr uint32_t A_ZQ = 0;      // z1 0..127, z3 128..255
+constexpr uint32_t A_H = 256;     // h as bf16 pairs, 64 columns
+constexpr uint32_t A_O = 320;     // o accumulator, 64 columns
+
+constexpr uint32_t IDESC_KZ = idesc_bf16(128, KT, false, false);   // Z1t/Z3t/Pt
+constexpr uint32_t IDESC_KS = idesc_bf16(128, D, false, true);     // S accumulations, B MN-major
+constexpr uint32_t IDESC_AZ = idesc_bf16(128, 2 * F, false, false);
+constexpr uint32_t IDESC_AO = idesc_bf16(128, D, false, false);
+
+constexpr size_t KEY_SMEM = (size_t)KSTAGES * 2 * KT * 128;
+constexpr size_t APPLY_SMEM = 2 * F * 128 + 2 * D * 128 + (size_t)QSTAGES * QT * 128;
+constexpr size_t DYN_SMEM = 1024 + (KEY_SMEM > APPLY_SMEM ? KEY_SMEM : APPLY_SMEM);
+
+struct TmaMaps {
+  CUtensorMap q;   // box 64 x 1 x 128 tokens
+  CUtensorMap k;   // box 64 x 1 x 32 tokens
+  CUtensorMap v;   // box 64 x 1 x 32 tokens
+};
+
+struct Bars {
+  uint64_t kv_full[KSTAGES], kv_empty[KSTAGES];
+  uint64_t zp_full[2], ug_full[2], buf_free[2], s_done;
+  uint64_t q_full[QSTAGES], q_empty[QSTAGES];
+  uint64_t zq_full, zq_free, h_full, o_full;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__device__ __forceinline__ float silu_prime_from(float s, float a) { return fmaf(a, 1.f - s, s); }
+
+// ---------------------------------------------------------------------------
+// KEY role
+// ---------------------------------------------------------------------------
+__device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& it, const float* w, uint8_t* sm,
+                         Bars& B, uint32_t tb) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int h = it.chain % p.H;
+  const int64_t t0 = it.t0, t1 = it.t1;
+  const int ntiles = (int)((t1 - t0 + KT - 1) / KT);
+  uint8_t* Ks = sm;                         // KSTAGES x [32][64] bf16, 4 KB each
+  uint8_t* Vs = sm + KSTAGES * KT * 128;
+  volatile int* abort = &B.abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < ntiles; ++i) {
+        const int s = i % KSTAGES;
+        if (!mbar_wait(&B.kv_empty[s], ((i / KSTAGES) & 1) ^ 1, abort)) break;
+        mbar_arrive_expect_tx(&B.kv_full[s], 2 * KT * 128);
+        const int32_t tok = (int32_t)(t0 + (int64_t)i * KT);
+        tma_load_3d(Ks + s * KT * 128, &maps.k, &B.kv_full[s], 0, h, tok);
+        tma_load_3d(Vs + s * KT * 128, &maps.v, &B.kv_full[s], 0, h, tok);
+      }
+    }
+    __syncwarp();
+    return;
+  }
+
+  if (warp == 1) {
+    if (lane == 0) {
+      auto issue_s = [&](int j) -> bool {
+        const int b = j & 1, s = j % KSTAGES;
+        if (!mbar_wait(&B.ug_full[b], (j >> 1) & 1, abort)) return false;
+        tc_fence_after();
+        const uint32_t zb = K_BUF + 96 * b;
+        const uint32_t ks_addr = smem_u32(Ks + s * KT * 128), vs_addr = smem_u32(Vs + s * KT * 128);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t kdesc = sdesc_sw128(ks_addr + kk * 2048, 1024, 1024);
+          const uint64_t vdesc = sdesc_sw128(vs_addr + kk * 2048, 1024, 1024);
+          mma_ts(tb + K_S1, tb + zb + 32 + 16 * kk, kdesc, IDESC_KS, acc);   // g1~ in the z3 slot
+          mma_ts(tb + K_S3, tb + zb + 64 + 16 * kk, kdesc, IDESC_KS, acc);   // g3~ in the p slot
+          mma_ts(tb + K_S2T, tb + zb + 0 + 16 * kk, vdesc, IDESC_KS, acc);   // u~ in the z1 slot
+        }
+        mma_commit(&B.buf_free[b]);
+        mma_commit(&B.kv_empty[s]);
+        return true;
+      };
+      bool ok = true;
+      for (int i = 0; i < ntiles && ok; ++i) {
+        const int b = i & 1, s = i % KSTAGES;
+        if (!mbar_wait(&B.kv_full[s], (i / KSTAGES) & 1, abort)) break;
+        if (!mbar_wait(&B.buf_free[b], ((i >> 1) & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t zb = K_BUF + 96 * b;
+        const uint32_t ks_addr = smem_u32(Ks + s * KT * 128), vs_addr = smem_u32(Vs + s * KT * 128);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t kdesc = sdesc_sw128(ks_addr + kk * 32, 16, 1024);
+          const uint64_t vdesc = sdesc_sw128(vs_addr + kk * 32, 16, 1024);
+          mma_ts(tb + zb + 0, tb + K_AW1 + 8 * kk, kdesc, IDESC_KZ, kk > 0);
+          mma_ts(tb + zb + 32, tb + K_AW3 + 8 * kk, kdesc, IDESC_KZ, kk > 0);
+          mma_ts(tb + zb + 64, tb + K_AW2T + 8 * kk, vdesc, IDESC_KZ, kk > 0);
+        }
+        mma_commit(&B.zp_full[b]);
+        if (i >= 1) ok = issue_s(i - 1);
+      }
+      if (ok && !*abort) {
+        if (issue_s(ntiles - 1)) mma_commit(&B.s_done);
+      }
+    }
+    __syncwarp();
+    return;
+  }
+
+  // epilogue warps
+  const int ew = warp - 2;
+  const int half = ew >> 2;               // tokens [16*half, 16*half + 16) of each tile
+  const uint32_t row = 32u * (warp & 3) + lane;   // hidden unit f
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  for (int i = 0; i < ntiles; ++i) {
+    const int b = i & 1;
+    const int64_t tok0 = t0 + (int64_t)i * KT + 16 * half;
+    float eta_l = 0.f;
+    if (lane < 16 && tok0 + lane < t1) eta_l = p.lr[(size_t)(tok0 + lane) * p.H + h];
+    if (!mbar_wait(&B.zp_full[b], (i >> 1) & 1, abort)) break;
+    tc_fence_after();
+    const uint32_t zb = tb + lane_base + K_BUF + 96 * b + 16 * half;
+    float z1[16], z3[16], pp[16];
+    tmem_ld16x3(zb, zb + 32, zb + 64, z1, z3, pp);
+    uint32_t uu[8], g1[8], g3[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      float ut[2], g1t[2], g3t[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = 2 * m + q;
+        const float e = __shfl_sync(0xffffffffu, eta_l, j);
+        const float x = z1[j];
+        const float sg = sigmoid_fast(x);
+        const float a = x * sg;
+        const float sp = silu_prime_from(sg, a);
+        const float pe = e * pp[j];
+        ut[q] = e * a * z3[j];
+        g1t[q] = pe * z3[j] * sp;
+        g3t[q] = pe * a;
+      }
+      uu[m] = pack_bf16(ut[0], ut[1]);
+      g1[m] = pack_bf16(g1t[0], g1t[1]);
+      g3[m] = pack_bf16(g3t[0], g3t[1]);
+    }
+    tmem_st8(zb, uu);
+    tmem_st8(zb + 32, g1);
+    tmem_st8(zb + 64, g3);
+    tmem_st_wait();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&B.ug_full[b]);
+  }
+  if (!*abort && mbar_wait(&B.s_done, 0, abort)) {
+    tc_fence_after();
+    float* out = p.part + (size_t)it.slot * 3 * F * D + (size_t)row * D + 32 * half;
+    const uint32_t mats[3] = {K_S1, K_S3, K_S2T};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 32; c += 16) {
+        tmem_ld16(tb + lane_base + mats[m] + 32 * half + c, v);
+        float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
+      }
+    }
+  }
 }
 
-cudaError_t launch_bf16_bsweep(const Params&, const WorkItem*, int, int, const void*, cudaStream_t) {
-  return cudaErrorNotSupported;
+// Weights into TMEM as A operands: lane f holds W1[f][:], W3[f][:], W2[:][f]
+// as bf16 pairs along d.
+__device__ void key_load_weights(const float* w, uint32_t tb) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int ew = warp - 2, half = ew >> 2;
+  const uint32_t f = 32u * (warp & 3) + lane;
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  uint32_t r[16];
+  // half 0: W1 row f; half 1: W3 row f
+  const float* src = w + (size_t)half * F * D + (size_t)f * D;
+#pragma unroll
+  for (int c0 = 0; c0 < 32; c0 += 16) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) r[j] = pack_bf16(src[2 * (c0 + j)], src[2 * (c0 + j) + 1]);
+    tmem_st16(tb + lane_base + (half ? K_AW3 : K_AW1) + c0, r);
+  }
+  // W2^T row f = column f of W2 [D][F]; half h covers d in [32h, 32h + 32)
+  const float* w2 = w + 2 * (size_t)F * D;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int d = 32 * half + 2 * j;
+    r[j] = pack_bf16(w2[(size_t)d * F + f], w2[(size_t)(d + 1) * F + f]);
+  }
+  tmem_st16(tb + lane_base + K_AW2T + 16 * half, r);
+  tmem_st_wait();
+}
+
+// ---------------------------------------------------------------------------
+// APPLY role
+// ---------------------------------------------------------------------------
+__device__ void apply_load_weights(const float* w, uint8_t* sm) {
+  // [W1; W3] as 256 rows x 64 (K-major, swizzled) and W2 as two [64][64]
+  // K-blocks (rows d, columns f).  One 16-byte chunk (8 elements) per step.
+  uint8_t* wb13 = sm;
+  uint8_t* wb2 = sm + 2 * F * 128;
+  const int t = threadIdx.x - 64;   // epilogue threads 0..255
+  for (int c = t; c < 2 * F * 8; c += 256) {
+    const int r = c >> 3, col = (c & 7) * 8;
+    const float* src = w + (size_t)r * D + col;   // W1 rows then W3 rows, contiguous
+    const float4 a = *reinterpret_cast<const float4*>(src);
+    const float4 bq = *reinterpret_cast<const float4*>(src + 4);
+    uint4 pk = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(bq.x, bq.y), pack_bf16(bq.z, bq.w));
+    *reinterpret_cast<uint4*>(wb13 + sw128_offset(r, col)) = pk;
+  }
+  const float* w2 = w + 2 * (size_t)F * D;
+  for (int c = t; c < D * (F / 8); c += 256) {
+    const int r = c / (F / 8), col = (c % (F / 8)) * 8;   // row d, first f of the chunk
+    const float* src = w2 + (size_t)r * F + col;
+    const float4 a = *reinterpret_cast<const float4*>(src);
+    const float4 bq = *reinterpret_cast<const float4*>(src + 4);
+    uint4 pk = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(bq.x, bq.y), pack_bf16(bq.z, bq.w));
+    *reinterpret_cast<uint4*>(wb2 + (col / 64) * (D * 128) + sw128_offset(r, col % 64)) = pk;
+  }
+  fence_proxy_async_smem();
+}
+
+__device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
+                           uint32_t tb) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int h = it.chain % p.H;
+  const int64_t t0 = it.t0, t1 = it.t1;
+  const int ntiles = (int)((t1 - t0 + QT - 1) / QT);
+  uint8_t* wb13 = sm;
+  uint8_t* wb2 = sm + 2 * F * 128;
+  uint8_t* Qs = wb2 + 2 * D * 128;
+  volatile int* abort = &B.abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < ntiles; ++i) {
+        const int s = i % QSTAGES;
+        if (!mbar_wait(&B.q_empty[s], ((i / QSTAGES) & 1) ^ 1, abort)) break;
+        mbar_arrive_expect_tx(&B.q_full[s], QT * 128);
+        tma_load_3d(Qs + s * QT * 128, &maps.q, &B.q_full[s], 0, h, (int32_t)(t0 + (int64_t)i * QT));
+      }
+    }
+    __syncwarp();
+    return;
+  }
+
+  if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t w13 = smem_u32(wb13), w2a = smem_u32(wb2);
+      auto issue_zq = [&](int i) -> bool {
+        const int s = i % QSTAGES;
+        if (!mbar_wait(&B.q_full[s], (i / QSTAGES) & 1, abort)) return false;
+        if (!mbar_wait(&B.zq_free, (i & 1) ^ 1, abort)) return false;
+        tc_fence_after();
+        const uint32_t qa = smem_u32(Qs + s * QT * 128);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_ss(tb + A_ZQ, sdesc_sw128(qa + kk * 32, 16, 1024), sdesc_sw128(w13 + kk * 32, 16, 1024), IDESC_AZ,
+                 kk > 0);
+        mma_commit(&B.zq_full);
+        mma_commit(&B.q_empty[s]);
+        return true;
+      };
+      bool ok = issue_zq(0);
+      for (int i = 0; i < ntiles && ok; ++i) {
+        if (i + 1 < ntiles && !issue_zq(i + 1)) break;
+        if (!mbar_wait(&B.h_full, i & 1, abort)) break;
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          mma_ts(tb + A_O, tb + A_H + 8 * kk, sdesc_sw128(w2a + (kk / 4) * (D * 128) + (kk % 4) * 32, 16, 1024),
+                 IDESC_AO, kk > 0);
+        mma_commit(&B.o_full);
+      }
+    }
+    __syncwarp();
+    return;
+  }
+
+  // epilogue: thread = token row of the tile; half selects f in [64*half, 64*half+64)
+  const int ew = warp - 2, half = ew >> 2;
+  const uint32_t row = 32u * (warp & 3) + lane;
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(p.o);
+  auto store_o = [&](int i) -> bool {
+    if (!mbar_wait(&B.o_full, i & 1, abort)) return false;
+    tc_fence_after();
+    float v0[16], v1[16];
+    tmem_ld16(tb + lane_base + A_O + 32 * half, v0);
+    tmem_ld16(tb + lane_base + A_O + 32 * half + 16, v1);
+    const int64_t tok = t0 + (int64_t)i * QT + row;
+    if (tok < t1) {
+      uint4* dst = reinterpret_cast<uint4*>(o + ((size_t)tok * p.H + h) * D + 32 * half);
+      dst[0] = make_uint4(pack_bf16(v0[0], v0[1]), pack_bf16(v0[2], v0[3]), pack_bf16(v0[4], v0[5]), pack_bf16(v0[6], v0[7]));
+      dst[1] = make_uint4(pack_bf16(v0[8], v0[9]), pack_bf16(v0[10], v0[11]), pack_bf16(v0[12], v0[13]), pack_bf16(v0[14], v0[15]));
+      dst[2] = make_uint4(pack_bf16(v1[0], v1[1]), pack_bf16(v1[2], v1[3]), pack_bf16(v1[4], v1[5]), pack_bf16(v1[6], v1[7]));
+      dst[3] = make_uint4(pack_bf16(v1[8], v1[9]), pack_bf16(v1[10], v1[11]), pack_bf16(v1[12], v1[13]), pack_bf16(v1[14], v1[15]));
+    }
+    return true;
+  };
+  for (int i = 0; i < ntiles; ++i) {
+    if (i > 0 && !store_o(i - 1)) break;
+    if (!mbar_wait(&B.zq_full, i & 1, abort)) break;
+    tc_fence_after();
+    float z1[64], z3[64];
+    {
+      float a[16], bq[16];
+#pragma unroll
+      for (int c = 0; c < 64; c += 16) {
+        tmem_ld16(tb + lane_base + A_ZQ + 64 * half + c, a);
+        tmem_ld16(tb + lane_base + A_ZQ + F + 64 * half + c, bq);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          z1[c + j] = a[j];
+          z3[c + j] = bq[j];
+        }
+      }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&B.zq_free);
+    uint32_t hp[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+      const float x0 = z1[2 * m], x1 = z1[2 * m + 1];
+      const float h0 = x0 * sigmoid_fast(x0) * z3[2 * m];
+      const float h1 = x1 * sigmoid_fast(x1) * z3[2 * m + 1];
+      hp[m] = pack_bf16(h0, h1);
+    }
+    uint32_t r0[16], r1[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      r0[m] = hp[m];
+      r1[m] = hp[16 + m];
+    }
+    tmem_st16(tb + lane_base + A_H + 32 * half, r0);
+    tmem_st16(tb + lane_base + A_H + 32 * half + 16, r1);
+    tmem_st_wait();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&B.h_full);
+  }
+  if (!*abort) store_o(ntiles - 1);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHREADS, 1)
+bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const WorkItem* __restrict__ items,
+                  int step) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  __shared__ Bars B;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const WorkItem it = items[blockIdx.x];
+  const int chains = p.S * p.H;
+  const float* w = p.wm + ((size_t)(step & 1) * chains + it.chain) * 3 * F * D;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < KSTAGES; ++i) {
+      mbar_init(&B.kv_full[i], 1);
+      mbar_init(&B.kv_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&B.zp_full[i], 1);
+      mbar_init(&B.ug_full[i], 8);
+      mbar_init(&B.buf_free[i], 1);
+    }
+    mbar_init(&B.s_done, 1);
+    for (int i = 0; i < QSTAGES; ++i) {
+      mbar_init(&B.q_full[i], 1);
+      mbar_init(&B.q_empty[i], 1);
+    }
+    mbar_init(&B.zq_full, 1);
+    mbar_init(&B.zq_free, 8);
+    mbar_init(&B.h_full, 8);
+    mbar_init(&B.o_full, 1);
+    B.abort_flag = 0;
+    fence_barrier_init();
+    prefetch_tmap(&maps.q);
+    prefetch_tmap(&maps.k);
+    prefetch_tmap(&maps.v);
+  }
+  if (warp == 1) {
+    tmem_alloc(&B.tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = B.tmem_base;
+
+  // weights
+  if (warp >= 2) {
+    if (it.role == ROLE_KEY) key_load_weights(w, tb);
+    else apply_load_weights(w, sm);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (it.role == ROLE_KEY) key_role(maps, p, it, w, sm, B, tb);
+  else apply_role(maps, p, it, sm, B, tb);
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (B.abort_flag && threadIdx.x == 0) atomicExch(p.status, SCAL3R_ERR_TIMEOUT);
+  if (warp == 1) tmem_dealloc(tb, 512);
+  (void)lane;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// [T, H, 64] bf16 token tensor, boxes of 64 x 1 x box_tokens, 128-byte swizzle.
+bool make_token_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_tokens) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)H, (cuuint64_t)T};
+  cuuint64_t strides[2] = {(cuuint64_t)D * 2, (cuuint64_t)H * D * 2};
+  cuuint32_t box[3] = {(cuuint32_t)D, 1, (cuuint32_t)box_tokens};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_simt_bsweep_bf16io(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st);
+
+bool bf16_shape_supported(int Dd, int Ff) { return Dd == D && Ff == F; }
+
+cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
+                               cudaStream_t st) {
+  return launch_simt_bsweep_bf16io(prm, items, n, step, st);
+}
+
+cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (prm.T <= 0) return cudaErrorInvalidValue;
+  TmaMaps maps;
+  if (!make_token_map(&maps.q, prm.q, prm.T, prm.H, QT) || !make_token_map(&maps.k, prm.k, prm.T, prm.H, KT) ||
+      !make_token_map(&maps.v, prm.v, prm.T, prm.H, KT))
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(bf16_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  bf16_sweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items, step);
+  return cudaGetLastError();
 }
 
 }  // namespace scal3r

@@ -20,12 +20,19 @@
 //          L1 += dz1 k^T, L3 += dz3 k^T, L2t += dp e^T (+ u dy^T for MSE).
 //   BAPPLY VJP of o = f_W(q): dq and L1 += dzq1 q^T, L3 += dzq3 q^T,
 //          L2t += uq do^T.
+#include <cuda_bf16.h>
+
 #include "ttt_internal.h"
 
 namespace scal3r {
 namespace {
 
 constexpr int NTH = 256;
+
+__device__ __forceinline__ float ldio(const float* p, size_t i) { return p[i]; }
+__device__ __forceinline__ float ldio(const __nv_bfloat16* p, size_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void stio(float* p, size_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void stio(__nv_bfloat16* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
 
 template <int D, int F>
 struct Geo {
@@ -53,11 +60,11 @@ __device__ void load_weights(float* ws, const float* __restrict__ w) {
   }
 }
 
-template <int D, int F, int TT>
-__device__ void load_rows(float* dst, const float* __restrict__ src, int64_t t, int n, int H, int h) {
+template <int D, int F, int TT, typename TIO>
+__device__ void load_rows(float* dst, const TIO* __restrict__ src, int64_t t, int n, int H, int h) {
   for (int i = threadIdx.x; i < TT * D; i += NTH) {
     const int r = i / D, c = i % D;
-    dst[i] = (r < n) ? src[((size_t)(t + r) * H + h) * D + c] : 0.f;
+    dst[i] = (r < n) ? ldio(src, ((size_t)(t + r) * H + h) * D + c) : 0.f;
   }
 }
 
@@ -110,7 +117,7 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
     for (int64_t t = it.t0; t < it.t1; t += TT) {
       const int n = (int)((it.t1 - t) < TT ? (it.t1 - t) : TT);
       __syncthreads();
-      load_rows<D, F, TT>(Ks, q, t, n, H, h);
+      load_rows<D, F, TT, float>(Ks, q, t, n, H, h);
       __syncthreads();
       {
         const int f = tid % F;
@@ -153,8 +160,8 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   for (int64_t t = it.t0; t < it.t1; t += TT) {
     const int n = (int)((it.t1 - t) < TT ? (it.t1 - t) : TT);
     __syncthreads();
-    load_rows<D, F, TT>(Ks, kk, t, n, H, h);
-    load_rows<D, F, TT>(Vs, vv, t, n, H, h);
+    load_rows<D, F, TT, float>(Ks, kk, t, n, H, h);
+    load_rows<D, F, TT, float>(Vs, vv, t, n, H, h);
     for (int i = tid; i < TT; i += NTH) etas[i] = (i < n) ? p.lr[(size_t)(t + i) * H + h] : 0.f;
     __syncthreads();
     {  // z1, z3 and the SiLU pieces
@@ -235,7 +242,7 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 // backward
 // ---------------------------------------------------------------------------
 
-template <int D, int F>
+template <int D, int F, typename TIO>
 __global__ void __launch_bounds__(NTH, 1)
 fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   using G = Geo<D, F>;
@@ -286,14 +293,14 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 
   if (it.role == ROLE_BAPPLY) {
     load_weights<D, F>(sm, w);
-    const float* q = (const float*)p.q;
-    const float* go = (const float*)p.d_o;
-    float* dq = (float*)p.dq;
+    const TIO* q = (const TIO*)p.q;
+    const TIO* go = (const TIO*)p.d_o;
+    TIO* dq = (TIO*)p.dq;
     for (int64_t t = it.t0; t < it.t1; t += TT) {
       const int n = (int)((it.t1 - t) < TT ? (it.t1 - t) : TT);
       __syncthreads();
-      load_rows<D, F, TT>(Ks, q, t, n, H, h);
-      load_rows<D, F, TT>(Vs, go, t, n, H, h);
+      load_rows<D, F, TT, TIO>(Ks, q, t, n, H, h);
+      load_rows<D, F, TT, TIO>(Vs, go, t, n, H, h);
       __syncthreads();
       {
         const int f = tid % F;
@@ -321,7 +328,7 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 #pragma unroll 16
           for (int f = 0; f < F; ++f)
             g = fmaf(DZ1s[i * F + f], M1[f * G::LDW + d], fmaf(DZ3s[i * F + f], M3[f * G::LDW + d], g));
-          if (i < n) dq[((size_t)(t + i) * H + h) * D + d] = g;
+          if (i < n) stio(dq, ((size_t)(t + i) * H + h) * D + d, g);
         }
       }
       {
@@ -352,16 +359,16 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   }
 
   // ROLE_BKEY
-  const float* kk = (const float*)p.k;
-  const float* vv = (const float*)p.v;
-  float* dk = (float*)p.dk;
-  float* dv = (float*)p.dv;
+  const TIO* kk = (const TIO*)p.k;
+  const TIO* vv = (const TIO*)p.v;
+  TIO* dk = (TIO*)p.dk;
+  TIO* dv = (TIO*)p.dv;
   for (int64_t t = it.t0; t < it.t1; t += TT) {
     const int n = (int)((it.t1 - t) < TT ? (it.t1 - t) : TT);
     __syncthreads();
     load_weights<D, F>(sm, w);
-    load_rows<D, F, TT>(Ks, kk, t, n, H, h);
-    load_rows<D, F, TT>(Vs, vv, t, n, H, h);
+    load_rows<D, F, TT, TIO>(Ks, kk, t, n, H, h);
+    load_rows<D, F, TT, TIO>(Vs, vv, t, n, H, h);
     for (int i = tid; i < TT; i += NTH) etas[i] = (i < n) ? p.lr[(size_t)(t + i) * H + h] : 0.f;
     __syncthreads();
     // ---- recompute at W -------------------------------------------------
@@ -472,7 +479,7 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
           dh = -Vs[i * D + d] * de;
         }
         DHs[i * D + d] = dh;
-        if (i < n) dv[((size_t)(t + i) * H + h) * D + d] = dvv;
+        if (i < n) stio(dv, ((size_t)(t + i) * H + h) * D + d, dvv);
       }
     }
     __syncthreads();
@@ -498,7 +505,7 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 #pragma unroll 16
         for (int f = 0; f < F; ++f)
           g = fmaf(DZ1s[i * F + f], M1[f * G::LDW + d], fmaf(DZ3s[i * F + f], M3[f * G::LDW + d], g));
-        if (i < n) dk[((size_t)(t + i) * H + h) * D + d] = g;
+        if (i < n) stio(dk, ((size_t)(t + i) * H + h) * D + d, g);
       }
       for (int i = tid; i < n; i += NTH) {
         float a = 0.f;
@@ -552,12 +559,13 @@ cudaError_t launch_fwd(const Params& prm, const WorkItem* items, int n, int step
   return cudaGetLastError();
 }
 
-template <int D, int F>
+template <int D, int F, typename TIO>
 cudaError_t launch_bwd(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st) {
   const size_t smem = bwd_smem<D, F>();
-  cudaError_t e = cudaFuncSetAttribute(fp32_bsweep_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fp32_bsweep_kernel<D, F, TIO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  fp32_bsweep_kernel<D, F><<<n, NTH, smem, st>>>(prm, items, step);
+  fp32_bsweep_kernel<D, F, TIO><<<n, NTH, smem, st>>>(prm, items, step);
   return cudaGetLastError();
 }
 
@@ -576,8 +584,15 @@ cudaError_t launch_fp32_sweep(const Params& prm, const WorkItem* items, int n, i
 
 cudaError_t launch_fp32_bsweep(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (prm.D == 64 && prm.F == 128) return launch_bwd<64, 128>(prm, items, n, step, st);
-  if (prm.D == 16 && prm.F == 32) return launch_bwd<16, 32>(prm, items, n, step, st);
+  if (prm.D == 64 && prm.F == 128) return launch_bwd<64, 128, float>(prm, items, n, step, st);
+  if (prm.D == 16 && prm.F == 32) return launch_bwd<16, 32, float>(prm, items, n, step, st);
+  return cudaErrorInvalidValue;
+}
+
+// Backward of the BF16 path on CUDA cores: bf16 token tensors, fp32 arithmetic.
+cudaError_t launch_simt_bsweep_bf16io(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (prm.D == 64 && prm.F == 128) return launch_bwd<64, 128, __nv_bfloat16>(prm, items, n, step, st);
   return cudaErrorInvalidValue;
 }
 
