@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 test-time-training layer (Scal3R, arXiv 2604.08542).
+
+One step = one forward pass (chunk-wise gradient step, row normalisation,
+apply; Eq. 8, Eq. 9, Eq. 4) plus the hand-written backward through every
+chunk update, on a synthetic VGGT-shaped token stream: 1 sequence x 64 frames
+x 1041 tokens, 16 heads x 64, SwiGLU hidden 128, chunk 16 frames, bfloat16
+q/k/v with float32 fast weights.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torchrun, one process per GPU; every rank processes its own
+batch (different seed) with no collective on the data path ("weak" scaling);
+value = tokens of all ranks / max-over-ranks time.  --impl reference times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import ttt_synth as syn  # noqa: E402
+
+METRIC = "TTT-layer tokens/s fwd and fwd+bwd (BF16 vs FP32) + % tensor-core peak, 1 GB300"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+NUM_SMS_GB300 = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="bf16_vggt64")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--fp32-steps", type=int, default=3)
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w: syn.Workload, seed: int, heads=(0,)):
+    """Inputs of a bounded sample of the workload: the given heads, all tokens."""
+    lay = w.layout()
+    x = syn.make_inputs(lay.num_tokens, w.heads, w.head_dim, w.hidden, seed=seed, dtype=w.dtype,
+                        heads=list(heads), with_grad_out=True)
+    return lay, x
+
+
+def time_oracle_step(w, lay, x) -> float:
+    import oracle
+    t = time.perf_counter()
+    oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, w.head_dim, w.hidden, eps=1e-6)
+    oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], w.head_dim, w.hidden, eps=1e-6)
+    return time.perf_counter() - t
+
+
+def cpu_threads() -> int:
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return None
+    w = syn.workload(args.workload)
+    lay, x = oracle_sample(w, args.seed)
+    frac = 1.0 / w.heads
+    for _ in range(args.warmup):
+        time_oracle_step(w, lay, x)
+    ts = [time_oracle_step(w, lay, x) for _ in range(args.steps)]
+    sec = statistics.mean(ts)
+    value = lay.num_tokens * frac / sec
+    sample = f"1 of {w.heads} heads of {w.name} (all {lay.num_tokens} tokens), forward+backward per step"
+    return {"metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3 / frac, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "description": w.description, "step": "forward+backward"},
+            "cpu_baseline": {"value": value, "unit": "tokens/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "tokens/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    from paper_2604_08542_gb300 import build as builder
+
+    builder.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = syn.workload(args.workload)
+    lay = w.layout()
+    T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
+    off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
+    x = syn.make_inputs(T, H, D, F, seed=args.seed + 1000 * rank, dtype="bf16", with_grad_out=True)
+    host = {}
+    for n, a in x.items():
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        if n in ("q", "k", "v", "d_o"):
+            t = t.to(torch.bfloat16)
+        host[n] = t.pin_memory()
+    g = {n: t.to(dev, non_blocking=False) for n, t in host.items()}
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(gg):
+        o, ck, wn, _ = layer.forward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr)
+        grads = layer.backward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr, gg["d_o"], ck, wn)
+        return o, grads
+
+    def fwd_only(gg):
+        return layer.forward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr, save_for_backward=False)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed_loop(fn, steps, profile=False):
+        if profile:
+            ttt.scal3r_ttt_profile_enable(layer.handle, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)                       # evict L2 between steps (not timed)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = None
+        if profile:
+            prof = {ttt.KERNEL_KINDS[k]: ttt.scal3r_ttt_profile_read(layer.handle, k) for k in ttt.KERNEL_KINDS}
+            ttt.scal3r_ttt_profile_enable(layer.handle, False)
+        return ms, prof
+
+    for _ in range(args.warmup):
+        step(g)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+
+    clocks = ClockSampler(dev.index if world == 1 else int(os.environ.get("LOCAL_RANK", 0)))
+    clocks.start()
+    ms, prof = timed_loop(lambda: step(g), args.steps, profile=True)
+    clk = clocks.stop()
+    ms_step = sum(ms) / len(ms)
+    t_max = torch.tensor([sum(ms)], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = world * T * args.steps / (total_ms / 1e3)
+
+    # forward only, same workload
+    for _ in range(2):
+        fwd_only(g)
+    fms, fprof = timed_loop(lambda: fwd_only(g), args.steps, profile=True)
+    fwd_value = T / (statistics.mean(fms) / 1e3)
+
+    # end to end through the public API: pinned host inputs in, results out
+    outs_host = {"o": torch.empty_like(host["q"]).pin_memory()}
+    for n in ("q", "k", "v", "lr", "w0"):
+        outs_host["d" + n] = torch.empty_like(host[n]).pin_memory()
+
+    def e2e():
+        gg = {n: t.to(dev, non_blocking=True) for n, t in host.items()}
+        o, grads = step(gg)
+        outs_host["o"].copy_(o, non_blocking=True)
+        for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
+            outs_host[n].copy_(t, non_blocking=True)
+
+    e2e()
+    ems, _ = timed_loop(e2e, max(3, args.steps // 2))
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = sum(t.numel() * t.element_size() for t in outs_host.values())
+    e2e_value = world * T / (statistics.mean(ems) / 1e3)
+
+    # the plain FP32 SIMT path on the same workload
+    fp32 = None
+    if not args.no_fp32 and rank == 0:
+        l32 = ttt.TTT(H, D, F, dtype=torch.float32)
+        g32 = {n: (t.float() if n in ("q", "k", "v", "d_o") else t) for n, t in g.items()}
+
+        def step32():
+            o, ck, wn, _ = l32.forward(g32["q"], g32["k"], g32["v"], g32["lr"], g32["w0"], off, ptr)
+            l32.backward(g32["q"], g32["k"], g32["v"], g32["lr"], g32["w0"], off, ptr, g32["d_o"], ck, wn)
+
+        def fwd32():
+            l32.forward(g32["q"], g32["k"], g32["v"], g32["lr"], g32["w0"], off, ptr, save_for_backward=False)
+
+        step32()
+        torch.cuda.synchronize()
+        m32, _ = timed_loop(step32, args.fp32_steps)
+        f32, _ = timed_loop(fwd32, args.fp32_steps)
+        fp32 = {"fwdbwd_tokens_per_s": T / (statistics.mean(m32) / 1e3),
+                "fwd_tokens_per_s": T / (statistics.mean(f32) / 1e3),
+                "fwdbwd_ms": statistics.mean(m32), "fwd_ms": statistics.mean(f32)}
+        fp32["bf16_speedup_fwdbwd"] = (value / world) / fp32["fwdbwd_tokens_per_s"]
+        fp32["bf16_speedup_fwd"] = fwd_value / fp32["fwd_tokens_per_s"]
+
+    assert layer.status() == 0
+    if rank != 0:
+        return None
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    pk, pk_src = peaks()
+    tot = sum(v["ms"] for v in prof.values())
+    kernels = {}
+    for name, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        kernels[name] = {"launches": v["launches"], "ms_total": v["ms"], "share": v["ms"] / tot,
+                         "avg_ms": v["ms"] / v["launches"]}
+        if v["flops"] > 0:
+            kernels[name]["tflops"] = v["flops"] / (v["ms"] / 1e3) / 1e12
+            kernels[name]["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+    dom = max(kernels, key=lambda n: kernels[n]["ms_total"])
+    dv = prof[dom]
+    per_launch_flops = dv["flops"] / dv["launches"]
+    avg_s = dv["ms"] / dv["launches"] / 1e3
+    achieved = per_launch_flops / avg_s / 1e12 if per_launch_flops > 0 else 0.0
+    simt_dom = (dom == "bwd_sweep")           # the backward sweep runs on CUDA cores (FP32 FMA)
+    if simt_dom:
+        sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+        peak = NUM_SMS_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x median SM clock under load"}
+    else:
+        peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+        roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": f"bf16_tflops ({pk_src})"}
+    # forward sweep roofline as well (the tensor-core kernel of the forward)
+    fs = fprof["fwd_sweep"]
+    fwd_sweep_tflops = fs["flops"] / (fs["ms"] / 1e3) / 1e12 if fs["ms"] > 0 else 0.0
+    gpu_launches = sum(v["launches"] for v in prof.values())
+
+    cpu = None
+    if not args.no_cpu:
+        slay, sx = oracle_sample(w, args.seed)
+        sec = time_oracle_step(w, slay, sx)
+        cpu = {"value": T / H / sec, "unit": "tokens/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"1 of {H} heads of {w.name} (all {T} tokens), one forward+backward, scaled to all heads"}
+
+    return {
+        "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "tokens": T, "heads": H, "head_dim": D,
+                   "hidden": F, "chunk_tokens": w.chunk_frames * w.tokens_per_frame, "sequences": lay.num_seqs,
+                   "step": "forward+backward (all hot-path rows)", "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (q,k,v,d_o 545 MB) and a 256 MB buffer written between steps"},
+        "roofline": roof,
+        "fwd": {"tokens_per_s": fwd_value, "ms": statistics.mean(fms), "sweep_tflops": fwd_sweep_tflops,
+                "sweep_frac_of_bf16_peak": fwd_sweep_tflops / pk.get("bf16_tflops", 1900.0),
+                "sweep_ms_per_step": fs["ms"] / args.steps},
+        "fp32": fp32,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+        "peaks_source": pk_src,
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    import torch
+    if world > 1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

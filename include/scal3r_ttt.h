@@ -147,6 +147,28 @@ int scal3r_ttt_backward(scal3r_ttt_handle* handle,
                         void* dq, void* dk, void* dv, float* dlr, float* dw0,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* Optional per-kernel timing.  While enabled, every kernel launch of
+ * forward/backward calls on this handle is bracketed by two CUDA events
+ * recorded on the call's stream (do not enable it while capturing a graph).
+ * Enabling (1) clears the counters; 0 stops recording. */
+int scal3r_ttt_profile_enable(scal3r_ttt_handle* handle, int32_t enable);
+
+/* Kernel kinds of scal3r_ttt_profile_read. */
+#define SCAL3R_KERNEL_FWD_SWEEP   0  /* forward token sweeps (gradient + apply pieces) */
+#define SCAL3R_KERNEL_FWD_UPDATE  1  /* forward weight update + row normalisation */
+#define SCAL3R_KERNEL_BWD_SWEEP   2  /* backward token sweeps */
+#define SCAL3R_KERNEL_BWD_UPDATE  3  /* backward normalisation adjoint */
+#define SCAL3R_KERNEL_OTHER       4  /* prologue / epilogue kernels */
+
+/* Synchronise on the recorded events and report, for one kernel kind, the
+ * number of launches, their summed device time (ms), and the summed
+ * algorithmic FLOPs and HBM bytes of those launches (token-level model:
+ * forward 12*D*F FLOPs per gradient token-head and 6*D*F per applied
+ * token-head; backward 24*D*F per key token-head and 12*D*F per query
+ * token-head, recomputation excluded). */
+int scal3r_ttt_profile_read(scal3r_ttt_handle* handle, int32_t kind, int64_t* launches,
+                            double* total_ms, double* flops, double* bytes);
+
 /* Synchronise the stream and return the device status word of the last
  * calls on this handle (SCAL3R_ERR_TIMEOUT if a bounded device wait gave
  * up), then clear it. */

@@ -37,9 +37,16 @@ SCAL3R_NORM_ROW_W0 = 0
 SCAL3R_NORM_NONE = 1
 SCAL3R_NORM_UNIT = 2
 
+SCAL3R_KERNEL_FWD_SWEEP = 0
+SCAL3R_KERNEL_FWD_UPDATE = 1
+SCAL3R_KERNEL_BWD_SWEEP = 2
+SCAL3R_KERNEL_BWD_UPDATE = 3
+SCAL3R_KERNEL_OTHER = 4
+KERNEL_KINDS = {0: "fwd_sweep", 1: "fwd_update", 2: "bwd_sweep", 3: "bwd_update", 4: "other"}
+
 EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", "scal3r_ttt_plan",
             "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
-            "scal3r_ttt_get_status")
+            "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read", "scal3r_ttt_get_status")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -83,6 +90,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32,
                                         vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.scal3r_ttt_backward.restype = ctypes.c_int
+    lib.scal3r_ttt_profile_enable.argtypes = [vp, i32]
+    lib.scal3r_ttt_profile_enable.restype = ctypes.c_int
+    lib.scal3r_ttt_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.scal3r_ttt_profile_read.restype = ctypes.c_int
     lib.scal3r_ttt_get_status.argtypes = [vp, vp]
     lib.scal3r_ttt_get_status.restype = ctypes.c_int
     _lib_handle = lib
@@ -155,6 +167,18 @@ def scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, s
     return load_library().scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
                                               len(off) - 1, ptr.ctypes.data, len(ptr) - 1, d_o, w_ckpt, wnorm,
                                               dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_profile_enable(handle: int, enable: bool) -> None:
+    _check(load_library().scal3r_ttt_profile_enable(handle, int(bool(enable))), "scal3r_ttt_profile_enable")
+
+
+def scal3r_ttt_profile_read(handle: int, kind: int) -> dict:
+    n = ctypes.c_int64()
+    ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load_library().scal3r_ttt_profile_read(handle, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                                  ctypes.byref(by)), "scal3r_ttt_profile_read")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
 def scal3r_ttt_get_status(handle: int, stream=None) -> int:

@@ -22,6 +22,12 @@ cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 
 using namespace scal3r;
 
+struct ProfRecord {
+  int kind;
+  cudaEvent_t a, b;
+  double flops, bytes;
+};
+
 struct scal3r_ttt_handle {
   scal3r_ttt_config cfg{};
   Shape shape{};
@@ -30,6 +36,10 @@ struct scal3r_ttt_handle {
   int num_sms = 0;
   Plan plan;
   int* d_status = nullptr;
+  bool prof_on = false;
+  std::vector<ProfRecord> prof;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
 };
 
 namespace {
@@ -78,6 +88,45 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+cudaEvent_t pool_event(scal3r_ttt_handle* hd) {
+  if (hd->pool_used == hd->pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    hd->pool.push_back(e);
+  }
+  return hd->pool[hd->pool_used++];
+}
+
+// Algorithmic work of one sweep launch (token-level model, recompute excluded).
+void sweep_work(const scal3r_ttt_handle* hd, const WorkItem* items, int n, double& flops, double& bytes) {
+  const double DF = (double)hd->shape.D * hd->shape.F;
+  const double es = hd->cfg.dtype == SCAL3R_BF16 ? 2.0 : 4.0;
+  const double D = hd->shape.D;
+  flops = bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    const double t = (double)(items[i].t1 - items[i].t0);
+    switch (items[i].role) {
+      case ROLE_KEY: flops += 12 * DF * t; bytes += t * (2 * D * es + 4); break;
+      case ROLE_APPLY: flops += 6 * DF * t; bytes += t * (2 * D * es); break;
+      case ROLE_BKEY: flops += 24 * DF * t; bytes += t * (4 * D * es + 8); break;
+      case ROLE_BAPPLY: flops += 12 * DF * t; bytes += t * (3 * D * es); break;
+    }
+  }
+}
+
+// Run `fn` (one kernel launch on st), bracketed by events when profiling.
+template <class Fn>
+cudaError_t timed(scal3r_ttt_handle* hd, int kind, double flops, double bytes, cudaStream_t st, Fn fn) {
+  if (!hd->prof_on) return fn();
+  cudaEvent_t a = pool_event(hd), b = pool_event(hd);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, st);
+  cudaError_t e = fn();
+  cudaEventRecord(b, st);
+  hd->prof.push_back({kind, a, b, flops, bytes});
+  return e;
+}
 
 void fill_common(const scal3r_ttt_handle* hd, Params& prm) {
   prm.H = hd->shape.H;
@@ -146,6 +195,7 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
 
 void scal3r_ttt_destroy(scal3r_ttt_handle* hd) {
   if (!hd) return;
+  for (cudaEvent_t e : hd->pool) cudaEventDestroy(e);
   free_plan(hd->plan);
   if (hd->d_status) cudaFree(hd->d_status);
   delete hd;
@@ -197,16 +247,23 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   carve_workspace(pl, sh, false, workspace, prm);
   cudaStream_t st = (cudaStream_t)stream;
   const int chains = pl.S * sh.H;
-  if (launch_prep(prm, chains, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
   for (size_t j = 0; j < pl.steps.size(); ++j) {
     const Step& s = pl.steps[j];
-    cudaError_t e;
-    if (hd->cfg.dtype == SCAL3R_BF16)
-      e = launch_bf16_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st);
-    else
-      e = launch_fp32_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, st);
+    double fl = 0, by = 0;
+    if (hd->prof_on) sweep_work(hd, pl.items.data() + s.item0, s.nitems, fl, by);
+    cudaError_t e = cudaSuccess;
+    if (s.nitems > 0)
+      e = timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st)
+                                            : launch_fp32_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, st);
+      });
     if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
-    if (launch_update(prm, pl.d_updates + s.upd0, s.nupd, (int)j, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
+          return launch_update(prm, pl.d_updates + s.upd0, s.nupd, (int)j, st);
+        }) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
   }
   return SCAL3R_OK;
 }
@@ -249,18 +306,54 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   carve_workspace(pl, sh, true, workspace, prm);
   cudaStream_t st = (cudaStream_t)stream;
   const int chains = pl.S * sh.H;
-  if (launch_bprep(prm, chains, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bprep(prm, chains, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
   for (size_t j = 0; j < pl.bsteps.size(); ++j) {
     const Step& s = pl.bsteps[j];
-    cudaError_t e;
-    if (hd->cfg.dtype == SCAL3R_BF16)
-      e = launch_bf16_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st);
-    else
-      e = launch_fp32_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, st);
+    double fl = 0, by = 0;
+    if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, s.nitems, fl, by);
+    cudaError_t e = cudaSuccess;
+    if (s.nitems > 0)
+      e = timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16
+                   ? launch_bf16_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
+                   : launch_fp32_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, st);
+      });
     if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
-    if (launch_bupdate(prm, pl.d_bupdates + s.upd0, s.nupd, (int)j, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_BWD_UPDATE, 0, 0, st, [&] {
+          return launch_bupdate(prm, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
+        }) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
   }
-  if (launch_bfinal(prm, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bfinal(prm, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_profile_enable(scal3r_ttt_handle* hd, int32_t enable) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  hd->prof.clear();
+  hd->pool_used = 0;
+  hd->prof_on = enable != 0;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_profile_read(scal3r_ttt_handle* hd, int32_t kind, int64_t* launches, double* total_ms,
+                            double* flops, double* bytes) {
+  if (!hd || !launches || !total_ms || !flops || !bytes || kind < 0 || kind > SCAL3R_KERNEL_OTHER)
+    return SCAL3R_ERR_INVALID_ARG;
+  *launches = 0;
+  *total_ms = *flops = *bytes = 0;
+  for (const auto& r : hd->prof) {
+    if (r.kind != kind) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    *launches += 1;
+    *total_ms += ms;
+    *flops += r.flops;
+    *bytes += r.bytes;
+  }
   return SCAL3R_OK;
 }
 

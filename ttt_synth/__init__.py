@@ -24,6 +24,8 @@ tokens per frame; frames are grouped into chunks of a fixed frame count
 from __future__ import annotations
 
 import dataclasses
+import os
+
 import numpy as np
 
 TOKENS_PER_FRAME = 1041
@@ -212,10 +214,21 @@ WORKLOADS = ["fp32_small", "bf16_vggt64", "bf16_fwdbwd_2x32", "bf16_ragged24", "
 
 def _per_head_normals(seed: int, stream: int, T: int, H: int, D: int, heads) -> np.ndarray:
     """[T, len(heads), D] normals; head h draws from its own sub-stream, so a
-    single head can be regenerated without the others."""
+    single head can be regenerated without the others.  Heads are drawn on a
+    thread pool (numpy releases the GIL in its array loops)."""
     out = np.empty((T, len(heads), D), dtype=np.float32)
-    for j, h in enumerate(heads):
+
+    def one(j_h):
+        j, h = j_h
         out[:, j, :] = normal(_stream_key(seed, stream, h), T * D).reshape(T, D)
+
+    if len(heads) > 1 and T * D > 65536:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(max_workers=min(len(heads), os.cpu_count() or 1)) as ex:
+            list(ex.map(one, enumerate(heads)))
+    else:
+        for jh in enumerate(heads):
+            one(jh)
     return out
 
 
