@@ -463,7 +463,7 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   (void)lane;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn_fwd() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     cudaDriverEntryPointQueryResult q;
@@ -478,7 +478,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // [T, H, 64] bf16 token tensor, boxes of 64 x 1 x box_tokens, 128-byte swizzle.
 bool make_token_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_tokens) {
-  auto fn = encode_fn();
+  auto fn = encode_fn_fwd();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)H, (cuuint64_t)T};
   cuuint64_t strides[2] = {(cuuint64_t)D * 2, (cuuint64_t)H * D * 2};
@@ -491,14 +491,7 @@ bool make_token_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_
 
 }  // namespace
 
-cudaError_t launch_simt_bsweep_bf16io(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st);
-
 bool bf16_shape_supported(int Dd, int Ff) { return Dd == D && Ff == F; }
-
-cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
-                               cudaStream_t st) {
-  return launch_simt_bsweep_bf16io(prm, items, n, step, st);
-}
 
 cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
                               cudaStream_t st) {

@@ -24,6 +24,7 @@ namespace scal3r {
 namespace {
 
 constexpr int64_t kAlign = 128;   // piece boundaries fall on 128-token tiles
+constexpr size_t kScratchTileBytes = 3 * 32 * 1024;   // BF16 backward: three 128x128 bf16 images per tile
 
 struct Task {
   int32_t chain, seq, role, chunk;
@@ -102,6 +103,14 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   };
   std::stable_sort(step_items.begin(), step_items.end(),
                    [&](const WorkItem& a, const WorkItem& b) { return cost_of(a) > cost_of(b); });
+  if (backward) {
+    int32_t tiles = 0;
+    for (auto& w : step_items) {
+      w.aux = tiles;
+      tiles += (int32_t)((w.t1 - w.t0 + 127) / 128);
+    }
+    st.scratch_tiles = tiles;
+  }
   items.insert(items.end(), step_items.begin(), step_items.end());
   upds.insert(upds.end(), upd.begin(), upd.end());
   st.nitems = (int32_t)step_items.size();
@@ -201,6 +210,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
       }
     }
     lay_out_step(tasks, sch, num_sms, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
+    p.bscratch_tiles = std::max<int64_t>(p.bscratch_tiles, p.bsteps.back().scratch_tiles);
   }
   p.valid = true;
   plan = std::move(p);
@@ -219,6 +229,7 @@ size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
     b += al(chains * s.P() * sizeof(float));                    // rbuf
     b += al(chains * s.R() * sizeof(float));                    // drho
     b += al(chains * s.P() * sizeof(float));                    // dw0 per chain
+    b += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);   // BF16 backward scratch
   }
   return b;
 }
@@ -241,8 +252,11 @@ void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws
     c += al(chains * s.R() * sizeof(float));
     prm.dw0_chain = (float*)c;
     c += al(chains * s.P() * sizeof(float));
+    prm.scratch = (void*)(((uintptr_t)c + 1023) & ~(uintptr_t)1023);
+    c += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);
   } else {
     prm.rbuf = prm.drho = prm.dw0_chain = nullptr;
+    prm.scratch = nullptr;
   }
 }
 

@@ -28,7 +28,7 @@ struct WorkItem {
   int32_t slot;     // partial-sum slot written by this piece (-1: none)
   int32_t seq;
   int32_t wchunk;   // backward: checkpoint holding the weights (-1: w0)
-  int32_t pad;
+  int32_t aux;      // backward: first scratch tile of this piece within its step
 };
 
 // The update of one chain that closes a chunk step: reduce the partial sums
@@ -48,6 +48,7 @@ struct Step {
   int32_t item0, nitems;  // sweep pieces
   int32_t upd0, nupd;     // updates after the sweep
   int32_t nslots;         // partial slots used in this step
+  int32_t scratch_tiles;  // backward: 128-token scratch tiles of all pieces
 };
 
 struct Plan {
@@ -66,6 +67,7 @@ struct Plan {
   std::vector<UpdateItem> bupdates;
   std::vector<Step> bsteps;
   int32_t bmax_slots = 0;
+  int64_t bscratch_tiles = 0;   // max over backward steps of the 128-token tiles of all pieces
   // device copies (owned by the handle)
   WorkItem* d_items = nullptr;
   UpdateItem* d_updates = nullptr;
@@ -118,6 +120,7 @@ struct Params {
   float* rbuf;      // backward: [chains][P] adjoint R of the next update
   float* drho;      // backward: [chains][R]
   float* dw0_chain; // backward: [chains][P] per-chain dW0 (shared w0 only)
+  void* scratch;    // backward, BF16 path: per-piece factors of the weight adjoints
   int* status;      // handle-owned status word
   // shape and options
   int32_t H, D, F, S;

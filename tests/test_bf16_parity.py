@@ -111,3 +111,27 @@ def test_bf16_backward_matches_oracle():
     errs = {n: rel_inf(to_np(t), rb[n]) for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads)}
     bad = {n: e for n, e in errs.items() if not e <= TOL}
     assert not bad, f"above {TOL}: {bad}; all {errs}"
+
+
+def test_bf16_backward_full_size_sampled_heads():
+    """2 sequences x 32 frames x 1041 tokens, 16 heads, chunk 8 frames (the
+    forward+backward workload); the oracle checks the gradients of two heads."""
+    import torch
+    w = syn.workload("bf16_fwdbwd_2x32")
+    lay = w.layout()
+    x = syn.make_inputs(lay.num_tokens, 16, 64, 128, seed=3, dtype="bf16", with_grad_out=True)
+    g = upload(x, torch.bfloat16)
+    layer = _layer(16)
+    o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    heads = [2, 13]
+    xs = {n: x[n][:, heads] for n in ("q", "k", "v", "lr", "d_o")}
+    rb = oracle.backward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][heads], lay, xs["d_o"], 64, 128, eps=1e-6)
+    errs = {}
+    for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
+        a = to_np(t)
+        errs[n] = rel_inf(a[heads] if n == "dw0" else a[:, heads], rb[n])
+    print("fwdbwd_2x32 gradient errors", errs)
+    bad = {n: e for n, e in errs.items() if not e <= TOL}
+    assert not bad, f"above {TOL}: {bad}; all {errs}"
