@@ -312,7 +312,7 @@ def run_gpu(args, rank: int, world: int):
     per_launch_flops = dv["flops"] / dv["launches"]
     avg_s = dv["ms"] / dv["launches"] / 1e3
     achieved = per_launch_flops / avg_s / 1e12 if per_launch_flops > 0 else 0.0
-    simt_dom = (dom == "bwd_sweep")           # the backward sweep runs on CUDA cores (FP32 FMA)
+    simt_dom = dom not in ("fwd_sweep", "bwd_sweep")   # only the sweeps run on the tensor cores
     if simt_dom:
         sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
         peak = NUM_SMS_GB300 * 128 * 2 * sm_mhz * 1e6 / 1e12
