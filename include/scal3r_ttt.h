@@ -130,6 +130,36 @@ int scal3r_ttt_forward(scal3r_ttt_handle* handle,
                        void* o, float* w_ckpt, float* wnorm, float* w_final,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* The forward pass for callers that cannot allocate device memory.  The
+ * paper has no counterpart of this entry point; it exists for code that may
+ * not call cudaMalloc: code that runs while another thread holds a stream in
+ * global-mode graph capture (cudaMalloc is refused then), plugins inside a
+ * host framework that owns all device memory through its own allocator, and
+ * latency-critical paths that must not enter the driver's allocator.
+ *   It takes the configuration instead of a handle and no workspace; every
+ * other argument means what it means for scal3r_ttt_forward, and the results
+ * are those of scal3r_ttt_forward.  Its scratch (schedule, master weights,
+ * partial sums, status word) is one fixed 32 MiB device array inside the
+ * library, held by every GPU that loads the library until the process exits.
+ *  - The scratch needs 2 x 4P bytes of master weights per chain (sequence x
+ *    head; P = 3*F*D) plus 4P bytes per piece of the busiest chunk step (the
+ *    schedule cuts a step into about one piece per SM): at D=64, F=128 about
+ *    90 chains fit.  A layout whose scratch does not fit returns
+ *    SCAL3R_ERR_WORKSPACE before any work is enqueued.
+ *  - The first call on a device sets up the array's device address; make it
+ *    before any stream capture.
+ *  - All calls on a device share the array and it keeps the last call's
+ *    contents: calls whose GPU work overlaps race.  Order them on one stream.
+ *  - A device-side wait that times out leaves the outputs undefined; this
+ *    entry point does not report it. */
+int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg,
+                               const void* q, const void* k, const void* v,
+                               const float* lr, const float* w0, int64_t w0_seq_stride,
+                               const int64_t* chunk_offsets, int32_t num_chunks,
+                               const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                               void* o, float* w_ckpt, float* wnorm, float* w_final,
+                               void* stream);
+
 /* Backward pass: gradients of sum(d_o * o) through every chunk update.
  *   d_o      [T,H,D] upstream gradient, dtype of q.
  *   w_ckpt, wnorm: as written by the forward on the same inputs.

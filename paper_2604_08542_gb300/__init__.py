@@ -46,7 +46,8 @@ KERNEL_KINDS = {0: "fwd_sweep", 1: "fwd_update", 2: "bwd_sweep", 3: "bwd_update"
 
 EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", "scal3r_ttt_plan",
             "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
-            "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read", "scal3r_ttt_get_status")
+            "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read", "scal3r_ttt_get_status",
+            "scal3r_ttt_forward_noalloc")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -90,6 +91,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32,
                                         vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.scal3r_ttt_backward.restype = ctypes.c_int
+    lib.scal3r_ttt_forward_noalloc.argtypes = [ctypes.POINTER(scal3r_ttt_config), vp, vp, vp, vp, vp, i64, vp,
+                                               i32, vp, i32, vp, vp, vp, vp, vp]
+    lib.scal3r_ttt_forward_noalloc.restype = ctypes.c_int
     lib.scal3r_ttt_profile_enable.argtypes = [vp, i32]
     lib.scal3r_ttt_profile_enable.restype = ctypes.c_int
     lib.scal3r_ttt_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
@@ -167,6 +171,17 @@ def scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, s
     return load_library().scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
                                               len(off) - 1, ptr.ctypes.data, len(ptr) - 1, d_o, w_ckpt, wnorm,
                                               dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_forward_noalloc(cfg: scal3r_ttt_config, q, k, v, lr, w0, w0_seq_stride, chunk_offsets,
+                               seq_chunk_ptr, o, w_ckpt, wnorm, w_final, stream) -> int:
+    """Forward pass for callers that cannot allocate device memory: no handle,
+    no workspace; its scratch is a fixed 32 MiB device array inside the
+    library (see the C header).  Pointers are device pointers (int) or None."""
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    return load_library().scal3r_ttt_forward_noalloc(ctypes.byref(cfg), q, k, v, lr, w0, w0_seq_stride,
+                                                     off.ctypes.data, len(off) - 1, ptr.ctypes.data, len(ptr) - 1,
+                                                     o, w_ckpt, wnorm, w_final, stream)
 
 
 def scal3r_ttt_profile_enable(handle: int, enable: bool) -> None:

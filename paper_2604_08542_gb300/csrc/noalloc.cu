@@ -1,0 +1,162 @@
+// scal3r_ttt_forward_noalloc: the forward pass without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while another thread
+// holds a stream in global-mode graph capture (cudaMalloc is refused then),
+// plugins inside a host framework that owns all device memory through its
+// own allocator, and latency-critical paths that must not enter the driver's
+// allocator (cudaMalloc may synchronise the device).  For them this entry
+// point needs no handle and no workspace: its scratch (schedule tables,
+// master weights, row-norm targets, partial sums, status word) lives in one
+// fixed file-scope device array, kNoallocBytes large, that every GPU which
+// loads the library holds until the process exits.
+//
+// Rules of use:
+//  - The first call on a device looks up the array's device address
+//    (cudaGetSymbolAddress, which may load the module); make that first call
+//    before any stream capture.
+//  - Every call on a device shares the one array and leaves its contents
+//    behind; calls whose GPU work overlaps (different streams, or threads
+//    without ordering) race on it.  Order them on one stream.
+//  - A problem whose scratch does not fit returns SCAL3R_ERR_WORKSPACE
+//    before any work is enqueued.
+#include <mutex>
+
+#include "ttt_internal.h"
+
+namespace scal3r {
+bool fp32_shape_supported(int D, int F);
+bool bf16_shape_supported(int D, int F);
+}  // namespace scal3r
+
+using namespace scal3r;
+
+namespace {
+
+constexpr size_t kNoallocBytes = 32ull << 20;   // 32 MiB
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device (set up once per device).
+int scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return SCAL3R_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCAL3R_ERR_CUDA;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return SCAL3R_OK;
+}
+
+size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const void* q, const void* k,
+                                          const void* v, const float* lr, const float* w0,
+                                          int64_t w0_seq_stride, const int64_t* chunk_offsets, int32_t num_chunks,
+                                          const int32_t* seq_chunk_ptr, int32_t num_seqs, void* o, float* w_ckpt,
+                                          float* wnorm, float* w_final, void* stream) {
+  // configuration (the same checks as scal3r_ttt_init)
+  if (!cfg) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->reserved != 0)
+    return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->weight_norm < 0 || cfg->weight_norm > 2) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
+    return SCAL3R_ERR_UNSUPPORTED;
+  if (cfg->dtype == SCAL3R_BF16 &&
+      (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
+    return SCAL3R_ERR_UNSUPPORTED;
+  int dev = 0, major = 0, minor = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SCAL3R_ERR_NO_DEVICE;
+  if (major != 10 || minor != 3) return SCAL3R_ERR_NO_DEVICE;
+
+  // schedule (host memory only)
+  const Shape sh{cfg->num_heads, cfg->head_dim, cfg->hidden_dim};
+  Plan pl;
+  int rc = build_plan(pl, sh, Schedule{}, sms, chunk_offsets, num_chunks, seq_chunk_ptr, num_seqs);
+  if (rc != SCAL3R_OK) return rc;
+  if (pl.T > 0 && (!q || !k || !v || !lr || !o)) return SCAL3R_ERR_INVALID_ARG;
+  if (!w0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
+  if (w0_seq_stride != 0 && w0_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
+  for (const void* p : {q, k, v, (const void*)o, (const void*)lr, (const void*)w0})
+    if (((uintptr_t)p & 15u) != 0) return SCAL3R_ERR_MISALIGNED;
+
+  // layout of the static array: status | items | updates | wm | rho | partials
+  const size_t chains = (size_t)pl.S * sh.H;
+  const size_t b_status = 256;
+  const size_t b_items = al256(std::max<size_t>(pl.items.size(), 1) * sizeof(WorkItem));
+  const size_t b_upd = al256(std::max<size_t>(pl.updates.size(), 1) * sizeof(UpdateItem));
+  const size_t b_wm = al256(2 * chains * sh.P() * sizeof(float));
+  const size_t b_rho = al256(chains * sh.R() * sizeof(float));
+  const size_t b_part = al256((size_t)std::max(pl.max_slots, 1) * sh.P() * sizeof(float));
+  if (b_status + b_items + b_upd + b_wm + b_rho + b_part > kNoallocBytes) return SCAL3R_ERR_WORKSPACE;
+
+  void* base = nullptr;
+  rc = scratch_address(dev, &base);
+  if (rc != SCAL3R_OK) return rc;
+  char* c = static_cast<char*>(base);
+  int* status = reinterpret_cast<int*>(c);
+  WorkItem* d_items = reinterpret_cast<WorkItem*>(c + b_status);
+  UpdateItem* d_upd = reinterpret_cast<UpdateItem*>(c + b_status + b_items);
+  char* regions = c + b_status + b_items + b_upd;
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the status word must start at zero; every other region is written before it is read
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  if (!pl.items.empty() &&
+      cudaMemcpyAsync(d_items, pl.items.data(), pl.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  if (!pl.updates.empty() &&
+      cudaMemcpyAsync(d_upd, pl.updates.data(), pl.updates.size() * sizeof(UpdateItem), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+
+  Params prm{};
+  prm.H = sh.H;
+  prm.D = sh.D;
+  prm.F = sh.F;
+  prm.S = pl.S;
+  prm.T = pl.T;
+  prm.loss = cfg->loss;
+  prm.norm = cfg->weight_norm;
+  prm.eps = cfg->norm_eps > 0.f ? cfg->norm_eps : 1e-6f;
+  prm.status = status;
+  prm.q = q;
+  prm.k = k;
+  prm.v = v;
+  prm.lr = lr;
+  prm.w0 = w0;
+  prm.w0_seq_stride = w0_seq_stride;
+  prm.o = o;
+  prm.w_ckpt = w_ckpt;
+  prm.wnorm = wnorm;
+  prm.w_final = w_final;
+  prm.wm = reinterpret_cast<float*>(regions);
+  prm.rho = reinterpret_cast<float*>(regions + b_wm);
+  prm.part = reinterpret_cast<float*>(regions + b_wm + b_rho);
+
+  if (launch_prep(prm, (int)chains, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  for (size_t j = 0; j < pl.steps.size(); ++j) {
+    const Step& s = pl.steps[j];
+    cudaError_t e = cudaSuccess;
+    if (s.nitems > 0)
+      e = cfg->dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, d_items + s.item0, s.nitems, (int)j, nullptr, st)
+                                    : launch_fp32_sweep(prm, d_items + s.item0, s.nitems, (int)j, st);
+    if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.nupd > 0 && launch_update(prm, d_upd + s.upd0, s.nupd, (int)j, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+  }
+  return SCAL3R_OK;
+}
