@@ -418,9 +418,10 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
     const uint32_t lane_base = (32u * (warp & 3)) << 16;
     if (mbar_wait(&B.lam_done, 0, abort)) {
       tc_fence_after();
-      float* out = p.part + (size_t)it.slot * 3 * F * D + (size_t)row * D + 32 * half;
+      float* slot = p.part + (size_t)it.slot * 3 * F * D;
+      float* out = slot + (size_t)row * D + 32 * half;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
+      for (int m = 0; m < 2; ++m) {
         float v[16];
 #pragma unroll
         for (int c = 0; c < 32; c += 16) {
@@ -429,6 +430,14 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
 #pragma unroll
           for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
         }
+      }
+      // L2t[f][d] is dL/dW2[d][f]: stored in W2's orientation
+#pragma unroll
+      for (int c = 0; c < 32; c += 16) {
+        float v[16];
+        tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
       }
     }
   }

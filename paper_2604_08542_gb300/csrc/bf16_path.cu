@@ -14,8 +14,9 @@
 //   and write them back to TMEM as bf16 over the columns they just read;
 //   then, with the raw K / V tiles as MN-major B operands,
 //     S1 += G1~^T K, S3 += G3~^T K, S2t += U~^T V      (M 128, N 64, K 16/step)
-//   accumulate in TMEM for the whole piece.  W1 += S1, W3 += S3, W2 += S2t^T
-//   after the fixed-order sum over pieces (update.cu).
+//   accumulate in TMEM for the whole piece and go to the piece's slot packed
+//   like the weights (S2t transposed); W += the fixed-order sum over pieces
+//   (update.cu).
 // APPLY (o = f_W(q), Eq. 4).  Lanes = token (M = 128 tokens per tile):
 //     Zq = Q [W1; W3]^T                                 (M 128, N 256, K 64)
 //   the epilogue (thread = token) forms h = SiLU(zq1) zq3 as bf16 into TMEM,
@@ -202,10 +203,11 @@ __device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& i
   }
   if (!*abort && mbar_wait(&B.s_done, 0, abort)) {
     tc_fence_after();
-    float* out = p.part + (size_t)it.slot * 3 * F * D + (size_t)row * D + 32 * half;
-    const uint32_t mats[3] = {K_S1, K_S3, K_S2T};
+    float* slot = p.part + (size_t)it.slot * 3 * F * D;
+    float* out = slot + (size_t)row * D + 32 * half;
+    const uint32_t mats[2] = {K_S1, K_S3};
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < 2; ++m) {
       float v[16];
 #pragma unroll
       for (int c = 0; c < 32; c += 16) {
@@ -214,6 +216,15 @@ __device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& i
 #pragma unroll
         for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
       }
+    }
+    // S2t[f][d] is the increment of W2[d][f]: stored in W2's orientation
+    // (lanes = consecutive f, so each store instruction is one 128-byte line)
+#pragma unroll
+    for (int c = 0; c < 32; c += 16) {
+      float v[16];
+      tmem_ld16(tb + lane_base + K_S2T + 32 * half + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
     }
   }
 }

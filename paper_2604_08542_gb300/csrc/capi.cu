@@ -17,6 +17,7 @@
 namespace scal3r {
 bool fp32_shape_supported(int D, int F);
 bool bf16_shape_supported(int D, int F);
+bool update_shape_supported(int D, int F);
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 }  // namespace scal3r
 
@@ -228,7 +229,8 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!w0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w0_seq_stride != 0 && w0_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
   if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(o)) return SCAL3R_ERR_MISALIGNED;
-  if (!aligned16(lr) || !aligned16(w0)) return SCAL3R_ERR_MISALIGNED;
+  if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
+  if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
   const size_t need = workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
@@ -282,8 +284,10 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   if (pl.C > 0 && (!w_ckpt || !wnorm)) return SCAL3R_ERR_INVALID_ARG;
   if (!w0 || !dw0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w0_seq_stride != 0 && w0_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
-  for (const void* p : {q, k, v, d_o, (const void*)dq, (const void*)dk, (const void*)dv})
+  for (const void* p : {q, k, v, d_o, (const void*)dq, (const void*)dk, (const void*)dv, (const void*)w_ckpt,
+                        (const void*)w0, (const void*)dw0})
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
+  if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   const size_t need = workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 

@@ -5,7 +5,8 @@
 // memory (rows padded by one float so that lanes reading different rows hit
 // different banks); token tiles and their intermediates sit in shared memory;
 // the per-piece sums over tokens stay in registers, 3*F*D/256 per thread, and
-// are written to the piece's partial-sum slot at the end.
+// are written to the piece's partial-sum slot at the end (packed like the
+// weights: W1 [F][D], W3 [F][D], W2 [D][F]).
 //
 // Forward roles (Sec. 4.2, Eq. 8, Eq. 9, Supp. Sec. A):
 //   KEY    gradient partial of the chunk at the pre-chunk weights W:
@@ -73,12 +74,18 @@ __device__ void store_partial(float* __restrict__ out, const float (&acc)[3][Geo
   using G = Geo<D, F>;
   const int dg = threadIdx.x % 16, fg = threadIdx.x / 16;
 #pragma unroll
-  for (int m = 0; m < 3; ++m)
+  for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int b = 0; b < G::NF; ++b)
 #pragma unroll
       for (int a = 0; a < G::ND; ++a)
         out[(size_t)m * F * D + (size_t)(fg + 16 * b) * D + dg + 16 * a] = acc[m][b][a];
+  // the W2 part in W2's own orientation [D][F]
+#pragma unroll
+  for (int b = 0; b < G::NF; ++b)
+#pragma unroll
+    for (int a = 0; a < G::ND; ++a)
+      out[2 * (size_t)F * D + (size_t)(dg + 16 * a) * F + fg + 16 * b] = acc[2][b][a];
 }
 
 // ---------------------------------------------------------------------------

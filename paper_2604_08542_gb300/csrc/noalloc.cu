@@ -90,8 +90,10 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   if (pl.T > 0 && (!q || !k || !v || !lr || !o)) return SCAL3R_ERR_INVALID_ARG;
   if (!w0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w0_seq_stride != 0 && w0_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
-  for (const void* p : {q, k, v, (const void*)o, (const void*)lr, (const void*)w0})
+  for (const void* p : {q, k, v, (const void*)o, (const void*)lr, (const void*)w0, (const void*)w_ckpt,
+                        (const void*)w_final})
     if (((uintptr_t)p & 15u) != 0) return SCAL3R_ERR_MISALIGNED;
+  if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
 
   // layout of the static array: status | items | updates | wm | rho | partials
   const size_t chains = (size_t)pl.S * sh.H;

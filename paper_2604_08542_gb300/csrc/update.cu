@@ -1,70 +1,88 @@
 // Per-chain kernels that close a chunk step: the weight update of Eq. 8 with
 // the row normalisation, and, in the backward, the adjoint of both.
 //
-// Partial sums written by the sweep kernels use one layout for all three
-// matrices, [F][D] float32 each (rows = hidden unit):
-//   forward  slot = [ A1 | A3 | A2t ] with W1 += A1, W3 += A3, W2 += A2t^T
-//   backward slot = [ L1 | L3 | L2t ] with dL/dW1 += L1, dL/dW3 += L3,
-//                                         dL/dW2 += L2t^T
-// Weights (and the adjoint R) are packed W1 [F][D], W3 [F][D], W2 [D][F].
+// Weights, the adjoint R and every partial-sum slot share one packed layout:
+// W1 [F][D], W3 [F][D], W2 [D][F], row-major float32.
+//   forward slot  = the chunk's weight increment sum of one piece (W += sum)
+//   backward slot = one piece's contribution to dL/dW
 // Row r of the packed weights: r < F is W1 row r, r < 2F is W3 row r-F,
-// otherwise W2 row r-2F (length F).  Row norms are reduced with warp
-// shuffles, one warp per row, in a fixed order.
+// otherwise W2 row r-2F.  Each thread owns four consecutive elements of one
+// row (a float4); a row's L2 norm is reduced over the D/4 (or F/4) lanes that
+// hold it with shuffles, in a fixed order.  Blocks along y cover the rows:
+// first the W1/W3 rows (1024/D per block), then the W2 rows (1024/F per block).
 #include "ttt_internal.h"
 
 namespace scal3r {
 namespace {
 
-constexpr int kWarps = 8;
+constexpr int kThreads = 256;
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+struct RowSlice {
+  bool valid;
+  int r;        // packed row index
+  size_t off;   // offset of this thread's float4 in the packed layout
+  int group;    // lanes per row
+  int c4;       // float4 index inside the row
+};
+
+__device__ __forceinline__ int blocks13(int D, int F) { return (2 * F * D + 1023) / 1024; }
+
+__device__ __forceinline__ RowSlice row_slice(int by, int D, int F) {
+  RowSlice s;
+  const int t = threadIdx.x;
+  const int nb13 = blocks13(D, F);
+  if (by < nb13) {
+    s.group = D / 4;
+    const int row = by * (1024 / D) + t / s.group;
+    s.c4 = t % s.group;
+    s.valid = row < 2 * F;
+    s.r = row;
+    s.off = (size_t)row * D + 4 * s.c4;
+  } else {
+    s.group = F / 4;
+    const int d = (by - nb13) * (1024 / F) + t / s.group;
+    s.c4 = t % s.group;
+    s.valid = d < D;
+    s.r = 2 * F + d;
+    s.off = 2 * (size_t)F * D + (size_t)d * F + 4 * s.c4;
+  }
+  return s;
+}
+
+// Sum over the `group` lanes holding one row (group divides 32).
+__device__ __forceinline__ float group_sum(float x, int group) {
+  for (int o = group >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 
 __device__ __forceinline__ const float* chain_w0(const Params& p, int chain) {
   const int s = chain / p.H, h = chain % p.H;
   return p.w0 + (size_t)s * p.w0_seq_stride + (size_t)h * 3 * p.F * p.D;
 }
 
-// Element j (0 <= j < len) of row r of the packed weights; also the offset of
-// the same element in the [F][D] partial-sum layout.
-__device__ __forceinline__ void row_geom(int r, int F, int D, int& len, size_t& wbase,
-                                         size_t& pbase, int& pstride) {
-  if (r < 2 * F) {          // W1 / W3 row: contiguous in both layouts
-    len = D;
-    wbase = (size_t)r * D;
-    pbase = (size_t)r * D;
-    pstride = 1;
-  } else {                  // W2 row d: column d of the transposed partial
-    const int d = r - 2 * F;
-    len = F;
-    wbase = (size_t)2 * F * D + (size_t)d * F;
-    pbase = (size_t)2 * F * D + d;
-    pstride = D;
-  }
+__device__ __forceinline__ float row_target(const Params& p, float ss) {
+  return (p.norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
 }
 
 // Copy the starting weights of every chain into master buffer 0 and compute
 // the row-norm targets.
-__global__ void prep_kernel(Params p, int chains) {
+__global__ void prep_kernel(Params p) {
   const int chain = blockIdx.x;
-  if (chain >= chains) return;
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
   const float* w0 = chain_w0(p, chain);
-  float* wm = p.wm + (size_t)chain * P;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) wm[i] = w0[i];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int r = warp; r < R; r += blockDim.x / 32) {
-    int len, pstride;
-    size_t wb, pb;
-    row_geom(r, p.F, p.D, len, wb, pb, pstride);
-    float ss = 0.f;
-    for (int j = lane; j < len; j += 32) ss += w0[wb + j] * w0[wb + j];
-    ss = warp_sum(ss);
-    if (lane == 0) p.rho[(size_t)chain * R + r] = (p.norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
-  }
+  float4 w = s.valid ? ld4(w0 + s.off) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s.valid) st4(p.wm + (size_t)chain * P + s.off, w);
+  const float ss = group_sum(dot4(w, w), s.group);
+  if (s.valid && s.c4 == 0) p.rho[(size_t)chain * R + s.r] = row_target(p, ss);
 }
 
 // Forward update of one chain at step `step`:
@@ -72,162 +90,97 @@ __global__ void prep_kernel(Params p, int chains) {
 //   W_{step+1} row = W~ row * rho / max(||W~ row||, eps).
 __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int step) {
   const UpdateItem u = upd[blockIdx.x];
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
   const int chains = p.S * p.H;
   const int h = u.chain % p.H;
   const float* wcur = p.wm + ((size_t)(step & 1) * chains + u.chain) * P;
   float* wnext = p.wm + ((size_t)((step + 1) & 1) * chains + u.chain) * P;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int rows_per_block = (R + gridDim.y - 1) / gridDim.y;
-  const int r0 = blockIdx.y * rows_per_block;
-  const int r1 = min(R, r0 + rows_per_block);
   if (u.chunk < 0) {   // sequence without chunks: w_final = w0
-    if (p.w_final && blockIdx.y == 0) {
-      float* wf = p.w_final + ((size_t)u.seq * p.H + h) * P;
-      for (int i = threadIdx.x; i < P; i += blockDim.x) wf[i] = wcur[i];
-    }
+    if (p.w_final && s.valid) st4(p.w_final + ((size_t)u.seq * p.H + h) * P + s.off, ld4(wcur + s.off));
     return;
   }
-  float* ck = p.w_ckpt ? p.w_ckpt + ((size_t)u.chunk * p.H + h) * P : nullptr;
-  float* wf = (p.w_final && u.last) ? p.w_final + ((size_t)u.seq * p.H + h) * P : nullptr;
-  constexpr int kMaxPer = 8;  // row length <= 256
-  for (int r = r0 + warp; r < r1; r += kWarps) {
-    int len, pstride;
-    size_t wb, pb;
-    row_geom(r, p.F, p.D, len, wb, pb, pstride);
-    float x[kMaxPer];
-    float ss = 0.f;
-#pragma unroll
-    for (int i = 0; i < kMaxPer; ++i) {
-      const int j = lane + 32 * i;
-      x[i] = 0.f;
-      if (j < len) {
-        float a = wcur[wb + j];
-        for (int sl = 0; sl < u.nslots; ++sl)
-          a += p.part[(size_t)(u.slot0 + sl) * P + pb + (size_t)j * pstride];
-        x[i] = a;
-        ss += a * a;
-      }
-    }
-    ss = warp_sum(ss);
-    const float n = sqrtf(ss);
-    float scale = 1.f;
-    if (p.norm != SCAL3R_NORM_NONE) scale = p.rho[(size_t)u.chain * R + r] / fmaxf(n, p.eps);
-#pragma unroll
-    for (int i = 0; i < kMaxPer; ++i) {
-      const int j = lane + 32 * i;
-      if (j < len) {
-        const float w = x[i] * scale;
-        wnext[wb + j] = w;
-        if (ck) ck[wb + j] = w;
-        if (wf) wf[wb + j] = w;
-      }
-    }
-    if (lane == 0 && p.wnorm) p.wnorm[((size_t)u.chunk * p.H + h) * R + r] = n;
+  float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s.valid) {
+    x = ld4(wcur + s.off);
+    for (int sl = 0; sl < u.nslots; ++sl) x = add4(x, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
   }
+  const float n = sqrtf(group_sum(dot4(x, x), s.group));
+  if (!s.valid) return;
+  float scale = 1.f;
+  if (p.norm != SCAL3R_NORM_NONE) scale = p.rho[(size_t)u.chain * R + s.r] / fmaxf(n, p.eps);
+  const float4 w = scale4(x, scale);
+  st4(wnext + s.off, w);
+  if (p.w_ckpt) st4(p.w_ckpt + ((size_t)u.chunk * p.H + h) * P + s.off, w);
+  if (p.w_final && u.last) st4(p.w_final + ((size_t)u.seq * p.H + h) * P + s.off, w);
+  if (p.wnorm && s.c4 == 0) p.wnorm[((size_t)u.chunk * p.H + h) * R + s.r] = n;
 }
 
 // Backward: zero the carried row-norm adjoints and per-chain dW0, compute
 // the row-norm targets from w0.
-__global__ void bprep_kernel(Params p, int chains) {
+__global__ void bprep_kernel(Params p) {
   const int chain = blockIdx.x;
-  if (chain >= chains) return;
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
   const float* w0 = chain_w0(p, chain);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) p.dw0_chain[(size_t)chain * P + i] = 0.f;
-  for (int i = threadIdx.x; i < R; i += blockDim.x) p.drho[(size_t)chain * R + i] = 0.f;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int r = warp; r < R; r += blockDim.x / 32) {
-    int len, pstride;
-    size_t wb, pb;
-    row_geom(r, p.F, p.D, len, wb, pb, pstride);
-    float ss = 0.f;
-    for (int j = lane; j < len; j += 32) ss += w0[wb + j] * w0[wb + j];
-    ss = warp_sum(ss);
-    if (lane == 0) p.rho[(size_t)chain * R + r] = (p.norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
+  const float4 w = s.valid ? ld4(w0 + s.off) : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s.valid) st4(p.dw0_chain + (size_t)chain * P + s.off, make_float4(0.f, 0.f, 0.f, 0.f));
+  const float ss = group_sum(dot4(w, w), s.group);
+  if (s.valid && s.c4 == 0) {
+    p.rho[(size_t)chain * R + s.r] = row_target(p, ss);
+    p.drho[(size_t)chain * R + s.r] = 0.f;
   }
 }
 
 // Backward step closing: Lambda = R_next (unless this is the chain's last
 // chunk) + sum_slots partial.  Then either the VJP of the row normalisation
-// of update `chunk` (R = dL/dW~, written to rbuf; row-norm target adjoint
+// of update `chunk` (R = dL/dW~ into rbuf; the row-norm target's adjoint
 // accumulated in drho) or, for the first chunk, dW0 = Lambda + drho * W0 / rho.
+//   W_row = rho w~ / max(||w~||, eps), w_hat = W_row / rho:
+//   unclamped  R = (rho / ||w~||) (lambda - w_hat (w_hat . lambda))
+//   clamped    R = (rho / eps) lambda;      drho += w_hat . lambda in both
 __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int step) {
+  (void)step;
   const UpdateItem u = upd[blockIdx.x];
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
   const int h = u.chain % p.H;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int rows_per_block = (R + gridDim.y - 1) / gridDim.y;
-  const int r0 = blockIdx.y * rows_per_block;
-  const int r1 = min(R, r0 + rows_per_block);
   float* rb = p.rbuf + (size_t)u.chain * P;
-  const float* wc = (u.chunk >= 0) ? p.w_ckpt_in + ((size_t)u.chunk * p.H + h) * P : nullptr;
-  const float* nrm = (u.chunk >= 0) ? p.wnorm_in + ((size_t)u.chunk * p.H + h) * R : nullptr;
-  const float* w0 = chain_w0(p, u.chain);
-  constexpr int kMaxPer = 8;
-  for (int r = r0 + warp; r < r1; r += kWarps) {
-    int len, pstride;
-    size_t wb, pb;
-    row_geom(r, p.F, p.D, len, wb, pb, pstride);
-    float lam[kMaxPer];
-#pragma unroll
-    for (int i = 0; i < kMaxPer; ++i) {
-      const int j = lane + 32 * i;
-      lam[i] = 0.f;
-      if (j < len) {
-        float a = u.last ? 0.f : rb[wb + j];
-        for (int sl = 0; sl < u.nslots; ++sl)
-          a += p.part[(size_t)(u.slot0 + sl) * P + pb + (size_t)j * pstride];
-        lam[i] = a;
-      }
-    }
-    const float rho = p.rho[(size_t)u.chain * R + r];
-    float* drho = p.drho + (size_t)u.chain * R + r;
-    if (u.first) {
-      // dW0 = Lambda + drho * W0_row / rho   (rho = ||W0 row|| for ROW_W0)
-      float coef = 0.f;
-      if (p.norm == SCAL3R_NORM_ROW_W0 && rho > 0.f) coef = *drho / rho;
-      float* out = p.dw0_chain + (size_t)u.chain * P;
-#pragma unroll
-      for (int i = 0; i < kMaxPer; ++i) {
-        const int j = lane + 32 * i;
-        if (j < len) out[wb + j] = lam[i] + coef * w0[wb + j];
-      }
-      continue;
-    }
-    if (p.norm == SCAL3R_NORM_NONE) {
-#pragma unroll
-      for (int i = 0; i < kMaxPer; ++i) {
-        const int j = lane + 32 * i;
-        if (j < len) rb[wb + j] = lam[i];
-      }
-      continue;
-    }
-    // W_row = rho * w~ / max(||w~||, eps);  w_hat = W_row / rho
-    float what[kMaxPer];
-    float proj = 0.f;
-    const float inv_rho = rho > 0.f ? 1.f / rho : 0.f;
-#pragma unroll
-    for (int i = 0; i < kMaxPer; ++i) {
-      const int j = lane + 32 * i;
-      what[i] = (j < len) ? wc[wb + j] * inv_rho : 0.f;
-      proj += what[i] * lam[i];
-    }
-    proj = warp_sum(proj);
-    const float n = nrm[r];
-    const bool clamped = !(n >= p.eps);
-#pragma unroll
-    for (int i = 0; i < kMaxPer; ++i) {
-      const int j = lane + 32 * i;
-      if (j < len) {
-        float rr;
-        if (clamped) rr = (rho / p.eps) * lam[i];
-        else rr = (rho / n) * (lam[i] - what[i] * proj);
-        rb[wb + j] = rr;
-      }
-    }
-    if (lane == 0 && p.norm == SCAL3R_NORM_ROW_W0) *drho += proj;
+  float4 lam = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s.valid) {
+    if (!u.last) lam = ld4(rb + s.off);
+    for (int sl = 0; sl < u.nslots; ++sl) lam = add4(lam, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
   }
+  const float rho = s.valid ? p.rho[(size_t)u.chain * R + s.r] : 0.f;
+  if (u.first) {
+    if (!s.valid) return;
+    float coef = 0.f;
+    if (p.norm == SCAL3R_NORM_ROW_W0 && rho > 0.f) coef = p.drho[(size_t)u.chain * R + s.r] / rho;
+    const float4 w0 = ld4(chain_w0(p, u.chain) + s.off);
+    st4(p.dw0_chain + (size_t)u.chain * P + s.off,
+        make_float4(lam.x + coef * w0.x, lam.y + coef * w0.y, lam.z + coef * w0.z, lam.w + coef * w0.w));
+    return;
+  }
+  if (p.norm == SCAL3R_NORM_NONE) {
+    if (s.valid) st4(rb + s.off, lam);
+    return;
+  }
+  const float inv_rho = rho > 0.f ? 1.f / rho : 0.f;
+  float4 what = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s.valid) what = scale4(ld4(p.w_ckpt_in + ((size_t)u.chunk * p.H + h) * P + s.off), inv_rho);
+  const float proj = group_sum(dot4(what, lam), s.group);
+  if (!s.valid) return;
+  const float n = p.wnorm_in[((size_t)u.chunk * p.H + h) * R + s.r];
+  float4 out;
+  if (!(n >= p.eps)) {
+    out = scale4(lam, rho / p.eps);
+  } else {
+    const float c = rho / n;
+    out = make_float4(c * (lam.x - what.x * proj), c * (lam.y - what.y * proj), c * (lam.z - what.z * proj),
+                      c * (lam.w - what.w * proj));
+  }
+  st4(rb + s.off, out);
+  if (s.c4 == 0 && p.norm == SCAL3R_NORM_ROW_W0) p.drho[(size_t)u.chain * R + s.r] += proj;
 }
 
 // dw0 from the per-chain results: summed over sequences in order when w0 is
@@ -247,31 +200,38 @@ __global__ void bfinal_kernel(Params p) {
   }
 }
 
+int row_blocks(const Params& p) { return (2 * p.F * p.D + 1023) / 1024 + (p.F * p.D + 1023) / 1024; }
+
 }  // namespace
 
+// Shapes the row kernels handle: D/4 and F/4 powers of two dividing 32.
+bool update_shape_supported(int D, int F) {
+  auto ok = [](int x) { return x % 4 == 0 && x / 4 <= 32 && ((x / 4) & (x / 4 - 1)) == 0; };
+  return ok(D) && ok(F);
+}
+
 cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st) {
-  prep_kernel<<<chains, 256, 0, st>>>(prm, chains);
+  if (chains == 0) return cudaSuccess;
+  prep_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st) {
   if (nupd == 0) return cudaSuccess;
-  dim3 grid(nupd, 4);
-  update_kernel<<<grid, kWarps * 32, 0, st>>>(prm, upd, step);
+  update_kernel<<<dim3(nupd, row_blocks(prm)), kThreads, 0, st>>>(prm, upd, step);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st) {
   if (nupd == 0) return cudaSuccess;
-  // the drho accumulation is per row and each row belongs to one warp
-  dim3 grid(nupd, 4);
-  bupdate_kernel<<<grid, kWarps * 32, 0, st>>>(prm, upd, step);
+  bupdate_kernel<<<dim3(nupd, row_blocks(prm)), kThreads, 0, st>>>(prm, upd, step);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st) {
-  bprep_kernel<<<chains, 256, 0, st>>>(prm, chains);
+  if (chains == 0) return cudaSuccess;
+  bprep_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm);
   return cudaGetLastError();
 }
 
