@@ -25,9 +25,11 @@
 // dzq3, uq) are also written, pre-swizzled, to the item's scratch.
 // Pass B (lanes = hidden unit): the weight-adjoint partial sums over tokens
 //   L1 += dz1^T X, L3 += dz3^T X, L2t += (-lr dp)^T Y   (M 128, N 64, K 16/step)
-// with the scratch rows as MN-major A and the token tiles as MN-major B,
-// written to the item's partial slot.  The scratch of an item is read back by
-// the same CTA right after it was written, so it stays in L2.
+// with the scratch rows as MN-major A and 32-token tiles as MN-major B.
+// A piece is processed in sub-pieces of kBwdSubTiles tiles, pass A then pass
+// B for each; the L accumulators stay in TMEM for the whole piece and go to
+// the piece's partial slot at the end.  Each CTA's scratch holds one
+// sub-piece (384 KB), read back right after it was written, so it stays in L2.
 #include <cudaTypedefs.h>
 
 #include "sm100.cuh"
@@ -42,7 +44,6 @@ constexpr int D = 64;
 constexpr int F = 128;
 constexpr int NTHREADS = 320;
 constexpr int BT = 128;                      // pass A tile (tokens)
-constexpr int HT = 64;                       // pass B half tile (tokens)
 constexpr int NQ = 4;                        // hidden-unit quarters
 constexpr uint32_t QBYTES = 24 * 1024;       // weights of one quarter: 192 rows x 128 B
 constexpr uint32_t WQ_OFF = 0;               // 4 quarters, 96 KB
@@ -50,25 +51,28 @@ constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB)
 constexpr uint32_t SA_OFF = 160 * 1024;      // [128 tok][128] K-major, 2 x 16 KB blocks
 constexpr uint32_t SE_OFF = 192 * 1024;      // [128 tok][64] 16 KB
 constexpr uint32_t PASS_A_BYTES = 208 * 1024;
-constexpr uint32_t B_STAGE = 64 * 1024;      // A1 16 KB, A3 16 KB, A2 16 KB, X 8 KB, Y 8 KB
-constexpr int BSTAGES = 3;
+constexpr int PB_T = 32;                     // pass B tile (tokens)
+constexpr uint32_t PB_STAGE = 32 * 1024;     // A1, A3, A2 (2 x 4 KB each), X 4 KB, Y 4 KB
+constexpr int PB_STAGES = 3;
+constexpr uint32_t PB_OFF = 96 * 1024;       // pass B stages reuse pass A's token/staging region
 constexpr size_t DYN_SMEM = 1024 + PASS_A_BYTES;
 constexpr uint32_t TILE_SCRATCH = 3 * 32 * 1024;   // three [128 tok][128 hidden] bf16 images
 
 // TMEM columns
-constexpr uint32_t A_BUF = 0;       // 2 x 192: G1 (128) | G2 (64)
+constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each, resident for the whole piece
+constexpr uint32_t A_BUF = 192;     // G1 (128) | G2 (64)
 constexpr uint32_t A_DX = 384;      // dk / dq accumulator [tok][64]
 constexpr uint32_t A_DY = 448;      // dv accumulator [tok][64]
-constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each
 
 struct TmaMaps {
-  CUtensorMap x_k, y_v, x_q, y_do;   // boxes of 64 x 1 x 64 tokens
+  CUtensorMap x_k, y_v, x_q, y_do;           // boxes of 64 x 1 x 64 tokens (pass A)
+  CUtensorMap x_k32, y_v32, x_q32, y_do32;   // boxes of 64 x 1 x 32 tokens (pass B)
 };
 
 struct Bars {
-  uint64_t xy_full[2], xy_empty[2], g_full[2], g_free[2];
+  uint64_t xy_full[2], xy_empty[2], g_full, g_free;
   uint64_t st_full, st_free, acc_full, acc_free, eta_full[2], eta_free[2];
-  uint64_t b_full[BSTAGES], b_empty[BSTAGES], lam_done;
+  uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone;
   uint32_t tmem_base;
   int abort_flag;
   float eta_red[2][BT];
@@ -85,6 +89,7 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
 // each row 64 values (d) in the 128-byte swizzled layout.
 __device__ void load_weights(const float* w, const float* r, bool with_r, uint8_t* sm) {
   const int t = threadIdx.x - 64;   // 256 epilogue threads
+#pragma unroll 4
   for (int c = t; c < NQ * 192 * 8; c += 256) {
     const int q = c / (192 * 8);
     const int rr = (c / 8) % 192;
@@ -119,9 +124,11 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
   const int h = it.chain % H;
   const int64_t t0 = it.t0, t1 = it.t1;
   const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
-  const int nq = ntiles * NQ;
+  const int nsub = (ntiles + kBwdSubTiles - 1) / kBwdSubTiles;
   const CUtensorMap* mx = KEY ? &maps.x_k : &maps.x_q;
   const CUtensorMap* my = KEY ? &maps.y_v : &maps.y_do;
+  const CUtensorMap* mx32 = KEY ? &maps.x_k32 : &maps.x_q32;
+  const CUtensorMap* my32 = KEY ? &maps.y_v32 : &maps.y_do32;
   uint8_t* scratch = reinterpret_cast<uint8_t*>(p.scratch) + (size_t)it.aux * TILE_SCRATCH;
   volatile int* abort = &B.abort_flag;
   constexpr uint32_t N1 = KEY ? 128 : 64;
@@ -131,202 +138,201 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
   constexpr uint32_t IDESC_G2 = idesc_bf16(128, N2, false, false);
   constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
   constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
+  const int ew = warp - 2, half = ew >> 2;               // epilogue warps only
+  const uint32_t row = 32u * (warp & 3) + lane;
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  // learning rate of this thread's token, one tile ahead (BKEY epilogue)
+  float eta_next = 0.f;
+  if (KEY && warp >= 2 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
 
-  // ======================= pass A =======================
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int i = 0; i < ntiles; ++i) {
-        const int s = i & 1;
-        if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
-        mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
-        uint8_t* xs = sm + XY_OFF + s * 32768;
-        const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
-        tma_load_3d(xs, mx, &B.xy_full[s], 0, h, tok);
-        tma_load_3d(xs + 8192, mx, &B.xy_full[s], 0, h, tok + 64);
-        tma_load_3d(xs + 16384, my, &B.xy_full[s], 0, h, tok);
-        tma_load_3d(xs + 24576, my, &B.xy_full[s], 0, h, tok + 64);
+  bool aborted = false;
+  for (int sp = 0; sp < nsub; ++sp) {
+    const int ta = sp * kBwdSubTiles;
+    const int te = min(ntiles, ta + kBwdSubTiles);
+    // ======================= pass A on tiles [ta, te) =======================
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int i = ta; i < te; ++i) {
+          const int s = i & 1;
+          if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+          mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
+          uint8_t* xs = sm + XY_OFF + s * 32768;
+          const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
+          tma_load_3d(xs, mx, &B.xy_full[s], 0, h, tok);
+          tma_load_3d(xs + 8192, mx, &B.xy_full[s], 0, h, tok + 64);
+          tma_load_3d(xs + 16384, my, &B.xy_full[s], 0, h, tok);
+          tma_load_3d(xs + 24576, my, &B.xy_full[s], 0, h, tok + 64);
+        }
       }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t wq = smem_u32(sm + WQ_OFF), sa = smem_u32(sm + SA_OFF), se = smem_u32(sm + SE_OFF);
-      auto issue_acc = [&](int m) -> bool {
-        const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
-        if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
-        tc_fence_after();
-        const uint32_t wb = wq + q * QBYTES;
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        const uint32_t wq = smem_u32(sm + WQ_OFF), sa = smem_u32(sm + SA_OFF), se = smem_u32(sm + SE_OFF);
+        auto issue_acc = [&](int m) -> bool {
+          const int i = m / NQ, q = m % NQ;
+          if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
+          if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+          tc_fence_after();
+          const uint32_t wb = wq + q * QBYTES;
 #pragma unroll
-        for (int ks = 0; ks < KDX; ++ks)
-          mma_ss(tb + A_DX, sdesc_sw128(sa + (ks / 4) * 16384 + (ks % 4) * 32, 16, 1024),
-                 sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-        if (KEY) {
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            mma_ss(tb + A_DY, sdesc_sw128(se + ks * 32, 16, 1024), sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024),
-                   IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-        }
-        mma_commit(&B.st_free);
-        if (q == NQ - 1) {
-          mma_commit(&B.acc_full);
-          mma_commit(&B.xy_empty[i & 1]);
-        }
-        return true;
-      };
-      bool ok = true;
-      for (int n = 0; n < nq && ok; ++n) {
-        const int i = n / NQ, q = n % NQ, b = n & 1;
-        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait(&B.g_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
-        const uint32_t wb = wq + q * QBYTES;
-        const uint32_t buf = tb + A_BUF + 192 * b;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          mma_ss(buf, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
-          mma_ss(buf + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 16384 + ks * 32, 16, 1024),
-                 IDESC_G2, ks > 0);
-        }
-        mma_commit(&B.g_full[b]);
-        if (n >= 1) ok = issue_acc(n - 1);
-      }
-      if (ok && !*abort) issue_acc(nq - 1);
-    }
-    __syncwarp();
-  } else {
-    // epilogue: thread = token row of the tile; half selects hidden units
-    // [16*half, 16*half + 16) of every quarter.
-    const int ew = warp - 2, half = ew >> 2;
-    const uint32_t row = 32u * (warp & 3) + lane;
-    const uint32_t lane_base = (32u * (warp & 3)) << 16;
-    uint8_t* sa = sm + SA_OFF;
-    uint8_t* se = sm + SE_OFF;
-    float eta = 0.f, deta = 0.f;
-    for (int n = 0; n < nq; ++n) {
-      const int i = n / NQ, q = n % NQ, b = n & 1;
-      const int64_t tok = t0 + (int64_t)i * BT + row;
-      const bool valid = tok < t1;
-      if (q == 0) {
-        eta = (KEY && valid) ? p.lr[(size_t)tok * H + h] : 0.f;
-        deta = 0.f;
-      }
-      if (!mbar_wait(&B.g_full[b], (n >> 1) & 1, abort)) break;
-      tc_fence_after();
-      const uint32_t buf = tb + lane_base + A_BUF + 192 * b;
-      float o_dz1[16], o_dz3[16], o_g1[16], o_g3[16], o_dpe[16], o_ue[16];
-#pragma unroll
-      for (int sb = 0; sb < 2; ++sb) {
-        const uint32_t c = 16 * half + 8 * sb;
-        float r[6][8];
-        if (KEY) {
-          tmem_ld8x6(buf + c, buf + 32 + c, buf + 64 + c, buf + 96 + c, buf + 128 + c, buf + 160 + c, r);
-        } else {
-          tmem_ld8x6(buf + c, buf + 32 + c, buf + 128 + c, buf + c, buf + c, buf + c, r);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int k = 8 * sb + j;
-          const float z1 = r[0][j], z3 = r[1][j];
-          const float sg = sigmoid_fast(z1);
-          const float a = z1 * sg;
-          const float sp = fmaf(a, 1.f - sg, sg);
+          for (int ks = 0; ks < KDX; ++ks)
+            mma_ss(tb + A_DX, sdesc_sw128(sa + (ks / 4) * 16384 + (ks % 4) * 32, 16, 1024),
+                   sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
           if (KEY) {
-            const float dg1 = r[2][j], dg3 = r[3][j], praw = r[4][j], ndu = r[5][j];
-            const float spp = sg * (1.f - sg) * fmaf(z1, 1.f - 2.f * sg, 2.f);
-            const float u = a * z3;
-            const float pp = -eta * praw;
-            const float du = -eta * ndu;
-            const float dp = dg3 * a + dg1 * z3 * sp;
-            const float da = dg3 * pp + du * z3;
-            o_dz3[k] = dg1 * pp * sp + du * a;
-            o_dz1[k] = dg1 * pp * z3 * spp + da * sp;
-            o_g1[k] = pp * z3 * sp;
-            o_g3[k] = pp * a;
-            o_dpe[k] = -eta * dp;
-            o_ue[k] = -eta * u;
-            deta -= praw * dp + ndu * u;
-          } else {
-            const float du = valid ? r[2][j] : 0.f;
-            o_dz3[k] = du * a;
-            o_dz1[k] = du * z3 * sp;
-            o_dpe[k] = valid ? a * z3 : 0.f;    // uq, the third scratch factor
-            o_g1[k] = o_g3[k] = o_ue[k] = 0.f;
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&B.g_free[b]);
-      // scratch for pass B: hidden unit f = 32q + 16 half + j, block f / 64
-      {
-        const uint32_t f0 = 32u * q + 16u * half;
-        uint8_t* tile = scratch + (size_t)i * TILE_SCRATCH + (f0 / 64) * 16384;
-        const uint32_t c0 = f0 % 64;
-        const float* srcs[3] = {o_dz1, o_dz3, o_dpe};
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          float v0[8], v1[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            v0[j] = srcs[m][j];
-            v1[j] = srcs[m][8 + j];
+            for (int ks = 0; ks < 4; ++ks)
+              mma_ss(tb + A_DY, sdesc_sw128(se + ks * 32, 16, 1024), sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024),
+                     IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
           }
-          *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0)) = pack8(v0);
-          *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0 + 8)) = pack8(v1);
-        }
-      }
-      // staging for the dk/dq (and dv) products of this quarter
-      if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
-      {
-        auto put = [&](uint8_t* base, uint32_t col, const float (&v)[16]) {
-          float v0[8], v1[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            v0[j] = v[j];
-            v1[j] = v[8 + j];
+          mma_commit(&B.st_free);
+          if (q == NQ - 1) {
+            mma_commit(&B.acc_full);
+            mma_commit(&B.xy_empty[i & 1]);
           }
-          *reinterpret_cast<uint4*>(base + sw128_offset(row, col)) = pack8(v0);
-          *reinterpret_cast<uint4*>(base + sw128_offset(row, col + 8)) = pack8(v1);
+          return true;
         };
-        const uint32_t c = 16u * half;
-        put(sa, c, o_dz1);
-        put(sa, 32 + c, o_dz3);
-        if (KEY) {
-          put(sa + 16384, c, o_g1);
-          put(sa + 16384, 32 + c, o_g3);
-          put(se, c, o_dpe);
-          put(se, 32 + c, o_ue);
+        bool ok = true;
+        for (int n = ta * NQ; n < te * NQ && ok; ++n) {
+          const int i = n / NQ, q = n % NQ;
+          if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+          if (!mbar_wait(&B.g_free, (n & 1) ^ 1, abort)) break;
+          tc_fence_after();
+          const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
+          const uint32_t wb = wq + q * QBYTES;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            mma_ss(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
+                   ks > 0);
+            mma_ss(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
+                   sdesc_sw128(wb + 16384 + ks * 32, 16, 1024), IDESC_G2, ks > 0);
+          }
+          mma_commit(&B.g_full);
+          if (n > ta * NQ) ok = issue_acc(n - 1);
         }
+        if (ok && !*abort) issue_acc(te * NQ - 1);
       }
-      fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&B.st_full);
-      if (q == NQ - 1) {
-        // tile finished: read dk/dq and dv, combine the dlr halves
-        if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+    } else {
+      // epilogue: thread = token row of the tile; half selects hidden units
+      // [16*half, 16*half + 16) of every quarter.
+      uint8_t* sa = sm + SA_OFF;
+      uint8_t* se = sm + SE_OFF;
+      float eta = 0.f, deta = 0.f;
+      for (int n = ta * NQ; n < te * NQ; ++n) {
+        const int i = n / NQ, q = n % NQ;
+        const int64_t tok = t0 + (int64_t)i * BT + row;
+        const bool valid = tok < t1;
+        if (q == 0) {
+          eta = KEY ? eta_next : 0.f;
+          deta = 0.f;
+          const int64_t tn = tok + BT;
+          eta_next = (KEY && i + 1 < ntiles && tn < t1) ? p.lr[(size_t)tn * H + h] : 0.f;
+        }
+        if (!mbar_wait(&B.g_full, n & 1, abort)) break;
         tc_fence_after();
-        float v0[16], v1[16];
-        tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
-        tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
-        __nv_bfloat16* dx = reinterpret_cast<__nv_bfloat16*>(KEY ? p.dk : p.dq);
-        if (valid) {
-          uint4* dst = reinterpret_cast<uint4*>(dx + ((size_t)tok * H + h) * D + 32 * half);
-          float a8[8];
+        const uint32_t buf = tb + lane_base + A_BUF;
+        float o_dz1[16], o_dz3[16], o_g1[16], o_g3[16], o_dpe[16], o_ue[16];
+        float r[2][6][8];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) a8[j] = (x < 2) ? v0[8 * x + j] : v1[8 * (x - 2) + j];
-            dst[x] = pack8(a8);
+        for (int sb = 0; sb < 2; ++sb) {
+          const uint32_t c = 16 * half + 8 * sb;
+          if (KEY) {
+            tmem_ld8x6(buf + c, buf + 32 + c, buf + 64 + c, buf + 96 + c, buf + 128 + c, buf + 160 + c, r[sb]);
+          } else {
+            tmem_ld8x6(buf + c, buf + 32 + c, buf + 128 + c, buf + c, buf + c, buf + c, r[sb]);
           }
         }
-        if (KEY) {
-          tmem_ld16(tb + lane_base + A_DY + 32 * half, v0);
-          tmem_ld16(tb + lane_base + A_DY + 32 * half + 16, v1);
+        // the quarter's GEMM results are in registers: release the buffer
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.g_free);
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = 8 * sb + j;
+            const float z1 = r[sb][0][j], z3 = r[sb][1][j];
+            const float sg = sigmoid_fast(z1);
+            const float a = z1 * sg;
+            const float sp = fmaf(a, 1.f - sg, sg);
+            if (KEY) {
+              const float dg1 = r[sb][2][j], dg3 = r[sb][3][j], praw = r[sb][4][j], ndu = r[sb][5][j];
+              const float spp = sg * (1.f - sg) * fmaf(z1, 1.f - 2.f * sg, 2.f);
+              const float u = a * z3;
+              const float pp = -eta * praw;
+              const float du = -eta * ndu;
+              const float dp = dg3 * a + dg1 * z3 * sp;
+              const float da = dg3 * pp + du * z3;
+              o_dz3[k] = dg1 * pp * sp + du * a;
+              o_dz1[k] = dg1 * pp * z3 * spp + da * sp;
+              o_g1[k] = pp * z3 * sp;
+              o_g3[k] = pp * a;
+              o_dpe[k] = -eta * dp;
+              o_ue[k] = -eta * u;
+              deta -= praw * dp + ndu * u;
+            } else {
+              const float du = valid ? r[sb][2][j] : 0.f;
+              o_dz3[k] = du * a;
+              o_dz1[k] = du * z3 * sp;
+              o_dpe[k] = valid ? a * z3 : 0.f;    // uq, the third scratch factor
+              o_g1[k] = o_g3[k] = o_ue[k] = 0.f;
+            }
+          }
+        }
+        // scratch for pass B: hidden unit f = 32q + 16 half + j, block f / 64
+        {
+          const uint32_t f0 = 32u * q + 16u * half;
+          uint8_t* tile = scratch + (size_t)(i - ta) * TILE_SCRATCH + (f0 / 64) * 16384;
+          const uint32_t c0 = f0 % 64;
+          const float* srcs[3] = {o_dz1, o_dz3, o_dpe};
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            float v0[8], v1[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              v0[j] = srcs[m][j];
+              v1[j] = srcs[m][8 + j];
+            }
+            *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0)) = pack8(v0);
+            *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0 + 8)) = pack8(v1);
+          }
+        }
+        // staging for the dk/dq (and dv) products of this quarter
+        if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
+        {
+          auto put = [&](uint8_t* base, uint32_t col, const float (&v)[16]) {
+            float v0[8], v1[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              v0[j] = v[j];
+              v1[j] = v[8 + j];
+            }
+            *reinterpret_cast<uint4*>(base + sw128_offset(row, col)) = pack8(v0);
+            *reinterpret_cast<uint4*>(base + sw128_offset(row, col + 8)) = pack8(v1);
+          };
+          const uint32_t c = 16u * half;
+          put(sa, c, o_dz1);
+          put(sa, 32 + c, o_dz3);
+          if (KEY) {
+            put(sa + 16384, c, o_g1);
+            put(sa + 16384, 32 + c, o_g3);
+            put(se, c, o_dpe);
+            put(se, 32 + c, o_ue);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.st_full);
+        if (q == NQ - 1) {
+          // tile finished: read dk/dq and dv, combine the dlr halves
+          if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+          tc_fence_after();
+          float v0[16], v1[16];
+          tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
+          tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
+          __nv_bfloat16* dx = reinterpret_cast<__nv_bfloat16*>(KEY ? p.dk : p.dq);
           if (valid) {
-            __nv_bfloat16* dv = reinterpret_cast<__nv_bfloat16*>(p.dv);
-            uint4* dst = reinterpret_cast<uint4*>(dv + ((size_t)tok * H + h) * D + 32 * half);
+            uint4* dst = reinterpret_cast<uint4*>(dx + ((size_t)tok * H + h) * D + 32 * half);
             float a8[8];
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
@@ -335,111 +341,137 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
               dst[x] = pack8(a8);
             }
           }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&B.acc_free);
-        if (KEY) {
-          // dlr of the token = sum of the two halves' partials (half 1 hands
-          // its partial to half 0 through shared memory)
-          const int e = i & 1;
-          if (half == 1) {
-            if (!mbar_wait(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
-            B.eta_red[e][row] = deta;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&B.eta_full[e]);
-          } else {
-            if (!mbar_wait(&B.eta_full[e], (i >> 1) & 1, abort)) break;
-            if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&B.eta_free[e]);
+          if (KEY) {
+            tmem_ld16(tb + lane_base + A_DY + 32 * half, v0);
+            tmem_ld16(tb + lane_base + A_DY + 32 * half + 16, v1);
+            if (valid) {
+              __nv_bfloat16* dv = reinterpret_cast<__nv_bfloat16*>(p.dv);
+              uint4* dst = reinterpret_cast<uint4*>(dv + ((size_t)tok * H + h) * D + 32 * half);
+              float a8[8];
+#pragma unroll
+              for (int x = 0; x < 4; ++x) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) a8[j] = (x < 2) ? v0[8 * x + j] : v1[8 * (x - 2) + j];
+                dst[x] = pack8(a8);
+              }
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&B.acc_free);
+          if (KEY) {
+            // dlr of the token = sum of the two halves' partials (half 1 hands
+            // its partial to half 0 through shared memory)
+            const int e = i & 1;
+            if (half == 1) {
+              if (!mbar_wait(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
+              B.eta_red[e][row] = deta;
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&B.eta_full[e]);
+            } else {
+              if (!mbar_wait(&B.eta_full[e], (i >> 1) & 1, abort)) break;
+              if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&B.eta_free[e]);
+            }
           }
         }
       }
+      fence_proxy_async_global();
     }
-    fence_proxy_async_global();
+    // pass A of the sub-piece done (its MMAs completed: the epilogue waited for
+    // the last tile's accumulators); its scratch is visible to bulk copies.
+    // Every thread takes the same decision on an abort.
+    tc_fence_before();
+    const int stop_a = __syncthreads_or(*abort);
+    tc_fence_after();
+    if (stop_a) {
+      aborted = true;
+      break;
+    }
+
+    // ======================= pass B on 32-token tiles of [ta, te) =======================
+    const int jb0 = ta * (BT / PB_T), jb1 = te * (BT / PB_T);
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int j = jb0; j < jb1; ++j) {
+          const int s = j % PB_STAGES;
+          if (!mbar_wait(&B.b_empty[s], ((j / PB_STAGES) & 1) ^ 1, abort)) break;
+          mbar_arrive_expect_tx(&B.b_full[s], PB_STAGE);
+          uint8_t* st = sm + PB_OFF + s * PB_STAGE;
+          const int il = j / (BT / PB_T) - ta, r = j % (BT / PB_T);
+          const uint8_t* src = scratch + (size_t)il * TILE_SCRATCH + r * (PB_T * 128);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            bulk_load(st + m * 8192, src + m * 32768, PB_T * 128, &B.b_full[s]);
+            bulk_load(st + m * 8192 + 4096, src + m * 32768 + 16384, PB_T * 128, &B.b_full[s]);
+          }
+          const int32_t tok = (int32_t)(t0 + (int64_t)j * PB_T);
+          tma_load_3d(st + 24576, mx32, &B.b_full[s], 0, h, tok);
+          tma_load_3d(st + 28672, my32, &B.b_full[s], 0, h, tok);
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        bool ok = true;
+        for (int j = jb0; j < jb1; ++j) {
+          const int s = j % PB_STAGES;
+          if (!mbar_wait(&B.b_full[s], (j / PB_STAGES) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
+            const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
+            mma_ss(tb + B_L, sdesc_sw128(st + ks * 2048, 4096, 1024), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 64, sdesc_sw128(st + 8192 + ks * 2048, 4096, 1024), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 128, sdesc_sw128(st + 16384 + ks * 2048, 4096, 1024), yd, IDESC_LAM, acc);
+          }
+          mma_commit(&B.b_empty[s]);
+        }
+        if (ok) mma_commit(&B.bdone);
+      }
+      __syncwarp();
+    }
+    // everyone waits for the sub-piece's weight-adjoint products before the
+    // next pass A reuses their shared memory
+    mbar_wait(&B.bdone, sp & 1, abort);
+    tc_fence_before();
+    const int stop_b = __syncthreads_or(*abort);
+    tc_fence_after();
+    if (stop_b) {
+      aborted = true;
+      break;
+    }
   }
+  if (aborted || warp < 2) return;
 
-  // all pass-A work done; shared memory is reused by pass B
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (*abort) return;
-
-  // ======================= pass B =======================
-  const int nh = 2 * ntiles;
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int j = 0; j < nh; ++j) {
-        const int s = j % BSTAGES;
-        if (!mbar_wait(&B.b_empty[s], ((j / BSTAGES) & 1) ^ 1, abort)) break;
-        mbar_arrive_expect_tx(&B.b_full[s], B_STAGE);
-        uint8_t* st = sm + s * B_STAGE;
-        const uint8_t* src = scratch + (size_t)(j >> 1) * TILE_SCRATCH + (j & 1) * 8192;
+  // weight-adjoint partial sums of the piece -> its slot (lanes = hidden unit)
+  float* slot = p.part + (size_t)it.slot * 3 * F * D;
+  float* out = slot + (size_t)row * D + 32 * half;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          bulk_load(st + m * 16384, src + m * 32768, 8192, &B.b_full[s]);
-          bulk_load(st + m * 16384 + 8192, src + m * 32768 + 16384, 8192, &B.b_full[s]);
-        }
-        const int32_t tok = (int32_t)(t0 + (int64_t)j * HT);
-        tma_load_3d(st + 49152, mx, &B.b_full[s], 0, h, tok);
-        tma_load_3d(st + 57344, my, &B.b_full[s], 0, h, tok);
-      }
+  for (int m = 0; m < 2; ++m) {
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 32; c += 16) {
+      tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
+      float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
     }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      bool ok = true;
-      for (int j = 0; j < nh; ++j) {
-        const int s = j % BSTAGES;
-        if (!mbar_wait(&B.b_full[s], (j / BSTAGES) & 1, abort)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t st = smem_u32(sm + s * B_STAGE);
+  }
+  // L2t[f][d] is dL/dW2[d][f]: stored in W2's orientation
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
-          const uint64_t xd = sdesc_sw128(st + 49152 + ks * 2048, 1024, 1024);
-          const uint64_t yd = sdesc_sw128(st + 57344 + ks * 2048, 1024, 1024);
-          mma_ss(tb + B_L, sdesc_sw128(st + ks * 2048, 8192, 1024), xd, IDESC_LAM, acc);
-          mma_ss(tb + B_L + 64, sdesc_sw128(st + 16384 + ks * 2048, 8192, 1024), xd, IDESC_LAM, acc);
-          mma_ss(tb + B_L + 128, sdesc_sw128(st + 32768 + ks * 2048, 8192, 1024), yd, IDESC_LAM, acc);
-        }
-        mma_commit(&B.b_empty[s]);
-      }
-      if (ok) mma_commit(&B.lam_done);
-    }
-    __syncwarp();
-  } else {
-    const int ew = warp - 2, half = ew >> 2;
-    const uint32_t row = 32u * (warp & 3) + lane;   // hidden unit f
-    const uint32_t lane_base = (32u * (warp & 3)) << 16;
-    if (mbar_wait(&B.lam_done, 0, abort)) {
-      tc_fence_after();
-      float* slot = p.part + (size_t)it.slot * 3 * F * D;
-      float* out = slot + (size_t)row * D + 32 * half;
+  for (int c = 0; c < 32; c += 16) {
+    float v[16];
+    tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
 #pragma unroll
-      for (int m = 0; m < 2; ++m) {
-        float v[16];
-#pragma unroll
-        for (int c = 0; c < 32; c += 16) {
-          tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
-          float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
-#pragma unroll
-          for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
-        }
-      }
-      // L2t[f][d] is dL/dW2[d][f]: stored in W2's orientation
-#pragma unroll
-      for (int c = 0; c < 32; c += 16) {
-        float v[16];
-        tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
-      }
-    }
+    for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
   }
 }
 
@@ -461,9 +493,9 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.xy_full[i], 1);
       mbar_init(&B.xy_empty[i], 1);
-      mbar_init(&B.g_full[i], 1);
-      mbar_init(&B.g_free[i], 8);
     }
+    mbar_init(&B.g_full, 1);
+    mbar_init(&B.g_free, 8);
     mbar_init(&B.st_full, 8);
     mbar_init(&B.st_free, 1);
     mbar_init(&B.acc_full, 1);
@@ -472,11 +504,11 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
       mbar_init(&B.eta_full[i], 4);
       mbar_init(&B.eta_free[i], 4);
     }
-    for (int i = 0; i < BSTAGES; ++i) {
+    for (int i = 0; i < PB_STAGES; ++i) {
       mbar_init(&B.b_full[i], 1);
       mbar_init(&B.b_empty[i], 1);
     }
-    mbar_init(&B.lam_done, 1);
+    mbar_init(&B.bdone, 1);
     B.abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(key ? &maps.x_k : &maps.x_q);
@@ -513,12 +545,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map64(CUtensorMap* m, const void* base, int64_t T, int H) {
+bool make_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_tokens) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)H, (cuuint64_t)T};
   cuuint64_t strides[2] = {(cuuint64_t)D * 2, (cuuint64_t)H * D * 2};
-  cuuint32_t box[3] = {(cuuint32_t)D, 1, (cuuint32_t)HT};
+  cuuint32_t box[3] = {(cuuint32_t)D, 1, (cuuint32_t)box_tokens};
   cuuint32_t es[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -535,8 +567,10 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
   if (n == 0) return cudaSuccess;
   if (prm.T <= 0 || !prm.scratch) return cudaErrorInvalidValue;
   TmaMaps maps;
-  if (!make_map64(&maps.x_k, prm.k, prm.T, prm.H) || !make_map64(&maps.y_v, prm.v, prm.T, prm.H) ||
-      !make_map64(&maps.x_q, prm.q, prm.T, prm.H) || !make_map64(&maps.y_do, prm.d_o, prm.T, prm.H))
+  if (!make_map(&maps.x_k, prm.k, prm.T, prm.H, 64) || !make_map(&maps.y_v, prm.v, prm.T, prm.H, 64) ||
+      !make_map(&maps.x_q, prm.q, prm.T, prm.H, 64) || !make_map(&maps.y_do, prm.d_o, prm.T, prm.H, 64) ||
+      !make_map(&maps.x_k32, prm.k, prm.T, prm.H, PB_T) || !make_map(&maps.y_v32, prm.v, prm.T, prm.H, PB_T) ||
+      !make_map(&maps.x_q32, prm.q, prm.T, prm.H, PB_T) || !make_map(&maps.y_do32, prm.d_o, prm.T, prm.H, PB_T))
     return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {

@@ -162,11 +162,18 @@ __device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& i
   const int half = ew >> 2;               // tokens [16*half, 16*half + 16) of each tile
   const uint32_t row = 32u * (warp & 3) + lane;   // hidden unit f
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  // lane j < 16 holds the learning rate of token 16*half + j of a tile,
+  // loaded two tiles ahead of its use
+  auto load_eta = [&](int i) -> float {
+    const int64_t tok = t0 + (int64_t)i * KT + 16 * half + lane;
+    return (i < ntiles && lane < 16 && tok < t1) ? p.lr[(size_t)tok * p.H + h] : 0.f;
+  };
+  float eta_a = load_eta(0), eta_b = load_eta(1);
   for (int i = 0; i < ntiles; ++i) {
     const int b = i & 1;
-    const int64_t tok0 = t0 + (int64_t)i * KT + 16 * half;
-    float eta_l = 0.f;
-    if (lane < 16 && tok0 + lane < t1) eta_l = p.lr[(size_t)(tok0 + lane) * p.H + h];
+    const float eta_l = eta_a;
+    eta_a = eta_b;
+    eta_b = load_eta(i + 2);
     if (!mbar_wait(&B.zp_full[b], (i >> 1) & 1, abort)) break;
     tc_fence_after();
     const uint32_t zb = tb + lane_base + K_BUF + 96 * b + 16 * half;
@@ -265,6 +272,7 @@ __device__ void apply_load_weights(const float* w, uint8_t* sm) {
   uint8_t* wb13 = sm;
   uint8_t* wb2 = sm + 2 * F * 128;
   const int t = threadIdx.x - 64;   // epilogue threads 0..255
+#pragma unroll 4
   for (int c = t; c < 2 * F * 8; c += 256) {
     const int r = c >> 3, col = (c & 7) * 8;
     const float* src = w + (size_t)r * D + col;   // W1 rows then W3 rows, contiguous
@@ -274,6 +282,7 @@ __device__ void apply_load_weights(const float* w, uint8_t* sm) {
     *reinterpret_cast<uint4*>(wb13 + sw128_offset(r, col)) = pk;
   }
   const float* w2 = w + 2 * (size_t)F * D;
+#pragma unroll 4
   for (int c = t; c < D * (F / 8); c += 256) {
     const int r = c / (F / 8), col = (c % (F / 8)) * 8;   // row d, first f of the chunk
     const float* src = w2 + (size_t)r * F + col;

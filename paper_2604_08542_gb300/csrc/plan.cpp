@@ -104,10 +104,11 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   std::stable_sort(step_items.begin(), step_items.end(),
                    [&](const WorkItem& a, const WorkItem& b) { return cost_of(a) > cost_of(b); });
   if (backward) {
+    // one sub-piece of scratch per piece (BF16 backward)
     int32_t tiles = 0;
     for (auto& w : step_items) {
       w.aux = tiles;
-      tiles += (int32_t)((w.t1 - w.t0 + 127) / 128);
+      tiles += kBwdSubTiles;
     }
     st.scratch_tiles = tiles;
   }

@@ -76,6 +76,10 @@ struct Plan {
   bool valid = false;
 };
 
+// BF16 backward: 128-token tiles per sub-piece (pass A then pass B); each
+// piece's scratch holds one sub-piece.
+constexpr int kBwdSubTiles = 4;
+
 // Scheduling knobs (the autotuner's search space).
 struct Schedule {
   int32_t ctas_per_wave = 0;   // 0: number of SMs
