@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fwd-only", action="store_true", help="a step is the forward pass alone")
     return ap.parse_args()
 
 
@@ -185,19 +186,30 @@ def run_gpu(args, rank: int, world: int):
     lay = w.layout()
     T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
     off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
-    x = syn.make_inputs(T, H, D, F, seed=args.seed + 1000 * rank, dtype="bf16", with_grad_out=True)
-    host = {}
-    for n, a in x.items():
-        t = torch.from_numpy(np.ascontiguousarray(a))
-        if n in ("q", "k", "v", "d_o"):
-            t = t.to(torch.bfloat16)
-        host[n] = t.pin_memory()
-    g = {n: t.to(dev, non_blocking=False) for n, t in host.items()}
+    # seeded synthetic inputs drawn on the device (the generator's
+    # distributions: q, k, v ~ N(0,1) then L2-normalised per token and head,
+    # lr ~ U[0, 0.1], w0 ~ N(0, 1/64), d_o ~ N(0,1)); pinned host copies feed
+    # the end-to-end loop
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed + 1000 * rank)
+
+    def unit_rows():
+        x = torch.randn((T, H, D), generator=gen, device=dev)
+        return (x / x.norm(dim=-1, keepdim=True)).to(torch.bfloat16)
+
+    g = {"q": unit_rows(), "k": unit_rows(), "v": unit_rows(),
+         "lr": torch.rand((T, H), generator=gen, device=dev) * 0.1,
+         "w0": torch.randn((H, 3 * F * D), generator=gen, device=dev) * 0.125,
+         "d_o": torch.randn((T, H, D), generator=gen, device=dev).to(torch.bfloat16)}
+    host = {n: t.cpu().pin_memory() for n, t in g.items()}
     layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
-    def step(gg):
+    def step(gg, lay_=None):
+        if args.fwd_only:
+            o, _, _, _ = layer.forward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr, save_for_backward=False)
+            return o, ()
         o, ck, wn, _ = layer.forward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr)
         grads = layer.backward(gg["q"], gg["k"], gg["v"], gg["lr"], gg["w0"], off, ptr, gg["d_o"], ck, wn)
         return o, grads
@@ -244,6 +256,14 @@ def run_gpu(args, rank: int, world: int):
     total_ms = float(t_max.item())
     value = world * T * args.steps / (total_ms / 1e3)
 
+    # the same step replayed from CUDA graphs (no per-launch events)
+    layer.set_graph_mode(True)
+    for _ in range(2):
+        step(g)
+    gms, _ = timed_loop(lambda: step(g), args.steps)
+    graph_value = world * T / (statistics.mean(gms) / 1e3)
+    layer.set_graph_mode(False)
+
     # forward only, same workload
     for _ in range(2):
         fwd_only(g)
@@ -252,11 +272,13 @@ def run_gpu(args, rank: int, world: int):
 
     # end to end through the public API: pinned host inputs in, results out
     outs_host = {"o": torch.empty_like(host["q"]).pin_memory()}
-    for n in ("q", "k", "v", "lr", "w0"):
-        outs_host["d" + n] = torch.empty_like(host[n]).pin_memory()
+    if not args.fwd_only:
+        for n in ("q", "k", "v", "lr", "w0"):
+            outs_host["d" + n] = torch.empty_like(host[n]).pin_memory()
+    e2e_inputs = [n for n in host if not (args.fwd_only and n == "d_o")]
 
     def e2e():
-        gg = {n: t.to(dev, non_blocking=True) for n, t in host.items()}
+        gg = {n: host[n].to(dev, non_blocking=True) for n in e2e_inputs}
         o, grads = step(gg)
         outs_host["o"].copy_(o, non_blocking=True)
         for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
@@ -264,13 +286,13 @@ def run_gpu(args, rank: int, world: int):
 
     e2e()
     ems, _ = timed_loop(e2e, max(3, args.steps // 2))
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    h2d = sum(host[n].numel() * host[n].element_size() for n in e2e_inputs)
     d2h = sum(t.numel() * t.element_size() for t in outs_host.values())
     e2e_value = world * T / (statistics.mean(ems) / 1e3)
 
     # the plain FP32 SIMT path on the same workload
     fp32 = None
-    if not args.no_fp32 and rank == 0:
+    if not args.no_fp32 and rank == 0 and not args.fwd_only:
         l32 = ttt.TTT(H, D, F, dtype=torch.float32)
         g32 = {n: (t.float() if n in ("q", "k", "v", "d_o") else t) for n, t in g.items()}
 
@@ -341,13 +363,16 @@ def run_gpu(args, rank: int, world: int):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": w.name, "description": w.description, "tokens": T, "heads": H, "head_dim": D,
                    "hidden": F, "chunk_tokens": w.chunk_frames * w.tokens_per_frame, "sequences": lay.num_seqs,
-                   "step": "forward+backward (all hot-path rows)", "parallelism": f"replicas{world}",
+                   "step": "forward only" if args.fwd_only else "forward+backward (all hot-path rows)",
+                   "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (q,k,v,d_o 545 MB) and a 256 MB buffer written between steps"},
         "roofline": roof,
         "fwd": {"tokens_per_s": fwd_value, "ms": statistics.mean(fms), "sweep_tflops": fwd_sweep_tflops,
                 "sweep_frac_of_bf16_peak": fwd_sweep_tflops / pk.get("bf16_tflops", 1900.0),
                 "sweep_ms_per_step": fs["ms"] / args.steps},
         "fp32": fp32,
+        "graph": {"tokens_per_s": graph_value, "ms_per_step": statistics.mean(gms),
+                  "note": "the same step replayed from CUDA graphs captured by the library"},
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -177,6 +177,47 @@ int scal3r_ttt_backward(scal3r_ttt_handle* handle,
                         void* dq, void* dk, void* dv, float* dlr, float* dw0,
                         void* workspace, size_t workspace_bytes, void* stream);
 
+/* How each chunk step is cut into per-CTA pieces (the autotuner's search
+ * space).  Chunk lengths are part of the method and are never tuned. */
+typedef struct scal3r_ttt_schedule {
+  int32_t fwd_waves;        /* forward: pieces per chunk step ~ fwd_waves x SM count (1..8) */
+  int32_t bwd_waves;        /* backward: same for the backward steps (1..8) */
+  int32_t min_piece_tokens; /* smallest piece, tokens (>= 128) */
+  float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0) */
+  float   bwd_key_cost;     /* backward: cost of an update-VJP token vs an apply-VJP token (> 0) */
+  int32_t reserved;         /* must be 0 */
+} scal3r_ttt_schedule;
+
+/* Replace / read the handle's schedule.  Setting it drops the cached plan
+ * (the next call re-plans; do it outside stream capture). */
+int scal3r_ttt_set_schedule(scal3r_ttt_handle* handle, const scal3r_ttt_schedule* sch);
+int scal3r_ttt_get_schedule(const scal3r_ttt_handle* handle, scal3r_ttt_schedule* sch);
+
+/* Graph mode (default off).  When on, scal3r_ttt_forward / scal3r_ttt_backward
+ * record their launch sequence into a CUDA graph the first time they see a
+ * given layout and argument set, and afterwards replay it with one
+ * cudaGraphLaunch on the caller's stream; a new argument set with the same
+ * layout updates the executable graph in place.  The recording itself is
+ * done on an internal stream, so the caller's stream may be the legacy
+ * default stream.  Profiling (scal3r_ttt_profile_enable) bypasses the graph. */
+int scal3r_ttt_set_graph_mode(scal3r_ttt_handle* handle, int32_t enable);
+
+/* Autotuner: time candidate schedules on the given inputs and keep the
+ * fastest in the handle (and return it in *best, with its time in *best_ms).
+ * with_backward = 0 tunes the forward alone; 1 tunes forward + backward
+ * (then d_o, dq, dk, dv, dlr, dw0 must be given and are overwritten).  The
+ * forward outputs o, w_ckpt, wnorm are overwritten.  The tuner allocates and
+ * frees its own workspace; it synchronises the stream. */
+int scal3r_ttt_autotune(scal3r_ttt_handle* handle,
+                        const void* q, const void* k, const void* v,
+                        const float* lr, const float* w0, int64_t w0_seq_stride,
+                        const int64_t* chunk_offsets, int32_t num_chunks,
+                        const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                        void* o, float* w_ckpt, float* wnorm,
+                        const void* d_o, void* dq, void* dk, void* dv, float* dlr, float* dw0,
+                        int32_t with_backward, void* stream,
+                        scal3r_ttt_schedule* best, float* best_ms);
+
 /* Optional per-kernel timing.  While enabled, every kernel launch of
  * forward/backward calls on this handle is bracketed by two CUDA events
  * recorded on the call's stream (do not enable it while capturing a graph).

@@ -46,8 +46,9 @@ KERNEL_KINDS = {0: "fwd_sweep", 1: "fwd_update", 2: "bwd_sweep", 3: "bwd_update"
 
 EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", "scal3r_ttt_plan",
             "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
-            "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read", "scal3r_ttt_get_status",
-            "scal3r_ttt_forward_noalloc")
+            "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
+            "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
+            "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -55,6 +56,15 @@ class scal3r_ttt_config(ctypes.Structure):
                 ("hidden_dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("loss", ctypes.c_int32), ("weight_norm", ctypes.c_int32),
                 ("norm_eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class scal3r_ttt_schedule(ctypes.Structure):
+    _fields_ = [("fwd_waves", ctypes.c_int32), ("bwd_waves", ctypes.c_int32),
+                ("min_piece_tokens", ctypes.c_int32), ("fwd_key_cost", ctypes.c_float),
+                ("bwd_key_cost", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 class Scal3rError(RuntimeError):
@@ -91,6 +101,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32,
                                         vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     lib.scal3r_ttt_backward.restype = ctypes.c_int
+    lib.scal3r_ttt_set_schedule.argtypes = [vp, ctypes.POINTER(scal3r_ttt_schedule)]
+    lib.scal3r_ttt_set_schedule.restype = ctypes.c_int
+    lib.scal3r_ttt_get_schedule.argtypes = [vp, ctypes.POINTER(scal3r_ttt_schedule)]
+    lib.scal3r_ttt_get_schedule.restype = ctypes.c_int
+    lib.scal3r_ttt_set_graph_mode.argtypes = [vp, i32]
+    lib.scal3r_ttt_set_graph_mode.restype = ctypes.c_int
+    lib.scal3r_ttt_autotune.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp,
+                                        vp, vp, i32, vp, ctypes.POINTER(scal3r_ttt_schedule),
+                                        ctypes.POINTER(ctypes.c_float)]
+    lib.scal3r_ttt_autotune.restype = ctypes.c_int
     lib.scal3r_ttt_forward_noalloc.argtypes = [ctypes.POINTER(scal3r_ttt_config), vp, vp, vp, vp, vp, i64, vp,
                                                i32, vp, i32, vp, vp, vp, vp, vp]
     lib.scal3r_ttt_forward_noalloc.restype = ctypes.c_int
@@ -171,6 +191,33 @@ def scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, s
     return load_library().scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
                                               len(off) - 1, ptr.ctypes.data, len(ptr) - 1, d_o, w_ckpt, wnorm,
                                               dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_set_schedule(handle: int, sch: scal3r_ttt_schedule) -> None:
+    _check(load_library().scal3r_ttt_set_schedule(handle, ctypes.byref(sch)), "scal3r_ttt_set_schedule")
+
+
+def scal3r_ttt_get_schedule(handle: int) -> scal3r_ttt_schedule:
+    sch = scal3r_ttt_schedule()
+    _check(load_library().scal3r_ttt_get_schedule(handle, ctypes.byref(sch)), "scal3r_ttt_get_schedule")
+    return sch
+
+
+def scal3r_ttt_set_graph_mode(handle: int, enable: bool) -> None:
+    _check(load_library().scal3r_ttt_set_graph_mode(handle, int(bool(enable))), "scal3r_ttt_set_graph_mode")
+
+
+def scal3r_ttt_autotune(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, seq_chunk_ptr, o, w_ckpt, wnorm,
+                        d_o, dq, dk, dv, dlr, dw0, with_backward, stream):
+    """Raw entry point; returns (schedule, best_ms)."""
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    best = scal3r_ttt_schedule()
+    ms = ctypes.c_float()
+    _check(load_library().scal3r_ttt_autotune(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
+                                              len(off) - 1, ptr.ctypes.data, len(ptr) - 1, o, w_ckpt, wnorm, d_o,
+                                              dq, dk, dv, dlr, dw0, int(bool(with_backward)), stream,
+                                              ctypes.byref(best), ctypes.byref(ms)), "scal3r_ttt_autotune")
+    return best, ms.value
 
 
 def scal3r_ttt_forward_noalloc(cfg: scal3r_ttt_config, q, k, v, lr, w0, w0_seq_stride, chunk_offsets,

@@ -561,6 +561,10 @@ bool make_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_tokens
 
 size_t bf16_bwd_scratch_tile_bytes() { return TILE_SCRATCH; }
 
+cudaError_t prepare_bf16_backward() {
+  return cudaFuncSetAttribute(bf16_bsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN_SMEM);
+}
+
 cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
                                cudaStream_t st) {
   (void)step;
@@ -572,13 +576,6 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
       !make_map(&maps.x_k32, prm.k, prm.T, prm.H, PB_T) || !make_map(&maps.y_v32, prm.v, prm.T, prm.H, PB_T) ||
       !make_map(&maps.x_q32, prm.q, prm.T, prm.H, PB_T) || !make_map(&maps.y_do32, prm.d_o, prm.T, prm.H, PB_T))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bf16_bsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   bf16_bsweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items);
   return cudaGetLastError();
 }

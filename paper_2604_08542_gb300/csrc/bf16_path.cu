@@ -513,6 +513,10 @@ bool make_token_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_
 
 bool bf16_shape_supported(int Dd, int Ff) { return Dd == D && Ff == F; }
 
+cudaError_t prepare_bf16_forward() {
+  return cudaFuncSetAttribute(bf16_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN_SMEM);
+}
+
 cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, int step, const void*,
                               cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -521,12 +525,6 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, i
   if (!make_token_map(&maps.q, prm.q, prm.T, prm.H, QT) || !make_token_map(&maps.k, prm.k, prm.T, prm.H, KT) ||
       !make_token_map(&maps.v, prm.v, prm.T, prm.H, KT))
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bf16_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DYN_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   bf16_sweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items, step);
   return cudaGetLastError();
 }

@@ -19,6 +19,15 @@ bool fp32_shape_supported(int D, int F);
 bool bf16_shape_supported(int D, int F);
 bool update_shape_supported(int D, int F);
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
+cudaError_t prepare_fp32();
+cudaError_t prepare_bf16_forward();
+cudaError_t prepare_bf16_backward();
+cudaError_t prepare_kernels() {
+  cudaError_t e = prepare_fp32();
+  if (e == cudaSuccess) e = prepare_bf16_forward();
+  if (e == cudaSuccess) e = prepare_bf16_backward();
+  return e;
+}
 }  // namespace scal3r
 
 using namespace scal3r;
@@ -29,6 +38,12 @@ struct ProfRecord {
   double flops, bytes;
 };
 
+struct GraphSlot {
+  bool valid = false;
+  uint64_t key = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct scal3r_ttt_handle {
   scal3r_ttt_config cfg{};
   Shape shape{};
@@ -36,11 +51,15 @@ struct scal3r_ttt_handle {
   int device = 0;
   int num_sms = 0;
   Plan plan;
+  uint64_t plan_gen = 0;        // bumped whenever the plan changes
   int* d_status = nullptr;
   bool prof_on = false;
   std::vector<ProfRecord> prof;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  bool graph_on = false;
+  cudaStream_t capture_stream = nullptr;
+  GraphSlot gfwd, gbwd;
 };
 
 namespace {
@@ -85,10 +104,64 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
   }
   free_plan(hd->plan);
   hd->plan = std::move(np);
+  hd->plan_gen++;
   return SCAL3R_OK;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+void drop_graph(GraphSlot& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g = GraphSlot{};
+}
+
+// Record `enqueue` (a sequence of launches on the given stream) into a graph
+// on the handle's capture stream, keep it in `slot` under `key` (updating an
+// existing executable graph in place when possible) and launch it on `st`.
+template <class Fn>
+int run_graph(scal3r_ttt_handle* hd, GraphSlot& slot, uint64_t key, cudaStream_t st, Fn enqueue) {
+  if (!(slot.valid && slot.key == key)) {
+    if (cudaStreamBeginCapture(hd->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
+    int rc = enqueue(hd->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(hd->capture_stream, &graph);
+    if (rc != SCAL3R_OK || e != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc != SCAL3R_OK ? rc : SCAL3R_ERR_CUDA;
+    }
+    bool updated = false;
+    if (slot.valid) {
+      cudaGraphExecUpdateResultInfo info;
+      updated = cudaGraphExecUpdate(slot.exec, graph, &info) == cudaSuccess;
+      if (!updated) {
+        cudaGetLastError();
+        drop_graph(slot);
+      }
+    }
+    if (!updated) {
+      cudaGraphExec_t exec = nullptr;
+      if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return SCAL3R_ERR_CUDA;
+      }
+      slot.exec = exec;
+    }
+    cudaGraphDestroy(graph);
+    slot.valid = true;
+    slot.key = key;
+  }
+  return cudaGraphLaunch(slot.exec, st) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
 
 cudaEvent_t pool_event(scal3r_ttt_handle* hd) {
   if (hd->pool_used == hd->pool.size()) {
@@ -141,6 +214,81 @@ void fill_common(const scal3r_ttt_handle* hd, Params& prm) {
   prm.status = hd->d_status;
 }
 
+// The forward launch sequence on `st` (see the file comment).
+int enqueue_forward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) {
+  const Plan& pl = hd->plan;
+  const int chains = pl.S * hd->shape.H;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  for (size_t j = 0; j < pl.steps.size(); ++j) {
+    const Step& s = pl.steps[j];
+    double fl = 0, by = 0;
+    if (hd->prof_on) sweep_work(hd, pl.items.data() + s.item0, s.nitems, fl, by);
+    cudaError_t e = cudaSuccess;
+    if (s.nitems > 0)
+      e = timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st)
+                                            : launch_fp32_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, st);
+      });
+    if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
+          return launch_update(prm, pl.d_updates + s.upd0, s.nupd, (int)j, st);
+        }) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
+  }
+  return SCAL3R_OK;
+}
+
+// The backward launch sequence on `st`.
+int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) {
+  const Plan& pl = hd->plan;
+  const int chains = pl.S * hd->shape.H;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bprep(prm, chains, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  for (size_t j = 0; j < pl.bsteps.size(); ++j) {
+    const Step& s = pl.bsteps[j];
+    double fl = 0, by = 0;
+    if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, s.nitems, fl, by);
+    cudaError_t e = cudaSuccess;
+    if (s.nitems > 0)
+      e = timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16
+                   ? launch_bf16_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
+                   : launch_fp32_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, st);
+      });
+    if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_BWD_UPDATE, 0, 0, st, [&] {
+          return launch_bupdate(prm, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
+        }) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
+  }
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bfinal(prm, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
+bool valid_schedule(const scal3r_ttt_schedule& s) {
+  return s.fwd_waves >= 1 && s.fwd_waves <= 8 && s.bwd_waves >= 1 && s.bwd_waves <= 8 &&
+         s.min_piece_tokens >= 128 && s.fwd_key_cost > 0.f && s.bwd_key_cost > 0.f && s.reserved == 0;
+}
+
+void to_internal(const scal3r_ttt_schedule& s, Schedule& o) {
+  o.fwd_waves = s.fwd_waves;
+  o.bwd_waves = s.bwd_waves;
+  o.min_tokens = s.min_piece_tokens;
+  o.key_cost = s.fwd_key_cost;
+  o.bkey_cost = s.bwd_key_cost;
+}
+
+void to_public(const Schedule& o, scal3r_ttt_schedule& s) {
+  s.fwd_waves = o.fwd_waves;
+  s.bwd_waves = o.bwd_waves;
+  s.min_piece_tokens = o.min_tokens;
+  s.fwd_key_cost = o.key_cost;
+  s.bwd_key_cost = o.bkey_cost;
+  s.reserved = 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -180,13 +328,16 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return SCAL3R_ERR_NO_DEVICE;
   if (major != 10 || minor != 3) return SCAL3R_ERR_NO_DEVICE;
+  if (prepare_kernels() != cudaSuccess) return SCAL3R_ERR_CUDA;
   auto* hd = new scal3r_ttt_handle();
   hd->cfg = *cfg;
   hd->shape = Shape{cfg->num_heads, cfg->head_dim, cfg->hidden_dim};
   hd->device = dev;
   hd->num_sms = sms;
   if (cudaMalloc((void**)&hd->d_status, sizeof(int)) != cudaSuccess ||
-      cudaMemset(hd->d_status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(hd->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&hd->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (hd->d_status) cudaFree(hd->d_status);
     delete hd;
     return SCAL3R_ERR_CUDA;
   }
@@ -197,6 +348,9 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
 void scal3r_ttt_destroy(scal3r_ttt_handle* hd) {
   if (!hd) return;
   for (cudaEvent_t e : hd->pool) cudaEventDestroy(e);
+  drop_graph(hd->gfwd);
+  drop_graph(hd->gbwd);
+  if (hd->capture_stream) cudaStreamDestroy(hd->capture_stream);
   free_plan(hd->plan);
   if (hd->d_status) cudaFree(hd->d_status);
   delete hd;
@@ -234,7 +388,8 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   const size_t need = workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
-  Params prm{};
+  Params prm;
+  std::memset(&prm, 0, sizeof(prm));   // the graph key hashes the whole struct
   fill_common(hd, prm);
   prm.q = q;
   prm.k = k;
@@ -248,26 +403,11 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   prm.w_final = w_final;
   carve_workspace(pl, sh, false, workspace, prm);
   cudaStream_t st = (cudaStream_t)stream;
-  const int chains = pl.S * sh.H;
-  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
-    return SCAL3R_ERR_CUDA;
-  for (size_t j = 0; j < pl.steps.size(); ++j) {
-    const Step& s = pl.steps[j];
-    double fl = 0, by = 0;
-    if (hd->prof_on) sweep_work(hd, pl.items.data() + s.item0, s.nitems, fl, by);
-    cudaError_t e = cudaSuccess;
-    if (s.nitems > 0)
-      e = timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
-        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st)
-                                            : launch_fp32_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, st);
-      });
-    if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
-    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
-          return launch_update(prm, pl.d_updates + s.upd0, s.nupd, (int)j, st);
-        }) != cudaSuccess)
-      return SCAL3R_ERR_CUDA;
+  if (hd->graph_on && !hd->prof_on) {
+    uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 1);
+    return run_graph(hd, hd->gfwd, key, st, [&](cudaStream_t cs) { return enqueue_forward(hd, prm, cs); });
   }
-  return SCAL3R_OK;
+  return enqueue_forward(hd, prm, st);
 }
 
 int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
@@ -291,7 +431,8 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   const size_t need = workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
-  Params prm{};
+  Params prm;
+  std::memset(&prm, 0, sizeof(prm));   // the graph key hashes the whole struct
   fill_common(hd, prm);
   prm.q = q;
   prm.k = k;
@@ -309,28 +450,148 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   prm.dw0 = dw0;
   carve_workspace(pl, sh, true, workspace, prm);
   cudaStream_t st = (cudaStream_t)stream;
-  const int chains = pl.S * sh.H;
-  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bprep(prm, chains, st); }) != cudaSuccess)
-    return SCAL3R_ERR_CUDA;
-  for (size_t j = 0; j < pl.bsteps.size(); ++j) {
-    const Step& s = pl.bsteps[j];
-    double fl = 0, by = 0;
-    if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, s.nitems, fl, by);
-    cudaError_t e = cudaSuccess;
-    if (s.nitems > 0)
-      e = timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fl, by, st, [&] {
-        return hd->cfg.dtype == SCAL3R_BF16
-                   ? launch_bf16_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
-                   : launch_fp32_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, st);
-      });
-    if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
-    if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_BWD_UPDATE, 0, 0, st, [&] {
-          return launch_bupdate(prm, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
-        }) != cudaSuccess)
-      return SCAL3R_ERR_CUDA;
+  if (hd->graph_on && !hd->prof_on) {
+    uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 2);
+    return run_graph(hd, hd->gbwd, key, st, [&](cudaStream_t cs) { return enqueue_backward(hd, prm, cs); });
   }
-  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bfinal(prm, st); }) != cudaSuccess)
-    return SCAL3R_ERR_CUDA;
+  return enqueue_backward(hd, prm, st);
+}
+
+int scal3r_ttt_set_schedule(scal3r_ttt_handle* hd, const scal3r_ttt_schedule* sch) {
+  if (!hd || !sch || !valid_schedule(*sch)) return SCAL3R_ERR_INVALID_ARG;
+  to_internal(*sch, hd->sched);
+  free_plan(hd->plan);
+  hd->plan = Plan{};
+  hd->plan_gen++;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_get_schedule(const scal3r_ttt_handle* hd, scal3r_ttt_schedule* sch) {
+  if (!hd || !sch) return SCAL3R_ERR_INVALID_ARG;
+  to_public(hd->sched, *sch);
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_set_graph_mode(scal3r_ttt_handle* hd, int32_t enable) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  hd->graph_on = enable != 0;
+  if (!hd->graph_on) {
+    drop_graph(hd->gfwd);
+    drop_graph(hd->gbwd);
+  }
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
+                        const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C, const int32_t* ptr,
+                        int32_t S, void* o, float* w_ckpt, float* wnorm, const void* d_o, void* dq, void* dk,
+                        void* dv, float* dlr, float* dw0, int32_t with_backward, void* stream,
+                        scal3r_ttt_schedule* best, float* best_ms) {
+  if (!hd || !best || !best_ms) return SCAL3R_ERR_INVALID_ARG;
+  if (with_backward && (!d_o || !dq || !dk || !dv || !dlr || !dw0 || !w_ckpt || !wnorm))
+    return SCAL3R_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool graph_was = hd->graph_on, prof_was = hd->prof_on;
+  hd->graph_on = false;
+  hd->prof_on = false;
+  const Schedule saved = hd->sched;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SCAL3R_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SCAL3R_ERR_CUDA;
+
+  // time one schedule: 1 warm-up run, then the mean of 3 timed runs
+  auto trial = [&](const Schedule& sc, bool bwd, float& ms) -> int {
+    hd->sched = sc;
+    free_plan(hd->plan);
+    hd->plan = Plan{};
+    hd->plan_gen++;
+    int r = ensure_plan(hd, off, C, ptr, S);
+    if (r != SCAL3R_OK) return r;
+    const size_t need = workspace_bytes(hd->plan, hd->shape, true);
+    if (need > ws_bytes) {
+      if (ws) cudaFree(ws);
+      ws = nullptr;
+      if (cudaMalloc(&ws, need) != cudaSuccess) return SCAL3R_ERR_CUDA;
+      ws_bytes = need;
+    }
+    auto once = [&]() -> int {
+      int x = scal3r_ttt_forward(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, o, w_ckpt, wnorm, nullptr, ws,
+                                 ws_bytes, stream);
+      if (x == SCAL3R_OK && bwd)
+        x = scal3r_ttt_backward(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, d_o, w_ckpt, wnorm, dq, dk, dv,
+                                dlr, dw0, ws, ws_bytes, stream);
+      return x;
+    };
+    r = once();
+    if (r != SCAL3R_OK) return r;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    for (int i = 0; i < 3 && r == SCAL3R_OK; ++i) r = once();
+    if (r != SCAL3R_OK) return r;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    ms = t / 3.f;
+    return SCAL3R_OK;
+  };
+
+  Schedule bestc = saved;
+  float bestt = 0.f;
+  if (rc == SCAL3R_OK) {
+    // forward: pieces per step and the gradient/apply cost ratio
+    bool first = true;
+    for (int wv : {1, 2, 3})
+      for (float kc : {1.5f, 2.0f, 3.0f}) {
+        Schedule sc = saved;
+        sc.fwd_waves = wv;
+        sc.key_cost = kc;
+        float t = 0.f;
+        rc = trial(sc, false, t);
+        if (rc != SCAL3R_OK) break;
+        if (first || t < bestt) {
+          bestc = sc;
+          bestt = t;
+          first = false;
+        }
+      }
+  }
+  if (rc == SCAL3R_OK && with_backward) {
+    // backward, with the forward fixed at its best schedule
+    bool first = true;
+    const Schedule fb = bestc;
+    for (int wv : {1, 2, 3})
+      for (float kc : {1.5f, 2.5f, 4.0f}) {
+        Schedule sc = fb;
+        sc.bwd_waves = wv;
+        sc.bkey_cost = kc;
+        float t = 0.f;
+        rc = trial(sc, true, t);
+        if (rc != SCAL3R_OK) break;
+        if (first || t < bestt) {
+          bestc = sc;
+          bestt = t;
+          first = false;
+        }
+      }
+  }
+  if (ws) {
+    cudaStreamSynchronize(st);
+    cudaFree(ws);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  hd->sched = rc == SCAL3R_OK ? bestc : saved;
+  free_plan(hd->plan);
+  hd->plan = Plan{};
+  hd->plan_gen++;
+  hd->graph_on = graph_was;
+  hd->prof_on = prof_was;
+  drop_graph(hd->gfwd);
+  drop_graph(hd->gbwd);
+  if (rc != SCAL3R_OK) return rc;
+  to_public(bestc, *best);
+  *best_ms = bestt;
   return SCAL3R_OK;
 }
 

@@ -560,8 +560,6 @@ constexpr size_t bwd_smem() {
 template <int D, int F>
 cudaError_t launch_fwd(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st) {
   const size_t smem = fwd_smem<D, F>();
-  cudaError_t e = cudaFuncSetAttribute(fp32_sweep_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   fp32_sweep_kernel<D, F><<<n, NTH, smem, st>>>(prm, items, step);
   return cudaGetLastError();
 }
@@ -569,14 +567,27 @@ cudaError_t launch_fwd(const Params& prm, const WorkItem* items, int n, int step
 template <int D, int F, typename TIO>
 cudaError_t launch_bwd(const Params& prm, const WorkItem* items, int n, int step, cudaStream_t st) {
   const size_t smem = bwd_smem<D, F>();
-  cudaError_t e = cudaFuncSetAttribute(fp32_bsweep_kernel<D, F, TIO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
   fp32_bsweep_kernel<D, F, TIO><<<n, NTH, smem, st>>>(prm, items, step);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t prepare_fp32() {
+  const struct {
+    const void* f;
+    size_t smem;
+  } ks[] = {{(const void*)fp32_sweep_kernel<64, 128>, fwd_smem<64, 128>()},
+            {(const void*)fp32_sweep_kernel<16, 32>, fwd_smem<16, 32>()},
+            {(const void*)fp32_bsweep_kernel<64, 128, float>, bwd_smem<64, 128>()},
+            {(const void*)fp32_bsweep_kernel<16, 32, float>, bwd_smem<16, 32>()},
+            {(const void*)fp32_bsweep_kernel<64, 128, __nv_bfloat16>, bwd_smem<64, 128>()}};
+  for (const auto& k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 bool fp32_shape_supported(int D, int F) {
   return (D == 64 && F == 128) || (D == 16 && F == 32);

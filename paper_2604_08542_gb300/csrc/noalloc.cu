@@ -12,8 +12,8 @@
 //
 // Rules of use:
 //  - The first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress, which may load the module); make that first call
-//    before any stream capture.
+//    (cudaGetSymbolAddress, which may load the module) and sets the kernels'
+//    shared-memory attributes; make that first call before any stream capture.
 //  - Every call on a device shares the one array and leaves its contents
 //    behind; calls whose GPU work overlaps (different streams, or threads
 //    without ordering) race on it.  Order them on one stream.
@@ -47,6 +47,7 @@ int scratch_address(int dev, void** out) {
   if (!g_addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCAL3R_ERR_CUDA;
+    if (prepare_kernels() != cudaSuccess) return SCAL3R_ERR_CUDA;   // kernel attributes, once per device
     g_addr[dev] = p;
   }
   *out = g_addr[dev];

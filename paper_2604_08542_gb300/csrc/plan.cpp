@@ -52,7 +52,7 @@ std::vector<std::pair<int64_t, int64_t>> split(int64_t t0, int64_t t1, int n) {
   return out;
 }
 
-void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_sms,
+void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_sms, int waves,
                   bool backward, std::vector<WorkItem>& items, std::vector<UpdateItem>& upds,
                   std::vector<Step>& steps, int32_t& max_slots,
                   const std::vector<UpdateItem>& step_updates_template) {
@@ -62,7 +62,7 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   double total = 0;
   for (auto& t : tasks) total += t.cost;
   int ctas = sch.ctas_per_wave > 0 ? sch.ctas_per_wave : num_sms;
-  double target = std::max(1, sch.waves * ctas);
+  double target = std::max(1, waves * ctas);
   double piece_cost = std::max((double)sch.min_tokens, total / target);
   // pieces per task
   std::vector<WorkItem> step_items;
@@ -180,7 +180,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
         }
       }
     }
-    lay_out_step(tasks, sch, num_sms, false, p.items, p.updates, p.steps, p.max_slots, upd);
+    lay_out_step(tasks, sch, num_sms, sch.fwd_waves, false, p.items, p.updates, p.steps, p.max_slots, upd);
   }
 
   // ---- backward: steps j = maxn .. 0 -------------------------------------
@@ -210,7 +210,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
         upd.push_back(u);
       }
     }
-    lay_out_step(tasks, sch, num_sms, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
+    lay_out_step(tasks, sch, num_sms, sch.bwd_waves, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
     p.bscratch_tiles = std::max<int64_t>(p.bscratch_tiles, p.bsteps.back().scratch_tiles);
   }
   p.valid = true;

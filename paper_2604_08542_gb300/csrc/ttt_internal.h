@@ -83,7 +83,8 @@ constexpr int kBwdSubTiles = 4;
 // Scheduling knobs (the autotuner's search space).
 struct Schedule {
   int32_t ctas_per_wave = 0;   // 0: number of SMs
-  int32_t waves = 1;           // target CTAs per step = waves * ctas_per_wave
+  int32_t fwd_waves = 1;       // forward: target CTAs per step = fwd_waves * ctas_per_wave
+  int32_t bwd_waves = 1;       // backward: same for the backward steps
   int32_t min_tokens = 256;    // smallest piece (tokens)
   float key_cost = 2.0f;       // relative cost of a key token vs a query token
   float bkey_cost = 2.0f;      // backward: key-side VJP vs apply-side VJP
@@ -150,5 +151,7 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int nite
                               const void* tmaps, cudaStream_t st);
 cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int nitems, int step,
                                const void* tmaps, cudaStream_t st);
+// Set kernel attributes once (outside any stream capture).
+cudaError_t prepare_kernels();
 
 }  // namespace scal3r

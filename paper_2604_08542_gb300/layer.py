@@ -12,10 +12,15 @@ from __future__ import annotations
 import numpy as np
 import torch
 
+import hashlib
+import json
+import os
+
 from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3R_NORM_NONE,
-               SCAL3R_NORM_ROW_W0, SCAL3R_NORM_UNIT, Scal3rError, _check, scal3r_ttt_backward,
-               scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_status,
-               scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_workspace_size)
+               SCAL3R_NORM_ROW_W0, SCAL3R_NORM_UNIT, Scal3rError, _check, scal3r_ttt_autotune, scal3r_ttt_backward,
+               scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_schedule,
+               scal3r_ttt_get_status, scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_schedule,
+               scal3r_ttt_set_graph_mode, scal3r_ttt_set_schedule, scal3r_ttt_workspace_size)
 
 NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
 LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
@@ -127,6 +132,64 @@ class TTT:
 
     def status(self) -> int:
         return scal3r_ttt_get_status(self.handle, torch.cuda.current_stream().cuda_stream)
+
+    # -- graphs and schedules ---------------------------------------------
+    def set_graph_mode(self, enable: bool = True) -> None:
+        """Record forward/backward launch sequences into CUDA graphs and replay them."""
+        scal3r_ttt_set_graph_mode(self.handle, enable)
+
+    def schedule(self) -> dict:
+        return scal3r_ttt_get_schedule(self.handle).as_dict()
+
+    def set_schedule(self, **kw) -> None:
+        sch = scal3r_ttt_get_schedule(self.handle)
+        for k, v in kw.items():
+            setattr(sch, k, v)
+        scal3r_ttt_set_schedule(self.handle, sch)
+
+    def layout_key(self, chunk_offsets, seq_chunk_ptr) -> str:
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        h = hashlib.sha1(off.tobytes() + b"|" + ptr.tobytes())
+        h.update(f"{self.H},{self.D},{self.F},{self.dtype}".encode())
+        return h.hexdigest()[:16]
+
+    def autotune(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, d_o=None, cache_path=None) -> dict:
+        """Pick the piece schedule for this layout by timing candidates (the
+        library's tuner); forward only unless d_o is given.  With cache_path,
+        results are kept in a JSON file keyed by the layout."""
+        key = self.layout_key(chunk_offsets, seq_chunk_ptr) + ("b" if d_o is not None else "f")
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                self.set_schedule(**cache[key]["schedule"])
+                return cache[key]
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        T, C, S = int(off[-1]), len(off) - 1, len(ptr) - 1
+        stride = self._w0_stride(w0, S)
+        dev = q.device
+        o = torch.empty_like(q)
+        ck = torch.empty((C, self.H, self.P), dtype=torch.float32, device=dev)
+        wn = torch.empty((C, self.H, self.R), dtype=torch.float32, device=dev)
+        grads = [None] * 6
+        if d_o is not None:
+            grads = [d_o, torch.empty_like(q), torch.empty_like(k), torch.empty_like(v), torch.empty_like(lr),
+                     torch.empty_like(w0)]
+        st = torch.cuda.current_stream(dev).cuda_stream
+        best, ms = scal3r_ttt_autotune(self.handle, _ptr(q), _ptr(k), _ptr(v), _ptr(lr), _ptr(w0), stride, off, ptr,
+                                       _ptr(o), _ptr(ck), _ptr(wn), *(_ptr(g) for g in grads), d_o is not None, st)
+        res = {"schedule": best.as_dict(), "ms": ms}
+        if cache_path:
+            cache = {}
+            if os.path.exists(cache_path):
+                with open(cache_path) as f:
+                    cache = json.load(f)
+            cache[key] = res
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        return res
 
 
 class TTTFunction(torch.autograd.Function):

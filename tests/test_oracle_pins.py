@@ -320,3 +320,12 @@ def test_workload_layouts():
     assert w4.num_chunks == 63 and int(w4.chunk_offsets[-1] - w4.chunk_offsets[-2]) == 16 * 1041
     w3 = syn.workload("bf16_ragged24")
     assert len(w3.frames) == 24 and min(w3.frames) >= 8 and max(w3.frames) <= 200
+
+
+def test_generator_token_ranges_match_the_full_draw():
+    full = syn.make_inputs(37, 3, 8, 16, seed=9, with_grad_out=True)
+    part = syn.make_inputs(37, 3, 8, 16, seed=9, with_grad_out=True, heads=[1, 2], tokens=(11, 30))
+    for n in ("q", "k", "v", "lr", "d_o"):
+        np.testing.assert_array_equal(part[n], full[n][11:30, 1:3])
+    z = syn.normal(syn._stream_key(2, 1, 1), 101)
+    np.testing.assert_array_equal(syn.normal(syn._stream_key(2, 1, 1), 40, start=33), z[33:73])

@@ -61,16 +61,19 @@ def uniform01(key: np.uint64, start: int, count: int) -> np.ndarray:
     return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
 
 
-def normal(key: np.uint64, count: int) -> np.ndarray:
-    """``count`` standard normals by Box-Muller on consecutive uniform pairs."""
-    n2 = (count + 1) // 2
-    u = uniform01(key, 0, 2 * n2)
+def normal(key: np.uint64, count: int, start: int = 0) -> np.ndarray:
+    """Standard normals start .. start+count-1 of the stream: Box-Muller on
+    consecutive uniform pairs (normals 2i and 2i+1 come from uniforms 2i, 2i+1)."""
+    p0 = start // 2
+    p1 = (start + count + 1) // 2
+    u = uniform01(key, 2 * p0, 2 * (p1 - p0))
     r = np.sqrt(-2.0 * np.log(u[0::2]))
     t = 2.0 * np.pi * u[1::2]
-    out = np.empty(2 * n2, dtype=np.float64)
+    out = np.empty(2 * (p1 - p0), dtype=np.float64)
     out[0::2] = r * np.cos(t)
     out[1::2] = r * np.sin(t)
-    return out[:count]
+    o = start - 2 * p0
+    return out[o:o + count]
 
 
 def round_bf16(x: np.ndarray) -> np.ndarray:
@@ -212,15 +215,16 @@ WORKLOADS = ["fp32_small", "bf16_vggt64", "bf16_fwdbwd_2x32", "bf16_ragged24", "
 # tensors
 # ---------------------------------------------------------------------------
 
-def _per_head_normals(seed: int, stream: int, T: int, H: int, D: int, heads) -> np.ndarray:
-    """[T, len(heads), D] normals; head h draws from its own sub-stream, so a
-    single head can be regenerated without the others.  Heads are drawn on a
-    thread pool (numpy releases the GIL in its array loops)."""
+def _per_head_normals(seed: int, stream: int, T: int, H: int, D: int, heads, t0: int = 0) -> np.ndarray:
+    """[T, len(heads), D] normals of tokens t0 .. t0+T-1; head h draws from its
+    own sub-stream, so a single head (or token range) can be regenerated
+    without the others.  Heads are drawn on a thread pool (numpy releases the
+    GIL in its array loops)."""
     out = np.empty((T, len(heads), D), dtype=np.float32)
 
     def one(j_h):
         j, h = j_h
-        out[:, j, :] = normal(_stream_key(seed, stream, h), T * D).reshape(T, D)
+        out[:, j, :] = normal(_stream_key(seed, stream, h), T * D, start=t0 * D).reshape(T, D)
 
     if len(heads) > 1 and T * D > 65536:
         import concurrent.futures as cf
@@ -240,7 +244,7 @@ def _l2_rows(x: np.ndarray) -> np.ndarray:
 
 def make_inputs(T: int, H: int, D: int, F: int, seed: int = 0, dtype: str = "fp32",
                 heads=None, lr_max: float = 0.1, with_grad_out: bool = False,
-                w0_std: float = 0.125) -> dict:
+                w0_std: float = 0.125, tokens=None) -> dict:
     """Seeded inputs of one batch.
 
     q, k, v: [T, H', D] float32, N(0,1) per element then L2-normalised per
@@ -250,16 +254,20 @@ def make_inputs(T: int, H: int, D: int, F: int, seed: int = 0, dtype: str = "fp3
     w0:      [H', 2*F*D + D*F] float32, N(0, w0_std^2), packed W1 [F,D], W3 [F,D], W2 [D,F].
     d_o:     [T, H', D] float32 N(0,1) (bfloat16-rounded for "bf16") if with_grad_out.
     ``heads`` selects a subset of heads (default: all H); values for head h
-    do not depend on which other heads are generated.
+    do not depend on which other heads are generated.  ``tokens`` = (a, b)
+    draws only tokens a .. b-1 of the T-token batch (the same values as the
+    full draw); T is then the batch size and the arrays have b - a rows.
     """
     heads = list(range(H)) if heads is None else list(heads)
+    a, b = (0, T) if tokens is None else (int(tokens[0]), int(tokens[1]))
+    n = b - a
     out = {}
     for name, st in (("q", S_Q), ("k", S_K), ("v", S_V)):
-        x = _l2_rows(_per_head_normals(seed, st, T, H, D, heads))
+        x = _l2_rows(_per_head_normals(seed, st, n, H, D, heads, t0=a))
         out[name] = round_bf16(x) if dtype == "bf16" else x
-    lr = np.empty((T, len(heads)), dtype=np.float32)
+    lr = np.empty((n, len(heads)), dtype=np.float32)
     for j, h in enumerate(heads):
-        lr[:, j] = (uniform01(_stream_key(seed, S_LR, h), 0, T) * lr_max).astype(np.float32)
+        lr[:, j] = (uniform01(_stream_key(seed, S_LR, h), a, n) * lr_max).astype(np.float32)
     out["lr"] = lr
     P = 3 * F * D
     w0 = np.empty((len(heads), P), dtype=np.float32)
@@ -267,7 +275,7 @@ def make_inputs(T: int, H: int, D: int, F: int, seed: int = 0, dtype: str = "fp3
         w0[j] = (normal(_stream_key(seed, S_W0, h), P) * w0_std).astype(np.float32)
     out["w0"] = w0
     if with_grad_out:
-        g = _per_head_normals(seed, S_DO, T, H, D, heads)
+        g = _per_head_normals(seed, S_DO, n, H, D, heads, t0=a)
         out["d_o"] = round_bf16(g) if dtype == "bf16" else g
     return out
 
