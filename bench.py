@@ -251,10 +251,8 @@ def run_gpu(args, rank: int, world: int):
     ms, prof = timed_loop(lambda: step(g), args.steps, profile=True)
     clk = clocks.stop()
     ms_step = sum(ms) / len(ms)
-    t_max = torch.tensor([sum(ms)], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    from paper_2604_08542_gb300.distributed import max_over_ranks
+    total_ms = max_over_ranks(sum(ms), device=dev)
     value = world * T * args.steps / (total_ms / 1e3)
 
     # the same step replayed from CUDA graphs (no per-launch events)
