@@ -1,12 +1,12 @@
 // BF16 tensor-core backward sweep of the test-time-training layer (sm_103a).
 //
-// One CTA = one work item (a token range of one chain at one backward step),
-// two passes that share the CTA's shared memory and tensor memory:
+// One CTA = one work item (a token range of one chain at one backward step).
+// X, Y are the item's token tensors: (k, v) for the VJP of a chunk update
+// (BKEY) and (q, d_o) for the VJP of a chunk apply (BAPPLY).  The piece is cut
+// into sub-pieces of kBwdSubTiles 128-token tiles; each sub-piece runs two
+// passes that share the CTA's shared and tensor memory:
 //
-// Pass A (token lanes: TMEM lane = token, 128-token tiles, hidden units in
-// quarters of 32).  X, Y are the item's token tensors: (k, v) for the VJP of a
-// chunk update (BKEY) and (q, d_o) for the VJP of a chunk apply (BAPPLY).
-// Per quarter q:
+// Pass A (TMEM lane = token, hidden units in quarters of 32).  Per quarter q:
 //   G1 = X [W1_q; W3_q; -R1_q; -R3_q]^T    -> z1, z3, dg1, dg3   (BKEY, N 128)
 //   G1 = X [W1_q; W3_q]^T                  -> zq1, zq3           (BAPPLY, N 64)
 //   G2 = Y [W2^T_q; -R2^T_q]^T             -> W2^T v, -R2^T v    (BKEY, N 64)
@@ -17,19 +17,20 @@
 //   dp = dg3 a + dg1 z3 s', da = dg3 p + du z3,
 //   dz3 = dg1 p s' + du a,  dz1 = dg1 p z3 s'' + da s',
 //   dlr -= W2^T v . dp - R2^T v . u   (summed over hidden units)
-// and stages them as bf16 A operands for the token-dim outputs
+// and stages them as bf16 tiles [128 tokens][32 hidden] in the 64-byte
+// swizzle, the K-blocks of the token-dim products
 //   dk (or dq) += [dz1 dz3 g1 g3] [W1_q; W3_q; -R1_q; -R3_q]      (K 128)
 //   dv        += [-lr dp, -lr u] [W2^T_q; -R2^T_q]               (K 64)
-// which accumulate in TMEM over the four quarters.  The three per-(token,
-// hidden) factors of the weight adjoints (dz1, dz3, -lr dp; for BAPPLY dzq1,
-// dzq3, uq) are also written, pre-swizzled, to the item's scratch.
+// that accumulate in TMEM over the four quarters.  The same tiles of dz1, dz3
+// and -lr dp (for BAPPLY dzq1, dzq3, uq) are copied in bulk to the piece's
+// scratch, where they are, byte for byte, MN-major A operands of pass B.
+// dk/dv/dq are staged in shared memory and written by TMA tile stores.
 // Pass B (lanes = hidden unit): the weight-adjoint partial sums over tokens
 //   L1 += dz1^T X, L3 += dz3^T X, L2t += (-lr dp)^T Y   (M 128, N 64, K 16/step)
-// with the scratch rows as MN-major A and 32-token tiles as MN-major B.
-// A piece is processed in sub-pieces of kBwdSubTiles tiles, pass A then pass
-// B for each; the L accumulators stay in TMEM for the whole piece and go to
-// the piece's partial slot at the end.  Each CTA's scratch holds one
-// sub-piece (384 KB), read back right after it was written, so it stays in L2.
+// over 32-token tiles bulk-copied back from the scratch (still in L2).  The L
+// accumulators stay in TMEM for the whole piece and go to its partial slot.
+//
+// Warps: 0 TMA loads, 1 MMA issue, 2 bulk / TMA stores, 3..10 epilogue.
 #include <cudaTypedefs.h>
 
 #include "sm100.cuh"
@@ -42,21 +43,22 @@ using namespace sm100;
 
 constexpr int D = 64;
 constexpr int F = 128;
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 352;
+constexpr int EPI0 = 3;                      // first epilogue warp
 constexpr int BT = 128;                      // pass A tile (tokens)
 constexpr int NQ = 4;                        // hidden-unit quarters
 constexpr uint32_t QBYTES = 24 * 1024;       // weights of one quarter: 192 rows x 128 B
 constexpr uint32_t WQ_OFF = 0;               // 4 quarters, 96 KB
-constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB)
-constexpr uint32_t SA_OFF = 160 * 1024;      // [128 tok][128] K-major, 2 x 16 KB blocks
-constexpr uint32_t SE_OFF = 192 * 1024;      // [128 tok][64] 16 KB
+constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB); reused for dk/dv/dq staging
+constexpr uint32_t ST_OFF = 160 * 1024;      // six [128 tok][32] SW64 tiles: dz1 dz3 g1 g3 dpe ue (48 KB)
+constexpr uint32_t ST_TILE = 8192;
 constexpr uint32_t PASS_A_BYTES = 208 * 1024;
 constexpr int PB_T = 32;                     // pass B tile (tokens)
-constexpr uint32_t PB_STAGE = 32 * 1024;     // A1, A3, A2 (2 x 4 KB each), X 4 KB, Y 4 KB
+constexpr uint32_t PB_STAGE = 32 * 1024;     // A1, A3, A2 (4 quarter blocks x 2 KB each), X 4 KB, Y 4 KB
 constexpr int PB_STAGES = 3;
 constexpr uint32_t PB_OFF = 96 * 1024;       // pass B stages reuse pass A's token/staging region
 constexpr size_t DYN_SMEM = 1024 + PASS_A_BYTES;
-constexpr uint32_t TILE_SCRATCH = 3 * 32 * 1024;   // three [128 tok][128 hidden] bf16 images
+constexpr uint32_t TILE_SCRATCH = 3 * 4 * ST_TILE;   // [factor][quarter][128 tok][32 hidden] bf16, 96 KB
 
 // TMEM columns
 constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each, resident for the whole piece
@@ -65,20 +67,22 @@ constexpr uint32_t A_DX = 384;      // dk / dq accumulator [tok][64]
 constexpr uint32_t A_DY = 448;      // dv accumulator [tok][64]
 
 struct TmaMaps {
-  CUtensorMap x_k, y_v, x_q, y_do;           // boxes of 64 x 1 x 64 tokens (pass A)
-  CUtensorMap x_k32, y_v32, x_q32, y_do32;   // boxes of 64 x 1 x 32 tokens (pass B)
+  CUtensorMap x_k, y_v, x_q, y_do;           // loads, boxes of 64 x 1 x 64 tokens (pass A)
+  CUtensorMap x_k32, y_v32, x_q32, y_do32;   // loads, boxes of 64 x 1 x 32 tokens (pass B)
+  CUtensorMap s_dk, s_dv, s_dq;              // stores, boxes of 64 x 1 x 64 tokens
 };
 
 struct Bars {
   uint64_t xy_full[2], xy_empty[2], g_full, g_free;
-  uint64_t st_full, st_free, acc_full, acc_free, eta_full[2], eta_free[2];
+  uint64_t st_full, st_free, stg_done, acc_full, acc_free, out_full;
+  uint64_t eta_full[2], eta_free[2];
   uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone;
   uint32_t tmem_base;
   int abort_flag;
   float eta_red[2][BT];
 };
 
-__device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
+__device__ __forceinline__ uint4 pack8(const float* v) {
   return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 
@@ -88,7 +92,7 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8]) {
 //                  128..159 W2[:][32q + r]      rows 160..191 -R2[:][32q + r]
 // each row 64 values (d) in the 128-byte swizzled layout.
 __device__ void load_weights(const float* w, const float* r, bool with_r, uint8_t* sm) {
-  const int t = threadIdx.x - 64;   // 256 epilogue threads
+  const int t = threadIdx.x - 32 * EPI0;   // 256 epilogue threads
 #pragma unroll 4
   for (int c = t; c < NQ * 192 * 8; c += 256) {
     const int q = c / (192 * 8);
@@ -133,17 +137,17 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
   volatile int* abort = &B.abort_flag;
   constexpr uint32_t N1 = KEY ? 128 : 64;
   constexpr uint32_t N2 = KEY ? 64 : 32;
-  constexpr int KDX = KEY ? 8 : 4;    // K-steps of the dk/dq product
+  constexpr int KDX = KEY ? 8 : 4;    // K-steps of the dk/dq product (16 hidden units each)
   constexpr uint32_t IDESC_G1 = idesc_bf16(128, N1, false, false);
   constexpr uint32_t IDESC_G2 = idesc_bf16(128, N2, false, false);
   constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
   constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
-  const int ew = warp - 2, half = ew >> 2;               // epilogue warps only
+  const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
   const uint32_t row = 32u * (warp & 3) + lane;
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
   // learning rate of this thread's token, one tile ahead (BKEY epilogue)
   float eta_next = 0.f;
-  if (KEY && warp >= 2 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
+  if (KEY && warp >= EPI0 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
 
   bool aborted = false;
   for (int sp = 0; sp < nsub; ++sp) {
@@ -167,7 +171,7 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
       __syncwarp();
     } else if (warp == 1) {
       if (lane == 0) {
-        const uint32_t wq = smem_u32(sm + WQ_OFF), sa = smem_u32(sm + SA_OFF), se = smem_u32(sm + SE_OFF);
+        const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
         auto issue_acc = [&](int m) -> bool {
           const int i = m / NQ, q = m % NQ;
           if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
@@ -176,19 +180,16 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
           const uint32_t wb = wq + q * QBYTES;
 #pragma unroll
           for (int ks = 0; ks < KDX; ++ks)
-            mma_ss(tb + A_DX, sdesc_sw128(sa + (ks / 4) * 16384 + (ks % 4) * 32, 16, 1024),
+            mma_ss(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
                    sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
           if (KEY) {
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
-              mma_ss(tb + A_DY, sdesc_sw128(se + ks * 32, 16, 1024), sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024),
-                     IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+              mma_ss(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
+                     sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
           }
           mma_commit(&B.st_free);
-          if (q == NQ - 1) {
-            mma_commit(&B.acc_full);
-            mma_commit(&B.xy_empty[i & 1]);
-          }
+          if (q == NQ - 1) mma_commit(&B.acc_full);
           return true;
         };
         bool ok = true;
@@ -212,11 +213,45 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
         if (ok && !*abort) issue_acc(te * NQ - 1);
       }
       __syncwarp();
+    } else if (warp == 2) {
+      // stores: the scratch factors of every quarter, dk/dv/dq of every tile
+      if (lane == 0) {
+        for (int n = ta * NQ; n < te * NQ; ++n) {
+          const int i = n / NQ, q = n % NQ;
+          if (!mbar_wait(&B.st_full, n & 1, abort)) break;
+          uint8_t* tile = scratch + (size_t)(i - ta) * TILE_SCRATCH + q * ST_TILE;
+          bulk_store(tile, sm + ST_OFF + 0 * ST_TILE, ST_TILE);                   // dz1
+          bulk_store(tile + 4 * ST_TILE, sm + ST_OFF + 1 * ST_TILE, ST_TILE);     // dz3
+          bulk_store(tile + 8 * ST_TILE, sm + ST_OFF + (KEY ? 4 : 2) * ST_TILE, ST_TILE);   // -lr dp | uq
+          bulk_commit();
+          bulk_wait_read_all();
+          mbar_arrive(&B.stg_done);
+          if (q == NQ - 1) {
+            // dk / dv / dq of the tile, staged over the tile's X/Y stage
+            if (!mbar_wait(&B.out_full, i & 1, abort)) break;
+            const int64_t tok = t0 + (int64_t)i * BT;
+            if (tok + BT <= t1) {
+              uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+              const CUtensorMap* m0 = KEY ? &maps.s_dk : &maps.s_dq;
+              tma_store_3d(m0, xs, 0, h, (int32_t)tok);
+              tma_store_3d(m0, xs + 8192, 0, h, (int32_t)(tok + 64));
+              if (KEY) {
+                tma_store_3d(&maps.s_dv, xs + 16384, 0, h, (int32_t)tok);
+                tma_store_3d(&maps.s_dv, xs + 24576, 0, h, (int32_t)(tok + 64));
+              }
+              bulk_commit();
+              bulk_wait_read_all();
+            }
+            mbar_arrive(&B.xy_empty[i & 1]);
+          }
+        }
+        bulk_wait_all();   // scratch written before pass B reads it back
+      }
+      __syncwarp();
     } else {
       // epilogue: thread = token row of the tile; half selects hidden units
       // [16*half, 16*half + 16) of every quarter.
-      uint8_t* sa = sm + SA_OFF;
-      uint8_t* se = sm + SE_OFF;
+      uint8_t* stg = sm + ST_OFF;
       float eta = 0.f, deta = 0.f;
       for (int n = ta * NQ; n < te * NQ; ++n) {
         const int i = n / NQ, q = n % NQ;
@@ -231,7 +266,7 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
         if (!mbar_wait(&B.g_full, n & 1, abort)) break;
         tc_fence_after();
         const uint32_t buf = tb + lane_base + A_BUF;
-        float o_dz1[16], o_dz3[16], o_g1[16], o_g3[16], o_dpe[16], o_ue[16];
+        float o[6][16];   // dz1 dz3 g1 g3 dpe ue
         float r[2][6][8];
 #pragma unroll
         for (int sb = 0; sb < 2; ++sb) {
@@ -263,102 +298,73 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
               const float du = -eta * ndu;
               const float dp = dg3 * a + dg1 * z3 * sp;
               const float da = dg3 * pp + du * z3;
-              o_dz3[k] = dg1 * pp * sp + du * a;
-              o_dz1[k] = dg1 * pp * z3 * spp + da * sp;
-              o_g1[k] = pp * z3 * sp;
-              o_g3[k] = pp * a;
-              o_dpe[k] = -eta * dp;
-              o_ue[k] = -eta * u;
+              o[1][k] = dg1 * pp * sp + du * a;
+              o[0][k] = dg1 * pp * z3 * spp + da * sp;
+              o[2][k] = pp * z3 * sp;
+              o[3][k] = pp * a;
+              o[4][k] = -eta * dp;
+              o[5][k] = -eta * u;
               deta -= praw * dp + ndu * u;
             } else {
               const float du = valid ? r[sb][2][j] : 0.f;
-              o_dz3[k] = du * a;
-              o_dz1[k] = du * z3 * sp;
-              o_dpe[k] = valid ? a * z3 : 0.f;    // uq, the third scratch factor
-              o_g1[k] = o_g3[k] = o_ue[k] = 0.f;
+              o[1][k] = du * a;
+              o[0][k] = du * z3 * sp;
+              o[2][k] = valid ? a * z3 : 0.f;    // uq, the third scratch factor
             }
           }
         }
-        // scratch for pass B: hidden unit f = 32q + 16 half + j, block f / 64
-        {
-          const uint32_t f0 = 32u * q + 16u * half;
-          uint8_t* tile = scratch + (size_t)(i - ta) * TILE_SCRATCH + (f0 / 64) * 16384;
-          const uint32_t c0 = f0 % 64;
-          const float* srcs[3] = {o_dz1, o_dz3, o_dpe};
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            float v0[8], v1[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              v0[j] = srcs[m][j];
-              v1[j] = srcs[m][8 + j];
-            }
-            *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0)) = pack8(v0);
-            *reinterpret_cast<uint4*>(tile + m * 32768 + sw128_offset(row, c0 + 8)) = pack8(v1);
-          }
-        }
-        // staging for the dk/dq (and dv) products of this quarter
+        // staging of the quarter: free once the previous quarter's products
+        // and its scratch copy have read it
         if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
+        if (!mbar_wait(&B.stg_done, (n & 1) ^ 1, abort)) break;
         {
-          auto put = [&](uint8_t* base, uint32_t col, const float (&v)[16]) {
-            float v0[8], v1[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              v0[j] = v[j];
-              v1[j] = v[8 + j];
-            }
-            *reinterpret_cast<uint4*>(base + sw128_offset(row, col)) = pack8(v0);
-            *reinterpret_cast<uint4*>(base + sw128_offset(row, col + 8)) = pack8(v1);
-          };
           const uint32_t c = 16u * half;
-          put(sa, c, o_dz1);
-          put(sa, 32 + c, o_dz3);
-          if (KEY) {
-            put(sa + 16384, c, o_g1);
-            put(sa + 16384, 32 + c, o_g3);
-            put(se, c, o_dpe);
-            put(se, 32 + c, o_ue);
+          constexpr int NT = KEY ? 6 : 3;
+#pragma unroll
+          for (int m = 0; m < NT; ++m) {
+            uint8_t* t = stg + m * ST_TILE;
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
           }
         }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.st_full);
         if (q == NQ - 1) {
-          // tile finished: read dk/dq and dv, combine the dlr halves
+          // tile finished: dk/dq (and dv) to shared memory for the TMA store
+          // (rows of a partial tile are stored directly), combine the dlr halves
           if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
           tc_fence_after();
-          float v0[16], v1[16];
-          tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
-          tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
-          __nv_bfloat16* dx = reinterpret_cast<__nv_bfloat16*>(KEY ? p.dk : p.dq);
-          if (valid) {
-            uint4* dst = reinterpret_cast<uint4*>(dx + ((size_t)tok * H + h) * D + 32 * half);
-            float a8[8];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) a8[j] = (x < 2) ? v0[8 * x + j] : v1[8 * (x - 2) + j];
-              dst[x] = pack8(a8);
+          const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
+          uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+          for (int m = 0; m < (KEY ? 2 : 1); ++m) {
+            float v0[16], v1[16];
+            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half, v0);
+            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half + 16, v1);
+            if (full_tile) {
+              uint8_t* t = xs + m * 16384 + (row >> 6) * 8192;
+              const uint32_t rr = row & 63;
+              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half)) = pack8(v0);
+              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 8)) = pack8(v0 + 8);
+              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 16)) = pack8(v1);
+              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 24)) = pack8(v1 + 8);
+            } else if (valid) {
+              __nv_bfloat16* dst0 =
+                  reinterpret_cast<__nv_bfloat16*>(KEY ? (m ? p.dv : p.dk) : p.dq) + ((size_t)tok * H + h) * D;
+              uint4* dst = reinterpret_cast<uint4*>(dst0 + 32 * half);
+              dst[0] = pack8(v0);
+              dst[1] = pack8(v0 + 8);
+              dst[2] = pack8(v1);
+              dst[3] = pack8(v1 + 8);
             }
           }
-          if (KEY) {
-            tmem_ld16(tb + lane_base + A_DY + 32 * half, v0);
-            tmem_ld16(tb + lane_base + A_DY + 32 * half + 16, v1);
-            if (valid) {
-              __nv_bfloat16* dv = reinterpret_cast<__nv_bfloat16*>(p.dv);
-              uint4* dst = reinterpret_cast<uint4*>(dv + ((size_t)tok * H + h) * D + 32 * half);
-              float a8[8];
-#pragma unroll
-              for (int x = 0; x < 4; ++x) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) a8[j] = (x < 2) ? v0[8 * x + j] : v1[8 * (x - 2) + j];
-                dst[x] = pack8(a8);
-              }
-            }
-          }
+          fence_proxy_async_smem();
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&B.acc_free);
+          if (lane == 0) {
+            mbar_arrive(&B.acc_free);
+            mbar_arrive(&B.out_full);
+          }
           if (KEY) {
             // dlr of the token = sum of the two halves' partials (half 1 hands
             // its partial to half 0 through shared memory)
@@ -377,11 +383,10 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
           }
         }
       }
-      fence_proxy_async_global();
     }
-    // pass A of the sub-piece done (its MMAs completed: the epilogue waited for
-    // the last tile's accumulators); its scratch is visible to bulk copies.
-    // Every thread takes the same decision on an abort.
+    // pass A of the sub-piece done: its MMAs completed (the epilogue waited for
+    // the last tile's accumulators) and its scratch copies are complete (the
+    // store warp waited for them).  Every thread takes the same abort decision.
     tc_fence_before();
     const int stop_a = __syncthreads_or(*abort);
     tc_fence_after();
@@ -400,12 +405,12 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
           mbar_arrive_expect_tx(&B.b_full[s], PB_STAGE);
           uint8_t* st = sm + PB_OFF + s * PB_STAGE;
           const int il = j / (BT / PB_T) - ta, r = j % (BT / PB_T);
-          const uint8_t* src = scratch + (size_t)il * TILE_SCRATCH + r * (PB_T * 128);
+          const uint8_t* src = scratch + (size_t)il * TILE_SCRATCH + r * (PB_T * 64);
 #pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            bulk_load(st + m * 8192, src + m * 32768, PB_T * 128, &B.b_full[s]);
-            bulk_load(st + m * 8192 + 4096, src + m * 32768 + 16384, PB_T * 128, &B.b_full[s]);
-          }
+          for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+              bulk_load(st + m * 8192 + q * 2048, src + (m * NQ + q) * ST_TILE, PB_T * 64, &B.b_full[s]);
           const int32_t tok = (int32_t)(t0 + (int64_t)j * PB_T);
           tma_load_3d(st + 24576, mx32, &B.b_full[s], 0, h, tok);
           tma_load_3d(st + 28672, my32, &B.b_full[s], 0, h, tok);
@@ -428,9 +433,9 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
             const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
             const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
             const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
-            mma_ss(tb + B_L, sdesc_sw128(st + ks * 2048, 4096, 1024), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 64, sdesc_sw128(st + 8192 + ks * 2048, 4096, 1024), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 128, sdesc_sw128(st + 16384 + ks * 2048, 4096, 1024), yd, IDESC_LAM, acc);
+            mma_ss(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
           }
           mma_commit(&B.b_empty[s]);
         }
@@ -449,7 +454,8 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
       break;
     }
   }
-  if (aborted || warp < 2) return;
+  if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv/dq stores complete
+  if (aborted || warp < EPI0) return;
 
   // weight-adjoint partial sums of the piece -> its slot (lanes = hidden unit)
   float* slot = p.part + (size_t)it.slot * 3 * F * D;
@@ -493,17 +499,17 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.xy_full[i], 1);
       mbar_init(&B.xy_empty[i], 1);
+      mbar_init(&B.eta_full[i], 4);
+      mbar_init(&B.eta_free[i], 4);
     }
     mbar_init(&B.g_full, 1);
     mbar_init(&B.g_free, 8);
     mbar_init(&B.st_full, 8);
     mbar_init(&B.st_free, 1);
+    mbar_init(&B.stg_done, 1);
     mbar_init(&B.acc_full, 1);
     mbar_init(&B.acc_free, 8);
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&B.eta_full[i], 4);
-      mbar_init(&B.eta_free[i], 4);
-    }
+    mbar_init(&B.out_full, 8);
     for (int i = 0; i < PB_STAGES; ++i) {
       mbar_init(&B.b_full[i], 1);
       mbar_init(&B.b_empty[i], 1);
@@ -518,7 +524,7 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     tmem_alloc(&B.tmem_base, 512);
     tmem_relinquish();
   }
-  if (warp >= 2) load_weights(w, r, key, sm);
+  if (warp >= EPI0) load_weights(w, r, key, sm);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -574,7 +580,9 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
   if (!make_map(&maps.x_k, prm.k, prm.T, prm.H, 64) || !make_map(&maps.y_v, prm.v, prm.T, prm.H, 64) ||
       !make_map(&maps.x_q, prm.q, prm.T, prm.H, 64) || !make_map(&maps.y_do, prm.d_o, prm.T, prm.H, 64) ||
       !make_map(&maps.x_k32, prm.k, prm.T, prm.H, PB_T) || !make_map(&maps.y_v32, prm.v, prm.T, prm.H, PB_T) ||
-      !make_map(&maps.x_q32, prm.q, prm.T, prm.H, PB_T) || !make_map(&maps.y_do32, prm.d_o, prm.T, prm.H, PB_T))
+      !make_map(&maps.x_q32, prm.q, prm.T, prm.H, PB_T) || !make_map(&maps.y_do32, prm.d_o, prm.T, prm.H, PB_T) ||
+      !make_map(&maps.s_dk, prm.dk, prm.T, prm.H, 64) || !make_map(&maps.s_dv, prm.dv, prm.T, prm.H, 64) ||
+      !make_map(&maps.s_dq, prm.dq, prm.T, prm.H, 64))
     return cudaErrorInvalidValue;
   bf16_bsweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items);
   return cudaGetLastError();
