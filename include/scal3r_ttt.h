@@ -180,7 +180,8 @@ int scal3r_ttt_backward(scal3r_ttt_handle* handle,
 /* How each chunk step is cut into per-CTA pieces (the autotuner's search
  * space).  Chunk lengths are part of the method and are never tuned. */
 typedef struct scal3r_ttt_schedule {
-  int32_t fwd_waves;        /* forward: pieces per chunk step ~ fwd_waves x SM count (1..8) */
+  int32_t fwd_waves;        /* forward: at most fwd_waves x SM count pieces per chunk step (1..8);
+                               pieces are cut so that the costliest one is as cheap as possible */
   int32_t bwd_waves;        /* backward: same for the backward steps (1..8) */
   int32_t min_piece_tokens; /* smallest piece, tokens (>= 128) */
   float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0) */

@@ -1,35 +1,47 @@
 // BF16 tensor-core backward sweep of the test-time-training layer (sm_103a).
 //
 // One CTA = one work item (a token range of one chain at one backward step).
-// X, Y are the item's token tensors: (k, v) for the VJP of a chunk update
-// (BKEY) and (q, d_o) for the VJP of a chunk apply (BAPPLY).  The piece is cut
-// into sub-pieces of kBwdSubTiles 128-token tiles; each sub-piece runs two
-// passes that share the CTA's shared and tensor memory:
+// BKEY items differentiate a chunk update (token tensors X = k, Y = v), BAPPLY
+// items a chunk apply (X = q, Y = d_o).  Both form the per-(token, hidden
+// unit) adjoints of the SwiGLU chain (reverse-mode differentiation of the
+// forward step; dot loss) and contract them twice: over hidden units into the
+// token gradients (dk and dv, or dq), and over tokens into the
+// weight-adjoint partial sums L of the piece, which go to its partial slot.
+// TMEM lane = token for the per-token products; hidden units are taken in
+// quarters of 32.
 //
-// Pass A (TMEM lane = token, hidden units in quarters of 32).  Per quarter q:
-//   G1 = X [W1_q; W3_q; -R1_q; -R3_q]^T    -> z1, z3, dg1, dg3   (BKEY, N 128)
-//   G1 = X [W1_q; W3_q]^T                  -> zq1, zq3           (BAPPLY, N 64)
-//   G2 = Y [W2^T_q; -R2^T_q]^T             -> W2^T v, -R2^T v    (BKEY, N 64)
-//   G2 = Y [W2^T_q]^T                      -> du = W2^T d_o      (BAPPLY, N 32)
-// The epilogue (thread = token) forms the per-(token, hidden) adjoints of the
-// SwiGLU chain (reverse-mode differentiation of the forward step; dot loss):
+// BKEY, per 128-token tile and quarter q:
+//   G1 = X [W1_q; W3_q; -R1_q; -R3_q]^T    -> z1, z3, dg1, dg3   (N 128)
+//   G2 = Y [W2^T_q; -R2^T_q]^T             -> W2^T v, -R2^T v    (N 64)
 //   p = -lr W2^T v, g1 = p z3 s', g3 = p a, du = lr R2^T v,
 //   dp = dg3 a + dg1 z3 s', da = dg3 p + du z3,
 //   dz3 = dg1 p s' + du a,  dz1 = dg1 p z3 s'' + da s',
 //   dlr -= W2^T v . dp - R2^T v . u   (summed over hidden units)
-// and stages them as bf16 tiles [128 tokens][32 hidden] in the 64-byte
-// swizzle, the K-blocks of the token-dim products
-//   dk (or dq) += [dz1 dz3 g1 g3] [W1_q; W3_q; -R1_q; -R3_q]      (K 128)
-//   dv        += [-lr dp, -lr u] [W2^T_q; -R2^T_q]               (K 64)
-// that accumulate in TMEM over the four quarters.  The same tiles of dz1, dz3
-// and -lr dp (for BAPPLY dzq1, dzq3, uq) are copied in bulk to the piece's
-// scratch, where they are, byte for byte, MN-major A operands of pass B.
-// dk/dv/dq are staged in shared memory and written by TMA tile stores.
-// Pass B (lanes = hidden unit): the weight-adjoint partial sums over tokens
+//   dk += [dz1 dz3 g1 g3] [W1_q; W3_q; -R1_q; -R3_q]      (K 128)
+//   dv += [-lr dp, -lr u] [W2^T_q; -R2^T_q]               (K 64)
+// The factors are staged as bf16 tiles [128 tokens][32 hidden] in the 64-byte
+// swizzle (K-major A operands of dk/dv).  The six weight matrices take 96 KB
+// of shared memory, so the four quarters of a tile cannot stay resident for
+// the token-contracted products (M = 128 hidden units): dz1, dz3 and -lr dp
+// are written to the piece's scratch by TMA tile stores, in 32-token groups
+// [group][factor][quarter][32 tok][32 hidden], and a second pass reads one
+// group per TMA load (the swizzle undone on the way out and redone on the
+// way in), as MN-major A operands of
 //   L1 += dz1^T X, L3 += dz3^T X, L2t += (-lr dp)^T Y   (M 128, N 64, K 16/step)
-// over 32-token tiles bulk-copied back from the scratch (still in L2).  The L
-// accumulators stay in TMEM for the whole piece and go to its partial slot.
+// The piece runs in sub-pieces of kBwdSubTiles tiles so that the scratch is
+// read back from L2.  The second pass keeps six 32-token stages in flight,
+// three of them over the weights, which are copied to the scratch once and
+// copied back while the second pass finishes.
 //
+// BAPPLY needs only W1, W3, W2^T (48 KB), so the tile's factors of all four
+// quarters stay in shared memory and every tile is finished in one pass:
+//   G1 = X [W1_q; W3_q]^T -> zq1, zq3,   G2 = Y [W2^T_q]^T -> du = W2^T d_o
+//   dzq1 = du z3 s', dzq3 = du a, uq = a z3
+//   dq += [dzq1 dzq3] [W1_q; W3_q]                          (K 64)
+//   after the fourth quarter: L1 += dzq1^T X, L3 += dzq3^T X, L2t += uq^T Y
+// Its G buffer is double-buffered in TMEM.
+//
+// dk/dv/dq are staged in shared memory and written by TMA tile stores.
 // Warps: 0 TMA loads, 1 MMA issue, 2 bulk / TMA stores, 3..10 epilogue.
 #include <cudaTypedefs.h>
 
@@ -45,38 +57,52 @@ constexpr int D = 64;
 constexpr int F = 128;
 constexpr int NTHREADS = 352;
 constexpr int EPI0 = 3;                      // first epilogue warp
-constexpr int BT = 128;                      // pass A tile (tokens)
+constexpr int BT = 128;                      // tile (tokens)
 constexpr int NQ = 4;                        // hidden-unit quarters
+constexpr uint32_t ST_TILE = 8192;           // [128 tok][32 hidden] bf16, 64-byte swizzle
+
+// BKEY shared memory
 constexpr uint32_t QBYTES = 24 * 1024;       // weights of one quarter: 192 rows x 128 B
 constexpr uint32_t WQ_OFF = 0;               // 4 quarters, 96 KB
-constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB); reused for dk/dv/dq staging
-constexpr uint32_t ST_OFF = 160 * 1024;      // six [128 tok][32] SW64 tiles: dz1 dz3 g1 g3 dpe ue (48 KB)
-constexpr uint32_t ST_TILE = 8192;
-constexpr uint32_t PASS_A_BYTES = 208 * 1024;
+constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB); reused for dk/dv staging
+constexpr uint32_t ST_OFF = 160 * 1024;      // six tiles: dz1 dz3 g1 g3 dpe ue (48 KB)
 constexpr int PB_T = 32;                     // pass B tile (tokens)
 constexpr uint32_t PB_STAGE = 32 * 1024;     // A1, A3, A2 (4 quarter blocks x 2 KB each), X 4 KB, Y 4 KB
-constexpr int PB_STAGES = 3;
-constexpr uint32_t PB_OFF = 96 * 1024;       // pass B stages reuse pass A's token/staging region
-constexpr size_t DYN_SMEM = 1024 + PASS_A_BYTES;
+constexpr int PB_STAGES = 6;
+constexpr uint32_t PB_OFF = 0;               // pass B stages reuse the weights, token and staging regions
+constexpr int PB_WQ_STAGES = 3;              // stages 0..2 lie over the weights
+constexpr uint32_t WQ_BYTES = 4 * QBYTES;
 constexpr uint32_t TILE_SCRATCH = 3 * 4 * ST_TILE;   // [factor][quarter][128 tok][32 hidden] bf16, 96 KB
+
+// BAPPLY shared memory
+constexpr uint32_t AQ_BYTES = 12 * 1024;     // W1_q, W3_q, W2^T_q: 96 rows x 128 B
+constexpr uint32_t AW_OFF = 0;               // 4 quarters, 48 KB
+constexpr uint32_t AXY_OFF = 48 * 1024;      // 2 stages x (X 16 KB + Y 16 KB)
+constexpr uint32_t AST_OFF = 112 * 1024;     // [factor][quarter] tiles of dzq1, dzq3, uq (96 KB)
+constexpr uint32_t ADQ_OFF = 208 * 1024;     // dq staging, two 64-token boxes (16 KB)
+
+constexpr uint32_t SMEM_BYTES = 224 * 1024;
+constexpr size_t DYN_SMEM = 1024 + SMEM_BYTES;
 
 // TMEM columns
 constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each, resident for the whole piece
-constexpr uint32_t A_BUF = 192;     // G1 (128) | G2 (64)
+constexpr uint32_t A_BUF = 192;     // BKEY: G1 (128) | G2 (64); BAPPLY: two buffers of G1 (64) | G2 (32)
+constexpr uint32_t A_GBUF = 96;     // BAPPLY: columns of one G buffer
 constexpr uint32_t A_DX = 384;      // dk / dq accumulator [tok][64]
 constexpr uint32_t A_DY = 448;      // dv accumulator [tok][64]
 
 struct TmaMaps {
-  CUtensorMap x_k, y_v, x_q, y_do;           // loads, boxes of 64 x 1 x 64 tokens (pass A)
-  CUtensorMap x_k32, y_v32, x_q32, y_do32;   // loads, boxes of 64 x 1 x 32 tokens (pass B)
+  CUtensorMap x_k, y_v, x_q, y_do;           // loads, boxes of 64 x 1 x 64 tokens
+  CUtensorMap x_k32, y_v32;                  // loads, boxes of 64 x 1 x 32 tokens (BKEY pass B)
+  CUtensorMap sc_st, sc_ld;                  // BKEY scratch: one factor tile out, one 32-token group in
   CUtensorMap s_dk, s_dv, s_dq;              // stores, boxes of 64 x 1 x 64 tokens
 };
 
 struct Bars {
-  uint64_t xy_full[2], xy_empty[2], g_full, g_free;
-  uint64_t st_full, st_free, stg_done, acc_full, acc_free, out_full;
+  uint64_t xy_full[2], xy_empty[2], g_full, g_free, ga_full[2], ga_free[2], sq_full[NQ];
+  uint64_t st_full, st_free, stg_done, acc_full, acc_free, out_full, out_free;
   uint64_t eta_full[2], eta_free[2];
-  uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone;
+  uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone, wq_full;
   uint32_t tmem_base;
   int abort_flag;
   float eta_red[2][BT];
@@ -86,12 +112,19 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
   return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 
-// Weights of the step into shared memory, bf16, quarter-major:
+// Eight consecutive values of W2 / R2 column f (rows col..col+7), i.e. of
+// row f of W2^T.
+__device__ __forceinline__ void load_col8(const float* m2, int f, int col, float* v) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = m2[(size_t)(col + j) * F + f];
+}
+
+// BKEY weights into shared memory, bf16, quarter-major:
 //   quarter q rows   0.. 31 W1[32q + r][:]      rows  32.. 63 W3[32q + r][:]
 //                   64.. 95 -R1[32q + r][:]     rows  96..127 -R3[32q + r][:]
 //                  128..159 W2[:][32q + r]      rows 160..191 -R2[:][32q + r]
 // each row 64 values (d) in the 128-byte swizzled layout.
-__device__ void load_weights(const float* w, const float* r, bool with_r, uint8_t* sm) {
+__device__ void load_weights_key(const float* w, const float* r, uint8_t* sm) {
   const int t = threadIdx.x - 32 * EPI0;   // 256 epilogue threads
 #pragma unroll 4
   for (int c = t; c < NQ * 192 * 8; c += 256) {
@@ -99,7 +132,6 @@ __device__ void load_weights(const float* w, const float* r, bool with_r, uint8_
     const int rr = (c / 8) % 192;
     const int col = (c % 8) * 8;
     const int blk = rr / 32, f = 32 * q + rr % 32;
-    if (!with_r && (blk == 2 || blk == 3 || blk == 5)) continue;
     float v[8];
     if (blk < 4) {
       const float* src = (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col;
@@ -107,9 +139,7 @@ __device__ void load_weights(const float* w, const float* r, bool with_r, uint8_
       const float4 b = *reinterpret_cast<const float4*>(src + 4);
       v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
     } else {
-      const float* src = (blk == 4 ? w : r) + 2 * (size_t)F * D + f;   // W2 / R2 [D][F], column f
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = src[(size_t)(col + j) * F];
+      load_col8((blk == 4 ? w : r) + 2 * (size_t)F * D, f, col, v);
     }
     if (blk == 2 || blk == 3 || blk == 5) {
 #pragma unroll
@@ -120,344 +150,57 @@ __device__ void load_weights(const float* w, const float* r, bool with_r, uint8_
   fence_proxy_async_smem();
 }
 
-template <bool KEY>
-__device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
-                         uint32_t tb) {
+// BAPPLY weights: quarter q rows 0..31 W1[32q + r][:], 32..63 W3[32q + r][:],
+// 64..95 W2[:][32q + r], 128-byte swizzle.
+__device__ void load_weights_apply(const float* w, uint8_t* sm) {
+  const int t = threadIdx.x - 32 * EPI0;
+#pragma unroll 4
+  for (int c = t; c < NQ * 96 * 8; c += 256) {
+    const int q = c / (96 * 8);
+    const int rr = (c / 8) % 96;
+    const int col = (c % 8) * 8;
+    const int blk = rr / 32, f = 32 * q + rr % 32;
+    float v[8];
+    if (blk < 2) {
+      const float* src = w + (size_t)blk * F * D + (size_t)f * D + col;
+      const float4 a = *reinterpret_cast<const float4*>(src);
+      const float4 b = *reinterpret_cast<const float4*>(src + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+      load_col8(w + 2 * (size_t)F * D, f, col, v);
+    }
+    *reinterpret_cast<uint4*>(sm + AW_OFF + q * AQ_BYTES + sw128_offset(rr, col)) = pack8(v);
+  }
+  fence_proxy_async_smem();
+}
+
+// 32 fp32 accumulator columns of this thread's token row -> bf16 in a
+// [128 tok][64] tile pair (two 64-token boxes, 128-byte swizzle).
+__device__ __forceinline__ void stage_row64(uint8_t* base, uint32_t row, int half, const float* v0,
+                                            const float* v1) {
+  uint8_t* t = base + (row >> 6) * 8192;
+  const uint32_t rr = row & 63;
+  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half)) = pack8(v0);
+  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 8)) = pack8(v0 + 8);
+  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 16)) = pack8(v1);
+  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 24)) = pack8(v1 + 8);
+}
+
+__device__ __forceinline__ void store_row64(__nv_bfloat16* dst0, int half, const float* v0, const float* v1) {
+  uint4* dst = reinterpret_cast<uint4*>(dst0 + 32 * half);
+  dst[0] = pack8(v0);
+  dst[1] = pack8(v0 + 8);
+  dst[2] = pack8(v1);
+  dst[3] = pack8(v1 + 8);
+}
+
+// Weight-adjoint partial sums of the piece (TMEM lanes = hidden unit) -> its
+// slot, in the layout of W: L1 [F][D], L3 [F][D], L2 [D][F].
+__device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int H = p.H;
-  const int h = it.chain % H;
-  const int64_t t0 = it.t0, t1 = it.t1;
-  const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
-  const int nsub = (ntiles + kBwdSubTiles - 1) / kBwdSubTiles;
-  const CUtensorMap* mx = KEY ? &maps.x_k : &maps.x_q;
-  const CUtensorMap* my = KEY ? &maps.y_v : &maps.y_do;
-  const CUtensorMap* mx32 = KEY ? &maps.x_k32 : &maps.x_q32;
-  const CUtensorMap* my32 = KEY ? &maps.y_v32 : &maps.y_do32;
-  uint8_t* scratch = reinterpret_cast<uint8_t*>(p.scratch) + (size_t)it.aux * TILE_SCRATCH;
-  volatile int* abort = &B.abort_flag;
-  constexpr uint32_t N1 = KEY ? 128 : 64;
-  constexpr uint32_t N2 = KEY ? 64 : 32;
-  constexpr int KDX = KEY ? 8 : 4;    // K-steps of the dk/dq product (16 hidden units each)
-  constexpr uint32_t IDESC_G1 = idesc_bf16(128, N1, false, false);
-  constexpr uint32_t IDESC_G2 = idesc_bf16(128, N2, false, false);
-  constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
-  constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
-  const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
+  const int half = (warp - EPI0) >> 2;
   const uint32_t row = 32u * (warp & 3) + lane;
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  // learning rate of this thread's token, one tile ahead (BKEY epilogue)
-  float eta_next = 0.f;
-  if (KEY && warp >= EPI0 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
-
-  bool aborted = false;
-  for (int sp = 0; sp < nsub; ++sp) {
-    const int ta = sp * kBwdSubTiles;
-    const int te = min(ntiles, ta + kBwdSubTiles);
-    // ======================= pass A on tiles [ta, te) =======================
-    if (warp == 0) {
-      if (lane == 0) {
-        for (int i = ta; i < te; ++i) {
-          const int s = i & 1;
-          if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
-          mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
-          uint8_t* xs = sm + XY_OFF + s * 32768;
-          const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
-          tma_load_3d(xs, mx, &B.xy_full[s], 0, h, tok);
-          tma_load_3d(xs + 8192, mx, &B.xy_full[s], 0, h, tok + 64);
-          tma_load_3d(xs + 16384, my, &B.xy_full[s], 0, h, tok);
-          tma_load_3d(xs + 24576, my, &B.xy_full[s], 0, h, tok + 64);
-        }
-      }
-      __syncwarp();
-    } else if (warp == 1) {
-      if (lane == 0) {
-        const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
-        auto issue_acc = [&](int m) -> bool {
-          const int i = m / NQ, q = m % NQ;
-          if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
-          if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
-          tc_fence_after();
-          const uint32_t wb = wq + q * QBYTES;
-#pragma unroll
-          for (int ks = 0; ks < KDX; ++ks)
-            mma_ss(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
-                   sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-          if (KEY) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_ss(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
-                     sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-          }
-          mma_commit(&B.st_free);
-          if (q == NQ - 1) mma_commit(&B.acc_full);
-          return true;
-        };
-        bool ok = true;
-        for (int n = ta * NQ; n < te * NQ && ok; ++n) {
-          const int i = n / NQ, q = n % NQ;
-          if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-          if (!mbar_wait(&B.g_free, (n & 1) ^ 1, abort)) break;
-          tc_fence_after();
-          const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
-          const uint32_t wb = wq + q * QBYTES;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            mma_ss(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
-                   ks > 0);
-            mma_ss(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
-                   sdesc_sw128(wb + 16384 + ks * 32, 16, 1024), IDESC_G2, ks > 0);
-          }
-          mma_commit(&B.g_full);
-          if (n > ta * NQ) ok = issue_acc(n - 1);
-        }
-        if (ok && !*abort) issue_acc(te * NQ - 1);
-      }
-      __syncwarp();
-    } else if (warp == 2) {
-      // stores: the scratch factors of every quarter, dk/dv/dq of every tile
-      if (lane == 0) {
-        for (int n = ta * NQ; n < te * NQ; ++n) {
-          const int i = n / NQ, q = n % NQ;
-          if (!mbar_wait(&B.st_full, n & 1, abort)) break;
-          uint8_t* tile = scratch + (size_t)(i - ta) * TILE_SCRATCH + q * ST_TILE;
-          bulk_store(tile, sm + ST_OFF + 0 * ST_TILE, ST_TILE);                   // dz1
-          bulk_store(tile + 4 * ST_TILE, sm + ST_OFF + 1 * ST_TILE, ST_TILE);     // dz3
-          bulk_store(tile + 8 * ST_TILE, sm + ST_OFF + (KEY ? 4 : 2) * ST_TILE, ST_TILE);   // -lr dp | uq
-          bulk_commit();
-          bulk_wait_read_all();
-          mbar_arrive(&B.stg_done);
-          if (q == NQ - 1) {
-            // dk / dv / dq of the tile, staged over the tile's X/Y stage
-            if (!mbar_wait(&B.out_full, i & 1, abort)) break;
-            const int64_t tok = t0 + (int64_t)i * BT;
-            if (tok + BT <= t1) {
-              uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
-              const CUtensorMap* m0 = KEY ? &maps.s_dk : &maps.s_dq;
-              tma_store_3d(m0, xs, 0, h, (int32_t)tok);
-              tma_store_3d(m0, xs + 8192, 0, h, (int32_t)(tok + 64));
-              if (KEY) {
-                tma_store_3d(&maps.s_dv, xs + 16384, 0, h, (int32_t)tok);
-                tma_store_3d(&maps.s_dv, xs + 24576, 0, h, (int32_t)(tok + 64));
-              }
-              bulk_commit();
-              bulk_wait_read_all();
-            }
-            mbar_arrive(&B.xy_empty[i & 1]);
-          }
-        }
-        bulk_wait_all();   // scratch written before pass B reads it back
-      }
-      __syncwarp();
-    } else {
-      // epilogue: thread = token row of the tile; half selects hidden units
-      // [16*half, 16*half + 16) of every quarter.
-      uint8_t* stg = sm + ST_OFF;
-      float eta = 0.f, deta = 0.f;
-      for (int n = ta * NQ; n < te * NQ; ++n) {
-        const int i = n / NQ, q = n % NQ;
-        const int64_t tok = t0 + (int64_t)i * BT + row;
-        const bool valid = tok < t1;
-        if (q == 0) {
-          eta = KEY ? eta_next : 0.f;
-          deta = 0.f;
-          const int64_t tn = tok + BT;
-          eta_next = (KEY && i + 1 < ntiles && tn < t1) ? p.lr[(size_t)tn * H + h] : 0.f;
-        }
-        if (!mbar_wait(&B.g_full, n & 1, abort)) break;
-        tc_fence_after();
-        const uint32_t buf = tb + lane_base + A_BUF;
-        float o[6][16];   // dz1 dz3 g1 g3 dpe ue
-        float r[2][6][8];
-#pragma unroll
-        for (int sb = 0; sb < 2; ++sb) {
-          const uint32_t c = 16 * half + 8 * sb;
-          if (KEY) {
-            tmem_ld8x6(buf + c, buf + 32 + c, buf + 64 + c, buf + 96 + c, buf + 128 + c, buf + 160 + c, r[sb]);
-          } else {
-            tmem_ld8x6(buf + c, buf + 32 + c, buf + 128 + c, buf + c, buf + c, buf + c, r[sb]);
-          }
-        }
-        // the quarter's GEMM results are in registers: release the buffer
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&B.g_free);
-#pragma unroll
-        for (int sb = 0; sb < 2; ++sb) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int k = 8 * sb + j;
-            const float z1 = r[sb][0][j], z3 = r[sb][1][j];
-            const float sg = sigmoid_fast(z1);
-            const float a = z1 * sg;
-            const float sp = fmaf(a, 1.f - sg, sg);
-            if (KEY) {
-              const float dg1 = r[sb][2][j], dg3 = r[sb][3][j], praw = r[sb][4][j], ndu = r[sb][5][j];
-              const float spp = sg * (1.f - sg) * fmaf(z1, 1.f - 2.f * sg, 2.f);
-              const float u = a * z3;
-              const float pp = -eta * praw;
-              const float du = -eta * ndu;
-              const float dp = dg3 * a + dg1 * z3 * sp;
-              const float da = dg3 * pp + du * z3;
-              o[1][k] = dg1 * pp * sp + du * a;
-              o[0][k] = dg1 * pp * z3 * spp + da * sp;
-              o[2][k] = pp * z3 * sp;
-              o[3][k] = pp * a;
-              o[4][k] = -eta * dp;
-              o[5][k] = -eta * u;
-              deta -= praw * dp + ndu * u;
-            } else {
-              const float du = valid ? r[sb][2][j] : 0.f;
-              o[1][k] = du * a;
-              o[0][k] = du * z3 * sp;
-              o[2][k] = valid ? a * z3 : 0.f;    // uq, the third scratch factor
-            }
-          }
-        }
-        // staging of the quarter: free once the previous quarter's products
-        // and its scratch copy have read it
-        if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
-        if (!mbar_wait(&B.stg_done, (n & 1) ^ 1, abort)) break;
-        {
-          const uint32_t c = 16u * half;
-          constexpr int NT = KEY ? 6 : 3;
-#pragma unroll
-          for (int m = 0; m < NT; ++m) {
-            uint8_t* t = stg + m * ST_TILE;
-            *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
-            *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
-          }
-        }
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&B.st_full);
-        if (q == NQ - 1) {
-          // tile finished: dk/dq (and dv) to shared memory for the TMA store
-          // (rows of a partial tile are stored directly), combine the dlr halves
-          if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
-          tc_fence_after();
-          const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
-          uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
-          for (int m = 0; m < (KEY ? 2 : 1); ++m) {
-            float v0[16], v1[16];
-            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half, v0);
-            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half + 16, v1);
-            if (full_tile) {
-              uint8_t* t = xs + m * 16384 + (row >> 6) * 8192;
-              const uint32_t rr = row & 63;
-              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half)) = pack8(v0);
-              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 8)) = pack8(v0 + 8);
-              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 16)) = pack8(v1);
-              *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 24)) = pack8(v1 + 8);
-            } else if (valid) {
-              __nv_bfloat16* dst0 =
-                  reinterpret_cast<__nv_bfloat16*>(KEY ? (m ? p.dv : p.dk) : p.dq) + ((size_t)tok * H + h) * D;
-              uint4* dst = reinterpret_cast<uint4*>(dst0 + 32 * half);
-              dst[0] = pack8(v0);
-              dst[1] = pack8(v0 + 8);
-              dst[2] = pack8(v1);
-              dst[3] = pack8(v1 + 8);
-            }
-          }
-          fence_proxy_async_smem();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(&B.acc_free);
-            mbar_arrive(&B.out_full);
-          }
-          if (KEY) {
-            // dlr of the token = sum of the two halves' partials (half 1 hands
-            // its partial to half 0 through shared memory)
-            const int e = i & 1;
-            if (half == 1) {
-              if (!mbar_wait(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
-              B.eta_red[e][row] = deta;
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&B.eta_full[e]);
-            } else {
-              if (!mbar_wait(&B.eta_full[e], (i >> 1) & 1, abort)) break;
-              if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&B.eta_free[e]);
-            }
-          }
-        }
-      }
-    }
-    // pass A of the sub-piece done: its MMAs completed (the epilogue waited for
-    // the last tile's accumulators) and its scratch copies are complete (the
-    // store warp waited for them).  Every thread takes the same abort decision.
-    tc_fence_before();
-    const int stop_a = __syncthreads_or(*abort);
-    tc_fence_after();
-    if (stop_a) {
-      aborted = true;
-      break;
-    }
-
-    // ======================= pass B on 32-token tiles of [ta, te) =======================
-    const int jb0 = ta * (BT / PB_T), jb1 = te * (BT / PB_T);
-    if (warp == 0) {
-      if (lane == 0) {
-        for (int j = jb0; j < jb1; ++j) {
-          const int s = j % PB_STAGES;
-          if (!mbar_wait(&B.b_empty[s], ((j / PB_STAGES) & 1) ^ 1, abort)) break;
-          mbar_arrive_expect_tx(&B.b_full[s], PB_STAGE);
-          uint8_t* st = sm + PB_OFF + s * PB_STAGE;
-          const int il = j / (BT / PB_T) - ta, r = j % (BT / PB_T);
-          const uint8_t* src = scratch + (size_t)il * TILE_SCRATCH + r * (PB_T * 64);
-#pragma unroll
-          for (int m = 0; m < 3; ++m)
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-              bulk_load(st + m * 8192 + q * 2048, src + (m * NQ + q) * ST_TILE, PB_T * 64, &B.b_full[s]);
-          const int32_t tok = (int32_t)(t0 + (int64_t)j * PB_T);
-          tma_load_3d(st + 24576, mx32, &B.b_full[s], 0, h, tok);
-          tma_load_3d(st + 28672, my32, &B.b_full[s], 0, h, tok);
-        }
-      }
-      __syncwarp();
-    } else if (warp == 1) {
-      if (lane == 0) {
-        bool ok = true;
-        for (int j = jb0; j < jb1; ++j) {
-          const int s = j % PB_STAGES;
-          if (!mbar_wait(&B.b_full[s], (j / PB_STAGES) & 1, abort)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t acc = (j > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
-            const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
-            mma_ss(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
-          }
-          mma_commit(&B.b_empty[s]);
-        }
-        if (ok) mma_commit(&B.bdone);
-      }
-      __syncwarp();
-    }
-    // everyone waits for the sub-piece's weight-adjoint products before the
-    // next pass A reuses their shared memory
-    mbar_wait(&B.bdone, sp & 1, abort);
-    tc_fence_before();
-    const int stop_b = __syncthreads_or(*abort);
-    tc_fence_after();
-    if (stop_b) {
-      aborted = true;
-      break;
-    }
-  }
-  if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv/dq stores complete
-  if (aborted || warp < EPI0) return;
-
-  // weight-adjoint partial sums of the piece -> its slot (lanes = hidden unit)
   float* slot = p.part + (size_t)it.slot * 3 * F * D;
   float* out = slot + (size_t)row * D + 32 * half;
 #pragma unroll
@@ -481,6 +224,524 @@ __device__ void run_item(const TmaMaps& maps, const Params& p, const WorkItem& i
   }
 }
 
+// ---------------------------------------------------------------------------
+// BKEY: the VJP of a chunk update (two passes per sub-piece)
+// ---------------------------------------------------------------------------
+__device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
+                            uint32_t tb) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int H = p.H;
+  const int h = it.chain % H;
+  const int64_t t0 = it.t0, t1 = it.t1;
+  const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
+  const int nsub = (ntiles + kBwdSubTiles - 1) / kBwdSubTiles;
+  // the piece's scratch: kBwdSubTiles tiles of factor groups, then the weights
+  const int32_t g0 = 4 * it.aux;   // first 32-token group of the piece
+  uint8_t* wq_image = reinterpret_cast<uint8_t*>(p.scratch) + (size_t)(it.aux + kBwdSubTiles) * TILE_SCRATCH;
+  volatile int* abort = &B.abort_flag;
+  constexpr int KDX = 8;    // K-steps of the dk product (16 hidden units each)
+  constexpr uint32_t IDESC_G1 = idesc_bf16(128, 128, false, false);
+  constexpr uint32_t IDESC_G2 = idesc_bf16(128, 64, false, false);
+  constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
+  constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
+  const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
+  const uint32_t row = 32u * (warp & 3) + lane;
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+  // learning rate of this thread's token, one tile ahead
+  float eta_next = 0.f;
+  if (warp >= EPI0 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
+
+  // pass B stage use counts (parity per stage), kept alike by the producer
+  // and the MMA thread
+  uint32_t pb_uses = 0;
+  bool aborted = false;
+  for (int sp = 0; sp < nsub; ++sp) {
+    const int ta = sp * kBwdSubTiles;
+    const int te = min(ntiles, ta + kBwdSubTiles);
+    // ======================= pass A on tiles [ta, te) =======================
+    if (warp == 0) {
+      if (lane == 0) {
+        for (int i = ta; i < te; ++i) {
+          const int s = i & 1;
+          if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+          mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
+          uint8_t* xs = sm + XY_OFF + s * 32768;
+          const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
+          tma_load_3d(xs, &maps.x_k, &B.xy_full[s], 0, h, tok);
+          tma_load_3d(xs + 8192, &maps.x_k, &B.xy_full[s], 0, h, tok + 64);
+          tma_load_3d(xs + 16384, &maps.y_v, &B.xy_full[s], 0, h, tok);
+          tma_load_3d(xs + 24576, &maps.y_v, &B.xy_full[s], 0, h, tok + 64);
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
+        auto issue_acc = [&](int m) -> bool {
+          const int i = m / NQ, q = m % NQ;
+          if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
+          if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+          tc_fence_after();
+          const uint32_t wb = wq + q * QBYTES;
+#pragma unroll
+          for (int ks = 0; ks < KDX; ++ks)
+            mma_ss(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
+                   sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            mma_ss(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
+                   sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+          mma_commit(&B.st_free);
+          if (q == NQ - 1) mma_commit(&B.acc_full);
+          return true;
+        };
+        bool ok = true;
+        // pass B of the previous sub-piece overwrote the weights
+        if (sp > 0 && !mbar_wait(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
+        for (int n = ta * NQ; n < te * NQ && ok; ++n) {
+          const int i = n / NQ, q = n % NQ;
+          if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+          if (!mbar_wait(&B.g_free, (n & 1) ^ 1, abort)) break;
+          tc_fence_after();
+          const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
+          const uint32_t wb = wq + q * QBYTES;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            mma_ss(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
+                   ks > 0);
+            mma_ss(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
+                   sdesc_sw128(wb + 16384 + ks * 32, 16, 1024), IDESC_G2, ks > 0);
+          }
+          mma_commit(&B.g_full);
+          if (n > ta * NQ) ok = issue_acc(n - 1);
+        }
+        if (ok && !*abort) issue_acc(te * NQ - 1);
+      }
+      __syncwarp();
+    } else if (warp == 2) {
+      // stores: the weights (once), the scratch factors of every quarter,
+      // dk/dv of every tile
+      if (lane == 0) {
+        if (sp == 0 && nsub > 1) {
+          bulk_store(wq_image, sm + WQ_OFF, WQ_BYTES);
+          bulk_commit();
+        }
+        for (int n = ta * NQ; n < te * NQ; ++n) {
+          const int i = n / NQ, q = n % NQ;
+          if (!mbar_wait(&B.st_full, n & 1, abort)) break;
+          const int32_t g = g0 + 4 * (i - ta);
+          tma_store_5d(&maps.sc_st, sm + ST_OFF + 0 * ST_TILE, 0, 0, q, 0, g);   // dz1
+          tma_store_5d(&maps.sc_st, sm + ST_OFF + 1 * ST_TILE, 0, 0, q, 1, g);   // dz3
+          tma_store_5d(&maps.sc_st, sm + ST_OFF + 4 * ST_TILE, 0, 0, q, 2, g);   // -lr dp
+          bulk_commit();
+          bulk_wait_read_all();
+          mbar_arrive(&B.stg_done);
+          if (q == NQ - 1) {
+            // dk / dv of the tile, staged over the tile's X/Y stage
+            if (!mbar_wait(&B.out_full, i & 1, abort)) break;
+            const int64_t tok = t0 + (int64_t)i * BT;
+            if (tok + BT <= t1) {
+              uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+              tma_store_3d(&maps.s_dk, xs, 0, h, (int32_t)tok);
+              tma_store_3d(&maps.s_dk, xs + 8192, 0, h, (int32_t)(tok + 64));
+              tma_store_3d(&maps.s_dv, xs + 16384, 0, h, (int32_t)tok);
+              tma_store_3d(&maps.s_dv, xs + 24576, 0, h, (int32_t)(tok + 64));
+              bulk_commit();
+              bulk_wait_read_all();
+            }
+            mbar_arrive(&B.xy_empty[i & 1]);
+          }
+        }
+        bulk_wait_all();   // scratch written before pass B reads it back
+      }
+      __syncwarp();
+    } else {
+      // epilogue: thread = token row of the tile; half selects hidden units
+      // [16*half, 16*half + 16) of every quarter.
+      uint8_t* stg = sm + ST_OFF;
+      float eta = 0.f, deta = 0.f;
+      for (int n = ta * NQ; n < te * NQ; ++n) {
+        const int i = n / NQ, q = n % NQ;
+        const int64_t tok = t0 + (int64_t)i * BT + row;
+        const bool valid = tok < t1;
+        if (q == 0) {
+          eta = eta_next;
+          deta = 0.f;
+          const int64_t tn = tok + BT;
+          eta_next = (i + 1 < ntiles && tn < t1) ? p.lr[(size_t)tn * H + h] : 0.f;
+        }
+        if (!mbar_wait(&B.g_full, n & 1, abort)) break;
+        tc_fence_after();
+        const uint32_t buf = tb + lane_base + A_BUF;
+        float o[6][16];   // dz1 dz3 g1 g3 dpe ue
+        float r[2][6][8];
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+          const uint32_t c = 16 * half + 8 * sb;
+          tmem_ld8x6(buf + c, buf + 32 + c, buf + 64 + c, buf + 96 + c, buf + 128 + c, buf + 160 + c, r[sb]);
+        }
+        // the quarter's GEMM results are in registers: release the buffer
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.g_free);
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int k = 8 * sb + j;
+            const float z1 = r[sb][0][j], z3 = r[sb][1][j];
+            const float sg = sigmoid_fast(z1);
+            const float a = z1 * sg;
+            const float sp = fmaf(a, 1.f - sg, sg);
+            const float dg1 = r[sb][2][j], dg3 = r[sb][3][j], praw = r[sb][4][j], ndu = r[sb][5][j];
+            const float spp = sg * (1.f - sg) * fmaf(z1, 1.f - 2.f * sg, 2.f);
+            const float u = a * z3;
+            const float pp = -eta * praw;
+            const float du = -eta * ndu;
+            const float dp = dg3 * a + dg1 * z3 * sp;
+            const float da = dg3 * pp + du * z3;
+            o[1][k] = dg1 * pp * sp + du * a;
+            o[0][k] = dg1 * pp * z3 * spp + da * sp;
+            o[2][k] = pp * z3 * sp;
+            o[3][k] = pp * a;
+            o[4][k] = -eta * dp;
+            o[5][k] = -eta * u;
+            deta -= praw * dp + ndu * u;
+          }
+        }
+        // staging of the quarter: free once the previous quarter's products
+        // and its scratch copy have read it
+        if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
+        if (!mbar_wait(&B.stg_done, (n & 1) ^ 1, abort)) break;
+        {
+          const uint32_t c = 16u * half;
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            uint8_t* t = stg + m * ST_TILE;
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&B.st_full);
+        if (q == NQ - 1) {
+          // tile finished: dk and dv to shared memory for the TMA store
+          // (rows of a partial tile are stored directly), combine the dlr halves
+          if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+          tc_fence_after();
+          const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
+          uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            float v0[16], v1[16];
+            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half, v0);
+            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half + 16, v1);
+            if (full_tile) {
+              stage_row64(xs + m * 16384, row, half, v0, v1);
+            } else if (valid) {
+              store_row64(reinterpret_cast<__nv_bfloat16*>(m ? p.dv : p.dk) + ((size_t)tok * H + h) * D, half, v0,
+                          v1);
+            }
+          }
+          fence_proxy_async_smem();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) {
+            mbar_arrive(&B.acc_free);
+            mbar_arrive(&B.out_full);
+          }
+          // dlr of the token = sum of the two halves' partials (half 1 hands
+          // its partial to half 0 through shared memory)
+          const int e = i & 1;
+          if (half == 1) {
+            if (!mbar_wait(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
+            B.eta_red[e][row] = deta;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.eta_full[e]);
+          } else {
+            if (!mbar_wait(&B.eta_full[e], (i >> 1) & 1, abort)) break;
+            if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&B.eta_free[e]);
+          }
+        }
+      }
+    }
+    // pass A of the sub-piece done: its MMAs completed (the epilogue waited for
+    // the last tile's accumulators) and its scratch copies are complete (the
+    // store warp waited for them).  Every thread takes the same abort decision.
+    tc_fence_before();
+    const int stop_a = __syncthreads_or(*abort);
+    tc_fence_after();
+    if (stop_a) {
+      aborted = true;
+      break;
+    }
+
+    // ======================= pass B on 32-token tiles of [ta, te) =======================
+    // Tile j (0..nb-1) of the sub-piece uses stage (j + rot) % PB_STAGES, so
+    // that the last three tiles use the stages off the weights: the weights
+    // of the next sub-piece are copied back while those finish.
+    const int jb0 = ta * (BT / PB_T), nb = (te - ta) * (BT / PB_T);
+    const int rot = (PB_STAGES - nb % PB_STAGES) % PB_STAGES;
+    if (warp == 0) {
+      if (lane == 0) {
+        bool ok = true;
+        for (int j = 0; j < nb; ++j) {
+          const int s = (j + rot) % PB_STAGES;
+          if (!mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort)) {
+            ok = false;
+            break;
+          }
+          pb_uses ^= 1u << s;
+          mbar_arrive_expect_tx(&B.b_full[s], PB_STAGE);
+          uint8_t* st = sm + PB_OFF + s * PB_STAGE;
+          tma_load_5d(st, &maps.sc_ld, &B.b_full[s], 0, 0, 0, 0, g0 + j);
+          const int32_t tok = (int32_t)(t0 + (int64_t)(jb0 + j) * PB_T);
+          tma_load_3d(st + 24576, &maps.x_k32, &B.b_full[s], 0, h, tok);
+          tma_load_3d(st + 28672, &maps.y_v32, &B.b_full[s], 0, h, tok);
+        }
+        if (ok && sp + 1 < nsub) {
+          // the stages over the weights are read: copy the weights back
+          for (int s = 0; s < PB_WQ_STAGES && ok; ++s)
+            ok = mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort);
+          if (ok) {
+            mbar_arrive_expect_tx(&B.wq_full, WQ_BYTES);
+            bulk_load(sm + WQ_OFF, wq_image, WQ_BYTES, &B.wq_full);
+          }
+        }
+      }
+      __syncwarp();
+    } else if (warp == 1) {
+      if (lane == 0) {
+        bool ok = true;
+        for (int j = 0; j < nb; ++j) {
+          const int s = (j + rot) % PB_STAGES;
+          if (!mbar_wait(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          pb_uses ^= 1u << s;
+          tc_fence_after();
+          const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint32_t acc = (jb0 + j > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
+            const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
+            mma_ss(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
+          }
+          mma_commit(&B.b_empty[s]);
+        }
+        if (ok) mma_commit(&B.bdone);
+      }
+      __syncwarp();
+    }
+    // everyone waits for the sub-piece's weight-adjoint products before the
+    // next pass A reuses their shared memory
+    mbar_wait(&B.bdone, sp & 1, abort);
+    tc_fence_before();
+    const int stop_b = __syncthreads_or(*abort);
+    tc_fence_after();
+    if (stop_b) {
+      aborted = true;
+      break;
+    }
+  }
+  if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv stores complete
+  if (aborted || warp < EPI0) return;
+  store_lambda(p, it, tb);
+}
+
+// ---------------------------------------------------------------------------
+// BAPPLY: the VJP of a chunk apply (one pass)
+// ---------------------------------------------------------------------------
+__device__ void run_apply_vjp(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
+                              uint32_t tb) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int H = p.H;
+  const int h = it.chain % H;
+  const int64_t t0 = it.t0, t1 = it.t1;
+  const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
+  const int nq = ntiles * NQ;
+  volatile int* abort = &B.abort_flag;
+  constexpr uint32_t IDESC_G1 = idesc_bf16(128, 64, false, false);
+  constexpr uint32_t IDESC_G2 = idesc_bf16(128, 32, false, false);
+  constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
+  constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
+  const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
+  const uint32_t row = 32u * (warp & 3) + lane;
+  const uint32_t lane_base = (32u * (warp & 3)) << 16;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int i = 0; i < ntiles; ++i) {
+        const int s = i & 1;
+        if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+        mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
+        uint8_t* xs = sm + AXY_OFF + s * 32768;
+        const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
+        tma_load_3d(xs, &maps.x_q, &B.xy_full[s], 0, h, tok);
+        tma_load_3d(xs + 8192, &maps.x_q, &B.xy_full[s], 0, h, tok + 64);
+        tma_load_3d(xs + 16384, &maps.y_do, &B.xy_full[s], 0, h, tok);
+        tma_load_3d(xs + 24576, &maps.y_do, &B.xy_full[s], 0, h, tok + 64);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t wq = smem_u32(sm + AW_OFF), stg = smem_u32(sm + AST_OFF);
+      // dq products of quarter m; after the tile's last quarter, its
+      // weight-adjoint products (A = the staged factors of all four quarters,
+      // hidden-unit blocks of 32 at a stride of one staging tile)
+      auto issue_acc = [&](int m) -> bool {
+        const int i = m / NQ, q = m % NQ;
+        if (!mbar_wait(&B.sq_full[q], i & 1, abort)) return false;
+        if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+        tc_fence_after();
+        const uint32_t wb = wq + q * AQ_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          mma_ss(tb + A_DX, sdesc_sw64(stg + ((ks / 2) * NQ + q) * ST_TILE + (ks % 2) * 32, 16, 512),
+                 sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+        if (q == NQ - 1) {
+          mma_commit(&B.acc_full);
+          const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
+#pragma unroll
+          for (int ks = 0; ks < BT / 16; ++ks) {
+            const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t xd = sdesc_sw128(xs + ks * 2048, 1024, 1024);
+            const uint64_t yd = sdesc_sw128(xs + 16384 + ks * 2048, 1024, 1024);
+            mma_ss(tb + B_L, sdesc_sw64(stg + 0 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 64, sdesc_sw64(stg + 1 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
+            mma_ss(tb + B_L + 128, sdesc_sw64(stg + 2 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), yd, IDESC_LAM,
+                   acc);
+          }
+          mma_commit(&B.st_free);            // the tile's staging may be overwritten
+          mma_commit(&B.xy_empty[i & 1]);    // its X/Y stage may be reloaded
+        }
+        return true;
+      };
+      bool ok = true;
+      for (int n = 0; n < nq && ok; ++n) {
+        const int i = n / NQ, q = n % NQ, b = n & 1;
+        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+        if (!mbar_wait(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
+        const uint32_t wb = wq + q * AQ_BYTES;
+        const uint32_t gb = tb + A_BUF + b * A_GBUF;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          mma_ss(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
+          mma_ss(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
+                 IDESC_G2, ks > 0);
+        }
+        mma_commit(&B.ga_full[b]);
+        if (n > 0) ok = issue_acc(n - 1);
+      }
+      if (ok && !*abort && nq > 0) ok = issue_acc(nq - 1);
+      if (ok && !*abort) mma_commit(&B.bdone);
+    }
+    __syncwarp();
+  } else if (warp == 2) {
+    // dq of every full tile by TMA store
+    if (lane == 0) {
+      for (int i = 0; i < ntiles; ++i) {
+        if (!mbar_wait(&B.out_full, i & 1, abort)) break;
+        const int64_t tok = t0 + (int64_t)i * BT;
+        if (tok + BT <= t1) {
+          tma_store_3d(&maps.s_dq, sm + ADQ_OFF, 0, h, (int32_t)tok);
+          tma_store_3d(&maps.s_dq, sm + ADQ_OFF + 8192, 0, h, (int32_t)(tok + 64));
+          bulk_commit();
+          bulk_wait_read_all();
+        }
+        mbar_arrive(&B.out_free);
+      }
+      bulk_wait_all();
+    }
+    __syncwarp();
+  } else {
+    // epilogue: thread = token row of the tile; half selects hidden units
+    // [16*half, 16*half + 16) of every quarter.
+    uint8_t* stg = sm + AST_OFF;
+    for (int n = 0; n < nq; ++n) {
+      const int i = n / NQ, q = n % NQ, b = n & 1;
+      const int64_t tok = t0 + (int64_t)i * BT + row;
+      const bool valid = tok < t1;
+      if (!mbar_wait(&B.ga_full[b], (n >> 1) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t buf = tb + lane_base + A_BUF + b * A_GBUF + 16 * half;
+      float r[3][16];   // zq1 zq3 du
+      tmem_ld16x3(buf, buf + 32, buf + 64, r[0], r[1], r[2]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&B.ga_free[b]);
+      float o[3][16];   // dzq1 dzq3 uq
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float z1 = r[0][k], z3 = r[1][k];
+        const float sg = sigmoid_fast(z1);
+        const float a = z1 * sg;
+        const float sp = fmaf(a, 1.f - sg, sg);
+        const float du = valid ? r[2][k] : 0.f;
+        o[0][k] = du * z3 * sp;
+        o[1][k] = du * a;
+        o[2][k] = valid ? a * z3 : 0.f;
+      }
+      // the tile's staging is free once the previous tile's products read it
+      if (q == 0 && !mbar_wait(&B.st_free, (i & 1) ^ 1, abort)) break;
+      {
+        const uint32_t c = 16u * half;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          uint8_t* t = stg + (m * NQ + q) * ST_TILE;
+          *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
+          *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      // one barrier per quarter slot: quarters of a tile do not wait for one
+      // another, so a single barrier could run two phases ahead of its waiter
+      if (lane == 0) mbar_arrive(&B.sq_full[q]);
+      if (q == NQ - 1) {
+        // tile finished: dq to shared memory for the TMA store (rows of a
+        // partial tile are stored directly)
+        if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+        tc_fence_after();
+        const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
+        if (full_tile && !mbar_wait(&B.out_free, (i & 1) ^ 1, abort)) break;
+        float v0[16], v1[16];
+        tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
+        tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
+        if (full_tile) {
+          stage_row64(sm + ADQ_OFF, row, half, v0, v1);
+        } else if (valid) {
+          store_row64(reinterpret_cast<__nv_bfloat16*>(p.dq) + ((size_t)tok * H + h) * D, half, v0, v1);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&B.acc_free);
+          mbar_arrive(&B.out_full);
+        }
+      }
+    }
+    // the last weight-adjoint products complete before they are read
+    mbar_wait(&B.bdone, 0, abort);
+  }
+  tc_fence_before();
+  const int stop = __syncthreads_or(*abort);
+  tc_fence_after();
+  if (stop || warp < EPI0) return;
+  store_lambda(p, it, tb);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
 bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const WorkItem* __restrict__ items) {
   extern __shared__ uint8_t smraw[];
@@ -499,6 +760,8 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.xy_full[i], 1);
       mbar_init(&B.xy_empty[i], 1);
+      mbar_init(&B.ga_full[i], 1);
+      mbar_init(&B.ga_free[i], 8);
       mbar_init(&B.eta_full[i], 4);
       mbar_init(&B.eta_free[i], 4);
     }
@@ -510,11 +773,14 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     mbar_init(&B.acc_full, 1);
     mbar_init(&B.acc_free, 8);
     mbar_init(&B.out_full, 8);
+    mbar_init(&B.out_free, 1);
     for (int i = 0; i < PB_STAGES; ++i) {
       mbar_init(&B.b_full[i], 1);
       mbar_init(&B.b_empty[i], 1);
     }
+    for (int i = 0; i < NQ; ++i) mbar_init(&B.sq_full[i], 8);
     mbar_init(&B.bdone, 1);
+    mbar_init(&B.wq_full, 1);
     B.abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(key ? &maps.x_k : &maps.x_q);
@@ -524,13 +790,16 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     tmem_alloc(&B.tmem_base, 512);
     tmem_relinquish();
   }
-  if (warp >= EPI0) load_weights(w, r, key, sm);
+  if (warp >= EPI0) {
+    if (key) load_weights_key(w, r, sm);
+    else load_weights_apply(w, sm);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = B.tmem_base;
-  if (key) run_item<true>(maps, p, it, sm, B, tb);
-  else run_item<false>(maps, p, it, sm, B, tb);
+  if (key) run_key_vjp(maps, p, it, sm, B, tb);
+  else run_apply_vjp(maps, p, it, sm, B, tb);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -549,6 +818,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
   }
   return fn;
+}
+
+// The BKEY scratch as a 5-D bf16 tensor [group][factor 3][quarter 4][32 tok][32 hidden]
+// (64-byte swizzle on the shared-memory side).
+bool make_scratch_map(CUtensorMap* m, void* base, int64_t groups, const cuuint32_t (&box)[5]) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[5] = {32, 32, 4, 3, (cuuint64_t)groups};
+  cuuint64_t strides[4] = {64, 2048, 8192, 24576};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, const_cast<cuuint32_t*>(box), es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 bool make_map(CUtensorMap* m, const void* base, int64_t T, int H, int box_tokens) {
@@ -575,12 +857,15 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
                                cudaStream_t st) {
   (void)step;
   if (n == 0) return cudaSuccess;
-  if (prm.T <= 0 || !prm.scratch) return cudaErrorInvalidValue;
+  if (prm.T <= 0 || !prm.scratch || prm.scratch_tiles <= 0) return cudaErrorInvalidValue;
   TmaMaps maps;
+  const cuuint32_t box_st[5] = {32, 32, 1, 1, 4}, box_ld[5] = {32, 32, 4, 3, 1};
+  if (!make_scratch_map(&maps.sc_st, prm.scratch, 4 * prm.scratch_tiles, box_st) ||
+      !make_scratch_map(&maps.sc_ld, prm.scratch, 4 * prm.scratch_tiles, box_ld))
+    return cudaErrorInvalidValue;
   if (!make_map(&maps.x_k, prm.k, prm.T, prm.H, 64) || !make_map(&maps.y_v, prm.v, prm.T, prm.H, 64) ||
       !make_map(&maps.x_q, prm.q, prm.T, prm.H, 64) || !make_map(&maps.y_do, prm.d_o, prm.T, prm.H, 64) ||
       !make_map(&maps.x_k32, prm.k, prm.T, prm.H, PB_T) || !make_map(&maps.y_v32, prm.v, prm.T, prm.H, PB_T) ||
-      !make_map(&maps.x_q32, prm.q, prm.T, prm.H, PB_T) || !make_map(&maps.y_do32, prm.d_o, prm.T, prm.H, PB_T) ||
       !make_map(&maps.s_dk, prm.dk, prm.T, prm.H, 64) || !make_map(&maps.s_dv, prm.dv, prm.T, prm.H, 64) ||
       !make_map(&maps.s_dq, prm.dq, prm.T, prm.H, 64))
     return cudaErrorInvalidValue;

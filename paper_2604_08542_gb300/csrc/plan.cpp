@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <queue>
 
 #include "ttt_internal.h"
 
@@ -52,6 +53,30 @@ std::vector<std::pair<int64_t, int64_t>> split(int64_t t0, int64_t t1, int n) {
   return out;
 }
 
+// Pieces per task.  Every task starts with one piece; then, while the step
+// has CTAs left, the task whose pieces are costliest gets one more.  This
+// minimises the costliest piece (which sets the step's duration) without
+// ever launching more pieces than CTAs.  A piece keeps at least one tile and
+// min_tokens tokens.
+std::vector<int> pieces_per_task(const std::vector<Task>& tasks, const Schedule& sch, int64_t ctas) {
+  std::vector<int> n(tasks.size(), 1);
+  std::priority_queue<std::pair<double, size_t>> heap;
+  for (size_t i = 0; i < tasks.size(); ++i) heap.push({(double)tasks[i].cost, i});
+  int64_t used = (int64_t)tasks.size();
+  while (used < ctas && !heap.empty()) {
+    const size_t i = heap.top().second;
+    heap.pop();
+    const int64_t len = tasks[i].t1 - tasks[i].t0;
+    const int64_t tiles = (len + kAlign - 1) / kAlign;
+    const int m = n[i] + 1;
+    if (m > tiles || len / m < sch.min_tokens) continue;   // cannot be cut further
+    n[i] = m;
+    ++used;
+    heap.push({(double)tasks[i].cost / m, i});
+  }
+  return n;
+}
+
 void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_sms, int waves,
                   bool backward, std::vector<WorkItem>& items, std::vector<UpdateItem>& upds,
                   std::vector<Step>& steps, int32_t& max_slots,
@@ -59,11 +84,8 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   Step st{};
   st.item0 = (int32_t)items.size();
   st.upd0 = (int32_t)upds.size();
-  double total = 0;
-  for (auto& t : tasks) total += t.cost;
   int ctas = sch.ctas_per_wave > 0 ? sch.ctas_per_wave : num_sms;
-  double target = std::max(1, waves * ctas);
-  double piece_cost = std::max((double)sch.min_tokens, total / target);
+  const std::vector<int> npieces = pieces_per_task(tasks, sch, std::max<int64_t>(1, (int64_t)waves * ctas));
   // pieces per task
   std::vector<WorkItem> step_items;
   // slots: per chain, slots are contiguous (key pieces, and in the backward
@@ -73,23 +95,23 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   for (auto& u : upd) {
     u.slot0 = slot;
     u.nslots = 0;
-    for (auto& t : tasks) {
+    for (size_t ti = 0; ti < tasks.size(); ++ti) {
+      const Task& t = tasks[ti];
       if (t.chain != u.chain) continue;
       bool reduces = backward || t.role == ROLE_KEY;
       if (!reduces) continue;
-      int n = std::max(1, (int)std::lround(t.cost / piece_cost));
-      for (auto& pr : split(t.t0, t.t1, n)) {
+      for (auto& pr : split(t.t0, t.t1, npieces[ti])) {
         WorkItem w{pr.first, pr.second, t.chain, t.role, slot++, t.seq, t.wchunk, 0};
         step_items.push_back(w);
         u.nslots++;
       }
     }
   }
-  for (auto& t : tasks) {
+  for (size_t ti = 0; ti < tasks.size(); ++ti) {
+    const Task& t = tasks[ti];
     bool reduces = backward || t.role == ROLE_KEY;
     if (reduces) continue;
-    int n = std::max(1, (int)std::lround(t.cost / piece_cost));
-    for (auto& pr : split(t.t0, t.t1, n)) {
+    for (auto& pr : split(t.t0, t.t1, npieces[ti])) {
       WorkItem w{pr.first, pr.second, t.chain, t.role, -1, t.seq, t.wchunk, 0};
       step_items.push_back(w);
     }
@@ -104,11 +126,12 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   std::stable_sort(step_items.begin(), step_items.end(),
                    [&](const WorkItem& a, const WorkItem& b) { return cost_of(a) > cost_of(b); });
   if (backward) {
-    // one sub-piece of scratch per piece (BF16 backward)
+    // one sub-piece of scratch and a weight image per update-VJP piece (BF16
+    // backward; the apply-VJP pieces keep their factors in shared memory)
     int32_t tiles = 0;
     for (auto& w : step_items) {
       w.aux = tiles;
-      tiles += kBwdSubTiles;
+      if (w.role == ROLE_BKEY) tiles += kBwdScratchTiles;
     }
     st.scratch_tiles = tiles;
   }
@@ -254,10 +277,12 @@ void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws
     prm.dw0_chain = (float*)c;
     c += al(chains * s.P() * sizeof(float));
     prm.scratch = (void*)(((uintptr_t)c + 1023) & ~(uintptr_t)1023);
+    prm.scratch_tiles = p.bscratch_tiles;
     c += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);
   } else {
     prm.rbuf = prm.drho = prm.dw0_chain = nullptr;
     prm.scratch = nullptr;
+    prm.scratch_tiles = 0;
   }
 }
 

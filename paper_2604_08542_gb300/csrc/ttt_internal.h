@@ -76,9 +76,11 @@ struct Plan {
   bool valid = false;
 };
 
-// BF16 backward: 128-token tiles per sub-piece (pass A then pass B); each
-// piece's scratch holds one sub-piece.
+// BF16 backward: 128-token tiles per sub-piece of an update-VJP piece (pass A
+// then pass B); each such piece's scratch holds one sub-piece and a copy of
+// the piece's bf16 weights.
 constexpr int kBwdSubTiles = 4;
+constexpr int kBwdScratchTiles = kBwdSubTiles + 1;
 
 // Scheduling knobs (the autotuner's search space).
 struct Schedule {
@@ -87,7 +89,7 @@ struct Schedule {
   int32_t bwd_waves = 1;       // backward: same for the backward steps
   int32_t min_tokens = 256;    // smallest piece (tokens)
   float key_cost = 2.0f;       // relative cost of a key token vs a query token
-  float bkey_cost = 2.0f;      // backward: key-side VJP vs apply-side VJP
+  float bkey_cost = 2.25f;     // backward: update-VJP token vs apply-VJP token (measured on GB300)
 };
 
 struct Shape {
@@ -126,6 +128,7 @@ struct Params {
   float* drho;      // backward: [chains][R]
   float* dw0_chain; // backward: [chains][P] per-chain dW0 (shared w0 only)
   void* scratch;    // backward, BF16 path: per-piece factors of the weight adjoints
+  int64_t scratch_tiles;   // its size in 96 KB tiles
   int* status;      // handle-owned status word
   // shape and options
   int32_t H, D, F, S;
