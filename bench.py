@@ -36,6 +36,14 @@ METRIC = "TTT-layer tokens/s fwd and fwd+bwd (BF16 vs FP32) + % tensor-core peak
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 NUM_SMS_GB300 = 152
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each sweep kernel, from an ncu capture of the named workload: backward step 1
+# (update VJP of chunk 1 with apply VJP of chunk 0) and forward step 3.  It
+# belongs to the kernels as they were captured: retake it when they change.
+NCU_TRAFFIC = {
+    "bf16_vggt64": {"bwd_sweep": 193_159_680 + 217_255_168, "fwd_sweep": 105_451_776 + 15_560_448},
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -318,6 +326,7 @@ def run_gpu(args, rank: int, world: int):
 
     # roofline of the dominant kernel (largest share of the timed region)
     pk, pk_src = peaks()
+    traffic = NCU_TRAFFIC.get(w.name, {})
     tot = sum(v["ms"] for v in prof.values())
     kernels = {}
     for name, v in prof.items():
@@ -343,7 +352,8 @@ def run_gpu(args, rank: int, world: int):
     else:
         peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
         roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": f"bf16_tflops ({pk_src})"}
+                "frac": achieved / peak, "traffic": traffic.get(dom), "traffic_unit": "bytes/launch",
+                "peak_source": f"bf16_tflops ({pk_src})"}
     # forward sweep roofline as well (the tensor-core kernel of the forward)
     fs = fprof["fwd_sweep"]
     fwd_sweep_tflops = fs["flops"] / (fs["ms"] / 1e3) / 1e12 if fs["ms"] > 0 else 0.0
