@@ -112,66 +112,64 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
   return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
 }
 
-// Eight consecutive values of W2 / R2 column f (rows col..col+7), i.e. of
-// row f of W2^T.
-__device__ __forceinline__ void load_col8(const float* m2, int f, int col, float* v) {
+// Weights into shared memory, bf16, in the 128-byte swizzled layout: each of
+// the 256 epilogue threads takes 8-value chunks (one row of W1, W3, -R1, -R3,
+// or a column of W2, R2 = a row of W2^T, -R2^T).  A batch of chunks is loaded
+// before any is stored, so the load costs a few round trips, not one per chunk.
+template <bool KEY, int BATCH>
+__device__ void load_weight_chunks(const float* w, const float* r, uint8_t* dst, uint32_t qbytes) {
+  constexpr int QROWS = KEY ? 192 : 96;   // rows of one quarter's block
+  const int t = threadIdx.x - 32 * EPI0;   // 256 epilogue threads
+  constexpr int NCH = NQ * QROWS * 8 / 256;   // chunks per thread
+  static_assert(NCH % BATCH == 0, "batch");
+#pragma unroll 1
+  for (int b0 = 0; b0 < NCH; b0 += BATCH) {
+    float v[BATCH][8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = m2[(size_t)(col + j) * F + f];
+    for (int i = 0; i < BATCH; ++i) {
+      const int c = t + 256 * (b0 + i);
+      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
+      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4), f = 32 * q + rr % 32;
+      if (blk < 4) {   // W1, W3, R1, R3: row f
+        const float4* src = reinterpret_cast<const float4*>(
+            (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col);
+        const float4 a = __ldg(src), bq = __ldg(src + 1);
+        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
+        v[i][4] = bq.x; v[i][5] = bq.y; v[i][6] = bq.z; v[i][7] = bq.w;
+      } else {         // W2, R2 [D][F]: column f
+        const float* src = (blk == 4 ? w : r) + 2 * (size_t)F * D + f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[i][j] = __ldg(src + (size_t)(col + j) * F);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < BATCH; ++i) {
+      const int c = t + 256 * (b0 + i);
+      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
+      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4);
+      if (blk == 2 || blk == 3 || blk == 5) {   // the adjoint enters negated
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[i][j] = -v[i][j];
+      }
+      *reinterpret_cast<uint4*>(dst + q * qbytes + sw128_offset(rr, col)) = pack8(v[i]);
+    }
+  }
+  fence_proxy_async_smem();
 }
 
-// BKEY weights into shared memory, bf16, quarter-major:
+// BKEY weights, quarter-major:
 //   quarter q rows   0.. 31 W1[32q + r][:]      rows  32.. 63 W3[32q + r][:]
 //                   64.. 95 -R1[32q + r][:]     rows  96..127 -R3[32q + r][:]
 //                  128..159 W2[:][32q + r]      rows 160..191 -R2[:][32q + r]
-// each row 64 values (d) in the 128-byte swizzled layout.
+// each row 64 values (d).
 __device__ void load_weights_key(const float* w, const float* r, uint8_t* sm) {
-  const int t = threadIdx.x - 32 * EPI0;   // 256 epilogue threads
-#pragma unroll 4
-  for (int c = t; c < NQ * 192 * 8; c += 256) {
-    const int q = c / (192 * 8);
-    const int rr = (c / 8) % 192;
-    const int col = (c % 8) * 8;
-    const int blk = rr / 32, f = 32 * q + rr % 32;
-    float v[8];
-    if (blk < 4) {
-      const float* src = (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col;
-      const float4 a = *reinterpret_cast<const float4*>(src);
-      const float4 b = *reinterpret_cast<const float4*>(src + 4);
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-      load_col8((blk == 4 ? w : r) + 2 * (size_t)F * D, f, col, v);
-    }
-    if (blk == 2 || blk == 3 || blk == 5) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = -v[j];
-    }
-    *reinterpret_cast<uint4*>(sm + WQ_OFF + q * QBYTES + sw128_offset(rr, col)) = pack8(v);
-  }
-  fence_proxy_async_smem();
+  load_weight_chunks<true, 12>(w, r, sm + WQ_OFF, QBYTES);
 }
 
 // BAPPLY weights: quarter q rows 0..31 W1[32q + r][:], 32..63 W3[32q + r][:],
-// 64..95 W2[:][32q + r], 128-byte swizzle.
+// 64..95 W2[:][32q + r].
 __device__ void load_weights_apply(const float* w, uint8_t* sm) {
-  const int t = threadIdx.x - 32 * EPI0;
-#pragma unroll 4
-  for (int c = t; c < NQ * 96 * 8; c += 256) {
-    const int q = c / (96 * 8);
-    const int rr = (c / 8) % 96;
-    const int col = (c % 8) * 8;
-    const int blk = rr / 32, f = 32 * q + rr % 32;
-    float v[8];
-    if (blk < 2) {
-      const float* src = w + (size_t)blk * F * D + (size_t)f * D + col;
-      const float4 a = *reinterpret_cast<const float4*>(src);
-      const float4 b = *reinterpret_cast<const float4*>(src + 4);
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
-      load_col8(w + 2 * (size_t)F * D, f, col, v);
-    }
-    *reinterpret_cast<uint4*>(sm + AW_OFF + q * AQ_BYTES + sw128_offset(rr, col)) = pack8(v);
-  }
-  fence_proxy_async_smem();
+  load_weight_chunks<false, 12>(w, w, sm + AW_OFF, AQ_BYTES);
 }
 
 // 32 fp32 accumulator columns of this thread's token row -> bf16 in a

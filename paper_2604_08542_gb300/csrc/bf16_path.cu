@@ -238,27 +238,35 @@ __device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& i
 
 // Weights into TMEM as A operands: lane f holds W1[f][:], W3[f][:], W2[:][f]
 // as bf16 pairs along d.
+// All loads of a thread are issued before any of its TMEM stores (those are
+// ordered against memory), so the weights cost one round trip, not one per chunk.
 __device__ void key_load_weights(const float* w, uint32_t tb) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int ew = warp - 2, half = ew >> 2;
   const uint32_t f = 32u * (warp & 3) + lane;
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  uint32_t r[16];
-  // half 0: W1 row f; half 1: W3 row f
-  const float* src = w + (size_t)half * F * D + (size_t)f * D;
+  // half 0: W1 row f; half 1: W3 row f (64 values)
+  const float4* row = reinterpret_cast<const float4*>(w + (size_t)half * F * D + (size_t)f * D);
+  float4 a[16];
 #pragma unroll
-  for (int c0 = 0; c0 < 32; c0 += 16) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) r[j] = pack_bf16(src[2 * (c0 + j)], src[2 * (c0 + j) + 1]);
-    tmem_st16(tb + lane_base + (half ? K_AW3 : K_AW1) + c0, r);
-  }
+  for (int j = 0; j < 16; ++j) a[j] = __ldg(row + j);
   // W2^T row f = column f of W2 [D][F]; half h covers d in [32h, 32h + 32)
-  const float* w2 = w + 2 * (size_t)F * D;
+  const float* w2 = w + 2 * (size_t)F * D + f;
+  float b[32];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int d = 32 * half + 2 * j;
-    r[j] = pack_bf16(w2[(size_t)d * F + f], w2[(size_t)(d + 1) * F + f]);
+  for (int j = 0; j < 32; ++j) b[j] = __ldg(w2 + (size_t)(32 * half + j) * F);
+  uint32_t r[16];
+#pragma unroll
+  for (int c0 = 0; c0 < 2; ++c0) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      r[2 * j] = pack_bf16(a[8 * c0 + j].x, a[8 * c0 + j].y);
+      r[2 * j + 1] = pack_bf16(a[8 * c0 + j].z, a[8 * c0 + j].w);
+    }
+    tmem_st16(tb + lane_base + (half ? K_AW3 : K_AW1) + 16 * c0, r);
   }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) r[j] = pack_bf16(b[2 * j], b[2 * j + 1]);
   tmem_st16(tb + lane_base + K_AW2T + 16 * half, r);
   tmem_st_wait();
 }
@@ -268,28 +276,39 @@ __device__ void key_load_weights(const float* w, uint32_t tb) {
 // ---------------------------------------------------------------------------
 __device__ void apply_load_weights(const float* w, uint8_t* sm) {
   // [W1; W3] as 256 rows x 64 (K-major, swizzled) and W2 as two [64][64]
-  // K-blocks (rows d, columns f).  One 16-byte chunk (8 elements) per step.
+  // K-blocks (rows d, columns f).  Chunks of 8 values: 8 of [W1; W3] and 4 of
+  // W2 per thread, all loaded before any is stored.
   uint8_t* wb13 = sm;
   uint8_t* wb2 = sm + 2 * F * 128;
   const int t = threadIdx.x - 64;   // epilogue threads 0..255
-#pragma unroll 4
-  for (int c = t; c < 2 * F * 8; c += 256) {
-    const int r = c >> 3, col = (c & 7) * 8;
-    const float* src = w + (size_t)r * D + col;   // W1 rows then W3 rows, contiguous
-    const float4 a = *reinterpret_cast<const float4*>(src);
-    const float4 bq = *reinterpret_cast<const float4*>(src + 4);
-    uint4 pk = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(bq.x, bq.y), pack_bf16(bq.z, bq.w));
-    *reinterpret_cast<uint4*>(wb13 + sw128_offset(r, col)) = pk;
+  constexpr int N13 = 2 * F * 8 / 256, N2 = D * (F / 8) / 256;
+  float4 v[N13 + N2][2];
+#pragma unroll
+  for (int i = 0; i < N13; ++i) {
+    const int c = t + 256 * i;
+    const float4* src = reinterpret_cast<const float4*>(w + (size_t)(c >> 3) * D + (c & 7) * 8);
+    v[i][0] = __ldg(src);
+    v[i][1] = __ldg(src + 1);
   }
   const float* w2 = w + 2 * (size_t)F * D;
-#pragma unroll 4
-  for (int c = t; c < D * (F / 8); c += 256) {
-    const int r = c / (F / 8), col = (c % (F / 8)) * 8;   // row d, first f of the chunk
-    const float* src = w2 + (size_t)r * F + col;
-    const float4 a = *reinterpret_cast<const float4*>(src);
-    const float4 bq = *reinterpret_cast<const float4*>(src + 4);
-    uint4 pk = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(bq.x, bq.y), pack_bf16(bq.z, bq.w));
-    *reinterpret_cast<uint4*>(wb2 + (col / 64) * (D * 128) + sw128_offset(r, col % 64)) = pk;
+#pragma unroll
+  for (int i = 0; i < N2; ++i) {
+    const int c = t + 256 * i;
+    const float4* src = reinterpret_cast<const float4*>(w2 + (size_t)(c / (F / 8)) * F + (c % (F / 8)) * 8);
+    v[N13 + i][0] = __ldg(src);
+    v[N13 + i][1] = __ldg(src + 1);
+  }
+#pragma unroll
+  for (int i = 0; i < N13 + N2; ++i) {
+    const int c = t + 256 * (i < N13 ? i : i - N13);
+    const float4 a = v[i][0], bq = v[i][1];
+    const uint4 pk = make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(bq.x, bq.y), pack_bf16(bq.z, bq.w));
+    if (i < N13) {
+      *reinterpret_cast<uint4*>(wb13 + sw128_offset(c >> 3, (c & 7) * 8)) = pk;
+    } else {
+      const int r = c / (F / 8), col = (c % (F / 8)) * 8;   // row d, first f of the chunk
+      *reinterpret_cast<uint4*>(wb2 + (col / 64) * (D * 128) + sw128_offset(r, col % 64)) = pk;
+    }
   }
   fence_proxy_async_smem();
 }
