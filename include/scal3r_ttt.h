@@ -160,6 +160,55 @@ int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg,
                                void* o, float* w_ckpt, float* wnorm, float* w_final,
                                void* stream);
 
+/* ---- Global Context Synchronisation (Sec. 4.2, Eq. 10) -------------------
+ * When one chunk's tokens are spread over several processes (GPUs), the
+ * chunk gradient is the sum of the per-process gradients over their token
+ * shards, all taken at the same weights (Eq. 10).  These three calls split a
+ * chunk step into its local parts, so that a caller can sum the gradients
+ * with any collective (an all-reduce over NCCL, MPI, ...) in between:
+ *   partial_grad (each process, its shard) -> all-reduce(sum) ->
+ *   apply_update (each process, identical result) -> apply (its queries).
+ * With one process this is exactly scal3r_ttt_forward on a layout with one
+ * chunk per sequence.  The layouts passed to partial_grad and apply give
+ * every sequence at most one chunk (the process's shard); otherwise
+ * SCAL3R_ERR_INVALID_ARG.  The token tensors, lr, workspace and stream mean
+ * what they mean for scal3r_ttt_forward.  Not available on the
+ * allocation-free entry point. */
+
+/* The gradient G = d/dW sum_i lr_i L(f_W(k_i), v_i) of Eq. 8 over the tokens
+ * of each sequence's chunk, at the weights w (no update is made).
+ *   w     float32 weights per sequence, [H,P] at w_seq_stride floats (0 = the
+ *         same weights for every sequence), P = 3*F*D, packed W1, W3, W2.
+ *   grad  [S,H,P] float32 out; a sequence without a chunk gets zeros.
+ *   workspace: at least scal3r_ttt_workspace_size(.., 0) bytes for this layout. */
+int scal3r_ttt_partial_grad(scal3r_ttt_handle* handle,
+                            const void* k, const void* v, const float* lr,
+                            const float* w, int64_t w_seq_stride,
+                            const int64_t* chunk_offsets, int32_t num_chunks,
+                            const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                            float* grad, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The update of Eq. 8 with a gradient summed outside: w_out = W - grad, with
+ * every row rescaled by the handle's weight_norm (targets from w0, as in the
+ * forward).  Per sequence s and head h.
+ *   w     [H,P] per sequence at w_seq_stride (0 = shared); grad [S,H,P].
+ *   w0    the sequence's starting weights, for the row targets, at w0_seq_stride.
+ *   w_out [S,H,P] out; wnorm [S,H,2F+D] out or NULL: each row's L2 norm before
+ *         rescaling (the forward's wnorm).  No workspace. */
+int scal3r_ttt_apply_update(scal3r_ttt_handle* handle,
+                            const float* w, int64_t w_seq_stride, const float* grad,
+                            const float* w0, int64_t w0_seq_stride, int32_t num_seqs,
+                            float* w_out, float* wnorm, void* stream);
+
+/* The apply of Eq. 4, o = f_W(q), for the tokens of each sequence's chunk
+ * with that sequence's weights w ([H,P] at w_seq_stride).  o [T,H,D] out in
+ * the dtype of q. */
+int scal3r_ttt_apply(scal3r_ttt_handle* handle, const void* q,
+                     const float* w, int64_t w_seq_stride,
+                     const int64_t* chunk_offsets, int32_t num_chunks,
+                     const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                     void* o, void* workspace, size_t workspace_bytes, void* stream);
+
 /* Backward pass: gradients of sum(d_o * o) through every chunk update.
  *   d_o      [T,H,D] upstream gradient, dtype of q.
  *   w_ckpt, wnorm: as written by the forward on the same inputs.

@@ -48,7 +48,8 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
-            "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc")
+            "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
+            "scal3r_ttt_apply_update", "scal3r_ttt_apply")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -121,6 +122,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_profile_read.restype = ctypes.c_int
     lib.scal3r_ttt_get_status.argtypes = [vp, vp]
     lib.scal3r_ttt_get_status.restype = ctypes.c_int
+    lib.scal3r_ttt_partial_grad.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp]
+    lib.scal3r_ttt_partial_grad.restype = ctypes.c_int
+    lib.scal3r_ttt_apply_update.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp]
+    lib.scal3r_ttt_apply_update.restype = ctypes.c_int
+    lib.scal3r_ttt_apply.argtypes = [vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp]
+    lib.scal3r_ttt_apply.restype = ctypes.c_int
     _lib_handle = lib
     return lib
 
@@ -191,6 +198,27 @@ def scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, chunk_offsets, s
     return load_library().scal3r_ttt_backward(handle, q, k, v, lr, w0, w0_seq_stride, off.ctypes.data,
                                               len(off) - 1, ptr.ctypes.data, len(ptr) - 1, d_o, w_ckpt, wnorm,
                                               dq, dk, dv, dlr, dw0, workspace, workspace_bytes, stream)
+
+
+def scal3r_ttt_partial_grad(handle, k, v, lr, w, w_seq_stride, chunk_offsets, seq_chunk_ptr, grad,
+                            workspace, workspace_bytes, stream) -> int:
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    return load_library().scal3r_ttt_partial_grad(handle, k, v, lr, w, w_seq_stride, off.ctypes.data, len(off) - 1,
+                                                  ptr.ctypes.data, len(ptr) - 1, grad, workspace, workspace_bytes,
+                                                  stream)
+
+
+def scal3r_ttt_apply_update(handle, w, w_seq_stride, grad, w0, w0_seq_stride, num_seqs, w_out, wnorm,
+                            stream) -> int:
+    return load_library().scal3r_ttt_apply_update(handle, w, w_seq_stride, grad, w0, w0_seq_stride, num_seqs,
+                                                  w_out, wnorm, stream)
+
+
+def scal3r_ttt_apply(handle, q, w, w_seq_stride, chunk_offsets, seq_chunk_ptr, o, workspace, workspace_bytes,
+                     stream) -> int:
+    off, ptr = _host_layout(chunk_offsets, seq_chunk_ptr)
+    return load_library().scal3r_ttt_apply(handle, q, w, w_seq_stride, off.ctypes.data, len(off) - 1,
+                                           ptr.ctypes.data, len(ptr) - 1, o, workspace, workspace_bytes, stream)
 
 
 def scal3r_ttt_set_schedule(handle: int, sch: scal3r_ttt_schedule) -> None:

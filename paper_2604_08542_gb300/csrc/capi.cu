@@ -622,6 +622,133 @@ int scal3r_ttt_profile_read(scal3r_ttt_handle* hd, int32_t kind, int64_t* launch
   return SCAL3R_OK;
 }
 
+// ---- Global Context Synchronisation (Eq. 10) ---------------------------------
+
+namespace {
+// The layout gives every sequence at most one chunk (the caller's shard of the
+// chunk being synchronised).
+bool one_chunk_per_seq(const Plan& pl) {
+  for (int32_t s = 0; s < pl.S; ++s)
+    if (pl.seq_chunk_ptr[s + 1] - pl.seq_chunk_ptr[s] > 1) return false;
+  return true;
+}
+}  // namespace
+
+int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v, const float* lr, const float* w,
+                            int64_t w_seq_stride, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S,
+                            float* grad, void* workspace, size_t workspace_bytes_, void* stream) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  int rc = ensure_plan(hd, off, C, ptr, S);
+  if (rc != SCAL3R_OK) return rc;
+  const Plan& pl = hd->plan;
+  const Shape& sh = hd->shape;
+  if (!one_chunk_per_seq(pl)) return SCAL3R_ERR_INVALID_ARG;
+  if (pl.T > 0 && (!k || !v || !lr)) return SCAL3R_ERR_INVALID_ARG;
+  if (!w || !grad || w_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
+  if (w_seq_stride != 0 && w_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
+  if (!aligned16(k) || !aligned16(v) || !aligned16(lr) || !aligned16(w) || !aligned16(grad) ||
+      (w_seq_stride & 3) != 0)
+    return SCAL3R_ERR_MISALIGNED;
+  const size_t need = workspace_bytes(pl, sh, false);
+  if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
+
+  Params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  fill_common(hd, prm);
+  prm.q = k;   // no query is read; the token maps need a valid tensor
+  prm.k = k;
+  prm.v = v;
+  prm.lr = lr;
+  prm.w0 = w;
+  prm.w0_seq_stride = w_seq_stride;
+  carve_workspace(pl, sh, false, workspace, prm);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chains = pl.S * sh.H;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  const Step& s0 = pl.steps[0];   // the gradient pieces of every sequence's chunk, at w
+  double fl = 0, by = 0;
+  if (hd->prof_on) sweep_work(hd, pl.items.data() + s0.item0, s0.nitems, fl, by);
+  if (s0.nitems > 0 && timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s0.item0, s0.nitems, 0, nullptr, st)
+                                            : launch_fp32_sweep(prm, pl.d_items + s0.item0, s0.nitems, 0, st);
+      }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st,
+            [&] { return launch_gsum(prm, pl.d_updates + s0.upd0, s0.nupd, grad, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_apply_update(scal3r_ttt_handle* hd, const float* w, int64_t w_seq_stride, const float* grad,
+                            const float* w0, int64_t w0_seq_stride, int32_t num_seqs, float* w_out, float* wnorm,
+                            void* stream) {
+  if (!hd || num_seqs < 0) return SCAL3R_ERR_INVALID_ARG;
+  const Shape& sh = hd->shape;
+  if (num_seqs == 0) return SCAL3R_OK;
+  if (!w || !grad || !w0 || !w_out || w_seq_stride < 0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
+  for (int64_t stride : {w_seq_stride, w0_seq_stride})
+    if (stride != 0 && stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
+  if (!aligned16(w) || !aligned16(grad) || !aligned16(w0) || !aligned16(w_out) || (w_seq_stride & 3) != 0 ||
+      (w0_seq_stride & 3) != 0)
+    return SCAL3R_ERR_MISALIGNED;
+  Params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  fill_common(hd, prm);
+  prm.S = num_seqs;
+  prm.w0 = w0;
+  prm.w0_seq_stride = w0_seq_stride;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
+        return launch_gcs_update(prm, num_seqs * sh.H, w, w_seq_stride, grad, w_out, wnorm, st);
+      }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64_t w_seq_stride, const int64_t* off,
+                     int32_t C, const int32_t* ptr, int32_t S, void* o, void* workspace, size_t workspace_bytes_,
+                     void* stream) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  int rc = ensure_plan(hd, off, C, ptr, S);
+  if (rc != SCAL3R_OK) return rc;
+  const Plan& pl = hd->plan;
+  const Shape& sh = hd->shape;
+  if (!one_chunk_per_seq(pl)) return SCAL3R_ERR_INVALID_ARG;
+  if (pl.T > 0 && (!q || !o)) return SCAL3R_ERR_INVALID_ARG;
+  if (!w || w_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
+  if (w_seq_stride != 0 && w_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
+  if (!aligned16(q) || !aligned16(o) || !aligned16(w) || (w_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
+  const size_t need = workspace_bytes(pl, sh, false);
+  if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
+  if (pl.T == 0 || pl.steps.size() < 2) return SCAL3R_OK;   // no token to apply
+
+  Params prm;
+  std::memset(&prm, 0, sizeof(prm));
+  fill_common(hd, prm);
+  prm.q = q;
+  prm.k = q;   // no key or value is read; the token maps need a valid tensor
+  prm.v = q;
+  prm.o = o;
+  prm.w0 = w;
+  prm.w0_seq_stride = w_seq_stride;
+  carve_workspace(pl, sh, false, workspace, prm);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chains = pl.S * sh.H;
+  // chunk step 1 applies each sequence's chunk with master buffer 1
+  if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_loadw(prm, chains, 1, st); }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  const Step& s1 = pl.steps[1];
+  double fl = 0, by = 0;
+  if (hd->prof_on) sweep_work(hd, pl.items.data() + s1.item0, s1.nitems, fl, by);
+  if (s1.nitems > 0 && timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s1.item0, s1.nitems, 1, nullptr, st)
+                                            : launch_fp32_sweep(prm, pl.d_items + s1.item0, s1.nitems, 1, st);
+      }) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
 int scal3r_ttt_get_status(scal3r_ttt_handle* hd, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return SCAL3R_ERR_CUDA;

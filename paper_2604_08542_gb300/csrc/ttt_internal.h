@@ -148,6 +148,10 @@ cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st);
 cudaError_t launch_update(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st);
 cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st);
 cudaError_t launch_bfinal(const Params& prm, cudaStream_t st);
+cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, float* grad, cudaStream_t st);
+cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st);
+cudaError_t launch_gcs_update(const Params& prm, int chains, const float* w, int64_t w_stride, const float* g,
+                              float* w_out, float* wnorm, cudaStream_t st);
 cudaError_t launch_fp32_sweep(const Params& prm, const WorkItem* items, int nitems, int step, cudaStream_t st);
 cudaError_t launch_fp32_bsweep(const Params& prm, const WorkItem* items, int nitems, int step, cudaStream_t st);
 cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int nitems, int step,

@@ -200,6 +200,57 @@ __global__ void bfinal_kernel(Params p) {
   }
 }
 
+// ---- Global Context Synchronisation (Eq. 10): a chunk's gradient summed over
+// token shards held by several callers, then one update applied by each.
+
+// The chunk gradient of every chain over this call's tokens: G = -(sum of the
+// step's forward slots, which hold the increments), in the packed layout.
+// Chains without a chunk get G = 0.
+__global__ void gsum_kernel(Params p, const UpdateItem* __restrict__ upd, float* grad) {
+  const UpdateItem u = upd[blockIdx.x];
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
+  if (!s.valid) return;
+  const int P = 3 * p.F * p.D;
+  const int h = u.chain % p.H;
+  float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (u.chunk >= 0)
+    for (int sl = 0; sl < u.nslots; ++sl) x = add4(x, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
+  st4(grad + ((size_t)u.seq * p.H + h) * P + s.off, scale4(x, -1.f));
+}
+
+// The weights given in (w0, w0_seq_stride) into master buffer `buf`.
+__global__ void loadw_kernel(Params p, int buf) {
+  const int chain = blockIdx.x;
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
+  if (!s.valid) return;
+  const int P = 3 * p.F * p.D;
+  st4(p.wm + ((size_t)buf * p.S * p.H + chain) * P + s.off, ld4(chain_w0(p, chain) + s.off));
+}
+
+// W_next = W - G with every row rescaled to its target (taken from w0, as in
+// the forward), per chain; the pre-rescale row norms optionally.
+__global__ void gcs_update_kernel(Params p, const float* w, int64_t w_stride, const float* g, float* w_out,
+                                  float* wnorm) {
+  const int chain = blockIdx.x;
+  const int seq = chain / p.H, h = chain % p.H;
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
+  const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
+  float4 x = make_float4(0.f, 0.f, 0.f, 0.f), t = x;
+  if (s.valid) {
+    const float4 a = ld4(w + (size_t)seq * w_stride + (size_t)h * P + s.off);
+    const float4 b = ld4(g + (size_t)chain * P + s.off);
+    x = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    t = ld4(chain_w0(p, chain) + s.off);
+  }
+  const float n = sqrtf(group_sum(dot4(x, x), s.group));
+  const float ss = group_sum(dot4(t, t), s.group);
+  if (!s.valid) return;
+  float scale = 1.f;
+  if (p.norm != SCAL3R_NORM_NONE) scale = row_target(p, ss) / fmaxf(n, p.eps);
+  st4(w_out + (size_t)chain * P + s.off, scale4(x, scale));
+  if (wnorm && s.c4 == 0) wnorm[(size_t)chain * R + s.r] = n;
+}
+
 int row_blocks(const Params& p) { return (2 * p.F * p.D + 1023) / 1024 + (p.F * p.D + 1023) / 1024; }
 
 }  // namespace
@@ -232,6 +283,25 @@ cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st) {
   if (chains == 0) return cudaSuccess;
   bprep_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, float* grad, cudaStream_t st) {
+  if (nupd == 0) return cudaSuccess;
+  gsum_kernel<<<dim3(nupd, row_blocks(prm)), kThreads, 0, st>>>(prm, upd, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st) {
+  if (chains == 0) return cudaSuccess;
+  loadw_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm, buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gcs_update(const Params& prm, int chains, const float* w, int64_t w_stride, const float* g,
+                              float* w_out, float* wnorm, cudaStream_t st) {
+  if (chains == 0) return cudaSuccess;
+  gcs_update_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm, w, w_stride, g, w_out, wnorm);
   return cudaGetLastError();
 }
 

@@ -67,3 +67,27 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def gcs_forward(q, k, v, lr, w0, chunk_bounds, *, partial_grad, apply_update, apply, all_reduce):
+    """One sequence under Global Context Synchronisation (Sec. 4.2, Eq. 10):
+    the tokens of every chunk are spread over the ranks, and this rank holds
+    rows [a, b) of its own q, k, v, lr arrays for chunk j
+    (chunk_bounds[j] = (a, b); an empty range is allowed).
+
+    For each chunk, in order:
+      G_local = partial_grad(k[a:b], v[a:b], lr[a:b], W)   this rank's tokens
+      G = all_reduce(G_local)                              the sum over ranks
+      W = apply_update(W, G, w0)                           the same on every rank
+      o[a:b] = apply(q[a:b], W)                            this rank's queries
+    and W starts at w0.  The callables are whatever computes those pieces for
+    this rank (the library's calls on a GPU, or a reference); this function
+    only orders them.  Returns (the list of per-chunk outputs, the final W).
+    """
+    w = w0
+    outs = []
+    for a, b in chunk_bounds:
+        g = all_reduce(partial_grad(k[a:b], v[a:b], lr[a:b], w))
+        w = apply_update(w, g, w0)
+        outs.append(apply(q[a:b], w))
+    return outs, w

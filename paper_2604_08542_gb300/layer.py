@@ -20,7 +20,8 @@ from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3
                SCAL3R_NORM_ROW_W0, SCAL3R_NORM_UNIT, Scal3rError, _check, scal3r_ttt_autotune, scal3r_ttt_backward,
                scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_schedule,
                scal3r_ttt_get_status, scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_schedule,
-               scal3r_ttt_set_graph_mode, scal3r_ttt_set_schedule, scal3r_ttt_workspace_size)
+               scal3r_ttt_set_graph_mode, scal3r_ttt_set_schedule, scal3r_ttt_workspace_size,
+               scal3r_ttt_partial_grad, scal3r_ttt_apply_update, scal3r_ttt_apply)
 
 NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
 LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
@@ -129,6 +130,54 @@ class TTT:
                                  _ptr(dw0), _ptr(ws), ws.numel(), st)
         _check(rc, "scal3r_ttt_backward")
         return dq, dk, dv, dlr, dw0
+
+    # -- Global Context Synchronisation (Eq. 10): a chunk step in local parts ----
+    def partial_grad(self, k, v, lr, w, chunk_offsets, seq_chunk_ptr, *, workspace=None):
+        """The inner gradient of Eq. 8 over each sequence's (single) chunk at
+        the weights w ([H, P] or [S, H, P]); returns grad [S, H, P] float32."""
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        T, S = int(off[-1]), len(ptr) - 1
+        for n, t in (("k", k), ("v", v)):
+            self._check_tokens(n, t, T)
+        if lr.dtype != torch.float32 or tuple(lr.shape) != (T, self.H) or not lr.is_contiguous():
+            raise ValueError("lr must be a contiguous float32 tensor of shape [T, H]")
+        stride = self._w0_stride(w, S)
+        grad = torch.empty((S, self.H, self.P), dtype=torch.float32, device=k.device)
+        ws = self.workspace(off, ptr, False, k.device) if workspace is None else workspace
+        st = torch.cuda.current_stream(k.device).cuda_stream
+        _check(scal3r_ttt_partial_grad(self.handle, _ptr(k), _ptr(v), _ptr(lr), _ptr(w), stride, off, ptr,
+                                       _ptr(grad), _ptr(ws), ws.numel(), st), "scal3r_ttt_partial_grad")
+        return grad
+
+    def apply_update(self, w, grad, w0):
+        """W - grad with the rows rescaled (targets from w0); returns
+        (w_next [S, H, P], wnorm [S, H, 2F+D])."""
+        if grad.dtype != torch.float32 or grad.dim() != 3 or grad.shape[1:] != (self.H, self.P) \
+                or not grad.is_contiguous():
+            raise ValueError("grad must be a contiguous float32 tensor [S, H, 3*F*D]")
+        S = grad.shape[0]
+        ws, w0s = self._w0_stride(w, S), self._w0_stride(w0, S)
+        w_out = torch.empty_like(grad)
+        wnorm = torch.empty((S, self.H, self.R), dtype=torch.float32, device=grad.device)
+        st = torch.cuda.current_stream(grad.device).cuda_stream
+        _check(scal3r_ttt_apply_update(self.handle, _ptr(w), ws, _ptr(grad), _ptr(w0), w0s, S, _ptr(w_out),
+                                       _ptr(wnorm), st), "scal3r_ttt_apply_update")
+        return w_out, wnorm
+
+    def apply(self, q, w, chunk_offsets, seq_chunk_ptr, *, workspace=None):
+        """o = f_W(q) for each sequence's (single) chunk with its weights w."""
+        off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
+        ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+        T, S = int(off[-1]), len(ptr) - 1
+        self._check_tokens("q", q, T)
+        stride = self._w0_stride(w, S)
+        o = torch.empty_like(q)
+        ws = self.workspace(off, ptr, False, q.device) if workspace is None else workspace
+        st = torch.cuda.current_stream(q.device).cuda_stream
+        _check(scal3r_ttt_apply(self.handle, _ptr(q), _ptr(w), stride, off, ptr, _ptr(o), _ptr(ws), ws.numel(), st),
+               "scal3r_ttt_apply")
+        return o
 
     def status(self) -> int:
         return scal3r_ttt_get_status(self.handle, torch.cuda.current_stream().cuda_stream)
