@@ -34,17 +34,18 @@
 // copied back while the second pass finishes.
 //
 // BAPPLY needs only W1, W3, W2^T (48 KB), so the tile's factors of all four
-// quarters stay in shared memory and every tile is finished in one pass:
+// quarters stay in shared memory and every tile is finished in one pass
+// (bf16_token_lane.cuh, shared with the forward's gradient pieces):
 //   G1 = X [W1_q; W3_q]^T -> zq1, zq3,   G2 = Y [W2^T_q]^T -> du = W2^T d_o
 //   dzq1 = du z3 s', dzq3 = du a, uq = a z3
 //   dq += [dzq1 dzq3] [W1_q; W3_q]                          (K 64)
 //   after the fourth quarter: L1 += dzq1^T X, L3 += dzq3^T X, L2t += uq^T Y
-// Its G buffer is double-buffered in TMEM.
 //
 // dk/dv/dq are staged in shared memory and written by TMA tile stores.
 // Warps: 0 TMA loads, 1 MMA issue, 2 bulk / TMA stores, 3..10 epilogue.
 #include <cudaTypedefs.h>
 
+#include "bf16_token_lane.cuh"
 #include "sm100.cuh"
 #include "ttt_internal.h"
 
@@ -53,13 +54,16 @@ namespace {
 
 using namespace sm100;
 
-constexpr int D = 64;
-constexpr int F = 128;
+using tl::BT;
+using tl::D;
+using tl::F;
+using tl::NQ;
+using tl::ST_TILE;
+using tl::pack8;
+using tl::stage_row64;
+using tl::store_row64;
 constexpr int NTHREADS = 352;
 constexpr int EPI0 = 3;                      // first epilogue warp
-constexpr int BT = 128;                      // tile (tokens)
-constexpr int NQ = 4;                        // hidden-unit quarters
-constexpr uint32_t ST_TILE = 8192;           // [128 tok][32 hidden] bf16, 64-byte swizzle
 
 // BKEY shared memory
 constexpr uint32_t QBYTES = 24 * 1024;       // weights of one quarter: 192 rows x 128 B
@@ -74,21 +78,12 @@ constexpr int PB_WQ_STAGES = 3;              // stages 0..2 lie over the weights
 constexpr uint32_t WQ_BYTES = 4 * QBYTES;
 constexpr uint32_t TILE_SCRATCH = 3 * 4 * ST_TILE;   // [factor][quarter][128 tok][32 hidden] bf16, 96 KB
 
-// BAPPLY shared memory
-constexpr uint32_t AQ_BYTES = 12 * 1024;     // W1_q, W3_q, W2^T_q: 96 rows x 128 B
-constexpr uint32_t AW_OFF = 0;               // 4 quarters, 48 KB
-constexpr uint32_t AXY_OFF = 48 * 1024;      // 2 stages x (X 16 KB + Y 16 KB)
-constexpr uint32_t AST_OFF = 112 * 1024;     // [factor][quarter] tiles of dzq1, dzq3, uq (96 KB)
-constexpr uint32_t ADQ_OFF = 208 * 1024;     // dq staging, two 64-token boxes (16 KB)
+constexpr size_t DYN_SMEM = 1024 + tl::SMEM_BYTES;   // the apply VJP's layout is the larger
 
-constexpr uint32_t SMEM_BYTES = 224 * 1024;
-constexpr size_t DYN_SMEM = 1024 + SMEM_BYTES;
-
-// TMEM columns
+// TMEM columns (BKEY)
 constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each, resident for the whole piece
-constexpr uint32_t A_BUF = 192;     // BKEY: G1 (128) | G2 (64); BAPPLY: two buffers of G1 (64) | G2 (32)
-constexpr uint32_t A_GBUF = 96;     // BAPPLY: columns of one G buffer
-constexpr uint32_t A_DX = 384;      // dk / dq accumulator [tok][64]
+constexpr uint32_t A_BUF = 192;     // G1 (128) | G2 (64)
+constexpr uint32_t A_DX = 384;      // dk accumulator [tok][64]
 constexpr uint32_t A_DY = 448;      // dv accumulator [tok][64]
 
 struct TmaMaps {
@@ -98,9 +93,9 @@ struct TmaMaps {
   CUtensorMap s_dk, s_dv, s_dq;              // stores, boxes of 64 x 1 x 64 tokens
 };
 
-struct Bars {
-  uint64_t xy_full[2], xy_empty[2], g_full, g_free, ga_full[2], ga_free[2], sq_full[NQ];
-  uint64_t st_full, st_free, stg_done, acc_full, acc_free, out_full, out_free;
+struct Bars {   // BKEY
+  uint64_t xy_full[2], xy_empty[2], g_full, g_free;
+  uint64_t st_full, st_free, stg_done, acc_full, acc_free, out_full;
   uint64_t eta_full[2], eta_free[2];
   uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone, wq_full;
   uint32_t tmem_base;
@@ -108,118 +103,13 @@ struct Bars {
   float eta_red[2][BT];
 };
 
-__device__ __forceinline__ uint4 pack8(const float* v) {
-  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-}
-
-// Weights into shared memory, bf16, in the 128-byte swizzled layout: each of
-// the 256 epilogue threads takes 8-value chunks (one row of W1, W3, -R1, -R3,
-// or a column of W2, R2 = a row of W2^T, -R2^T).  A batch of chunks is loaded
-// before any is stored, so the load costs a few round trips, not one per chunk.
-template <bool KEY, int BATCH>
-__device__ void load_weight_chunks(const float* w, const float* r, uint8_t* dst, uint32_t qbytes) {
-  constexpr int QROWS = KEY ? 192 : 96;   // rows of one quarter's block
-  const int t = threadIdx.x - 32 * EPI0;   // 256 epilogue threads
-  constexpr int NCH = NQ * QROWS * 8 / 256;   // chunks per thread
-  static_assert(NCH % BATCH == 0, "batch");
-#pragma unroll 1
-  for (int b0 = 0; b0 < NCH; b0 += BATCH) {
-    float v[BATCH][8];
-#pragma unroll
-    for (int i = 0; i < BATCH; ++i) {
-      const int c = t + 256 * (b0 + i);
-      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
-      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4), f = 32 * q + rr % 32;
-      if (blk < 4) {   // W1, W3, R1, R3: row f
-        const float4* src = reinterpret_cast<const float4*>(
-            (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col);
-        const float4 a = __ldg(src), bq = __ldg(src + 1);
-        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
-        v[i][4] = bq.x; v[i][5] = bq.y; v[i][6] = bq.z; v[i][7] = bq.w;
-      } else {         // W2, R2 [D][F]: column f
-        const float* src = (blk == 4 ? w : r) + 2 * (size_t)F * D + f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[i][j] = __ldg(src + (size_t)(col + j) * F);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < BATCH; ++i) {
-      const int c = t + 256 * (b0 + i);
-      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
-      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4);
-      if (blk == 2 || blk == 3 || blk == 5) {   // the adjoint enters negated
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[i][j] = -v[i][j];
-      }
-      *reinterpret_cast<uint4*>(dst + q * qbytes + sw128_offset(rr, col)) = pack8(v[i]);
-    }
-  }
-  fence_proxy_async_smem();
-}
-
 // BKEY weights, quarter-major:
 //   quarter q rows   0.. 31 W1[32q + r][:]      rows  32.. 63 W3[32q + r][:]
 //                   64.. 95 -R1[32q + r][:]     rows  96..127 -R3[32q + r][:]
 //                  128..159 W2[:][32q + r]      rows 160..191 -R2[:][32q + r]
 // each row 64 values (d).
 __device__ void load_weights_key(const float* w, const float* r, uint8_t* sm) {
-  load_weight_chunks<true, 12>(w, r, sm + WQ_OFF, QBYTES);
-}
-
-// BAPPLY weights: quarter q rows 0..31 W1[32q + r][:], 32..63 W3[32q + r][:],
-// 64..95 W2[:][32q + r].
-__device__ void load_weights_apply(const float* w, uint8_t* sm) {
-  load_weight_chunks<false, 12>(w, w, sm + AW_OFF, AQ_BYTES);
-}
-
-// 32 fp32 accumulator columns of this thread's token row -> bf16 in a
-// [128 tok][64] tile pair (two 64-token boxes, 128-byte swizzle).
-__device__ __forceinline__ void stage_row64(uint8_t* base, uint32_t row, int half, const float* v0,
-                                            const float* v1) {
-  uint8_t* t = base + (row >> 6) * 8192;
-  const uint32_t rr = row & 63;
-  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half)) = pack8(v0);
-  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 8)) = pack8(v0 + 8);
-  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 16)) = pack8(v1);
-  *reinterpret_cast<uint4*>(t + sw128_offset(rr, 32 * half + 24)) = pack8(v1 + 8);
-}
-
-__device__ __forceinline__ void store_row64(__nv_bfloat16* dst0, int half, const float* v0, const float* v1) {
-  uint4* dst = reinterpret_cast<uint4*>(dst0 + 32 * half);
-  dst[0] = pack8(v0);
-  dst[1] = pack8(v0 + 8);
-  dst[2] = pack8(v1);
-  dst[3] = pack8(v1 + 8);
-}
-
-// Weight-adjoint partial sums of the piece (TMEM lanes = hidden unit) -> its
-// slot, in the layout of W: L1 [F][D], L3 [F][D], L2 [D][F].
-__device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int half = (warp - EPI0) >> 2;
-  const uint32_t row = 32u * (warp & 3) + lane;
-  const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  float* slot = p.part + (size_t)it.slot * 3 * F * D;
-  float* out = slot + (size_t)row * D + 32 * half;
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    float v[16];
-#pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-      tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
-      float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
-#pragma unroll
-      for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
-    }
-  }
-  // L2t[f][d] is dL/dW2[d][f]: stored in W2's orientation
-#pragma unroll
-  for (int c = 0; c < 32; c += 16) {
-    float v[16];
-    tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
-  }
+  tl::load_weight_chunks<true, 12, EPI0>(w, r, sm + WQ_OFF, QBYTES);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,193 +441,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   }
   if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv stores complete
   if (aborted || warp < EPI0) return;
-  store_lambda(p, it, tb);
-}
-
-// ---------------------------------------------------------------------------
-// BAPPLY: the VJP of a chunk apply (one pass)
-// ---------------------------------------------------------------------------
-__device__ void run_apply_vjp(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
-                              uint32_t tb) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int H = p.H;
-  const int h = it.chain % H;
-  const int64_t t0 = it.t0, t1 = it.t1;
-  const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
-  const int nq = ntiles * NQ;
-  volatile int* abort = &B.abort_flag;
-  constexpr uint32_t IDESC_G1 = idesc_bf16(128, 64, false, false);
-  constexpr uint32_t IDESC_G2 = idesc_bf16(128, 32, false, false);
-  constexpr uint32_t IDESC_ACC = idesc_bf16(128, D, false, true);
-  constexpr uint32_t IDESC_LAM = idesc_bf16(128, D, true, true);
-  const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
-  const uint32_t row = 32u * (warp & 3) + lane;
-  const uint32_t lane_base = (32u * (warp & 3)) << 16;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int i = 0; i < ntiles; ++i) {
-        const int s = i & 1;
-        if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
-        mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
-        uint8_t* xs = sm + AXY_OFF + s * 32768;
-        const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
-        tma_load_3d(xs, &maps.x_q, &B.xy_full[s], 0, h, tok);
-        tma_load_3d(xs + 8192, &maps.x_q, &B.xy_full[s], 0, h, tok + 64);
-        tma_load_3d(xs + 16384, &maps.y_do, &B.xy_full[s], 0, h, tok);
-        tma_load_3d(xs + 24576, &maps.y_do, &B.xy_full[s], 0, h, tok + 64);
-      }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t wq = smem_u32(sm + AW_OFF), stg = smem_u32(sm + AST_OFF);
-      // dq products of quarter m; after the tile's last quarter, its
-      // weight-adjoint products (A = the staged factors of all four quarters,
-      // hidden-unit blocks of 32 at a stride of one staging tile)
-      auto issue_acc = [&](int m) -> bool {
-        const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait(&B.sq_full[q], i & 1, abort)) return false;
-        if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
-        tc_fence_after();
-        const uint32_t wb = wq + q * AQ_BYTES;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-          mma_ss(tb + A_DX, sdesc_sw64(stg + ((ks / 2) * NQ + q) * ST_TILE + (ks % 2) * 32, 16, 512),
-                 sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-        if (q == NQ - 1) {
-          mma_commit(&B.acc_full);
-          const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
-#pragma unroll
-          for (int ks = 0; ks < BT / 16; ++ks) {
-            const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t xd = sdesc_sw128(xs + ks * 2048, 1024, 1024);
-            const uint64_t yd = sdesc_sw128(xs + 16384 + ks * 2048, 1024, 1024);
-            mma_ss(tb + B_L, sdesc_sw64(stg + 0 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 64, sdesc_sw64(stg + 1 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 128, sdesc_sw64(stg + 2 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), yd, IDESC_LAM,
-                   acc);
-          }
-          mma_commit(&B.st_free);            // the tile's staging may be overwritten
-          mma_commit(&B.xy_empty[i & 1]);    // its X/Y stage may be reloaded
-        }
-        return true;
-      };
-      bool ok = true;
-      for (int n = 0; n < nq && ok; ++n) {
-        const int i = n / NQ, q = n % NQ, b = n & 1;
-        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
-        const uint32_t wb = wq + q * AQ_BYTES;
-        const uint32_t gb = tb + A_BUF + b * A_GBUF;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          mma_ss(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
-          mma_ss(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
-                 IDESC_G2, ks > 0);
-        }
-        mma_commit(&B.ga_full[b]);
-        if (n > 0) ok = issue_acc(n - 1);
-      }
-      if (ok && !*abort && nq > 0) ok = issue_acc(nq - 1);
-      if (ok && !*abort) mma_commit(&B.bdone);
-    }
-    __syncwarp();
-  } else if (warp == 2) {
-    // dq of every full tile by TMA store
-    if (lane == 0) {
-      for (int i = 0; i < ntiles; ++i) {
-        if (!mbar_wait(&B.out_full, i & 1, abort)) break;
-        const int64_t tok = t0 + (int64_t)i * BT;
-        if (tok + BT <= t1) {
-          tma_store_3d(&maps.s_dq, sm + ADQ_OFF, 0, h, (int32_t)tok);
-          tma_store_3d(&maps.s_dq, sm + ADQ_OFF + 8192, 0, h, (int32_t)(tok + 64));
-          bulk_commit();
-          bulk_wait_read_all();
-        }
-        mbar_arrive(&B.out_free);
-      }
-      bulk_wait_all();
-    }
-    __syncwarp();
-  } else {
-    // epilogue: thread = token row of the tile; half selects hidden units
-    // [16*half, 16*half + 16) of every quarter.
-    uint8_t* stg = sm + AST_OFF;
-    for (int n = 0; n < nq; ++n) {
-      const int i = n / NQ, q = n % NQ, b = n & 1;
-      const int64_t tok = t0 + (int64_t)i * BT + row;
-      const bool valid = tok < t1;
-      if (!mbar_wait(&B.ga_full[b], (n >> 1) & 1, abort)) break;
-      tc_fence_after();
-      const uint32_t buf = tb + lane_base + A_BUF + b * A_GBUF + 16 * half;
-      float r[3][16];   // zq1 zq3 du
-      tmem_ld16x3(buf, buf + 32, buf + 64, r[0], r[1], r[2]);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&B.ga_free[b]);
-      float o[3][16];   // dzq1 dzq3 uq
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float z1 = r[0][k], z3 = r[1][k];
-        const float sg = sigmoid_fast(z1);
-        const float a = z1 * sg;
-        const float sp = fmaf(a, 1.f - sg, sg);
-        const float du = valid ? r[2][k] : 0.f;
-        o[0][k] = du * z3 * sp;
-        o[1][k] = du * a;
-        o[2][k] = valid ? a * z3 : 0.f;
-      }
-      // the tile's staging is free once the previous tile's products read it
-      if (q == 0 && !mbar_wait(&B.st_free, (i & 1) ^ 1, abort)) break;
-      {
-        const uint32_t c = 16u * half;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          uint8_t* t = stg + (m * NQ + q) * ST_TILE;
-          *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
-          *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
-        }
-      }
-      fence_proxy_async_smem();
-      __syncwarp();
-      // one barrier per quarter slot: quarters of a tile do not wait for one
-      // another, so a single barrier could run two phases ahead of its waiter
-      if (lane == 0) mbar_arrive(&B.sq_full[q]);
-      if (q == NQ - 1) {
-        // tile finished: dq to shared memory for the TMA store (rows of a
-        // partial tile are stored directly)
-        if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
-        tc_fence_after();
-        const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
-        if (full_tile && !mbar_wait(&B.out_free, (i & 1) ^ 1, abort)) break;
-        float v0[16], v1[16];
-        tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
-        tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
-        if (full_tile) {
-          stage_row64(sm + ADQ_OFF, row, half, v0, v1);
-        } else if (valid) {
-          store_row64(reinterpret_cast<__nv_bfloat16*>(p.dq) + ((size_t)tok * H + h) * D, half, v0, v1);
-        }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&B.acc_free);
-          mbar_arrive(&B.out_full);
-        }
-      }
-    }
-    // the last weight-adjoint products complete before they are read
-    mbar_wait(&B.bdone, 0, abort);
-  }
-  tc_fence_before();
-  const int stop = __syncthreads_or(*abort);
-  tc_fence_after();
-  if (stop || warp < EPI0) return;
-  store_lambda(p, it, tb);
+  tl::store_lambda<EPI0>(p, it, tb);
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -745,6 +449,7 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Bars B;
+  __shared__ tl::Bars TB;
   const int warp = threadIdx.x / 32;
   const WorkItem it = items[blockIdx.x];
   const int H = p.H, P = 3 * F * D;
@@ -758,8 +463,6 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     for (int i = 0; i < 2; ++i) {
       mbar_init(&B.xy_full[i], 1);
       mbar_init(&B.xy_empty[i], 1);
-      mbar_init(&B.ga_full[i], 1);
-      mbar_init(&B.ga_free[i], 8);
       mbar_init(&B.eta_full[i], 4);
       mbar_init(&B.eta_free[i], 4);
     }
@@ -771,15 +474,14 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     mbar_init(&B.acc_full, 1);
     mbar_init(&B.acc_free, 8);
     mbar_init(&B.out_full, 8);
-    mbar_init(&B.out_free, 1);
     for (int i = 0; i < PB_STAGES; ++i) {
       mbar_init(&B.b_full[i], 1);
       mbar_init(&B.b_empty[i], 1);
     }
-    for (int i = 0; i < NQ; ++i) mbar_init(&B.sq_full[i], 8);
     mbar_init(&B.bdone, 1);
     mbar_init(&B.wq_full, 1);
     B.abort_flag = 0;
+    tl::init_bars(TB);
     fence_barrier_init();
     prefetch_tmap(key ? &maps.x_k : &maps.x_q);
     prefetch_tmap(key ? &maps.y_v : &maps.y_do);
@@ -790,18 +492,18 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
   }
   if (warp >= EPI0) {
     if (key) load_weights_key(w, r, sm);
-    else load_weights_apply(w, sm);
+    else tl::load_weights<EPI0>(w, sm);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = B.tmem_base;
   if (key) run_key_vjp(maps, p, it, sm, B, tb);
-  else run_apply_vjp(maps, p, it, sm, B, tb);
+  else tl::token_lane_pass<true, EPI0>(&maps.x_q, &maps.y_do, &maps.s_dq, p, it, sm, TB, tb);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (B.abort_flag && threadIdx.x == 0) atomicExch(p.status, SCAL3R_ERR_TIMEOUT);
+  if ((B.abort_flag || TB.abort_flag) && threadIdx.x == 0) atomicExch(p.status, SCAL3R_ERR_TIMEOUT);
   if (warp == 1) tmem_dealloc(tb, 512);
 }
 

@@ -5,18 +5,14 @@
 // Work item roles (see plan.cpp for the chunk-step schedule):
 //
 // KEY  (gradient partial of a chunk at the pre-chunk weights, Eq. 8, Eq. 9).
-//   Lanes of TMEM = hidden unit f (F = 128 = the MMA's M), columns = tokens.
-//   The three weight matrices are A operands resident in TMEM (bf16, packed
-//   along the contraction dim D).  Per tile of 32 tokens:
-//     Z1t = W1 K^T, Z3t = W3 K^T, Pt = W2^T V^T       (M 128, N 32, K 64)
-//   the epilogue warps (thread = f) form, per token t with learning rate e,
-//     a = SiLU(z1), u~ = e a z3, p~ = e p, g1~ = p~ z3 SiLU'(z1), g3~ = p~ a
-//   and write them back to TMEM as bf16 over the columns they just read;
-//   then, with the raw K / V tiles as MN-major B operands,
-//     S1 += G1~^T K, S3 += G3~^T K, S2t += U~^T V      (M 128, N 64, K 16/step)
-//   accumulate in TMEM for the whole piece and go to the piece's slot packed
-//   like the weights (S2t transposed); W += the fixed-order sum over pieces
-//   (update.cu).
+//   The token-lane weight-adjoint pass of bf16_token_lane.cuh with the
+//   factors scaled by each token's learning rate e (dot loss):
+//     Z1 = K W1^T, Z3 = K W3^T, P = V W2 (p = W2^T v)   per hidden quarter
+//     g1~ = e p z3 SiLU'(z1), g3~ = e p a, u~ = e a z3   (a = SiLU(z1))
+//     S1 += G1~^T K, S3 += G3~^T K, S2t += U~^T V          (M 128 hidden, N 64, K 128 tokens)
+//   S accumulates in TMEM for the whole piece and goes to the piece's slot
+//   packed like the weights (S2t transposed); W += the fixed-order sum over
+//   pieces (update.cu).
 // APPLY (o = f_W(q), Eq. 4).  Lanes = token (M = 128 tokens per tile):
 //     Zq = Q [W1; W3]^T                                 (M 128, N 256, K 64)
 //   the epilogue (thread = token) forms h = SiLU(zq1) zq3 as bf16 into TMEM,
@@ -30,6 +26,7 @@
 // to SCAL3R_ERR_TIMEOUT and TMEM is freed.
 #include <cudaTypedefs.h>
 
+#include "bf16_token_lane.cuh"
 #include "sm100.cuh"
 #include "ttt_internal.h"
 
@@ -41,235 +38,35 @@ using namespace sm100;
 constexpr int D = 64;
 constexpr int F = 128;
 constexpr int NTHREADS = 320;
-constexpr int KT = 32;        // key tile (tokens)
+constexpr int EPI0 = 2;       // first epilogue warp
 constexpr int QT = 128;       // query tile (tokens)
-constexpr int KSTAGES = 6;    // K/V stages, 8 KB each
 constexpr int QSTAGES = 3;    // Q stages, 16 KB each
 
-// TMEM columns, key role
-constexpr uint32_t K_AW1 = 0, K_AW3 = 32, K_AW2T = 64;     // A operands (bf16 x2 per column)
-constexpr uint32_t K_S1 = 96, K_S3 = 160, K_S2T = 224;     // fp32 accumulators [f][d]
-constexpr uint32_t K_BUF = 288;                            // 2 x (z1 | z3 | p), 32 columns each
 // TMEM columns, apply role
 constexpr uint32_t A_ZQ = 0;      // z1 0..127, z3 128..255
 constexpr uint32_t A_H = 256;     // h as bf16 pairs, 64 columns
 constexpr uint32_t A_O = 320;     // o accumulator, 64 columns
 
-constexpr uint32_t IDESC_KZ = idesc_bf16(128, KT, false, false);   // Z1t/Z3t/Pt
-constexpr uint32_t IDESC_KS = idesc_bf16(128, D, false, true);     // S accumulations, B MN-major
 constexpr uint32_t IDESC_AZ = idesc_bf16(128, 2 * F, false, false);
 constexpr uint32_t IDESC_AO = idesc_bf16(128, D, false, false);
 
-constexpr size_t KEY_SMEM = (size_t)KSTAGES * 2 * KT * 128;
+constexpr size_t KEY_SMEM = tl::SMEM_BYTES;
 constexpr size_t APPLY_SMEM = 2 * F * 128 + 2 * D * 128 + (size_t)QSTAGES * QT * 128;
 constexpr size_t DYN_SMEM = 1024 + (KEY_SMEM > APPLY_SMEM ? KEY_SMEM : APPLY_SMEM);
 
 struct TmaMaps {
   CUtensorMap q;   // box 64 x 1 x 128 tokens
-  CUtensorMap k;   // box 64 x 1 x 32 tokens
-  CUtensorMap v;   // box 64 x 1 x 32 tokens
+  CUtensorMap k;   // box 64 x 1 x 64 tokens
+  CUtensorMap v;   // box 64 x 1 x 64 tokens
 };
 
-struct Bars {
-  uint64_t kv_full[KSTAGES], kv_empty[KSTAGES];
-  uint64_t zp_full[2], ug_full[2], buf_free[2], s_done;
+struct Bars {   // APPLY
   uint64_t q_full[QSTAGES], q_empty[QSTAGES];
   uint64_t zq_full, zq_free, h_full, o_full;
   uint32_t tmem_base;
   int abort_flag;
 };
 
-__device__ __forceinline__ float silu_prime_from(float s, float a) { return fmaf(a, 1.f - s, s); }
-
-// ---------------------------------------------------------------------------
-// KEY role
-// ---------------------------------------------------------------------------
-__device__ void key_role(const TmaMaps& maps, const Params& p, const WorkItem& it, const float* w, uint8_t* sm,
-                         Bars& B, uint32_t tb) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int h = it.chain % p.H;
-  const int64_t t0 = it.t0, t1 = it.t1;
-  const int ntiles = (int)((t1 - t0 + KT - 1) / KT);
-  uint8_t* Ks = sm;                         // KSTAGES x [32][64] bf16, 4 KB each
-  uint8_t* Vs = sm + KSTAGES * KT * 128;
-  volatile int* abort = &B.abort_flag;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int i = 0; i < ntiles; ++i) {
-        const int s = i % KSTAGES;
-        if (!mbar_wait(&B.kv_empty[s], ((i / KSTAGES) & 1) ^ 1, abort)) break;
-        mbar_arrive_expect_tx(&B.kv_full[s], 2 * KT * 128);
-        const int32_t tok = (int32_t)(t0 + (int64_t)i * KT);
-        tma_load_3d(Ks + s * KT * 128, &maps.k, &B.kv_full[s], 0, h, tok);
-        tma_load_3d(Vs + s * KT * 128, &maps.v, &B.kv_full[s], 0, h, tok);
-      }
-    }
-    __syncwarp();
-    return;
-  }
-
-  if (warp == 1) {
-    if (lane == 0) {
-      auto issue_s = [&](int j) -> bool {
-        const int b = j & 1, s = j % KSTAGES;
-        if (!mbar_wait(&B.ug_full[b], (j >> 1) & 1, abort)) return false;
-        tc_fence_after();
-        const uint32_t zb = K_BUF + 96 * b;
-        const uint32_t ks_addr = smem_u32(Ks + s * KT * 128), vs_addr = smem_u32(Vs + s * KT * 128);
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t kdesc = sdesc_sw128(ks_addr + kk * 2048, 1024, 1024);
-          const uint64_t vdesc = sdesc_sw128(vs_addr + kk * 2048, 1024, 1024);
-          mma_ts(tb + K_S1, tb + zb + 32 + 16 * kk, kdesc, IDESC_KS, acc);   // g1~ in the z3 slot
-          mma_ts(tb + K_S3, tb + zb + 64 + 16 * kk, kdesc, IDESC_KS, acc);   // g3~ in the p slot
-          mma_ts(tb + K_S2T, tb + zb + 0 + 16 * kk, vdesc, IDESC_KS, acc);   // u~ in the z1 slot
-        }
-        mma_commit(&B.buf_free[b]);
-        mma_commit(&B.kv_empty[s]);
-        return true;
-      };
-      bool ok = true;
-      for (int i = 0; i < ntiles && ok; ++i) {
-        const int b = i & 1, s = i % KSTAGES;
-        if (!mbar_wait(&B.kv_full[s], (i / KSTAGES) & 1, abort)) break;
-        if (!mbar_wait(&B.buf_free[b], ((i >> 1) & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t zb = K_BUF + 96 * b;
-        const uint32_t ks_addr = smem_u32(Ks + s * KT * 128), vs_addr = smem_u32(Vs + s * KT * 128);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t kdesc = sdesc_sw128(ks_addr + kk * 32, 16, 1024);
-          const uint64_t vdesc = sdesc_sw128(vs_addr + kk * 32, 16, 1024);
-          mma_ts(tb + zb + 0, tb + K_AW1 + 8 * kk, kdesc, IDESC_KZ, kk > 0);
-          mma_ts(tb + zb + 32, tb + K_AW3 + 8 * kk, kdesc, IDESC_KZ, kk > 0);
-          mma_ts(tb + zb + 64, tb + K_AW2T + 8 * kk, vdesc, IDESC_KZ, kk > 0);
-        }
-        mma_commit(&B.zp_full[b]);
-        if (i >= 1) ok = issue_s(i - 1);
-      }
-      if (ok && !*abort) {
-        if (issue_s(ntiles - 1)) mma_commit(&B.s_done);
-      }
-    }
-    __syncwarp();
-    return;
-  }
-
-  // epilogue warps
-  const int ew = warp - 2;
-  const int half = ew >> 2;               // tokens [16*half, 16*half + 16) of each tile
-  const uint32_t row = 32u * (warp & 3) + lane;   // hidden unit f
-  const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  // lane j < 16 holds the learning rate of token 16*half + j of a tile,
-  // loaded two tiles ahead of its use
-  auto load_eta = [&](int i) -> float {
-    const int64_t tok = t0 + (int64_t)i * KT + 16 * half + lane;
-    return (i < ntiles && lane < 16 && tok < t1) ? p.lr[(size_t)tok * p.H + h] : 0.f;
-  };
-  float eta_a = load_eta(0), eta_b = load_eta(1);
-  for (int i = 0; i < ntiles; ++i) {
-    const int b = i & 1;
-    const float eta_l = eta_a;
-    eta_a = eta_b;
-    eta_b = load_eta(i + 2);
-    if (!mbar_wait(&B.zp_full[b], (i >> 1) & 1, abort)) break;
-    tc_fence_after();
-    const uint32_t zb = tb + lane_base + K_BUF + 96 * b + 16 * half;
-    float z1[16], z3[16], pp[16];
-    tmem_ld16x3(zb, zb + 32, zb + 64, z1, z3, pp);
-    uint32_t uu[8], g1[8], g3[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      float ut[2], g1t[2], g3t[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int j = 2 * m + q;
-        const float e = __shfl_sync(0xffffffffu, eta_l, j);
-        const float x = z1[j];
-        const float sg = sigmoid_fast(x);
-        const float a = x * sg;
-        const float sp = silu_prime_from(sg, a);
-        const float pe = e * pp[j];
-        ut[q] = e * a * z3[j];
-        g1t[q] = pe * z3[j] * sp;
-        g3t[q] = pe * a;
-      }
-      uu[m] = pack_bf16(ut[0], ut[1]);
-      g1[m] = pack_bf16(g1t[0], g1t[1]);
-      g3[m] = pack_bf16(g3t[0], g3t[1]);
-    }
-    tmem_st8(zb, uu);
-    tmem_st8(zb + 32, g1);
-    tmem_st8(zb + 64, g3);
-    tmem_st_wait();
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&B.ug_full[b]);
-  }
-  if (!*abort && mbar_wait(&B.s_done, 0, abort)) {
-    tc_fence_after();
-    float* slot = p.part + (size_t)it.slot * 3 * F * D;
-    float* out = slot + (size_t)row * D + 32 * half;
-    const uint32_t mats[2] = {K_S1, K_S3};
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      float v[16];
-#pragma unroll
-      for (int c = 0; c < 32; c += 16) {
-        tmem_ld16(tb + lane_base + mats[m] + 32 * half + c, v);
-        float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
-#pragma unroll
-        for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
-      }
-    }
-    // S2t[f][d] is the increment of W2[d][f]: stored in W2's orientation
-    // (lanes = consecutive f, so each store instruction is one 128-byte line)
-#pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-      float v[16];
-      tmem_ld16(tb + lane_base + K_S2T + 32 * half + c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
-    }
-  }
-}
-
-// Weights into TMEM as A operands: lane f holds W1[f][:], W3[f][:], W2[:][f]
-// as bf16 pairs along d.
-// All loads of a thread are issued before any of its TMEM stores (those are
-// ordered against memory), so the weights cost one round trip, not one per chunk.
-__device__ void key_load_weights(const float* w, uint32_t tb) {
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int ew = warp - 2, half = ew >> 2;
-  const uint32_t f = 32u * (warp & 3) + lane;
-  const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  // half 0: W1 row f; half 1: W3 row f (64 values)
-  const float4* row = reinterpret_cast<const float4*>(w + (size_t)half * F * D + (size_t)f * D);
-  float4 a[16];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) a[j] = __ldg(row + j);
-  // W2^T row f = column f of W2 [D][F]; half h covers d in [32h, 32h + 32)
-  const float* w2 = w + 2 * (size_t)F * D + f;
-  float b[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) b[j] = __ldg(w2 + (size_t)(32 * half + j) * F);
-  uint32_t r[16];
-#pragma unroll
-  for (int c0 = 0; c0 < 2; ++c0) {
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      r[2 * j] = pack_bf16(a[8 * c0 + j].x, a[8 * c0 + j].y);
-      r[2 * j + 1] = pack_bf16(a[8 * c0 + j].z, a[8 * c0 + j].w);
-    }
-    tmem_st16(tb + lane_base + (half ? K_AW3 : K_AW1) + 16 * c0, r);
-  }
-#pragma unroll
-  for (int j = 0; j < 16; ++j) r[j] = pack_bf16(b[2 * j], b[2 * j + 1]);
-  tmem_st16(tb + lane_base + K_AW2T + 16 * half, r);
-  tmem_st_wait();
-}
 
 // ---------------------------------------------------------------------------
 // APPLY role
@@ -443,22 +240,14 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
   __shared__ Bars B;
+  __shared__ tl::Bars TB;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const WorkItem it = items[blockIdx.x];
   const int chains = p.S * p.H;
   const float* w = p.wm + ((size_t)(step & 1) * chains + it.chain) * 3 * F * D;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < KSTAGES; ++i) {
-      mbar_init(&B.kv_full[i], 1);
-      mbar_init(&B.kv_empty[i], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&B.zp_full[i], 1);
-      mbar_init(&B.ug_full[i], 8);
-      mbar_init(&B.buf_free[i], 1);
-    }
-    mbar_init(&B.s_done, 1);
+    tl::init_bars(TB);
     for (int i = 0; i < QSTAGES; ++i) {
       mbar_init(&B.q_full[i], 1);
       mbar_init(&B.q_empty[i], 1);
@@ -484,20 +273,20 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
 
   // weights
   if (warp >= 2) {
-    if (it.role == ROLE_KEY) key_load_weights(w, tb);
+    if (it.role == ROLE_KEY) tl::load_weights<EPI0>(w, sm);
     else apply_load_weights(w, sm);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
 
-  if (it.role == ROLE_KEY) key_role(maps, p, it, w, sm, B, tb);
+  if (it.role == ROLE_KEY) tl::token_lane_pass<false, EPI0>(&maps.k, &maps.v, nullptr, p, it, sm, TB, tb);
   else apply_role(maps, p, it, sm, B, tb);
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (B.abort_flag && threadIdx.x == 0) atomicExch(p.status, SCAL3R_ERR_TIMEOUT);
+  if ((B.abort_flag || TB.abort_flag) && threadIdx.x == 0) atomicExch(p.status, SCAL3R_ERR_TIMEOUT);
   if (warp == 1) tmem_dealloc(tb, 512);
   (void)lane;
 }
@@ -541,8 +330,8 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, i
   if (n == 0) return cudaSuccess;
   if (prm.T <= 0) return cudaErrorInvalidValue;
   TmaMaps maps;
-  if (!make_token_map(&maps.q, prm.q, prm.T, prm.H, QT) || !make_token_map(&maps.k, prm.k, prm.T, prm.H, KT) ||
-      !make_token_map(&maps.v, prm.v, prm.T, prm.H, KT))
+  if (!make_token_map(&maps.q, prm.q, prm.T, prm.H, QT) || !make_token_map(&maps.k, prm.k, prm.T, prm.H, 64) ||
+      !make_token_map(&maps.v, prm.v, prm.T, prm.H, 64))
     return cudaErrorInvalidValue;
   bf16_sweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items, step);
   return cudaGetLastError();
