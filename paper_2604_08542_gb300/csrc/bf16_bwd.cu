@@ -42,7 +42,9 @@
 //   after the fourth quarter: L1 += dzq1^T X, L3 += dzq3^T X, L2t += uq^T Y
 //
 // dk/dv/dq are staged in shared memory and written by TMA tile stores.
-// Warps: 0 TMA loads, 1 MMA issue, 2 bulk / TMA stores, 3..10 epilogue.
+// Warps: 0 TMA loads, 1 MMA issue, 2 bulk / TMA stores, 3..10 epilogue; in
+// BAPPLY warp 11 issues the dq and L products (bf16_token_lane.cuh), in BKEY
+// it idles.
 #include <cudaTypedefs.h>
 
 #include "bf16_token_lane.cuh"
@@ -62,7 +64,7 @@ using tl::ST_TILE;
 using tl::pack8;
 using tl::stage_row64;
 using tl::store_row64;
-constexpr int NTHREADS = 352;
+constexpr int NTHREADS = 384;
 constexpr int EPI0 = 3;                      // first epilogue warp
 
 // BKEY shared memory
@@ -137,7 +139,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
   // learning rate of this thread's token, one tile ahead
   float eta_next = 0.f;
-  if (warp >= EPI0 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
+  if (warp >= EPI0 && warp < EPI0 + 8 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
 
   // pass B stage use counts (parity per stage), kept alike by the producer
   // and the MMA thread
@@ -243,7 +245,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         bulk_wait_all();   // scratch written before pass B reads it back
       }
       __syncwarp();
-    } else {
+    } else if (warp < EPI0 + 8) {
       // epilogue: thread = token row of the tile; half selects hidden units
       // [16*half, 16*half + 16) of every quarter.
       uint8_t* stg = sm + ST_OFF;
@@ -440,7 +442,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
     }
   }
   if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv stores complete
-  if (aborted || warp < EPI0) return;
+  if (aborted || warp < EPI0 || warp >= EPI0 + 8) return;
   tl::store_lambda<EPI0>(p, it, tb);
 }
 
@@ -490,7 +492,7 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     tmem_alloc(&B.tmem_base, 512);
     tmem_relinquish();
   }
-  if (warp >= EPI0) {
+  if (warp >= EPI0 && warp < EPI0 + 8) {
     if (key) load_weights_key(w, r, sm);
     else tl::load_weights<EPI0>(w, sm);
   }

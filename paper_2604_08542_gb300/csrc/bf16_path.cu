@@ -20,10 +20,11 @@
 //   with H as the TMEM A operand, and stores O as bf16.
 //
 // Warp roles: warp 0 issues TMA loads, warp 1 allocates TMEM and issues the
-// MMAs (one thread), warps 2..9 are the epilogue (two warps per TMEM lane
-// quarter).  Every wait is an mbarrier wait bounded in time: on timeout the
-// CTA raises an abort flag, every role leaves its loop, the status word is set
-// to SCAL3R_ERR_TIMEOUT and TMEM is freed.
+// MMAs (one thread; in the KEY role warp 10 issues the S products), warps
+// 2..9 are the epilogue (two warps per TMEM lane quarter).  Every wait is an
+// mbarrier wait bounded in time: on timeout the CTA raises an abort flag,
+// every role leaves its loop, the status word is set to SCAL3R_ERR_TIMEOUT
+// and TMEM is freed.
 #include <cudaTypedefs.h>
 
 #include "bf16_token_lane.cuh"
@@ -37,7 +38,7 @@ using namespace sm100;
 
 constexpr int D = 64;
 constexpr int F = 128;
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 352;   // the KEY role's second MMA warp is warp 10
 constexpr int EPI0 = 2;       // first epilogue warp
 constexpr int QT = 128;       // query tile (tokens)
 constexpr int QSTAGES = 3;    // Q stages, 16 KB each
@@ -167,6 +168,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     return;
   }
 
+  if (warp >= 10) return;   // not a warp of this role
   // epilogue: thread = token row of the tile; half selects f in [64*half, 64*half+64)
   const int ew = warp - 2, half = ew >> 2;
   const uint32_t row = 32u * (warp & 3) + lane;
@@ -272,7 +274,7 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   const uint32_t tb = B.tmem_base;
 
   // weights
-  if (warp >= 2) {
+  if (warp >= 2 && warp < 10) {
     if (it.role == ROLE_KEY) tl::load_weights<EPI0>(w, sm);
     else apply_load_weights(w, sm);
   }

@@ -20,7 +20,9 @@
 // Shared memory (224 KB): W1_q, W3_q, W2^T_q for the four quarters (48 KB),
 // two X/Y stages (64 KB), the factor tiles (96 KB), dq staging (16 KB).
 // TMEM: L at columns 0..191, two G buffers at 192 and 288, dq at 384.
-// Warps: 0 TMA loads, 1 MMA issue, (with dq) 2 TMA stores, EPI0..EPI0+7 epilogue.
+// Warps: 0 TMA loads, 1 issues the G products, (with dq) 2 TMA stores,
+// EPI0..EPI0+7 epilogue, EPI0+8 issues the dq and L products: the two MMA
+// streams wait on different conditions, so neither holds the other back.
 #pragma once
 
 #include <cudaTypedefs.h>
@@ -49,9 +51,11 @@ constexpr uint32_t A_BUF = 192;              // two buffers of G1 (64) | G2 (32)
 constexpr uint32_t A_GBUF = 96;
 constexpr uint32_t A_DX = 384;               // dq accumulator [tok][64]
 
+constexpr int RG = 4;                        // token-row groups of 32 (one per TMEM lane quarter)
+
 struct Bars {
-  uint64_t xy_full[2], xy_empty[2], ga_full[2], ga_free[2], sq_full[NQ];
-  uint64_t st_free, acc_full, acc_free, out_full, out_free, bdone;
+  uint64_t xy_full[2], xy_empty[2], ga_full[2], ga_free[2], sq_full[NQ], st_free[RG];
+  uint64_t acc_full, acc_free, out_full, out_free, bdone;
   int abort_flag;
 };
 
@@ -64,7 +68,7 @@ __device__ inline void init_bars(Bars& B) {
     mbar_init(&B.ga_free[i], 8);   // the 8 epilogue warps free it
   }
   for (int i = 0; i < NQ; ++i) mbar_init(&B.sq_full[i], 8);
-  mbar_init(&B.st_free, 1);
+  for (int i = 0; i < RG; ++i) mbar_init(&B.st_free[i], 1);
   mbar_init(&B.acc_full, 1);
   mbar_init(&B.acc_free, 8);
   mbar_init(&B.out_full, 8);
@@ -222,15 +226,40 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     }
     __syncwarp();
   } else if (warp == 1) {
+    // the G products of every quarter, as soon as a G buffer is free
+    if (lane == 0) {
+      const uint32_t wq = smem_u32(sm + AW_OFF);
+      for (int n = 0; n < nq; ++n) {
+        const int i = n / NQ, q = n % NQ, b = n & 1;
+        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+        if (!mbar_wait(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
+        const uint32_t wb = wq + q * AQ_BYTES;
+        const uint32_t gb = tb + A_BUF + b * A_GBUF;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          mma_ss(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
+          mma_ss(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
+                 IDESC_G2, ks > 0);
+        }
+        mma_commit(&B.ga_full[b]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == EPI0 + 8) {
+    // dq products of every staged quarter (DQ); after a tile's last quarter,
+    // its L products (A = the staged factors of all four quarters, hidden-unit
+    // blocks of 32 at a stride of one staging tile).  The tile's G products
+    // all completed before its last quarter was staged, so the commits after
+    // the L products also cover every read of the tile's X/Y stage.
     if (lane == 0) {
       const uint32_t wq = smem_u32(sm + AW_OFF), stg = smem_u32(sm + AST_OFF);
-      // dq products of quarter m (DQ); after the tile's last quarter, its
-      // L products (A = the staged factors of all four quarters, hidden-unit
-      // blocks of 32 at a stride of one staging tile)
-      auto issue_acc = [&](int m) -> bool {
+      bool ok = true;
+      for (int m = 0; m < nq && ok; ++m) {
         const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait(&B.sq_full[q], i & 1, abort)) return false;
-        if (DQ && q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+        if (!mbar_wait(&B.sq_full[q], i & 1, abort)) break;
+        if (DQ && q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) break;
         tc_fence_after();
         if (DQ) {
           const uint32_t wb = wq + q * AQ_BYTES;
@@ -251,31 +280,12 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
             mma_ss(tb + B_L + 64, sdesc_sw64(stg + 1 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
             mma_ss(tb + B_L + 128, sdesc_sw64(stg + 2 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), yd, IDESC_LAM,
                    acc);
+            // token rows [32g, 32g + 32) of the staging are read after K-step 2g + 1
+            if (ks & 1) mma_commit(&B.st_free[ks >> 1]);
           }
-          mma_commit(&B.st_free);            // the tile's staging may be overwritten
           mma_commit(&B.xy_empty[i & 1]);    // its X/Y stage may be reloaded
         }
-        return true;
-      };
-      bool ok = true;
-      for (int n = 0; n < nq && ok; ++n) {
-        const int i = n / NQ, q = n % NQ, b = n & 1;
-        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
-        const uint32_t wb = wq + q * AQ_BYTES;
-        const uint32_t gb = tb + A_BUF + b * A_GBUF;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          mma_ss(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
-          mma_ss(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
-                 IDESC_G2, ks > 0);
-        }
-        mma_commit(&B.ga_full[b]);
-        if (n > 0) ok = issue_acc(n - 1);
       }
-      if (ok && !*abort && nq > 0) ok = issue_acc(nq - 1);
       if (ok && !*abort) mma_commit(&B.bdone);
     }
     __syncwarp();
@@ -296,7 +306,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       bulk_wait_all();
     }
     __syncwarp();
-  } else if (warp >= EPI0) {
+  } else if (warp >= EPI0 && warp < EPI0 + 8) {
     // epilogue: thread = token row of the tile; half selects hidden units
     // [16*half, 16*half + 16) of every quarter.
     uint8_t* stg = sm + AST_OFF;
@@ -326,8 +336,9 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
         o[1][k] = pk * a;
         o[2][k] = DQ ? (valid ? a * z3 : 0.f) : eta * (a * z3);
       }
-      // the tile's staging is free once the previous tile's products read it
-      if (q == 0 && !mbar_wait(&B.st_free, (i & 1) ^ 1, abort)) break;
+      // this thread's staging rows are free once the previous tile's L
+      // products have read them
+      if (q == 0 && !mbar_wait(&B.st_free[warp & 3], (i & 1) ^ 1, abort)) break;
       {
         const uint32_t c = 16u * half;
 #pragma unroll
@@ -372,7 +383,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
   tc_fence_before();
   const int stop = __syncthreads_or(*abort);
   tc_fence_after();
-  if (stop || warp < EPI0) return;
+  if (stop || warp < EPI0 || warp >= EPI0 + 8) return;
   store_lambda<EPI0>(p, it, tb);
 }
 

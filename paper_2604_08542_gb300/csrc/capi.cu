@@ -542,7 +542,7 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
     // forward: pieces per step and the gradient/apply cost ratio
     bool first = true;
     for (int wv : {1, 2, 3})
-      for (float kc : {1.5f, 2.0f, 3.0f}) {
+      for (float kc : {1.6f, 1.85f, 2.1f}) {
         Schedule sc = saved;
         sc.fwd_waves = wv;
         sc.key_cost = kc;
@@ -561,7 +561,7 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
     bool first = true;
     const Schedule fb = bestc;
     for (int wv : {1, 2, 3})
-      for (float kc : {1.5f, 2.5f, 4.0f}) {
+      for (float kc : {2.25f, 2.95f, 3.6f}) {
         Schedule sc = fb;
         sc.bwd_waves = wv;
         sc.bkey_cost = kc;
