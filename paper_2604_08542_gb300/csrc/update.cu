@@ -63,6 +63,24 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
 __device__ __forceinline__ float4 scale4(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
 __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
 
+// x + the slots slot0 .. slot0 + n - 1 at element offset `off`, added one by
+// one in slot order (fixed-order reduction); the loads of a batch of eight
+// slots are issued before any of them is added, so the sum costs one memory
+// round trip per eight slots rather than one per slot.
+__device__ __forceinline__ float4 add_slots(float4 x, const float* part, int slot0, int n, size_t P, size_t off) {
+  constexpr int kBatch = 8;
+  for (int b = 0; b < n; b += kBatch) {
+    float4 v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if (b + j < n) v[j] = ld4(part + (size_t)(slot0 + b + j) * P + off);
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if (b + j < n) x = add4(x, v[j]);
+  }
+  return x;
+}
+
 __device__ __forceinline__ const float* chain_w0(const Params& p, int chain) {
   const int s = chain / p.H, h = chain % p.H;
   return p.w0 + (size_t)s * p.w0_seq_stride + (size_t)h * 3 * p.F * p.D;
@@ -102,8 +120,7 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
   }
   float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
   if (s.valid) {
-    x = ld4(wcur + s.off);
-    for (int sl = 0; sl < u.nslots; ++sl) x = add4(x, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
+    x = add_slots(ld4(wcur + s.off), p.part, u.slot0, u.nslots, P, s.off);
   }
   const float n = sqrtf(group_sum(dot4(x, x), s.group));
   if (!s.valid) return;
@@ -149,7 +166,7 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
   float4 lam = make_float4(0.f, 0.f, 0.f, 0.f);
   if (s.valid) {
     if (!u.last) lam = ld4(rb + s.off);
-    for (int sl = 0; sl < u.nslots; ++sl) lam = add4(lam, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
+    lam = add_slots(lam, p.part, u.slot0, u.nslots, P, s.off);
   }
   const float rho = s.valid ? p.rho[(size_t)u.chain * R + s.r] : 0.f;
   if (u.first) {
@@ -213,8 +230,7 @@ __global__ void gsum_kernel(Params p, const UpdateItem* __restrict__ upd, float*
   const int P = 3 * p.F * p.D;
   const int h = u.chain % p.H;
   float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (u.chunk >= 0)
-    for (int sl = 0; sl < u.nslots; ++sl) x = add4(x, ld4(p.part + (size_t)(u.slot0 + sl) * P + s.off));
+  if (u.chunk >= 0) x = add_slots(x, p.part, u.slot0, u.nslots, P, s.off);
   st4(grad + ((size_t)u.seq * p.H + h) * P + s.off, scale4(x, -1.f));
 }
 
