@@ -165,49 +165,48 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       }
       __syncwarp();
     } else if (warp == 1) {
-      if (lane == 0) {
-        const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
-        auto issue_acc = [&](int m) -> bool {
-          const int i = m / NQ, q = m % NQ;
-          if (!mbar_wait(&B.st_full, m & 1, abort)) return false;
-          if (q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) return false;
-          tc_fence_after();
-          const uint32_t wb = wq + q * QBYTES;
+      // the whole warp runs the issue loop (uniform control flow); one
+      // elected lane issues each MMA and commit
+      const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
+      auto issue_acc = [&](int m) -> bool {
+        const int i = m / NQ, q = m % NQ;
+        if (!mbar_wait_w(&B.st_full, m & 1, abort)) return false;
+        if (q == 0 && !mbar_wait_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+        tc_fence_after();
+        const uint32_t wb = wq + q * QBYTES;
 #pragma unroll
-          for (int ks = 0; ks < KDX; ++ks)
-            mma_ss(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
+        for (int ks = 0; ks < KDX; ++ks)
+          mma_ss_w(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
                    sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            mma_ss(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
+        for (int ks = 0; ks < 4; ++ks)
+          mma_ss_w(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
                    sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-          mma_commit(&B.st_free);
-          if (q == NQ - 1) mma_commit(&B.acc_full);
-          return true;
-        };
-        bool ok = true;
-        // pass B of the previous sub-piece overwrote the weights
-        if (sp > 0 && !mbar_wait(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
-        for (int n = ta * NQ; n < te * NQ && ok; ++n) {
-          const int i = n / NQ, q = n % NQ;
-          if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-          if (!mbar_wait(&B.g_free, (n & 1) ^ 1, abort)) break;
-          tc_fence_after();
-          const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
-          const uint32_t wb = wq + q * QBYTES;
+        mma_commit_w(&B.st_free);
+        if (q == NQ - 1) mma_commit_w(&B.acc_full);
+        return true;
+      };
+      bool ok = true;
+      // pass B of the previous sub-piece overwrote the weights
+      if (sp > 0 && !mbar_wait_w(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
+      for (int n = ta * NQ; n < te * NQ && ok; ++n) {
+        const int i = n / NQ, q = n % NQ;
+        if (q == 0 && !mbar_wait_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+        if (!mbar_wait_w(&B.g_free, (n & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
+        const uint32_t wb = wq + q * QBYTES;
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            mma_ss(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
+        for (int ks = 0; ks < 4; ++ks) {
+          mma_ss_w(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
                    ks > 0);
-            mma_ss(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
+          mma_ss_w(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
                    sdesc_sw128(wb + 16384 + ks * 32, 16, 1024), IDESC_G2, ks > 0);
-          }
-          mma_commit(&B.g_full);
-          if (n > ta * NQ) ok = issue_acc(n - 1);
         }
-        if (ok && !*abort) issue_acc(te * NQ - 1);
+        mma_commit_w(&B.g_full);
+        if (n > ta * NQ) ok = issue_acc(n - 1);
       }
-      __syncwarp();
+      if (__all_sync(0xffffffffu, ok && !*abort)) issue_acc(te * NQ - 1);
     } else if (warp == 2) {
       // stores: the weights (once), the scratch factors of every quarter,
       // dk/dv of every tile
@@ -404,31 +403,28 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       }
       __syncwarp();
     } else if (warp == 1) {
-      if (lane == 0) {
-        bool ok = true;
-        for (int j = 0; j < nb; ++j) {
-          const int s = (j + rot) % PB_STAGES;
-          if (!mbar_wait(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
-            ok = false;
-            break;
-          }
-          pb_uses ^= 1u << s;
-          tc_fence_after();
-          const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t acc = (jb0 + j > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
-            const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
-            mma_ss(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
-          }
-          mma_commit(&B.b_empty[s]);
+      bool ok = true;
+      for (int j = 0; j < nb; ++j) {
+        const int s = (j + rot) % PB_STAGES;
+        if (!mbar_wait_w(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
+          ok = false;
+          break;
         }
-        if (ok) mma_commit(&B.bdone);
+        pb_uses ^= 1u << s;
+        tc_fence_after();
+        const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t acc = (jb0 + j > 0 || ks > 0) ? 1u : 0u;
+          const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
+          const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
+          mma_ss_w(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+          mma_ss_w(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
+          mma_ss_w(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
+        }
+        mma_commit_w(&B.b_empty[s]);
       }
-      __syncwarp();
+      if (ok) mma_commit_w(&B.bdone);
     }
     // everyone waits for the sub-piece's weight-adjoint products before the
     // next pass A reuses their shared memory

@@ -136,35 +136,33 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
   }
 
   if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t w13 = smem_u32(wb13), w2a = smem_u32(wb2);
-      auto issue_zq = [&](int i) -> bool {
-        const int s = i % QSTAGES;
-        if (!mbar_wait(&B.q_full[s], (i / QSTAGES) & 1, abort)) return false;
-        if (!mbar_wait(&B.zq_free, (i & 1) ^ 1, abort)) return false;
-        tc_fence_after();
-        const uint32_t qa = smem_u32(Qs + s * QT * 128);
+    // the whole warp runs the issue loop; one elected lane issues
+    const uint32_t w13 = smem_u32(wb13), w2a = smem_u32(wb2);
+    auto issue_zq = [&](int i) -> bool {
+      const int s = i % QSTAGES;
+      if (!mbar_wait_w(&B.q_full[s], (i / QSTAGES) & 1, abort)) return false;
+      if (!mbar_wait_w(&B.zq_free, (i & 1) ^ 1, abort)) return false;
+      tc_fence_after();
+      const uint32_t qa = smem_u32(Qs + s * QT * 128);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_ss(tb + A_ZQ, sdesc_sw128(qa + kk * 32, 16, 1024), sdesc_sw128(w13 + kk * 32, 16, 1024), IDESC_AZ,
+      for (int kk = 0; kk < 4; ++kk)
+        mma_ss_w(tb + A_ZQ, sdesc_sw128(qa + kk * 32, 16, 1024), sdesc_sw128(w13 + kk * 32, 16, 1024), IDESC_AZ,
                  kk > 0);
-        mma_commit(&B.zq_full);
-        mma_commit(&B.q_empty[s]);
-        return true;
-      };
-      bool ok = issue_zq(0);
-      for (int i = 0; i < ntiles && ok; ++i) {
-        if (i + 1 < ntiles && !issue_zq(i + 1)) break;
-        if (!mbar_wait(&B.h_full, i & 1, abort)) break;
-        tc_fence_after();
+      mma_commit_w(&B.zq_full);
+      mma_commit_w(&B.q_empty[s]);
+      return true;
+    };
+    bool ok = issue_zq(0);
+    for (int i = 0; i < ntiles && ok; ++i) {
+      if (i + 1 < ntiles && !issue_zq(i + 1)) break;
+      if (!mbar_wait_w(&B.h_full, i & 1, abort)) break;
+      tc_fence_after();
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          mma_ts(tb + A_O, tb + A_H + 8 * kk, sdesc_sw128(w2a + (kk / 4) * (D * 128) + (kk % 4) * 32, 16, 1024),
+      for (int kk = 0; kk < 8; ++kk)
+        mma_ts_w(tb + A_O, tb + A_H + 8 * kk, sdesc_sw128(w2a + (kk / 4) * (D * 128) + (kk % 4) * 32, 16, 1024),
                  IDESC_AO, kk > 0);
-        mma_commit(&B.o_full);
-      }
+      mma_commit_w(&B.o_full);
     }
-    __syncwarp();
     return;
   }
 

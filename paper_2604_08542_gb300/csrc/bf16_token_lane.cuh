@@ -226,69 +226,65 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     }
     __syncwarp();
   } else if (warp == 1) {
-    // the G products of every quarter, as soon as a G buffer is free
-    if (lane == 0) {
-      const uint32_t wq = smem_u32(sm + AW_OFF);
-      for (int n = 0; n < nq; ++n) {
-        const int i = n / NQ, q = n % NQ, b = n & 1;
-        if (q == 0 && !mbar_wait(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
-        const uint32_t wb = wq + q * AQ_BYTES;
-        const uint32_t gb = tb + A_BUF + b * A_GBUF;
+    // the G products of every quarter, as soon as a G buffer is free (the
+    // whole warp runs the loop; one elected lane issues)
+    const uint32_t wq = smem_u32(sm + AW_OFF);
+    for (int n = 0; n < nq; ++n) {
+      const int i = n / NQ, q = n % NQ, b = n & 1;
+      if (q == 0 && !mbar_wait_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+      if (!mbar_wait_w(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
+      tc_fence_after();
+      const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
+      const uint32_t wb = wq + q * AQ_BYTES;
+      const uint32_t gb = tb + A_BUF + b * A_GBUF;
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          mma_ss(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
-          mma_ss(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
+      for (int ks = 0; ks < 4; ++ks) {
+        mma_ss_w(gb, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1, ks > 0);
+        mma_ss_w(gb + 64, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024), sdesc_sw128(wb + 8192 + ks * 32, 16, 1024),
                  IDESC_G2, ks > 0);
-        }
-        mma_commit(&B.ga_full[b]);
       }
+      mma_commit_w(&B.ga_full[b]);
     }
-    __syncwarp();
   } else if (warp == EPI0 + 8) {
     // dq products of every staged quarter (DQ); after a tile's last quarter,
     // its L products (A = the staged factors of all four quarters, hidden-unit
     // blocks of 32 at a stride of one staging tile).  The tile's G products
     // all completed before its last quarter was staged, so the commits after
-    // the L products also cover every read of the tile's X/Y stage.
-    if (lane == 0) {
-      const uint32_t wq = smem_u32(sm + AW_OFF), stg = smem_u32(sm + AST_OFF);
-      bool ok = true;
-      for (int m = 0; m < nq && ok; ++m) {
-        const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait(&B.sq_full[q], i & 1, abort)) break;
-        if (DQ && q == 0 && !mbar_wait(&B.acc_free, (i & 1) ^ 1, abort)) break;
-        tc_fence_after();
-        if (DQ) {
-          const uint32_t wb = wq + q * AQ_BYTES;
+    // the L products also cover every read of the tile's X/Y stage.  The
+    // whole warp runs the loop; one elected lane issues.
+    const uint32_t wq = smem_u32(sm + AW_OFF), stg = smem_u32(sm + AST_OFF);
+    bool ok = true;
+    for (int m = 0; m < nq && ok; ++m) {
+      const int i = m / NQ, q = m % NQ;
+      if (!mbar_wait_w(&B.sq_full[q], i & 1, abort)) break;
+      if (DQ && q == 0 && !mbar_wait_w(&B.acc_free, (i & 1) ^ 1, abort)) break;
+      tc_fence_after();
+      if (DQ) {
+        const uint32_t wb = wq + q * AQ_BYTES;
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            mma_ss(tb + A_DX, sdesc_sw64(stg + ((ks / 2) * NQ + q) * ST_TILE + (ks % 2) * 32, 16, 512),
+        for (int ks = 0; ks < 4; ++ks)
+          mma_ss_w(tb + A_DX, sdesc_sw64(stg + ((ks / 2) * NQ + q) * ST_TILE + (ks % 2) * 32, 16, 512),
                    sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
-        }
-        if (q == NQ - 1) {
-          if (DQ) mma_commit(&B.acc_full);
-          const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
-#pragma unroll
-          for (int ks = 0; ks < BT / 16; ++ks) {
-            const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t xd = sdesc_sw128(xs + ks * 2048, 1024, 1024);
-            const uint64_t yd = sdesc_sw128(xs + 16384 + ks * 2048, 1024, 1024);
-            mma_ss(tb + B_L, sdesc_sw64(stg + 0 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 64, sdesc_sw64(stg + 1 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
-            mma_ss(tb + B_L + 128, sdesc_sw64(stg + 2 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), yd, IDESC_LAM,
-                   acc);
-            // token rows [32g, 32g + 32) of the staging are read after K-step 2g + 1
-            if (ks & 1) mma_commit(&B.st_free[ks >> 1]);
-          }
-          mma_commit(&B.xy_empty[i & 1]);    // its X/Y stage may be reloaded
-        }
       }
-      if (ok && !*abort) mma_commit(&B.bdone);
+      if (q == NQ - 1) {
+        if (DQ) mma_commit_w(&B.acc_full);
+        const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
+#pragma unroll
+        for (int ks = 0; ks < BT / 16; ++ks) {
+          const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+          const uint64_t xd = sdesc_sw128(xs + ks * 2048, 1024, 1024);
+          const uint64_t yd = sdesc_sw128(xs + 16384 + ks * 2048, 1024, 1024);
+          mma_ss_w(tb + B_L, sdesc_sw64(stg + 0 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
+          mma_ss_w(tb + B_L + 64, sdesc_sw64(stg + 1 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), xd, IDESC_LAM, acc);
+          mma_ss_w(tb + B_L + 128, sdesc_sw64(stg + 2 * NQ * ST_TILE + ks * 1024, ST_TILE, 512), yd, IDESC_LAM,
+                   acc);
+          // token rows [32g, 32g + 32) of the staging are read after K-step 2g + 1
+          if (ks & 1) mma_commit_w(&B.st_free[ks >> 1]);
+        }
+        mma_commit_w(&B.xy_empty[i & 1]);    // its X/Y stage may be reloaded
+      }
     }
-    __syncwarp();
+    if (__all_sync(0xffffffffu, ok && !*abort)) mma_commit_w(&B.bdone);
   } else if (DQ && warp == 2) {
     // dq of every full tile by TMA store
     if (lane == 0) {
