@@ -10,6 +10,7 @@
 // chunk j-1's apply, at W_j), update(j) (normalisation VJP), then dw0.
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 
 #include "ttt_internal.h"
@@ -22,10 +23,17 @@ cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 cudaError_t prepare_fp32();
 cudaError_t prepare_bf16_forward();
 cudaError_t prepare_bf16_backward();
+bool wide_shape_supported(int D, int F);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s);
+cudaError_t prepare_wide();
+cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
+                         const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
+                         cudaStream_t st);
 cudaError_t prepare_kernels() {
   cudaError_t e = prepare_fp32();
   if (e == cudaSuccess) e = prepare_bf16_forward();
   if (e == cudaSuccess) e = prepare_bf16_backward();
+  if (e == cudaSuccess) e = prepare_wide();
   return e;
 }
 }  // namespace scal3r
@@ -58,6 +66,7 @@ struct scal3r_ttt_handle {
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   bool graph_on = false;
+  bool wide = false;            // BF16 wide-weight path (head_dim, hidden multiples of 256)
   cudaStream_t capture_stream = nullptr;
   GraphSlot gfwd, gbwd;
 };
@@ -317,8 +326,9 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (cfg->weight_norm < 0 || cfg->weight_norm > 2) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
     return SCAL3R_ERR_UNSUPPORTED;
+  const bool wide = cfg->dtype == SCAL3R_BF16 && wide_shape_supported(cfg->head_dim, cfg->hidden_dim);
   if (cfg->dtype == SCAL3R_BF16 &&
-      (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
+      ((!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) && !wide) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
@@ -334,6 +344,7 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   hd->shape = Shape{cfg->num_heads, cfg->head_dim, cfg->hidden_dim};
   hd->device = dev;
   hd->num_sms = sms;
+  hd->wide = wide;
   if (cudaMalloc((void**)&hd->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(hd->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&hd->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -366,6 +377,11 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   if (!hd || !bytes) return SCAL3R_ERR_INVALID_ARG;
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
+  if (hd->wide) {
+    if (with_backward) return SCAL3R_ERR_UNSUPPORTED;
+    *bytes = wide_workspace_bytes(hd->plan, hd->shape);
+    return SCAL3R_OK;
+  }
   *bytes = workspace_bytes(hd->plan, hd->shape, with_backward != 0);
   return SCAL3R_OK;
 }
@@ -385,8 +401,36 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(o)) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
+  if (hd->wide) {
+    Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    fill_common(hd, prm);
+    prm.q = q;
+    prm.k = k;
+    prm.v = v;
+    prm.lr = lr;
+    prm.w0 = w0;
+    prm.w0_seq_stride = w0_seq_stride;
+    prm.o = o;
+    prm.w_ckpt = w_ckpt;
+    prm.wnorm = wnorm;
+    prm.w_final = w_final;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto enqueue = [&](cudaStream_t cs) -> int {
+      auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
+        return timed(hd, kind == 0 ? SCAL3R_KERNEL_FWD_SWEEP : SCAL3R_KERNEL_FWD_UPDATE, flops, bytes, cs, fn);
+      };
+      return wide_forward(pl, sh, prm, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+    };
+    if (hd->graph_on && !hd->prof_on) {
+      uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 7);
+      key = fnv1a(&workspace, sizeof(workspace), key);
+      return run_graph(hd, hd->gfwd, key, st, enqueue);
+    }
+    return enqueue(st);
+  }
 
   Params prm;
   std::memset(&prm, 0, sizeof(prm));   // the graph key hashes the whole struct
@@ -416,6 +460,7 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         const float* wnorm, void* dq, void* dk, void* dv, float* dlr, float* dw0,
                         void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -488,6 +533,7 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         void* dv, float* dlr, float* dw0, int32_t with_backward, void* stream,
                         scal3r_ttt_schedule* best, float* best_ms) {
   if (!hd || !best || !best_ms) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   if (with_backward && (!d_o || !dq || !dk || !dv || !dlr || !dw0 || !w_ckpt || !wnorm))
     return SCAL3R_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -638,6 +684,7 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
                             int64_t w_seq_stride, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S,
                             float* grad, void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -684,6 +731,7 @@ int scal3r_ttt_apply_update(scal3r_ttt_handle* hd, const float* w, int64_t w_seq
                             const float* w0, int64_t w0_seq_stride, int32_t num_seqs, float* w_out, float* wnorm,
                             void* stream) {
   if (!hd || num_seqs < 0) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   const Shape& sh = hd->shape;
   if (num_seqs == 0) return SCAL3R_OK;
   if (!w || !grad || !w0 || !w_out || w_seq_stride < 0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
@@ -710,6 +758,7 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
                      int32_t C, const int32_t* ptr, int32_t S, void* o, void* workspace, size_t workspace_bytes_,
                      void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;

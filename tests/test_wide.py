@@ -1,0 +1,91 @@
+"""The wide-weight BF16 forward (head_dim and hidden multiples of 256, up to the
+paper's own AMU shape: one head, hd = 1024, hidden = 4 hd) through the C ABI,
+against the FP64 oracle on the same bfloat16-rounded q, k, v (GPU).
+
+Bar: normwise relative error <= 2e-2 on o, every checkpoint, the
+pre-normalisation row norms and w_final, as for the head_dim-64 BF16 path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import ttt_synth as syn
+from _util import rel_inf, to_np, upload
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-2
+
+
+def _run(H, D, F, lengths, seed, graph=False, layer=None):
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=seed, dtype="bf16")
+    g = upload(x, torch.bfloat16)
+    if layer is None:
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    layer.set_graph_mode(graph)
+    out = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                        want_final=True)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    return layer, lay, x, out
+
+
+def _check(out, ref, tol=TOL):
+    o, ck, wn, wf = (to_np(t) for t in out)
+    errs = {"o": rel_inf(o, ref["o"]), "w_ckpt": rel_inf(ck, ref["w_ckpt"]), "wnorm": rel_inf(wn, ref["wnorm"]),
+            "w_final": rel_inf(wf, ref["w_final"])}
+    bad = {n: e for n, e in errs.items() if not e <= tol}
+    assert not bad, f"above {tol}: {bad}; all {errs}"
+    return errs
+
+
+def test_wide_two_heads_ragged_matches_oracle():
+    """D = 256, F = 512, two heads, two sequences; chunk lengths off the
+    128-token tile (300, 129) and a short sequence (77)."""
+    H, D, F = 2, 256, 512
+    _, lay, x, out = _run(H, D, F, [[300, 129], [77]], seed=41)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+
+
+def test_wide_paper_shape_matches_oracle():
+    """The paper's AMU: one head, hd = 1024, hidden 4096 (k = 4); two chunks."""
+    H, D, F = 1, 1024, 4096
+    _, lay, x, out = _run(H, D, F, [[640, 200]], seed=42)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+
+
+@pytest.mark.parametrize("k_scale", [1, 2])
+def test_wide_state_size_ablation_shapes(k_scale):
+    """hd = 512 with hidden k * hd for k = 1, 2 (the state-size ablation's k)."""
+    H, D = 1, 512
+    F = k_scale * D
+    _, lay, x, out = _run(H, D, F, [[383, 260]], seed=43 + k_scale)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+
+
+def test_wide_graph_replay_and_determinism():
+    import torch
+    layer, lay, x, a = _run(1, 256, 512, [[500, 300]], seed=44)
+    a = [t.clone() for t in a]
+    _, _, _, b = _run(1, 256, 512, [[500, 300]], seed=44, layer=layer)
+    for _ in range(2):
+        _, _, _, c = _run(1, 256, 512, [[500, 300]], seed=44, graph=True, layer=layer)
+    for u, w, z in zip(a, b, c):
+        assert torch.equal(u, w) and torch.equal(u, z)
+
+
+def test_wide_backward_is_refused():
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    layer, lay, x, out = _run(1, 256, 256, [[130]], seed=45)
+    g = upload(x, torch.bfloat16)
+    d_o = torch.zeros_like(g["q"])
+    with pytest.raises(ttt.Scal3rError):
+        layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr, d_o,
+                       out[1], out[2])
