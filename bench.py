@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="a step is the forward pass alone")
+    ap.add_argument("--no-amu", action="store_true", help="skip the paper-shape (hd 1024) forward line")
     return ap.parse_args()
 
 
@@ -186,6 +187,75 @@ def run_reference(args, rank: int):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def amu_leg(args, dev, peak_tflops):
+    """The forward at the paper's own AMU shape (one head, hd 1024, hidden
+    4096; workload bf16_amu1024): graph-replay tokens/s, and the GEMM rate
+    from a direct-launch loop with per-kernel events."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    w = syn.workload("bf16_amu1024")
+    lay = w.layout()
+    T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
+    off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed + 77)
+
+    def unit_rows():
+        x = torch.randn((T, H, D), generator=gen, device=dev)
+        return (x / x.norm(dim=-1, keepdim=True)).to(torch.bfloat16)
+
+    q, k, v = unit_rows(), unit_rows(), unit_rows()
+    lr = torch.rand((T, H), generator=gen, device=dev) * 0.1
+    w0 = torch.randn((H, 3 * F * D), generator=gen, device=dev) * 0.125
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    ws = layer.workspace(off, ptr, False, dev)
+    o = torch.empty_like(q)
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd():
+        layer.forward(q, k, v, lr, w0, off, ptr, save_for_backward=False, workspace=ws, o=o)
+
+    def loop(n, profile=False):
+        if profile:
+            ttt.scal3r_ttt_profile_enable(layer.handle, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        torch.cuda.synchronize()
+        for i in range(n):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            fwd()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = {ttt.KERNEL_KINDS[kk]: ttt.scal3r_ttt_profile_read(layer.handle, kk) for kk in ttt.KERNEL_KINDS}
+            ttt.scal3r_ttt_profile_enable(layer.handle, False)
+        return [a.elapsed_time(b) for a, b in ev], prof
+
+    steps = max(3, args.steps // 4)
+    for _ in range(2):
+        fwd()
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    layer.set_graph_mode(True)
+    for _ in range(2):
+        fwd()
+    ms, _ = loop(steps)
+    layer.set_graph_mode(False)
+    _, prof = loop(steps, profile=True)
+    assert layer.status() == 0
+    gm = prof["fwd_sweep"]
+    gemm_tflops = gm["flops"] / (gm["ms"] / 1e3) / 1e12 if gm["ms"] > 0 else 0.0
+    step_ms = statistics.mean(ms)
+    return {"workload": w.name, "description": w.description, "tokens_per_s": T / (step_ms / 1e3),
+            "ms_per_step": step_ms, "step_tflops": 18.0 * T * D * F / (step_ms / 1e3) / 1e12,
+            "gemm_tflops": gemm_tflops, "gemm_frac_of_bf16_peak": gemm_tflops / peak_tflops,
+            "gemm_ms_per_step": gm["ms"] / steps, "gemm_launches_per_step": gm["launches"] // steps,
+            "update_ms_per_step": prof["fwd_update"]["ms"] / steps,
+            "note": "forward only; algorithmic FLOPs 18*D*F per token; GEMM rate from a direct-launch loop"}
+
 
 def run_gpu(args, rank: int, world: int):
     import torch
@@ -373,6 +443,10 @@ def run_gpu(args, rank: int, world: int):
     fwd_sweep_tflops = fs["flops"] / (fs["ms"] / 1e3) / 1e12 if fs["ms"] > 0 else 0.0
     gpu_launches = sum(v["launches"] for v in prof.values())
 
+    amu = None
+    if not args.no_amu and rank == 0 and not args.fwd_only and world == 1:
+        amu = amu_leg(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+
     cpu = None
     if not args.no_cpu:
         slay, sx = oracle_sample(w, args.seed)
@@ -396,6 +470,7 @@ def run_gpu(args, rank: int, world: int):
                 "sweep_frac_of_bf16_peak": fwd_sweep_tflops / pk.get("bf16_tflops", 1900.0),
                 "sweep_ms_per_step": fs["ms"] / args.steps},
         "fp32": fp32,
+        "paper_amu": amu,
         "eager_profiled": {"tokens_per_s": eager_value, "ms_per_step": statistics.mean(pms),
                            "note": "the same step launched directly, an event pair around every kernel; "
                                    "the kernel breakdown and the roofline come from this loop"},

@@ -186,7 +186,7 @@ class Workload:
 
 
 def workload(name: str, seed: int = 0) -> Workload:
-    """The five workloads of the layer's benchmark suite, by name."""
+    """The workloads of the layer's benchmark suite, by name."""
     if name == "fp32_small":
         return Workload(name, [8], 128, 1, 1, 64, 128, "fp32", False,
                         "1 seq x 8 frames x 128 tokens, 1 head, D=64, F=128, chunk 128 tokens, FP32")
@@ -205,10 +205,15 @@ def workload(name: str, seed: int = 0) -> Workload:
     if name == "bf16_window256":
         return Workload(name, [256], TOKENS_PER_FRAME, 32, 16, 64, 128, "bf16", True,
                         "1 seq x 256 frames x 1041 tokens, 16 heads x 64, F=128, chunk 32 frames, BF16 fwd+bwd")
+    if name == "bf16_amu1024":
+        return Workload(name, [64], TOKENS_PER_FRAME, 16, 1, 1024, 4096, "bf16", False,
+                        "1 seq x 64 frames x 1041 tokens, 1 head x 1024 (the paper's AMU), F=4096 (k=4), "
+                        "chunk 16 frames, BF16 forward")
     raise KeyError(name)
 
 
-WORKLOADS = ["fp32_small", "bf16_vggt64", "bf16_fwdbwd_2x32", "bf16_ragged24", "bf16_long2000", "bf16_window256"]
+WORKLOADS = ["fp32_small", "bf16_vggt64", "bf16_fwdbwd_2x32", "bf16_ragged24", "bf16_long2000", "bf16_window256",
+             "bf16_amu1024"]
 
 
 # ---------------------------------------------------------------------------
