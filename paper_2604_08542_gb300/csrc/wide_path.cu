@@ -12,11 +12,11 @@
 //   G1 = g1^T K, G3 = g3^T K         [F x D],  G2 = V^T u~   [D x F]
 //   W <- W - G, rows rescaled (row norm targets of W0)       (wide_update_kernel)
 //   O  = (silu(Q W1^T) o (Q W3^T)) W2^T                      (two GEMMs)
-// All GEMMs run on one tcgen05 kernel: 128 x 256 output tiles, K in steps of
-// 64 through a four-stage TMA pipeline (128-byte swizzle, either operand K- or
-// MN-major), one elected thread of a converged warp issuing M128 N256 K16
-// MMAs into a 256-column TMEM accumulator, and four epilogue warps (TMEM lane
-// = output row).  The Z1/Z3 GEMMs read W1 and W3 rows of the same 128 hidden
+// All GEMMs run on one persistent tcgen05 kernel: 128 x 256 output tiles, K
+// in steps of 64 through a four-stage TMA pipeline (128-byte swizzle, either
+// operand K- or MN-major), one elected thread of a converged warp issuing
+// M128 N256 K16 MMAs into two 256-column TMEM accumulators in turn, and two
+// groups of four epilogue warps (TMEM lane = output row), one per accumulator.  The Z1/Z3 GEMMs read W1 and W3 rows of the same 128 hidden
 // units into one N = 256 operand, so one tile holds both halves of the gate.
 #include <cudaTypedefs.h>
 
@@ -38,7 +38,7 @@ constexpr uint32_t A_STAGE = BM * BK * 2;               // 16 KB
 constexpr uint32_t B_STAGE = BN * BK * 2;               // 32 KB
 constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;
 constexpr size_t GEMM_SMEM = 1024 + STAGES * STAGE_BYTES;
-constexpr int GEMM_THREADS = 192;                       // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int GEMM_THREADS = 320;                       // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 
 enum Epi : int { EPI_F32 = 0, EPI_BF16 = 1, EPI_KEY = 2, EPI_APPLY = 3 };
 
@@ -64,16 +64,20 @@ __device__ __forceinline__ float silu_d(float z, float& sg) {
   return z * sg;
 }
 
+// Persistent: CTA b takes output tiles b, b + gridDim.x, ... (consecutive
+// CTAs share an A row-block).  The TMA warp runs the stage ring across tiles;
+// the MMA warp alternates between two 256-column accumulators; epilogue group
+// g (four warps, all 128 TMEM lanes) drains the tiles of accumulator g, so a
+// tile's epilogue overlaps the next tile's MMAs.
 __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full;
+  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = g.N / BN;
-  const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int ntiles = ((g.M + BM - 1) / BM) * tiles_n;
   const int nk = (g.K + BK - 1) / BK;
   volatile int* abort = &abort_flag;
 
@@ -82,7 +86,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
     abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&g.a);
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     if (g.gate) prefetch_tmap(&g.b1);
   }
   if (warp == 1) {
-    tmem_alloc(&tmem_base, 256);
+    tmem_alloc(&tmem_base, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -100,62 +107,90 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1, abort)) break;
-        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-        uint8_t* as = sm + s * STAGE_BYTES;
-        uint8_t* bs = as + A_STAGE;
-        const int k0 = kb * BK;
-        if (!g.a_mn) {
-          tma_load_3d(as, &g.a, &full[s], k0, g.ha, g.ya + m0);
-        } else {
-          tma_load_3d(as, &g.a, &full[s], m0, g.ha, g.ya + k0);
-          tma_load_3d(as + 8192, &g.a, &full[s], m0 + 64, g.ha, g.ya + k0);
-        }
-        if (g.gate) {
-          const int f0 = tn * (BN / 2);
-          tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + f0);
-          tma_load_3d(bs + B_STAGE / 2, &g.b1, &full[s], k0, g.hb, g.yb + f0);
-        } else if (!g.b_mn) {
-          tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + n0);
-        } else {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int tm = t / tiles_n, tn = t % tiles_n;
+        const int m0 = tm * BM, n0 = tn * BN;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+          uint8_t* as = sm + s * STAGE_BYTES;
+          uint8_t* bs = as + A_STAGE;
+          const int k0 = kb * BK;
+          if (!g.a_mn) {
+            tma_load_3d(as, &g.a, &full[s], k0, g.ha, g.ya + m0);
+          } else {
+            tma_load_3d(as, &g.a, &full[s], m0, g.ha, g.ya + k0);
+            tma_load_3d(as + 8192, &g.a, &full[s], m0 + 64, g.ha, g.ya + k0);
+          }
+          if (g.gate) {
+            const int f0 = tn * (BN / 2);
+            tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + f0);
+            tma_load_3d(bs + B_STAGE / 2, &g.b1, &full[s], k0, g.hb, g.yb + f0);
+          } else if (!g.b_mn) {
+            tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + n0);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) tma_load_3d(bs + 8192 * j, &g.b0, &full[s], n0 + 64 * j, g.hb, g.yb + k0);
+            for (int j = 0; j < 4; ++j) tma_load_3d(bs + 8192 * j, &g.b0, &full[s], n0 + 64 * j, g.hb, g.yb + k0);
+          }
         }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     const uint32_t idesc = idesc_bf16(BM, BN, g.a_mn != 0, g.b_mn != 0);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait_w(&full[s], (kb / STAGES) & 1, abort)) break;
+    uint32_t it = 0;
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      const int ac = i & 1;
+      if (!mbar_wait_w(&acc_empty[ac], ((i >> 1) & 1) ^ 1, abort)) break;
       tc_fence_after();
-      const uint32_t as = smem_u32(sm + s * STAGE_BYTES), bs = as + A_STAGE;
+      const uint32_t acc = tb + ac * 256;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = it % STAGES;
+        if (!mbar_wait_w(&full[s], (it / STAGES) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t as = smem_u32(sm + s * STAGE_BYTES), bs = as + A_STAGE;
 #pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint64_t ad = g.a_mn ? sdesc_sw128(as + ks * 2048, 8192, 1024) : sdesc_sw128(as + ks * 32, 16, 1024);
-        const uint64_t bd = g.b_mn ? sdesc_sw128(bs + ks * 2048, 8192, 1024) : sdesc_sw128(bs + ks * 32, 16, 1024);
-        mma_ss_w(tb, ad, bd, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint64_t ad = g.a_mn ? sdesc_sw128(as + ks * 2048, 8192, 1024) : sdesc_sw128(as + ks * 32, 16, 1024);
+          const uint64_t bd = g.b_mn ? sdesc_sw128(bs + ks * 2048, 8192, 1024) : sdesc_sw128(bs + ks * 32, 16, 1024);
+          mma_ss_w(acc, ad, bd, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+        }
+        mma_commit_w(&empty[s]);
       }
-      mma_commit_w(&empty[s]);
+      if (ok) mma_commit_w(&acc_full[ac]);
     }
-    mma_commit_w(&acc_full);
   } else {
-    // epilogue: thread = output row m0 + row; TMEM lanes of this warp
+    // epilogue group gp = warps 2..5 (gp 0) or 6..9 (gp 1); thread = output
+    // row m0 + row of the TMEM lanes of this warp
+    const int gp = (warp - 2) >> 2;
     const uint32_t row = 32u * (warp & 3) + lane;
     const uint32_t lane_base = (32u * (warp & 3)) << 16;
-    const int m = m0 + (int)row;
-    const bool valid = m < g.M;
-    if (mbar_wait(&acc_full, 0, abort)) {
+    const uint32_t accb = tb + lane_base + gp * 256;
+    int i = gp;
+    for (int t = blockIdx.x + gp * gridDim.x; t < ntiles; t += 2 * gridDim.x, i += 2) {
+      if (!mbar_wait(&acc_full[gp], (i >> 1) & 1, abort)) break;
       tc_fence_after();
+      const int tm = t / tiles_n, tn = t % tiles_n;
+      const int m0 = tm * BM, n0 = tn * BN;
+      const int m = m0 + (int)row;
+      const bool valid = m < g.M;
       if (g.epi == EPI_F32 || g.epi == EPI_BF16) {
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           float v0[16], v1[16];
-          tmem_ld16(tb + lane_base + c, v0);
-          tmem_ld16(tb + lane_base + c + 16, v1);
+          tmem_ld16(accb + c, v0);
+          tmem_ld16(accb + c + 16, v1);
           if (!valid) continue;
           if (g.epi == EPI_F32) {
             float* o = reinterpret_cast<float*>(g.out0) + (size_t)m * g.ld_out + n0 + c;
@@ -185,11 +220,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         // units f0 .. f0 + 127
         const int f0 = tn * (BN / 2);
         const float eta = (g.epi == EPI_KEY && valid) ? g.eta[(size_t)m * g.eta_stride] : 0.f;
-#pragma unroll 1
+        // KEY: this row's 128 values of P, loaded at once (one memory latency
+        // per tile instead of one per 16 columns)
+        uint4 prow[16];
+        if (g.epi == EPI_KEY && valid) {
+          const uint4* pp = reinterpret_cast<const uint4*>(g.p + (size_t)m * g.ld_out + f0);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) prow[j] = __ldg(pp + j);
+        }
+#pragma unroll
         for (int c = 0; c < BN / 2; c += 16) {
           float z1[16], z3[16];
-          tmem_ld16(tb + lane_base + c, z1);
-          tmem_ld16(tb + lane_base + 128 + c, z3);
+          tmem_ld16(accb + c, z1);
+          tmem_ld16(accb + 128 + c, z3);
           if (!valid) continue;
           const size_t off = (size_t)m * g.ld_out + f0 + c;
           if (g.epi == EPI_APPLY) {
@@ -204,8 +247,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             o[0] = make_uint4(h[0], h[1], h[2], h[3]);
             o[1] = make_uint4(h[4], h[5], h[6], h[7]);
           } else {
-            const uint4* pp = reinterpret_cast<const uint4*>(g.p + off);
-            const uint4 pr0 = pp[0], pr1 = pp[1];
+            const uint4 pr0 = prow[c / 8], pr1 = prow[c / 8 + 1];
             const uint32_t pw[8] = {pr0.x, pr0.y, pr0.z, pr0.w, pr1.x, pr1.y, pr1.z, pr1.w};
             uint32_t o1[8], o3[8], ou[8];
 #pragma unroll
@@ -241,13 +283,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           }
         }
       }
+      // the accumulator is drained: the MMA warp may reuse it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gp]);
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (abort_flag && threadIdx.x == 0) atomicExch(g.status, SCAL3R_ERR_TIMEOUT);
-  if (warp == 1) tmem_dealloc(tb, 256);
+  if (warp == 1) tmem_dealloc(tb, 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -421,9 +467,20 @@ WideBufs carve(const Plan& p, const Shape& s, void* ws) {
   return w;
 }
 
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
 cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N % BN != 0 || a.K <= 0) return cudaErrorInvalidValue;
-  const int grid = ((a.M + BM - 1) / BM) * (a.N / BN);
+  const int tiles = ((a.M + BM - 1) / BM) * (a.N / BN);
+  const int grid = std::min(tiles, num_sms());
   wide_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   return cudaGetLastError();
 }
