@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="a step is the forward pass alone")
     ap.add_argument("--no-amu", action="store_true", help="skip the paper-shape (hd 1024) forward line")
+    ap.add_argument("--amu-only", action="store_true",
+                    help="run only the paper-shape forward (two direct forwards first: 33 launches each)")
     return ap.parse_args()
 
 
@@ -493,6 +495,13 @@ def main():
             print(json.dumps(out))
         return
     import torch
+    if args.amu_only:
+        from paper_2604_08542_gb300 import build as builder
+        builder.build()
+        pk, _ = peaks()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        print(json.dumps({"paper_amu": amu_leg(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))}))
+        return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
