@@ -24,11 +24,14 @@ cudaError_t prepare_fp32();
 cudaError_t prepare_bf16_forward();
 cudaError_t prepare_bf16_backward();
 bool wide_shape_supported(int D, int F);
-size_t wide_workspace_bytes(const Plan& p, const Shape& s);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward);
 cudaError_t prepare_wide();
 cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
                          cudaStream_t st);
+cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
+                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
+                          cudaStream_t st);
 cudaError_t prepare_kernels() {
   cudaError_t e = prepare_fp32();
   if (e == cudaSuccess) e = prepare_bf16_forward();
@@ -378,8 +381,7 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   if (hd->wide) {
-    if (with_backward) return SCAL3R_ERR_UNSUPPORTED;
-    *bytes = wide_workspace_bytes(hd->plan, hd->shape);
+    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0);
     return SCAL3R_OK;
   }
   *bytes = workspace_bytes(hd->plan, hd->shape, with_backward != 0);
@@ -401,7 +403,7 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(o)) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh) : workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -460,7 +462,6 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         const float* wnorm, void* dq, void* dk, void* dv, float* dlr, float* dw0,
                         void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -473,7 +474,7 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         (const void*)w0, (const void*)dw0})
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
   if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = workspace_bytes(pl, sh, true);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, true) : workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
   Params prm;
@@ -493,8 +494,22 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   prm.dv = dv;
   prm.dlr = dlr;
   prm.dw0 = dw0;
-  carve_workspace(pl, sh, true, workspace, prm);
   cudaStream_t st = (cudaStream_t)stream;
+  if (hd->wide) {
+    auto enqueue = [&](cudaStream_t cs) -> int {
+      auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
+        return timed(hd, kind == 0 ? SCAL3R_KERNEL_BWD_SWEEP : SCAL3R_KERNEL_BWD_UPDATE, flops, bytes, cs, fn);
+      };
+      return wide_backward(pl, sh, prm, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+    };
+    if (hd->graph_on && !hd->prof_on) {
+      uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 9);
+      key = fnv1a(&workspace, sizeof(workspace), key);
+      return run_graph(hd, hd->gbwd, key, st, enqueue);
+    }
+    return enqueue(st);
+  }
+  carve_workspace(pl, sh, true, workspace, prm);
   if (hd->graph_on && !hd->prof_on) {
     uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 2);
     return run_graph(hd, hd->gbwd, key, st, [&](cudaStream_t cs) { return enqueue_backward(hd, prm, cs); });

@@ -40,28 +40,94 @@ constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;
 constexpr size_t GEMM_SMEM = 1024 + STAGES * STAGE_BYTES;
 constexpr int GEMM_THREADS = 320;                       // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 
-enum Epi : int { EPI_F32 = 0, EPI_BF16 = 1, EPI_KEY = 2, EPI_APPLY = 3 };
+enum Epi : int {
+  EPI_F32 = 0,      // out[0] = acc (float32)
+  EPI_BF16 = 1,     // out[0] = acc (bf16)
+  EPI_KEY = 2,      // forward gradient gate: z1 | z3 of 128 hidden, in0 = P -> g1, g3, u~
+  EPI_APPLY = 3,    // forward apply gate: z1 | z3 -> h
+  EPI_F32_ADD = 4,  // out[0] += acc (float32)
+  EPI_BAPPLY = 5,   // apply VJP gate: zq1 | zq3 of 128 hidden, in0 = W2^T d_o -> dzq1, dzq3, uq
+  EPI_BKEY = 6,     // update VJP gate: z1 | z3 | dg1 | dg3 of 64 hidden, in0 = W2^T v, in1 = -R2^T v
+                    //   -> dz1, dz3, g1, g3, -eta dp, -eta u and a partial of d eta
+};
 
 struct GemmArgs {
-  CUtensorMap a, b0, b1;   // operand maps; b1: W3 rows of the gate GEMMs
+  CUtensorMap a[4], b[4];  // operand maps: K segment s reads a[s] / b[s]; N block j of the B tile reads b[j]
   int M, N, K;             // output rows, output columns (N = 256 * tiles), reduction length
-  int a_mn, b_mn, gate;    // operand major-ness; gate: B = [W1 rows; W3 rows] of 128 hidden units
+  int kseg, nseg;          // nseg > 1: K is nseg segments of kseg (a multiple of 64)
+  int nbn;                 // > 1: the B tile is nbn blocks of 256 / nbn rows (K-major, one segment)
+  int a_mn, b_mn;          // operand major-ness
   int ha, hb;              // coordinate 1 of the A / B maps (the head of a [T, H, D] tensor)
   int ya, yb;              // row offset added to the A / B map's row coordinate
   int epi;
-  void* out0;              // F32 / BF16: [M x N]; KEY: g1; APPLY: h
-  void* out1;              // KEY: g3
-  void* out2;              // KEY: u~
-  int64_t ld_out;          // row stride of the outputs (elements)
-  const __nv_bfloat16* p;  // KEY: raw P = V W2, [M x F] with row stride ld_out
-  const float* eta;        // KEY: learning rate of output row m at eta[m * eta_stride]
+  void* out[6];            // outputs (see Epi); token-major [M x ...] with row stride ld_out
+  int64_t ld_out;
+  const __nv_bfloat16* in0;  // epilogue inputs [M x F], row stride ld_out
+  const __nv_bfloat16* in1;
+  const float* eta;        // learning rate of output row m at eta[m * eta_stride]
   int64_t eta_stride;
+  float* part;             // EPI_BKEY: d eta partial of row m, tile column tn at part[m * ld_part + tn]
+  int64_t ld_part;
   int* status;
 };
 
 __device__ __forceinline__ float silu_d(float z, float& sg) {
   sg = sigmoid_fast(z);
   return z * sg;
+}
+
+// Packs 16 floats to 8 bf16x2 words and stores them (two 16-byte stores).
+__device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
+  uint4* o = reinterpret_cast<uint4*>(dst);
+  o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+  o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                    pack_bf16(v[14], v[15]));
+}
+
+// Four 8-column TMEM loads (z1, z3, dg1, dg3 of the same rows) and one wait.
+__device__ __forceinline__ void tmem_ld8x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, float (&r)[4][8]) {
+  uint32_t u[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+        "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]),
+        "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
+        "=r"(u[30]), "=r"(u[31])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "memory");
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[m][i] = __uint_as_float(u[8 * m + i]);
+}
+
+// Unpacks 8 bf16 (one 16-byte word) to floats.
+__device__ __forceinline__ void unpack8(const uint4& a, float* v) {
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    v[2 * j] = __uint_as_float(w[j] << 16);
+    v[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+  }
+}
+
+__device__ __forceinline__ uint4 pack8f(const float* v) {
+  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
+// Unpacks 16 bf16 (two 16-byte words) to floats.
+__device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* v) {
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v[2 * j] = __uint_as_float(w[j] << 16);
+    v[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+  }
 }
 
 // Persistent: CTA b takes output tiles b, b + gridDim.x, ... (consecutive
@@ -79,6 +145,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
   const int tiles_n = g.N / BN;
   const int ntiles = ((g.M + BM - 1) / BM) * tiles_n;
   const int nk = (g.K + BK - 1) / BK;
+  const int kps = g.nseg > 1 ? g.kseg / BK : nk;   // K blocks per segment
   volatile int* abort = &abort_flag;
 
   if (threadIdx.x == 0) {
@@ -92,9 +159,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     }
     abort_flag = 0;
     fence_barrier_init();
-    prefetch_tmap(&g.a);
-    prefetch_tmap(&g.b0);
-    if (g.gate) prefetch_tmap(&g.b1);
+    for (int j = 0; j < g.nseg; ++j) prefetch_tmap(&g.a[j]);
+    for (int j = 0; j < (g.nbn > g.nseg ? g.nbn : g.nseg); ++j) prefetch_tmap(&g.b[j]);
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base, 512);
@@ -121,22 +187,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
           uint8_t* as = sm + s * STAGE_BYTES;
           uint8_t* bs = as + A_STAGE;
-          const int k0 = kb * BK;
+          const int sg = kb / kps, k0 = (kb % kps) * BK;
+          const CUtensorMap* am = &g.a[sg];
           if (!g.a_mn) {
-            tma_load_3d(as, &g.a, &full[s], k0, g.ha, g.ya + m0);
+            tma_load_3d(as, am, &full[s], k0, g.ha, g.ya + m0);
           } else {
-            tma_load_3d(as, &g.a, &full[s], m0, g.ha, g.ya + k0);
-            tma_load_3d(as + 8192, &g.a, &full[s], m0 + 64, g.ha, g.ya + k0);
+            tma_load_3d(as, am, &full[s], m0, g.ha, g.ya + k0);
+            tma_load_3d(as + 8192, am, &full[s], m0 + 64, g.ha, g.ya + k0);
           }
-          if (g.gate) {
-            const int f0 = tn * (BN / 2);
-            tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + f0);
-            tma_load_3d(bs + B_STAGE / 2, &g.b1, &full[s], k0, g.hb, g.yb + f0);
+          if (g.nbn > 1) {
+            const int rows = BN / g.nbn;
+            for (int j = 0; j < g.nbn; ++j)
+              tma_load_3d(bs + j * (B_STAGE / g.nbn), &g.b[j], &full[s], k0, g.hb, g.yb + tn * rows);
           } else if (!g.b_mn) {
-            tma_load_3d(bs, &g.b0, &full[s], k0, g.hb, g.yb + n0);
+            tma_load_3d(bs, &g.b[sg], &full[s], k0, g.hb, g.yb + n0);
           } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) tma_load_3d(bs + 8192 * j, &g.b0, &full[s], n0 + 64 * j, g.hb, g.yb + k0);
+            for (int j = 0; j < 4; ++j) tma_load_3d(bs + 8192 * j, &g.b[sg], &full[s], n0 + 64 * j, g.hb, g.yb + k0);
           }
         }
       }
@@ -185,46 +252,91 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       const int m0 = tm * BM, n0 = tn * BN;
       const int m = m0 + (int)row;
       const bool valid = m < g.M;
-      if (g.epi == EPI_F32 || g.epi == EPI_BF16) {
+      if (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD) {
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           float v0[16], v1[16];
           tmem_ld16(accb + c, v0);
           tmem_ld16(accb + c + 16, v1);
           if (!valid) continue;
-          if (g.epi == EPI_F32) {
-            float* o = reinterpret_cast<float*>(g.out0) + (size_t)m * g.ld_out + n0 + c;
+          if (g.epi == EPI_BF16) {
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c;
+            st_bf16x16(o, v0);
+            st_bf16x16(o + 16, v1);
+          } else {
+            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              reinterpret_cast<float4*>(o)[j] = make_float4(v0[4 * j], v0[4 * j + 1], v0[4 * j + 2], v0[4 * j + 3]);
-              reinterpret_cast<float4*>(o + 16)[j] =
-                  make_float4(v1[4 * j], v1[4 * j + 1], v1[4 * j + 2], v1[4 * j + 3]);
-            }
-          } else {
-            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(g.out0) + (size_t)m * g.ld_out + n0 + c;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              reinterpret_cast<uint4*>(o)[j] = make_uint4(pack_bf16(v0[8 * j], v0[8 * j + 1]),
-                                                          pack_bf16(v0[8 * j + 2], v0[8 * j + 3]),
-                                                          pack_bf16(v0[8 * j + 4], v0[8 * j + 5]),
-                                                          pack_bf16(v0[8 * j + 6], v0[8 * j + 7]));
-              reinterpret_cast<uint4*>(o + 16)[j] = make_uint4(pack_bf16(v1[8 * j], v1[8 * j + 1]),
-                                                               pack_bf16(v1[8 * j + 2], v1[8 * j + 3]),
-                                                               pack_bf16(v1[8 * j + 4], v1[8 * j + 5]),
-                                                               pack_bf16(v1[8 * j + 6], v1[8 * j + 7]));
+              float4 x0 = make_float4(v0[4 * j], v0[4 * j + 1], v0[4 * j + 2], v0[4 * j + 3]);
+              float4 x1 = make_float4(v1[4 * j], v1[4 * j + 1], v1[4 * j + 2], v1[4 * j + 3]);
+              if (g.epi == EPI_F32_ADD) {
+                const float4 y0 = o[j], y1 = o[4 + j];
+                x0 = make_float4(y0.x + x0.x, y0.y + x0.y, y0.z + x0.z, y0.w + x0.w);
+                x1 = make_float4(y1.x + x1.x, y1.y + x1.y, y1.z + x1.z, y1.w + x1.w);
+              }
+              o[j] = x0;
+              o[4 + j] = x1;
             }
           }
         }
+      } else if (g.epi == EPI_BKEY) {
+        // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
+        // hidden units f0 .. f0 + 63 (dg = -R k)
+        const int f0 = tn * (BN / 4);
+        const float eta = valid ? g.eta[(size_t)m * g.eta_stride] : 0.f;
+        float deta = 0.f;
+        const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
+        const uint4* np = reinterpret_cast<const uint4*>(g.in1 + (size_t)m * g.ld_out + f0);
+#pragma unroll 1
+        for (int c = 0; c < 64; c += 8) {
+          uint4 pw = make_uint4(0, 0, 0, 0), nw = pw;
+          if (valid) {   // in flight during the TMEM loads
+            pw = __ldg(pp + c / 8);
+            nw = __ldg(np + c / 8);
+          }
+          float zz[4][8];
+          tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
+          if (!valid) continue;
+          float praw[8], ndu[8];
+          unpack8(pw, praw);
+          unpack8(nw, ndu);
+          float o[6][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float sg;
+            const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
+            const float a = silu_d(x1, sg);
+            const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
+            const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);    // silu''(z1)
+            const float u = a * x3;
+            const float pv = -eta * praw[e];
+            const float du = -eta * ndu[e];
+            const float dp = d3 * a + d1 * x3 * sp;
+            const float da = d3 * pv + du * x3;
+            o[1][e] = d1 * pv * sp + du * a;                 // dz3
+            o[0][e] = d1 * pv * x3 * spp + da * sp;          // dz1
+            o[2][e] = pv * x3 * sp;                          // g1
+            o[3][e] = pv * a;                                // g3
+            o[4][e] = -eta * dp;                             // -eta dp
+            o[5][e] = -eta * u;                              // -eta u
+            deta -= praw[e] * dp + ndu[e] * u;
+          }
+          const size_t off = (size_t)m * g.ld_out + f0 + c;
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
+        }
+        if (valid) g.part[(size_t)m * g.ld_part + tn] = deta;
       } else {
         // gate epilogues: columns [0, 128) are z1, [128, 256) z3 of hidden
         // units f0 .. f0 + 127
         const int f0 = tn * (BN / 2);
         const float eta = (g.epi == EPI_KEY && valid) ? g.eta[(size_t)m * g.eta_stride] : 0.f;
-        // KEY: this row's 128 values of P, loaded at once (one memory latency
-        // per tile instead of one per 16 columns)
+        // this row's 128 values of the epilogue input (KEY: P; BAPPLY:
+        // W2^T d_o), loaded at once: one memory latency per tile
         uint4 prow[16];
-        if (g.epi == EPI_KEY && valid) {
-          const uint4* pp = reinterpret_cast<const uint4*>(g.p + (size_t)m * g.ld_out + f0);
+        if (g.epi != EPI_APPLY && valid) {
+          const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
 #pragma unroll
           for (int j = 0; j < 16; ++j) prow[j] = __ldg(pp + j);
         }
@@ -236,50 +348,37 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           if (!valid) continue;
           const size_t off = (size_t)m * g.ld_out + f0 + c;
           if (g.epi == EPI_APPLY) {
-            uint32_t h[8];
+            float h[16];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float s0, s1;
-              const float a0 = silu_d(z1[2 * j], s0), a1 = silu_d(z1[2 * j + 1], s1);
-              h[j] = pack_bf16(a0 * z3[2 * j], a1 * z3[2 * j + 1]);
+            for (int e = 0; e < 16; ++e) {
+              float sg;
+              h[e] = silu_d(z1[e], sg) * z3[e];
             }
-            uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out0) + off);
-            o[0] = make_uint4(h[0], h[1], h[2], h[3]);
-            o[1] = make_uint4(h[4], h[5], h[6], h[7]);
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, h);
           } else {
-            const uint4 pr0 = prow[c / 8], pr1 = prow[c / 8 + 1];
-            const uint32_t pw[8] = {pr0.x, pr0.y, pr0.z, pr0.w, pr1.x, pr1.y, pr1.z, pr1.w};
-            uint32_t o1[8], o3[8], ou[8];
+            float r[16];
+            unpack16(prow[c / 8], prow[c / 8 + 1], r);
+            float o0[16], o1[16], o2[16];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float r[2];
-              r[0] = __uint_as_float(pw[j] << 16);
-              r[1] = __uint_as_float(pw[j] & 0xFFFF0000u);
-              float v1[2], v3[2], vu[2];
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                const float x1 = z1[2 * j + e], x3 = z3[2 * j + e];
-                float sg;
-                const float a = silu_d(x1, sg);
-                const float sp = fmaf(a, 1.f - sg, sg);     // silu'(z1)
-                const float pv = -eta * r[e];               // p = W2^T e, e = -eta v
-                v1[e] = pv * x3 * sp;
-                v3[e] = pv * a;
-                vu[e] = -eta * a * x3;
+            for (int e = 0; e < 16; ++e) {
+              float sg;
+              const float x1 = z1[e], x3 = z3[e];
+              const float a = silu_d(x1, sg);
+              const float sp = fmaf(a, 1.f - sg, sg);     // silu'(z1)
+              if (g.epi == EPI_KEY) {
+                const float pv = -eta * r[e];             // p = W2^T e, e = -eta v
+                o0[e] = pv * x3 * sp;                     // g1
+                o1[e] = pv * a;                           // g3
+                o2[e] = -eta * a * x3;                    // u~ = -eta u
+              } else {                                    // EPI_BAPPLY, r = W2^T d_o
+                o0[e] = r[e] * x3 * sp;                   // dzq1
+                o1[e] = r[e] * a;                         // dzq3
+                o2[e] = a * x3;                           // uq
               }
-              o1[j] = pack_bf16(v1[0], v1[1]);
-              o3[j] = pack_bf16(v3[0], v3[1]);
-              ou[j] = pack_bf16(vu[0], vu[1]);
             }
-            uint4* d1 = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out0) + off);
-            uint4* d3 = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out1) + off);
-            uint4* du = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out2) + off);
-            d1[0] = make_uint4(o1[0], o1[1], o1[2], o1[3]);
-            d1[1] = make_uint4(o1[4], o1[5], o1[6], o1[7]);
-            d3[0] = make_uint4(o3[0], o3[1], o3[2], o3[3]);
-            d3[1] = make_uint4(o3[4], o3[5], o3[6], o3[7]);
-            du[0] = make_uint4(ou[0], ou[1], ou[2], ou[3]);
-            du[1] = make_uint4(ou[4], ou[5], ou[6], ou[7]);
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, o0);
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off, o1);
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[2]) + off, o2);
           }
         }
       }
@@ -389,6 +488,114 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_update_kernel(float* __restr
   }
 }
 
+// Backward setup of one chain: row-norm targets of W0 and their adjoints.
+__global__ void __launch_bounds__(ROW_THREADS) wide_bprep_kernel(const float* __restrict__ w0, float* __restrict__ rho,
+                                                                 float* __restrict__ drho, int D, int F, int norm) {
+  __shared__ float red[ROW_THREADS / 32 + 1];
+  size_t off;
+  int len;
+  row_geometry(blockIdx.x, D, F, off, len);
+  float ss = 0.f;
+  for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+    const float4 x = *reinterpret_cast<const float4*>(w0 + off + i);
+    ss += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+  }
+  ss = block_sum(ss, red);
+  if (threadIdx.x == 0) {
+    rho[blockIdx.x] = (norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
+    drho[blockIdx.x] = 0.f;
+  }
+}
+
+// Operands of one backward step: bf16 W (from w), bf16 -R (from r, if any),
+// and the adjoint accumulator lam = R (or 0).
+__global__ void wide_bstep_setup_kernel(const float* __restrict__ w, const float* __restrict__ r,
+                                        __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ nrb,
+                                        float* __restrict__ lam, size_t P) {
+  for (size_t i = 4 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x); i < P; i += 4 * (size_t)gridDim.x * blockDim.x) {
+    const float4 x = *reinterpret_cast<const float4*>(w + i);
+    *reinterpret_cast<uint2*>(wb + i) = make_uint2(pack_bf16(x.x, x.y), pack_bf16(x.z, x.w));
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r) {
+      y = *reinterpret_cast<const float4*>(r + i);
+      *reinterpret_cast<uint2*>(nrb + i) = make_uint2(pack_bf16(-y.x, -y.y), pack_bf16(-y.z, -y.w));
+    }
+    *reinterpret_cast<float4*>(lam + i) = y;
+  }
+}
+
+// Closing a backward step (one block per row).  lam = dL/dW_j.  For j > 0 the
+// VJP of the row normalisation of update j-1 (W_j = rho w~ / max(|w~|, eps)):
+//   unclamped  R = (rho / |w~|) (lam - w_hat (w_hat . lam)),  clamped  R = (rho / eps) lam,
+//   w_hat = W_j / rho, drho += w_hat . lam;
+// for j = 0, dW0 = lam + drho W0 / rho (added to dw0 when accumulate is set).
+__global__ void __launch_bounds__(ROW_THREADS) wide_bupdate_kernel(const float* __restrict__ lam,
+                                                                   const float* __restrict__ wj,
+                                                                   const float* __restrict__ wnorm,
+                                                                   const float* __restrict__ rho, float* drho,
+                                                                   float* __restrict__ rout, const float* w0,
+                                                                   float* dw0, int accumulate, int D, int F, int norm,
+                                                                   float eps) {
+  __shared__ float red[ROW_THREADS / 32 + 1];
+  size_t off;
+  int len;
+  row_geometry(blockIdx.x, D, F, off, len);
+  const float rh = rho[blockIdx.x];
+  if (dw0) {
+    const float coef = (norm == SCAL3R_NORM_ROW_W0 && rh > 0.f) ? drho[blockIdx.x] / rh : 0.f;
+    for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+      const float4 l = *reinterpret_cast<const float4*>(lam + off + i);
+      const float4 x = *reinterpret_cast<const float4*>(w0 + off + i);
+      float4 y = make_float4(l.x + coef * x.x, l.y + coef * x.y, l.z + coef * x.z, l.w + coef * x.w);
+      if (accumulate) {
+        const float4 z = *reinterpret_cast<const float4*>(dw0 + off + i);
+        y = make_float4(z.x + y.x, z.y + y.y, z.z + y.z, z.w + y.w);
+      }
+      *reinterpret_cast<float4*>(dw0 + off + i) = y;
+    }
+    return;
+  }
+  if (norm == SCAL3R_NORM_NONE) {
+    for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS)
+      *reinterpret_cast<float4*>(rout + off + i) = *reinterpret_cast<const float4*>(lam + off + i);
+    return;
+  }
+  const float inv = rh > 0.f ? 1.f / rh : 0.f;
+  float pr = 0.f;
+  for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+    const float4 l = *reinterpret_cast<const float4*>(lam + off + i);
+    const float4 x = *reinterpret_cast<const float4*>(wj + off + i);
+    pr += (x.x * l.x + x.y * l.y + x.z * l.z + x.w * l.w) * inv;
+  }
+  const float proj = block_sum(pr, red);
+  const float n = wnorm[blockIdx.x];
+  const bool clamped = !(n >= eps);
+  const float c = clamped ? rh / eps : rh / n;
+  for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+    const float4 l = *reinterpret_cast<const float4*>(lam + off + i);
+    const float4 x = *reinterpret_cast<const float4*>(wj + off + i);
+    float4 y;
+    if (clamped) {
+      y = make_float4(c * l.x, c * l.y, c * l.z, c * l.w);
+    } else {
+      y = make_float4(c * (l.x - x.x * inv * proj), c * (l.y - x.y * inv * proj), c * (l.z - x.z * inv * proj),
+                      c * (l.w - x.w * inv * proj));
+    }
+    *reinterpret_cast<float4*>(rout + off + i) = y;
+  }
+  if (threadIdx.x == 0 && norm == SCAL3R_NORM_ROW_W0) drho[blockIdx.x] += proj;
+}
+
+// d eta of the chunk's tokens: the per-tile partials summed in tile order.
+__global__ void wide_deta_kernel(const float* __restrict__ part, int64_t ld_part, int nparts, float* __restrict__ dlr,
+                                 int64_t stride, int M) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  float a = 0.f;
+  for (int j = 0; j < nparts; ++j) a += part[(size_t)m * ld_part + j];
+  dlr[(size_t)m * stride] = a;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -420,51 +627,58 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int heads, int64_t
 }  // namespace
 
 bool wide_shape_supported(int D, int F) {
-  return D >= 128 && D % 256 == 0 && F >= 256 && F % 256 == 0 && F <= 4096 && D <= 4096;
-}
-
-size_t wide_workspace_bytes(const Plan& p, const Shape& s) {
-  int64_t mmax = 0;
-  for (size_t c = 0; c + 1 < p.chunk_offsets.size(); ++c)
-    mmax = std::max<int64_t>(mmax, p.chunk_offsets[c + 1] - p.chunk_offsets[c]);
-  mmax = (mmax + BM - 1) / BM * BM;
-  const size_t P = (size_t)s.P();
-  const size_t act = (size_t)mmax * s.F * 2;           // one [M x F] bf16 buffer
-  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  return 4 * al(act) + 2 * al(P * 4) + al(P * 2) + al((size_t)s.R() * 4);
-}
-
-cudaError_t prepare_wide() {
-  return cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  return D >= 256 && D % 256 == 0 && F >= 256 && F % 256 == 0 && F <= 4096 && D <= 4096;
 }
 
 namespace {
 
-struct WideBufs {
-  __nv_bfloat16 *pb, *g1, *g3, *ut;   // [mmax x F] each; pb also holds h
-  float *wm, *gr, *rho;
-  __nv_bfloat16* wb;
-};
-
-WideBufs carve(const Plan& p, const Shape& s, void* ws) {
+int64_t max_chunk(const Plan& p) {
   int64_t mmax = 0;
   for (size_t c = 0; c + 1 < p.chunk_offsets.size(); ++c)
     mmax = std::max<int64_t>(mmax, p.chunk_offsets[c + 1] - p.chunk_offsets[c]);
-  mmax = (mmax + BM - 1) / BM * BM;
+  return (mmax + BM - 1) / BM * BM;
+}
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Workspace: activation buffers [mmax x F] bf16 (4 forward, 8 backward),
+// then float32 and bf16 weight-sized buffers.
+struct WideBufs {
+  __nv_bfloat16* act[8];
+  float* wm;      // forward: master weights;  backward: lam (dL/dW_j)
+  float* gr;      // forward: chunk gradient;  backward: R (dL/dW~ of the next update)
+  __nv_bfloat16* wb;    // bf16 weights
+  __nv_bfloat16* nrb;   // backward: bf16 -R
+  float* rho;
+  float* drho;
+  float* part;    // backward: d eta partials [mmax x F/64]
+};
+
+size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, WideBufs* w, void* ws) {
   const size_t P = (size_t)s.P();
-  const size_t act = (size_t)mmax * s.F * 2;
-  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  uint8_t* b = reinterpret_cast<uint8_t*>(ws);
-  WideBufs w;
-  w.pb = reinterpret_cast<__nv_bfloat16*>(b); b += al(act);
-  w.g1 = reinterpret_cast<__nv_bfloat16*>(b); b += al(act);
-  w.g3 = reinterpret_cast<__nv_bfloat16*>(b); b += al(act);
-  w.ut = reinterpret_cast<__nv_bfloat16*>(b); b += al(act);
-  w.wm = reinterpret_cast<float*>(b); b += al(P * 4);
-  w.gr = reinterpret_cast<float*>(b); b += al(P * 4);
-  w.wb = reinterpret_cast<__nv_bfloat16*>(b); b += al(P * 2);
-  w.rho = reinterpret_cast<float*>(b);
-  return w;
+  const int64_t mmax = max_chunk(p);
+  const size_t act = al256((size_t)mmax * s.F * 2);
+  uint8_t* base = reinterpret_cast<uint8_t*>(ws);
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    uint8_t* q = base ? base + o : nullptr;
+    o += al256(n);
+    return q;
+  };
+  const int nact = bwd ? 8 : 4;
+  WideBufs x{};
+  for (int i = 0; i < nact; ++i) x.act[i] = reinterpret_cast<__nv_bfloat16*>(take(act));
+  x.wm = reinterpret_cast<float*>(take(P * 4));
+  x.gr = reinterpret_cast<float*>(take(P * 4));
+  x.wb = reinterpret_cast<__nv_bfloat16*>(take(P * 2));
+  if (bwd) x.nrb = reinterpret_cast<__nv_bfloat16*>(take(P * 2));
+  x.rho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
+  if (bwd) {
+    x.drho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
+    x.part = reinterpret_cast<float*>(take((size_t)mmax * (s.F / 64) * 4));
+  }
+  if (w) *w = x;
+  return o;
 }
 
 int num_sms() {
@@ -479,119 +693,309 @@ int num_sms() {
 
 cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   if (a.M <= 0 || a.N % BN != 0 || a.K <= 0) return cudaErrorInvalidValue;
+  if (a.nseg < 1) a.nseg = 1;
+  if (a.nbn < 1) a.nbn = 1;
+  if (a.nseg > 1 && (a.kseg % BK != 0 || a.kseg * a.nseg != a.K || a.nbn != 1)) return cudaErrorInvalidValue;
   const int tiles = ((a.M + BM - 1) / BM) * (a.N / BN);
   const int grid = std::min(tiles, num_sms());
   wide_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
+// Maps: a token tensor [T][H][D] (rows = tokens of head h) and a plain matrix [rows][cols].
+bool tok_map(CUtensorMap* m, const void* base, int64_t T, int H, int D, int box_rows) {
+  return make_map(m, base, T, H, D, (int64_t)H * D, box_rows);
+}
+bool mat_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int box_rows) {
+  return make_map(m, base, rows, 1, cols, cols, box_rows);
+}
+
+using LaunchFn = std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>;
+
+struct Ctx {
+  const Plan& pl;
+  const Shape& sh;
+  const Params& prm;
+  const LaunchFn& launch;
+  cudaStream_t st;
+};
+
+#define WIDE_TRY(x)                          \
+  do {                                       \
+    cudaError_t e_ = (x);                    \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
+#define WIDE_MAP(x)                                  \
+  do {                                               \
+    if (!(x)) return cudaErrorInvalidValue;          \
+  } while (0)
+
+cudaError_t run_gemm(const Ctx& c, GemmArgs& a, double flops) {
+  a.status = c.prm.status;
+  return c.launch(0, flops, 0, [&] { return gemm(a, c.st); });
+}
+
 }  // namespace
+
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
+  return layout_bytes(p, s, with_backward, nullptr, nullptr);
+}
+
+cudaError_t prepare_wide() {
+  return cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+}
 
 // The forward of every chain, chunk after chunk (see the file comment).
 // `launch` wraps each launch (profiling); kind 0 = GEMM, 1 = update / prep.
-cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
-                         const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
+cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const LaunchFn& launch,
                          cudaStream_t st) {
+  const Ctx cx{pl, sh, prm, launch, st};
   const int H = sh.H, D = sh.D, F = sh.F;
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
-  WideBufs w = carve(pl, sh, ws);
+  WideBufs w;
+  layout_bytes(pl, sh, false, &w, ws);
+  __nv_bfloat16 *pb = w.act[0], *g1 = w.act[1], *g3 = w.act[2], *ut = w.act[3];
   const int64_t T = pl.T;
+  const __nv_bfloat16* w1 = w.wb;
+  const __nv_bfloat16* w3 = w.wb + (size_t)F * D;
+  const __nv_bfloat16* w2 = w.wb + 2 * (size_t)F * D;
   for (int s = 0; s < pl.S; ++s) {
     for (int h = 0; h < H; ++h) {
       const float* w0 = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
-      cudaError_t e = launch(1, 0, 0, [&] {
+      WIDE_TRY(launch(1, 0, 0, [&] {
         wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(w0, w.wm, w.wb, w.rho, D, F, prm.norm);
         return cudaGetLastError();
-      });
-      if (e != cudaSuccess) return e;
-      // bf16 weight views: W1 [F][D], W3 [F][D], W2 [D][F]
-      const __nv_bfloat16* w1 = w.wb;
-      const __nv_bfloat16* w3 = w.wb + (size_t)F * D;
-      const __nv_bfloat16* w2 = w.wb + 2 * (size_t)F * D;
+      }));
       const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
       for (int c = c0; c < c1; ++c) {
         const int64_t t0 = pl.chunk_offsets[c], t1 = pl.chunk_offsets[c + 1];
         const int M = (int)(t1 - t0);
         const double mfd = 2.0 * M * (double)F * D;
-        GemmArgs g;
-        std::memset(&g, 0, sizeof(g));
-        g.status = prm.status;
-        // P = V W2: A = v rows of the chunk (K-major), B = W2 as [D][F] (MN-major)
-        {
-          GemmArgs a = g;
-          if (!make_map(&a.a, prm.v, T, H, D, (int64_t)H * D, 128) || !make_map(&a.b0, w2, D, 1, F, F, 64))
-            return cudaErrorInvalidValue;
+        {   // P = V W2
+          GemmArgs a{};
+          WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
           a.M = M; a.N = F; a.K = D; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_BF16; a.out0 = w.pb; a.ld_out = F;
-          e = launch(0, mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+          a.epi = EPI_BF16; a.out[0] = pb; a.ld_out = F;
+          WIDE_TRY(run_gemm(cx, a, mfd));
         }
-        // Z1, Z3 = K [W1; W3]^T with the gradient epilogue -> g1, g3, u~
-        {
-          GemmArgs a = g;
-          if (!make_map(&a.a, prm.k, T, H, D, (int64_t)H * D, 128) || !make_map(&a.b0, w1, F, 1, D, D, 128) ||
-              !make_map(&a.b1, w3, F, 1, D, D, 128))
-            return cudaErrorInvalidValue;
-          a.M = M; a.N = 2 * F; a.K = D; a.gate = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_KEY; a.out0 = w.g1; a.out1 = w.g3; a.out2 = w.ut; a.ld_out = F;
-          a.p = w.pb; a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
-          e = launch(0, 2 * mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+        {   // Z1, Z3 = K [W1; W3]^T with the gradient epilogue -> g1, g3, u~
+          GemmArgs a{};
+          WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+                   mat_map(&a.b[1], w3, F, D, 128));
+          a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+          a.epi = EPI_KEY; a.out[0] = g1; a.out[1] = g3; a.out[2] = ut; a.ld_out = F;
+          a.in0 = pb; a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+          WIDE_TRY(run_gemm(cx, a, 2 * mfd));
         }
-        // G1 = g1^T K, G3 = g3^T K: A = g (MN-major, rows = the chunk's tokens), B = k (MN-major)
-        for (int j = 0; j < 2; ++j) {
-          GemmArgs a = g;
-          if (!make_map(&a.a, j ? w.g3 : w.g1, M, 1, F, F, 64) || !make_map(&a.b0, prm.k, T, H, D, (int64_t)H * D, 64))
-            return cudaErrorInvalidValue;
+        for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
+          GemmArgs a{};
+          WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
           a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
-          a.epi = EPI_F32; a.out0 = w.gr + (size_t)j * F * D; a.ld_out = D;
-          e = launch(0, mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+          a.epi = EPI_F32; a.out[0] = w.gr + (size_t)j * F * D; a.ld_out = D;
+          WIDE_TRY(run_gemm(cx, a, mfd));
         }
-        // G2 = V^T u~: A = v (MN-major), B = u~ (MN-major)
-        {
-          GemmArgs a = g;
-          if (!make_map(&a.a, prm.v, T, H, D, (int64_t)H * D, 64) || !make_map(&a.b0, w.ut, M, 1, F, F, 64))
-            return cudaErrorInvalidValue;
+        {   // G2 = V^T u~
+          GemmArgs a{};
+          WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], ut, M, F, 64));
           a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_F32; a.out0 = w.gr + 2 * (size_t)F * D; a.ld_out = F;
-          e = launch(0, mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+          a.epi = EPI_F32; a.out[0] = w.gr + 2 * (size_t)F * D; a.ld_out = F;
+          WIDE_TRY(run_gemm(cx, a, mfd));
         }
-        // update and normalise
-        {
+        {   // update and normalise
           float* ck = prm.w_ckpt ? prm.w_ckpt + ((size_t)c * H + h) * P : nullptr;
           float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
           float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
-          e = launch(1, 0, 0, [&] {
+          WIDE_TRY(launch(1, 0, 0, [&] {
             wide_update_kernel<<<R, ROW_THREADS, 0, st>>>(w.wm, w.gr, w.wb, w.rho, ck, wn, wf, D, F, prm.norm,
                                                          prm.eps);
             return cudaGetLastError();
-          });
-          if (e != cudaSuccess) return e;
+          }));
         }
-        // apply: h = silu(Q W1^T) o (Q W3^T), then o = h W2^T
-        {
-          GemmArgs a = g;
-          if (!make_map(&a.a, prm.q, T, H, D, (int64_t)H * D, 128) || !make_map(&a.b0, w1, F, 1, D, D, 128) ||
-              !make_map(&a.b1, w3, F, 1, D, D, 128))
-            return cudaErrorInvalidValue;
-          a.M = M; a.N = 2 * F; a.K = D; a.gate = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_APPLY; a.out0 = w.pb; a.ld_out = F;
-          e = launch(0, 2 * mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+        {   // apply: h = silu(Q W1^T) o (Q W3^T)
+          GemmArgs a{};
+          WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+                   mat_map(&a.b[1], w3, F, D, 128));
+          a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+          a.epi = EPI_APPLY; a.out[0] = pb; a.ld_out = F;
+          WIDE_TRY(run_gemm(cx, a, 2 * mfd));
         }
-        {
-          GemmArgs a = g;
-          if (!make_map(&a.a, w.pb, M, 1, F, F, 128) || !make_map(&a.b0, w2, D, 1, F, F, 256))
-            return cudaErrorInvalidValue;
+        {   // o = h W2^T
+          GemmArgs a{};
+          WIDE_MAP(mat_map(&a.a[0], pb, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
           a.M = M; a.N = D; a.K = F;
-          a.epi = EPI_BF16; a.out0 = reinterpret_cast<__nv_bfloat16*>(prm.o) + ((size_t)t0 * H + h) * D;
+          a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.o) + ((size_t)t0 * H + h) * D;
           a.ld_out = (int64_t)H * D;
-          e = launch(0, mfd, 0, [&] { return gemm(a, st); });
-          if (e != cudaSuccess) return e;
+          WIDE_TRY(run_gemm(cx, a, mfd));
         }
+      }
+    }
+  }
+  return cudaSuccess;
+}
+
+// The backward of every chain: for j = n .. 0 (n = the sequence's chunks), at
+// W_j (W0, or the checkpoint after update j-1):
+//   apply VJP of chunk j-1:   du = W2^T d_o, gate -> dzq1, dzq3, uq;
+//                             dq = dzq1 W1 + dzq3 W3;  lam += [dzq1^T Q, dzq3^T Q, d_O^T uq]
+//   update VJP of chunk j with R = dL/dW~_{j+1}:  praw = W2^T v, ndu = -R2^T v,
+//                             gate [W1; W3; -R1; -R3] -> dz1, dz3, g1, g3, -eta dp, -eta u, d eta;
+//                             dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3], dv = [-eta dp, -eta u] [W2^T; -R2^T];
+//                             lam += R + [dz1^T K, dz3^T K, V^T (-eta dp)]
+//   normalisation VJP of update j-1 (R for the next step), or dW0 at j = 0.
+cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const LaunchFn& launch,
+                          cudaStream_t st) {
+  const Ctx cx{pl, sh, prm, launch, st};
+  const int H = sh.H, D = sh.D, F = sh.F;
+  const size_t P = (size_t)sh.P();
+  const int R = sh.R();
+  WideBufs w;
+  layout_bytes(pl, sh, true, &w, ws);
+  const int64_t T = pl.T;
+  const size_t FD = (size_t)F * D;
+  const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
+  const __nv_bfloat16 *r1 = w.nrb, *r3 = w.nrb + FD, *r2 = w.nrb + 2 * FD;   // -R
+  float *lam1 = w.wm, *lam3 = w.wm + FD, *lam2 = w.wm + 2 * FD;
+  const int nparts = F / 64;
+  for (int s = 0; s < pl.S; ++s) {
+    for (int h = 0; h < H; ++h) {
+      const float* w0 = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
+      float* dw0 = prm.dw0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
+      const bool acc_dw0 = prm.w0_seq_stride == 0 && s > 0;
+      WIDE_TRY(launch(1, 0, 0, [&] {
+        wide_bprep_kernel<<<R, ROW_THREADS, 0, st>>>(w0, w.rho, w.drho, D, F, prm.norm);
+        return cudaGetLastError();
+      }));
+      const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
+      const int n = c1 - c0;
+      for (int j = n; j >= 0; --j) {
+        const float* wj = (j == 0) ? w0 : prm.w_ckpt_in + ((size_t)(c0 + j - 1) * H + h) * P;
+        const bool key = j < n;
+        WIDE_TRY(launch(1, 0, 0, [&] {
+          wide_bstep_setup_kernel<<<4 * num_sms(), 256, 0, st>>>(wj, key ? w.gr : nullptr, w.wb, w.nrb, w.wm, P);
+          return cudaGetLastError();
+        }));
+        if (j >= 1) {   // apply VJP of chunk j-1
+          const int c = c0 + j - 1;
+          const int64_t t0 = pl.chunk_offsets[c];
+          const int M = (int)(pl.chunk_offsets[c + 1] - t0);
+          const double mfd = 2.0 * M * (double)F * D;
+          __nv_bfloat16 *du = w.act[0], *dz1 = w.act[1], *dz3 = w.act[2], *uq = w.act[3];
+          {   // du = d_o W2 (token rows)
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.d_o, T, H, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
+            a.M = M; a.N = F; a.K = D; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_BF16; a.out[0] = du; a.ld_out = F;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+          {   // gate on q -> dzq1, dzq3, uq
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+                     mat_map(&a.b[1], w3, F, D, 128));
+            a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_BAPPLY; a.out[0] = dz1; a.out[1] = dz3; a.out[2] = uq; a.ld_out = F; a.in0 = du;
+            WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+          }
+          {   // dq = dzq1 W1 + dzq3 W3
+            GemmArgs a{};
+            WIDE_MAP(mat_map(&a.a[0], dz1, M, F, 128) && mat_map(&a.a[1], dz3, M, F, 128) &&
+                     mat_map(&a.b[0], w1, F, D, 64) && mat_map(&a.b[1], w3, F, D, 64));
+            a.M = M; a.N = D; a.K = 2 * F; a.kseg = F; a.nseg = 2; a.b_mn = 1;
+            a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.dq) + ((size_t)t0 * H + h) * D;
+            a.ld_out = (int64_t)H * D;
+            WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+          }
+          for (int i = 0; i < 2; ++i) {   // lam1 += dzq1^T Q, lam3 += dzq3^T Q
+            GemmArgs a{};
+            WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.q, T, H, D, 64));
+            a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
+            a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+          {   // lam2 += d_O^T uq
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.d_o, T, H, D, 64) && mat_map(&a.b[0], uq, M, F, 64));
+            a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+        }
+        if (key) {   // update VJP of chunk j
+          const int c = c0 + j;
+          const int64_t t0 = pl.chunk_offsets[c];
+          const int M = (int)(pl.chunk_offsets[c + 1] - t0);
+          const double mfd = 2.0 * M * (double)F * D;
+          __nv_bfloat16 *pr = w.act[0], *nd = w.act[1];
+          __nv_bfloat16 *dz1 = w.act[2], *dz3 = w.act[3], *g1 = w.act[4], *g3 = w.act[5], *dpe = w.act[6],
+                        *ue = w.act[7];
+          for (int i = 0; i < 2; ++i) {   // praw = V W2, ndu = V (-R2)
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 128) && mat_map(&a.b[0], i ? r2 : w2, D, F, 64));
+            a.M = M; a.N = F; a.K = D; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_BF16; a.out[0] = i ? nd : pr; a.ld_out = F;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+          {   // gate [W1; W3; -R1; -R3] on k -> the six factors and d eta partials
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 64) &&
+                     mat_map(&a.b[1], w3, F, D, 64) && mat_map(&a.b[2], r1, F, D, 64) &&
+                     mat_map(&a.b[3], r3, F, D, 64));
+            a.M = M; a.N = 4 * F; a.K = D; a.nbn = 4; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_BKEY;
+            a.out[0] = dz1; a.out[1] = dz3; a.out[2] = g1; a.out[3] = g3; a.out[4] = dpe; a.out[5] = ue;
+            a.ld_out = F; a.in0 = pr; a.in1 = nd;
+            a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+            a.part = w.part; a.ld_part = nparts;
+            WIDE_TRY(run_gemm(cx, a, 4 * mfd));
+          }
+          {   // dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3]
+            GemmArgs a{};
+            WIDE_MAP(mat_map(&a.a[0], dz1, M, F, 128) && mat_map(&a.a[1], dz3, M, F, 128) &&
+                     mat_map(&a.a[2], g1, M, F, 128) && mat_map(&a.a[3], g3, M, F, 128) &&
+                     mat_map(&a.b[0], w1, F, D, 64) && mat_map(&a.b[1], w3, F, D, 64) &&
+                     mat_map(&a.b[2], r1, F, D, 64) && mat_map(&a.b[3], r3, F, D, 64));
+            a.M = M; a.N = D; a.K = 4 * F; a.kseg = F; a.nseg = 4; a.b_mn = 1;
+            a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.dk) + ((size_t)t0 * H + h) * D;
+            a.ld_out = (int64_t)H * D;
+            WIDE_TRY(run_gemm(cx, a, 4 * mfd));
+          }
+          {   // dv = [-eta dp, -eta u] [W2^T; -R2^T]
+            GemmArgs a{};
+            WIDE_MAP(mat_map(&a.a[0], dpe, M, F, 128) && mat_map(&a.a[1], ue, M, F, 128) &&
+                     mat_map(&a.b[0], w2, D, F, 256) && mat_map(&a.b[1], r2, D, F, 256));
+            a.M = M; a.N = D; a.K = 2 * F; a.kseg = F; a.nseg = 2;
+            a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.dv) + ((size_t)t0 * H + h) * D;
+            a.ld_out = (int64_t)H * D;
+            WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+          }
+          for (int i = 0; i < 2; ++i) {   // lam1 += dz1^T K, lam3 += dz3^T K
+            GemmArgs a{};
+            WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
+            a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
+            a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+          {   // lam2 += V^T (-eta dp)
+            GemmArgs a{};
+            WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], dpe, M, F, 64));
+            a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+            a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
+            WIDE_TRY(run_gemm(cx, a, mfd));
+          }
+          WIDE_TRY(launch(1, 0, 0, [&] {
+            wide_deta_kernel<<<(M + 127) / 128, 128, 0, st>>>(w.part, nparts, nparts, prm.dlr + (size_t)t0 * H + h,
+                                                               H, M);
+            return cudaGetLastError();
+          }));
+        }
+        // normalisation VJP of update j-1 -> R, or dW0
+        const float* wn = (j >= 1) ? prm.wnorm_in + ((size_t)(c0 + j - 1) * H + h) * R : nullptr;
+        WIDE_TRY(launch(1, 0, 0, [&] {
+          wide_bupdate_kernel<<<R, ROW_THREADS, 0, st>>>(w.wm, wj, wn, w.rho, w.drho, w.gr, w0,
+                                                         j == 0 ? dw0 : nullptr, acc_dw0 ? 1 : 0, D, F, prm.norm,
+                                                         prm.eps);
+          return cudaGetLastError();
+        }));
       }
     }
   }

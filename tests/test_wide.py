@@ -80,12 +80,63 @@ def test_wide_graph_replay_and_determinism():
         assert torch.equal(u, w) and torch.equal(u, z)
 
 
-def test_wide_backward_is_refused():
+def _fwd_bwd(H, D, F, lengths, seed, layer=None, graph=False, per_seq_w0=False):
     import torch
     import paper_2604_08542_gb300 as ttt
-    layer, lay, x, out = _run(1, 256, 256, [[130]], seed=45)
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=seed, dtype="bf16", with_grad_out=True)
+    if per_seq_w0:
+        S = len(lengths)
+        x["w0"] = np.stack([x["w0"] * (1.0 + 0.1 * s) for s in range(S)]).astype(np.float32)
     g = upload(x, torch.bfloat16)
-    d_o = torch.zeros_like(g["q"])
-    with pytest.raises(ttt.Scal3rError):
-        layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr, d_o,
-                       out[1], out[2])
+    if layer is None:
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    layer.set_graph_mode(graph)
+    o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    return layer, lay, x, grads
+
+
+def _check_grads(grads, rb, tol=TOL):
+    errs = {n: rel_inf(to_np(t), rb[n]) for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads)}
+    bad = {n: e for n, e in errs.items() if not e <= tol}
+    assert not bad, f"above {tol}: {bad}; all {errs}"
+    return errs
+
+
+def test_wide_backward_two_heads_ragged_matches_oracle():
+    """dq, dk, dv, d eta and dW0 (shared over two sequences) at hd 256, hidden
+    512: chunks off the tile (300, 129) and a one-chunk sequence (77)."""
+    H, D, F = 2, 256, 512
+    _, lay, x, grads = _fwd_bwd(H, D, F, [[300, 129], [77]], seed=51)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_backward_per_sequence_w0_matches_oracle():
+    """Three chunks in one sequence and a second sequence with its own w0."""
+    H, D, F = 1, 512, 1024
+    _, lay, x, grads = _fwd_bwd(H, D, F, [[200, 256, 70], [140]], seed=52, per_seq_w0=True)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_backward_paper_shape_matches_oracle():
+    """The paper's AMU: one head, hd 1024, hidden 4096; two chunks."""
+    H, D, F = 1, 1024, 4096
+    _, lay, x, grads = _fwd_bwd(H, D, F, [[384, 200]], seed=53)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_backward_graph_replay_is_bitwise_equal():
+    import torch
+    layer, lay, x, a = _fwd_bwd(1, 256, 512, [[300, 200]], seed=54)
+    a = [t.clone() for t in a]
+    for _ in range(2):
+        _, _, _, b = _fwd_bwd(1, 256, 512, [[300, 200]], seed=54, layer=layer, graph=True)
+        for u, w in zip(a, b):
+            assert torch.equal(u, w)
