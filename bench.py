@@ -216,10 +216,17 @@ def amu_leg(args, dev, peak_tflops):
     flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    d_o = torch.randn((T, H, D), generator=gen, device=dev).to(torch.bfloat16)
+    wsb = torch.empty(ttt.scal3r_ttt_workspace_size(layer.handle, off, ptr, True), dtype=torch.uint8, device=dev)
+
     def fwd():
         layer.forward(q, k, v, lr, w0, off, ptr, save_for_backward=False, workspace=ws, o=o)
 
-    def loop(n, profile=False):
+    def fwd_bwd():
+        _, ck, wn, _ = layer.forward(q, k, v, lr, w0, off, ptr, workspace=wsb, o=o)
+        layer.backward(q, k, v, lr, w0, off, ptr, d_o, ck, wn, workspace=wsb)
+
+    def loop(n, profile=False, fn=fwd):
         if profile:
             ttt.scal3r_ttt_profile_enable(layer.handle, True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
@@ -227,7 +234,7 @@ def amu_leg(args, dev, peak_tflops):
         for i in range(n):
             flush.fill_(i & 0xFF)
             ev[i][0].record(stream)
-            fwd()
+            fn()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         prof = None
@@ -251,12 +258,34 @@ def amu_leg(args, dev, peak_tflops):
     gm = prof["fwd_sweep"]
     gemm_tflops = gm["flops"] / (gm["ms"] / 1e3) / 1e12 if gm["ms"] > 0 else 0.0
     step_ms = statistics.mean(ms)
-    return {"workload": w.name, "description": w.description, "tokens_per_s": T / (step_ms / 1e3),
-            "ms_per_step": step_ms, "step_tflops": 18.0 * T * D * F / (step_ms / 1e3) / 1e12,
-            "gemm_tflops": gemm_tflops, "gemm_frac_of_bf16_peak": gemm_tflops / peak_tflops,
-            "gemm_ms_per_step": gm["ms"] / steps, "gemm_launches_per_step": gm["launches"] // steps,
-            "update_ms_per_step": prof["fwd_update"]["ms"] / steps,
-            "note": "forward only; algorithmic FLOPs 18*D*F per token; GEMM rate from a direct-launch loop"}
+    out = {"workload": w.name, "description": w.description, "tokens_per_s": T / (step_ms / 1e3),
+           "ms_per_step": step_ms, "step_tflops": 18.0 * T * D * F / (step_ms / 1e3) / 1e12,
+           "gemm_tflops": gemm_tflops, "gemm_frac_of_bf16_peak": gemm_tflops / peak_tflops,
+           "gemm_ms_per_step": gm["ms"] / steps, "gemm_launches_per_step": gm["launches"] // steps,
+           "update_ms_per_step": prof["fwd_update"]["ms"] / steps,
+           "note": "forward only; algorithmic FLOPs 18*D*F per token; GEMM rate from a direct-launch loop"}
+    # forward + backward (the backward's algorithmic FLOPs are 36*D*F per token)
+    for _ in range(2):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    layer.set_graph_mode(True)
+    for _ in range(2):
+        fwd_bwd()
+    bms, _ = loop(steps, fn=fwd_bwd)
+    layer.set_graph_mode(False)
+    _, bprof = loop(steps, profile=True, fn=fwd_bwd)
+    assert layer.status() == 0
+    gb = bprof["bwd_sweep"]
+    gf = bprof["fwd_sweep"]
+    both = (gb["flops"] + gf["flops"]) / ((gb["ms"] + gf["ms"]) / 1e3) / 1e12
+    bstep = statistics.mean(bms)
+    out["fwdbwd"] = {"tokens_per_s": T / (bstep / 1e3), "ms_per_step": bstep,
+                     "step_tflops": 54.0 * T * D * F / (bstep / 1e3) / 1e12,
+                     "bwd_gemm_tflops": gb["flops"] / (gb["ms"] / 1e3) / 1e12 if gb["ms"] > 0 else 0.0,
+                     "gemm_tflops": both, "gemm_frac_of_bf16_peak": both / peak_tflops,
+                     "note": "algorithmic FLOPs 54*D*F per token (forward 18, backward 36); the kernels recompute "
+                             "the forward products the backward needs"}
+    return out
 
 
 def run_gpu(args, rank: int, world: int):
