@@ -20,6 +20,15 @@
  * The backward entry point differentiates sum(d_o * o) through the whole
  * chain of updates (gradients to q, k, v, lr and w0).
  *
+ * Two BF16 implementations sit behind the same entry points, chosen by the
+ * config's shape: head_dim 64 / hidden 128 runs fused per-head sweep kernels
+ * (the weights of a head stay on chip for a chunk); head_dim and hidden that
+ * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
+ * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
+ * step as a large tcgen05 GEMM, forward and backward.  The wide path takes
+ * the dot loss; the GCS split entry points and the autotuner are for the
+ * head_dim-64 path (SCAL3R_ERR_UNSUPPORTED otherwise).
+ *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
  *  - q, k, v, o, d_o, dq, dk, dv: [T, H, D] contiguous, element type given by
@@ -76,8 +85,11 @@ extern "C" {
 
 typedef struct scal3r_ttt_config {
   int32_t num_heads;    /* H >= 1 */
-  int32_t head_dim;     /* D; the BF16 path needs 64, the FP32 path 1..128 */
-  int32_t hidden_dim;   /* F; the BF16 path needs 128, the FP32 path 1..256 */
+  int32_t head_dim;     /* D; BF16: 64 (fused per-head kernels) or a multiple of 256 up to 4096
+                           (wide-weight GEMM path, e.g. the paper's AMU with hd = 1024);
+                           FP32: 16 or 64 */
+  int32_t hidden_dim;   /* F; BF16: 128 with D = 64, else a multiple of 256 up to 4096 (k * hd);
+                           FP32: 32 or 128 */
   int32_t dtype;        /* SCAL3R_FP32 | SCAL3R_BF16 */
   int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 path) */
   int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
