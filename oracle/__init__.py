@@ -8,3 +8,4 @@ from .ttt_oracle import (  # noqa: F401
     unpack, pack, row_norm_count, apply, inner_gradient, row_targets, normalise,
     chain_forward, forward, chain_backward, backward,
 )
+from .gcm_oracle import gcm_forward, gcm_backward  # noqa: F401,E402
