@@ -49,7 +49,8 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
             "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
-            "scal3r_ttt_apply_update", "scal3r_ttt_apply")
+            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_gemm", "scal3r_gcm_workspace_size",
+            "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -128,6 +129,20 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_apply_update.restype = ctypes.c_int
     lib.scal3r_ttt_apply.argtypes = [vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp]
     lib.scal3r_ttt_apply.restype = ctypes.c_int
+    f32 = ctypes.c_float
+    lib.scal3r_ttt_gemm.argtypes = [vp, vp, i64, i32, vp, i64, i32, vp, i64, i32, i32, i64, i64, i64, vp]
+    lib.scal3r_ttt_gemm.restype = ctypes.c_int
+    lib.scal3r_gcm_workspace_size.argtypes = [vp, i64, ctypes.POINTER(sz)]
+    lib.scal3r_gcm_workspace_size.restype = ctypes.c_int
+    lib.scal3r_gcm_prep.argtypes = [vp, vp, vp, vp, vp, vp, f32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.scal3r_gcm_prep.restype = ctypes.c_int
+    lib.scal3r_gcm_gate.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+    lib.scal3r_gcm_gate.restype = ctypes.c_int
+    lib.scal3r_gcm_gate_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    lib.scal3r_gcm_gate_backward.restype = ctypes.c_int
+    lib.scal3r_gcm_prep_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, i64, vp, vp, vp, vp, vp,
+                                             sz, vp]
+    lib.scal3r_gcm_prep_backward.restype = ctypes.c_int
     _lib_handle = lib
     return lib
 
@@ -273,6 +288,40 @@ def scal3r_ttt_profile_read(handle: int, kind: int) -> dict:
 
 def scal3r_ttt_get_status(handle: int, stream=None) -> int:
     return load_library().scal3r_ttt_get_status(handle, stream)
+
+
+# -- the GEMM and the row steps of the GCM module around the layer (raw entry
+#    points: device pointers as ints, sizes as ints) --------------------------
+def scal3r_ttt_gemm(handle, a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K,
+                    stream) -> int:
+    return load_library().scal3r_ttt_gemm(handle, a, lda, int(a_kmajor), b, ldb, int(b_kmajor), c, ldc,
+                                          int(out_fp32), int(accumulate), M, N, K, stream)
+
+
+def scal3r_gcm_workspace_size(handle: int, T: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().scal3r_gcm_workspace_size(handle, T, ctypes.byref(n)), "scal3r_gcm_workspace_size")
+    return n.value
+
+
+def scal3r_gcm_prep(handle, qkv_raw, bqkv, x, w_eta, b_eta, base_lr, T, q, k, v, lr, qn, kn, sig, stream) -> int:
+    return load_library().scal3r_gcm_prep(handle, qkv_raw, bqkv, x, w_eta, b_eta, float(base_lr), T, q, k, v, lr,
+                                          qn, kn, sig, stream)
+
+
+def scal3r_gcm_gate(handle, y, x, alpha, T, out, stream) -> int:
+    return load_library().scal3r_gcm_gate(handle, y, x, alpha, T, out, stream)
+
+
+def scal3r_gcm_gate_backward(handle, d_out, y, alpha, T, dy, dx, dalpha, workspace, workspace_bytes, stream) -> int:
+    return load_library().scal3r_gcm_gate_backward(handle, d_out, y, alpha, T, dy, dx, dalpha, workspace,
+                                                   workspace_bytes, stream)
+
+
+def scal3r_gcm_prep_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, base_lr, T, dqkv, dlogit, dbqkv, db_eta,
+                             workspace, workspace_bytes, stream) -> int:
+    return load_library().scal3r_gcm_prep_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, float(base_lr), T,
+                                                   dqkv, dlogit, dbqkv, db_eta, workspace, workspace_bytes, stream)
 
 
 from .layer import TTT, TTTFunction  # noqa: E402,F401

@@ -37,7 +37,7 @@ def _sources() -> list[str]:
 
 def _deps() -> list[str]:
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(ROOT, "include", "scal3r_ttt.h"), os.path.abspath(__file__)]
+        glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

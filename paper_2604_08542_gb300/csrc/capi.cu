@@ -9,13 +9,32 @@
 // Backward, for j = n .. 0: sweep(j) (VJP pieces of chunk j's update and
 // chunk j-1's apply, at W_j), update(j) (normalisation VJP), then dw0.
 #include <cstdio>
+#include <cuda_bf16.h>
 #include <cstring>
 #include <functional>
 #include <mutex>
 
+#include "../../include/scal3r_gcm.h"
 #include "ttt_internal.h"
 
 namespace scal3r {
+cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
+                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, int* status,
+                           cudaStream_t st);
+size_t gcm_partial_bytes(int64_t T, int d, int H);
+bool gcm_heads_supported(int H);
+cudaError_t gcm_prep(const float* raw, const float* bqkv, const __nv_bfloat16* x, const float* w_eta,
+                     const float* b_eta, float base, int64_t T, int H, int D, __nv_bfloat16* q, __nv_bfloat16* k,
+                     __nv_bfloat16* v, float* lr, float* qn, float* kn, float* sig, cudaStream_t st);
+cudaError_t gcm_gate(const float* y, const __nv_bfloat16* x, const float* alpha, int64_t T, int d,
+                     __nv_bfloat16* out, cudaStream_t st);
+cudaError_t gcm_gate_backward(const __nv_bfloat16* dout, const float* y, const float* alpha, int64_t T, int d,
+                              __nv_bfloat16* dy, float* dx, float* dalpha, float* part, cudaStream_t st);
+cudaError_t gcm_prep_backward(const __nv_bfloat16* dq, const __nv_bfloat16* dk, const __nv_bfloat16* dv,
+                              const float* dlr, const __nv_bfloat16* q, const __nv_bfloat16* k, const float* qn,
+                              const float* kn, const float* sig, float base, int64_t T, int H, int D,
+                              __nv_bfloat16* dqkv, __nv_bfloat16* dlogit, float* dbqkv, float* db_eta, float* part,
+                              cudaStream_t st);
 bool fp32_shape_supported(int D, int F);
 bool bf16_shape_supported(int D, int F);
 bool update_shape_supported(int D, int F);
@@ -811,6 +830,92 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
       }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
   return SCAL3R_OK;
+}
+
+int scal3r_ttt_gemm(scal3r_ttt_handle* hd, const void* a, int64_t lda, int32_t a_kmajor, const void* b, int64_t ldb,
+                    int32_t b_kmajor, void* c, int64_t ldc, int32_t out_fp32, int32_t accumulate, int64_t M, int64_t N,
+                    int64_t K, void* stream) {
+  if (!hd || !a || !b || !c) return SCAL3R_ERR_INVALID_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || N % 256 != 0 || lda % 8 != 0 || ldb % 8 != 0 || ldc < N) return SCAL3R_ERR_UNSUPPORTED;
+  if ((a_kmajor ? lda < K : lda < M) || (b_kmajor ? ldb < K : ldb < N)) return SCAL3R_ERR_INVALID_ARG;
+  if (!aligned16(a) || !aligned16(b) || !aligned16(c) || (ldc * (out_fp32 ? 4 : 2)) % 16 != 0)
+    return SCAL3R_ERR_MISALIGNED;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 2.0 * M * N * K, 0, st, [&] {
+    return wide_gemm_bf16(a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K, hd->d_status,
+                          st);
+  });
+  if (e == cudaErrorInvalidValue) return SCAL3R_ERR_UNSUPPORTED;
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_workspace_size(scal3r_ttt_handle* hd, int64_t T, size_t* bytes) {
+  if (!hd || !bytes || T < 0) return SCAL3R_ERR_INVALID_ARG;
+  *bytes = gcm_partial_bytes(T, hd->shape.H * hd->shape.D, hd->shape.H);
+  return SCAL3R_OK;
+}
+
+int scal3r_gcm_prep(scal3r_ttt_handle* hd, const float* qkv_raw, const float* bqkv, const void* x,
+                    const float* w_eta, const float* b_eta, float base_lr, int64_t T, void* q, void* k, void* v,
+                    float* lr, float* qn, float* kn, float* sig, void* stream) {
+  if (!hd || T < 0 || !(base_lr > 0.f)) return SCAL3R_ERR_INVALID_ARG;
+  if (!gcm_heads_supported(hd->shape.H) || hd->cfg.dtype != SCAL3R_BF16) return SCAL3R_ERR_UNSUPPORTED;
+  if (T > 0 && (!qkv_raw || !bqkv || !x || !w_eta || !b_eta || !q || !k || !v || !lr || !qn || !kn || !sig))
+    return SCAL3R_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
+    return gcm_prep(qkv_raw, bqkv, static_cast<const __nv_bfloat16*>(x), w_eta, b_eta, base_lr, T, hd->shape.H,
+                    hd->shape.D, static_cast<__nv_bfloat16*>(q), static_cast<__nv_bfloat16*>(k),
+                    static_cast<__nv_bfloat16*>(v), lr, qn, kn, sig, st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_gate(scal3r_ttt_handle* hd, const float* y, const void* x, const float* alpha, int64_t T, void* out,
+                    void* stream) {
+  if (!hd || T < 0 || (T > 0 && (!y || !x || !alpha || !out))) return SCAL3R_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
+    return gcm_gate(y, static_cast<const __nv_bfloat16*>(x), alpha, T, hd->shape.H * hd->shape.D,
+                    static_cast<__nv_bfloat16*>(out), st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_gate_backward(scal3r_ttt_handle* hd, const void* d_out, const float* y, const float* alpha, int64_t T,
+                             void* dy, float* dx, float* dalpha, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  if (!hd || T < 0 || !dalpha || (T > 0 && (!d_out || !y || !alpha || !dy || !dx))) return SCAL3R_ERR_INVALID_ARG;
+  const int d = hd->shape.H * hd->shape.D;
+  if (!workspace || workspace_bytes < gcm_partial_bytes(T, d, hd->shape.H) || !aligned16(workspace))
+    return SCAL3R_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
+    return gcm_gate_backward(static_cast<const __nv_bfloat16*>(d_out), y, alpha, T, d, static_cast<__nv_bfloat16*>(dy),
+                             dx, dalpha, static_cast<float*>(workspace), st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_prep_backward(scal3r_ttt_handle* hd, const void* dq, const void* dk, const void* dv, const float* dlr,
+                             const void* q, const void* k, const float* qn, const float* kn, const float* sig,
+                             float base_lr, int64_t T, void* dqkv, void* dlogit, float* dbqkv, float* db_eta,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+  if (!hd || T < 0 || !dbqkv || !db_eta) return SCAL3R_ERR_INVALID_ARG;
+  if (T > 0 && (!dq || !dk || !dv || !dlr || !q || !k || !qn || !kn || !sig || !dqkv || !dlogit))
+    return SCAL3R_ERR_INVALID_ARG;
+  if (!gcm_heads_supported(hd->shape.H) || hd->cfg.dtype != SCAL3R_BF16) return SCAL3R_ERR_UNSUPPORTED;
+  const int H = hd->shape.H, D = hd->shape.D;
+  if (!workspace || workspace_bytes < gcm_partial_bytes(T, H * D, H) || !aligned16(workspace))
+    return SCAL3R_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto B = [](const void* p) { return static_cast<const __nv_bfloat16*>(p); };
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
+    return gcm_prep_backward(B(dq), B(dk), B(dv), dlr, B(q), B(k), qn, kn, sig, base_lr, T, H, D,
+                             static_cast<__nv_bfloat16*>(dqkv), static_cast<__nv_bfloat16*>(dlogit), dbqkv, db_eta,
+                             static_cast<float*>(workspace), st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
 }
 
 int scal3r_ttt_get_status(scal3r_ttt_handle* hd, void* stream) {

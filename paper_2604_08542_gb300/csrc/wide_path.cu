@@ -741,6 +741,31 @@ size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
   return layout_bytes(p, s, with_backward, nullptr, nullptr);
 }
 
+// C = A B^T on the GEMM kernel (bf16 operands, fp32 accumulation); see
+// scal3r_ttt_gemm in the header.  Returns cudaErrorInvalidValue on a shape the
+// kernel does not take.
+cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
+                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, int* status,
+                           cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || N % BN != 0 || M > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
+  GemmArgs g{};
+  const bool am = !a_kmajor, bm = !b_kmajor;
+  if (!(am ? make_map(&g.a[0], a, K, 1, M, lda, 64) : make_map(&g.a[0], a, M, 1, K, lda, 128)))
+    return cudaErrorInvalidValue;
+  if (!(bm ? make_map(&g.b[0], b, K, 1, N, ldb, 64) : make_map(&g.b[0], b, N, 1, K, ldb, 256)))
+    return cudaErrorInvalidValue;
+  g.M = (int)M;
+  g.N = (int)N;
+  g.K = (int)K;
+  g.a_mn = am;
+  g.b_mn = bm;
+  g.epi = out_fp32 ? (accumulate ? EPI_F32_ADD : EPI_F32) : EPI_BF16;
+  g.out[0] = c;
+  g.ld_out = ldc;
+  g.status = status;
+  return gemm(g, st);
+}
+
 cudaError_t prepare_wide() {
   return cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
 }

@@ -10,12 +10,12 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "scal3r_ttt.h")
+HEADERS = [os.path.join(ROOT, "include", n) for n in ("scal3r_ttt.h", "scal3r_gcm.h")]
 
 
 def _declared():
-    src = open(HEADER).read()
-    return sorted(set(re.findall(r"\b(scal3r_ttt_[a-z_]+)\s*\(", src)))
+    src = "".join(open(h).read() for h in HEADERS)
+    return sorted(set(re.findall(r"\b(scal3r_(?:ttt|gcm)_[a-z_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def test_header_declares_the_abi():
 
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\sT\s+(scal3r_ttt_\w+)", out))
+    exported = set(re.findall(r"\sT\s+(scal3r_(?:ttt|gcm)_\w+)", out))
     missing = [n for n in _declared() if n not in exported]
     assert not missing, missing
 

@@ -1,0 +1,65 @@
+"""The GCM module around the layer (Sec. 4.1, Eq. 5) through the C ABI: the
+projections on the tcgen05 GEMM, the row steps, and the layer, forward and
+backward, against the FP64 oracle on the same bf16-rounded tensors (GPU).
+
+Bar: normwise relative error <= 2e-2 (the BF16 bar) on out and on every
+gradient (x, Wqkv, bqkv, w_eta, b_eta, Wo, alpha, w0)."""
+import numpy as np
+import pytest
+
+import oracle
+import ttt_synth as syn
+from _util import rel_inf, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-2
+BASE = 0.1
+
+
+def _bf(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def _case(H, D, F, lengths, seed):
+    import torch
+    from paper_2604_08542_gb300.gcm import GCM
+    rng = np.random.default_rng(seed)
+    lay = syn.layout_from_lengths(lengths)
+    T, d = lay.num_tokens, H * D
+    host = {"x": _bf(rng.normal(size=(T, d))), "wqkv": _bf(rng.normal(size=(3 * d, d)) / np.sqrt(d)),
+            "wo": _bf(rng.normal(size=(d, d)) / np.sqrt(d)), "d_out": _bf(rng.normal(size=(T, d)))}
+    f32 = {"bqkv": 0.1 * rng.normal(size=3 * d), "w_eta": 0.3 / np.sqrt(d) * rng.normal(size=(H, d)),
+           "b_eta": -1.0 + 0.1 * rng.normal(size=H), "alpha": 0.5 * rng.normal(size=d),
+           "w0": 0.125 * rng.normal(size=(H, 3 * F * D))}
+    g = {n: t.cuda() for n, t in host.items()}
+    g.update({n: torch.from_numpy(a.astype(np.float32)).cuda() for n, a in f32.items()})
+    m = GCM(H, D, F, base_lr=BASE)
+    out, saved = m.forward(g["x"], g["wqkv"], g["bqkv"], g["w_eta"], g["b_eta"], g["wo"], g["alpha"], g["w0"],
+                           lay.chunk_offsets, lay.seq_chunk_ptr)
+    grads = m.backward(saved, g["d_out"])
+    torch.cuda.synchronize()
+    assert m.ttt.status() == 0
+    ref = {n: host[n].float().numpy().astype(np.float64) for n in host}
+    ref.update({n: f32[n].astype(np.float32).astype(np.float64) for n in f32})
+    args = (ref["x"], ref["wqkv"], ref["bqkv"], ref["w_eta"], ref["b_eta"], BASE, ref["wo"], ref["alpha"], ref["w0"],
+            lay)
+    fo = oracle.gcm_forward(*args, H, D, F, eps=1e-6)
+    bo = oracle.gcm_backward(*args, ref["d_out"], H, D, F, eps=1e-6)
+    errs = {"out": rel_inf(to_np(out), fo["out"])}
+    for n, t in zip(("dx", "dwqkv", "dbqkv", "dw_eta", "db_eta", "dwo", "dalpha", "dw0"), grads):
+        errs[n] = rel_inf(to_np(t), bo[n])
+    bad = {n: e for n, e in errs.items() if not e <= TOL}
+    assert not bad, f"above {TOL}: {bad}; all {errs}"
+    return errs
+
+
+def test_gcm_module_sixteen_heads_of_64():
+    """d = 1024 as 16 heads x 64 (the fused per-head layer), two sequences."""
+    _case(16, 64, 128, [[300, 129], [77]], seed=61)
+
+
+def test_gcm_module_wide_heads():
+    """d = 512 as 2 heads x 256 (the wide-weight layer), one sequence of two chunks."""
+    _case(2, 256, 512, [[300, 200]], seed=62)
