@@ -94,7 +94,10 @@ typedef struct scal3r_ttt_config {
   int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 path) */
   int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
   float   norm_eps;     /* clamp of the row norm; <= 0 selects 1e-6 */
-  int32_t reserved;     /* must be 0 */
+  int32_t ckpt_every;   /* chunks between stored checkpoints: 0 or 1 = every chunk.  n > 1 (the
+                           wide-weight path only) stores the weights after local chunks n-1,
+                           2n-1, ... of each sequence; the backward recomputes the weights in
+                           between with the forward's own gradient steps (bitwise the same) */
 } scal3r_ttt_config;
 
 typedef struct scal3r_ttt_handle scal3r_ttt_handle;
@@ -124,10 +127,17 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* handle,
                               const int32_t* seq_chunk_ptr, int32_t num_seqs,
                               int32_t with_backward, size_t* bytes);
 
+/* Checkpoint slots the forward writes for this layout: the number of chunks
+ * C, or with ckpt_every = n > 1 the sum over sequences of floor(chunks / n). */
+int scal3r_ttt_ckpt_slots(const scal3r_ttt_handle* handle, const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                          int64_t* slots);
+
 /* Forward pass (Eq. 8, Eq. 9, Eq. 4 chunk by chunk; see the file comment).
  *   o        [T,H,D] out, dtype of q.
  *   w_ckpt   [C,H,P] float32 out or NULL: the weights after each chunk's
- *            update (needed by the backward).
+ *            update (needed by the backward).  With ckpt_every = n > 1:
+ *            [scal3r_ttt_ckpt_slots, H, P], the weights after local chunks
+ *            n-1, 2n-1, ... of sequence 0, then of sequence 1, ...
  *   wnorm    [C,H,2F+D] float32 out or NULL: each row's L2 norm after the
  *            gradient step and before rescaling (needed by the backward).
  *   w_final  [S,H,P] float32 out or NULL: the weights after the last chunk

@@ -49,7 +49,7 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
             "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
-            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_gemm", "scal3r_gcm_workspace_size",
+            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_gcm_workspace_size",
             "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
 
 
@@ -57,7 +57,7 @@ class scal3r_ttt_config(ctypes.Structure):
     _fields_ = [("num_heads", ctypes.c_int32), ("head_dim", ctypes.c_int32),
                 ("hidden_dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("loss", ctypes.c_int32), ("weight_norm", ctypes.c_int32),
-                ("norm_eps", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("norm_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int32)]
 
 
 class scal3r_ttt_schedule(ctypes.Structure):
@@ -130,6 +130,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_apply.argtypes = [vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp]
     lib.scal3r_ttt_apply.restype = ctypes.c_int
     f32 = ctypes.c_float
+    lib.scal3r_ttt_ckpt_slots.argtypes = [vp, vp, i32, ctypes.POINTER(i64)]
+    lib.scal3r_ttt_ckpt_slots.restype = ctypes.c_int
     lib.scal3r_ttt_gemm.argtypes = [vp, vp, i64, i32, vp, i64, i32, vp, i64, i32, i32, i64, i64, i64, vp]
     lib.scal3r_ttt_gemm.restype = ctypes.c_int
     lib.scal3r_gcm_workspace_size.argtypes = [vp, i64, ctypes.POINTER(sz)]
@@ -288,6 +290,14 @@ def scal3r_ttt_profile_read(handle: int, kind: int) -> dict:
 
 def scal3r_ttt_get_status(handle: int, stream=None) -> int:
     return load_library().scal3r_ttt_get_status(handle, stream)
+
+
+def scal3r_ttt_ckpt_slots(handle: int, seq_chunk_ptr) -> int:
+    ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
+    n = ctypes.c_int64()
+    _check(load_library().scal3r_ttt_ckpt_slots(handle, ptr.ctypes.data, len(ptr) - 1, ctypes.byref(n)),
+           "scal3r_ttt_ckpt_slots")
+    return n.value
 
 
 # -- the GEMM and the row steps of the GCM module around the layer (raw entry

@@ -43,12 +43,13 @@ cudaError_t prepare_fp32();
 cudaError_t prepare_bf16_forward();
 cudaError_t prepare_bf16_backward();
 bool wide_shape_supported(int D, int F);
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every);
+int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n);
 cudaError_t prepare_wide();
-cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
+cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
                          cudaStream_t st);
-cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, void* ws,
+cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                           const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
                           cudaStream_t st);
 cudaError_t prepare_kernels() {
@@ -341,7 +342,7 @@ const char* scal3r_ttt_error_string(int status) {
 int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (!cfg || !out) return SCAL3R_ERR_INVALID_ARG;
   *out = nullptr;
-  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->reserved != 0)
+  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every < 0)
     return SCAL3R_ERR_INVALID_ARG;
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
@@ -352,6 +353,7 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (cfg->dtype == SCAL3R_BF16 &&
       ((!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) && !wide) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
+  if (cfg->ckpt_every > 1 && !wide) return SCAL3R_ERR_UNSUPPORTED;   // sparse checkpoints: the wide path
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
   int major = 0, minor = 0, sms = 0;
@@ -400,7 +402,7 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   if (hd->wide) {
-    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0);
+    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every);
     return SCAL3R_OK;
   }
   *bytes = workspace_bytes(hd->plan, hd->shape, with_backward != 0);
@@ -422,7 +424,8 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(o)) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false) : workspace_bytes(pl, sh, false);
+  const size_t need =
+      hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -443,7 +446,8 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
       auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
         return timed(hd, kind == 0 ? SCAL3R_KERNEL_FWD_SWEEP : SCAL3R_KERNEL_FWD_UPDATE, flops, bytes, cs, fn);
       };
-      return wide_forward(pl, sh, prm, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+      return wide_forward(pl, sh, prm, hd->cfg.ckpt_every, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK
+                                                                                                  : SCAL3R_ERR_CUDA;
     };
     if (hd->graph_on && !hd->prof_on) {
       uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 7);
@@ -493,7 +497,8 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         (const void*)w0, (const void*)dw0})
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
   if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, true) : workspace_bytes(pl, sh, true);
+  const size_t need =
+      hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every) : workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
   Params prm;
@@ -519,7 +524,8 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
       auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
         return timed(hd, kind == 0 ? SCAL3R_KERNEL_BWD_SWEEP : SCAL3R_KERNEL_BWD_UPDATE, flops, bytes, cs, fn);
       };
-      return wide_backward(pl, sh, prm, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+      return wide_backward(pl, sh, prm, hd->cfg.ckpt_every, workspace, launch, cs) == cudaSuccess ? SCAL3R_OK
+                                                                                                   : SCAL3R_ERR_CUDA;
     };
     if (hd->graph_on && !hd->prof_on) {
       uint64_t key = fnv1a(&prm, sizeof(prm), hd->plan_gen * 0x9E3779B97F4A7C15ull + 9);
@@ -829,6 +835,20 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
                                             : launch_fp32_sweep(prm, pl.d_items + s1.item0, s1.nitems, 1, st);
       }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_ckpt_slots(const scal3r_ttt_handle* hd, const int32_t* seq_chunk_ptr, int32_t num_seqs,
+                          int64_t* slots) {
+  if (!hd || !seq_chunk_ptr || num_seqs < 0 || !slots) return SCAL3R_ERR_INVALID_ARG;
+  const int n = hd->cfg.ckpt_every > 1 ? hd->cfg.ckpt_every : 1;
+  int64_t total = 0;
+  for (int s = 0; s < num_seqs; ++s) {
+    const int c = seq_chunk_ptr[s + 1] - seq_chunk_ptr[s];
+    if (c < 0) return SCAL3R_ERR_INVALID_ARG;
+    total += c / n;
+  }
+  *slots = total;
   return SCAL3R_OK;
 }
 

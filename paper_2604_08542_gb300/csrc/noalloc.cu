@@ -65,7 +65,7 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
                                           float* wnorm, float* w_final, void* stream) {
   // configuration (the same checks as scal3r_ttt_init)
   if (!cfg) return SCAL3R_ERR_INVALID_ARG;
-  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->reserved != 0)
+  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every > 1 || cfg->ckpt_every < 0)
     return SCAL3R_ERR_INVALID_ARG;
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;

@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_prep_kernel(const float* __r
     ss += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
   }
   ss = block_sum(ss, red);
-  if (threadIdx.x == 0) rho[blockIdx.x] = (norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
+  if (rho && threadIdx.x == 0) rho[blockIdx.x] = (norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(ss);
 }
 
 // W <- W - G, then each row rescaled to its target (Eq. 8 and the row
@@ -652,9 +652,11 @@ struct WideBufs {
   float* rho;
   float* drho;
   float* part;    // backward: d eta partials [mmax x F/64]
+  float* rgr;     // backward with sparse checkpoints: the recomputed chunk gradient
+  float* seg;     // backward with sparse checkpoints: W_j of one segment, ckpt_every - 1 blocks of P
 };
 
-size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, WideBufs* w, void* ws) {
+size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, WideBufs* w, void* ws) {
   const size_t P = (size_t)s.P();
   const int64_t mmax = max_chunk(p);
   const size_t act = al256((size_t)mmax * s.F * 2);
@@ -676,6 +678,10 @@ size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, WideBufs* w, void* 
   if (bwd) {
     x.drho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
     x.part = reinterpret_cast<float*>(take((size_t)mmax * (s.F / 64) * 4));
+    if (ckpt_every > 1) {   // recomputation between stored checkpoints
+      x.rgr = reinterpret_cast<float*>(take(P * 4));
+      x.seg = reinterpret_cast<float*>(take(P * 4 * (size_t)(ckpt_every - 1)));
+    }
   }
   if (w) *w = x;
   return o;
@@ -737,8 +743,19 @@ cudaError_t run_gemm(const Ctx& c, GemmArgs& a, double flops) {
 
 }  // namespace
 
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
-  return layout_bytes(p, s, with_backward, nullptr, nullptr);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every) {
+  return layout_bytes(p, s, with_backward, ckpt_every, nullptr, nullptr);
+}
+
+// Checkpoint slot of W_j (the weights after local chunk j-1) of sequence s, or
+// -1 if it is not stored: every chunk with ckpt_every <= 1, else the weights
+// after local chunks n-1, 2n-1, ... (slots of the sequences one after another).
+int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n) {
+  if (n <= 1) return p.seq_chunk_ptr[s] + j - 1;
+  if (j < 1 || j % n != 0) return -1;
+  int64_t base = 0;
+  for (int t = 0; t < s; ++t) base += (p.seq_chunk_ptr[t + 1] - p.seq_chunk_ptr[t]) / n;
+  return base + j / n - 1;
 }
 
 // C = A B^T on the GEMM kernel (bf16 operands, fp32 accumulation); see
@@ -770,17 +787,74 @@ cudaError_t prepare_wide() {
   return cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
 }
 
+namespace {
+
+// One chunk's gradient step (Eq. 8, 9) on chain (s, h): W (master wm, bf16 wb)
+// becomes normalise(W - G) in place; optionally the checkpoint, the
+// pre-normalisation row norms and w_final are written.  act: four [M x F]
+// bf16 buffers; gr: the gradient buffer (P floats).
+cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
+                       __nv_bfloat16* const* act, float* ck, float* wn, float* wf) {
+  const Shape& sh = cx.sh;
+  const Params& prm = cx.prm;
+  const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
+  const int64_t T = cx.pl.T;
+  const __nv_bfloat16* w1 = wb;
+  const __nv_bfloat16* w3 = wb + (size_t)F * D;
+  const __nv_bfloat16* w2 = wb + 2 * (size_t)F * D;
+  __nv_bfloat16 *pb = act[0], *g1 = act[1], *g3 = act[2], *ut = act[3];
+  const int64_t t0 = cx.pl.chunk_offsets[c], t1 = cx.pl.chunk_offsets[c + 1];
+  const int M = (int)(t1 - t0);
+  const double mfd = 2.0 * M * (double)F * D;
+  {   // P = V W2
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
+    a.M = M; a.N = F; a.K = D; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_BF16; a.out[0] = pb; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // Z1, Z3 = K [W1; W3]^T with the gradient epilogue -> g1, g3, u~
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+             mat_map(&a.b[1], w3, F, D, 128));
+    a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_KEY; a.out[0] = g1; a.out[1] = g3; a.out[2] = ut; a.ld_out = F;
+    a.in0 = pb; a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+  }
+  for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
+    a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
+    a.epi = EPI_F32; a.out[0] = gr + (size_t)j * F * D; a.ld_out = D;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // G2 = V^T u~
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], ut, M, F, 64));
+    a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  return cx.launch(1, 0, 0, [&] {   // update and normalise
+    wide_update_kernel<<<R, ROW_THREADS, 0, cx.st>>>(wm, gr, wb, rho, ck, wn, wf, D, F, prm.norm, prm.eps);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace
+
 // The forward of every chain, chunk after chunk (see the file comment).
 // `launch` wraps each launch (profiling); kind 0 = GEMM, 1 = update / prep.
-cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const LaunchFn& launch,
-                         cudaStream_t st) {
+cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
+                         const LaunchFn& launch, cudaStream_t st) {
   const Ctx cx{pl, sh, prm, launch, st};
   const int H = sh.H, D = sh.D, F = sh.F;
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
   WideBufs w;
-  layout_bytes(pl, sh, false, &w, ws);
-  __nv_bfloat16 *pb = w.act[0], *g1 = w.act[1], *g3 = w.act[2], *ut = w.act[3];
+  layout_bytes(pl, sh, false, ckpt_every, &w, ws);
+  __nv_bfloat16* pb = w.act[0];
   const int64_t T = pl.T;
   const __nv_bfloat16* w1 = w.wb;
   const __nv_bfloat16* w3 = w.wb + (size_t)F * D;
@@ -797,46 +871,11 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, voi
         const int64_t t0 = pl.chunk_offsets[c], t1 = pl.chunk_offsets[c + 1];
         const int M = (int)(t1 - t0);
         const double mfd = 2.0 * M * (double)F * D;
-        {   // P = V W2
-          GemmArgs a{};
-          WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
-          a.M = M; a.N = F; a.K = D; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_BF16; a.out[0] = pb; a.ld_out = F;
-          WIDE_TRY(run_gemm(cx, a, mfd));
-        }
-        {   // Z1, Z3 = K [W1; W3]^T with the gradient epilogue -> g1, g3, u~
-          GemmArgs a{};
-          WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
-                   mat_map(&a.b[1], w3, F, D, 128));
-          a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_KEY; a.out[0] = g1; a.out[1] = g3; a.out[2] = ut; a.ld_out = F;
-          a.in0 = pb; a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
-          WIDE_TRY(run_gemm(cx, a, 2 * mfd));
-        }
-        for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
-          GemmArgs a{};
-          WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
-          a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
-          a.epi = EPI_F32; a.out[0] = w.gr + (size_t)j * F * D; a.ld_out = D;
-          WIDE_TRY(run_gemm(cx, a, mfd));
-        }
-        {   // G2 = V^T u~
-          GemmArgs a{};
-          WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], ut, M, F, 64));
-          a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
-          a.epi = EPI_F32; a.out[0] = w.gr + 2 * (size_t)F * D; a.ld_out = F;
-          WIDE_TRY(run_gemm(cx, a, mfd));
-        }
-        {   // update and normalise
-          float* ck = prm.w_ckpt ? prm.w_ckpt + ((size_t)c * H + h) * P : nullptr;
-          float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
-          float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
-          WIDE_TRY(launch(1, 0, 0, [&] {
-            wide_update_kernel<<<R, ROW_THREADS, 0, st>>>(w.wm, w.gr, w.wb, w.rho, ck, wn, wf, D, F, prm.norm,
-                                                         prm.eps);
-            return cudaGetLastError();
-          }));
-        }
+        const int64_t slot = wide_ckpt_slot(pl, s, c - c0 + 1, ckpt_every);
+        float* ck = (prm.w_ckpt && slot >= 0) ? prm.w_ckpt + ((size_t)slot * H + h) * P : nullptr;
+        float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
+        float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
+        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, ck, wn, wf));
         {   // apply: h = silu(Q W1^T) o (Q W3^T)
           GemmArgs a{};
           WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
@@ -868,14 +907,15 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, voi
 //                             dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3], dv = [-eta dp, -eta u] [W2^T; -R2^T];
 //                             lam += R + [dz1^T K, dz3^T K, V^T (-eta dp)]
 //   normalisation VJP of update j-1 (R for the next step), or dW0 at j = 0.
-cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const LaunchFn& launch,
-                          cudaStream_t st) {
+cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
+                          const LaunchFn& launch, cudaStream_t st) {
   const Ctx cx{pl, sh, prm, launch, st};
   const int H = sh.H, D = sh.D, F = sh.F;
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
   WideBufs w;
-  layout_bytes(pl, sh, true, &w, ws);
+  layout_bytes(pl, sh, true, ckpt_every, &w, ws);
+  const int nck = ckpt_every > 1 ? ckpt_every : 1;
   const int64_t T = pl.T;
   const size_t FD = (size_t)F * D;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
@@ -893,8 +933,24 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, vo
       }));
       const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
       const int n = c1 - c0;
-      for (int j = n; j >= 0; --j) {
-        const float* wj = (j == 0) ? w0 : prm.w_ckpt_in + ((size_t)(c0 + j - 1) * H + h) * P;
+      // segments [j0, j1] from the last: W_j0 is stored (or w0); with sparse
+      // checkpoints W_j0+1 .. W_j1 are recomputed from it first, by the
+      // forward's own gradient steps (the same kernels on the same inputs,
+      // so bitwise the weights the forward had)
+      for (int j0 = (n / nck) * nck; j0 >= 0; j0 -= nck) {
+      const int j1 = std::min(j0 + nck - 1, n);
+      const float* wbase = (j0 == 0) ? w0 : prm.w_ckpt_in + ((size_t)wide_ckpt_slot(pl, s, j0, nck) * H + h) * P;
+      if (j1 > j0) {
+        WIDE_TRY(launch(1, 0, 0, [&] {
+          wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wbase, w.wm, w.wb, nullptr, D, F, prm.norm);
+          return cudaGetLastError();
+        }));
+        for (int jj = j0; jj < j1; ++jj)
+          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.seg + (size_t)(jj - j0) * P,
+                              nullptr, nullptr));
+      }
+      for (int j = j1; j >= j0; --j) {
+        const float* wj = (j == j0) ? wbase : w.seg + (size_t)(j - j0 - 1) * P;
         const bool key = j < n;
         WIDE_TRY(launch(1, 0, 0, [&] {
           wide_bstep_setup_kernel<<<4 * num_sms(), 256, 0, st>>>(wj, key ? w.gr : nullptr, w.wb, w.nrb, w.wm, P);
@@ -1021,6 +1077,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, vo
                                                          prm.eps);
           return cudaGetLastError();
         }));
+      }
       }
     }
   }

@@ -21,7 +21,7 @@ from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3
                scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_schedule,
                scal3r_ttt_get_status, scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_schedule,
                scal3r_ttt_set_graph_mode, scal3r_ttt_set_schedule, scal3r_ttt_workspace_size,
-               scal3r_ttt_partial_grad, scal3r_ttt_apply_update, scal3r_ttt_apply)
+               scal3r_ttt_partial_grad, scal3r_ttt_apply_update, scal3r_ttt_apply, scal3r_ttt_ckpt_slots)
 
 NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
 LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
@@ -36,14 +36,14 @@ class TTT:
 
     def __init__(self, num_heads: int, head_dim: int = 64, hidden_dim: int = 128,
                  dtype: torch.dtype = torch.bfloat16, loss: str = "dot", weight_norm: str = "row_w0",
-                 norm_eps: float = 1e-6):
+                 norm_eps: float = 1e-6, ckpt_every: int = 1):
         if dtype not in (torch.bfloat16, torch.float32):
             raise ValueError("dtype must be torch.bfloat16 or torch.float32")
         self.H, self.D, self.F = num_heads, head_dim, hidden_dim
         self.dtype = dtype
         self.cfg = scal3r_ttt_config(num_heads, head_dim, hidden_dim,
                                      SCAL3R_BF16 if dtype == torch.bfloat16 else SCAL3R_FP32,
-                                     LOSSES[loss], NORMS[weight_norm], float(norm_eps), 0)
+                                     LOSSES[loss], NORMS[weight_norm], float(norm_eps), int(ckpt_every))
         self.handle = scal3r_ttt_init(self.cfg)
         self._ws = None
 
@@ -103,7 +103,8 @@ class TTT:
         stride = self._w0_stride(w0, S)
         dev = q.device
         o = torch.empty_like(q) if o is None else o
-        w_ckpt = torch.empty((C, self.H, self.P), dtype=torch.float32, device=dev) if save_for_backward else None
+        slots = C if self.cfg.ckpt_every <= 1 else scal3r_ttt_ckpt_slots(self.handle, ptr)
+        w_ckpt = torch.empty((slots, self.H, self.P), dtype=torch.float32, device=dev) if save_for_backward else None
         wnorm = torch.empty((C, self.H, self.R), dtype=torch.float32, device=dev) if save_for_backward else None
         w_final = torch.empty((S, self.H, self.P), dtype=torch.float32, device=dev) if want_final else None
         ws = self.workspace(off, ptr, False, dev) if workspace is None else workspace

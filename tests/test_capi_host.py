@@ -67,13 +67,14 @@ def test_bad_config_rejected_before_device_query(libpath):
            ttt.scal3r_ttt_config(16, 64, 128, 7, 0, 0, 1e-6, 0),       # bad dtype
            ttt.scal3r_ttt_config(16, 64, 128, 1, 5, 0, 1e-6, 0),       # bad loss
            ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 9, 1e-6, 0),       # bad norm
-           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 3)]       # reserved != 0
+           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, -1)]      # negative checkpoint interval
     for c in bad:
         with pytest.raises(ttt.Scal3rError) as e:
             ttt.scal3r_ttt_init(c)
         assert e.value.status == ttt.SCAL3R_ERR_INVALID_ARG
-    for c in (ttt.scal3r_ttt_config(16, 32, 128, 1, 0, 0, 1e-6, 0),     # BF16 needs D=64, F=128
-              ttt.scal3r_ttt_config(16, 48, 100, 0, 0, 0, 1e-6, 0)):    # FP32 shape not built
+    for c in (ttt.scal3r_ttt_config(16, 32, 128, 1, 0, 0, 1e-6, 0),     # BF16 needs D=64, F=128 or wide
+              ttt.scal3r_ttt_config(16, 48, 100, 0, 0, 0, 1e-6, 0),     # FP32 shape not built
+              ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 3)):    # sparse checkpoints: wide path only
         with pytest.raises(ttt.Scal3rError) as e:
             ttt.scal3r_ttt_init(c)
         assert e.value.status == ttt.SCAL3R_ERR_UNSUPPORTED

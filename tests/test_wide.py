@@ -140,3 +140,35 @@ def test_wide_backward_graph_replay_is_bitwise_equal():
         _, _, _, b = _fwd_bwd(1, 256, 512, [[300, 200]], seed=54, layer=layer, graph=True)
         for u, w in zip(a, b):
             assert torch.equal(u, w)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_wide_sparse_checkpoints_are_bitwise_the_dense_ones(n):
+    """ckpt_every = n stores the weights after local chunks n-1, 2n-1, ... of
+    each sequence; the backward recomputes the rest with the forward's own
+    steps, so every output equals the every-chunk run bit for bit."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F = 1, 256, 512
+    lengths = [[200, 256, 70, 130, 90], [140, 60]]
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=55, dtype="bf16", with_grad_out=True)
+    g = upload(x, torch.bfloat16)
+    out = {}
+    for every in (1, n):
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, ckpt_every=every)
+        o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets,
+                                      lay.seq_chunk_ptr, want_final=True)
+        grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        out[every] = (o, ck, wn, wf, grads)
+    o1, ck1, wn1, wf1, g1 = out[1]
+    on, ckn, wnn, wfn, gn = out[n]
+    stored = [c0 + j - 1 for s, (c0, c1) in enumerate(zip(lay.seq_chunk_ptr[:-1], lay.seq_chunk_ptr[1:]))
+              for j in range(n, c1 - c0 + 1, n)]
+    assert ckn.shape[0] == len(stored)
+    assert torch.equal(ckn, ck1[stored])
+    for a, b in [(o1, on), (wn1, wnn), (wf1, wfn), *zip(g1, gn)]:
+        assert torch.equal(a, b)
