@@ -26,8 +26,8 @@
  * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
  * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
  * step as a large tcgen05 GEMM, forward and backward.  The wide path takes
- * the dot loss; the GCS split entry points and the autotuner are for the
- * head_dim-64 path (SCAL3R_ERR_UNSUPPORTED otherwise).
+ * the dot loss; the autotuner is for the head_dim-64 path
+ * (SCAL3R_ERR_UNSUPPORTED otherwise).
  *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.

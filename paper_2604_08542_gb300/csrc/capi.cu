@@ -45,6 +45,13 @@ cudaError_t prepare_bf16_backward();
 bool wide_shape_supported(int D, int F);
 size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every);
 int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n);
+using WideLaunch = std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>;
+cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm, float* grad, void* ws,
+                              const WideLaunch& launch, cudaStream_t st);
+cudaError_t wide_apply_update(const Shape& sh, const Params& prm, int S, const float* w, int64_t w_stride,
+                              const float* grad, float* w_out, float* wnorm, const WideLaunch& launch, cudaStream_t st);
+cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const WideLaunch& launch,
+                       cudaStream_t st);
 cudaError_t prepare_wide();
 cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
@@ -573,7 +580,7 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         void* dv, float* dlr, float* dw0, int32_t with_backward, void* stream,
                         scal3r_ttt_schedule* best, float* best_ms) {
   if (!hd || !best || !best_ms) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
+  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the schedule knobs are the head_dim-64 path's
   if (with_backward && (!d_o || !dq || !dk || !dv || !dlr || !dw0 || !w_ckpt || !wnorm))
     return SCAL3R_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -724,7 +731,6 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
                             int64_t w_seq_stride, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S,
                             float* grad, void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -736,8 +742,23 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
   if (!aligned16(k) || !aligned16(v) || !aligned16(lr) || !aligned16(w) || !aligned16(grad) ||
       (w_seq_stride & 3) != 0)
     return SCAL3R_ERR_MISALIGNED;
-  const size_t need = workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
+  if (hd->wide) {
+    Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    fill_common(hd, prm);
+    prm.k = k;
+    prm.v = v;
+    prm.lr = lr;
+    prm.w0 = w;
+    prm.w0_seq_stride = w_seq_stride;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
+      return timed(hd, kind == 0 ? SCAL3R_KERNEL_FWD_SWEEP : SCAL3R_KERNEL_OTHER, flops, bytes, st, fn);
+    };
+    return wide_partial_grad(pl, sh, prm, grad, workspace, launch, st) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+  }
 
   Params prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -771,7 +792,6 @@ int scal3r_ttt_apply_update(scal3r_ttt_handle* hd, const float* w, int64_t w_seq
                             const float* w0, int64_t w0_seq_stride, int32_t num_seqs, float* w_out, float* wnorm,
                             void* stream) {
   if (!hd || num_seqs < 0) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   const Shape& sh = hd->shape;
   if (num_seqs == 0) return SCAL3R_OK;
   if (!w || !grad || !w0 || !w_out || w_seq_stride < 0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
@@ -787,6 +807,14 @@ int scal3r_ttt_apply_update(scal3r_ttt_handle* hd, const float* w, int64_t w_seq
   prm.w0 = w0;
   prm.w0_seq_stride = w0_seq_stride;
   cudaStream_t st = (cudaStream_t)stream;
+  if (hd->wide) {
+    auto launch = [&](int, double flops, double bytes, const std::function<cudaError_t()>& fn) {
+      return timed(hd, SCAL3R_KERNEL_FWD_UPDATE, flops, bytes, st, fn);
+    };
+    return wide_apply_update(sh, prm, num_seqs, w, w_seq_stride, grad, w_out, wnorm, launch, st) == cudaSuccess
+               ? SCAL3R_OK
+               : SCAL3R_ERR_CUDA;
+  }
   if (timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
         return launch_gcs_update(prm, num_seqs * sh.H, w, w_seq_stride, grad, w_out, wnorm, st);
       }) != cudaSuccess)
@@ -798,7 +826,6 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
                      int32_t C, const int32_t* ptr, int32_t S, void* o, void* workspace, size_t workspace_bytes_,
                      void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the wide-weight path has a forward only
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -808,9 +835,23 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
   if (!w || w_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w_seq_stride != 0 && w_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
   if (!aligned16(q) || !aligned16(o) || !aligned16(w) || (w_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (pl.T == 0 || pl.steps.size() < 2) return SCAL3R_OK;   // no token to apply
+  if (hd->wide) {
+    Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    fill_common(hd, prm);
+    prm.q = q;
+    prm.o = o;
+    prm.w0 = w;
+    prm.w0_seq_stride = w_seq_stride;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto launch = [&](int kind, double flops, double bytes, const std::function<cudaError_t()>& fn) {
+      return timed(hd, kind == 0 ? SCAL3R_KERNEL_FWD_SWEEP : SCAL3R_KERNEL_OTHER, flops, bytes, st, fn);
+    };
+    return wide_apply(pl, sh, prm, workspace, launch, st) == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+  }
 
   Params prm;
   std::memset(&prm, 0, sizeof(prm));

@@ -789,12 +789,9 @@ cudaError_t prepare_wide() {
 
 namespace {
 
-// One chunk's gradient step (Eq. 8, 9) on chain (s, h): W (master wm, bf16 wb)
-// becomes normalise(W - G) in place; optionally the checkpoint, the
-// pre-normalisation row norms and w_final are written.  act: four [M x F]
-// bf16 buffers; gr: the gradient buffer (P floats).
-cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
-                       __nv_bfloat16* const* act, float* ck, float* wn, float* wf) {
+// The gradient G of chunk c (Eq. 8, 9) at the bf16 weights wb of head h,
+// into gr (P floats, packed like the weights).  act: four [M x F] bf16 buffers.
+cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act) {
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
@@ -836,6 +833,18 @@ cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb
     a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
+  return cudaSuccess;
+}
+
+// One chunk's gradient step on chain (s, h): W (master wm, bf16 wb) becomes
+// normalise(W - G) in place; optionally the checkpoint, the pre-normalisation
+// row norms and w_final are written.  gr: the gradient buffer (P floats).
+cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
+                       __nv_bfloat16* const* act, float* ck, float* wn, float* wf) {
+  WIDE_TRY(key_grad(cx, h, c, wb, gr, act));
+  const Shape& sh = cx.sh;
+  const Params& prm = cx.prm;
+  const int D = sh.D, F = sh.F, R = sh.R();
   return cx.launch(1, 0, 0, [&] {   // update and normalise
     wide_update_kernel<<<R, ROW_THREADS, 0, cx.st>>>(wm, gr, wb, rho, ck, wn, wf, D, F, prm.norm, prm.eps);
     return cudaGetLastError();
@@ -895,6 +904,135 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
       }
     }
   }
+  return cudaSuccess;
+}
+
+// ---- Global Context Synchronisation (Sec. 4.2, Eq. 10) on the wide path: a
+// chunk step in local parts; every sequence holds one chunk.
+
+namespace {
+
+// w_out = normalise(w - g) per row, targets from w0 (one block per row).
+__global__ void __launch_bounds__(ROW_THREADS) wide_gcs_update_kernel(const float* __restrict__ w,
+                                                                      const float* __restrict__ g,
+                                                                      const float* __restrict__ w0,
+                                                                      float* __restrict__ w_out, float* wnorm, int D,
+                                                                      int F, int norm, float eps) {
+  __shared__ float red[ROW_THREADS / 32 + 1];
+  size_t off;
+  int len;
+  row_geometry(blockIdx.x, D, F, off, len);
+  float ss = 0.f, st = 0.f;
+  for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+    const float4 a = *reinterpret_cast<const float4*>(w + off + i);
+    const float4 b = *reinterpret_cast<const float4*>(g + off + i);
+    const float4 t = *reinterpret_cast<const float4*>(w0 + off + i);
+    const float4 x = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    ss += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+    st += t.x * t.x + t.y * t.y + t.z * t.z + t.w * t.w;
+  }
+  ss = block_sum(ss, red);
+  st = block_sum(st, red);
+  const float n = sqrtf(ss);
+  const float rho = (norm == SCAL3R_NORM_UNIT) ? 1.f : sqrtf(st);
+  const float scale = (norm == SCAL3R_NORM_NONE) ? 1.f : rho / fmaxf(n, eps);
+  if (threadIdx.x == 0 && wnorm) wnorm[blockIdx.x] = n;
+  for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
+    const float4 a = *reinterpret_cast<const float4*>(w + off + i);
+    const float4 b = *reinterpret_cast<const float4*>(g + off + i);
+    *reinterpret_cast<float4*>(w_out + off + i) =
+        make_float4((a.x - b.x) * scale, (a.y - b.y) * scale, (a.z - b.z) * scale, (a.w - b.w) * scale);
+  }
+}
+
+}  // namespace
+
+// grad[s, h] = G of sequence s's chunk at w[s, h] (0 without a chunk).
+cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm, float* grad, void* ws,
+                              const LaunchFn& launch, cudaStream_t st) {
+  const Ctx cx{pl, sh, prm, launch, st};
+  const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
+  const size_t P = (size_t)sh.P();
+  WideBufs w;
+  layout_bytes(pl, sh, false, 1, &w, ws);
+  for (int s = 0; s < pl.S; ++s) {
+    for (int h = 0; h < H; ++h) {
+      float* gout = grad + ((size_t)s * H + h) * P;
+      const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
+      if (c1 == c0) {
+        WIDE_TRY(cudaMemsetAsync(gout, 0, P * sizeof(float), st));
+        continue;
+      }
+      const float* wsrc = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
+      WIDE_TRY(launch(1, 0, 0, [&] {
+        wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wsrc, w.wm, w.wb, nullptr, D, F, prm.norm);
+        return cudaGetLastError();
+      }));
+      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act));
+    }
+  }
+  return cudaSuccess;
+}
+
+// w_out[s, h] = normalise(w[s, h] - grad[s, h]) with the targets of w0.
+cudaError_t wide_apply_update(const Shape& sh, const Params& prm, int S, const float* w, int64_t w_stride,
+                              const float* grad, float* w_out, float* wnorm, const LaunchFn& launch, cudaStream_t st) {
+  const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
+  const size_t P = (size_t)sh.P();
+  for (int s = 0; s < S; ++s)
+    for (int h = 0; h < H; ++h) {
+      const size_t chain = (size_t)s * H + h;
+      WIDE_TRY(launch(1, 0, 0, [&] {
+        wide_gcs_update_kernel<<<R, ROW_THREADS, 0, st>>>(w + (size_t)s * w_stride + (size_t)h * P, grad + chain * P,
+                                                          prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P,
+                                                          w_out + chain * P, wnorm ? wnorm + chain * R : nullptr, D, F,
+                                                          prm.norm, prm.eps);
+        return cudaGetLastError();
+      }));
+    }
+  return cudaSuccess;
+}
+
+// o = f_w(q) for every sequence's chunk, w[s, h] given in (prm.w0, stride).
+cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const LaunchFn& launch,
+                       cudaStream_t st) {
+  const Ctx cx{pl, sh, prm, launch, st};
+  const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
+  const size_t P = (size_t)sh.P();
+  WideBufs w;
+  layout_bytes(pl, sh, false, 1, &w, ws);
+  const int64_t T = pl.T;
+  const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + (size_t)F * D, *w2 = w.wb + 2 * (size_t)F * D;
+  __nv_bfloat16* pb = w.act[0];
+  for (int s = 0; s < pl.S; ++s)
+    for (int h = 0; h < H; ++h) {
+      const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
+      if (c1 == c0) continue;
+      const float* wsrc = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
+      WIDE_TRY(launch(1, 0, 0, [&] {
+        wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wsrc, w.wm, w.wb, nullptr, D, F, prm.norm);
+        return cudaGetLastError();
+      }));
+      const int64_t t0 = pl.chunk_offsets[c0];
+      const int M = (int)(pl.chunk_offsets[c0 + 1] - t0);
+      const double mfd = 2.0 * M * (double)F * D;
+      {
+        GemmArgs a{};
+        WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+                 mat_map(&a.b[1], w3, F, D, 128));
+        a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+        a.epi = EPI_APPLY; a.out[0] = pb; a.ld_out = F;
+        WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+      }
+      {
+        GemmArgs a{};
+        WIDE_MAP(mat_map(&a.a[0], pb, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
+        a.M = M; a.N = D; a.K = F;
+        a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.o) + ((size_t)t0 * H + h) * D;
+        a.ld_out = (int64_t)H * D;
+        WIDE_TRY(run_gemm(cx, a, mfd));
+      }
+    }
   return cudaSuccess;
 }
 

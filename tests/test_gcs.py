@@ -241,3 +241,37 @@ def test_gpu_gcs_rejects_two_chunks_per_sequence():
     w = torch.zeros((1, 3 * 128 * 64), device="cuda")
     with pytest.raises(ttt.Scal3rError):
         layer.partial_grad(k, k, lr, w, [0, 10, 20], [0, 2])
+
+
+@pytest.mark.gpu
+def test_gpu_gcs_wide_equals_forward():
+    """The split chunk step on the wide-weight path (2 heads x 256, hidden 512):
+    chunks 600/257/130 tokens cut at 300/128/64."""
+    import torch
+    o, ck, o_ref, ck_ref, ref = _gpu_gcs(torch.bfloat16, 2, 256, 512, [600, 257, 130], [300, 128, 64], seed=7)
+    assert rel_inf(o, o_ref) <= 5e-3 and rel_inf(ck, ck_ref) <= 1e-4
+    assert rel_inf(o, ref["o"]) <= 2e-2 and rel_inf(ck, ref["w_ckpt"]) <= 2e-2
+
+
+@pytest.mark.gpu
+def test_gpu_partial_grad_wide_sums_to_the_chunk_gradient():
+    """Eq. 10 at the paper's AMU shape (one head, hd 1024, hidden 4096): two
+    token shards' gradients at the same weights add up to the oracle's."""
+    import torch
+
+    import paper_2604_08542_gb300 as ttt
+    H, D, F, n, c = 1, 1024, 4096, 300, 129
+    x = syn.make_inputs(n, H, D, F, seed=10, dtype="bf16")
+    g = upload(x, torch.bfloat16)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    tot = 0
+    for a, b in ((0, c), (c, n)):
+        lo = syn.layout_from_lengths([[b - a]])
+        tot = tot + layer.partial_grad(g["k"][a:b].clone(), g["v"][a:b].clone(),
+                                       g["lr"][a:b].clone(), g["w0"], lo.chunk_offsets, lo.seq_chunk_ptr)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    ref = oracle.pack(oracle.inner_gradient(oracle.unpack(x["w0"][0].astype(np.float64), D, F),
+                                            x["k"][:, 0].astype(np.float64), x["v"][:, 0].astype(np.float64),
+                                            x["lr"][:, 0].astype(np.float64)))
+    assert rel_inf(to_np(tot)[0, 0], ref) <= 2e-2
