@@ -43,7 +43,7 @@ cudaError_t prepare_fp32();
 cudaError_t prepare_bf16_forward();
 cudaError_t prepare_bf16_backward();
 bool wide_shape_supported(int D, int F);
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss);
 int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n);
 using WideLaunch = std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>;
 cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm, float* grad, void* ws,
@@ -357,8 +357,9 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
     return SCAL3R_ERR_UNSUPPORTED;
   const bool wide = cfg->dtype == SCAL3R_BF16 && wide_shape_supported(cfg->head_dim, cfg->hidden_dim);
-  if (cfg->dtype == SCAL3R_BF16 &&
-      ((!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) && !wide) || cfg->loss != SCAL3R_LOSS_DOT))
+  // BF16: the D = 64, F = 128 path (dot loss) or the wide-weight path (both losses)
+  if (cfg->dtype == SCAL3R_BF16 && !wide &&
+      (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
   if (cfg->ckpt_every > 1 && !wide) return SCAL3R_ERR_UNSUPPORTED;   // sparse checkpoints: the wide path
   int dev = 0;
@@ -409,7 +410,7 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   if (hd->wide) {
-    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every);
+    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every, hd->cfg.loss);
     return SCAL3R_OK;
   }
   *bytes = workspace_bytes(hd->plan, hd->shape, with_backward != 0);
@@ -432,7 +433,7 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
   const size_t need =
-      hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every) : workspace_bytes(pl, sh, false);
+      hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every, hd->cfg.loss) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -505,7 +506,7 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
   if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   const size_t need =
-      hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every) : workspace_bytes(pl, sh, true);
+      hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every, hd->cfg.loss) : workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
   Params prm;
@@ -742,7 +743,7 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
   if (!aligned16(k) || !aligned16(v) || !aligned16(lr) || !aligned16(w) || !aligned16(grad) ||
       (w_seq_stride & 3) != 0)
     return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1) : workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -835,7 +836,7 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
   if (!w || w_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w_seq_stride != 0 && w_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
   if (!aligned16(q) || !aligned16(o) || !aligned16(w) || (w_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1) : workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (pl.T == 0 || pl.steps.size() < 2) return SCAL3R_OK;   // no token to apply
   if (hd->wide) {

@@ -49,6 +49,13 @@ enum Epi : int {
   EPI_BAPPLY = 5,   // apply VJP gate: zq1 | zq3 of 128 hidden, in0 = W2^T d_o -> dzq1, dzq3, uq
   EPI_BKEY = 6,     // update VJP gate: z1 | z3 | dg1 | dg3 of 64 hidden, in0 = W2^T v, in1 = -R2^T v
                     //   -> dz1, dz3, g1, g3, -eta dp, -eta u and a partial of d eta
+  // the squared-error loss (e = eta (W2 u - v)):
+  EPI_MSE_E = 7,    // acc = W2 u;  in0 = v  -> e = eta (acc - v), and (acc - v) if out[1]
+  EPI_ADD_BF16 = 8, // out[0] = acc + in0 (bf16)
+  EPI_MSE_DE = 9,   // acc = dL/de;  in0 = (W2 u - v) -> eta dE, -eta dE (out[1], its own stride),
+                    //   partial of d eta = sum (W2 u - v) . dE
+  EPI_BKEY_MSE1 = 10,  // update VJP gate, pass 1: in0 = p -> dp, g1, g3
+  EPI_BKEY_MSE2 = 11,  // update VJP gate, pass 2: in0 = p, in1 = du -> dz1, dz3
 };
 
 struct GemmArgs {
@@ -69,6 +76,9 @@ struct GemmArgs {
   float* part;             // EPI_BKEY: d eta partial of row m, tile column tn at part[m * ld_part + tn]
   int64_t ld_part;
   int* status;
+  int mse;                 // EPI_KEY: the squared-error loss (in0 is p itself; no u~ output)
+  int64_t ld_in;           // row stride of in0 / in1 when not ld_out (0: ld_out)
+  int64_t ld_out1;         // row stride of out[1] when not ld_out (0: ld_out)
 };
 
 __device__ __forceinline__ float silu_d(float z, float& sg) {
@@ -135,6 +145,9 @@ __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* 
 // the MMA warp alternates between two 256-column accumulators; epilogue group
 // g (four warps, all 128 TMEM lanes) drains the tiles of accumulator g, so a
 // tile's epilogue overlaps the next tile's MMAs.
+// XSET: the squared-error loss's epilogues, in their own instantiation so that
+// the common ones keep their register allocation.
+template <bool XSET>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
@@ -252,7 +265,89 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       const int m0 = tm * BM, n0 = tn * BN;
       const int m = m0 + (int)row;
       const bool valid = m < g.M;
-      if (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD) {
+      if (XSET) {
+        if (g.epi == EPI_MSE_E || g.epi == EPI_ADD_BF16 || g.epi == EPI_MSE_DE) {
+        const int64_t ldi = g.ld_in ? g.ld_in : g.ld_out;
+        const int64_t ld1 = g.ld_out1 ? g.ld_out1 : g.ld_out;
+        const float eta = (g.epi != EPI_ADD_BF16 && valid) ? g.eta[(size_t)m * g.eta_stride] : 0.f;
+        float deta = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+          uint4 i0 = make_uint4(0, 0, 0, 0), i1 = i0;
+          const uint4* ip = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
+          if (valid) {
+            i0 = __ldg(ip);
+            i1 = __ldg(ip + 1);
+          }
+          float acc[16];
+          tmem_ld16(accb + c, acc);
+          if (!valid) continue;
+          float x[16], o0[16], o1[16];
+          unpack16(i0, i1, x);
+          const size_t off0 = (size_t)m * g.ld_out + n0 + c, off1 = (size_t)m * ld1 + n0 + c;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            if (g.epi == EPI_MSE_E) {            // x = v
+              o1[e] = acc[e] - x[e];
+              o0[e] = eta * o1[e];
+            } else if (g.epi == EPI_ADD_BF16) {
+              o0[e] = acc[e] + x[e];
+            } else {                             // EPI_MSE_DE: x = W2 u - v, acc = dE
+              o0[e] = eta * acc[e];
+              o1[e] = -eta * acc[e];
+              deta = fmaf(x[e], acc[e], deta);
+            }
+          }
+          st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off0, o0);
+          if (g.epi != EPI_ADD_BF16 && g.out[1]) st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off1, o1);
+        }
+        if (g.epi == EPI_MSE_DE && valid) g.part[(size_t)m * g.ld_part + tn] = deta;
+        } else {
+        // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
+        // hidden units f0 .. f0 + 63 (dg = -R k); squared-error loss, p = W2^T e
+        const int f0 = tn * (BN / 4);
+        const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
+        const uint4* up = reinterpret_cast<const uint4*>((g.in1 ? g.in1 : g.in0) + (size_t)m * g.ld_out + f0);
+        const bool second = g.epi == EPI_BKEY_MSE2;
+#pragma unroll 1
+        for (int c = 0; c < 64; c += 8) {
+          uint4 pw = make_uint4(0, 0, 0, 0), uw = pw;
+          if (valid) {
+            pw = __ldg(pp + c / 8);
+            if (second) uw = __ldg(up + c / 8);
+          }
+          float zz[4][8];
+          tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
+          if (!valid) continue;
+          float pv[8], du[8];
+          unpack8(pw, pv);
+          unpack8(uw, du);
+          float o[3][8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float sg;
+            const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
+            const float a = silu_d(x1, sg);
+            const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
+            if (!second) {
+              o[0][e] = d3 * a + d1 * x3 * sp;                   // dp
+              o[1][e] = pv[e] * x3 * sp;                         // g1
+              o[2][e] = pv[e] * a;                               // g3
+            } else {
+              const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);  // silu''(z1)
+              const float da = d3 * pv[e] + du[e] * x3;
+              o[1][e] = d1 * pv[e] * sp + du[e] * a;             // dz3
+              o[0][e] = d1 * pv[e] * x3 * spp + da * sp;         // dz1
+            }
+          }
+          const size_t off = (size_t)m * g.ld_out + f0 + c;
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            if (q < (second ? 2 : 3))
+              *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
+        }
+        }
+      } else if (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD) {
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           float v0[16], v1[16];
@@ -366,10 +461,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
               const float a = silu_d(x1, sg);
               const float sp = fmaf(a, 1.f - sg, sg);     // silu'(z1)
               if (g.epi == EPI_KEY) {
-                const float pv = -eta * r[e];             // p = W2^T e, e = -eta v
+                const float pv = g.mse ? r[e] : -eta * r[e];   // p = W2^T e (dot loss: e = -eta v)
                 o0[e] = pv * x3 * sp;                     // g1
                 o1[e] = pv * a;                           // g3
-                o2[e] = -eta * a * x3;                    // u~ = -eta u
+                o2[e] = -eta * a * x3;                    // u~ = -eta u (dot loss)
               } else {                                    // EPI_BAPPLY, r = W2^T d_o
                 o0[e] = r[e] * x3 * sp;                   // dzq1
                 o1[e] = r[e] * a;                         // dzq3
@@ -378,7 +473,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             }
             st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, o0);
             st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off, o1);
-            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[2]) + off, o2);
+            if (g.out[2]) st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[2]) + off, o2);
           }
         }
       }
@@ -654,9 +749,14 @@ struct WideBufs {
   float* part;    // backward: d eta partials [mmax x F/64]
   float* rgr;     // backward with sparse checkpoints: the recomputed chunk gradient
   float* seg;     // backward with sparse checkpoints: W_j of one segment, ckpt_every - 1 blocks of P
+  __nv_bfloat16* ex[3];   // squared-error loss: [mmax x D] bf16 buffers (forward: E; backward: E, Y - V, dY)
 };
 
-size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, WideBufs* w, void* ws) {
+// d eta partials per token row: one per 64 hidden units (dot loss, from the
+// update-VJP gate) or per 256 output columns (squared-error loss, from dE).
+int deta_parts(const Shape& s, bool mse) { return mse ? s.D / BN : s.F / 64; }
+
+size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, bool mse, WideBufs* w, void* ws) {
   const size_t P = (size_t)s.P();
   const int64_t mmax = max_chunk(p);
   const size_t act = al256((size_t)mmax * s.F * 2);
@@ -677,12 +777,14 @@ size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, Wid
   x.rho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
   if (bwd) {
     x.drho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
-    x.part = reinterpret_cast<float*>(take((size_t)mmax * (s.F / 64) * 4));
+    x.part = reinterpret_cast<float*>(take((size_t)mmax * deta_parts(s, mse) * 4));
     if (ckpt_every > 1) {   // recomputation between stored checkpoints
       x.rgr = reinterpret_cast<float*>(take(P * 4));
       x.seg = reinterpret_cast<float*>(take(P * 4 * (size_t)(ckpt_every - 1)));
     }
   }
+  if (mse)
+    for (int i = 0; i < (bwd ? 3 : 1); ++i) x.ex[i] = reinterpret_cast<__nv_bfloat16*>(take((size_t)mmax * s.D * 2));
   if (w) *w = x;
   return o;
 }
@@ -704,7 +806,10 @@ cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   if (a.nseg > 1 && (a.kseg % BK != 0 || a.kseg * a.nseg != a.K || a.nbn != 1)) return cudaErrorInvalidValue;
   const int tiles = ((a.M + BM - 1) / BM) * (a.N / BN);
   const int grid = std::min(tiles, num_sms());
-  wide_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
+  if (a.epi >= EPI_MSE_E)
+    wide_gemm_kernel<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
+  else
+    wide_gemm_kernel<false><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -743,8 +848,8 @@ cudaError_t run_gemm(const Ctx& c, GemmArgs& a, double flops) {
 
 }  // namespace
 
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every) {
-  return layout_bytes(p, s, with_backward, ckpt_every, nullptr, nullptr);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss) {
+  return layout_bytes(p, s, with_backward, ckpt_every, loss == SCAL3R_LOSS_MSE, nullptr, nullptr);
 }
 
 // Checkpoint slot of W_j (the weights after local chunk j-1) of sequence s, or
@@ -784,14 +889,88 @@ cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void*
 }
 
 cudaError_t prepare_wide() {
-  return cudaFuncSetAttribute(wide_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  cudaError_t e =
+      cudaFuncSetAttribute(wide_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(wide_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+  return e;
 }
 
 namespace {
 
+// The squared-error loss's gradient (Eq. 8 with L = 1/2 |f_W(k) - v|^2): with
+// u = silu(z1) o z3 and e = eta (W2 u - v), p = W2^T e:
+//   U = gate(K), E = eta (U W2^T - V), P = E W2, gate(K) with p -> g1, g3;
+//   G1 = g1^T K, G3 = g3^T K, G2 = E^T U.
+cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
+                         __nv_bfloat16* eb) {
+  const Shape& sh = cx.sh;
+  const Params& prm = cx.prm;
+  const int H = sh.H, D = sh.D, F = sh.F;
+  const int64_t T = cx.pl.T;
+  const __nv_bfloat16* w1 = wb;
+  const __nv_bfloat16* w3 = wb + (size_t)F * D;
+  const __nv_bfloat16* w2 = wb + 2 * (size_t)F * D;
+  __nv_bfloat16 *pb = act[0], *g1 = act[1], *g3 = act[2], *ub = act[3];
+  const int64_t t0 = cx.pl.chunk_offsets[c], t1 = cx.pl.chunk_offsets[c + 1];
+  const int M = (int)(t1 - t0);
+  const double mfd = 2.0 * M * (double)F * D;
+  {   // U = silu(K W1^T) o (K W3^T)
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+             mat_map(&a.b[1], w3, F, D, 128));
+    a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_APPLY; a.out[0] = ub; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+  }
+  {   // E = eta (U W2^T - V)
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
+    a.M = M; a.N = D; a.K = F;
+    a.epi = EPI_MSE_E; a.out[0] = eb; a.ld_out = D;
+    a.in0 = reinterpret_cast<const __nv_bfloat16*>(prm.v) + ((size_t)t0 * H + h) * D; a.ld_in = (int64_t)H * D;
+    a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // P = E W2
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], eb, M, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
+    a.M = M; a.N = F; a.K = D; a.b_mn = 1;
+    a.epi = EPI_BF16; a.out[0] = pb; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // Z1, Z3 = K [W1; W3]^T with the gradient epilogue on p -> g1, g3
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+             mat_map(&a.b[1], w3, F, D, 128));
+    a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_KEY; a.mse = 1; a.out[0] = g1; a.out[1] = g3; a.ld_out = F; a.in0 = pb;
+    a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+  }
+  for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
+    a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
+    a.epi = EPI_F32; a.out[0] = gr + (size_t)j * F * D; a.ld_out = D;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // G2 = E^T U
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], eb, M, D, 64) && mat_map(&a.b[0], ub, M, F, 64));
+    a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1;
+    a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  return cudaSuccess;
+}
+
 // The gradient G of chunk c (Eq. 8, 9) at the bf16 weights wb of head h,
-// into gr (P floats, packed like the weights).  act: four [M x F] bf16 buffers.
-cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act) {
+// into gr (P floats, packed like the weights).  act: four [M x F] bf16 buffers;
+// eb: an [M x D] bf16 buffer (squared-error loss only).
+cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
+                     __nv_bfloat16* eb) {
+  if (cx.prm.loss == SCAL3R_LOSS_MSE) return key_grad_mse(cx, h, c, wb, gr, act, eb);
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
@@ -840,8 +1019,8 @@ cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float
 // normalise(W - G) in place; optionally the checkpoint, the pre-normalisation
 // row norms and w_final are written.  gr: the gradient buffer (P floats).
 cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
-                       __nv_bfloat16* const* act, float* ck, float* wn, float* wf) {
-  WIDE_TRY(key_grad(cx, h, c, wb, gr, act));
+                       __nv_bfloat16* const* act, __nv_bfloat16* eb, float* ck, float* wn, float* wf) {
+  WIDE_TRY(key_grad(cx, h, c, wb, gr, act, eb));
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int D = sh.D, F = sh.F, R = sh.R();
@@ -862,7 +1041,7 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
   WideBufs w;
-  layout_bytes(pl, sh, false, ckpt_every, &w, ws);
+  layout_bytes(pl, sh, false, ckpt_every, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
   __nv_bfloat16* pb = w.act[0];
   const int64_t T = pl.T;
   const __nv_bfloat16* w1 = w.wb;
@@ -884,7 +1063,7 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
         float* ck = (prm.w_ckpt && slot >= 0) ? prm.w_ckpt + ((size_t)slot * H + h) * P : nullptr;
         float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
         float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
-        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, ck, wn, wf));
+        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, w.ex[0], ck, wn, wf));
         {   // apply: h = silu(Q W1^T) o (Q W3^T)
           GemmArgs a{};
           WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
@@ -954,7 +1133,7 @@ cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
   const size_t P = (size_t)sh.P();
   WideBufs w;
-  layout_bytes(pl, sh, false, 1, &w, ws);
+  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
   for (int s = 0; s < pl.S; ++s) {
     for (int h = 0; h < H; ++h) {
       float* gout = grad + ((size_t)s * H + h) * P;
@@ -968,7 +1147,7 @@ cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm
         wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wsrc, w.wm, w.wb, nullptr, D, F, prm.norm);
         return cudaGetLastError();
       }));
-      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act));
+      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act, w.ex[0]));
     }
   }
   return cudaSuccess;
@@ -1000,7 +1179,7 @@ cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void*
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
   const size_t P = (size_t)sh.P();
   WideBufs w;
-  layout_bytes(pl, sh, false, 1, &w, ws);
+  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
   const int64_t T = pl.T;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + (size_t)F * D, *w2 = w.wb + 2 * (size_t)F * D;
   __nv_bfloat16* pb = w.act[0];
@@ -1036,6 +1215,121 @@ cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void*
   return cudaSuccess;
 }
 
+namespace {
+
+// Update VJP of one chunk under the squared-error loss (Eq. 8 with
+// L = 1/2 |f_W(k) - v|^2), at the bf16 weights w.wb with -R in w.nrb:
+//   U = gate(K), [E, Y - V] = eta (U W2^T - V), P = E W2, ND = E (-R2);
+//   gate [W1; W3; -R1; -R3] with p -> dp, g1, g3   (dg = -R k);
+//   dE = [U dP] [-R2 W2]^T -> dY = eta dE, dv = -eta dE, d eta = (Y - V) . dE;
+//   dU = ND + dY W2;  gate again with p, du -> dz1, dz3;
+//   dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3];
+//   lam1 += dz1^T K, lam3 += dz3^T K, lam2 += E^T dP + dY^T U.
+// The d eta partials (D / 256 per row) are left in w.part.
+cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBufs& w, float* lam1, float* lam3,
+                           float* lam2) {
+  const Shape& sh = cx.sh;
+  const Params& prm = cx.prm;
+  const int H = sh.H, D = sh.D, F = sh.F;
+  const int64_t T = cx.pl.T;
+  const size_t FD = (size_t)F * D;
+  const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
+  const __nv_bfloat16 *r1 = w.nrb, *r3 = w.nrb + FD, *r2 = w.nrb + 2 * FD;   // -R
+  __nv_bfloat16 *ub = w.act[0], *pb = w.act[1], *nd = w.act[2], *dp = w.act[3], *g1 = w.act[4], *g3 = w.act[5],
+                *du = w.act[6], *dz1 = w.act[7], *dz3 = w.act[2];   // dz3 overwrites nd once du is formed
+  __nv_bfloat16 *eb = w.ex[0], *ymv = w.ex[1], *dy = w.ex[2];
+  const double mfd = 2.0 * M * (double)F * D;
+  const float* eta = prm.lr + (size_t)t0 * H + h;
+  {   // U = silu(K W1^T) o (K W3^T)
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
+             mat_map(&a.b[1], w3, F, D, 128));
+    a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
+    a.epi = EPI_APPLY; a.out[0] = ub; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+  }
+  {   // E = eta (U W2^T - V), Y - V
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
+    a.M = M; a.N = D; a.K = F;
+    a.epi = EPI_MSE_E; a.out[0] = eb; a.out[1] = ymv; a.ld_out = D;
+    a.in0 = reinterpret_cast<const __nv_bfloat16*>(prm.v) + ((size_t)t0 * H + h) * D; a.ld_in = (int64_t)H * D;
+    a.eta = eta; a.eta_stride = H;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  for (int i = 0; i < 2; ++i) {   // P = E W2, ND = E (-R2)
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], eb, M, D, 128) && mat_map(&a.b[0], i ? r2 : w2, D, F, 64));
+    a.M = M; a.N = F; a.K = D; a.b_mn = 1;
+    a.epi = EPI_BF16; a.out[0] = i ? nd : pb; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      {   // dE = -U R2^T + dP W2^T -> dY, dv, d eta partials
+        GemmArgs a{};
+        WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.a[1], dp, M, F, 128) &&
+                 mat_map(&a.b[0], r2, D, F, 256) && mat_map(&a.b[1], w2, D, F, 256));
+        a.M = M; a.N = D; a.K = 2 * F; a.kseg = F; a.nseg = 2;
+        a.epi = EPI_MSE_DE; a.out[0] = dy; a.ld_out = D; a.in0 = ymv;
+        a.out[1] = reinterpret_cast<__nv_bfloat16*>(prm.dv) + ((size_t)t0 * H + h) * D; a.ld_out1 = (int64_t)H * D;
+        a.eta = eta; a.eta_stride = H;
+        a.part = w.part; a.ld_part = deta_parts(sh, true);
+        WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+      }
+      {   // dU = ND + dY W2
+        GemmArgs a{};
+        WIDE_MAP(mat_map(&a.a[0], dy, M, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
+        a.M = M; a.N = F; a.K = D; a.b_mn = 1;
+        a.epi = EPI_ADD_BF16; a.out[0] = du; a.ld_out = F; a.in0 = nd;
+        WIDE_TRY(run_gemm(cx, a, mfd));
+      }
+    }
+    // gate [W1; W3; -R1; -R3] on k: pass 0 -> dp, g1, g3; pass 1 -> dz1, dz3
+    GemmArgs a{};
+    WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 64) &&
+             mat_map(&a.b[1], w3, F, D, 64) && mat_map(&a.b[2], r1, F, D, 64) && mat_map(&a.b[3], r3, F, D, 64));
+    a.M = M; a.N = 4 * F; a.K = D; a.nbn = 4; a.ha = h; a.ya = (int)t0;
+    a.ld_out = F; a.in0 = pb;
+    if (pass == 0) {
+      a.epi = EPI_BKEY_MSE1; a.out[0] = dp; a.out[1] = g1; a.out[2] = g3;
+    } else {
+      a.epi = EPI_BKEY_MSE2; a.out[0] = dz1; a.out[1] = dz3; a.in1 = du;
+    }
+    WIDE_TRY(run_gemm(cx, a, 4 * mfd));
+  }
+  {   // dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3]
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], dz1, M, F, 128) && mat_map(&a.a[1], dz3, M, F, 128) &&
+             mat_map(&a.a[2], g1, M, F, 128) && mat_map(&a.a[3], g3, M, F, 128) &&
+             mat_map(&a.b[0], w1, F, D, 64) && mat_map(&a.b[1], w3, F, D, 64) &&
+             mat_map(&a.b[2], r1, F, D, 64) && mat_map(&a.b[3], r3, F, D, 64));
+    a.M = M; a.N = D; a.K = 4 * F; a.kseg = F; a.nseg = 4; a.b_mn = 1;
+    a.epi = EPI_BF16; a.out[0] = reinterpret_cast<__nv_bfloat16*>(prm.dk) + ((size_t)t0 * H + h) * D;
+    a.ld_out = (int64_t)H * D;
+    WIDE_TRY(run_gemm(cx, a, 4 * mfd));
+  }
+  for (int i = 0; i < 2; ++i) {   // lam1 += dz1^T K, lam3 += dz3^T K
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
+    a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
+    a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
+    WIDE_TRY(run_gemm(cx, a, mfd));
+  }
+  {   // lam2 += E^T dP + dY^T U: one reduction over both token segments
+    const int kseg = (M + BK - 1) / BK * BK;
+    GemmArgs a{};
+    WIDE_MAP(mat_map(&a.a[0], eb, M, D, 64) && mat_map(&a.a[1], dy, M, D, 64) && mat_map(&a.b[0], dp, M, F, 64) &&
+             mat_map(&a.b[1], ub, M, F, 64));
+    a.M = D; a.N = F; a.K = 2 * kseg; a.kseg = kseg; a.nseg = 2; a.a_mn = 1; a.b_mn = 1;
+    a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
+    WIDE_TRY(run_gemm(cx, a, 2 * mfd));
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 // The backward of every chain: for j = n .. 0 (n = the sequence's chunks), at
 // W_j (W0, or the checkpoint after update j-1):
 //   apply VJP of chunk j-1:   du = W2^T d_o, gate -> dzq1, dzq3, uq;
@@ -1052,14 +1346,15 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
   WideBufs w;
-  layout_bytes(pl, sh, true, ckpt_every, &w, ws);
+  const bool mse = prm.loss == SCAL3R_LOSS_MSE;
+  layout_bytes(pl, sh, true, ckpt_every, mse, &w, ws);
   const int nck = ckpt_every > 1 ? ckpt_every : 1;
   const int64_t T = pl.T;
   const size_t FD = (size_t)F * D;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
   const __nv_bfloat16 *r1 = w.nrb, *r3 = w.nrb + FD, *r2 = w.nrb + 2 * FD;   // -R
   float *lam1 = w.wm, *lam3 = w.wm + FD, *lam2 = w.wm + 2 * FD;
-  const int nparts = F / 64;
+  const int nparts = deta_parts(sh, mse);
   for (int s = 0; s < pl.S; ++s) {
     for (int h = 0; h < H; ++h) {
       const float* w0 = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
@@ -1084,8 +1379,8 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
           return cudaGetLastError();
         }));
         for (int jj = j0; jj < j1; ++jj)
-          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.seg + (size_t)(jj - j0) * P,
-                              nullptr, nullptr));
+          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.ex[0],
+                              w.seg + (size_t)(jj - j0) * P, nullptr, nullptr));
       }
       for (int j = j1; j >= j0; --j) {
         const float* wj = (j == j0) ? wbase : w.seg + (size_t)(j - j0 - 1) * P;
@@ -1139,7 +1434,17 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             WIDE_TRY(run_gemm(cx, a, mfd));
           }
         }
-        if (key) {   // update VJP of chunk j
+        if (key && mse) {   // update VJP of chunk j, squared-error loss
+          const int c = c0 + j;
+          const int64_t t0 = pl.chunk_offsets[c];
+          const int M = (int)(pl.chunk_offsets[c + 1] - t0);
+          WIDE_TRY(update_vjp_mse(cx, h, t0, M, w, lam1, lam3, lam2));
+          WIDE_TRY(launch(1, 0, 0, [&] {
+            wide_deta_kernel<<<(M + 127) / 128, 128, 0, st>>>(w.part, nparts, nparts, prm.dlr + (size_t)t0 * H + h,
+                                                               H, M);
+            return cudaGetLastError();
+          }));
+        } else if (key) {   // update VJP of chunk j
           const int c = c0 + j;
           const int64_t t0 = pl.chunk_offsets[c];
           const int M = (int)(pl.chunk_offsets[c + 1] - t0);

@@ -172,3 +172,57 @@ def test_wide_sparse_checkpoints_are_bitwise_the_dense_ones(n):
     assert torch.equal(ckn, ck1[stored])
     for a, b in [(o1, on), (wn1, wnn), (wf1, wfn), *zip(g1, gn)]:
         assert torch.equal(a, b)
+
+
+# ---- the squared-error loss (L = 1/2 |f_W(k) - v|^2 in Eq. 8) ----
+
+@pytest.mark.parametrize("H,D,F,lengths", [(2, 256, 512, [[300, 129], [77]]),
+                                           (1, 2048, 256, [[260, 130]])])
+def test_wide_mse_forward_and_backward_match_oracle(H, D, F, lengths):
+    """Forward outputs and every gradient under the squared-error loss; the
+    second shape has more output-column tiles (D / 256) than hidden-unit
+    groups of 64, the d eta partials' other sizing."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    lay = syn.layout_from_lengths(lengths)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, loss="mse")
+    _, _, x, out = _run(H, D, F, lengths, seed=61, layer=layer)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, loss="mse", eps=1e-6)
+    _check(out, ref)
+    _, _, x, grads = _fwd_bwd(H, D, F, lengths, seed=62, layer=layer)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, loss="mse", eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_mse_paper_shape_matches_oracle():
+    """The paper's AMU (hd 1024, hidden 4096) under the squared-error loss."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F, lengths = 1, 1024, 4096, [[384, 200]]
+    lay = syn.layout_from_lengths(lengths)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, loss="mse")
+    _, _, x, grads = _fwd_bwd(H, D, F, lengths, seed=63, layer=layer)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, loss="mse", eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_mse_sparse_checkpoints_are_bitwise_the_dense_ones():
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F = 1, 256, 512
+    lengths = [[200, 256, 70, 130]]
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=64, dtype="bf16", with_grad_out=True)
+    g = upload(x, torch.bfloat16)
+    res = []
+    for every in (1, 2):
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, loss="mse", ckpt_every=every)
+        o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets,
+                                     lay.seq_chunk_ptr)
+        grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        res.append((o, wn, *grads))
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
