@@ -24,7 +24,10 @@ What it computes (paper sections and equations of arXiv 2604.08542):
   after each update to the L2 norm it had in the initial weights
   ("row_w0"; "unit" rescales to 1, "none" skips it) with the clamp
   max(||row||, eps); the MSE loss is 1/2 ||f_W(k) - v||^2; the learning rate
-  is one scalar per (token, head) shared by W1, W3, W2.
+  is one scalar per (token, head) shared by W1, W3, W2, or, as an option,
+  one per matrix: lr [T, H, 3] with lr[..., 0], [..., 1], [..., 2] the rates
+  of W1, W3, W2, and G_j = d/dW_j sum_i eta_{j,i} L_i (Eq. 8 with the rate
+  of the matrix being updated).
 * ``model="linear"`` replaces f_W by the linear map f_W(x) = W x (W in
   R^{D x D}); with the dot loss and no normalisation the layer is then
   chunk-causal linear attention, a closed form the tests check.
@@ -33,7 +36,7 @@ The backward pass is written out by reverse-mode differentiation of the
 forward recurrence (the paper gives none); the tests pin it to central
 finite differences.
 
-Arrays: q, k, v, d_o [T, H, D]; lr [T, H]; w0 [H, P] (shared by all
+Arrays: q, k, v, d_o [T, H, D]; lr [T, H] (or [T, H, 3], one rate per matrix); w0 [H, P] (shared by all
 sequences) or [S, H, P] (per sequence), P = 3*F*D packed as W1, W3, W2
 row-major (linear model: P = D*D).  All arithmetic is float64.
 """
@@ -115,8 +118,11 @@ def inner_gradient(W: list, K: np.ndarray, V: np.ndarray, eta: np.ndarray,
     """G_j = d/dW_j sum_i eta_i L(f_W(k_i), v_i) at fixed W (Eq. 8, 9).
 
     Rows of K, V [M, D] are the chunk's keys and values, eta [M] their
-    learning rates.  Returned in the order of W.
+    learning rates (or [M, 3]: one rate per matrix W1, W3, W2).  Returned in
+    the order of W.
     """
+    if eta.ndim == 2:
+        return _inner_gradient_per_matrix(W, K, V, eta, loss, model)
     eta = eta[:, None]
     if model == "linear":
         (Wl,) = W
@@ -136,6 +142,24 @@ def inner_gradient(W: list, K: np.ndarray, V: np.ndarray, eta: np.ndarray,
     G3 = P * A
     G1 = P * Z3 * silu_prime(Z1)
     return [G1.T @ K, G3.T @ K, E.T @ U]                    # dW1, dW3, dW2
+
+
+def _inner_gradient_per_matrix(W, K, V, eta, loss, model):
+    """G_j = d/dW_j sum_i eta_{j,i} L_i: each matrix's gradient with its own
+    per-token rate, all at the same W."""
+    if model != "swiglu":
+        raise ValueError("per-matrix rates need the SwiGLU network's three matrices")
+    W1, W3, W2 = W
+    Z1 = K @ W1.T
+    Z3 = K @ W3.T
+    A = silu(Z1)
+    U = A * Z3
+    Eh = -V if loss == "dot" else U @ W2.T - V              # dL_i/df, without a rate
+    Ph = Eh @ W2                                            # W2^T e_i
+    e1, e3, e2 = eta[:, 0:1], eta[:, 1:2], eta[:, 2:3]
+    G1 = e1 * Ph * Z3 * silu_prime(Z1)
+    G3 = e3 * Ph * A
+    return [G1.T @ K, G3.T @ K, (e2 * Eh).T @ U]
 
 
 def row_targets(W0: list, norm: str) -> list:
@@ -283,6 +307,8 @@ def _update_vjp(W, K, V, eta, R, loss, model):
     """VJP of Wt = W - G(W; K, V, eta) given R = dL/dWt.
 
     Returns (dL/dW list, dK, dV, deta).  dG = -R."""
+    if eta.ndim == 2:
+        return _update_vjp_per_matrix(W, K, V, eta, R, loss, model)
     etac = eta[:, None]
     if model == "linear":
         (Wl,) = W
@@ -345,6 +371,54 @@ def _update_vjp(W, K, V, eta, R, loss, model):
         dU = dU + dY @ W2
         dW2 = dW2 + dY.T @ U
     # u = a z3 ; a = silu(z1)
+    dA = dA + dU * Z3
+    dZ3 = dZ3 + dU * A
+    dZ1 = dZ1 + dA * sp
+    dW1 = R1 + dZ1.T @ K
+    dW3 = R3 + dZ3.T @ K
+    dK = dK + dZ1 @ W1 + dZ3 @ W3
+    return [dW1, dW3, dW2], dK, dV, deta
+
+
+def _update_vjp_per_matrix(W, K, V, eta, R, loss, model):
+    """``_update_vjp`` with one rate per matrix (eta [M, 3]; deta [M, 3])."""
+    if model != "swiglu":
+        raise ValueError("per-matrix rates need the SwiGLU network's three matrices")
+    W1, W3, W2 = W
+    R1, R3, R2 = R
+    e1, e3, e2 = eta[:, 0:1], eta[:, 1:2], eta[:, 2:3]
+    Z1 = K @ W1.T
+    Z3 = K @ W3.T
+    sp = silu_prime(Z1)
+    spp = silu_second(Z1)
+    A = silu(Z1)
+    U = A * Z3
+    Eh = -V if loss == "dot" else U @ W2.T - V
+    Ph = Eh @ W2
+    H1 = Ph * Z3 * sp                     # G1 = (e1 H1)^T K
+    H3 = Ph * A                           # G3 = (e3 H3)^T K
+    # G2 = (e2 Eh)^T U; all three enter Wt with a minus sign
+    dS1 = -(K @ R1.T)                     # dL/d(e1 H1)
+    dS3 = -(K @ R3.T)                     # dL/d(e3 H3)
+    dS2 = -(U @ R2.T)                     # dL/d(e2 Eh)
+    deta = np.stack([np.sum(H1 * dS1, axis=1), np.sum(H3 * dS3, axis=1), np.sum(Eh * dS2, axis=1)], axis=1)
+    dK = -((e1 * H1) @ R1 + (e3 * H3) @ R3)
+    dU = -((e2 * Eh) @ R2)
+    dH1 = e1 * dS1
+    dH3 = e3 * dS3
+    dEh = e2 * dS2
+    # H1 = ph z3 s' ; H3 = ph a
+    dPh = dH1 * Z3 * sp + dH3 * A
+    dA = dH3 * Ph
+    dZ3 = dH1 * Ph * sp
+    dZ1 = dH1 * Ph * Z3 * spp
+    # ph = W2^T e
+    dEh = dEh + dPh @ W2.T
+    dW2 = R2 + Eh.T @ dPh
+    dV = -dEh
+    if loss != "dot":                     # e = W2 u - v
+        dU = dU + dEh @ W2
+        dW2 = dW2 + dEh.T @ U
     dA = dA + dU * Z3
     dZ3 = dZ3 + dU * A
     dZ1 = dZ1 + dA * sp

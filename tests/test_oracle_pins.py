@@ -212,6 +212,90 @@ def test_backward_matches_finite_differences(loss, norm, model, lr_max):
 
 
 # ---------------------------------------------------------------------------
+# per-matrix learning rates: G_j = d/dW_j sum_i eta_{j,i} L_i
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("loss", ["dot", "mse"])
+def test_per_matrix_inner_gradient_matches_finite_differences(loss):
+    """Each matrix's block is the central difference of the loss weighted by
+    that matrix's own rates (W1: eta[:, 0], W3: eta[:, 1], W2: eta[:, 2])."""
+    x = syn.make_inputs(5, 1, D, F, seed=4, w0_std=0.5)
+    K = torch.tensor(x["k"][:, 0], dtype=torch.float64)
+    V = torch.tensor(x["v"][:, 0], dtype=torch.float64)
+    eta3 = syn.per_matrix_lr(21, 5, 1, lr_max=0.5)[:, 0].astype(np.float64)
+    w = torch.tensor(x["w0"][0], dtype=torch.float64)
+    G = oracle.pack(oracle.inner_gradient(oracle.unpack(w.numpy(), D, F), K.numpy(), V.numpy(), eta3, loss))
+    h = 1e-6
+    fd = np.zeros_like(G)
+    for i in range(w.numel()):
+        j = min(i // (F * D), 2)            # packed W1, W3, W2 blocks of F*D each
+        eta = torch.tensor(eta3[:, j])
+        wp = w.clone(); wp[i] += h
+        wm = w.clone(); wm[i] -= h
+        fd[i] = (_loss_torch(wp, K, V, eta, loss) - _loss_torch(wm, K, V, eta, loss)) / (2 * h)
+    np.testing.assert_allclose(G, fd, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("loss", ["dot", "mse"])
+def test_equal_per_matrix_rates_reduce_to_one_rate(loss):
+    lay = _layout_2seq()
+    x = _tiny(31, T=lay.num_tokens, H=2)
+    lr3 = np.repeat(x["lr"][..., None], 3, axis=2)
+    a = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, loss=loss)
+    b = oracle.forward(x["q"], x["k"], x["v"], lr3, x["w0"], lay, D, F, loss=loss)
+    for n in ("o", "w_ckpt", "wnorm", "w_final"):
+        np.testing.assert_allclose(b[n], a[n], rtol=1e-12, atol=1e-14)
+    ga = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, loss=loss)
+    gb = oracle.backward(x["q"], x["k"], x["v"], lr3, x["w0"], lay, x["d_o"], D, F, loss=loss)
+    for n in ("dq", "dk", "dv", "dw0"):
+        np.testing.assert_allclose(gb[n], ga[n], rtol=1e-10, atol=1e-13)
+    assert gb["dlr"].shape == lr3.shape
+    np.testing.assert_allclose(gb["dlr"].sum(-1), ga["dlr"], rtol=1e-10, atol=1e-13)
+
+
+@pytest.mark.parametrize("zero", [0, 1, 2])
+def test_zero_rate_leaves_its_matrix(zero):
+    """With no row normalisation, a matrix whose rates are all zero keeps its
+    weights through every update while the others move (index pin)."""
+    lay = syn.layout_from_lengths([[6, 5]])
+    x = _tiny(32, T=lay.num_tokens)
+    lr3 = syn.per_matrix_lr(33, lay.num_tokens, 1, lr_max=0.3)
+    lr3[:, :, zero] = 0.0
+    out = oracle.forward(x["q"], x["k"], x["v"], lr3, x["w0"], lay, D, F, norm="none")
+    before = oracle.unpack(x["w0"][0].astype(np.float64), D, F)
+    after = oracle.unpack(out["w_final"][0, 0], D, F)
+    for j in range(3):
+        same = np.array_equal(after[j], before[j])
+        assert same == (j == zero), j
+
+
+@pytest.mark.parametrize("loss,norm,lr_max", [("dot", "row_w0", 0.3), ("mse", "none", 0.03)])
+def test_per_matrix_backward_matches_finite_differences(loss, norm, lr_max):
+    lay = _layout_2seq()
+    T = lay.num_tokens
+    x = _tiny(34, T=T, H=1, lr_max=lr_max)
+    inp = {n: x[n].astype(np.float64) for n in ("q", "k", "v", "w0")}
+    inp["lr"] = syn.per_matrix_lr(35, T, 1, lr_max=lr_max).astype(np.float64)
+    d_o = x["d_o"].astype(np.float64)
+    g = oracle.backward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, d_o, D, F, loss=loss, norm=norm)
+    h = 1e-6
+    for n, gn in {"q": "dq", "k": "dk", "v": "dv", "lr": "dlr", "w0": "dw0"}.items():
+        flat = inp[n].reshape(-1)
+        fd = np.zeros(flat.size)
+        for i in range(flat.size):
+            old = flat[i]
+            flat[i] = old + h
+            fp = _objective(inp, lay, d_o, loss, norm, "swiglu")
+            flat[i] = old - h
+            fm = _objective(inp, lay, d_o, loss, norm, "swiglu")
+            flat[i] = old
+            fd[i] = (fp - fm) / (2 * h)
+        scale = max(1.0, np.max(np.abs(fd)))
+        err = np.max(np.abs(g[gn].reshape(-1) - fd)) / scale
+        assert err < 2e-7, (n, err)
+
+
+# ---------------------------------------------------------------------------
 # invariants (P6 - P12)
 # ---------------------------------------------------------------------------
 

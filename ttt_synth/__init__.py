@@ -35,7 +35,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 # stream ids, one per drawn tensor
-S_Q, S_K, S_V, S_LR, S_W0, S_DO, S_FRAMES, S_DIR = range(8)
+S_Q, S_K, S_V, S_LR, S_W0, S_DO, S_FRAMES, S_DIR, S_LR3 = range(9)
 
 
 def _stream_key(seed: int, stream: int, sub: int) -> np.uint64:
@@ -283,6 +283,17 @@ def make_inputs(T: int, H: int, D: int, F: int, seed: int = 0, dtype: str = "fp3
         g = _per_head_normals(seed, S_DO, n, H, D, heads, t0=a)
         out["d_o"] = round_bf16(g) if dtype == "bf16" else g
     return out
+
+
+def per_matrix_lr(seed: int, T: int, H: int, lr_max: float = 0.1) -> np.ndarray:
+    """Seeded per-matrix learning rates [T, H, 3] float32, U[0, lr_max]; the
+    three rates of a (token, head) are those of W1, W3, W2, drawn from their
+    own streams (one per head and matrix)."""
+    lr = np.empty((T, H, 3), dtype=np.float32)
+    for h in range(H):
+        for j in range(3):
+            lr[:, h, j] = (uniform01(_stream_key(seed, S_LR3, 3 * h + j), 0, T) * lr_max).astype(np.float32)
+    return lr
 
 
 def random_direction(seed: int, shape, sub: int = 0) -> np.ndarray:
