@@ -33,7 +33,7 @@
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
  *  - q, k, v, o, d_o, dq, dk, dv: [T, H, D] contiguous, element type given by
  *    the config's dtype (float32 or bfloat16), 16-byte aligned device memory.
- *  - lr, dlr: [T, H] float32 device memory.
+ *  - lr, dlr: [T, H] float32 device memory ([T, H, 3] with lr_per_matrix).
  *  - Fast weights of one head are P = 3*F*D float32 values packed W1, W3, W2,
  *    each row-major.  w0 is [H, P] shared by all sequences (w0_seq_stride = 0)
  *    or one [H, P] block per sequence, w0_seq_stride floats apart.
@@ -91,13 +91,17 @@ typedef struct scal3r_ttt_config {
   int32_t hidden_dim;   /* F; BF16: 128 with D = 64, else a multiple of 256 up to 4096 (k * hd);
                            FP32: 32 or 128 */
   int32_t dtype;        /* SCAL3R_FP32 | SCAL3R_BF16 */
-  int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 path) */
+  int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 and wide-weight paths) */
   int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
   float   norm_eps;     /* clamp of the row norm; <= 0 selects 1e-6 */
   int32_t ckpt_every;   /* chunks between stored checkpoints: 0 or 1 = every chunk.  n > 1 (the
                            wide-weight path only) stores the weights after local chunks n-1,
                            2n-1, ... of each sequence; the backward recomputes the weights in
                            between with the forward's own gradient steps (bitwise the same) */
+  int32_t lr_per_matrix; /* 0: lr [T, H], one rate per token and head for all three matrices.
+                           1 (the wide-weight path only): lr [T, H, 3], the rates of W1, W3, W2
+                           in that order, each matrix's gradient (Eq. 8) weighted by its own
+                           rate; dlr then has the same [T, H, 3] layout */
 } scal3r_ttt_config;
 
 typedef struct scal3r_ttt_handle scal3r_ttt_handle;

@@ -57,7 +57,8 @@ class scal3r_ttt_config(ctypes.Structure):
     _fields_ = [("num_heads", ctypes.c_int32), ("head_dim", ctypes.c_int32),
                 ("hidden_dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("loss", ctypes.c_int32), ("weight_norm", ctypes.c_int32),
-                ("norm_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int32)]
+                ("norm_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int32),
+                ("lr_per_matrix", ctypes.c_int32)]
 
 
 class scal3r_ttt_schedule(ctypes.Structure):

@@ -43,7 +43,8 @@ cudaError_t prepare_fp32();
 cudaError_t prepare_bf16_forward();
 cudaError_t prepare_bf16_backward();
 bool wide_shape_supported(int D, int F);
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss,
+                            int lr_per_matrix);
 int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n);
 using WideLaunch = std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>;
 cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm, float* grad, void* ws,
@@ -248,6 +249,7 @@ void fill_common(const scal3r_ttt_handle* hd, Params& prm) {
   prm.S = hd->plan.S;
   prm.T = hd->plan.T;
   prm.loss = hd->cfg.loss;
+  prm.lr_mat = hd->cfg.lr_per_matrix ? 1 : 0;
   prm.norm = hd->cfg.weight_norm;
   prm.eps = hd->cfg.norm_eps > 0.f ? hd->cfg.norm_eps : 1e-6f;
   prm.status = hd->d_status;
@@ -349,7 +351,8 @@ const char* scal3r_ttt_error_string(int status) {
 int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (!cfg || !out) return SCAL3R_ERR_INVALID_ARG;
   *out = nullptr;
-  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every < 0)
+  if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every < 0 ||
+      cfg->lr_per_matrix < 0 || cfg->lr_per_matrix > 1)
     return SCAL3R_ERR_INVALID_ARG;
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
@@ -362,6 +365,7 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
       (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
   if (cfg->ckpt_every > 1 && !wide) return SCAL3R_ERR_UNSUPPORTED;   // sparse checkpoints: the wide path
+  if (cfg->lr_per_matrix && !wide) return SCAL3R_ERR_UNSUPPORTED;     // per-matrix rates: the wide path
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
   int major = 0, minor = 0, sms = 0;
@@ -410,7 +414,8 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   if (hd->wide) {
-    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every, hd->cfg.loss);
+    *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every, hd->cfg.loss,
+                                         hd->cfg.lr_per_matrix);
     return SCAL3R_OK;
   }
   *bytes = workspace_bytes(hd->plan, hd->shape, with_backward != 0);
@@ -433,7 +438,8 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
   const size_t need =
-      hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every, hd->cfg.loss) : workspace_bytes(pl, sh, false);
+      hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every, hd->cfg.loss,
+                                         hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -506,7 +512,8 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
   if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   const size_t need =
-      hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every, hd->cfg.loss) : workspace_bytes(pl, sh, true);
+      hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every, hd->cfg.loss,
+                                         hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, true);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
 
   Params prm;
@@ -743,7 +750,7 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
   if (!aligned16(k) || !aligned16(v) || !aligned16(lr) || !aligned16(w) || !aligned16(grad) ||
       (w_seq_stride & 3) != 0)
     return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss) : workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss, hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (hd->wide) {
     Params prm;
@@ -836,7 +843,7 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
   if (!w || w_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w_seq_stride != 0 && w_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
   if (!aligned16(q) || !aligned16(o) || !aligned16(w) || (w_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
-  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss) : workspace_bytes(pl, sh, false);
+  const size_t need = hd->wide ? wide_workspace_bytes(pl, sh, false, 1, hd->cfg.loss, hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, false);
   if (!workspace || workspace_bytes_ < need || !aligned16(workspace)) return SCAL3R_ERR_WORKSPACE;
   if (pl.T == 0 || pl.steps.size() < 2) return SCAL3R_OK;   // no token to apply
   if (hd->wide) {

@@ -134,6 +134,7 @@ struct Params {
   int32_t H, D, F, S;
   int64_t T;
   int32_t loss, norm;
+  int32_t lr_mat;   // 1: lr [T, H, 3], one rate per matrix (W1, W3, W2); 0: lr [T, H]
   float eps;
 };
 

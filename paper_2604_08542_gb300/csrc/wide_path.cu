@@ -43,19 +43,19 @@ constexpr int GEMM_THREADS = 320;                       // warp 0 TMA, warp 1 MM
 enum Epi : int {
   EPI_F32 = 0,      // out[0] = acc (float32)
   EPI_BF16 = 1,     // out[0] = acc (bf16)
-  EPI_KEY = 2,      // forward gradient gate: z1 | z3 of 128 hidden, in0 = P -> g1, g3, u~
+  EPI_KEY = 2,      // forward gradient gate: z1 | z3 of 128 hidden, in0 = P -> g1, g3, u~ (dot loss)
   EPI_APPLY = 3,    // forward apply gate: z1 | z3 -> h
   EPI_F32_ADD = 4,  // out[0] += acc (float32)
   EPI_BAPPLY = 5,   // apply VJP gate: zq1 | zq3 of 128 hidden, in0 = W2^T d_o -> dzq1, dzq3, uq
   EPI_BKEY = 6,     // update VJP gate: z1 | z3 | dg1 | dg3 of 64 hidden, in0 = W2^T v, in1 = -R2^T v
-                    //   -> dz1, dz3, g1, g3, -eta dp, -eta u and a partial of d eta
-  // the squared-error loss (e = eta (W2 u - v)):
-  EPI_MSE_E = 7,    // acc = W2 u;  in0 = v  -> e = eta (acc - v), and (acc - v) if out[1]
-  EPI_ADD_BF16 = 8, // out[0] = acc + in0 (bf16)
-  EPI_MSE_DE = 9,   // acc = dL/de;  in0 = (W2 u - v) -> eta dE, -eta dE (out[1], its own stride),
-                    //   partial of d eta = sum (W2 u - v) . dE
-  EPI_BKEY_MSE1 = 10,  // update VJP gate, pass 1: in0 = p -> dp, g1, g3
+                    //   -> dz1, dz3, g1, g3, -dp, -eta2 u and partials of d eta
+  // the squared-error loss; e = W2 u - v without a rate, p = W2^T e:
+  EPI_MSE_E = 7,    // acc = W2 u;  in0 = v  -> e = acc - v, and eta2 e if out[1]
+  EPI_ADD_BF16 = 8, // out[0] = acc + in0, or acc + eta2 in0 when eta is given
+  EPI_MSE_DE = 9,   // acc = dL/de -> out[0] = acc, out[1] = -acc (its own stride)
+  EPI_BKEY_MSE1 = 10,  // update VJP gate, pass 1: in0 = p, in1 = -R2^T e -> dp, g1, g3, partials of d eta
   EPI_BKEY_MSE2 = 11,  // update VJP gate, pass 2: in0 = p, in1 = du -> dz1, dz3
+  EPI_APPLY2 = 12,  // gate z1 | z3 -> u and eta2 u
 };
 
 struct GemmArgs {
@@ -71,12 +71,14 @@ struct GemmArgs {
   int64_t ld_out;
   const __nv_bfloat16* in0;  // epilogue inputs [M x F], row stride ld_out
   const __nv_bfloat16* in1;
-  const float* eta;        // learning rate of output row m at eta[m * eta_stride]
-  int64_t eta_stride;
-  float* part;             // EPI_BKEY: d eta partial of row m, tile column tn at part[m * ld_part + tn]
+  const float* eta;        // learning rates of output row m: eta[m * eta_stride + j * eta_mat] for
+  int64_t eta_stride;      //   W1, W3, W2 (j = 0, 1, 2); eta_mat = 0: one rate shared by all three
+  int eta_mat;
+  float* part;             // d eta partials of row m, tile column tn: part[m * ld_part + tn] (shared rate:
+                           //   the sum), or part[m * ld_part + 3 tn + j] for matrix j
   int64_t ld_part;
   int* status;
-  int mse;                 // EPI_KEY: the squared-error loss (in0 is p itself; no u~ output)
+  int mse;                 // EPI_KEY: the squared-error loss (in0 = W2^T e; no u~ output)
   int64_t ld_in;           // row stride of in0 / in1 when not ld_out (0: ld_out)
   int64_t ld_out1;         // row stride of out[1] when not ld_out (0: ld_out)
 };
@@ -147,6 +149,26 @@ __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* 
 // tile's epilogue overlaps the next tile's MMAs.
 // XSET: the squared-error loss's epilogues, in their own instantiation so that
 // the common ones keep their register allocation.
+// The three learning rates of output row m (W1, W3, W2).
+__device__ __forceinline__ void row_rates(const GemmArgs& g, int m, float& e1, float& e3, float& e2) {
+  const float* ep = g.eta + (size_t)m * g.eta_stride;
+  e1 = ep[0];
+  e3 = ep[g.eta_mat];
+  e2 = ep[2 * g.eta_mat];
+}
+
+// One tile's d eta partials of row m: the three per-matrix sums, or their total.
+__device__ __forceinline__ void store_deta(const GemmArgs& g, int m, int tn, float q1, float q3, float q2) {
+  float* p = g.part + (size_t)m * g.ld_part;
+  if (g.eta_mat) {
+    p[3 * tn] = q1;
+    p[3 * tn + 1] = q3;
+    p[3 * tn + 2] = q2;
+  } else {
+    p[tn] = q1 + q3 + q2;
+  }
+}
+
 template <bool XSET>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ uint8_t smraw[];
@@ -266,86 +288,111 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       const int m = m0 + (int)row;
       const bool valid = m < g.M;
       if (XSET) {
+        float e1 = 0.f, e3 = 0.f, e2 = 0.f;
+        if (g.eta && valid) row_rates(g, m, e1, e3, e2);
         if (g.epi == EPI_MSE_E || g.epi == EPI_ADD_BF16 || g.epi == EPI_MSE_DE) {
-        const int64_t ldi = g.ld_in ? g.ld_in : g.ld_out;
-        const int64_t ld1 = g.ld_out1 ? g.ld_out1 : g.ld_out;
-        const float eta = (g.epi != EPI_ADD_BF16 && valid) ? g.eta[(size_t)m * g.eta_stride] : 0.f;
-        float deta = 0.f;
+          const int64_t ldi = g.ld_in ? g.ld_in : g.ld_out;
+          const int64_t ld1 = g.ld_out1 ? g.ld_out1 : g.ld_out;
+          const float sx = g.eta ? e2 : 1.f;   // EPI_ADD_BF16: the scale of in0
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-          uint4 i0 = make_uint4(0, 0, 0, 0), i1 = i0;
-          const uint4* ip = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
-          if (valid) {
-            i0 = __ldg(ip);
-            i1 = __ldg(ip + 1);
-          }
-          float acc[16];
-          tmem_ld16(accb + c, acc);
-          if (!valid) continue;
-          float x[16], o0[16], o1[16];
-          unpack16(i0, i1, x);
-          const size_t off0 = (size_t)m * g.ld_out + n0 + c, off1 = (size_t)m * ld1 + n0 + c;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            if (g.epi == EPI_MSE_E) {            // x = v
-              o1[e] = acc[e] - x[e];
-              o0[e] = eta * o1[e];
-            } else if (g.epi == EPI_ADD_BF16) {
-              o0[e] = acc[e] + x[e];
-            } else {                             // EPI_MSE_DE: x = W2 u - v, acc = dE
-              o0[e] = eta * acc[e];
-              o1[e] = -eta * acc[e];
-              deta = fmaf(x[e], acc[e], deta);
+          for (int c = 0; c < BN; c += 16) {
+            uint4 i0 = make_uint4(0, 0, 0, 0), i1 = i0;
+            if (g.in0 && valid) {
+              const uint4* ip = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
+              i0 = __ldg(ip);
+              i1 = __ldg(ip + 1);
             }
+            float acc[16];
+            tmem_ld16(accb + c, acc);
+            if (!valid) continue;
+            float x[16], o0[16], o1[16];
+            unpack16(i0, i1, x);
+            const size_t off0 = (size_t)m * g.ld_out + n0 + c, off1 = (size_t)m * ld1 + n0 + c;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              if (g.epi == EPI_MSE_E) {            // x = v
+                o0[e] = acc[e] - x[e];
+                o1[e] = e2 * o0[e];
+              } else if (g.epi == EPI_ADD_BF16) {
+                o0[e] = fmaf(sx, x[e], acc[e]);
+              } else {                             // EPI_MSE_DE
+                o0[e] = acc[e];
+                o1[e] = -acc[e];
+              }
+            }
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off0, o0);
+            if (g.epi != EPI_ADD_BF16 && g.out[1]) st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off1, o1);
           }
-          st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off0, o0);
-          if (g.epi != EPI_ADD_BF16 && g.out[1]) st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off1, o1);
-        }
-        if (g.epi == EPI_MSE_DE && valid) g.part[(size_t)m * g.ld_part + tn] = deta;
+        } else if (g.epi == EPI_APPLY2) {
+          // columns [0, 128) z1, [128, 256) z3 of hidden units f0 .. f0 + 127
+          const int f0 = tn * (BN / 2);
+#pragma unroll 1
+          for (int c = 0; c < BN / 2; c += 16) {
+            float z1[16], z3[16];
+            tmem_ld16(accb + c, z1);
+            tmem_ld16(accb + 128 + c, z3);
+            if (!valid) continue;
+            float h[16], hs[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              float sg;
+              h[e] = silu_d(z1[e], sg) * z3[e];
+              hs[e] = e2 * h[e];
+            }
+            const size_t off = (size_t)m * g.ld_out + f0 + c;
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, h);
+            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off, hs);
+          }
         } else {
-        // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
-        // hidden units f0 .. f0 + 63 (dg = -R k); squared-error loss, p = W2^T e
-        const int f0 = tn * (BN / 4);
-        const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
-        const uint4* up = reinterpret_cast<const uint4*>((g.in1 ? g.in1 : g.in0) + (size_t)m * g.ld_out + f0);
-        const bool second = g.epi == EPI_BKEY_MSE2;
+          // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
+          // hidden units f0 .. f0 + 63 (dg = -R k); squared-error loss
+          const int f0 = tn * (BN / 4);
+          const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
+          const uint4* up = reinterpret_cast<const uint4*>(g.in1 + (size_t)m * g.ld_out + f0);
+          const bool second = g.epi == EPI_BKEY_MSE2;
+          float q1 = 0.f, q3 = 0.f, q2 = 0.f;
 #pragma unroll 1
-        for (int c = 0; c < 64; c += 8) {
-          uint4 pw = make_uint4(0, 0, 0, 0), uw = pw;
-          if (valid) {
-            pw = __ldg(pp + c / 8);
-            if (second) uw = __ldg(up + c / 8);
-          }
-          float zz[4][8];
-          tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
-          if (!valid) continue;
-          float pv[8], du[8];
-          unpack8(pw, pv);
-          unpack8(uw, du);
-          float o[3][8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            float sg;
-            const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
-            const float a = silu_d(x1, sg);
-            const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
-            if (!second) {
-              o[0][e] = d3 * a + d1 * x3 * sp;                   // dp
-              o[1][e] = pv[e] * x3 * sp;                         // g1
-              o[2][e] = pv[e] * a;                               // g3
-            } else {
-              const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);  // silu''(z1)
-              const float da = d3 * pv[e] + du[e] * x3;
-              o[1][e] = d1 * pv[e] * sp + du[e] * a;             // dz3
-              o[0][e] = d1 * pv[e] * x3 * spp + da * sp;         // dz1
+          for (int c = 0; c < 64; c += 8) {
+            uint4 pw = make_uint4(0, 0, 0, 0), uw = pw;
+            if (valid) {
+              pw = __ldg(pp + c / 8);
+              uw = __ldg(up + c / 8);
             }
-          }
-          const size_t off = (size_t)m * g.ld_out + f0 + c;
+            float zz[4][8];
+            tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
+            if (!valid) continue;
+            float pv[8], w[8];
+            unpack8(pw, pv);
+            unpack8(uw, w);
+            float o[3][8];
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
-            if (q < (second ? 2 : 3))
-              *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
-        }
+            for (int e = 0; e < 8; ++e) {
+              float sg;
+              const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
+              const float a = silu_d(x1, sg);
+              const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
+              const float t1 = d1 * x3 * sp;
+              if (!second) {                                       // w = -R2^T e
+                o[0][e] = e1 * t1 + e3 * d3 * a;                   // dp
+                o[1][e] = e1 * pv[e] * x3 * sp;                    // g1
+                o[2][e] = e3 * pv[e] * a;                          // g3
+                q1 = fmaf(pv[e], t1, q1);
+                q3 = fmaf(pv[e] * a, d3, q3);
+                q2 = fmaf(w[e], a * x3, q2);
+              } else {                                             // w = du
+                const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);  // silu''(z1)
+                const float da = e3 * d3 * pv[e] + w[e] * x3;
+                o[1][e] = e1 * d1 * pv[e] * sp + w[e] * a;         // dz3
+                o[0][e] = e1 * d1 * pv[e] * x3 * spp + da * sp;    // dz1
+              }
+            }
+            const size_t off = (size_t)m * g.ld_out + f0 + c;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              if (q < (second ? 2 : 3))
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
+          }
+          if (!second && valid) store_deta(g, m, tn, q1, q3, q2);
         }
       } else if (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD) {
 #pragma unroll 1
@@ -378,8 +425,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
         // hidden units f0 .. f0 + 63 (dg = -R k)
         const int f0 = tn * (BN / 4);
-        const float eta = valid ? g.eta[(size_t)m * g.eta_stride] : 0.f;
-        float deta = 0.f;
+        float e1 = 0.f, e3 = 0.f, e2 = 0.f;
+        if (valid) row_rates(g, m, e1, e3, e2);
+        float q1 = 0.f, q3 = 0.f, q2 = 0.f;
         const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
         const uint4* np = reinterpret_cast<const uint4*>(g.in1 + (size_t)m * g.ld_out + f0);
 #pragma unroll 1
@@ -404,29 +452,36 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
             const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);    // silu''(z1)
             const float u = a * x3;
-            const float pv = -eta * praw[e];
-            const float du = -eta * ndu[e];
-            const float dp = d3 * a + d1 * x3 * sp;
-            const float da = d3 * pv + du * x3;
-            o[1][e] = d1 * pv * sp + du * a;                 // dz3
-            o[0][e] = d1 * pv * x3 * spp + da * sp;          // dz1
-            o[2][e] = pv * x3 * sp;                          // g1
-            o[3][e] = pv * a;                                // g3
-            o[4][e] = -eta * dp;                             // -eta dp
-            o[5][e] = -eta * u;                              // -eta u
-            deta -= praw[e] * dp + ndu[e] * u;
+            const float p1 = -e1 * praw[e], p3 = -e3 * praw[e];   // rate times p (e = -v)
+            const float du = -e2 * ndu[e];
+            const float t1 = d1 * x3 * sp;
+            const float da = d3 * p3 + du * x3;
+            o[1][e] = d1 * p1 * sp + du * a;                 // dz3
+            o[0][e] = d1 * p1 * x3 * spp + da * sp;          // dz1
+            o[2][e] = p1 * x3 * sp;                          // g1
+            o[3][e] = p3 * a;                                // g3
+            o[4][e] = -(e1 * t1 + e3 * d3 * a);              // -dp
+            o[5][e] = -e2 * u;                               // -eta2 u
+            q1 = fmaf(-praw[e], t1, q1);
+            q3 = fmaf(-praw[e] * a, d3, q3);
+            q2 = fmaf(-ndu[e], u, q2);
           }
           const size_t off = (size_t)m * g.ld_out + f0 + c;
 #pragma unroll
           for (int q = 0; q < 6; ++q)
             *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
         }
-        if (valid) g.part[(size_t)m * g.ld_part + tn] = deta;
+        if (valid) store_deta(g, m, tn, q1, q3, q2);
       } else {
         // gate epilogues: columns [0, 128) are z1, [128, 256) z3 of hidden
         // units f0 .. f0 + 127
         const int f0 = tn * (BN / 2);
-        const float eta = (g.epi == EPI_KEY && valid) ? g.eta[(size_t)m * g.eta_stride] : 0.f;
+        float e1 = 0.f, e3 = 0.f, e2 = 0.f;
+        if (g.epi == EPI_KEY && valid) row_rates(g, m, e1, e3, e2);
+        if (!g.mse) {   // dot loss: e = -eta v
+          e1 = -e1;
+          e3 = -e3;
+        }
         // this row's 128 values of the epilogue input (KEY: P; BAPPLY:
         // W2^T d_o), loaded at once: one memory latency per tile
         uint4 prow[16];
@@ -460,11 +515,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
               const float x1 = z1[e], x3 = z3[e];
               const float a = silu_d(x1, sg);
               const float sp = fmaf(a, 1.f - sg, sg);     // silu'(z1)
-              if (g.epi == EPI_KEY) {
-                const float pv = g.mse ? r[e] : -eta * r[e];   // p = W2^T e (dot loss: e = -eta v)
-                o0[e] = pv * x3 * sp;                     // g1
-                o1[e] = pv * a;                           // g3
-                o2[e] = -eta * a * x3;                    // u~ = -eta u (dot loss)
+              if (g.epi == EPI_KEY) {                     // r = W2^T v (dot) or W2^T e (squared error)
+                o0[e] = e1 * r[e] * x3 * sp;              // g1
+                o1[e] = e3 * r[e] * a;                    // g3
+                o2[e] = -e2 * a * x3;                     // u~ = -eta2 u (dot loss)
               } else {                                    // EPI_BAPPLY, r = W2^T d_o
                 o0[e] = r[e] * x3 * sp;                   // dzq1
                 o1[e] = r[e] * a;                         // dzq3
@@ -681,14 +735,17 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_bupdate_kernel(const float* 
   if (threadIdx.x == 0 && norm == SCAL3R_NORM_ROW_W0) drho[blockIdx.x] += proj;
 }
 
-// d eta of the chunk's tokens: the per-tile partials summed in tile order.
-__global__ void wide_deta_kernel(const float* __restrict__ part, int64_t ld_part, int nparts, float* __restrict__ dlr,
-                                 int64_t stride, int M) {
+// d eta of the chunk's tokens: the per-tile partials summed in tile order
+// (nmat = 3: each matrix's rate from its own partials).
+__global__ void wide_deta_kernel(const float* __restrict__ part, int64_t ld_part, int ntiles, int nmat,
+                                 float* __restrict__ dlr, int64_t stride, int M) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  float a = 0.f;
-  for (int j = 0; j < nparts; ++j) a += part[(size_t)m * ld_part + j];
-  dlr[(size_t)m * stride] = a;
+  for (int j = 0; j < nmat; ++j) {
+    float a = 0.f;
+    for (int t = 0; t < ntiles; ++t) a += part[(size_t)m * ld_part + (size_t)t * nmat + j];
+    dlr[(size_t)m * stride + j] = a;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -749,14 +806,15 @@ struct WideBufs {
   float* part;    // backward: d eta partials [mmax x F/64]
   float* rgr;     // backward with sparse checkpoints: the recomputed chunk gradient
   float* seg;     // backward with sparse checkpoints: W_j of one segment, ckpt_every - 1 blocks of P
-  __nv_bfloat16* ex[3];   // squared-error loss: [mmax x D] bf16 buffers (forward: E; backward: E, Y - V, dY)
+  __nv_bfloat16* ex[2];   // squared-error loss: [mmax x D] bf16 (forward: e, eta2 e; backward: e, dY)
 };
 
-// d eta partials per token row: one per 64 hidden units (dot loss, from the
-// update-VJP gate) or per 256 output columns (squared-error loss, from dE).
-int deta_parts(const Shape& s, bool mse) { return mse ? s.D / BN : s.F / 64; }
+// d eta partials per token row: one per 64 hidden units (the update-VJP
+// gate's tiles), times three with per-matrix rates.
+int deta_parts(const Shape& s, int lr_mat) { return (s.F / 64) * (lr_mat ? 3 : 1); }
 
-size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, bool mse, WideBufs* w, void* ws) {
+size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, bool mse, int lr_mat, WideBufs* w,
+                    void* ws) {
   const size_t P = (size_t)s.P();
   const int64_t mmax = max_chunk(p);
   const size_t act = al256((size_t)mmax * s.F * 2);
@@ -777,14 +835,14 @@ size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, boo
   x.rho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
   if (bwd) {
     x.drho = reinterpret_cast<float*>(take((size_t)s.R() * 4));
-    x.part = reinterpret_cast<float*>(take((size_t)mmax * deta_parts(s, mse) * 4));
+    x.part = reinterpret_cast<float*>(take((size_t)mmax * deta_parts(s, lr_mat) * 4));
     if (ckpt_every > 1) {   // recomputation between stored checkpoints
       x.rgr = reinterpret_cast<float*>(take(P * 4));
       x.seg = reinterpret_cast<float*>(take(P * 4 * (size_t)(ckpt_every - 1)));
     }
   }
   if (mse)
-    for (int i = 0; i < (bwd ? 3 : 1); ++i) x.ex[i] = reinterpret_cast<__nv_bfloat16*>(take((size_t)mmax * s.D * 2));
+    for (int i = 0; i < 2; ++i) x.ex[i] = reinterpret_cast<__nv_bfloat16*>(take((size_t)mmax * s.D * 2));
   if (w) *w = x;
   return o;
 }
@@ -846,10 +904,34 @@ cudaError_t run_gemm(const Ctx& c, GemmArgs& a, double flops) {
   return c.launch(0, flops, 0, [&] { return gemm(a, c.st); });
 }
 
+// The learning rates of head h's tokens from t0 on: lr [T, H] or, with
+// per-matrix rates, [T, H, 3].
+void set_rates(GemmArgs& a, const Params& prm, int64_t t0, int h) {
+  const int n = prm.lr_mat ? 3 : 1;
+  a.eta = prm.lr + ((size_t)t0 * prm.H + h) * n;
+  a.eta_stride = (int64_t)prm.H * n;
+  a.eta_mat = prm.lr_mat ? 1 : 0;
+}
+
+// d eta of the chunk's M tokens from t0 (head h) from the gate's partials.
+cudaError_t chunk_deta(const Ctx& cx, const float* part, int64_t t0, int h, int M) {
+  const Params& prm = cx.prm;
+  const int nmat = prm.lr_mat ? 3 : 1;
+  const int ntiles = cx.sh.F / 64;
+  float* dlr = prm.dlr + ((size_t)t0 * prm.H + h) * nmat;
+  return cx.launch(1, 0, 0, [&] {
+    wide_deta_kernel<<<(M + 127) / 128, 128, 0, cx.st>>>(part, (int64_t)ntiles * nmat, ntiles, nmat, dlr,
+                                                         (int64_t)prm.H * nmat, M);
+    return cudaGetLastError();
+  });
+}
+
 }  // namespace
 
-size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss) {
-  return layout_bytes(p, s, with_backward, ckpt_every, loss == SCAL3R_LOSS_MSE, nullptr, nullptr);
+size_t wide_workspace_bytes(const Plan& p, const Shape& s, bool with_backward, int ckpt_every, int loss,
+                            int lr_per_matrix) {
+  return layout_bytes(p, s, with_backward, ckpt_every, loss == SCAL3R_LOSS_MSE, lr_per_matrix ? 1 : 0, nullptr,
+                      nullptr);
 }
 
 // Checkpoint slot of W_j (the weights after local chunk j-1) of sequence s, or
@@ -899,11 +981,11 @@ cudaError_t prepare_wide() {
 namespace {
 
 // The squared-error loss's gradient (Eq. 8 with L = 1/2 |f_W(k) - v|^2): with
-// u = silu(z1) o z3 and e = eta (W2 u - v), p = W2^T e:
-//   U = gate(K), E = eta (U W2^T - V), P = E W2, gate(K) with p -> g1, g3;
-//   G1 = g1^T K, G3 = g3^T K, G2 = E^T U.
+// u = silu(z1) o z3, e = W2 u - v and p = W2^T e (no rate yet):
+//   U = gate(K), [e, eta2 e] = U W2^T - V, P = e W2, gate(K) with p -> g1 = eta1 p z3 s', g3 = eta3 p a;
+//   G1 = g1^T K, G3 = g3^T K, G2 = (eta2 e)^T U.
 cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
-                         __nv_bfloat16* eb) {
+                         __nv_bfloat16* const* ex) {
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F;
@@ -912,6 +994,7 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
   const __nv_bfloat16* w3 = wb + (size_t)F * D;
   const __nv_bfloat16* w2 = wb + 2 * (size_t)F * D;
   __nv_bfloat16 *pb = act[0], *g1 = act[1], *g3 = act[2], *ub = act[3];
+  __nv_bfloat16 *eb = ex[0], *e2b = ex[1];
   const int64_t t0 = cx.pl.chunk_offsets[c], t1 = cx.pl.chunk_offsets[c + 1];
   const int M = (int)(t1 - t0);
   const double mfd = 2.0 * M * (double)F * D;
@@ -923,16 +1006,16 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
     a.epi = EPI_APPLY; a.out[0] = ub; a.ld_out = F;
     WIDE_TRY(run_gemm(cx, a, 2 * mfd));
   }
-  {   // E = eta (U W2^T - V)
+  {   // e = U W2^T - V and eta2 e
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
     a.M = M; a.N = D; a.K = F;
-    a.epi = EPI_MSE_E; a.out[0] = eb; a.ld_out = D;
+    a.epi = EPI_MSE_E; a.out[0] = eb; a.out[1] = e2b; a.ld_out = D;
     a.in0 = reinterpret_cast<const __nv_bfloat16*>(prm.v) + ((size_t)t0 * H + h) * D; a.ld_in = (int64_t)H * D;
-    a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    set_rates(a, prm, t0, h);
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
-  {   // P = E W2
+  {   // P = e W2
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], eb, M, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
     a.M = M; a.N = F; a.K = D; a.b_mn = 1;
@@ -945,7 +1028,7 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
              mat_map(&a.b[1], w3, F, D, 128));
     a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
     a.epi = EPI_KEY; a.mse = 1; a.out[0] = g1; a.out[1] = g3; a.ld_out = F; a.in0 = pb;
-    a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    set_rates(a, prm, t0, h);
     WIDE_TRY(run_gemm(cx, a, 2 * mfd));
   }
   for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
@@ -955,9 +1038,9 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
     a.epi = EPI_F32; a.out[0] = gr + (size_t)j * F * D; a.ld_out = D;
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
-  {   // G2 = E^T U
+  {   // G2 = (eta2 e)^T U
     GemmArgs a{};
-    WIDE_MAP(mat_map(&a.a[0], eb, M, D, 64) && mat_map(&a.b[0], ub, M, F, 64));
+    WIDE_MAP(mat_map(&a.a[0], e2b, M, D, 64) && mat_map(&a.b[0], ub, M, F, 64));
     a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1;
     a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
     WIDE_TRY(run_gemm(cx, a, mfd));
@@ -967,10 +1050,10 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
 
 // The gradient G of chunk c (Eq. 8, 9) at the bf16 weights wb of head h,
 // into gr (P floats, packed like the weights).  act: four [M x F] bf16 buffers;
-// eb: an [M x D] bf16 buffer (squared-error loss only).
+// ex: two [M x D] bf16 buffers (squared-error loss only).
 cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
-                     __nv_bfloat16* eb) {
-  if (cx.prm.loss == SCAL3R_LOSS_MSE) return key_grad_mse(cx, h, c, wb, gr, act, eb);
+                     __nv_bfloat16* const* ex) {
+  if (cx.prm.loss == SCAL3R_LOSS_MSE) return key_grad_mse(cx, h, c, wb, gr, act, ex);
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
@@ -994,8 +1077,8 @@ cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float
     WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
              mat_map(&a.b[1], w3, F, D, 128));
     a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
-    a.epi = EPI_KEY; a.out[0] = g1; a.out[1] = g3; a.out[2] = ut; a.ld_out = F;
-    a.in0 = pb; a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+    a.epi = EPI_KEY; a.out[0] = g1; a.out[1] = g3; a.out[2] = ut; a.ld_out = F; a.in0 = pb;
+    set_rates(a, prm, t0, h);
     WIDE_TRY(run_gemm(cx, a, 2 * mfd));
   }
   for (int j = 0; j < 2; ++j) {   // G1 = g1^T K, G3 = g3^T K
@@ -1019,8 +1102,8 @@ cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float
 // normalise(W - G) in place; optionally the checkpoint, the pre-normalisation
 // row norms and w_final are written.  gr: the gradient buffer (P floats).
 cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
-                       __nv_bfloat16* const* act, __nv_bfloat16* eb, float* ck, float* wn, float* wf) {
-  WIDE_TRY(key_grad(cx, h, c, wb, gr, act, eb));
+                       __nv_bfloat16* const* act, __nv_bfloat16* const* ex, float* ck, float* wn, float* wf) {
+  WIDE_TRY(key_grad(cx, h, c, wb, gr, act, ex));
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int D = sh.D, F = sh.F, R = sh.R();
@@ -1041,7 +1124,7 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
   const size_t P = (size_t)sh.P();
   const int R = sh.R();
   WideBufs w;
-  layout_bytes(pl, sh, false, ckpt_every, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
+  layout_bytes(pl, sh, false, ckpt_every, prm.loss == SCAL3R_LOSS_MSE, prm.lr_mat, &w, ws);
   __nv_bfloat16* pb = w.act[0];
   const int64_t T = pl.T;
   const __nv_bfloat16* w1 = w.wb;
@@ -1063,7 +1146,7 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
         float* ck = (prm.w_ckpt && slot >= 0) ? prm.w_ckpt + ((size_t)slot * H + h) * P : nullptr;
         float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
         float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
-        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, w.ex[0], ck, wn, wf));
+        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, w.ex, ck, wn, wf));
         {   // apply: h = silu(Q W1^T) o (Q W3^T)
           GemmArgs a{};
           WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
@@ -1133,7 +1216,7 @@ cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
   const size_t P = (size_t)sh.P();
   WideBufs w;
-  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
+  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, prm.lr_mat, &w, ws);
   for (int s = 0; s < pl.S; ++s) {
     for (int h = 0; h < H; ++h) {
       float* gout = grad + ((size_t)s * H + h) * P;
@@ -1147,7 +1230,7 @@ cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm
         wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wsrc, w.wm, w.wb, nullptr, D, F, prm.norm);
         return cudaGetLastError();
       }));
-      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act, w.ex[0]));
+      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act, w.ex));
     }
   }
   return cudaSuccess;
@@ -1179,7 +1262,7 @@ cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void*
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
   const size_t P = (size_t)sh.P();
   WideBufs w;
-  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, &w, ws);
+  layout_bytes(pl, sh, false, 1, prm.loss == SCAL3R_LOSS_MSE, prm.lr_mat, &w, ws);
   const int64_t T = pl.T;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + (size_t)F * D, *w2 = w.wb + 2 * (size_t)F * D;
   __nv_bfloat16* pb = w.act[0];
@@ -1218,14 +1301,15 @@ cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void*
 namespace {
 
 // Update VJP of one chunk under the squared-error loss (Eq. 8 with
-// L = 1/2 |f_W(k) - v|^2), at the bf16 weights w.wb with -R in w.nrb:
-//   U = gate(K), [E, Y - V] = eta (U W2^T - V), P = E W2, ND = E (-R2);
-//   gate [W1; W3; -R1; -R3] with p -> dp, g1, g3   (dg = -R k);
-//   dE = [U dP] [-R2 W2]^T -> dY = eta dE, dv = -eta dE, d eta = (Y - V) . dE;
-//   dU = ND + dY W2;  gate again with p, du -> dz1, dz3;
-//   dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3];
-//   lam1 += dz1^T K, lam3 += dz3^T K, lam2 += E^T dP + dY^T U.
-// The d eta partials (D / 256 per row) are left in w.part.
+// L = 1/2 |f_W(k) - v|^2), at the bf16 weights w.wb with -R in w.nrb; e = W2 u - v
+// and p = W2^T e carry no rate, eta1, eta3, eta2 are the rates of W1, W3, W2:
+//   [U, eta2 U] = gate(K), e = U W2^T - V, P = e W2, N = e (-R2);
+//   gate [W1; W3; -R1; -R3] with p, N -> dp = eta1 dg1 z3 s' + eta3 dg3 a, g1, g3 and the
+//     d eta partials (p z3 s' . dg1, p a . dg3, N . u)   (dg = -R k);
+//   dE = [eta2 U, dP] [-R2, W2]^T -> dY = dE, dv = -dE;  dU = eta2 N + dY W2;
+//   gate again with p, du -> dz1, dz3;  dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3];
+//   lam1 += dz1^T K, lam3 += dz3^T K, lam2 += e^T dP + dY^T U.
+// The d eta partials are left in w.part.
 cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBufs& w, float* lam1, float* lam3,
                            float* lam2) {
   const Shape& sh = cx.sh;
@@ -1235,64 +1319,65 @@ cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBu
   const size_t FD = (size_t)F * D;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
   const __nv_bfloat16 *r1 = w.nrb, *r3 = w.nrb + FD, *r2 = w.nrb + 2 * FD;   // -R
-  __nv_bfloat16 *ub = w.act[0], *pb = w.act[1], *nd = w.act[2], *dp = w.act[3], *g1 = w.act[4], *g3 = w.act[5],
-                *du = w.act[6], *dz1 = w.act[7], *dz3 = w.act[2];   // dz3 overwrites nd once du is formed
-  __nv_bfloat16 *eb = w.ex[0], *ymv = w.ex[1], *dy = w.ex[2];
+  // du overwrites eta2 U once dE is formed, dz3 overwrites N once du is formed
+  __nv_bfloat16 *ub = w.act[0], *pb = w.act[1], *nb = w.act[2], *dp = w.act[3], *g1 = w.act[4], *g3 = w.act[5],
+                *u2 = w.act[6], *du = w.act[6], *dz1 = w.act[7], *dz3 = w.act[2];
+  __nv_bfloat16 *eb = w.ex[0], *dy = w.ex[1];
   const double mfd = 2.0 * M * (double)F * D;
-  const float* eta = prm.lr + (size_t)t0 * H + h;
-  {   // U = silu(K W1^T) o (K W3^T)
+  {   // U and eta2 U
     GemmArgs a{};
     WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
              mat_map(&a.b[1], w3, F, D, 128));
     a.M = M; a.N = 2 * F; a.K = D; a.nbn = 2; a.ha = h; a.ya = (int)t0;
-    a.epi = EPI_APPLY; a.out[0] = ub; a.ld_out = F;
+    a.epi = EPI_APPLY2; a.out[0] = ub; a.out[1] = u2; a.ld_out = F;
+    set_rates(a, prm, t0, h);
     WIDE_TRY(run_gemm(cx, a, 2 * mfd));
   }
-  {   // E = eta (U W2^T - V), Y - V
+  {   // e = U W2^T - V
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.b[0], w2, D, F, 256));
     a.M = M; a.N = D; a.K = F;
-    a.epi = EPI_MSE_E; a.out[0] = eb; a.out[1] = ymv; a.ld_out = D;
+    a.epi = EPI_MSE_E; a.out[0] = eb; a.ld_out = D;
     a.in0 = reinterpret_cast<const __nv_bfloat16*>(prm.v) + ((size_t)t0 * H + h) * D; a.ld_in = (int64_t)H * D;
-    a.eta = eta; a.eta_stride = H;
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
-  for (int i = 0; i < 2; ++i) {   // P = E W2, ND = E (-R2)
+  for (int i = 0; i < 2; ++i) {   // P = e W2, N = e (-R2)
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], eb, M, D, 128) && mat_map(&a.b[0], i ? r2 : w2, D, F, 64));
     a.M = M; a.N = F; a.K = D; a.b_mn = 1;
-    a.epi = EPI_BF16; a.out[0] = i ? nd : pb; a.ld_out = F;
+    a.epi = EPI_BF16; a.out[0] = i ? nb : pb; a.ld_out = F;
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
-      {   // dE = -U R2^T + dP W2^T -> dY, dv, d eta partials
+      {   // dE = -eta2 U R2^T + dP W2^T -> dY, dv
         GemmArgs a{};
-        WIDE_MAP(mat_map(&a.a[0], ub, M, F, 128) && mat_map(&a.a[1], dp, M, F, 128) &&
+        WIDE_MAP(mat_map(&a.a[0], u2, M, F, 128) && mat_map(&a.a[1], dp, M, F, 128) &&
                  mat_map(&a.b[0], r2, D, F, 256) && mat_map(&a.b[1], w2, D, F, 256));
         a.M = M; a.N = D; a.K = 2 * F; a.kseg = F; a.nseg = 2;
-        a.epi = EPI_MSE_DE; a.out[0] = dy; a.ld_out = D; a.in0 = ymv;
+        a.epi = EPI_MSE_DE; a.out[0] = dy; a.ld_out = D;
         a.out[1] = reinterpret_cast<__nv_bfloat16*>(prm.dv) + ((size_t)t0 * H + h) * D; a.ld_out1 = (int64_t)H * D;
-        a.eta = eta; a.eta_stride = H;
-        a.part = w.part; a.ld_part = deta_parts(sh, true);
         WIDE_TRY(run_gemm(cx, a, 2 * mfd));
       }
-      {   // dU = ND + dY W2
+      {   // dU = eta2 N + dY W2
         GemmArgs a{};
         WIDE_MAP(mat_map(&a.a[0], dy, M, D, 128) && mat_map(&a.b[0], w2, D, F, 64));
         a.M = M; a.N = F; a.K = D; a.b_mn = 1;
-        a.epi = EPI_ADD_BF16; a.out[0] = du; a.ld_out = F; a.in0 = nd;
+        a.epi = EPI_ADD_BF16; a.out[0] = du; a.ld_out = F; a.in0 = nb;
+        set_rates(a, prm, t0, h);
         WIDE_TRY(run_gemm(cx, a, mfd));
       }
     }
-    // gate [W1; W3; -R1; -R3] on k: pass 0 -> dp, g1, g3; pass 1 -> dz1, dz3
+    // gate [W1; W3; -R1; -R3] on k: pass 0 -> dp, g1, g3, partials; pass 1 -> dz1, dz3
     GemmArgs a{};
     WIDE_MAP(tok_map(&a.a[0], prm.k, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 64) &&
              mat_map(&a.b[1], w3, F, D, 64) && mat_map(&a.b[2], r1, F, D, 64) && mat_map(&a.b[3], r3, F, D, 64));
     a.M = M; a.N = 4 * F; a.K = D; a.nbn = 4; a.ha = h; a.ya = (int)t0;
     a.ld_out = F; a.in0 = pb;
+    set_rates(a, prm, t0, h);
     if (pass == 0) {
-      a.epi = EPI_BKEY_MSE1; a.out[0] = dp; a.out[1] = g1; a.out[2] = g3;
+      a.epi = EPI_BKEY_MSE1; a.out[0] = dp; a.out[1] = g1; a.out[2] = g3; a.in1 = nb;
+      a.part = w.part; a.ld_part = deta_parts(sh, prm.lr_mat);
     } else {
       a.epi = EPI_BKEY_MSE2; a.out[0] = dz1; a.out[1] = dz3; a.in1 = du;
     }
@@ -1316,7 +1401,7 @@ cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBu
     a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
     WIDE_TRY(run_gemm(cx, a, mfd));
   }
-  {   // lam2 += E^T dP + dY^T U: one reduction over both token segments
+  {   // lam2 += e^T dP + dY^T U: one reduction over both token segments
     const int kseg = (M + BK - 1) / BK * BK;
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], eb, M, D, 64) && mat_map(&a.a[1], dy, M, D, 64) && mat_map(&a.b[0], dp, M, F, 64) &&
@@ -1335,9 +1420,11 @@ cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBu
 //   apply VJP of chunk j-1:   du = W2^T d_o, gate -> dzq1, dzq3, uq;
 //                             dq = dzq1 W1 + dzq3 W3;  lam += [dzq1^T Q, dzq3^T Q, d_O^T uq]
 //   update VJP of chunk j with R = dL/dW~_{j+1}:  praw = W2^T v, ndu = -R2^T v,
-//                             gate [W1; W3; -R1; -R3] -> dz1, dz3, g1, g3, -eta dp, -eta u, d eta;
-//                             dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3], dv = [-eta dp, -eta u] [W2^T; -R2^T];
-//                             lam += R + [dz1^T K, dz3^T K, V^T (-eta dp)]
+//                             gate [W1; W3; -R1; -R3] -> dz1, dz3, g1, g3, -dp, -eta2 u, d eta
+//                             (dp = eta1 dg1 z3 s' + eta3 dg3 a with dg = -R k);
+//                             dk = [dz1 dz3 g1 g3] [W1; W3; -R1; -R3], dv = [-dp, -eta2 u] [W2^T; -R2^T];
+//                             lam += R + [dz1^T K, dz3^T K, V^T (-dp)]
+//   (the squared-error loss: update_vjp_mse)
 //   normalisation VJP of update j-1 (R for the next step), or dW0 at j = 0.
 cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                           const LaunchFn& launch, cudaStream_t st) {
@@ -1347,14 +1434,14 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
   const int R = sh.R();
   WideBufs w;
   const bool mse = prm.loss == SCAL3R_LOSS_MSE;
-  layout_bytes(pl, sh, true, ckpt_every, mse, &w, ws);
+  layout_bytes(pl, sh, true, ckpt_every, mse, prm.lr_mat, &w, ws);
   const int nck = ckpt_every > 1 ? ckpt_every : 1;
   const int64_t T = pl.T;
   const size_t FD = (size_t)F * D;
   const __nv_bfloat16 *w1 = w.wb, *w3 = w.wb + FD, *w2 = w.wb + 2 * FD;
   const __nv_bfloat16 *r1 = w.nrb, *r3 = w.nrb + FD, *r2 = w.nrb + 2 * FD;   // -R
   float *lam1 = w.wm, *lam3 = w.wm + FD, *lam2 = w.wm + 2 * FD;
-  const int nparts = deta_parts(sh, mse);
+  const int nparts = deta_parts(sh, prm.lr_mat);
   for (int s = 0; s < pl.S; ++s) {
     for (int h = 0; h < H; ++h) {
       const float* w0 = prm.w0 + (size_t)s * prm.w0_seq_stride + (size_t)h * P;
@@ -1379,7 +1466,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
           return cudaGetLastError();
         }));
         for (int jj = j0; jj < j1; ++jj)
-          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.ex[0],
+          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.ex,
                               w.seg + (size_t)(jj - j0) * P, nullptr, nullptr));
       }
       for (int j = j1; j >= j0; --j) {
@@ -1439,11 +1526,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
           const int64_t t0 = pl.chunk_offsets[c];
           const int M = (int)(pl.chunk_offsets[c + 1] - t0);
           WIDE_TRY(update_vjp_mse(cx, h, t0, M, w, lam1, lam3, lam2));
-          WIDE_TRY(launch(1, 0, 0, [&] {
-            wide_deta_kernel<<<(M + 127) / 128, 128, 0, st>>>(w.part, nparts, nparts, prm.dlr + (size_t)t0 * H + h,
-                                                               H, M);
-            return cudaGetLastError();
-          }));
+          WIDE_TRY(chunk_deta(cx, w.part, t0, h, M));
         } else if (key) {   // update VJP of chunk j
           const int c = c0 + j;
           const int64_t t0 = pl.chunk_offsets[c];
@@ -1468,7 +1551,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             a.epi = EPI_BKEY;
             a.out[0] = dz1; a.out[1] = dz3; a.out[2] = g1; a.out[3] = g3; a.out[4] = dpe; a.out[5] = ue;
             a.ld_out = F; a.in0 = pr; a.in1 = nd;
-            a.eta = prm.lr + (size_t)t0 * H + h; a.eta_stride = H;
+            set_rates(a, prm, t0, h);
             a.part = w.part; a.ld_part = nparts;
             WIDE_TRY(run_gemm(cx, a, 4 * mfd));
           }
@@ -1483,7 +1566,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             a.ld_out = (int64_t)H * D;
             WIDE_TRY(run_gemm(cx, a, 4 * mfd));
           }
-          {   // dv = [-eta dp, -eta u] [W2^T; -R2^T]
+          {   // dv = [-dp, -eta2 u] [W2^T; -R2^T]
             GemmArgs a{};
             WIDE_MAP(mat_map(&a.a[0], dpe, M, F, 128) && mat_map(&a.a[1], ue, M, F, 128) &&
                      mat_map(&a.b[0], w2, D, F, 256) && mat_map(&a.b[1], r2, D, F, 256));
@@ -1499,18 +1582,14 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
             WIDE_TRY(run_gemm(cx, a, mfd));
           }
-          {   // lam2 += V^T (-eta dp)
+          {   // lam2 += V^T (-dp)
             GemmArgs a{};
             WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], dpe, M, F, 64));
             a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
             a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
             WIDE_TRY(run_gemm(cx, a, mfd));
           }
-          WIDE_TRY(launch(1, 0, 0, [&] {
-            wide_deta_kernel<<<(M + 127) / 128, 128, 0, st>>>(w.part, nparts, nparts, prm.dlr + (size_t)t0 * H + h,
-                                                               H, M);
-            return cudaGetLastError();
-          }));
+          WIDE_TRY(chunk_deta(cx, w.part, t0, h, M));
         }
         // normalisation VJP of update j-1 -> R, or dW0
         const float* wn = (j >= 1) ? prm.wnorm_in + ((size_t)(c0 + j - 1) * H + h) * R : nullptr;

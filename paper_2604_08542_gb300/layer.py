@@ -3,7 +3,7 @@
 Only argument marshalling happens here (shape/dtype checks, output and
 workspace allocation, the current CUDA stream); the computation is the
 library's.  Layouts follow the C header: q, k, v, o [T, H, D]; lr [T, H]
-float32; w0 [H, 3*F*D] (shared) or [S, H, 3*F*D] (per sequence) float32,
+float32 ([T, H, 3] with per-matrix rates: W1, W3, W2); w0 [H, 3*F*D] (shared) or [S, H, 3*F*D] (per sequence) float32,
 packed W1 [F, D], W3 [F, D], W2 [D, F]; chunk_offsets [C+1] int64 and
 seq_chunk_ptr [S+1] int32 on the host.
 """
@@ -36,14 +36,16 @@ class TTT:
 
     def __init__(self, num_heads: int, head_dim: int = 64, hidden_dim: int = 128,
                  dtype: torch.dtype = torch.bfloat16, loss: str = "dot", weight_norm: str = "row_w0",
-                 norm_eps: float = 1e-6, ckpt_every: int = 1):
+                 norm_eps: float = 1e-6, ckpt_every: int = 1, lr_per_matrix: bool = False):
         if dtype not in (torch.bfloat16, torch.float32):
             raise ValueError("dtype must be torch.bfloat16 or torch.float32")
         self.H, self.D, self.F = num_heads, head_dim, hidden_dim
         self.dtype = dtype
         self.cfg = scal3r_ttt_config(num_heads, head_dim, hidden_dim,
                                      SCAL3R_BF16 if dtype == torch.bfloat16 else SCAL3R_FP32,
-                                     LOSSES[loss], NORMS[weight_norm], float(norm_eps), int(ckpt_every))
+                                     LOSSES[loss], NORMS[weight_norm], float(norm_eps), int(ckpt_every),
+                                     int(bool(lr_per_matrix)))
+        self.lr_shape = (num_heads, 3) if lr_per_matrix else (num_heads,)
         self.handle = scal3r_ttt_init(self.cfg)
         self._ws = None
 
@@ -76,6 +78,10 @@ class TTT:
             self._ws = torch.empty(max(n, 256), dtype=torch.uint8, device=device)
         return self._ws
 
+    def _check_lr(self, lr, T):
+        if lr.dtype != torch.float32 or tuple(lr.shape) != (T, *self.lr_shape) or not lr.is_contiguous():
+            raise ValueError(f"lr must be a contiguous float32 tensor of shape {[T, *self.lr_shape]}")
+
     def _check_tokens(self, name, t, T):
         if t.dtype != self.dtype or t.dim() != 3 or tuple(t.shape) != (T, self.H, self.D) or not t.is_cuda \
                 or not t.is_contiguous():
@@ -98,8 +104,7 @@ class TTT:
         T, C, S = int(off[-1]), len(off) - 1, len(ptr) - 1
         for n, t in (("q", q), ("k", k), ("v", v)):
             self._check_tokens(n, t, T)
-        if lr.dtype != torch.float32 or tuple(lr.shape) != (T, self.H) or not lr.is_contiguous():
-            raise ValueError("lr must be a contiguous float32 tensor of shape [T, H]")
+        self._check_lr(lr, T)
         stride = self._w0_stride(w0, S)
         dev = q.device
         o = torch.empty_like(q) if o is None else o
@@ -120,6 +125,7 @@ class TTT:
         T, S = int(off[-1]), len(ptr) - 1
         for n, t in (("q", q), ("k", k), ("v", v), ("d_o", d_o)):
             self._check_tokens(n, t, T)
+        self._check_lr(lr, T)
         stride = self._w0_stride(w0, S)
         dq, dk, dv = torch.empty_like(q), torch.empty_like(k), torch.empty_like(v)
         dlr = torch.empty_like(lr)
@@ -141,8 +147,7 @@ class TTT:
         T, S = int(off[-1]), len(ptr) - 1
         for n, t in (("k", k), ("v", v)):
             self._check_tokens(n, t, T)
-        if lr.dtype != torch.float32 or tuple(lr.shape) != (T, self.H) or not lr.is_contiguous():
-            raise ValueError("lr must be a contiguous float32 tensor of shape [T, H]")
+        self._check_lr(lr, T)
         stride = self._w0_stride(w, S)
         grad = torch.empty((S, self.H, self.P), dtype=torch.float32, device=k.device)
         ws = self.workspace(off, ptr, False, k.device) if workspace is None else workspace

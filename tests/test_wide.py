@@ -226,3 +226,59 @@ def test_wide_mse_sparse_checkpoints_are_bitwise_the_dense_ones():
         res.append((o, wn, *grads))
     for a, b in zip(*res):
         assert torch.equal(a, b)
+
+
+# ---- per-matrix learning rates (lr [T, H, 3]: W1, W3, W2) ----
+
+@pytest.mark.parametrize("loss", ["dot", "mse"])
+def test_wide_per_matrix_rates_match_oracle(loss):
+    """Forward outputs and every gradient (dlr [T, H, 3]) with a rate per
+    matrix, both losses, two heads and ragged chunks."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F = 2, 256, 512
+    lengths = [[300, 129], [77]]
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=71, dtype="bf16", with_grad_out=True)
+    x["lr"] = syn.per_matrix_lr(72, lay.num_tokens, H, lr_max=0.1)
+    g = upload(x, torch.bfloat16)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, loss=loss, lr_per_matrix=True)
+    o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                                  want_final=True)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, loss=loss, eps=1e-6)
+    _check((o, ck, wn, wf), ref)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, loss=loss, eps=1e-6)
+    assert tuple(grads[3].shape) == x["lr"].shape
+    _check_grads(grads, rb)
+
+
+def test_wide_equal_per_matrix_rates_match_one_rate():
+    """Three equal rates per token give the one-rate layer's outputs (up to
+    the kernels' rounding order) and d eta split three ways."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F = 1, 512, 1024
+    lengths = [[260, 200]]
+    lay = syn.layout_from_lengths(lengths)
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=73, dtype="bf16", with_grad_out=True)
+    g = upload(x, torch.bfloat16)
+    res = []
+    for per in (False, True):
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, lr_per_matrix=per)
+        lr = g["lr"][..., None].expand(-1, -1, 3).contiguous() if per else g["lr"]
+        o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], lr, g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+        grads = layer.backward(g["q"], g["k"], g["v"], lr, g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        res.append((o, ck, grads))
+    (o1, ck1, g1), (o3, ck3, g3) = res
+    assert rel_inf(to_np(o3), to_np(o1)) < 5e-3
+    assert rel_inf(to_np(ck3), to_np(ck1)) < 1e-4
+    for n, a, b in zip(("dq", "dk", "dv", "dw0"), (g1[0], g1[1], g1[2], g1[4]), (g3[0], g3[1], g3[2], g3[4])):
+        assert rel_inf(to_np(b), to_np(a)) < 5e-3, n
+    assert rel_inf(to_np(g3[3]).sum(-1), to_np(g1[3])) < 5e-3
