@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fwd-only", action="store_true", help="a step is the forward pass alone")
     ap.add_argument("--no-amu", action="store_true", help="skip the paper-shape (hd 1024) forward line")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the paper-shape lines of the layer's options (MSE, per-matrix rates, sparse "
+                         "checkpoints, GCM, GCS split loop)")
     ap.add_argument("--amu-only", action="store_true",
                     help="run only the paper-shape forward (two direct forwards first: 33 launches each)")
     ap.add_argument("--amu-fwdbwd-twice", action="store_true",
@@ -296,6 +299,119 @@ def amu_leg(args, dev, peak_tflops):
     return out
 
 
+def amu_variants(args, dev, peak_tflops):
+    """Forward+backward at the paper's AMU shape (workload bf16_amu1024) for the
+    layer's options: the squared-error loss, per-matrix learning rates, sparse
+    checkpoints (every 4th chunk), the GCM module around the layer, and the
+    forward as the Global Context Synchronisation split loop (partial
+    gradient, update, apply per chunk; one shard, so no collective).  Each:
+    tokens/s over the timed steps (L2 flushed between steps) and the GEMM rate
+    from the library's per-launch events (executed FLOPs)."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    from paper_2604_08542_gb300.gcm import GCM
+    w = syn.workload("bf16_amu1024")
+    lay = w.layout()
+    T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
+    off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(args.seed + 91)
+
+    def unit_rows():
+        x = torch.randn((T, H, D), generator=gen, device=dev)
+        return (x / x.norm(dim=-1, keepdim=True)).to(torch.bfloat16)
+
+    q, k, v = unit_rows(), unit_rows(), unit_rows()
+    lr1 = torch.rand((T, H), generator=gen, device=dev) * 0.1
+    lr3 = torch.rand((T, H, 3), generator=gen, device=dev) * 0.1
+    w0 = torch.randn((H, 3 * F * D), generator=gen, device=dev) * 0.125
+    d_o = torch.randn((T, H, D), generator=gen, device=dev).to(torch.bfloat16)
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps = max(3, args.steps // 4)
+
+    def timed(fn, layer):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ttt.scal3r_ttt_profile_enable(layer.handle, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        prof = {ttt.KERNEL_KINDS[kk]: ttt.scal3r_ttt_profile_read(layer.handle, kk) for kk in ttt.KERNEL_KINDS}
+        ttt.scal3r_ttt_profile_enable(layer.handle, False)
+        assert layer.status() == 0
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        gemm = [prof[n] for n in ("fwd_sweep", "bwd_sweep")]
+        fl, gms = sum(g["flops"] for g in gemm), sum(g["ms"] for g in gemm)
+        tf = fl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
+        oth = prof["other"]
+        return {"tokens_per_s": T / (ms / 1e3), "ms_per_step": ms, "gemm_tflops_executed": tf,
+                "gemm_frac_of_bf16_peak": tf / peak_tflops,
+                "layer_gemm_ms_per_step": gms / steps, "other_ms_per_step": oth["ms"] / steps,
+                "other_tflops": oth["flops"] / (oth["ms"] / 1e3) / 1e12 if oth["ms"] > 0 else 0.0}
+
+    out = {"workload": w.name, "timing": "direct launches, event pair per step, 256 MB written between steps; "
+                                         "GEMM rate from per-launch events (the profiler on)"}
+
+    def layer_fwd_bwd(layer, lr):
+        ws = torch.empty(ttt.scal3r_ttt_workspace_size(layer.handle, off, ptr, True), dtype=torch.uint8, device=dev)
+        o = torch.empty_like(q)
+
+        def fn():
+            _, ck, wn, _ = layer.forward(q, k, v, lr, w0, off, ptr, workspace=ws, o=o)
+            layer.backward(q, k, v, lr, w0, off, ptr, d_o, ck, wn, workspace=ws)
+        return fn
+
+    for name, kw, lr in (("mse_fwdbwd", {"loss": "mse"}, lr1), ("per_matrix_lr_fwdbwd", {"lr_per_matrix": True}, lr3),
+                         ("ckpt_every4_fwdbwd", {"ckpt_every": 4}, lr1)):
+        layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, **kw)
+        out[name] = timed(layer_fwd_bwd(layer, lr), layer)
+        if name.startswith("ckpt"):
+            slots = ttt.scal3r_ttt_ckpt_slots(layer.handle, ptr)
+            out[name]["checkpoint_bytes"] = slots * H * 3 * F * D * 4
+            out[name]["dense_checkpoint_bytes"] = (len(off) - 1) * H * 3 * F * D * 4
+        layer.close()
+
+    # the GCM module (Eq. 5) around the layer: d = H * D
+    d = H * D
+    gcm = GCM(H, D, F)
+    x = torch.randn((T, d), generator=gen, device=dev).to(torch.bfloat16)
+    prm = {"wqkv": (torch.randn((3 * d, d), generator=gen, device=dev) / d ** 0.5).to(torch.bfloat16),
+           "bqkv": torch.zeros(3 * d, device=dev), "w_eta": torch.randn((H, d), generator=gen, device=dev) / d ** 0.5,
+           "b_eta": torch.zeros(H, device=dev),
+           "wo": (torch.randn((d, d), generator=gen, device=dev) / d ** 0.5).to(torch.bfloat16),
+           "alpha": torch.full((d,), 0.5, device=dev)}
+    d_out = torch.randn((T, d), generator=gen, device=dev).to(torch.bfloat16)
+
+    def gcm_step():
+        y, saved = gcm.forward(x, prm["wqkv"], prm["bqkv"], prm["w_eta"], prm["b_eta"], prm["wo"], prm["alpha"], w0,
+                               off, ptr)
+        gcm.backward(saved, d_out)
+    out["gcm_fwdbwd"] = timed(gcm_step, gcm.ttt)
+
+    # Global Context Synchronisation split loop, forward (one shard per chunk)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    bounds = [(int(off[c]), int(off[c + 1])) for c in range(len(off) - 1)]
+    one = [syn.layout_from_lengths([[b - a]]) for a, b in bounds]
+    wsg = layer.workspace(one[0].chunk_offsets, one[0].seq_chunk_ptr, False, dev)
+    o = torch.empty_like(q)
+
+    def gcs_fwd():
+        wcur = w0
+        for (a, b), lo in zip(bounds, one):
+            g = layer.partial_grad(k[a:b], v[a:b], lr1[a:b], wcur, lo.chunk_offsets, lo.seq_chunk_ptr, workspace=wsg)
+            wcur, _ = layer.apply_update(wcur, g, w0)
+            o[a:b] = layer.apply(q[a:b], wcur, lo.chunk_offsets, lo.seq_chunk_ptr, workspace=wsg)
+    out["gcs_split_fwd"] = timed(gcs_fwd, layer)
+    layer.close()
+    return out
+
+
 def run_gpu(args, rank: int, world: int):
     import torch
     import paper_2604_08542_gb300 as ttt
@@ -485,6 +601,8 @@ def run_gpu(args, rank: int, world: int):
     amu = None
     if not args.no_amu and rank == 0 and not args.fwd_only and world == 1:
         amu = amu_leg(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+        if not args.no_variants:
+            amu["variants"] = amu_variants(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
 
     cpu = None
     if not args.no_cpu:
@@ -537,7 +655,11 @@ def main():
         builder.build()
         pk, _ = peaks()
         dev = torch.device("cuda", torch.cuda.current_device())
-        print(json.dumps({"paper_amu": amu_leg(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))}))
+        pt = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+        amu = amu_leg(args, dev, pt)
+        if not args.no_variants and not args.amu_fwdbwd_twice:
+            amu["variants"] = amu_variants(args, dev, pt)
+        print(json.dumps({"paper_amu": amu}))
         return
     if world > 1:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
