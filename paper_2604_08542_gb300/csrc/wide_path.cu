@@ -1138,6 +1138,9 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
         return cudaGetLastError();
       }));
       const int c0 = pl.seq_chunk_ptr[s], c1 = pl.seq_chunk_ptr[s + 1];
+      if (c1 == c0 && prm.w_final)   // a sequence without chunks keeps its initial weights
+        WIDE_TRY(cudaMemcpyAsync(prm.w_final + ((size_t)s * H + h) * P, w0, P * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st));
       for (int c = c0; c < c1; ++c) {
         const int64_t t0 = pl.chunk_offsets[c], t1 = pl.chunk_offsets[c + 1];
         const int M = (int)(t1 - t0);

@@ -282,3 +282,69 @@ def test_wide_equal_per_matrix_rates_match_one_rate():
     for n, a, b in zip(("dq", "dk", "dv", "dw0"), (g1[0], g1[1], g1[2], g1[4]), (g3[0], g3[1], g3[2], g3[4])):
         assert rel_inf(to_np(b), to_np(a)) < 5e-3, n
     assert rel_inf(to_np(g3[3]).sum(-1), to_np(g1[3])) < 5e-3
+
+
+# ---- edge cases and the full-size paper workload ----
+
+def test_wide_tiny_and_empty_chunks_match_oracle():
+    """Chunks of 1, 63 and 65 tokens, an empty sequence and tile edges (127, 129)
+    at the smallest wide shape (hd 256, hidden 256), forward and backward."""
+    H, D, F = 2, 256, 256
+    lengths = [[1, 63, 65], [], [129, 127]]
+    _, lay, x, out = _run(H, D, F, lengths, seed=81)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+    _, lay, x, grads = _fwd_bwd(H, D, F, lengths, seed=82)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+@pytest.mark.parametrize("D,F", [(4096, 256), (256, 4096)])
+def test_wide_largest_dims_match_oracle(D, F):
+    """The largest head_dim and the largest hidden size the path takes."""
+    _, lay, x, grads = _fwd_bwd(1, D, F, [[200, 90]], seed=83)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+def test_wide_lr_zero_gives_plain_mlp():
+    """With every learning rate 0 the weights never move: o = f_W0(q) and every
+    checkpoint equals W0 (exactly, the row rescale of an unchanged row aside)."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    H, D, F = 1, 512, 1024
+    lay = syn.layout_from_lengths([[300, 212]])
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=84, dtype="bf16")
+    x["lr"][:] = 0.0
+    g = upload(x, torch.bfloat16)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    o, ck, _, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    W0 = oracle.unpack(x["w0"][0].astype(np.float64), D, F)
+    ref = oracle.apply(W0, x["q"][:, 0].astype(np.float64))
+    assert rel_inf(to_np(o)[:, 0], ref) <= TOL
+    assert rel_inf(to_np(ck)[:, 0], np.stack([x["w0"][0]] * 2)) <= 1e-6
+
+
+def test_wide_amu_full_size_graph_matches_oracle():
+    """The paper-shape bench workload at full size (66,624 tokens, one head,
+    hd 1024, hidden 4096, four chunks of 16,656 tokens) in graph mode, the
+    launch configuration the benchmark times: o, every checkpoint and the
+    pre-normalisation row norms against the oracle."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    w = syn.workload("bf16_amu1024")
+    lay = w.layout()
+    T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
+    x = syn.make_inputs(T, H, D, F, seed=85, dtype="bf16")
+    g = upload(x, torch.bfloat16)
+    layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)
+    layer.set_graph_mode(True)
+    for _ in range(2):
+        out = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                            want_final=True)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
