@@ -88,12 +88,21 @@ __device__ __forceinline__ float silu_d(float z, float& sg) {
   return z * sg;
 }
 
-// Packs 16 floats to 8 bf16x2 words and stores them (two 16-byte stores).
+// One 32-byte store of eight 32-bit words (dst 32-byte aligned).  Each thread
+// of an epilogue writes its own row, so a warp's store touches 32 rows: the
+// wider store halves the transactions per byte.
+__device__ __forceinline__ void st_global_v8(void* dst, const uint32_t (&a)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :: "l"(dst), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7])
+               : "memory");
+}
+
+// Packs 16 floats to 8 bf16x2 words and stores them (one 32-byte store).
 __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float* v) {
-  uint4* o = reinterpret_cast<uint4*>(dst);
-  o[0] = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-  o[1] = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                    pack_bf16(v[14], v[15]));
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) w[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+  st_global_v8(dst, w);
 }
 
 // Four 8-column TMEM loads (z1, z3, dg1, dg3 of the same rows) and one wait.
@@ -147,8 +156,8 @@ __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* 
 // the MMA warp alternates between two 256-column accumulators; epilogue group
 // g (four warps, all 128 TMEM lanes) drains the tiles of accumulator g, so a
 // tile's epilogue overlaps the next tile's MMAs.
-// XSET: the squared-error loss's epilogues, in their own instantiation so that
-// the common ones keep their register allocation.
+// XSET: the update-VJP gate and the squared-error loss's epilogues, in their own
+// instantiation so that the common ones keep their register allocation.
 // The three learning rates of output row m (W1, W3, W2).
 __device__ __forceinline__ void row_rates(const GemmArgs& g, int m, float& e1, float& e3, float& e2) {
   const float* ep = g.eta + (size_t)m * g.eta_stride;
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       const int m0 = tm * BM, n0 = tn * BN;
       const int m = m0 + (int)row;
       const bool valid = m < g.M;
-      if (XSET) {
+      if (XSET && g.epi != EPI_BKEY) {
         float e1 = 0.f, e3 = 0.f, e2 = 0.f;
         if (g.eta && valid) row_rates(g, m, e1, e3, e2);
         if (g.epi == EPI_MSE_E || g.epi == EPI_ADD_BF16 || g.epi == EPI_MSE_DE) {
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
 #pragma unroll 1
           for (int c = 0; c < 64; c += 8) {
             uint4 pw = make_uint4(0, 0, 0, 0), uw = pw;
-            if (valid) {
+            if (valid) {   // in flight during the TMEM loads
               pw = __ldg(pp + c / 8);
               uw = __ldg(up + c / 8);
             }
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           }
           if (!second && valid) store_deta(g, m, tn, q1, q3, q2);
         }
-      } else if (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD) {
+      } else if (!XSET && (g.epi == EPI_F32 || g.epi == EPI_BF16 || g.epi == EPI_F32_ADD)) {
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           float v0[16], v1[16];
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             }
           }
         }
-      } else if (g.epi == EPI_BKEY) {
+      } else if (XSET) {   // EPI_BKEY
         // columns [0,64) z1, [64,128) z3, [128,192) dg1, [192,256) dg3 of
         // hidden units f0 .. f0 + 63 (dg = -R k)
         const int f0 = tn * (BN / 4);
@@ -431,45 +440,55 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
         const uint4* np = reinterpret_cast<const uint4*>(g.in1 + (size_t)m * g.ld_out + f0);
 #pragma unroll 1
-        for (int c = 0; c < 64; c += 8) {
-          uint4 pw = make_uint4(0, 0, 0, 0), nw = pw;
-          if (valid) {   // in flight during the TMEM loads
-            pw = __ldg(pp + c / 8);
-            nw = __ldg(np + c / 8);
-          }
-          float zz[4][8];
-          tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
-          if (!valid) continue;
-          float praw[8], ndu[8];
-          unpack8(pw, praw);
-          unpack8(nw, ndu);
-          float o[6][8];
+        for (int c = 0; c < 64; c += 16) {
+          uint4 pcur[2], ncur[2];   // the inputs of the 16 columns, in flight during the TMEM loads
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            float sg;
-            const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
-            const float a = silu_d(x1, sg);
-            const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
-            const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);    // silu''(z1)
-            const float u = a * x3;
-            const float p1 = -e1 * praw[e], p3 = -e3 * praw[e];   // rate times p (e = -v)
-            const float du = -e2 * ndu[e];
-            const float t1 = d1 * x3 * sp;
-            const float da = d3 * p3 + du * x3;
-            o[1][e] = d1 * p1 * sp + du * a;                 // dz3
-            o[0][e] = d1 * p1 * x3 * spp + da * sp;          // dz1
-            o[2][e] = p1 * x3 * sp;                          // g1
-            o[3][e] = p3 * a;                                // g3
-            o[4][e] = -(e1 * t1 + e3 * d3 * a);              // -dp
-            o[5][e] = -e2 * u;                               // -eta2 u
-            q1 = fmaf(-praw[e], t1, q1);
-            q3 = fmaf(-praw[e] * a, d3, q3);
-            q2 = fmaf(-ndu[e], u, q2);
+          for (int j = 0; j < 2; ++j) {
+            pcur[j] = valid ? __ldg(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
+            ncur[j] = valid ? __ldg(np + c / 8 + j) : make_uint4(0, 0, 0, 0);
           }
-          const size_t off = (size_t)m * g.ld_out + f0 + c;
+          uint32_t pk[6][8];   // 16 columns of each output, packed bf16 pairs
 #pragma unroll
-          for (int q = 0; q < 6; ++q)
-            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
+          for (int hh = 0; hh < 2; ++hh) {
+            const int cc = c + 8 * hh;
+            float zz[4][8];
+            tmem_ld8x4(accb + cc, accb + 64 + cc, accb + 128 + cc, accb + 192 + cc, zz);
+            float praw[8], ndu[8];
+            unpack8(pcur[hh], praw);
+            unpack8(ncur[hh], ndu);
+            float o[6][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              float sg;
+              const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
+              const float a = silu_d(x1, sg);
+              const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
+              const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);    // silu''(z1)
+              const float u = a * x3;
+              const float p1 = -e1 * praw[e], p3 = -e3 * praw[e];   // rate times p (e = -v)
+              const float du = -e2 * ndu[e];
+              const float t1 = d1 * x3 * sp;
+              const float da = d3 * p3 + du * x3;
+              o[1][e] = d1 * p1 * sp + du * a;                 // dz3
+              o[0][e] = d1 * p1 * x3 * spp + da * sp;          // dz1
+              o[2][e] = p1 * x3 * sp;                          // g1
+              o[3][e] = p3 * a;                                // g3
+              o[4][e] = -(e1 * t1 + e3 * d3 * a);              // -dp
+              o[5][e] = -e2 * u;                               // -eta2 u
+              q1 = fmaf(-praw[e], t1, q1);
+              q3 = fmaf(-praw[e] * a, d3, q3);
+              q2 = fmaf(-ndu[e], u, q2);
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) pk[q][4 * hh + i] = pack_bf16(o[q][2 * i], o[q][2 * i + 1]);
+          }
+          if (valid) {
+            const size_t off = (size_t)m * g.ld_out + f0 + c;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off, pk[q]);
+          }
         }
         if (valid) store_deta(g, m, tn, q1, q3, q2);
       } else {
@@ -864,7 +883,7 @@ cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   if (a.nseg > 1 && (a.kseg % BK != 0 || a.kseg * a.nseg != a.K || a.nbn != 1)) return cudaErrorInvalidValue;
   const int tiles = ((a.M + BM - 1) / BM) * (a.N / BN);
   const int grid = std::min(tiles, num_sms());
-  if (a.epi >= EPI_MSE_E)
+  if (a.epi >= EPI_MSE_E || a.epi == EPI_BKEY)
     wide_gemm_kernel<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   else
     wide_gemm_kernel<false><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
