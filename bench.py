@@ -67,6 +67,8 @@ def parse():
                          "checkpoints, GCM, GCS split loop)")
     ap.add_argument("--amu-only", action="store_true",
                     help="run only the paper-shape forward (two direct forwards first: 33 launches each)")
+    ap.add_argument("--amu-small", action="store_true",
+                    help="with --amu-only: two chunks of 16,656 tokens instead of four (profiler captures)")
     ap.add_argument("--amu-fwdbwd-twice", action="store_true",
                     help="with --amu-only: run two direct forward+backward steps and exit (104 launches each)")
     return ap.parse_args()
@@ -203,6 +205,9 @@ def amu_leg(args, dev, peak_tflops):
     import paper_2604_08542_gb300 as ttt
     w = syn.workload("bf16_amu1024")
     lay = w.layout()
+    if args.amu_small:   # two of the workload's chunks (profiler captures)
+        n = int(lay.chunk_offsets[1])
+        lay = syn.layout_from_lengths([[n, n]])
     T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
     off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
     gen = torch.Generator(device=dev)

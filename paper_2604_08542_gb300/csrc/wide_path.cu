@@ -361,45 +361,56 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           const bool second = g.epi == EPI_BKEY_MSE2;
           float q1 = 0.f, q3 = 0.f, q2 = 0.f;
 #pragma unroll 1
-          for (int c = 0; c < 64; c += 8) {
-            uint4 pw = make_uint4(0, 0, 0, 0), uw = pw;
-            if (valid) {   // in flight during the TMEM loads
-              pw = __ldg(pp + c / 8);
-              uw = __ldg(up + c / 8);
-            }
-            float zz[4][8];
-            tmem_ld8x4(accb + c, accb + 64 + c, accb + 128 + c, accb + 192 + c, zz);
-            if (!valid) continue;
-            float pv[8], w[8];
-            unpack8(pw, pv);
-            unpack8(uw, w);
-            float o[3][8];
+          for (int c = 0; c < 64; c += 16) {
+            uint4 pw[2], uw[2];   // the inputs of the 16 columns, in flight during the TMEM loads
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              float sg;
-              const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
-              const float a = silu_d(x1, sg);
-              const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
-              const float t1 = d1 * x3 * sp;
-              if (!second) {                                       // w = -R2^T e
-                o[0][e] = e1 * t1 + e3 * d3 * a;                   // dp
-                o[1][e] = e1 * pv[e] * x3 * sp;                    // g1
-                o[2][e] = e3 * pv[e] * a;                          // g3
-                q1 = fmaf(pv[e], t1, q1);
-                q3 = fmaf(pv[e] * a, d3, q3);
-                q2 = fmaf(w[e], a * x3, q2);
-              } else {                                             // w = du
-                const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);  // silu''(z1)
-                const float da = e3 * d3 * pv[e] + w[e] * x3;
-                o[1][e] = e1 * d1 * pv[e] * sp + w[e] * a;         // dz3
-                o[0][e] = e1 * d1 * pv[e] * x3 * spp + da * sp;    // dz1
+            for (int j = 0; j < 2; ++j) {
+              pw[j] = valid ? __ldg(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
+              uw[j] = valid ? __ldg(up + c / 8 + j) : make_uint4(0, 0, 0, 0);
+            }
+            uint32_t pk[3][8];   // 16 columns of each output, packed bf16 pairs
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int cc = c + 8 * hh;
+              float zz[4][8];
+              tmem_ld8x4(accb + cc, accb + 64 + cc, accb + 128 + cc, accb + 192 + cc, zz);
+              float pv[8], w[8];
+              unpack8(pw[hh], pv);
+              unpack8(uw[hh], w);
+              float o[3][8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                float sg;
+                const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
+                const float a = silu_d(x1, sg);
+                const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
+                const float t1 = d1 * x3 * sp;
+                if (!second) {                                       // w = -R2^T e
+                  o[0][e] = e1 * t1 + e3 * d3 * a;                   // dp
+                  o[1][e] = e1 * pv[e] * x3 * sp;                    // g1
+                  o[2][e] = e3 * pv[e] * a;                          // g3
+                  q1 = fmaf(pv[e], t1, q1);
+                  q3 = fmaf(pv[e] * a, d3, q3);
+                  q2 = fmaf(w[e], a * x3, q2);
+                } else {                                             // w = du
+                  const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);  // silu''(z1)
+                  const float da = e3 * d3 * pv[e] + w[e] * x3;
+                  o[1][e] = e1 * d1 * pv[e] * sp + w[e] * a;         // dz3
+                  o[0][e] = e1 * d1 * pv[e] * x3 * spp + da * sp;    // dz1
+                  o[2][e] = 0.f;
+                }
               }
-            }
-            const size_t off = (size_t)m * g.ld_out + f0 + c;
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-              if (q < (second ? 2 : 3))
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off) = pack8f(o[q]);
+              for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pk[q][4 * hh + i] = pack_bf16(o[q][2 * i], o[q][2 * i + 1]);
+            }
+            if (valid) {
+              const size_t off = (size_t)m * g.ld_out + f0 + c;
+#pragma unroll
+              for (int q = 0; q < 3; ++q)
+                if (q < (second ? 2 : 3)) st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off, pk[q]);
+            }
           }
           if (!second && valid) store_deta(g, m, tn, q1, q3, q2);
         }
