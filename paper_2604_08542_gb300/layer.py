@@ -98,7 +98,9 @@ class TTT:
 
     # -- passes ------------------------------------------------------------
     def forward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, *, save_for_backward=True,
-                want_final=False, workspace=None, o=None):
+                want_final=False, workspace=None, o=None, w_ckpt=None, wnorm=None):
+        """Returns (o, w_ckpt, wnorm, w_final).  o, w_ckpt and wnorm may be
+        given (preallocated, e.g. to keep a captured graph's pointers)."""
         off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
         ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
         T, C, S = int(off[-1]), len(off) - 1, len(ptr) - 1
@@ -109,8 +111,15 @@ class TTT:
         dev = q.device
         o = torch.empty_like(q) if o is None else o
         slots = C if self.cfg.ckpt_every <= 1 else scal3r_ttt_ckpt_slots(self.handle, ptr)
-        w_ckpt = torch.empty((slots, self.H, self.P), dtype=torch.float32, device=dev) if save_for_backward else None
-        wnorm = torch.empty((C, self.H, self.R), dtype=torch.float32, device=dev) if save_for_backward else None
+        if save_for_backward:
+            if w_ckpt is None:
+                w_ckpt = torch.empty((slots, self.H, self.P), dtype=torch.float32, device=dev)
+            if wnorm is None:
+                wnorm = torch.empty((C, self.H, self.R), dtype=torch.float32, device=dev)
+            if tuple(w_ckpt.shape) != (slots, self.H, self.P) or tuple(wnorm.shape) != (C, self.H, self.R):
+                raise ValueError("w_ckpt / wnorm have the wrong shape for this layout")
+        else:
+            w_ckpt = wnorm = None
         w_final = torch.empty((S, self.H, self.P), dtype=torch.float32, device=dev) if want_final else None
         ws = self.workspace(off, ptr, False, dev) if workspace is None else workspace
         st = torch.cuda.current_stream(dev).cuda_stream
@@ -119,7 +128,9 @@ class TTT:
         _check(rc, "scal3r_ttt_forward")
         return o, w_ckpt, wnorm, w_final
 
-    def backward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, d_o, w_ckpt, wnorm, *, workspace=None):
+    def backward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, d_o, w_ckpt, wnorm, *, workspace=None,
+                 out=None):
+        """Returns (dq, dk, dv, dlr, dw0); ``out`` may give them preallocated."""
         off = np.ascontiguousarray(chunk_offsets, dtype=np.int64)
         ptr = np.ascontiguousarray(seq_chunk_ptr, dtype=np.int32)
         T, S = int(off[-1]), len(ptr) - 1
@@ -127,9 +138,13 @@ class TTT:
             self._check_tokens(n, t, T)
         self._check_lr(lr, T)
         stride = self._w0_stride(w0, S)
-        dq, dk, dv = torch.empty_like(q), torch.empty_like(k), torch.empty_like(v)
-        dlr = torch.empty_like(lr)
-        dw0 = torch.empty_like(w0)
+        if out is None:
+            dq, dk, dv, dlr, dw0 = (torch.empty_like(t) for t in (q, k, v, lr, w0))
+        else:
+            dq, dk, dv, dlr, dw0 = out
+            for a, b in zip(out, (q, k, v, lr, w0)):
+                if a.shape != b.shape or a.dtype != b.dtype or not a.is_contiguous():
+                    raise ValueError("out tensors must match q, k, v, lr, w0")
         ws = self.workspace(off, ptr, True, q.device) if workspace is None else workspace
         st = torch.cuda.current_stream(q.device).cuda_stream
         rc = scal3r_ttt_backward(self.handle, _ptr(q), _ptr(k), _ptr(v), _ptr(lr), _ptr(w0), stride, off, ptr,
