@@ -1,23 +1,31 @@
-// BF16 tensor-core forward for wide fast weights: the paper's own AMU shape
+// BF16 tensor-core path for wide fast weights: the paper's own AMU shape
 // (one head, hd = 1024, hidden = k * hd, Supp. "Global Context Memory module")
-// and any head_dim that is a multiple of 128 with hidden a multiple of 256.
+// and any head_dim and hidden that are multiples of 256 (up to 4096).
 //
 // At these sizes a chain's fast weights (3 * F * D values, 50 MB in float32 at
 // D = 1024, F = 4096) do not fit on chip, and every product of the chunk step
 // is a large GEMM.  One chunk step (Eq. 8, dot loss Eq. 9, then Eq. 4) of
 // chain (s, h), tokens of the chunk t in [t0, t1), M = t1 - t0, is
-//   P  = V W2                        [M x F]   (p = W2^T e = -eta P, e = -eta v)
+//   P  = V W2                        [M x F]   (p = W2^T e, e = -v)
 //   Z1 = K W1^T, Z3 = K W3^T         [M x F]   -> per (t, f): a = z1 sigmoid(z1),
-//        g1 = p z3 s'(z1), g3 = p a, u~ = -eta a z3          (epilogue, bf16 out)
+//        g1 = -eta1 P z3 s'(z1), g3 = -eta3 P a, u~ = -eta2 a z3   (epilogue, bf16 out)
 //   G1 = g1^T K, G3 = g3^T K         [F x D],  G2 = V^T u~   [D x F]
 //   W <- W - G, rows rescaled (row norm targets of W0)       (wide_update_kernel)
 //   O  = (silu(Q W1^T) o (Q W3^T)) W2^T                      (two GEMMs)
+// with one learning rate per token (eta1 = eta3 = eta2) or one per matrix.
+// The squared-error loss (key_grad_mse), the backward through the chunk
+// loop (wide_backward, update_vjp_mse), the Global Context Synchronisation
+// pieces (wide_partial_grad, wide_apply_update, wide_apply) and the plain
+// GEMM of the C ABI (wide_gemm_bf16) are built from the same GEMM kernel.
+//
 // All GEMMs run on one persistent tcgen05 kernel: 128 x 256 output tiles, K
 // in steps of 64 through a four-stage TMA pipeline (128-byte swizzle, either
 // operand K- or MN-major), one elected thread of a converged warp issuing
 // M128 N256 K16 MMAs into two 256-column TMEM accumulators in turn, and two
-// groups of four epilogue warps (TMEM lane = output row), one per accumulator.  The Z1/Z3 GEMMs read W1 and W3 rows of the same 128 hidden
-// units into one N = 256 operand, so one tile holds both halves of the gate.
+// groups of four epilogue warps (TMEM lane = output row), one per accumulator.
+// The gate GEMMs read W1 and W3 rows (and -R1, -R3 in the backward) of the same
+// hidden units into one N = 256 operand, so one tile holds every half of the
+// gate.  Epilogues store 32 bytes per thread and row.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
