@@ -39,10 +39,22 @@ extern "C" {
  *     accumulate = 1 adds to C) or bf16 (out_fp32 = 0).
  * N must be a multiple of 256; M, K >= 1 (ragged edges read zeros); lda, ldb
  * multiples of 8; every pointer 16-byte aligned.  SCAL3R_ERR_UNSUPPORTED
- * otherwise.  The handle carries the status word and the profiler. */
+ * otherwise.  The handle carries the status word and the profiler.
+ * A float32-output product with fewer 128 x 256 output tiles than half the
+ * SMs (a weight gradient: small M and N, long K) runs in K ranges into
+ * float32 partial planes in `workspace`, then sums them in a fixed order:
+ * give scal3r_ttt_gemm_workspace_size bytes (device memory, 16-byte aligned,
+ * owned by the caller, not touched after the stream reaches the end of the
+ * call).  With a smaller or NULL workspace the product runs unsplit; the
+ * result is the same up to float32 rounding order, and bitwise reproducible
+ * either way. */
 int scal3r_ttt_gemm(scal3r_ttt_handle* handle, const void* a, int64_t lda, int32_t a_kmajor, const void* b,
                     int64_t ldb, int32_t b_kmajor, void* c, int64_t ldc, int32_t out_fp32, int32_t accumulate,
-                    int64_t M, int64_t N, int64_t K, void* stream);
+                    int64_t M, int64_t N, int64_t K, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of workspace scal3r_ttt_gemm uses for an M x N x K product (0: none). */
+int scal3r_ttt_gemm_workspace_size(scal3r_ttt_handle* handle, int64_t M, int64_t N, int64_t K, int32_t out_fp32,
+                                   size_t* bytes);
 
 /* Bytes of device scratch the two backward row steps need for T tokens. */
 int scal3r_gcm_workspace_size(scal3r_ttt_handle* handle, int64_t T, size_t* bytes);

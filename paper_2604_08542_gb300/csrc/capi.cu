@@ -19,8 +19,9 @@
 
 namespace scal3r {
 cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
-                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, int* status,
-                           cudaStream_t st);
+                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
+                           size_t ws_bytes, int* status, cudaStream_t st);
+size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32);
 size_t gcm_partial_bytes(int64_t T, int d, int H);
 bool gcm_heads_supported(int H);
 cudaError_t gcm_prep(const float* raw, const float* bqkv, const __nv_bfloat16* x, const float* w_eta,
@@ -901,9 +902,16 @@ int scal3r_ttt_ckpt_slots(const scal3r_ttt_handle* hd, const int32_t* seq_chunk_
   return SCAL3R_OK;
 }
 
+int scal3r_ttt_gemm_workspace_size(scal3r_ttt_handle* hd, int64_t M, int64_t N, int64_t K, int32_t out_fp32,
+                                   size_t* bytes) {
+  if (!hd || !bytes || M < 0 || N < 0 || K < 0) return SCAL3R_ERR_INVALID_ARG;
+  *bytes = wide_gemm_workspace_bytes(M, N, K, out_fp32);
+  return SCAL3R_OK;
+}
+
 int scal3r_ttt_gemm(scal3r_ttt_handle* hd, const void* a, int64_t lda, int32_t a_kmajor, const void* b, int64_t ldb,
                     int32_t b_kmajor, void* c, int64_t ldc, int32_t out_fp32, int32_t accumulate, int64_t M, int64_t N,
-                    int64_t K, void* stream) {
+                    int64_t K, void* workspace, size_t workspace_bytes, void* stream) {
   if (!hd || !a || !b || !c) return SCAL3R_ERR_INVALID_ARG;
   if (M <= 0 || N <= 0 || K <= 0 || N % 256 != 0 || lda % 8 != 0 || ldb % 8 != 0 || ldc < N) return SCAL3R_ERR_UNSUPPORTED;
   if ((a_kmajor ? lda < K : lda < M) || (b_kmajor ? ldb < K : ldb < N)) return SCAL3R_ERR_INVALID_ARG;
@@ -911,8 +919,8 @@ int scal3r_ttt_gemm(scal3r_ttt_handle* hd, const void* a, int64_t lda, int32_t a
     return SCAL3R_ERR_MISALIGNED;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 2.0 * M * N * K, 0, st, [&] {
-    return wide_gemm_bf16(a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K, hd->d_status,
-                          st);
+    return wide_gemm_bf16(a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K, workspace,
+                          workspace_bytes, hd->d_status, st);
   });
   if (e == cudaErrorInvalidValue) return SCAL3R_ERR_UNSUPPORTED;
   return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;

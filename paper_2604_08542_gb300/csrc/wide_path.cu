@@ -89,6 +89,9 @@ struct GemmArgs {
   int mse;                 // EPI_KEY: the squared-error loss (in0 = W2^T e; no u~ output)
   int64_t ld_in;           // row stride of in0 / in1 when not ld_out (0: ld_out)
   int64_t ld_out1;         // row stride of out[1] when not ld_out (0: ld_out)
+  int ksplit;              // > 1: K is cut into ksplit ranges of kb_split K blocks; range s of a tile
+  int kb_split;            //   writes (EPI_F32) the partial plane out[0] + s * split_stride
+  int64_t split_stride;
 };
 
 __device__ __forceinline__ float silu_d(float z, float& sg) {
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int tiles_n = g.N / BN;
   const int ntiles = ((g.M + BM - 1) / BM) * tiles_n;
+  const int nunits = ntiles * g.ksplit;   // work units: K range s of tile t is unit s * ntiles + t
   const int nk = (g.K + BK - 1) / BK;
   const int kps = g.nseg > 1 ? g.kseg / BK : nk;   // K blocks per segment
   volatile int* abort = &abort_flag;
@@ -227,10 +231,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     if (lane == 0) {
       uint32_t it = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int t = u % ntiles, ks0 = (u / ntiles) * g.kb_split;
         const int tm = t / tiles_n, tn = t % tiles_n;
         const int m0 = tm * BM, n0 = tn * BN;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int kb_end = min(nk, ks0 + g.kb_split);
+        for (int kb = ks0; kb < kb_end; ++kb, ++it) {
           const int s = it % STAGES;
           if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1, abort)) {
             ok = false;
@@ -266,12 +272,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     uint32_t it = 0;
     int i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, ++i) {
       const int ac = i & 1;
+      const int ks0 = (u / ntiles) * g.kb_split, kb_end = min(nk, ks0 + g.kb_split);
       if (!mbar_wait_w(&acc_empty[ac], ((i >> 1) & 1) ^ 1, abort)) break;
       tc_fence_after();
       const uint32_t acc = tb + ac * 256;
-      for (int kb = 0; kb < nk; ++kb, ++it) {
+      for (int kb = ks0; kb < kb_end; ++kb, ++it) {
         const int s = it % STAGES;
         if (!mbar_wait_w(&full[s], (it / STAGES) & 1, abort)) {
           ok = false;
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         for (int ks = 0; ks < BK / 16; ++ks) {
           const uint64_t ad = g.a_mn ? sdesc_sw128(as + ks * 2048, 8192, 1024) : sdesc_sw128(as + ks * 32, 16, 1024);
           const uint64_t bd = g.b_mn ? sdesc_sw128(bs + ks * 2048, 8192, 1024) : sdesc_sw128(bs + ks * 32, 16, 1024);
-          mma_ss_w(acc, ad, bd, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+          mma_ss_w(acc, ad, bd, idesc, (kb > ks0 || ks > 0) ? 1u : 0u);
         }
         mma_commit_w(&empty[s]);
       }
@@ -297,9 +304,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     const uint32_t lane_base = (32u * (warp & 3)) << 16;
     const uint32_t accb = tb + lane_base + gp * 256;
     int i = gp;
-    for (int t = blockIdx.x + gp * gridDim.x; t < ntiles; t += 2 * gridDim.x, i += 2) {
+    for (int u = blockIdx.x + gp * gridDim.x; u < nunits; u += 2 * gridDim.x, i += 2) {
       if (!mbar_wait(&acc_full[gp], (i >> 1) & 1, abort)) break;
       tc_fence_after();
+      const int t = u % ntiles;
+      float* const part_plane = g.ksplit > 1 ? reinterpret_cast<float*>(g.out[0]) + (u / ntiles) * g.split_stride
+                                             : reinterpret_cast<float*>(g.out[0]);
       const int tm = t / tiles_n, tn = t % tiles_n;
       const int m0 = tm * BM, n0 = tn * BN;
       const int m = m0 + (int)row;
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             st_bf16x16(o, v0);
             st_bf16x16(o + 16, v1);
           } else {
-            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c);
+            float4* o = reinterpret_cast<float4*>(part_plane + (size_t)m * g.ld_out + n0 + c);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               float4 x0 = make_float4(v0[4 * j], v0[4 * j + 1], v0[4 * j + 2], v0[4 * j + 3]);
@@ -900,8 +910,16 @@ cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   if (a.nseg < 1) a.nseg = 1;
   if (a.nbn < 1) a.nbn = 1;
   if (a.nseg > 1 && (a.kseg % BK != 0 || a.kseg * a.nseg != a.K || a.nbn != 1)) return cudaErrorInvalidValue;
-  const int tiles = ((a.M + BM - 1) / BM) * (a.N / BN);
-  const int grid = std::min(tiles, num_sms());
+  const int nk = (a.K + BK - 1) / BK;
+  if (a.ksplit <= 1) {
+    a.ksplit = 1;
+    a.kb_split = nk;
+  } else if (a.nseg > 1 || a.epi != EPI_F32 || a.kb_split < 1 || (int64_t)(a.ksplit - 1) * a.kb_split >= nk) {
+    return cudaErrorInvalidValue;   // every K range non-empty, plain float32 partial planes only
+  }
+  const int64_t units = (int64_t)((a.M + BM - 1) / BM) * (a.N / BN) * a.ksplit;
+  if (units > INT32_MAX) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<int64_t>(units, num_sms());
   if (a.epi >= EPI_MSE_E || a.epi == EPI_BKEY)
     wide_gemm_kernel<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   else
@@ -983,12 +1001,66 @@ int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n) {
   return base + j / n - 1;
 }
 
+namespace {
+
+// K ranges of a float32-output GEMM whose output tiles do not fill the SMs:
+// the count s (>= 2) that minimises the rounds of work units, ceil(tiles s /
+// SMs) / s, with every range at least 4 K blocks long; 1 = no split.
+int split_count(int64_t M, int64_t N, int64_t K, int out_fp32) {
+  if (!out_fp32) return 1;
+  const int64_t tiles = ((M + BM - 1) / BM) * (N / BN);
+  const int sms = num_sms();
+  const int64_t nk = (K + BK - 1) / BK;
+  if (tiles <= 0 || tiles * 2 > sms) return 1;
+  int best = 1;
+  double best_t = 1.0;
+  for (int s = 2; s <= 64 && nk / s >= 4; ++s) {
+    const double t = (double)((tiles * s + sms - 1) / sms) / s;
+    if (t < best_t - 1e-9) {
+      best_t = t;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// C (+)= the sum of the partial planes in order s = 0 .. S-1 (fixed order:
+// the result does not depend on which CTA finished first).
+__global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64_t plane, int64_t M, int64_t N,
+                                    float* __restrict__ c, int64_t ldc, int accumulate) {
+  const int64_t nq = N / 4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M * nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / nq, n = 4 * (i % nq);
+    float4 acc = *reinterpret_cast<const float4*>(part + m * N + n);
+    for (int s = 1; s < S; ++s) {
+      const float4 x = *reinterpret_cast<const float4*>(part + s * plane + m * N + n);
+      acc = make_float4(acc.x + x.x, acc.y + x.y, acc.z + x.z, acc.w + x.w);
+    }
+    float4* dst = reinterpret_cast<float4*>(c + m * ldc + n);
+    if (accumulate) {
+      const float4 y = *dst;
+      acc = make_float4(y.x + acc.x, y.y + acc.y, y.z + acc.z, y.w + acc.w);
+    }
+    *dst = acc;
+  }
+}
+
+}  // namespace
+
+size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32) {
+  if (M <= 0 || N <= 0 || K <= 0 || N % BN != 0) return 0;
+  const int s = split_count(M, N, K, out_fp32);
+  return s > 1 ? (size_t)s * M * N * sizeof(float) : 0;
+}
+
 // C = A B^T on the GEMM kernel (bf16 operands, fp32 accumulation); see
-// scal3r_ttt_gemm in the header.  Returns cudaErrorInvalidValue on a shape the
-// kernel does not take.
+// scal3r_ttt_gemm in the header.  A float32-output GEMM with few output tiles
+// runs in K ranges into partial planes in `ws` (when it holds them) and a
+// fixed-order sum.  Returns cudaErrorInvalidValue on a shape the kernel does
+// not take.
 cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
-                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, int* status,
-                           cudaStream_t st) {
+                           int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
+                           size_t ws_bytes, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || N % BN != 0 || M > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
   GemmArgs g{};
   const bool am = !a_kmajor, bm = !b_kmajor;
@@ -1005,7 +1077,23 @@ cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void*
   g.out[0] = c;
   g.ld_out = ldc;
   g.status = status;
-  return gemm(g, st);
+  const int S = split_count(M, N, K, out_fp32);
+  const size_t need = S > 1 ? (size_t)S * M * N * sizeof(float) : 0;
+  if (S <= 1 || !ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 15) != 0) return gemm(g, st);
+  const int nk = (int)((K + BK - 1) / BK);
+  g.epi = EPI_F32;
+  g.out[0] = ws;
+  g.ld_out = N;
+  g.kb_split = (nk + S - 1) / S;
+  g.ksplit = (nk + g.kb_split - 1) / g.kb_split;   // every range non-empty
+  g.split_stride = M * N;
+  cudaError_t e = gemm(g, st);
+  if (e != cudaSuccess) return e;
+  const int64_t work = M * (N / 4);
+  const int blocks = (int)std::min<int64_t>((work + 255) / 256, 8 * (int64_t)num_sms());
+  split_reduce_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const float*>(ws), g.ksplit, M * N, M, N,
+                                              reinterpret_cast<float*>(c), ldc, accumulate);
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_wide() {

@@ -16,7 +16,7 @@ from __future__ import annotations
 import torch
 
 from . import (_check, scal3r_gcm_gate, scal3r_gcm_gate_backward, scal3r_gcm_prep, scal3r_gcm_prep_backward,
-               scal3r_gcm_workspace_size, scal3r_ttt_gemm)
+               scal3r_gcm_workspace_size, scal3r_ttt_gemm, scal3r_ttt_gemm_workspace_size)
 from .layer import TTT, _ptr
 
 _PAD = 64   # the learning-rate predictor's rows, zero-padded for the GEMMs
@@ -32,11 +32,16 @@ class GCM:
         self.H, self.D, self.F = num_heads, head_dim, hidden_dim
         self.d = num_heads * head_dim
         self.base_lr = float(base_lr)
+        self._gws = None   # split-K partial planes of the weight-gradient GEMMs (grown on demand)
 
     def _gemm(self, a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K):
         st = torch.cuda.current_stream(c.device).cuda_stream
+        n = scal3r_ttt_gemm_workspace_size(self.ttt.handle, M, N, K, out_fp32)
+        if n and (self._gws is None or self._gws.numel() < n or self._gws.device != c.device):
+            self._gws = torch.empty(n, dtype=torch.uint8, device=c.device)
+        ws = self._gws if n else None
         _check(scal3r_ttt_gemm(self.ttt.handle, _ptr(a), lda, a_kmajor, _ptr(b), ldb, b_kmajor, _ptr(c), ldc,
-                               out_fp32, accumulate, M, N, K, st), "scal3r_ttt_gemm")
+                               out_fp32, accumulate, M, N, K, _ptr(ws), n, st), "scal3r_ttt_gemm")
 
     def forward(self, x, wqkv, bqkv, w_eta, b_eta, wo, alpha, w0, chunk_offsets, seq_chunk_ptr):
         """Returns (out [T, d] bf16, saved) for :meth:`backward`."""

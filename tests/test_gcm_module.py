@@ -63,3 +63,55 @@ def test_gcm_module_sixteen_heads_of_64():
 def test_gcm_module_wide_heads():
     """d = 512 as 2 heads x 256 (the wide-weight layer), one sequence of two chunks."""
     _case(2, 256, 512, [[300, 200]], seed=62)
+
+
+@pytest.mark.parametrize("M,N,K,a_kmajor,b_kmajor", [(64, 1024, 8192, 0, 0), (1024, 512, 4100, 0, 0),
+                                                      (300, 256, 2048, 1, 1)])
+def test_gemm_split_k_matches_reference(M, N, K, a_kmajor, b_kmajor):
+    """The GEMM entry point on weight-gradient shapes (few output tiles, long K),
+    where it runs in K ranges with a fixed-order sum: against an FP64 product of
+    the same bf16 operands, against the unsplit run, accumulating into C, and
+    bitwise equal run to run."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16)
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16)
+    ref = A.double() @ B.double().T
+    a_dev = (A if a_kmajor else A.T.contiguous()).cuda()
+    b_dev = (B if b_kmajor else B.T.contiguous()).cuda()
+    lda = K if a_kmajor else M
+    ldb = K if b_kmajor else N
+    layer = ttt.TTT(1, 256, 256, dtype=torch.bfloat16)
+    h = layer.handle
+    st = torch.cuda.current_stream().cuda_stream
+    nbytes = ttt.scal3r_ttt_gemm_workspace_size(h, M, N, K, True)
+    if M <= 128 or M * N <= 512 * 1024:
+        assert nbytes > 0          # these shapes take the split path
+    ws = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+
+    def run(c, accumulate, use_ws):
+        rc = ttt.scal3r_ttt_gemm(h, a_dev.data_ptr(), lda, a_kmajor, b_dev.data_ptr(), ldb, b_kmajor, c.data_ptr(), N,
+                                 1, accumulate, M, N, K, ws.data_ptr() if use_ws else None,
+                                 nbytes if use_ws else 0, st)
+        assert rc == 0
+
+    c1 = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    c2 = torch.empty_like(c1)
+    c3 = torch.empty_like(c1)
+    run(c1, 0, True)
+    run(c2, 0, True)
+    run(c3, 0, False)
+    base = torch.full((M, N), 0.5, dtype=torch.float32, device="cuda")
+    run(base, 1, True)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    # float32 accumulation on the tensor cores over up to 8,192 K steps: within
+    # 5e-5 of the largest entry (bf16 rounding of the operands is not involved:
+    # the reference multiplies the same bf16 values)
+    scale = ref.abs().max().item()
+    for c in (c1, c3):
+        err = (c.cpu().double() - ref).abs().max().item() / scale
+        assert err < 5e-5, err
+    assert torch.equal(c1, c2)
+    assert (base.cpu().double() - 0.5 - ref).abs().max().item() / scale < 5e-5
