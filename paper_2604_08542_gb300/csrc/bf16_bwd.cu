@@ -262,7 +262,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (!mbar_wait(&B.g_full, n & 1, abort)) break;
         tc_fence_after();
         const uint32_t buf = tb + lane_base + A_BUF;
-        float o[6][16];   // dz1 dz3 g1 g3 dpe ue
+        uint32_t ob[6][8];   // dz1 dz3 g1 g3 dpe ue as bf16 pairs (hidden 2j, 2j + 1)
         float r[2][6][8];
 #pragma unroll
         for (int sb = 0; sb < 2; ++sb) {
@@ -273,30 +273,41 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.g_free);
+        {
+          // the chain rule on pairs of hidden units (packed float32 lanes)
+          const f32x2 neta = x2(-eta), one = x2(1.f), two = x2(2.f), mtwo = x2(-2.f);
+          f32x2 dsum = x2(0.f);
 #pragma unroll
-        for (int sb = 0; sb < 2; ++sb) {
+          for (int sb = 0; sb < 2; ++sb) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int k = 8 * sb + j;
-            const float z1 = r[sb][0][j], z3 = r[sb][1][j];
-            const float sg = sigmoid_fast(z1);
-            const float a = z1 * sg;
-            const float sp = fmaf(a, 1.f - sg, sg);
-            const float dg1 = r[sb][2][j], dg3 = r[sb][3][j], praw = r[sb][4][j], ndu = r[sb][5][j];
-            const float spp = sg * (1.f - sg) * fmaf(z1, 1.f - 2.f * sg, 2.f);
-            const float u = a * z3;
-            const float pp = -eta * praw;
-            const float du = -eta * ndu;
-            const float dp = dg3 * a + dg1 * z3 * sp;
-            const float da = dg3 * pp + du * z3;
-            o[1][k] = dg1 * pp * sp + du * a;
-            o[0][k] = dg1 * pp * z3 * spp + da * sp;
-            o[2][k] = pp * z3 * sp;
-            o[3][k] = pp * a;
-            o[4][k] = -eta * dp;
-            o[5][k] = -eta * u;
-            deta -= praw * dp + ndu * u;
+            for (int jp = 0; jp < 4; ++jp) {
+              const int j = 2 * jp;
+              const f32x2 z1 = x2(r[sb][0][j], r[sb][0][j + 1]), z3 = x2(r[sb][1][j], r[sb][1][j + 1]);
+              const f32x2 dg1 = x2(r[sb][2][j], r[sb][2][j + 1]), dg3 = x2(r[sb][3][j], r[sb][3][j + 1]);
+              const f32x2 praw = x2(r[sb][4][j], r[sb][4][j + 1]), ndu = x2(r[sb][5][j], r[sb][5][j + 1]);
+              const f32x2 sg = sigmoid2(z1);
+              const f32x2 a = mul2(z1, sg);
+              const f32x2 oms = sub2(one, sg);
+              const f32x2 sp = fma2(a, oms, sg);                                  // silu'(z1)
+              const f32x2 spp = mul2(mul2(sg, oms), fma2(z1, fma2(mtwo, sg, one), two));   // silu''(z1)
+              const f32x2 u = mul2(a, z3);
+              const f32x2 pp = mul2(neta, praw);
+              const f32x2 du = mul2(neta, ndu);
+              const f32x2 z3sp = mul2(z3, sp);
+              const f32x2 dp = fma2(dg3, a, mul2(dg1, z3sp));
+              const f32x2 da = fma2(dg3, pp, mul2(du, z3));
+              const f32x2 gp = mul2(dg1, pp);
+              const int w = 4 * sb + jp;
+              ob[1][w] = pack_bf16x2(fma2(gp, sp, mul2(du, a)));                  // dz3
+              ob[0][w] = pack_bf16x2(fma2(mul2(gp, z3), spp, mul2(da, sp)));      // dz1
+              ob[2][w] = pack_bf16x2(mul2(pp, z3sp));                            // g1
+              ob[3][w] = pack_bf16x2(mul2(pp, a));                               // g3
+              ob[4][w] = pack_bf16x2(mul2(neta, dp));                            // -lr dp
+              ob[5][w] = pack_bf16x2(mul2(neta, u));                             // -lr u
+              dsum = fma2(praw, dp, fma2(ndu, u, dsum));
+            }
           }
+          deta -= x2_lo(dsum) + x2_hi(dsum);
         }
         // staging of the quarter: free once the previous quarter's products
         // and its scratch copy have read it
@@ -307,8 +318,9 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
 #pragma unroll
           for (int m = 0; m < 6; ++m) {
             uint8_t* t = stg + m * ST_TILE;
-            *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
-            *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = make_uint4(ob[m][0], ob[m][1], ob[m][2], ob[m][3]);
+            *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) =
+                make_uint4(ob[m][4], ob[m][5], ob[m][6], ob[m][7]);
           }
         }
         fence_proxy_async_smem();

@@ -388,6 +388,48 @@ __device__ __forceinline__ float tanh_approx(float x) {
 // sigmoid(z) = (1 + tanh(z / 2)) / 2
 __device__ __forceinline__ float sigmoid_fast(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
 
+// Packed float32 pairs: one instruction does the same IEEE operation (round
+// to nearest even) on both lanes of a 64-bit register (sm_100 and later).
+// The epilogues evaluate their per-element chain rule on pairs of hidden
+// units this way, halving the arithmetic instructions per element.
+using f32x2 = unsigned long long;
+__device__ __forceinline__ f32x2 x2(float lo, float hi) {
+  return ((f32x2)__float_as_uint(hi) << 32) | (f32x2)__float_as_uint(lo);
+}
+__device__ __forceinline__ f32x2 x2(float v) { return x2(v, v); }
+__device__ __forceinline__ float x2_lo(f32x2 a) { return __uint_as_float((uint32_t)a); }
+__device__ __forceinline__ float x2_hi(f32x2 a) { return __uint_as_float((uint32_t)(a >> 32)); }
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// sigmoid of both lanes (the tanh is per lane: the MUFU has no pair form)
+__device__ __forceinline__ f32x2 sigmoid2(f32x2 z) {
+  const f32x2 h = mul2(x2(0.5f), z);
+  return fma2(x2(0.5f), x2(tanh_approx(x2_lo(h)), tanh_approx(x2_hi(h))), x2(0.5f));
+}
+// The pair as packed bf16x2 (round to nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(f32x2 a) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(x2_lo(a), x2_hi(a));
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
 // Two floats -> packed bf16x2 (round to nearest even), lo in the low half.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
