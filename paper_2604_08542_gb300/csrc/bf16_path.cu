@@ -211,11 +211,9 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     if (lane == 0) mbar_arrive(&B.zq_free);
     uint32_t hp[32];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-      const float x0 = z1[2 * m], x1 = z1[2 * m + 1];
-      const float h0 = x0 * sigmoid_fast(x0) * z3[2 * m];
-      const float h1 = x1 * sigmoid_fast(x1) * z3[2 * m + 1];
-      hp[m] = pack_bf16(h0, h1);
+    for (int m = 0; m < 32; ++m) {   // pairs of hidden units on packed float32 lanes
+      const f32x2 x = x2(z1[2 * m], z1[2 * m + 1]);
+      hp[m] = pack_bf16x2(mul2(mul2(x, sigmoid2(x)), x2(z3[2 * m], z3[2 * m + 1])));
     }
     uint32_t r0[16], r1[16];
 #pragma unroll

@@ -320,17 +320,23 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&B.ga_free[b]);
-      float o[3][16];   // A1 A3 A2
+      uint32_t ob[3][8];   // A1 A3 A2 as bf16 pairs (hidden 2j, 2j + 1)
+      {
+        // the chain rule on pairs of hidden units (packed float32 lanes); the
+        // scale is the learning rate (gradient) or the row's validity (dq)
+        const f32x2 scale = x2(DQ ? (valid ? 1.f : 0.f) : eta), one = x2(1.f);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float z1 = r[0][k], z3 = r[1][k];
-        const float sg = sigmoid_fast(z1);
-        const float a = z1 * sg;
-        const float sp = fmaf(a, 1.f - sg, sg);
-        const float pk = DQ ? (valid ? r[2][k] : 0.f) : eta * r[2][k];
-        o[0][k] = pk * z3 * sp;
-        o[1][k] = pk * a;
-        o[2][k] = DQ ? (valid ? a * z3 : 0.f) : eta * (a * z3);
+        for (int w = 0; w < 8; ++w) {
+          const int k = 2 * w;
+          const f32x2 z1 = x2(r[0][k], r[0][k + 1]), z3 = x2(r[1][k], r[1][k + 1]);
+          const f32x2 sg = sigmoid2(z1);
+          const f32x2 a = mul2(z1, sg);
+          const f32x2 sp = fma2(a, sub2(one, sg), sg);
+          const f32x2 pk = mul2(scale, x2(r[2][k], r[2][k + 1]));
+          ob[0][w] = pack_bf16x2(mul2(mul2(pk, z3), sp));
+          ob[1][w] = pack_bf16x2(mul2(pk, a));
+          ob[2][w] = pack_bf16x2(mul2(scale, mul2(a, z3)));
+        }
       }
       // this thread's staging rows are free once the previous tile's L
       // products have read them
@@ -340,8 +346,9 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           uint8_t* t = stg + (m * NQ + q) * ST_TILE;
-          *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = pack8(&o[m][0]);
-          *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) = pack8(&o[m][8]);
+          *reinterpret_cast<uint4*>(t + sw64_offset(row, c)) = make_uint4(ob[m][0], ob[m][1], ob[m][2], ob[m][3]);
+          *reinterpret_cast<uint4*>(t + sw64_offset(row, c + 8)) =
+              make_uint4(ob[m][4], ob[m][5], ob[m][6], ob[m][7]);
         }
       }
       fence_proxy_async_smem();
