@@ -148,9 +148,6 @@ __device__ __forceinline__ void unpack8(const uint4& a, float* v) {
   }
 }
 
-__device__ __forceinline__ uint4 pack8f(const float* v) {
-  return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-}
 
 // Unpacks 16 bf16 (two 16-byte words) to floats.
 __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* v) {
@@ -465,7 +462,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         const int f0 = tn * (BN / 4);
         float e1 = 0.f, e3 = 0.f, e2 = 0.f;
         if (valid) row_rates(g, m, e1, e3, e2);
-        float q1 = 0.f, q3 = 0.f, q2 = 0.f;
+        f32x2 aq1 = x2(0.f), aq3 = x2(0.f), aq2 = x2(0.f);   // d eta partials, negated, per lane
         const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
         const uint4* np = reinterpret_cast<const uint4*>(g.in1 + (size_t)m * g.ld_out + f0);
 #pragma unroll 1
@@ -485,33 +482,37 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             float praw[8], ndu[8];
             unpack8(pcur[hh], praw);
             unpack8(ncur[hh], ndu);
-            float o[6][8];
+            // the chain rule on pairs of hidden units (packed float32 lanes)
+            const f32x2 n1 = x2(-e1), n3 = x2(-e3), n2 = x2(-e2), one = x2(1.f), two = x2(2.f), mtwo = x2(-2.f);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              float sg;
-              const float x1 = zz[0][e], x3 = zz[1][e], d1 = zz[2][e], d3 = zz[3][e];
-              const float a = silu_d(x1, sg);
-              const float sp = fmaf(a, 1.f - sg, sg);                               // silu'(z1)
-              const float spp = sg * (1.f - sg) * fmaf(x1, 1.f - 2.f * sg, 2.f);    // silu''(z1)
-              const float u = a * x3;
-              const float p1 = -e1 * praw[e], p3 = -e3 * praw[e];   // rate times p (e = -v)
-              const float du = -e2 * ndu[e];
-              const float t1 = d1 * x3 * sp;
-              const float da = d3 * p3 + du * x3;
-              o[1][e] = d1 * p1 * sp + du * a;                 // dz3
-              o[0][e] = d1 * p1 * x3 * spp + da * sp;          // dz1
-              o[2][e] = p1 * x3 * sp;                          // g1
-              o[3][e] = p3 * a;                                // g3
-              o[4][e] = -(e1 * t1 + e3 * d3 * a);              // -dp
-              o[5][e] = -e2 * u;                               // -eta2 u
-              q1 = fmaf(-praw[e], t1, q1);
-              q3 = fmaf(-praw[e] * a, d3, q3);
-              q2 = fmaf(-ndu[e], u, q2);
+            for (int w = 0; w < 4; ++w) {
+              const int e = 2 * w;
+              const f32x2 x1 = x2(zz[0][e], zz[0][e + 1]), x3 = x2(zz[1][e], zz[1][e + 1]);
+              const f32x2 d1 = x2(zz[2][e], zz[2][e + 1]), d3 = x2(zz[3][e], zz[3][e + 1]);
+              const f32x2 pr = x2(praw[e], praw[e + 1]), nd = x2(ndu[e], ndu[e + 1]);
+              const f32x2 sg = sigmoid2(x1);
+              const f32x2 a = mul2(x1, sg);
+              const f32x2 oms = sub2(one, sg);
+              const f32x2 sp = fma2(a, oms, sg);                                         // silu'(z1)
+              const f32x2 spp = mul2(mul2(sg, oms), fma2(x1, fma2(mtwo, sg, one), two));  // silu''(z1)
+              const f32x2 u = mul2(a, x3);
+              const f32x2 p1 = mul2(n1, pr), p3 = mul2(n3, pr);   // rate times p (e = -v)
+              const f32x2 du = mul2(n2, nd);
+              const f32x2 x3sp = mul2(x3, sp);
+              const f32x2 t1 = mul2(d1, x3sp);
+              const f32x2 d3a = mul2(d3, a);
+              const f32x2 da = fma2(d3, p3, mul2(du, x3));
+              const f32x2 dp1 = mul2(d1, p1);
+              pk[1][4 * hh + w] = pack_bf16x2(fma2(dp1, sp, mul2(du, a)));                 // dz3
+              pk[0][4 * hh + w] = pack_bf16x2(fma2(mul2(dp1, x3), spp, mul2(da, sp)));     // dz1
+              pk[2][4 * hh + w] = pack_bf16x2(mul2(p1, x3sp));                           // g1
+              pk[3][4 * hh + w] = pack_bf16x2(mul2(p3, a));                              // g3
+              pk[4][4 * hh + w] = pack_bf16x2(fma2(n1, t1, mul2(n3, d3a)));              // -dp
+              pk[5][4 * hh + w] = pack_bf16x2(mul2(n2, u));                              // -eta2 u
+              aq1 = fma2(pr, t1, aq1);
+              aq3 = fma2(pr, d3a, aq3);
+              aq2 = fma2(nd, u, aq2);
             }
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-#pragma unroll
-              for (int i = 0; i < 4; ++i) pk[q][4 * hh + i] = pack_bf16(o[q][2 * i], o[q][2 * i + 1]);
           }
           if (valid) {
             const size_t off = (size_t)m * g.ld_out + f0 + c;
@@ -519,7 +520,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             for (int q = 0; q < 6; ++q) st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[q]) + off, pk[q]);
           }
         }
-        if (valid) store_deta(g, m, tn, q1, q3, q2);
+        if (valid)
+          store_deta(g, m, tn, -(x2_lo(aq1) + x2_hi(aq1)), -(x2_lo(aq3) + x2_hi(aq3)), -(x2_lo(aq2) + x2_hi(aq2)));
       } else {
         // gate epilogues: columns [0, 128) are z1, [128, 256) z3 of hidden
         // units f0 .. f0 + 127
@@ -538,6 +540,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
 #pragma unroll
           for (int j = 0; j < 16; ++j) prow[j] = __ldg(pp + j);
         }
+        // on pairs of hidden units (packed float32 lanes); KEY scales the
+        // factors by the rates, BAPPLY by 1
+        const bool key = g.epi == EPI_KEY;
+        const f32x2 s1 = x2(key ? e1 : 1.f), s3 = x2(key ? e3 : 1.f), s2 = x2(key ? -e2 : 1.f), one = x2(1.f);
 #pragma unroll
         for (int c = 0; c < BN / 2; c += 16) {
           float z1[16], z3[16];
@@ -546,36 +552,33 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           if (!valid) continue;
           const size_t off = (size_t)m * g.ld_out + f0 + c;
           if (g.epi == EPI_APPLY) {
-            float h[16];
+            uint32_t hw[8];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              float sg;
-              h[e] = silu_d(z1[e], sg) * z3[e];
+            for (int w = 0; w < 8; ++w) {
+              const f32x2 x = x2(z1[2 * w], z1[2 * w + 1]);
+              hw[w] = pack_bf16x2(mul2(mul2(x, sigmoid2(x)), x2(z3[2 * w], z3[2 * w + 1])));
             }
-            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, h);
+            st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, hw);
           } else {
             float r[16];
             unpack16(prow[c / 8], prow[c / 8 + 1], r);
-            float o0[16], o1[16], o2[16];
+            uint32_t w0[8], w1[8], w2[8];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              float sg;
-              const float x1 = z1[e], x3 = z3[e];
-              const float a = silu_d(x1, sg);
-              const float sp = fmaf(a, 1.f - sg, sg);     // silu'(z1)
-              if (g.epi == EPI_KEY) {                     // r = W2^T v (dot) or W2^T e (squared error)
-                o0[e] = e1 * r[e] * x3 * sp;              // g1
-                o1[e] = e3 * r[e] * a;                    // g3
-                o2[e] = -e2 * a * x3;                     // u~ = -eta2 u (dot loss)
-              } else {                                    // EPI_BAPPLY, r = W2^T d_o
-                o0[e] = r[e] * x3 * sp;                   // dzq1
-                o1[e] = r[e] * a;                         // dzq3
-                o2[e] = a * x3;                           // uq
-              }
+            for (int w = 0; w < 8; ++w) {
+              const f32x2 x1 = x2(z1[2 * w], z1[2 * w + 1]), x3 = x2(z3[2 * w], z3[2 * w + 1]);
+              const f32x2 rr = x2(r[2 * w], r[2 * w + 1]);
+              const f32x2 sg = sigmoid2(x1);
+              const f32x2 a = mul2(x1, sg);
+              const f32x2 sp = fma2(a, sub2(one, sg), sg);        // silu'(z1)
+              // KEY: r = W2^T v (dot) or W2^T e (squared error) -> g1, g3, u~ = -eta2 u;
+              // BAPPLY: r = W2^T d_o -> dzq1, dzq3, uq
+              w0[w] = pack_bf16x2(mul2(mul2(mul2(s1, rr), x3), sp));
+              w1[w] = pack_bf16x2(mul2(mul2(s3, rr), a));
+              w2[w] = pack_bf16x2(mul2(s2, mul2(a, x3)));
             }
-            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, o0);
-            st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off, o1);
-            if (g.out[2]) st_bf16x16(reinterpret_cast<__nv_bfloat16*>(g.out[2]) + off, o2);
+            st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off, w0);
+            st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off, w1);
+            if (g.out[2]) st_global_v8(reinterpret_cast<__nv_bfloat16*>(g.out[2]) + off, w2);
           }
         }
       }
