@@ -194,17 +194,22 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     tc_fence_after();
     float z1[64], z3[64];
     {
-      float a[16], bq[16];
+      // all eight loads in flight together: one TMEM latency
+      uint32_t u[8][16];
 #pragma unroll
-      for (int c = 0; c < 64; c += 16) {
-        tmem_ld16(tb + lane_base + A_ZQ + 64 * half + c, a);
-        tmem_ld16(tb + lane_base + A_ZQ + F + 64 * half + c, bq);
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld16_nowait(tb + lane_base + A_ZQ + 64 * half + 16 * c, u[c]);
+        tmem_ld16_nowait(tb + lane_base + A_ZQ + F + 64 * half + 16 * c, u[4 + c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) tmem_wait_ld16(u[c]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          z1[c + j] = a[j];
-          z3[c + j] = bq[j];
+          z1[16 * c + j] = __uint_as_float(u[c][j]);
+          z3[16 * c + j] = __uint_as_float(u[4 + c][j]);
         }
-      }
     }
     tc_fence_before();
     __syncwarp();

@@ -211,6 +211,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
   for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
 }
 
+// One 16-column TMEM load without the wait: the registers are not valid until
+// tmem_wait_ld16 on them, which takes them as read-write operands so that no
+// use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&u)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr)
+      : "memory");
+}
+// Waits for the thread's outstanding TMEM loads; u as read-write operands
+// orders every use of these registers after the wait.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&u)[16]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]), "+r"(u[6]), "+r"(u[7]),
+        "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]), "+r"(u[15])
+      :
+      : "memory");
+}
+
 // Six 8-column loads and one wait (backward epilogue).
 __device__ __forceinline__ void tmem_ld8x6(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
                                            uint32_t a5, float (&r)[6][8]) {
