@@ -153,7 +153,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       if (lane == 0) {
         for (int i = ta; i < te; ++i) {
           const int s = i & 1;
-          if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+          if (!mbar_wait_spin(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
           mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
           uint8_t* xs = sm + XY_OFF + s * 32768;
           const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
@@ -170,8 +170,8 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
       auto issue_acc = [&](int m) -> bool {
         const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait_w(&B.st_full, m & 1, abort)) return false;
-        if (q == 0 && !mbar_wait_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+        if (!mbar_wait_spin_w(&B.st_full, m & 1, abort)) return false;
+        if (q == 0 && !mbar_wait_spin_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
         tc_fence_after();
         const uint32_t wb = wq + q * QBYTES;
 #pragma unroll
@@ -188,11 +188,11 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       };
       bool ok = true;
       // pass B of the previous sub-piece overwrote the weights
-      if (sp > 0 && !mbar_wait_w(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
+      if (sp > 0 && !mbar_wait_spin_w(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
       for (int n = ta * NQ; n < te * NQ && ok; ++n) {
         const int i = n / NQ, q = n % NQ;
-        if (q == 0 && !mbar_wait_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait_w(&B.g_free, (n & 1) ^ 1, abort)) break;
+        if (q == 0 && !mbar_wait_spin_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+        if (!mbar_wait_spin_w(&B.g_free, (n & 1) ^ 1, abort)) break;
         tc_fence_after();
         const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
         const uint32_t wb = wq + q * QBYTES;
@@ -217,7 +217,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         }
         for (int n = ta * NQ; n < te * NQ; ++n) {
           const int i = n / NQ, q = n % NQ;
-          if (!mbar_wait(&B.st_full, n & 1, abort)) break;
+          if (!mbar_wait_spin(&B.st_full, n & 1, abort)) break;
           const int32_t g = g0 + 4 * (i - ta);
           tma_store_5d(&maps.sc_st, sm + ST_OFF + 0 * ST_TILE, 0, 0, q, 0, g);   // dz1
           tma_store_5d(&maps.sc_st, sm + ST_OFF + 1 * ST_TILE, 0, 0, q, 1, g);   // dz3
@@ -227,7 +227,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           mbar_arrive(&B.stg_done);
           if (q == NQ - 1) {
             // dk / dv of the tile, staged over the tile's X/Y stage
-            if (!mbar_wait(&B.out_full, i & 1, abort)) break;
+            if (!mbar_wait_spin(&B.out_full, i & 1, abort)) break;
             const int64_t tok = t0 + (int64_t)i * BT;
             if (tok + BT <= t1) {
               uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
@@ -259,7 +259,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           const int64_t tn = tok + BT;
           eta_next = (i + 1 < ntiles && tn < t1) ? p.lr[(size_t)tn * H + h] : 0.f;
         }
-        if (!mbar_wait(&B.g_full, n & 1, abort)) break;
+        if (!mbar_wait_spin(&B.g_full, n & 1, abort)) break;
         tc_fence_after();
         const uint32_t buf = tb + lane_base + A_BUF;
         uint32_t ob[6][8];   // dz1 dz3 g1 g3 dpe ue as bf16 pairs (hidden 2j, 2j + 1)
@@ -311,8 +311,8 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         }
         // staging of the quarter: free once the previous quarter's products
         // and its scratch copy have read it
-        if (!mbar_wait(&B.st_free, (n & 1) ^ 1, abort)) break;
-        if (!mbar_wait(&B.stg_done, (n & 1) ^ 1, abort)) break;
+        if (!mbar_wait_spin(&B.st_free, (n & 1) ^ 1, abort)) break;
+        if (!mbar_wait_spin(&B.stg_done, (n & 1) ^ 1, abort)) break;
         {
           const uint32_t c = 16u * half;
 #pragma unroll
@@ -329,7 +329,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (q == NQ - 1) {
           // tile finished: dk and dv to shared memory for the TMA store
           // (rows of a partial tile are stored directly), combine the dlr halves
-          if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+          if (!mbar_wait_spin(&B.acc_full, i & 1, abort)) break;
           tc_fence_after();
           const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
           uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
@@ -356,12 +356,12 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           // its partial to half 0 through shared memory)
           const int e = i & 1;
           if (half == 1) {
-            if (!mbar_wait(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
+            if (!mbar_wait_spin(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
             B.eta_red[e][row] = deta;
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.eta_full[e]);
           } else {
-            if (!mbar_wait(&B.eta_full[e], (i >> 1) & 1, abort)) break;
+            if (!mbar_wait_spin(&B.eta_full[e], (i >> 1) & 1, abort)) break;
             if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.eta_free[e]);
@@ -391,7 +391,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         bool ok = true;
         for (int j = 0; j < nb; ++j) {
           const int s = (j + rot) % PB_STAGES;
-          if (!mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort)) {
+          if (!mbar_wait_spin(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort)) {
             ok = false;
             break;
           }
@@ -406,7 +406,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (ok && sp + 1 < nsub) {
           // the stages over the weights are read: copy the weights back
           for (int s = 0; s < PB_WQ_STAGES && ok; ++s)
-            ok = mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort);
+            ok = mbar_wait_spin(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort);
           if (ok) {
             mbar_arrive_expect_tx(&B.wq_full, WQ_BYTES);
             bulk_load(sm + WQ_OFF, wq_image, WQ_BYTES, &B.wq_full);
@@ -418,7 +418,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       bool ok = true;
       for (int j = 0; j < nb; ++j) {
         const int s = (j + rot) % PB_STAGES;
-        if (!mbar_wait_w(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
+        if (!mbar_wait_spin_w(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
           ok = false;
           break;
         }
@@ -440,7 +440,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
     }
     // everyone waits for the sub-piece's weight-adjoint products before the
     // next pass A reuses their shared memory
-    mbar_wait(&B.bdone, sp & 1, abort);
+    mbar_wait_spin(&B.bdone, sp & 1, abort);
     tc_fence_before();
     const int stop_b = __syncthreads_or(*abort);
     tc_fence_after();

@@ -126,7 +126,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     if (lane == 0) {
       for (int i = 0; i < ntiles; ++i) {
         const int s = i % QSTAGES;
-        if (!mbar_wait(&B.q_empty[s], ((i / QSTAGES) & 1) ^ 1, abort)) break;
+        if (!mbar_wait_spin(&B.q_empty[s], ((i / QSTAGES) & 1) ^ 1, abort)) break;
         mbar_arrive_expect_tx(&B.q_full[s], QT * 128);
         tma_load_3d(Qs + s * QT * 128, &maps.q, &B.q_full[s], 0, h, (int32_t)(t0 + (int64_t)i * QT));
       }
@@ -140,8 +140,8 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     const uint32_t w13 = smem_u32(wb13), w2a = smem_u32(wb2);
     auto issue_zq = [&](int i) -> bool {
       const int s = i % QSTAGES;
-      if (!mbar_wait_w(&B.q_full[s], (i / QSTAGES) & 1, abort)) return false;
-      if (!mbar_wait_w(&B.zq_free, (i & 1) ^ 1, abort)) return false;
+      if (!mbar_wait_spin_w(&B.q_full[s], (i / QSTAGES) & 1, abort)) return false;
+      if (!mbar_wait_spin_w(&B.zq_free, (i & 1) ^ 1, abort)) return false;
       tc_fence_after();
       const uint32_t qa = smem_u32(Qs + s * QT * 128);
 #pragma unroll
@@ -155,7 +155,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     bool ok = issue_zq(0);
     for (int i = 0; i < ntiles && ok; ++i) {
       if (i + 1 < ntiles && !issue_zq(i + 1)) break;
-      if (!mbar_wait_w(&B.h_full, i & 1, abort)) break;
+      if (!mbar_wait_spin_w(&B.h_full, i & 1, abort)) break;
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
@@ -173,7 +173,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
   __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(p.o);
   auto store_o = [&](int i) -> bool {
-    if (!mbar_wait(&B.o_full, i & 1, abort)) return false;
+    if (!mbar_wait_spin(&B.o_full, i & 1, abort)) return false;
     tc_fence_after();
     float v0[16], v1[16];
     tmem_ld16(tb + lane_base + A_O + 32 * half, v0);
@@ -190,7 +190,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
   };
   for (int i = 0; i < ntiles; ++i) {
     if (i > 0 && !store_o(i - 1)) break;
-    if (!mbar_wait(&B.zq_full, i & 1, abort)) break;
+    if (!mbar_wait_spin(&B.zq_full, i & 1, abort)) break;
     tc_fence_after();
     float z1[64], z3[64];
     {

@@ -214,7 +214,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     if (lane == 0) {
       for (int i = 0; i < ntiles; ++i) {
         const int s = i & 1;
-        if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+        if (!mbar_wait_spin(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
         mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
         uint8_t* xs = sm + AXY_OFF + s * 32768;
         const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
@@ -231,8 +231,8 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     const uint32_t wq = smem_u32(sm + AW_OFF);
     for (int n = 0; n < nq; ++n) {
       const int i = n / NQ, q = n % NQ, b = n & 1;
-      if (q == 0 && !mbar_wait_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-      if (!mbar_wait_w(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
+      if (q == 0 && !mbar_wait_spin_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+      if (!mbar_wait_spin_w(&B.ga_free[b], ((n >> 1) & 1) ^ 1, abort)) break;
       tc_fence_after();
       const uint32_t xs = smem_u32(sm + AXY_OFF + (i & 1) * 32768);
       const uint32_t wb = wq + q * AQ_BYTES;
@@ -256,8 +256,8 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     bool ok = true;
     for (int m = 0; m < nq && ok; ++m) {
       const int i = m / NQ, q = m % NQ;
-      if (!mbar_wait_w(&B.sq_full[q], i & 1, abort)) break;
-      if (DQ && q == 0 && !mbar_wait_w(&B.acc_free, (i & 1) ^ 1, abort)) break;
+      if (!mbar_wait_spin_w(&B.sq_full[q], i & 1, abort)) break;
+      if (DQ && q == 0 && !mbar_wait_spin_w(&B.acc_free, (i & 1) ^ 1, abort)) break;
       tc_fence_after();
       if (DQ) {
         const uint32_t wb = wq + q * AQ_BYTES;
@@ -289,7 +289,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     // dq of every full tile by TMA store
     if (lane == 0) {
       for (int i = 0; i < ntiles; ++i) {
-        if (!mbar_wait(&B.out_full, i & 1, abort)) break;
+        if (!mbar_wait_spin(&B.out_full, i & 1, abort)) break;
         const int64_t tok = t0 + (int64_t)i * BT;
         if (tok + BT <= t1) {
           tma_store_3d(mdq, sm + ADQ_OFF, 0, h, (int32_t)tok);
@@ -312,7 +312,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       const int64_t tok = t0 + (int64_t)i * BT + row;
       const bool valid = tok < t1;
       if (!DQ && q == 0) eta = valid ? p.lr[(size_t)tok * H + h] : 0.f;
-      if (!mbar_wait(&B.ga_full[b], (n >> 1) & 1, abort)) break;
+      if (!mbar_wait_spin(&B.ga_full[b], (n >> 1) & 1, abort)) break;
       tc_fence_after();
       const uint32_t buf = tb + lane_base + A_BUF + b * A_GBUF + 16 * half;
       float r[3][16];   // z1 z3 p
@@ -340,7 +340,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       }
       // this thread's staging rows are free once the previous tile's L
       // products have read them
-      if (q == 0 && !mbar_wait(&B.st_free[warp & 3], (i & 1) ^ 1, abort)) break;
+      if (q == 0 && !mbar_wait_spin(&B.st_free[warp & 3], (i & 1) ^ 1, abort)) break;
       {
         const uint32_t c = 16u * half;
 #pragma unroll
@@ -359,10 +359,10 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       if (DQ && q == NQ - 1) {
         // tile finished: dq to shared memory for the TMA store (rows of a
         // partial tile are stored directly)
-        if (!mbar_wait(&B.acc_full, i & 1, abort)) break;
+        if (!mbar_wait_spin(&B.acc_full, i & 1, abort)) break;
         tc_fence_after();
         const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
-        if (full_tile && !mbar_wait(&B.out_free, (i & 1) ^ 1, abort)) break;
+        if (full_tile && !mbar_wait_spin(&B.out_free, (i & 1) ^ 1, abort)) break;
         float v0[16], v1[16];
         tmem_ld16(tb + lane_base + A_DX + 32 * half, v0);
         tmem_ld16(tb + lane_base + A_DX + 32 * half + 16, v1);
@@ -381,7 +381,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       }
     }
     // the last L products complete before they are read
-    mbar_wait(&B.bdone, 0, abort);
+    mbar_wait_spin(&B.bdone, 0, abort);
   }
   tc_fence_before();
   const int stop = __syncthreads_or(*abort);
