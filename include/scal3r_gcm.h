@@ -52,6 +52,15 @@ int scal3r_ttt_gemm(scal3r_ttt_handle* handle, const void* a, int64_t lda, int32
                     int64_t ldb, int32_t b_kmajor, void* c, int64_t ldc, int32_t out_fp32, int32_t accumulate,
                     int64_t M, int64_t N, int64_t K, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Test of failure detection without a GPU fault.  With enable = 1, every
+ * later scal3r_ttt_gemm on this handle stores its product as usual and then
+ * has its epilogue warps wait on a shared-memory barrier that no thread
+ * completes.  The wait gives up after 50 ms, and the kernel frees its tensor
+ * memory and returns; scal3r_ttt_get_status then reports SCAL3R_ERR_TIMEOUT.
+ * No copy or MMA is in flight at that point, so the context stays usable.
+ * enable = 0 turns it off. */
+int scal3r_ttt_gemm_timeout_test(scal3r_ttt_handle* handle, int32_t enable);
+
 /* Bytes of workspace scal3r_ttt_gemm uses for an M x N x K product (0: none). */
 int scal3r_ttt_gemm_workspace_size(scal3r_ttt_handle* handle, int64_t M, int64_t N, int64_t K, int32_t out_fp32,
                                    size_t* bytes);

@@ -20,7 +20,7 @@
 namespace scal3r {
 cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
                            int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
-                           size_t ws_bytes, int* status, cudaStream_t st);
+                           size_t ws_bytes, int timeout_test, int* status, cudaStream_t st);
 size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32);
 size_t gcm_partial_bytes(int64_t T, int d, int H);
 bool gcm_heads_supported(int H);
@@ -99,6 +99,7 @@ struct scal3r_ttt_handle {
   size_t pool_used = 0;
   bool graph_on = false;
   bool wide = false;            // BF16 wide-weight path (head_dim, hidden multiples of 256)
+  bool timeout_test = false;    // scal3r_ttt_gemm runs the bounded-wait test
   cudaStream_t capture_stream = nullptr;
   GraphSlot gfwd, gbwd;
 };
@@ -902,6 +903,12 @@ int scal3r_ttt_ckpt_slots(const scal3r_ttt_handle* hd, const int32_t* seq_chunk_
   return SCAL3R_OK;
 }
 
+int scal3r_ttt_gemm_timeout_test(scal3r_ttt_handle* hd, int32_t enable) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  hd->timeout_test = enable != 0;
+  return SCAL3R_OK;
+}
+
 int scal3r_ttt_gemm_workspace_size(scal3r_ttt_handle* hd, int64_t M, int64_t N, int64_t K, int32_t out_fp32,
                                    size_t* bytes) {
   if (!hd || !bytes || M < 0 || N < 0 || K < 0) return SCAL3R_ERR_INVALID_ARG;
@@ -920,7 +927,7 @@ int scal3r_ttt_gemm(scal3r_ttt_handle* hd, const void* a, int64_t lda, int32_t a
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 2.0 * M * N * K, 0, st, [&] {
     return wide_gemm_bf16(a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32, accumulate, M, N, K, workspace,
-                          workspace_bytes, hd->d_status, st);
+                          workspace_bytes, hd->timeout_test ? 1 : 0, hd->d_status, st);
   });
   if (e == cudaErrorInvalidValue) return SCAL3R_ERR_UNSUPPORTED;
   return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;

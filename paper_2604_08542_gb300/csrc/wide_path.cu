@@ -89,6 +89,8 @@ struct GemmArgs {
   int mse;                 // EPI_KEY: the squared-error loss (in0 = W2^T e; no u~ output)
   int64_t ld_in;           // row stride of in0 / in1 when not ld_out (0: ld_out)
   int64_t ld_out1;         // row stride of out[1] when not ld_out (0: ld_out)
+  int timeout_test;        // nonzero: after the last tile the epilogue warps wait, for at most
+                           //   50 ms, on a barrier that nothing completes (the bounded-wait test)
   int ksplit;              // > 1: K is cut into ksplit ranges of kb_split K blocks; range s of a tile
   int kb_split;            //   writes (EPI_F32) the partial plane out[0] + s * split_stride
   int64_t split_stride;
@@ -190,7 +192,7 @@ template <bool XSET>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], never_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);
     }
+    mbar_init(&never_bar, 1);   // no thread ever arrives
     abort_flag = 0;
     fence_barrier_init();
     for (int j = 0; j < g.nseg; ++j) prefetch_tmap(&g.a[j]);
@@ -587,6 +590,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[gp]);
     }
+    // bounded-wait test: every tile is stored and no copy or MMA is in flight;
+    // the wait runs out, raises the abort flag and the status word reports it
+    if (g.timeout_test) mbar_wait(&never_bar, 0, abort, 50000000ull);
   }
   tc_fence_before();
   __syncthreads();
@@ -1063,7 +1069,7 @@ size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32) 
 // not take.
 cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
                            int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
-                           size_t ws_bytes, int* status, cudaStream_t st) {
+                           size_t ws_bytes, int timeout_test, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || N % BN != 0 || M > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
   GemmArgs g{};
   const bool am = !a_kmajor, bm = !b_kmajor;
@@ -1080,6 +1086,7 @@ cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void*
   g.out[0] = c;
   g.ld_out = ldc;
   g.status = status;
+  g.timeout_test = timeout_test;
   const int S = split_count(M, N, K, out_fp32);
   const size_t need = S > 1 ? (size_t)S * M * N * sizeof(float) : 0;
   if (S <= 1 || !ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 15) != 0) return gemm(g, st);
