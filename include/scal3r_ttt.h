@@ -73,6 +73,8 @@ extern "C" {
 #define SCAL3R_ERR_TIMEOUT        5  /* a bounded device-side wait gave up */
 #define SCAL3R_ERR_WORKSPACE      6  /* workspace missing or too small */
 #define SCAL3R_ERR_NO_DEVICE      7  /* no sm_103 device current */
+#define SCAL3R_ERR_NONFINITE      8  /* a NaN or infinity in an input or output (finite checking on;
+                                        reported through scal3r_ttt_get_status) */
 
 /* config values */
 #define SCAL3R_FP32         0   /* q,k,v,o float32: plain SIMT path */
@@ -318,8 +320,17 @@ int scal3r_ttt_profile_read(scal3r_ttt_handle* handle, int32_t kind, int64_t* la
 
 /* Synchronise the stream and return the device status word of the last
  * calls on this handle (SCAL3R_ERR_TIMEOUT if a bounded device wait gave
- * up), then clear it. */
+ * up, SCAL3R_ERR_NONFINITE if finite checking found a NaN or infinity), then
+ * clear it. */
 int scal3r_ttt_get_status(scal3r_ttt_handle* handle, void* stream);
+
+/* Finite checking (off by default).  With enable = 1, scal3r_ttt_forward and
+ * scal3r_ttt_backward then scan, on the same stream and after their work, every
+ * tensor they were given or wrote (forward: q, k, v, lr, w0, o, w_final;
+ * backward: d_o, dq, dk, dv, dlr, dw0).  A NaN or an infinity sets the status
+ * word to SCAL3R_ERR_NONFINITE, read by scal3r_ttt_get_status.  The scans are
+ * memory-bound reads of those tensors; the call's own results are unchanged. */
+int scal3r_ttt_set_finite_check(scal3r_ttt_handle* handle, int32_t enable);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@ SCAL3R_ERR_CUDA = 4
 SCAL3R_ERR_TIMEOUT = 5
 SCAL3R_ERR_WORKSPACE = 6
 SCAL3R_ERR_NO_DEVICE = 7
+SCAL3R_ERR_NONFINITE = 8
 
 SCAL3R_FP32 = 0
 SCAL3R_BF16 = 1
@@ -49,7 +50,7 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
             "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
-            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_gcm_workspace_size",
+            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_ttt_set_finite_check", "scal3r_gcm_workspace_size",
             "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
 
 
@@ -136,6 +137,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_gemm.argtypes = [vp, vp, i64, i32, vp, i64, i32, vp, i64, i32, i32, i64, i64, i64, vp,
                                     ctypes.c_size_t, vp]
     lib.scal3r_ttt_gemm.restype = ctypes.c_int
+    lib.scal3r_ttt_set_finite_check.argtypes = [vp, i32]
+    lib.scal3r_ttt_set_finite_check.restype = ctypes.c_int
     lib.scal3r_ttt_gemm_timeout_test.argtypes = [vp, i32]
     lib.scal3r_ttt_gemm_timeout_test.restype = ctypes.c_int
     lib.scal3r_ttt_gemm_workspace_size.argtypes = [vp, i64, i64, i64, i32, ctypes.POINTER(sz)]
@@ -313,6 +316,10 @@ def scal3r_ttt_gemm(handle, a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32
     return load_library().scal3r_ttt_gemm(handle, a, lda, int(a_kmajor), b, ldb, int(b_kmajor), c, ldc,
                                           int(out_fp32), int(accumulate), M, N, K, workspace, workspace_bytes,
                                           stream)
+
+
+def scal3r_ttt_set_finite_check(handle: int, enable: bool) -> None:
+    _check(load_library().scal3r_ttt_set_finite_check(handle, int(enable)), "scal3r_ttt_set_finite_check")
 
 
 def scal3r_ttt_gemm_timeout_test(handle: int, enable: bool) -> None:

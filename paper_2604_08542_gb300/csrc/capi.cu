@@ -100,11 +100,51 @@ struct scal3r_ttt_handle {
   bool graph_on = false;
   bool wide = false;            // BF16 wide-weight path (head_dim, hidden multiples of 256)
   bool timeout_test = false;    // scal3r_ttt_gemm runs the bounded-wait test
+  bool finite_check = false;    // scan each call's tensors for NaN / infinity afterwards
   cudaStream_t capture_stream = nullptr;
   GraphSlot gfwd, gbwd;
 };
 
 namespace {
+
+// Sets the status word to SCAL3R_ERR_NONFINITE (unless it already holds an
+// error) if any element of the tensor is a NaN or an infinity: an all-ones
+// exponent, tested on the bit pattern (bf16: 0x7F80, float32: 0x7F800000).
+__global__ void finite_scan_kernel(const uint4* __restrict__ p, int64_t nvec, const void* tail, int64_t ntail,
+                                   int bf16, int* status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 x = p[i];
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (bf16)
+        bad |= ((w[j] & 0x7F80u) == 0x7F80u) || ((w[j] & 0x7F800000u) == 0x7F800000u);
+      else
+        bad |= (w[j] & 0x7F800000u) == 0x7F800000u;
+    }
+  }
+  if (blockIdx.x == 0)
+    for (int64_t i = threadIdx.x; i < ntail; i += blockDim.x) {
+      if (bf16)
+        bad |= (reinterpret_cast<const uint16_t*>(tail)[i] & 0x7F80u) == 0x7F80u;
+      else
+        bad |= (reinterpret_cast<const uint32_t*>(tail)[i] & 0x7F800000u) == 0x7F800000u;
+    }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0, SCAL3R_ERR_NONFINITE);
+}
+
+cudaError_t finite_scan(int* status, const void* p, int64_t n, bool bf16, int sms, cudaStream_t st) {
+  if (!p || n <= 0) return cudaSuccess;
+  const int64_t bytes = n * (bf16 ? 2 : 4);
+  const int64_t nvec = bytes / 16;
+  const int64_t ntail = (bytes - nvec * 16) / (bf16 ? 2 : 4);
+  const void* tail = reinterpret_cast<const uint8_t*>(p) + nvec * 16;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nvec + 255) / 256, 4 * (int64_t)sms));
+  finite_scan_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const uint4*>(p), nvec, tail, ntail, bf16 ? 1 : 0,
+                                              status);
+  return cudaGetLastError();
+}
 
 void free_plan(Plan& p) {
   if (p.d_items) cudaFree(p.d_items);
@@ -346,6 +386,7 @@ const char* scal3r_ttt_error_string(int status) {
     case SCAL3R_ERR_TIMEOUT: return "a bounded device wait timed out";
     case SCAL3R_ERR_WORKSPACE: return "workspace missing or too small";
     case SCAL3R_ERR_NO_DEVICE: return "no sm_103 device";
+    case SCAL3R_ERR_NONFINITE: return "a NaN or infinity in an input or output (finite checking on)";
     default: return "unknown status";
   }
 }
@@ -424,10 +465,10 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   return SCAL3R_OK;
 }
 
-int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
-                       const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
-                       const int32_t* ptr, int32_t S, void* o, float* w_ckpt, float* wnorm, float* w_final,
-                       void* workspace, size_t workspace_bytes_, void* stream) {
+static int forward_impl(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
+                        const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
+                        const int32_t* ptr, int32_t S, void* o, float* w_ckpt, float* wnorm, float* w_final,
+                        void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
@@ -495,7 +536,7 @@ int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, cons
   return enqueue_forward(hd, prm, st);
 }
 
-int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
+static int backward_impl(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
                         const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
                         const int32_t* ptr, int32_t S, const void* d_o, const float* w_ckpt,
                         const float* wnorm, void* dq, void* dk, void* dv, float* dlr, float* dw0,
@@ -571,6 +612,57 @@ int scal3r_ttt_set_schedule(scal3r_ttt_handle* hd, const scal3r_ttt_schedule* sc
 int scal3r_ttt_get_schedule(const scal3r_ttt_handle* hd, scal3r_ttt_schedule* sch) {
   if (!hd || !sch) return SCAL3R_ERR_INVALID_ARG;
   to_public(hd->sched, *sch);
+  return SCAL3R_OK;
+}
+
+int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
+                       const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
+                       const int32_t* ptr, int32_t S, void* o, float* w_ckpt, float* wnorm, float* w_final,
+                       void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = forward_impl(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, o, w_ckpt, wnorm, w_final, workspace,
+                        workspace_bytes, stream);
+  if (rc != SCAL3R_OK || !hd->finite_check) return rc;
+  // inputs and outputs of the call (shapes as checked by forward_impl)
+  const int64_t T = off[C], H = hd->shape.H, D = hd->shape.D, P = hd->shape.P();
+  const bool bf = hd->cfg.dtype == SCAL3R_BF16;
+  const int64_t nr = hd->cfg.lr_per_matrix ? 3 : 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* s_ = hd->d_status;
+  const int sms = hd->num_sms;
+  cudaError_t e = cudaSuccess;
+  for (const void* t : {q, k, v, (const void*)o})
+    if (e == cudaSuccess) e = finite_scan(s_, t, T * H * D, bf, sms, st);
+  if (e == cudaSuccess) e = finite_scan(s_, lr, T * H * nr, false, sms, st);
+  if (e == cudaSuccess) e = finite_scan(s_, w0, (w0_seq_stride ? S : 1) * H * P, false, sms, st);
+  if (e == cudaSuccess) e = finite_scan(s_, w_final, (int64_t)S * H * P, false, sms, st);
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
+                        const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
+                        const int32_t* ptr, int32_t S, const void* d_o, const float* w_ckpt,
+                        const float* wnorm, void* dq, void* dk, void* dv, float* dlr, float* dw0,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  int rc = backward_impl(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, d_o, w_ckpt, wnorm, dq, dk, dv, dlr,
+                         dw0, workspace, workspace_bytes, stream);
+  if (rc != SCAL3R_OK || !hd->finite_check) return rc;
+  const int64_t T = off[C], H = hd->shape.H, D = hd->shape.D, P = hd->shape.P();
+  const bool bf = hd->cfg.dtype == SCAL3R_BF16;
+  const int64_t nr = hd->cfg.lr_per_matrix ? 3 : 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* s_ = hd->d_status;
+  const int sms = hd->num_sms;
+  cudaError_t e = cudaSuccess;
+  for (const void* t : {d_o, (const void*)dq, (const void*)dk, (const void*)dv})
+    if (e == cudaSuccess) e = finite_scan(s_, t, T * H * D, bf, sms, st);
+  if (e == cudaSuccess) e = finite_scan(s_, dlr, T * H * nr, false, sms, st);
+  if (e == cudaSuccess) e = finite_scan(s_, dw0, (w0_seq_stride ? S : 1) * H * P, false, sms, st);
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_ttt_set_finite_check(scal3r_ttt_handle* hd, int32_t enable) {
+  if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  hd->finite_check = enable != 0;
   return SCAL3R_OK;
 }
 

@@ -21,7 +21,8 @@ from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3
                scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_schedule,
                scal3r_ttt_get_status, scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_schedule,
                scal3r_ttt_set_graph_mode, scal3r_ttt_set_schedule, scal3r_ttt_workspace_size,
-               scal3r_ttt_partial_grad, scal3r_ttt_apply_update, scal3r_ttt_apply, scal3r_ttt_ckpt_slots)
+               scal3r_ttt_partial_grad, scal3r_ttt_apply_update, scal3r_ttt_apply, scal3r_ttt_ckpt_slots,
+               scal3r_ttt_set_finite_check)
 
 NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
 LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
@@ -204,6 +205,11 @@ class TTT:
         return scal3r_ttt_get_status(self.handle, torch.cuda.current_stream().cuda_stream)
 
     # -- graphs and schedules ---------------------------------------------
+    def set_finite_check(self, enable: bool = True) -> None:
+        """Scan each call's inputs and outputs for NaN / infinity afterwards;
+        a hit shows as SCAL3R_ERR_NONFINITE from status()."""
+        scal3r_ttt_set_finite_check(self.handle, enable)
+
     def set_graph_mode(self, enable: bool = True) -> None:
         """Record forward/backward launch sequences into CUDA graphs and replay them."""
         scal3r_ttt_set_graph_mode(self.handle, enable)
