@@ -45,8 +45,8 @@ constexpr int QSTAGES = 3;    // Q stages, 16 KB each
 
 // TMEM columns, apply role
 constexpr uint32_t A_ZQ = 0;      // z1 0..127, z3 128..255
-constexpr uint32_t A_H = 256;     // h as bf16 pairs, 64 columns
-constexpr uint32_t A_O = 320;     // o accumulator, 64 columns
+constexpr uint32_t A_H = 256;     // two buffers of h as bf16 pairs, 64 columns each (tile i: i & 1)
+constexpr uint32_t A_O = 384;     // two o accumulators, 64 columns each
 
 constexpr uint32_t IDESC_AZ = idesc_bf16(128, 2 * F, false, false);
 constexpr uint32_t IDESC_AO = idesc_bf16(128, D, false, false);
@@ -63,7 +63,7 @@ struct TmaMaps {
 
 struct Bars {   // APPLY
   uint64_t q_full[QSTAGES], q_empty[QSTAGES];
-  uint64_t zq_full, zq_free, h_full, o_full;
+  uint64_t zq_full, zq_free, h_full[2], o_full[2], o_free[2];
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -154,14 +154,16 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     };
     bool ok = issue_zq(0);
     for (int i = 0; i < ntiles && ok; ++i) {
+      const int b = i & 1;
       if (i + 1 < ntiles && !issue_zq(i + 1)) break;
-      if (!mbar_wait_spin_w(&B.h_full, i & 1, abort)) break;
+      if (!mbar_wait_spin_w(&B.h_full[b], (i >> 1) & 1, abort)) break;
+      if (!mbar_wait_spin_w(&B.o_free[b], ((i >> 1) & 1) ^ 1, abort)) break;   // o of tile i - 2 was read
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk)
-        mma_ts_w(tb + A_O, tb + A_H + 8 * kk, sdesc_sw128(w2a + (kk / 4) * (D * 128) + (kk % 4) * 32, 16, 1024),
-                 IDESC_AO, kk > 0);
-      mma_commit_w(&B.o_full);
+        mma_ts_w(tb + A_O + 64 * b, tb + A_H + 64 * b + 8 * kk,
+                 sdesc_sw128(w2a + (kk / 4) * (D * 128) + (kk % 4) * 32, 16, 1024), IDESC_AO, kk > 0);
+      mma_commit_w(&B.o_full[b]);
     }
     return;
   }
@@ -173,11 +175,16 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
   __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(p.o);
   auto store_o = [&](int i) -> bool {
-    if (!mbar_wait_spin(&B.o_full, i & 1, abort)) return false;
+    const int b = i & 1;
+    if (!mbar_wait_spin(&B.o_full[b], (i >> 1) & 1, abort)) return false;
     tc_fence_after();
     float v0[16], v1[16];
-    tmem_ld16(tb + lane_base + A_O + 32 * half, v0);
-    tmem_ld16(tb + lane_base + A_O + 32 * half + 16, v1);
+    tmem_ld16(tb + lane_base + A_O + 64 * b + 32 * half, v0);
+    tmem_ld16(tb + lane_base + A_O + 64 * b + 32 * half + 16, v1);
+    // the accumulator is in registers: the next o product into it may start
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&B.o_free[b]);
     const int64_t tok = t0 + (int64_t)i * QT + row;
     if (tok < t1) {
       uint4* dst = reinterpret_cast<uint4*>(o + ((size_t)tok * p.H + h) * D + 32 * half);
@@ -188,8 +195,10 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     }
     return true;
   };
+  // tile i: h(i) into buffer i & 1, then the o of tile i - 1 out while the
+  // o product of tile i runs.  h buffer i & 1 was last read by the o product of
+  // tile i - 2, which completed before store_o(i - 2) in the previous iteration.
   for (int i = 0; i < ntiles; ++i) {
-    if (i > 0 && !store_o(i - 1)) break;
     if (!mbar_wait_spin(&B.zq_full, i & 1, abort)) break;
     tc_fence_after();
     float z1[64], z3[64];
@@ -226,12 +235,13 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
       r0[m] = hp[m];
       r1[m] = hp[16 + m];
     }
-    tmem_st16(tb + lane_base + A_H + 32 * half, r0);
-    tmem_st16(tb + lane_base + A_H + 32 * half + 16, r1);
+    tmem_st16(tb + lane_base + A_H + 64 * (i & 1) + 32 * half, r0);
+    tmem_st16(tb + lane_base + A_H + 64 * (i & 1) + 32 * half + 16, r1);
     tmem_st_wait();
     tc_fence_before();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&B.h_full);
+    if (lane == 0) mbar_arrive(&B.h_full[i & 1]);
+    if (i > 0 && !store_o(i - 1)) break;
   }
   if (!*abort) store_o(ntiles - 1);
 }
@@ -257,8 +267,11 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
     }
     mbar_init(&B.zq_full, 1);
     mbar_init(&B.zq_free, 8);
-    mbar_init(&B.h_full, 8);
-    mbar_init(&B.o_full, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&B.h_full[i], 8);   // the epilogue wrote h buffer i
+      mbar_init(&B.o_full[i], 1);   // the o product of buffer i completed
+      mbar_init(&B.o_free[i], 8);   // the epilogue read o accumulator i
+    }
     B.abort_flag = 0;
     fence_barrier_init();
     prefetch_tmap(&maps.q);
