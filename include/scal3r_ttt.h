@@ -25,9 +25,11 @@
  * (the weights of a head stay on chip for a chunk); head_dim and hidden that
  * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
  * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
- * step as a large tcgen05 GEMM, forward and backward.  The wide path takes
- * the dot loss; the autotuner is for the head_dim-64 path
- * (SCAL3R_ERR_UNSUPPORTED otherwise).
+ * step as a large tcgen05 GEMM, forward and backward.  The wide path also
+ * takes the squared-error loss, per-matrix learning rates (lr_per_matrix) and
+ * sparse checkpoints (ckpt_every > 1); the head_dim-64 path takes the dot loss
+ * with one rate per token and a checkpoint per chunk, and the autotuner is for
+ * it (SCAL3R_ERR_UNSUPPORTED otherwise).  The float32 path takes either loss.
  *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
