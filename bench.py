@@ -307,7 +307,8 @@ def amu_leg(args, dev, peak_tflops):
 def amu_variants(args, dev, peak_tflops):
     """Forward+backward at the paper's AMU shape (workload bf16_amu1024) for the
     layer's options: the squared-error loss, per-matrix learning rates, sparse
-    checkpoints (every 4th chunk), the GCM module around the layer, and the
+    checkpoints (every 4th chunk), the state-size ablation's smaller hidden
+    sizes (k = 1, 2), the GCM module around the layer, and the
     forward as the Global Context Synchronisation split loop (partial
     gradient, update, apply per chunk; one shard, so no collective).  Each:
     tokens/s over the timed steps (L2 flushed between steps) and the GEMM rate
@@ -363,13 +364,13 @@ def amu_variants(args, dev, peak_tflops):
     out = {"workload": w.name, "timing": "direct launches, event pair per step, 256 MB written between steps; "
                                          "GEMM rate from per-launch events (the profiler on)"}
 
-    def layer_fwd_bwd(layer, lr):
+    def layer_fwd_bwd(layer, lr, w=w0):
         ws = torch.empty(ttt.scal3r_ttt_workspace_size(layer.handle, off, ptr, True), dtype=torch.uint8, device=dev)
         o = torch.empty_like(q)
 
         def fn():
-            _, ck, wn, _ = layer.forward(q, k, v, lr, w0, off, ptr, workspace=ws, o=o)
-            layer.backward(q, k, v, lr, w0, off, ptr, d_o, ck, wn, workspace=ws)
+            _, ck, wn, _ = layer.forward(q, k, v, lr, w, off, ptr, workspace=ws, o=o)
+            layer.backward(q, k, v, lr, w, off, ptr, d_o, ck, wn, workspace=ws)
         return fn
 
     for name, kw, lr in (("mse_fwdbwd", {"loss": "mse"}, lr1), ("per_matrix_lr_fwdbwd", {"lr_per_matrix": True}, lr3),
@@ -380,6 +381,17 @@ def amu_variants(args, dev, peak_tflops):
             slots = ttt.scal3r_ttt_ckpt_slots(layer.handle, ptr)
             out[name]["checkpoint_bytes"] = slots * H * 3 * F * D * 4
             out[name]["dense_checkpoint_bytes"] = (len(off) - 1) * H * 3 * F * D * 4
+        layer.close()
+
+    # the state-size ablation: hidden k * hd for k = 1, 2 (the AMU itself is k = 4)
+    for kk in (1, 2):
+        Fk = kk * D
+        layer = ttt.TTT(H, D, Fk, dtype=torch.bfloat16)
+        name = f"state_k{kk}_fwdbwd"
+        out[name] = timed(layer_fwd_bwd(layer, lr1, w0[:, :3 * Fk * D].contiguous()), layer)
+        out[name]["hidden"] = Fk
+        out[name]["state_bytes_fp32"] = 3 * Fk * D * 4
+        out[name]["step_tflops"] = 54.0 * T * D * Fk / (out[name]["ms_per_step"] / 1e3) / 1e12
         layer.close()
 
     # the GCM module (Eq. 5) around the layer: d = H * D

@@ -864,7 +864,10 @@ struct WideBufs {
   float* rgr;     // backward with sparse checkpoints: the recomputed chunk gradient
   float* seg;     // backward with sparse checkpoints: W_j of one segment, ckpt_every - 1 blocks of P
   __nv_bfloat16* ex[2];   // squared-error loss: [mmax x D] bf16 (forward: e, eta2 e; backward: e, dY)
+  float* spl;     // partial planes of the split weight-sized reductions (null: none split)
 };
+
+int split_count(int64_t M, int64_t N, int64_t K, int out_fp32);
 
 // d eta partials per token row: one per 64 hidden units (the update-VJP
 // gate's tiles), times three with per-matrix rates.
@@ -900,6 +903,11 @@ size_t layout_bytes(const Plan& p, const Shape& s, bool bwd, int ckpt_every, boo
   }
   if (mse)
     for (int i = 0; i < 2; ++i) x.ex[i] = reinterpret_cast<__nv_bfloat16*>(take((size_t)mmax * s.D * 2));
+  // the [F x D] and [D x F] reductions over a chunk's tokens split their K
+  // ranges when their tiles leave SMs idle; the longest chunk needs the most
+  // ranges (split_count does not fall as K grows)
+  const int nspl = mmax > 0 ? std::max(split_count(s.F, s.D, mmax, 1), split_count(s.D, s.F, mmax, 1)) : 1;
+  if (nspl > 1) x.spl = reinterpret_cast<float*>(take((size_t)nspl * s.F * s.D * 4));
   if (w) *w = x;
   return o;
 }
@@ -1013,24 +1021,21 @@ int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n) {
 namespace {
 
 // K ranges of a float32-output GEMM whose output tiles do not fill the SMs:
-// the count s (>= 2) that minimises the rounds of work units, ceil(tiles s /
-// SMs) / s, with every range at least 4 K blocks long; 1 = no split.
+// as many ranges as fit the SMs in one round (tiles x s <= SMs), each at
+// least 4 K blocks long; 1 = no split.  Ranges beyond one round would trim
+// the last round a little, but each adds a partial plane to the fixed-order
+// sum: at 32 tiles of 128 x 256 and 16,656 tokens of K, 19 ranges (4 rounds)
+// take 16 % less GEMM time than 4 ranges (1 round) and write and re-read
+// 76 MB of planes instead of 16 MB, which costs more than it saves.  The
+// count never falls as K grows, so a workspace sized for the longest K holds
+// the planes of any shorter one.
 int split_count(int64_t M, int64_t N, int64_t K, int out_fp32) {
   if (!out_fp32) return 1;
   const int64_t tiles = ((M + BM - 1) / BM) * (N / BN);
-  const int sms = num_sms();
   const int64_t nk = (K + BK - 1) / BK;
-  if (tiles <= 0 || tiles * 2 > sms) return 1;
-  int best = 1;
-  double best_t = 1.0;
-  for (int s = 2; s <= 64 && nk / s >= 4; ++s) {
-    const double t = (double)((tiles * s + sms - 1) / sms) / s;
-    if (t < best_t - 1e-9) {
-      best_t = t;
-      best = s;
-    }
-  }
-  return best;
+  if (tiles <= 0) return 1;
+  const int64_t s = std::min<int64_t>(std::min<int64_t>(num_sms() / tiles, nk / 4), 64);
+  return s >= 2 ? (int)s : 1;
 }
 
 // C (+)= the sum of the partial planes in order s = 0 .. S-1 (fixed order:
@@ -1052,6 +1057,34 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64
     }
     *dst = acc;
   }
+}
+
+// A float32 reduction over a chunk's tokens, C = A^T B or C += A^T B with K
+// = the chunk's tokens (the weight gradients and adjoints): when its output
+// tiles leave SMs idle, K is cut into split_count ranges whose partial planes
+// go to `spl`, then summed in a fixed order onto C (the sum does not depend
+// on which CTA finished first).  Unsplit when spl is null or the tiles fill
+// the SMs.  The reduce is charged to the GEMM's kind.
+cudaError_t run_gemm_red(const Ctx& c, GemmArgs& a, double flops, float* spl) {
+  const bool acc = a.epi == EPI_F32_ADD;
+  const int S = (a.nseg <= 1 && (acc || a.epi == EPI_F32)) ? split_count(a.M, a.N, a.K, 1) : 1;
+  if (S <= 1 || !spl) return run_gemm(c, a, flops);
+  const int nk = (a.K + BK - 1) / BK;
+  float* const out = reinterpret_cast<float*>(a.out[0]);
+  const int64_t ldo = a.ld_out, M = a.M, N = a.N;
+  a.epi = EPI_F32;
+  a.out[0] = spl;
+  a.ld_out = N;
+  a.kb_split = (nk + S - 1) / S;
+  a.ksplit = (nk + a.kb_split - 1) / a.kb_split;   // every range non-empty
+  a.split_stride = M * N;
+  WIDE_TRY(run_gemm(c, a, flops));
+  const int ks = a.ksplit;
+  const int blocks = (int)std::min<int64_t>((M * (N / 4) + 255) / 256, 8 * (int64_t)num_sms());
+  return c.launch(0, 0, 0, [&] {
+    split_reduce_kernel<<<blocks, 256, 0, c.st>>>(spl, ks, M * N, M, N, out, ldo, acc ? 1 : 0);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace
@@ -1121,7 +1154,7 @@ namespace {
 //   U = gate(K), [e, eta2 e] = U W2^T - V, P = e W2, gate(K) with p -> g1 = eta1 p z3 s', g3 = eta3 p a;
 //   G1 = g1^T K, G3 = g3^T K, G2 = (eta2 e)^T U.
 cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
-                         __nv_bfloat16* const* ex) {
+                         __nv_bfloat16* const* ex, float* spl) {
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F;
@@ -1172,14 +1205,14 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
     WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
     a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
     a.epi = EPI_F32; a.out[0] = gr + (size_t)j * F * D; a.ld_out = D;
-    WIDE_TRY(run_gemm(cx, a, mfd));
+    WIDE_TRY(run_gemm_red(cx, a, mfd, spl));
   }
   {   // G2 = (eta2 e)^T U
     GemmArgs a{};
     WIDE_MAP(mat_map(&a.a[0], e2b, M, D, 64) && mat_map(&a.b[0], ub, M, F, 64));
     a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1;
     a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
-    WIDE_TRY(run_gemm(cx, a, mfd));
+    WIDE_TRY(run_gemm_red(cx, a, mfd, spl));
   }
   return cudaSuccess;
 }
@@ -1188,8 +1221,8 @@ cudaError_t key_grad_mse(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, f
 // into gr (P floats, packed like the weights).  act: four [M x F] bf16 buffers;
 // ex: two [M x D] bf16 buffers (squared-error loss only).
 cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float* gr, __nv_bfloat16* const* act,
-                     __nv_bfloat16* const* ex) {
-  if (cx.prm.loss == SCAL3R_LOSS_MSE) return key_grad_mse(cx, h, c, wb, gr, act, ex);
+                     __nv_bfloat16* const* ex, float* spl) {
+  if (cx.prm.loss == SCAL3R_LOSS_MSE) return key_grad_mse(cx, h, c, wb, gr, act, ex, spl);
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int H = sh.H, D = sh.D, F = sh.F, R = sh.R();
@@ -1222,14 +1255,14 @@ cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float
     WIDE_MAP(mat_map(&a.a[0], j ? g3 : g1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
     a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
     a.epi = EPI_F32; a.out[0] = gr + (size_t)j * F * D; a.ld_out = D;
-    WIDE_TRY(run_gemm(cx, a, mfd));
+    WIDE_TRY(run_gemm_red(cx, a, mfd, spl));
   }
   {   // G2 = V^T u~
     GemmArgs a{};
     WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], ut, M, F, 64));
     a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
     a.epi = EPI_F32; a.out[0] = gr + 2 * (size_t)F * D; a.ld_out = F;
-    WIDE_TRY(run_gemm(cx, a, mfd));
+    WIDE_TRY(run_gemm_red(cx, a, mfd, spl));
   }
   return cudaSuccess;
 }
@@ -1238,8 +1271,9 @@ cudaError_t key_grad(const Ctx& cx, int h, int c, const __nv_bfloat16* wb, float
 // normalise(W - G) in place; optionally the checkpoint, the pre-normalisation
 // row norms and w_final are written.  gr: the gradient buffer (P floats).
 cudaError_t key_update(const Ctx& cx, int h, int c, float* wm, __nv_bfloat16* wb, const float* rho, float* gr,
-                       __nv_bfloat16* const* act, __nv_bfloat16* const* ex, float* ck, float* wn, float* wf) {
-  WIDE_TRY(key_grad(cx, h, c, wb, gr, act, ex));
+                       __nv_bfloat16* const* act, __nv_bfloat16* const* ex, float* spl, float* ck, float* wn,
+                       float* wf) {
+  WIDE_TRY(key_grad(cx, h, c, wb, gr, act, ex, spl));
   const Shape& sh = cx.sh;
   const Params& prm = cx.prm;
   const int D = sh.D, F = sh.F, R = sh.R();
@@ -1285,7 +1319,7 @@ cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int
         float* ck = (prm.w_ckpt && slot >= 0) ? prm.w_ckpt + ((size_t)slot * H + h) * P : nullptr;
         float* wn = prm.wnorm ? prm.wnorm + ((size_t)c * H + h) * R : nullptr;
         float* wf = (prm.w_final && c == c1 - 1) ? prm.w_final + ((size_t)s * H + h) * P : nullptr;
-        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, w.ex, ck, wn, wf));
+        WIDE_TRY(key_update(cx, h, c, w.wm, w.wb, w.rho, w.gr, w.act, w.ex, w.spl, ck, wn, wf));
         {   // apply: h = silu(Q W1^T) o (Q W3^T)
           GemmArgs a{};
           WIDE_MAP(tok_map(&a.a[0], prm.q, T, H, D, 128) && mat_map(&a.b[0], w1, F, D, 128) &&
@@ -1369,7 +1403,7 @@ cudaError_t wide_partial_grad(const Plan& pl, const Shape& sh, const Params& prm
         wide_prep_kernel<<<R, ROW_THREADS, 0, st>>>(wsrc, w.wm, w.wb, nullptr, D, F, prm.norm);
         return cudaGetLastError();
       }));
-      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act, w.ex));
+      WIDE_TRY(key_grad(cx, h, c0, w.wb, gout, w.act, w.ex, w.spl));
     }
   }
   return cudaSuccess;
@@ -1538,7 +1572,7 @@ cudaError_t update_vjp_mse(const Ctx& cx, int h, int64_t t0, int M, const WideBu
     WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
     a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
     a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
-    WIDE_TRY(run_gemm(cx, a, mfd));
+    WIDE_TRY(run_gemm_red(cx, a, mfd, w.spl));
   }
   {   // lam2 += e^T dP + dY^T U: one reduction over both token segments
     const int kseg = (M + BK - 1) / BK * BK;
@@ -1605,7 +1639,7 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
           return cudaGetLastError();
         }));
         for (int jj = j0; jj < j1; ++jj)
-          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.ex,
+          WIDE_TRY(key_update(cx, h, c0 + jj, w.wm, w.wb, w.rho, w.rgr, w.act, w.ex, w.spl,
                               w.seg + (size_t)(jj - j0) * P, nullptr, nullptr));
       }
       for (int j = j1; j >= j0; --j) {
@@ -1650,14 +1684,14 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.q, T, H, D, 64));
             a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
             a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
-            WIDE_TRY(run_gemm(cx, a, mfd));
+            WIDE_TRY(run_gemm_red(cx, a, mfd, w.spl));
           }
           {   // lam2 += d_O^T uq
             GemmArgs a{};
             WIDE_MAP(tok_map(&a.a[0], prm.d_o, T, H, D, 64) && mat_map(&a.b[0], uq, M, F, 64));
             a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
             a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
-            WIDE_TRY(run_gemm(cx, a, mfd));
+            WIDE_TRY(run_gemm_red(cx, a, mfd, w.spl));
           }
         }
         if (key && mse) {   // update VJP of chunk j, squared-error loss
@@ -1719,14 +1753,14 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
             WIDE_MAP(mat_map(&a.a[0], i ? dz3 : dz1, M, F, 64) && tok_map(&a.b[0], prm.k, T, H, D, 64));
             a.M = F; a.N = D; a.K = M; a.a_mn = 1; a.b_mn = 1; a.hb = h; a.yb = (int)t0;
             a.epi = EPI_F32_ADD; a.out[0] = i ? lam3 : lam1; a.ld_out = D;
-            WIDE_TRY(run_gemm(cx, a, mfd));
+            WIDE_TRY(run_gemm_red(cx, a, mfd, w.spl));
           }
           {   // lam2 += V^T (-dp)
             GemmArgs a{};
             WIDE_MAP(tok_map(&a.a[0], prm.v, T, H, D, 64) && mat_map(&a.b[0], dpe, M, F, 64));
             a.M = D; a.N = F; a.K = M; a.a_mn = 1; a.b_mn = 1; a.ha = h; a.ya = (int)t0;
             a.epi = EPI_F32_ADD; a.out[0] = lam2; a.ld_out = F;
-            WIDE_TRY(run_gemm(cx, a, mfd));
+            WIDE_TRY(run_gemm_red(cx, a, mfd, w.spl));
           }
           WIDE_TRY(chunk_deta(cx, w.part, t0, h, M));
         }

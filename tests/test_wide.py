@@ -132,6 +132,24 @@ def test_wide_backward_paper_shape_matches_oracle():
     _check_grads(grads, rb)
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_wide_state_size_ablation_hd1024_forward_backward(k):
+    """The paper's state-size ablation: one head, hd 1024, hidden k * hd with
+    k = 1 and 2 (the AMU uses k = 4); forward outputs and every gradient, two
+    chunks off the 128-token tile.  The first chunk is long enough (16 and
+    10 K blocks of 64 tokens) for the weight-sized reductions, whose 32 and
+    64 output tiles leave most SMs idle, to run split over K (4 and 2
+    ranges) and be summed in a fixed order."""
+    H, D, F = 1, 1024, 1024 * k
+    lengths = [[1000 if k == 1 else 600, 141]]
+    _, lay, x, out = _run(H, D, F, lengths, seed=56 + k)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+    _, lay, x, grads = _fwd_bwd(H, D, F, lengths, seed=58 + k)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
 def test_wide_backward_graph_replay_is_bitwise_equal():
     import torch
     layer, lay, x, a = _fwd_bwd(1, 256, 512, [[300, 200]], seed=54)
@@ -142,15 +160,33 @@ def test_wide_backward_graph_replay_is_bitwise_equal():
             assert torch.equal(u, w)
 
 
+def test_wide_split_reductions_match_oracle():
+    """Chunks of 2600 and 900 tokens at hd 256, hidden 512 (4 output tiles
+    per weight-sized reduction): the reductions run in 10 and 3 K ranges
+    whose partial planes are summed in a fixed order; two heads, forward
+    and backward."""
+    H, D, F = 2, 256, 512
+    lengths = [[2600, 300], [900]]
+    _, lay, x, out = _run(H, D, F, lengths, seed=63)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    _check(out, ref)
+    _, lay, x, grads = _fwd_bwd(H, D, F, lengths, seed=64)
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=1e-6)
+    _check_grads(grads, rb)
+
+
+@pytest.mark.parametrize("lengths", [[[200, 256, 70, 130, 90], [140, 60]], [[1100, 256, 700, 130, 90], [140, 600]]],
+                         ids=["short", "split"])
 @pytest.mark.parametrize("n", [2, 3])
-def test_wide_sparse_checkpoints_are_bitwise_the_dense_ones(n):
+def test_wide_sparse_checkpoints_are_bitwise_the_dense_ones(n, lengths):
     """ckpt_every = n stores the weights after local chunks n-1, 2n-1, ... of
     each sequence; the backward recomputes the rest with the forward's own
-    steps, so every output equals the every-chunk run bit for bit."""
+    steps, so every output equals the every-chunk run bit for bit (also
+    when the chunks are long enough for the weight-sized reductions to run
+    split over K)."""
     import torch
     import paper_2604_08542_gb300 as ttt
     H, D, F = 1, 256, 512
-    lengths = [[200, 256, 70, 130, 90], [140, 60]]
     lay = syn.layout_from_lengths(lengths)
     x = syn.make_inputs(lay.num_tokens, H, D, F, seed=55, dtype="bf16", with_grad_out=True)
     g = upload(x, torch.bfloat16)
