@@ -77,6 +77,8 @@ extern "C" {
 #define SCAL3R_ERR_NO_DEVICE      7  /* no sm_103 device current */
 #define SCAL3R_ERR_NONFINITE      8  /* a NaN or infinity in an input or output (finite checking on;
                                         reported through scal3r_ttt_get_status) */
+#define SCAL3R_ERR_BOUNDS         9  /* bounds-checking build: a kernel access left every byte range
+                                        the call registered (reported through scal3r_ttt_get_status) */
 
 /* config values */
 #define SCAL3R_FP32         0   /* q,k,v,o float32: plain SIMT path */
@@ -333,6 +335,29 @@ int scal3r_ttt_get_status(scal3r_ttt_handle* handle, void* stream);
  * word to SCAL3R_ERR_NONFINITE, read by scal3r_ttt_get_status.  The scans are
  * memory-bound reads of those tensors; the call's own results are unchanged. */
 int scal3r_ttt_set_finite_check(scal3r_ttt_handle* handle, int32_t enable);
+
+/* Bounds checking.  A library built with SCAL3R_DEBUG_BOUNDS (the build
+ * script's "bounds" variant) registers, for each scal3r_ttt_forward and
+ * scal3r_ttt_backward call on a wide-weight handle (head_dim and hidden
+ * multiples of 256), the byte range of every tensor the call was given and of
+ * its workspace.  Every plain global load and store of the wide-weight
+ * kernels must then fall inside one of them; one that does not is skipped
+ * (a load reads zeros) and the status word becomes SCAL3R_ERR_BOUNDS.  TMA
+ * copies are bounded by their tensor maps and are not checked here.  The
+ * extents registered are:
+ *   q, k, v, o, d_o, dq, dk, dv: T*H*D elements of the dtype;
+ *   lr, dlr: T*H (or T*H*3) floats;  w0, dw0: H*P floats, or
+ *   (S-1)*w0_seq_stride + H*P;  w_ckpt: slots*H*P;  wnorm: C*H*(2F+D);
+ *   w_final: S*H*P floats;  workspace: the bytes passed.
+ * scal3r_ttt_debug_bounds(handle, tensor, shrink_bytes) registers tensor
+ * number `tensor` (0 q, 1 k, 2 v, 3 lr, 4 w0, 5 o, 6 w_ckpt, 7 wnorm,
+ * 8 w_final, 9 d_o, 10 dq, 11 dk, 12 dv, 13 dlr, 14 dw0, 15 workspace)
+ * shrink_bytes shorter on the handle's following calls (0 restores it): a
+ * test sees a violation reported while every access stays inside the real
+ * buffer.  tensor = -1 only reports the build.  Returns SCAL3R_OK in a
+ * bounds-checking build, SCAL3R_ERR_UNSUPPORTED otherwise,
+ * SCAL3R_ERR_INVALID_ARG for a bad index or a negative shrink. */
+int scal3r_ttt_debug_bounds(scal3r_ttt_handle* handle, int32_t tensor, int64_t shrink_bytes);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libscal3r_ttt.so")
+# SCAL3R_TTT_LIBRARY selects another build of the same ABI (the
+# bounds-checking variant, libscal3r_ttt_bounds.so).
+LIB_PATH = os.environ.get("SCAL3R_TTT_LIBRARY") or os.path.join(_HERE, "libscal3r_ttt.so")
 
 SCAL3R_OK = 0
 SCAL3R_ERR_INVALID_ARG = 1
@@ -29,6 +31,7 @@ SCAL3R_ERR_TIMEOUT = 5
 SCAL3R_ERR_WORKSPACE = 6
 SCAL3R_ERR_NO_DEVICE = 7
 SCAL3R_ERR_NONFINITE = 8
+SCAL3R_ERR_BOUNDS = 9
 
 SCAL3R_FP32 = 0
 SCAL3R_BF16 = 1
@@ -50,7 +53,7 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
             "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
-            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_ttt_set_finite_check", "scal3r_gcm_workspace_size",
+            "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_ttt_set_finite_check", "scal3r_ttt_debug_bounds", "scal3r_gcm_workspace_size",
             "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
 
 
@@ -123,6 +126,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.scal3r_ttt_profile_read.restype = ctypes.c_int
+    lib.scal3r_ttt_debug_bounds.argtypes = [vp, i32, i64]
+    lib.scal3r_ttt_debug_bounds.restype = ctypes.c_int
     lib.scal3r_ttt_get_status.argtypes = [vp, vp]
     lib.scal3r_ttt_get_status.restype = ctypes.c_int
     lib.scal3r_ttt_partial_grad.argtypes = [vp, vp, vp, vp, vp, i64, vp, i32, vp, i32, vp, vp, sz, vp]
@@ -316,6 +321,13 @@ def scal3r_ttt_gemm(handle, a, lda, a_kmajor, b, ldb, b_kmajor, c, ldc, out_fp32
     return load_library().scal3r_ttt_gemm(handle, a, lda, int(a_kmajor), b, ldb, int(b_kmajor), c, ldc,
                                           int(out_fp32), int(accumulate), M, N, K, workspace, workspace_bytes,
                                           stream)
+
+
+def scal3r_ttt_debug_bounds(handle: int, tensor: int, shrink_bytes: int) -> int:
+    """Bounds-checking build: register tensor number `tensor` shrink_bytes
+    shorter on the following calls.  Returns the status: SCAL3R_OK in that
+    build, SCAL3R_ERR_UNSUPPORTED in the ordinary one."""
+    return int(load_library().scal3r_ttt_debug_bounds(handle, int(tensor), int(shrink_bytes)))
 
 
 def scal3r_ttt_set_finite_check(handle: int, enable: bool) -> None:

@@ -2,7 +2,10 @@
 
 Compiles every translation unit under ``csrc/`` for sm_103a in parallel with
 nvcc and links ``libscal3r_ttt.so`` next to this file.  Rebuilds only when a
-source or header is newer than the library.
+source or header is newer than the library.  The "bounds" variant compiles the
+same sources with SCAL3R_DEBUG_BOUNDS into ``libscal3r_ttt_bounds.so``: the
+wide-weight kernels then check every plain global access against the byte
+ranges each call registers (see scal3r_ttt_debug_bounds in the header).
 """
 from __future__ import annotations
 
@@ -40,23 +43,33 @@ def _deps() -> list[str]:
         glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+VARIANTS = {"": [], "bounds": ["-DSCAL3R_DEBUG_BOUNDS"]}
+
+
+def lib_path(variant: str = "") -> str:
+    return LIB if not variant else os.path.join(HERE, f"libscal3r_ttt_{variant}.so")
+
+
+def up_to_date(variant: str = "") -> bool:
+    lib = lib_path(variant)
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
+def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None, variant: str = "") -> str:
     """Compile and link; returns the library path."""
-    if not force and up_to_date():
+    LIB = lib_path(variant)
+    BUILD_DIR = BUILD if not variant else BUILD + "_" + variant
+    if not force and up_to_date(variant):
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(BUILD_DIR, exist_ok=True)
     nvcc = _nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + VARIANTS[variant]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, *FLAGS, *extra, "-x", "c++", "-c", src, "-o", obj]

@@ -8,6 +8,7 @@
 //                    update(j)  W_{j+1} = normalise(W_j + sum of pieces)
 // Backward, for j = n .. 0: sweep(j) (VJP pieces of chunk j's update and
 // chunk j-1's apply, at W_j), update(j) (normalisation VJP), then dw0.
+#include <algorithm>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include <cstring>
@@ -15,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/scal3r_gcm.h"
+#include "bounds.cuh"
 #include "ttt_internal.h"
 
 namespace scal3r {
@@ -55,6 +57,9 @@ cudaError_t wide_apply_update(const Shape& sh, const Params& prm, int S, const f
 cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void* ws, const WideLaunch& launch,
                        cudaStream_t st);
 cudaError_t prepare_wide();
+#ifdef SCAL3R_DEBUG_BOUNDS
+cudaError_t wide_upload_bounds(const BoundsTable& t, cudaStream_t st);
+#endif
 cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
                          cudaStream_t st);
@@ -101,6 +106,7 @@ struct scal3r_ttt_handle {
   bool wide = false;            // BF16 wide-weight path (head_dim, hidden multiples of 256)
   bool timeout_test = false;    // scal3r_ttt_gemm runs the bounded-wait test
   bool finite_check = false;    // scan each call's tensors for NaN / infinity afterwards
+  int64_t bounds_shrink[16] = {};   // bounds-checking build: bytes taken off each registered tensor
   cudaStream_t capture_stream = nullptr;
   GraphSlot gfwd, gbwd;
 };
@@ -387,6 +393,7 @@ const char* scal3r_ttt_error_string(int status) {
     case SCAL3R_ERR_WORKSPACE: return "workspace missing or too small";
     case SCAL3R_ERR_NO_DEVICE: return "no sm_103 device";
     case SCAL3R_ERR_NONFINITE: return "a NaN or infinity in an input or output (finite checking on)";
+    case SCAL3R_ERR_BOUNDS: return "an access outside every registered range (bounds-checking build)";
     default: return "unknown status";
   }
 }
@@ -615,12 +622,93 @@ int scal3r_ttt_get_schedule(const scal3r_ttt_handle* hd, scal3r_ttt_schedule* sc
   return SCAL3R_OK;
 }
 
+// Bounds-checking build: the byte ranges of a call's tensors, in the order
+// of scal3r_ttt_debug_bounds (null entries are not registered), uploaded to
+// the wide-weight kernels' table before the call; bounds_end turns checking
+// off after it.  Without the build both do nothing.
+struct CallTensors {
+  const void* p[16] = {};
+  int64_t bytes[16] = {};
+};
+
+static CallTensors call_tensors(const scal3r_ttt_handle* hd, const void* q, const void* k, const void* v,
+                                const float* lr, const float* w0, int64_t w0_seq_stride, const int64_t* off,
+                                int32_t C, const int32_t* ptr, int32_t S, void* workspace, size_t workspace_bytes) {
+  CallTensors ct;
+  const int64_t T = off[C], H = hd->shape.H, D = hd->shape.D, P = hd->shape.P(), R = hd->shape.R();
+  const int64_t elt = hd->cfg.dtype == SCAL3R_BF16 ? 2 : 4;
+  const int64_t nr = hd->cfg.lr_per_matrix ? 3 : 1;
+  const int64_t wbytes = ((w0_seq_stride ? (int64_t)(S - 1) * w0_seq_stride : 0) + H * P) * 4;
+  int64_t slots = 0;
+  scal3r_ttt_ckpt_slots(hd, ptr, S, &slots);
+  const void* p[16] = {q, k, v, lr, w0};
+  const int64_t b[16] = {T * H * D * elt, T * H * D * elt, T * H * D * elt, T * H * nr * 4, wbytes,
+                         T * H * D * elt, slots * H * P * 4, (int64_t)C * H * R * 4, (int64_t)S * H * P * 4,
+                         T * H * D * elt, T * H * D * elt, T * H * D * elt, T * H * D * elt, T * H * nr * 4, wbytes,
+                         (int64_t)workspace_bytes};
+  for (int i = 0; i < 16; ++i) {
+    ct.p[i] = p[i];
+    ct.bytes[i] = b[i];
+  }
+  ct.p[15] = workspace;
+  return ct;
+}
+
+#ifdef SCAL3R_DEBUG_BOUNDS
+constexpr bool kBoundsBuild = true;
+#else
+constexpr bool kBoundsBuild = false;
+#endif
+
+// A checked call: the bounds-checking build, a wide-weight handle and a
+// layout its planner accepts (the tensors' extents come from the plan).
+static bool bounds_on(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S) {
+  return kBoundsBuild && hd && hd->wide && ensure_plan(hd, off, C, ptr, S) == SCAL3R_OK;
+}
+
+static void bounds_begin(const scal3r_ttt_handle* hd, const CallTensors& ct, cudaStream_t st) {
+#ifdef SCAL3R_DEBUG_BOUNDS
+  BoundsTable t{};
+  t.status = hd->d_status;
+  for (int i = 0; i < 16 && t.n < kMaxBoundsRanges; ++i) {
+    if (!ct.p[i] || ct.bytes[i] <= 0) continue;
+    const int64_t len = std::max<int64_t>(0, ct.bytes[i] - hd->bounds_shrink[i]);
+    t.lo[t.n] = reinterpret_cast<uint64_t>(ct.p[i]);
+    t.hi[t.n] = t.lo[t.n] + (uint64_t)len;
+    ++t.n;
+  }
+  if (t.n == 0) t.n = 1;   // nothing registered: every checked access is outside (lo = hi = 0)
+  wide_upload_bounds(t, st);
+#else
+  (void)hd; (void)ct; (void)st;
+#endif
+}
+
+static void bounds_end(cudaStream_t st) {
+#ifdef SCAL3R_DEBUG_BOUNDS
+  BoundsTable t{};
+  wide_upload_bounds(t, st);
+#else
+  (void)st;
+#endif
+}
+
 int scal3r_ttt_forward(scal3r_ttt_handle* hd, const void* q, const void* k, const void* v, const float* lr,
                        const float* w0, int64_t w0_seq_stride, const int64_t* off, int32_t C,
                        const int32_t* ptr, int32_t S, void* o, float* w_ckpt, float* wnorm, float* w_final,
                        void* workspace, size_t workspace_bytes, void* stream) {
+  const bool chk = bounds_on(hd, off, C, ptr, S);
+  if (chk) {
+    CallTensors ct = call_tensors(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, workspace, workspace_bytes);
+    ct.p[5] = o;
+    ct.p[6] = w_ckpt;
+    ct.p[7] = wnorm;
+    ct.p[8] = w_final;
+    bounds_begin(hd, ct, (cudaStream_t)stream);
+  }
   int rc = forward_impl(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, o, w_ckpt, wnorm, w_final, workspace,
                         workspace_bytes, stream);
+  if (chk) bounds_end((cudaStream_t)stream);
   if (rc != SCAL3R_OK || !hd->finite_check) return rc;
   // inputs and outputs of the call (shapes as checked by forward_impl)
   const int64_t T = off[C], H = hd->shape.H, D = hd->shape.D, P = hd->shape.P();
@@ -643,8 +731,22 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         const int32_t* ptr, int32_t S, const void* d_o, const float* w_ckpt,
                         const float* wnorm, void* dq, void* dk, void* dv, float* dlr, float* dw0,
                         void* workspace, size_t workspace_bytes, void* stream) {
+  const bool chk = bounds_on(hd, off, C, ptr, S);
+  if (chk) {
+    CallTensors ct = call_tensors(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, workspace, workspace_bytes);
+    ct.p[6] = w_ckpt;
+    ct.p[7] = wnorm;
+    ct.p[9] = d_o;
+    ct.p[10] = dq;
+    ct.p[11] = dk;
+    ct.p[12] = dv;
+    ct.p[13] = dlr;
+    ct.p[14] = dw0;
+    bounds_begin(hd, ct, (cudaStream_t)stream);
+  }
   int rc = backward_impl(hd, q, k, v, lr, w0, w0_seq_stride, off, C, ptr, S, d_o, w_ckpt, wnorm, dq, dk, dv, dlr,
                          dw0, workspace, workspace_bytes, stream);
+  if (chk) bounds_end((cudaStream_t)stream);
   if (rc != SCAL3R_OK || !hd->finite_check) return rc;
   const int64_t T = off[C], H = hd->shape.H, D = hd->shape.D, P = hd->shape.P();
   const bool bf = hd->cfg.dtype == SCAL3R_BF16;
@@ -658,6 +760,16 @@ int scal3r_ttt_backward(scal3r_ttt_handle* hd, const void* q, const void* k, con
   if (e == cudaSuccess) e = finite_scan(s_, dlr, T * H * nr, false, sms, st);
   if (e == cudaSuccess) e = finite_scan(s_, dw0, (w0_seq_stride ? S : 1) * H * P, false, sms, st);
   return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_ttt_debug_bounds(scal3r_ttt_handle* hd, int32_t tensor, int64_t shrink_bytes) {
+  if (!hd || tensor < -1 || tensor >= 16 || shrink_bytes < 0) return SCAL3R_ERR_INVALID_ARG;
+#ifdef SCAL3R_DEBUG_BOUNDS
+  if (tensor >= 0) hd->bounds_shrink[tensor] = shrink_bytes;
+  return SCAL3R_OK;
+#else
+  return SCAL3R_ERR_UNSUPPORTED;
+#endif
 }
 
 int scal3r_ttt_set_finite_check(scal3r_ttt_handle* hd, int32_t enable) {

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "sm100.cuh"
+#include "bounds.cuh"
 #include "ttt_internal.h"
 
 namespace scal3r {
@@ -105,6 +106,7 @@ __device__ __forceinline__ float silu_d(float z, float& sg) {
 // of an epilogue writes its own row, so a warp's store touches 32 rows: the
 // wider store halves the transactions per byte.
 __device__ __forceinline__ void st_global_v8(void* dst, const uint32_t (&a)[8]) {
+  if (!in_bounds(dst, 32)) return;
   asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
                :: "l"(dst), "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7])
                : "memory");
@@ -161,6 +163,18 @@ __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* 
   }
 }
 
+// A 16-byte read-only load (zeros when bounds checking rejects it).
+__device__ __forceinline__ uint4 ldg16(const uint4* p) {
+  return in_bounds(p, 16) ? __ldg(p) : make_uint4(0, 0, 0, 0);
+}
+
+// A null pointer is an unused operand; any other must lie inside a
+// registered range (bounds-checking build), else the block skips its work.
+#define ROW_CHECK(p, bytes)                                  \
+  do {                                                       \
+    if ((p) && !in_bounds((p), (uint32_t)(bytes))) return;   \
+  } while (0)
+
 // Persistent: CTA b takes output tiles b, b + gridDim.x, ... (consecutive
 // CTAs share an A row-block).  The TMA warp runs the stage ring across tiles;
 // the MMA warp alternates between two 256-column accumulators; epilogue group
@@ -171,6 +185,10 @@ __device__ __forceinline__ void unpack16(const uint4& a, const uint4& b, float* 
 // The three learning rates of output row m (W1, W3, W2).
 __device__ __forceinline__ void row_rates(const GemmArgs& g, int m, float& e1, float& e3, float& e2) {
   const float* ep = g.eta + (size_t)m * g.eta_stride;
+  if (!in_bounds(ep, 4 * (2 * g.eta_mat + 1))) {
+    e1 = e3 = e2 = 0.f;
+    return;
+  }
   e1 = ep[0];
   e3 = ep[g.eta_mat];
   e2 = ep[2 * g.eta_mat];
@@ -179,6 +197,7 @@ __device__ __forceinline__ void row_rates(const GemmArgs& g, int m, float& e1, f
 // One tile's d eta partials of row m: the three per-matrix sums, or their total.
 __device__ __forceinline__ void store_deta(const GemmArgs& g, int m, int tn, float q1, float q3, float q2) {
   float* p = g.part + (size_t)m * g.ld_part;
+  if (!in_bounds(p + (g.eta_mat ? 3 * tn : tn), g.eta_mat ? 12 : 4)) return;
   if (g.eta_mat) {
     p[3 * tn] = q1;
     p[3 * tn + 1] = q3;
@@ -326,8 +345,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             uint4 i0 = make_uint4(0, 0, 0, 0), i1 = i0;
             if (g.in0 && valid) {
               const uint4* ip = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
-              i0 = __ldg(ip);
-              i1 = __ldg(ip + 1);
+              i0 = ldg16(ip);
+              i1 = ldg16(ip + 1);
             }
             float acc[16];
             tmem_ld16(accb + c, acc);
@@ -383,8 +402,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             uint4 pw[2], uw[2];   // the inputs of the 16 columns, in flight during the TMEM loads
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-              pw[j] = valid ? __ldg(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
-              uw[j] = valid ? __ldg(up + c / 8 + j) : make_uint4(0, 0, 0, 0);
+              pw[j] = valid ? ldg16(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
+              uw[j] = valid ? ldg16(up + c / 8 + j) : make_uint4(0, 0, 0, 0);
             }
             uint32_t pk[3][8];   // 16 columns of each output, packed bf16 pairs
 #pragma unroll
@@ -445,6 +464,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
             st_bf16x16(o + 16, v1);
           } else {
             float4* o = reinterpret_cast<float4*>(part_plane + (size_t)m * g.ld_out + n0 + c);
+            if (!in_bounds(o, 128)) continue;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
               float4 x0 = make_float4(v0[4 * j], v0[4 * j + 1], v0[4 * j + 2], v0[4 * j + 3]);
@@ -473,8 +493,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
           uint4 pcur[2], ncur[2];   // the inputs of the 16 columns, in flight during the TMEM loads
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            pcur[j] = valid ? __ldg(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
-            ncur[j] = valid ? __ldg(np + c / 8 + j) : make_uint4(0, 0, 0, 0);
+            pcur[j] = valid ? ldg16(pp + c / 8 + j) : make_uint4(0, 0, 0, 0);
+            ncur[j] = valid ? ldg16(np + c / 8 + j) : make_uint4(0, 0, 0, 0);
           }
           uint32_t pk[6][8];   // 16 columns of each output, packed bf16 pairs
 #pragma unroll
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         if (g.epi != EPI_APPLY && valid) {
           const uint4* pp = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * g.ld_out + f0);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) prow[j] = __ldg(pp + j);
+          for (int j = 0; j < 16; ++j) prow[j] = ldg16(pp + j);
         }
         // on pairs of hidden units (packed float32 lanes); KEY scales the
         // factors by the rates, BAPPLY by 1
@@ -641,6 +661,10 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_prep_kernel(const float* __r
   size_t off;
   int len;
   row_geometry(blockIdx.x, D, F, off, len);
+  ROW_CHECK(w0 + off, 4 * len);
+  ROW_CHECK(wm + off, 4 * len);
+  ROW_CHECK(wb + off, 2 * len);
+  ROW_CHECK(rho ? rho + blockIdx.x : nullptr, 4);
   float ss = 0.f;
   for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
     const float4 x = *reinterpret_cast<const float4*>(w0 + off + i);
@@ -664,6 +688,13 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_update_kernel(float* __restr
   size_t off;
   int len;
   row_geometry(blockIdx.x, D, F, off, len);
+  ROW_CHECK(wm + off, 4 * len);
+  ROW_CHECK(gr + off, 4 * len);
+  ROW_CHECK(wb + off, 2 * len);
+  ROW_CHECK(norm == SCAL3R_NORM_NONE ? nullptr : rho + blockIdx.x, 4);
+  ROW_CHECK(wnorm ? wnorm + blockIdx.x : nullptr, 4);
+  ROW_CHECK(ckpt ? ckpt + off : nullptr, 4 * len);
+  ROW_CHECK(wfinal ? wfinal + off : nullptr, 4 * len);
   constexpr int kMaxPer = 4;   // float4 per thread: row length <= 4 * 4 * ROW_THREADS = 4096
   float4 x[kMaxPer];
   float ss = 0.f;
@@ -701,6 +732,9 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_bprep_kernel(const float* __
   size_t off;
   int len;
   row_geometry(blockIdx.x, D, F, off, len);
+  ROW_CHECK(w0 + off, 4 * len);
+  ROW_CHECK(rho + blockIdx.x, 4);
+  ROW_CHECK(drho + blockIdx.x, 4);
   float ss = 0.f;
   for (int i = 4 * threadIdx.x; i < len; i += 4 * ROW_THREADS) {
     const float4 x = *reinterpret_cast<const float4*>(w0 + off + i);
@@ -718,6 +752,11 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_bprep_kernel(const float* __
 __global__ void wide_bstep_setup_kernel(const float* __restrict__ w, const float* __restrict__ r,
                                         __nv_bfloat16* __restrict__ wb, __nv_bfloat16* __restrict__ nrb,
                                         float* __restrict__ lam, size_t P) {
+  ROW_CHECK(w, 4 * P);
+  ROW_CHECK(wb, 2 * P);
+  ROW_CHECK(r, 4 * P);
+  ROW_CHECK(r ? nrb : nullptr, 2 * P);
+  ROW_CHECK(lam, 4 * P);
   for (size_t i = 4 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x); i < P; i += 4 * (size_t)gridDim.x * blockDim.x) {
     const float4 x = *reinterpret_cast<const float4*>(w + i);
     *reinterpret_cast<uint2*>(wb + i) = make_uint2(pack_bf16(x.x, x.y), pack_bf16(x.z, x.w));
@@ -746,6 +785,20 @@ __global__ void __launch_bounds__(ROW_THREADS) wide_bupdate_kernel(const float* 
   size_t off;
   int len;
   row_geometry(blockIdx.x, D, F, off, len);
+  ROW_CHECK(rho + blockIdx.x, 4);
+  ROW_CHECK(lam + off, 4 * len);
+  if (dw0) {
+    ROW_CHECK(w0 + off, 4 * len);
+    ROW_CHECK(dw0 + off, 4 * len);
+    ROW_CHECK(norm == SCAL3R_NORM_ROW_W0 ? drho + blockIdx.x : nullptr, 4);
+  } else {
+    ROW_CHECK(rout + off, 4 * len);
+    if (norm != SCAL3R_NORM_NONE) {
+      ROW_CHECK(wj + off, 4 * len);
+      ROW_CHECK(wnorm + blockIdx.x, 4);
+      ROW_CHECK(norm == SCAL3R_NORM_ROW_W0 ? drho + blockIdx.x : nullptr, 4);
+    }
+  }
   const float rh = rho[blockIdx.x];
   if (dw0) {
     const float coef = (norm == SCAL3R_NORM_ROW_W0 && rh > 0.f) ? drho[blockIdx.x] / rh : 0.f;
@@ -798,6 +851,8 @@ __global__ void wide_deta_kernel(const float* __restrict__ part, int64_t ld_part
                                  float* __restrict__ dlr, int64_t stride, int M) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
+  ROW_CHECK(part + (size_t)m * ld_part, 4 * ntiles * nmat);
+  ROW_CHECK(dlr + (size_t)m * stride, 4 * nmat);
   for (int j = 0; j < nmat; ++j) {
     float a = 0.f;
     for (int t = 0; t < ntiles; ++t) a += part[(size_t)m * ld_part + (size_t)t * nmat + j];
@@ -1045,6 +1100,9 @@ __global__ void split_reduce_kernel(const float* __restrict__ part, int S, int64
   const int64_t nq = N / 4;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M * nq; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = i / nq, n = 4 * (i % nq);
+    if (!in_bounds(part + m * N + n, 16) || !in_bounds(part + (S - 1) * plane + m * N + n, 16) ||
+        !in_bounds(c + m * ldc + n, 16))
+      continue;
     float4 acc = *reinterpret_cast<const float4*>(part + m * N + n);
     for (int s = 1; s < S; ++s) {
       const float4 x = *reinterpret_cast<const float4*>(part + s * plane + m * N + n);
@@ -1778,5 +1836,9 @@ cudaError_t wide_backward(const Plan& pl, const Shape& sh, const Params& prm, in
   }
   return cudaSuccess;
 }
+
+#ifdef SCAL3R_DEBUG_BOUNDS
+cudaError_t wide_upload_bounds(const BoundsTable& t, cudaStream_t st) { return upload_bounds_table(t, st); }
+#endif
 
 }  // namespace scal3r
