@@ -34,9 +34,10 @@ TOL = 2e-2
 def _bounds_lib():
     from paper_2604_08542_gb300 import build as b
     try:
-        return b.build(variant="bounds")
+        b._nvcc()
     except RuntimeError as e:   # no nvcc on this machine
         pytest.skip(str(e))
+    return b.build(variant="bounds")   # a compile error fails the test
 
 
 def _declared():
