@@ -1076,11 +1076,11 @@ int64_t wide_ckpt_slot(const Plan& p, int s, int j, int n) {
 namespace {
 
 // K ranges of a float32-output GEMM whose output tiles do not fill the SMs:
-// as many ranges as fit the SMs in one round (tiles x s <= SMs), each at
-// least 4 K blocks long; 1 = no split.  Ranges beyond one round would trim
-// the last round a little, but each adds a partial plane to the fixed-order
-// sum: at 32 tiles of 128 x 256 and 16,656 tokens of K, 19 ranges (4 rounds)
-// take 16 % less GEMM time than 4 ranges (1 round) and write and re-read
+// as many ranges as fit the SMs in one wave (tiles x s <= SMs), each at
+// least 4 K blocks long; 1 = no split.  Ranges beyond one wave would trim
+// the last wave a little, but each adds a partial plane to the fixed-order
+// sum: at 32 tiles of 128 x 256 and 16,656 tokens of K, 19 ranges (4 waves)
+// take 16 % less GEMM time than 4 ranges (1 wave) and write and re-read
 // 76 MB of planes instead of 16 MB, which costs more than it saves.  The
 // count never falls as K grows, so a workspace sized for the longest K holds
 // the planes of any shorter one.
