@@ -120,3 +120,42 @@ def test_fp32_gradients_match_finite_differences():
         fd = (objective(plus) - objective(minus)) / (2 * eps)
         an = float(np.sum(gnp[n] * u))
         assert abs(an - fd) <= 1e-4 * max(1.0, abs(fd)), (n, an, fd)
+
+
+@pytest.mark.parametrize("dtype_name,D,F,tol", [("fp32", 16, 32, TOL), ("bf16", 64, 128, 2e-2)])
+def test_clamped_rows_match_oracle(dtype_name, D, F, tol):
+    """The clamp branch of the row rescale (reading A8: max(||row||, eps)) on
+    the GPU.  Every other row of w0 is scaled down, so the rows' norms fall in
+    two groups with a wide gap, and eps lies in the gap: the small rows are
+    rescaled by rho / eps (and stay below eps), the others by rho / ||row||.
+    Forward and backward against the oracle run with the same eps."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    dtype = torch.float32 if dtype_name == "fp32" else torch.bfloat16
+    lay = syn.layout_from_lengths([[300, 129], [257]])
+    H, T = 2, lay.num_tokens
+    x = syn.make_inputs(T, H, D, F, seed=41, dtype=dtype_name, with_grad_out=True, lr_max=0.3)
+    # rows of W1 and W3 hold D values, rows of W2 F values (packed W1, W3, W2)
+    rows = np.concatenate([np.repeat(np.arange(2 * F), D), 2 * F + np.repeat(np.arange(D), F)])
+    x["w0"] = (x["w0"] * np.where(rows % 2 == 0, 0.3, 1.0)[None, :]).astype(np.float32)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    n = np.sort(ref["wnorm"].reshape(-1))
+    gap = int(np.argmax(n[1:] / n[:-1]))                 # the widest gap between consecutive norms
+    eps = float(np.sqrt(n[gap] * n[gap + 1]))
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=eps)
+    n = ref["wnorm"].reshape(-1)
+    assert np.any(n < eps) and np.any(n > eps) and np.min(np.abs(n - eps)) > 0.1 * eps
+    g = upload(x, dtype)
+    layer = ttt.TTT(H, D, F, dtype=dtype, norm_eps=eps)
+    o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                                  want_final=True)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    rb = oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, x["d_o"], D, F, eps=eps)
+    out = {"o": (to_np(o), ref["o"]), "w_ckpt": (to_np(ck), ref["w_ckpt"]), "wnorm": (to_np(wn), ref["wnorm"]),
+           "w_final": (to_np(wf), ref["w_final"])}
+    for nme, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
+        out[nme] = (to_np(t), rb[nme])
+    _assert_all(out, tol)

@@ -212,6 +212,99 @@ def test_backward_matches_finite_differences(loss, norm, model, lr_max):
 
 
 # ---------------------------------------------------------------------------
+# P5b: the clamp branch of the row rescale (reading A8: max(||row||, eps))
+# ---------------------------------------------------------------------------
+
+def clamp_eps(inp, lay, loss, norm, margin=1e-3):
+    """An eps that some pre-rescale row norms of the run fall below and others
+    above, every norm at least `margin` (relative) away from it.  The run is
+    redone with each candidate, since clamping changes the later chunks."""
+    base = oracle.forward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, D, F, loss=loss, norm=norm)
+    qs = np.quantile(base["wnorm"], np.linspace(0.2, 0.8, 25))
+    for eps in qs * (1.0 + margin * 3):
+        out = oracle.forward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, D, F, loss=loss,
+                             norm=norm, eps=eps)
+        n = out["wnorm"].reshape(-1)
+        if np.any(n < eps) and np.any(n > eps) and np.min(np.abs(n - eps)) > margin * eps:
+            return float(eps)
+    raise AssertionError("no eps with a margin")
+
+
+def _fd_check(inp, lay, d_o, loss, norm, eps, h=1e-6, tol=2e-7, kink=()):
+    """The oracle's backward against central differences of <dO, o> for all
+    five inputs.  Entries of w0 listed in `kink` sit at a zero row, where
+    the target norm is |h| on either side: there the difference has an O(h)
+    term, so those entries are checked to converge to the backward's value
+    linearly in h instead."""
+    g = oracle.backward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, d_o, D, F,
+                        loss=loss, norm=norm, eps=eps)
+
+    def obj():
+        out = oracle.forward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, D, F, loss=loss,
+                             norm=norm, eps=eps)
+        return float(np.sum(out["o"] * d_o))
+
+    def cdiff(flat, i, step):
+        old = flat[i]
+        flat[i] = old + step
+        fp = obj()
+        flat[i] = old - step
+        fm = obj()
+        flat[i] = old
+        return (fp - fm) / (2 * step)
+    names = {"q": "dq", "k": "dk", "v": "dv", "lr": "dlr", "w0": "dw0"}
+    for n, gn in names.items():
+        flat = inp[n].reshape(-1)
+        ref = g[gn].reshape(-1)
+        skip = set(kink) if n == "w0" else set()
+        fd = np.array([cdiff(flat, i, h) if i not in skip else ref[i] for i in range(flat.size)])
+        scale = max(1.0, np.max(np.abs(fd)))
+        err = np.max(np.abs(ref - fd)) / scale
+        assert err < tol, (n, err)
+        for i in sorted(skip):
+            e7, e8 = abs(cdiff(flat, i, 1e-7) - ref[i]), abs(cdiff(flat, i, 1e-8) - ref[i])
+            assert e8 < 2e-6 * scale and e8 < 0.3 * e7 + 1e-7 * scale, (i, e7, e8)
+
+
+@pytest.mark.parametrize("loss,norm", [("dot", "row_w0"), ("mse", "row_w0"), ("dot", "unit")])
+def test_backward_with_clamped_rows_matches_finite_differences(loss, norm):
+    """Rows whose norm after the gradient step is below eps are rescaled by
+    rho / eps (R = (rho / eps) lambda, drho = w~ . lambda / eps); rows above it
+    by rho / ||row||.  A run with both kinds of rows, every norm away from
+    eps, against central differences of <dO, o> for all five inputs."""
+    lay = _layout_2seq()
+    x = _tiny(21, T=lay.num_tokens, H=1, lr_max=0.3)
+    inp = {n: x[n].astype(np.float64) for n in ("q", "k", "v", "lr", "w0")}
+    eps = clamp_eps(inp, lay, loss, norm)
+    out = oracle.forward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, D, F, loss=loss, norm=norm,
+                         eps=eps)
+    # the clamped rows' norm is rho * ||w~|| / eps, not rho
+    n = out["wnorm"][0, 0]
+    W = oracle.unpack(out["w_ckpt"][0, 0], D, F)
+    rows = np.concatenate([np.sqrt(np.sum(m * m, axis=1)) for m in W])
+    rho = (np.concatenate([np.sqrt(np.sum(m * m, axis=1)) for m in oracle.unpack(inp["w0"][0], D, F)])
+           if norm == "row_w0" else np.ones_like(n))
+    np.testing.assert_allclose(rows, rho * np.minimum(n / eps, 1.0), rtol=1e-12)
+    _fd_check(inp, lay, x["d_o"].astype(np.float64), loss, norm, eps)
+
+
+def test_backward_with_a_zero_initial_row_matches_finite_differences():
+    """A row of W0 that is zero has target 0: the row stays zero, and its
+    target contributes nothing to dW0 (the central difference of |h| is 0)."""
+    lay = _layout_2seq()
+    x = _tiny(23, T=lay.num_tokens, H=1, lr_max=0.3)
+    inp = {n: x[n].astype(np.float64) for n in ("q", "k", "v", "lr", "w0")}
+    inp["w0"][0, 3 * D:4 * D] = 0.0          # row 3 of W1
+    inp["w0"][0, 2 * F * D + F:2 * F * D + 2 * F] = 0.0           # row 1 of W2
+    out = oracle.forward(inp["q"], inp["k"], inp["v"], inp["lr"], inp["w0"], lay, D, F)
+    for c in range(lay.num_chunks):
+        W = oracle.unpack(out["w_ckpt"][c, 0], D, F)
+        assert np.all(W[0][3] == 0.0) and np.all(W[2][1] == 0.0)
+    kink = list(range(3 * D, 4 * D)) + list(range(2 * F * D + F, 2 * F * D + 2 * F))
+    _fd_check(inp, lay, x["d_o"].astype(np.float64), "dot", "row_w0", 1e-12, kink=kink)
+
+
+# ---------------------------------------------------------------------------
 # per-matrix learning rates: G_j = d/dW_j sum_i eta_{j,i} L_i
 # ---------------------------------------------------------------------------
 
@@ -360,6 +453,35 @@ def test_streaming_resume_equals_one_pass():
                        w_init=a["w_final"])
     np.testing.assert_array_equal(np.concatenate([a["o"], b["o"]]), out["o"])
     np.testing.assert_array_equal(b["w_final"], out["w_final"])
+
+
+@pytest.mark.parametrize("norm", ["row_w0", "unit"])
+def test_streaming_resume_with_row_rescale_equals_one_pass(norm):
+    # With the row rescale the resumed run takes its targets from the rows of
+    # w_init: every row of w_final already has its target norm (rho for
+    # row_w0, 1 for unit), so the resumed targets are the original ones up to
+    # rounding and the two runs agree to rounding.
+    lay = syn.layout_from_lengths([[5, 4, 6, 3]])
+    x = _tiny(19, T=18, H=2)
+    out = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, norm=norm)
+    la = syn.layout_from_lengths([[5, 4]])
+    lb = syn.layout_from_lengths([[6, 3]])
+    a = oracle.forward(*(x[n][:9] for n in ("q", "k", "v", "lr")), x["w0"], la, D, F, norm=norm)
+    if norm == "unit":
+        w_init = a["w_final"]
+    else:
+        # resuming under row_w0 with the original rows' norms: w_final rows
+        # have exactly those norms
+        w_init = a["w_final"]
+        rho = [np.sqrt(np.sum(m * m, axis=1)) for m in oracle.unpack(x["w0"][0].astype(np.float64), D, F)]
+        got = [np.sqrt(np.sum(m * m, axis=1)) for m in oracle.unpack(w_init[0, 0], D, F)]
+        for r, g in zip(rho, got):
+            np.testing.assert_allclose(g, r, rtol=1e-13)
+    b = oracle.forward(*(x[n][9:] for n in ("q", "k", "v", "lr")), x["w0"], lb, D, F, norm=norm,
+                       w_init=w_init)
+    np.testing.assert_allclose(np.concatenate([a["o"], b["o"]]), out["o"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b["w_final"], out["w_final"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b["wnorm"], out["wnorm"][2:], rtol=1e-12)
 
 
 def test_zero_lr_chunk_keeps_weights():
