@@ -173,17 +173,25 @@ int scal3r_ttt_forward(scal3r_ttt_handle* handle,
  * are those of scal3r_ttt_forward.  Its scratch (schedule, master weights,
  * partial sums, status word) is one fixed 32 MiB device array inside the
  * library, held by every GPU that loads the library until the process exits.
+ *  - Configurations: the float32 path at any shape it takes, either loss;
+ *    the bfloat16 path at head_dim 64, hidden 128 with the dot loss.  Every
+ *    normalisation, a shared or per-sequence w0.  Not: the wide-weight
+ *    bfloat16 shapes, the squared-error loss in bfloat16, per-matrix rates,
+ *    ckpt_every > 1 (each returns SCAL3R_ERR_UNSUPPORTED or, for a
+ *    ckpt_every below 0 or above 1, SCAL3R_ERR_INVALID_ARG).
  *  - The scratch needs 2 x 4P bytes of master weights per chain (sequence x
  *    head; P = 3*F*D) plus 4P bytes per piece of the busiest chunk step (the
  *    schedule cuts a step into about one piece per SM): at D=64, F=128 about
  *    90 chains fit.  A layout whose scratch does not fit returns
  *    SCAL3R_ERR_WORKSPACE before any work is enqueued.
- *  - The first call on a device sets up the array's device address; make it
- *    before any stream capture.
+ *  - The first call in a CUDA context sets up the array's device address;
+ *    make it before any stream capture.  The schedule reaches the array
+ *    through the parameters of copy kernels on `stream`: nothing is read
+ *    from host memory after the call returns, and no memory copy is issued.
  *  - All calls on a device share the array and it keeps the last call's
  *    contents: calls whose GPU work overlaps race.  Order them on one stream.
- *  - A device-side wait that times out leaves the outputs undefined; this
- *    entry point does not report it. */
+ *  - A device-side wait that gives up sets the array's status word, which
+ *    each call clears when it starts; scal3r_ttt_noalloc_status reads it. */
 int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg,
                                const void* q, const void* k, const void* v,
                                const float* lr, const float* w0, int64_t w0_seq_stride,
@@ -191,6 +199,15 @@ int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg,
                                const int32_t* seq_chunk_ptr, int32_t num_seqs,
                                void* o, float* w_ckpt, float* wnorm, float* w_final,
                                void* stream);
+
+/* The status word of scal3r_ttt_forward_noalloc's array (the paper has no
+ * counterpart): waits for the work on `stream` to finish, returns
+ * SCAL3R_OK, or SCAL3R_ERR_TIMEOUT if a kernel of an earlier call on the
+ * device gave up a wait (its outputs are then undefined), and clears the
+ * word.  It copies four bytes to host memory and synchronises the stream, so
+ * call it outside any stream capture.  Returns SCAL3R_ERR_CUDA or
+ * SCAL3R_ERR_NO_DEVICE if the runtime fails. */
+int scal3r_ttt_noalloc_status(void* stream);
 
 /* ---- Global Context Synchronisation (Sec. 4.2, Eq. 10) -------------------
  * When one chunk's tokens are spread over several processes (GPUs), the

@@ -52,7 +52,7 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_workspace_size", "scal3r_ttt_forward", "scal3r_ttt_backward",
             "scal3r_ttt_set_schedule", "scal3r_ttt_get_schedule", "scal3r_ttt_set_graph_mode",
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
-            "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_partial_grad",
+            "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_noalloc_status", "scal3r_ttt_partial_grad",
             "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_ttt_set_finite_check", "scal3r_ttt_debug_bounds", "scal3r_gcm_workspace_size",
             "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
 
@@ -121,6 +121,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_forward_noalloc.argtypes = [ctypes.POINTER(scal3r_ttt_config), vp, vp, vp, vp, vp, i64, vp,
                                                i32, vp, i32, vp, vp, vp, vp, vp]
     lib.scal3r_ttt_forward_noalloc.restype = ctypes.c_int
+    lib.scal3r_ttt_noalloc_status.argtypes = [vp]
+    lib.scal3r_ttt_noalloc_status.restype = ctypes.c_int
     lib.scal3r_ttt_profile_enable.argtypes = [vp, i32]
     lib.scal3r_ttt_profile_enable.restype = ctypes.c_int
     lib.scal3r_ttt_profile_read.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
@@ -288,6 +290,12 @@ def scal3r_ttt_forward_noalloc(cfg: scal3r_ttt_config, q, k, v, lr, w0, w0_seq_s
     return load_library().scal3r_ttt_forward_noalloc(ctypes.byref(cfg), q, k, v, lr, w0, w0_seq_stride,
                                                      off.ctypes.data, len(off) - 1, ptr.ctypes.data, len(ptr) - 1,
                                                      o, w_ckpt, wnorm, w_final, stream)
+
+
+def scal3r_ttt_noalloc_status(stream) -> int:
+    """The status word of the allocation-free forward's array (synchronises
+    `stream`; SCAL3R_OK or SCAL3R_ERR_TIMEOUT), cleared after the read."""
+    return load_library().scal3r_ttt_noalloc_status(stream)
 
 
 def scal3r_ttt_profile_enable(handle: int, enable: bool) -> None:

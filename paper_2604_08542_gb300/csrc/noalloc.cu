@@ -11,15 +11,27 @@
 // loads the library holds until the process exits.
 //
 // Rules of use:
-//  - The first call on a device looks up the array's device address
+//  - The first call in a CUDA context looks up the array's device address
 //    (cudaGetSymbolAddress, which may load the module) and sets the kernels'
-//    shared-memory attributes; make that first call before any stream capture.
+//    shared-memory attributes; make that first call before any stream
+//    capture.  The address is cached per context, so a call after a device
+//    reset looks it up again.
+//  - The schedule tables go to the array through the parameters of small
+//    copy kernels (launched on the caller's stream), not through memory
+//    copies: the call reads no host memory after it returns and issues no
+//    pageable copy.
 //  - Every call on a device shares the one array and leaves its contents
 //    behind; calls whose GPU work overlaps (different streams, or threads
 //    without ordering) race on it.  Order them on one stream.
 //  - A problem whose scratch does not fit returns SCAL3R_ERR_WORKSPACE
 //    before any work is enqueued.
+//  - scal3r_ttt_noalloc_status reads and clears the status word that the
+//    kernels' bounded waits set on a timeout.
+#include <algorithm>
+#include <cstring>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "ttt_internal.h"
 
@@ -38,21 +50,82 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+struct Cached {
+  CUcontext ctx;
+  void* addr;
+};
+Cached g_addr[kMaxDevices] = {};
 
-// Device address of the array on the current device (set up once per device).
+// The current context (the runtime's primary context of the device once the
+// runtime has set it up).
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext*);
+  static Fn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Fn>(f);
+  }
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of the array in the current context (looked up once per
+// context: a device reset makes a new context and a new lookup).
 int scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return SCAL3R_ERR_NO_DEVICE;
+  const CUcontext ctx = current_context();
+  if (!ctx) return SCAL3R_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev].addr || g_addr[dev].ctx != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCAL3R_ERR_CUDA;
-    if (prepare_kernels() != cudaSuccess) return SCAL3R_ERR_CUDA;   // kernel attributes, once per device
-    g_addr[dev] = p;
+    if (prepare_kernels() != cudaSuccess) return SCAL3R_ERR_CUDA;   // kernel attributes, once per context
+    g_addr[dev] = Cached{ctx, p};
   }
-  *out = g_addr[dev];
+  *out = g_addr[dev].addr;
   return SCAL3R_OK;
 }
+
+// A block of bytes for the array, carried in the kernel's parameters (the
+// launch copies them when it is enqueued).
+constexpr int kUploadBytes = 24 * 1024;
+struct UploadBlock {
+  unsigned long long* dst;   // 8-byte aligned
+  int* status;               // zeroed when not null
+  int words;                 // 8-byte words to copy
+  unsigned long long data[kUploadBytes / 8];
+};
+
+__global__ void noalloc_upload_kernel(const __grid_constant__ UploadBlock b) {
+  for (int i = threadIdx.x; i < b.words; i += blockDim.x) b.dst[i] = b.data[i];
+  if (b.status && threadIdx.x == 0) *b.status = 0;
+}
+
+// Copies `bytes` (a multiple of 8) from host memory to dst, in blocks of
+// kUploadBytes, on stream st.
+int upload(void* dst, const void* src, size_t bytes, int* status, cudaStream_t st) {
+  const unsigned char* s = static_cast<const unsigned char*>(src);
+  unsigned char* d = static_cast<unsigned char*>(dst);
+  static thread_local UploadBlock blk;
+  size_t off = 0;
+  do {
+    const size_t n = std::min<size_t>(kUploadBytes, bytes - off);
+    blk.dst = reinterpret_cast<unsigned long long*>(d + off);
+    blk.status = off == 0 ? status : nullptr;
+    blk.words = (int)(n / 8);
+    if (n) std::memcpy(blk.data, s + off, n);
+    noalloc_upload_kernel<<<1, 256, 0, st>>>(blk);
+    if (cudaGetLastError() != cudaSuccess) return SCAL3R_ERR_CUDA;
+    off += n;
+  } while (off < bytes);
+  return SCAL3R_OK;
+}
+
+__global__ void noalloc_clear_kernel(int* status) { *status = 0; }
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -118,16 +191,12 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   char* regions = c + b_status + b_items + b_upd;
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the status word must start at zero; every other region is written before it is read
-  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SCAL3R_ERR_CUDA;
-  if (!pl.items.empty() &&
-      cudaMemcpyAsync(d_items, pl.items.data(), pl.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess)
-    return SCAL3R_ERR_CUDA;
-  if (!pl.updates.empty() &&
-      cudaMemcpyAsync(d_upd, pl.updates.data(), pl.updates.size() * sizeof(UpdateItem), cudaMemcpyHostToDevice,
-                      st) != cudaSuccess)
-    return SCAL3R_ERR_CUDA;
+  // the schedule tables, and the status word set to zero with the first
+  // block; every other region is written before it is read
+  static_assert(sizeof(WorkItem) % 8 == 0 && sizeof(UpdateItem) % 8 == 0, "8-byte words");
+  rc = upload(d_items, pl.items.data(), pl.items.size() * sizeof(WorkItem), status, st);
+  if (rc == SCAL3R_OK) rc = upload(d_upd, pl.updates.data(), pl.updates.size() * sizeof(UpdateItem), nullptr, st);
+  if (rc != SCAL3R_OK) return rc;
 
   Params prm{};
   prm.H = sh.H;
@@ -165,4 +234,21 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
     if (s.nupd > 0 && launch_update(prm, d_upd + s.upd0, s.nupd, (int)j, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
   }
   return SCAL3R_OK;
+}
+
+extern "C" int scal3r_ttt_noalloc_status(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
+  void* base = nullptr;
+  const int rc = scratch_address(dev, &base);
+  if (rc != SCAL3R_OK) return rc;
+  int* status = static_cast<int*>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
+  noalloc_clear_kernel<<<1, 1, 0, st>>>(status);
+  if (cudaGetLastError() != cudaSuccess) return SCAL3R_ERR_CUDA;
+  return h;
 }

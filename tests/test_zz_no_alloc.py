@@ -5,10 +5,13 @@ running while a stream is in global-mode graph capture, plugins whose host
 framework owns all device memory, latency-critical paths that must not enter
 the driver's allocator); its scratch is a fixed device array inside the
 library.  Two calls in a row through the C ABI must both reproduce
-scal3r_ttt_forward within the tolerance of the parity tests.  This file is
-collected last so that a run stopping at the first failure has run every
-other test already; it also passes alone in a fresh process.
+scal3r_ttt_forward within the tolerance of the parity tests, and the array's
+status word, read after each call, must be clean.  This file is collected
+last so that a run stopping at the first failure has run every other test
+already; it also passes alone in a fresh process.
 """
+import threading
+
 import numpy as np
 import pytest
 
@@ -17,39 +20,117 @@ from _util import rel_inf, to_np, upload
 
 pytestmark = pytest.mark.gpu
 
+CASES = [("bf16", "dot", False, 2e-2), ("fp32", "dot", False, 1e-5), ("fp32", "mse", False, 1e-5),
+         ("fp32", "dot", True, 1e-5)]
 
-@pytest.mark.parametrize("dtype_name,tol", [("bf16", 2e-2), ("fp32", 1e-5)])
-def test_noalloc_forward_matches_forward_twice(dtype_name, tol):
+
+def _setup(dtype_name, loss, per_seq_w0, seed=31):
     import torch
     import paper_2604_08542_gb300 as ttt
     dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
     lay = syn.layout_from_lengths([[3000, 1500, 77], [1041], [2, 640]])
     H, D, F = 4, 64, 128
-    T, C, S = lay.num_tokens, lay.num_chunks, lay.num_seqs
-    x = syn.make_inputs(T, H, D, F, seed=31, dtype=dtype_name)
+    T, S = lay.num_tokens, lay.num_seqs
+    x = syn.make_inputs(T, H, D, F, seed=seed, dtype=dtype_name)
+    if loss == "mse":
+        x["lr"] = x["lr"] * 0.3   # keeps the squared-error recurrence in range
     g = upload(x, dtype)
-    layer = ttt.TTT(H, D, F, dtype=dtype)
+    if per_seq_w0:
+        w = syn.make_inputs(1, S * H, D, F, seed=seed + 1)["w0"].reshape(S, H, 3 * F * D)
+        g["w0"] = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    layer = ttt.TTT(H, D, F, dtype=dtype, loss=loss)
     ref = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
                         want_final=True)
     torch.cuda.synchronize()
     cfg = ttt.scal3r_ttt_config(H, D, F, ttt.SCAL3R_BF16 if dtype_name == "bf16" else ttt.SCAL3R_FP32,
-                                ttt.SCAL3R_LOSS_DOT, ttt.SCAL3R_NORM_ROW_W0, 1e-6, 0)
+                                ttt.SCAL3R_LOSS_MSE if loss == "mse" else ttt.SCAL3R_LOSS_DOT,
+                                ttt.SCAL3R_NORM_ROW_W0, 1e-6, 0)
+    stride = H * 3 * F * D if per_seq_w0 else 0
+    return lay, g, ref, cfg, stride, (H, D, F)
+
+
+def _outputs(lay, shape, like):
+    import torch
+    H, D, F = shape
+    C, S = lay.num_chunks, lay.num_seqs
+    return (torch.full_like(like, float("nan")),
+            torch.full((C, H, 3 * F * D), float("nan"), device="cuda"),
+            torch.full((C, H, 2 * F + D), float("nan"), device="cuda"),
+            torch.full((S, H, 3 * F * D), float("nan"), device="cuda"))
+
+
+def _call(ttt, cfg, g, stride, lay, outs, stream):
+    o, ck, wn, wf = outs
+    return ttt.scal3r_ttt_forward_noalloc(cfg, g["q"].data_ptr(), g["k"].data_ptr(), g["v"].data_ptr(),
+                                          g["lr"].data_ptr(), g["w0"].data_ptr(), stride, lay.chunk_offsets,
+                                          lay.seq_chunk_ptr, o.data_ptr(), ck.data_ptr(), wn.data_ptr(),
+                                          wf.data_ptr(), stream)
+
+
+def _check(outs, ref, tol, tag):
+    for name, a, b in zip(("o", "w_ckpt", "wnorm", "w_final"), outs, ref):
+        err = rel_inf(to_np(a), to_np(b))
+        assert np.isfinite(err) and err <= tol, (tag, name, err)
+
+
+@pytest.mark.parametrize("dtype_name,loss,per_seq_w0,tol", CASES)
+def test_noalloc_forward_matches_forward_twice(dtype_name, loss, per_seq_w0, tol):
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    lay, g, ref, cfg, stride, shape = _setup(dtype_name, loss, per_seq_w0)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
-        o = torch.full_like(g["q"], float("nan"))
-        ck = torch.full((C, H, 3 * F * D), float("nan"), device="cuda")
-        wn = torch.full((C, H, 2 * F + D), float("nan"), device="cuda")
-        wf = torch.full((S, H, 3 * F * D), float("nan"), device="cuda")
-        rc = ttt.scal3r_ttt_forward_noalloc(cfg, g["q"].data_ptr(), g["k"].data_ptr(), g["v"].data_ptr(),
-                                            g["lr"].data_ptr(), g["w0"].data_ptr(), 0, lay.chunk_offsets,
-                                            lay.seq_chunk_ptr, o.data_ptr(), ck.data_ptr(), wn.data_ptr(),
-                                            wf.data_ptr(), stream)
+        outs = _outputs(lay, shape, g["q"])
+        rc = _call(ttt, cfg, g, stride, lay, outs, stream)
         assert rc == ttt.SCAL3R_OK, ttt.error_string(rc)
-        torch.cuda.synchronize()
-        for name, a, b in (("o", o, ref[0]), ("w_ckpt", ck, ref[1]), ("wnorm", wn, ref[2]),
-                           ("w_final", wf, ref[3])):
-            err = rel_inf(to_np(a), to_np(b))
-            assert np.isfinite(err) and err <= tol, (call, name, err)
+        assert ttt.scal3r_ttt_noalloc_status(stream) == ttt.SCAL3R_OK
+        _check(outs, ref, tol, call)
+
+
+def test_noalloc_forward_while_another_thread_captures_in_global_mode():
+    # The first use named for this entry point: another thread holds a stream
+    # in global-mode capture (where cudaMalloc would be refused) while the
+    # forward runs on a stream of its own.  Neither the call nor the capture
+    # may fail, and the outputs are the ordinary forward's.
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    lay, g, ref, cfg, stride, shape = _setup("bf16", "dot", False, seed=5)
+    side, cap = torch.cuda.Stream(), torch.cuda.Stream()
+    warm = _outputs(lay, shape, g["q"])
+    assert _call(ttt, cfg, g, stride, lay, warm, side.cuda_stream) == ttt.SCAL3R_OK   # set-up outside capture
+    assert ttt.scal3r_ttt_noalloc_status(side.cuda_stream) == ttt.SCAL3R_OK
+    outs = _outputs(lay, shape, g["q"])
+    x = torch.zeros(4096, device="cuda")
+    torch.cuda.synchronize()
+    started, release, errors = threading.Event(), threading.Event(), []
+
+    def capture():
+        graph = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(graph, stream=cap, capture_error_mode="global"):
+                x.mul_(2.0)
+                started.set()
+                release.wait(60)
+                x.add_(1.0)
+            graph.replay()
+            torch.cuda.synchronize()
+        except Exception as e:   # reported below
+            errors.append(e)
+            started.set()
+
+    t = threading.Thread(target=capture)
+    t.start()
+    try:
+        assert started.wait(60)
+        rc = _call(ttt, cfg, g, stride, lay, outs, side.cuda_stream)
+    finally:
+        release.set()
+        t.join(120)
+    assert not errors, errors
+    assert rc == ttt.SCAL3R_OK, ttt.error_string(rc)
+    assert ttt.scal3r_ttt_noalloc_status(side.cuda_stream) == ttt.SCAL3R_OK
+    _check(outs, ref, 2e-2, "during capture")
+    assert torch.all(x == 1.0)   # the captured graph ran once: 0 * 2 + 1
 
 
 def test_noalloc_rejects_layouts_beyond_its_scratch():
