@@ -47,6 +47,8 @@ NUM_SMS_GB300 = 152
 NCU_TRAFFIC = {
     "bf16_vggt64": {"bwd_sweep": 197_449_472 + 220_089_856, "fwd_sweep": 105_362_944 + 13_213_952},
 }
+NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of each sweep, captured on "
+                      "the sweep kernels of commit 8b5f4ba (profiles/bf16_bsweep_kernel_vggt64.md)")
 
 
 def parse():
@@ -60,6 +62,9 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=3)
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations of the suite (FP32 small, 2 x 32 frames, ragged 24 "
+                         "sequences, 2,000 frames, the 256-frame window)")
     ap.add_argument("--fwd-only", action="store_true", help="a step is the forward pass alone")
     ap.add_argument("--no-amu", action="store_true", help="skip the paper-shape (hd 1024) forward line")
     ap.add_argument("--no-variants", action="store_true",
@@ -183,9 +188,11 @@ def run_reference(args, rank: int):
     ts = [time_oracle_step(w, lay, x) for _ in range(args.steps)]
     sec = statistics.mean(ts)
     value = lay.num_tokens * frac / sec
-    sample = f"1 of {w.heads} heads of {w.name} (all {lay.num_tokens} tokens), forward+backward per step"
+    sample = (f"1 of {w.heads} heads of {w.name} (all {lay.num_tokens} tokens), forward+backward per step; "
+              f"a step of the sample takes ms_per_step, the whole workload {w.heads} times that")
     return {"metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sec * 1e3 / frac, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "ms_per_step_all_heads_extrapolated": sec * 1e3 / frac, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": w.name, "description": w.description, "step": "forward+backward"},
             "cpu_baseline": {"value": value, "unit": "tokens/s", "cores": cpu_threads(), "kind": "oracle",
@@ -426,6 +433,142 @@ def amu_variants(args, dev, peak_tflops):
             o[a:b] = layer.apply(q[a:b], wcur, lo.chunk_offsets, lo.seq_chunk_ptr, workspace=wsg)
     out["gcs_split_fwd"] = timed(gcs_fwd, layer)
     layer.close()
+    return out
+
+
+# per (token, head) algorithmic FLOPs at D, F (dot loss): forward 18 D F;
+# backward 36 D F as the kernels count it (every product the reverse pass
+# forms, recompute excluded) and 38 D F as the hot-path table estimates it
+FWD_DF, BWD_DF, BWD_DF_TABLE = 18.0, 36.0, 38.0
+
+
+def config_legs(args, dev, pk, peak_tflops):
+    """Every configuration of the benchmark suite besides the headline: the
+    plain FP32 one (1,024 tokens), forward+backward on 2 x 32 frames, the
+    ragged 24-sequence forward (autotuned schedule, CUDA-graph replay), the
+    2,000-frame forward and the 256-frame window forward+backward.  Each:
+    tokens/s over graph-replayed steps with L2 flushed between them, the
+    sweeps' algorithmic rates from a direct-launch loop with per-kernel
+    events, the kernels' shares of that loop, and the FP64 oracle timed on a
+    stated part of the same workload (scaled to the whole, and labelled so)."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    import oracle
+    out = {}
+    flush = torch.empty(256 * 2**20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    legs = [("fp32_small", "forward", None), ("bf16_fwdbwd_2x32", "forward+backward", None),
+            ("bf16_ragged24", "forward", None), ("bf16_long2000", "forward", None),
+            ("bf16_window256", "forward+backward", None)]
+    for name, kind, _ in legs:
+        w = syn.workload(name, seed=args.seed)
+        lay = w.layout()
+        T, H, D, F = lay.num_tokens, w.heads, w.head_dim, w.hidden
+        off, ptr = lay.chunk_offsets, lay.seq_chunk_ptr
+        dtype = torch.bfloat16 if w.dtype == "bf16" else torch.float32
+        bwd = kind != "forward"
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(args.seed + 500)
+
+        def unit_rows():
+            x = torch.randn((T, H, D), generator=gen, device=dev)
+            return (x / x.norm(dim=-1, keepdim=True)).to(dtype)
+
+        q, k, v = unit_rows(), unit_rows(), unit_rows()
+        lr = torch.rand((T, H), generator=gen, device=dev) * 0.1
+        w0 = torch.randn((H, 3 * F * D), generator=gen, device=dev) * 0.125
+        d_o = torch.randn((T, H, D), generator=gen, device=dev).to(dtype) if bwd else None
+        layer = ttt.TTT(H, D, F, dtype=dtype)
+        tuned = None
+        if name == "bf16_ragged24":
+            tuned = layer.autotune(q, k, v, lr, w0, off, ptr)
+        ws = torch.empty(ttt.scal3r_ttt_workspace_size(layer.handle, off, ptr, bwd), dtype=torch.uint8, device=dev)
+        o = torch.empty_like(q)
+
+        def step():
+            if bwd:
+                _, ck, wn, _ = layer.forward(q, k, v, lr, w0, off, ptr, workspace=ws, o=o)
+                layer.backward(q, k, v, lr, w0, off, ptr, d_o, ck, wn, workspace=ws)
+            else:
+                layer.forward(q, k, v, lr, w0, off, ptr, save_for_backward=False, workspace=ws, o=o)
+
+        def loop(n, profile=False):
+            if profile:
+                ttt.scal3r_ttt_profile_enable(layer.handle, True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+            torch.cuda.synchronize()
+            for i in range(n):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            prof = None
+            if profile:
+                prof = {ttt.KERNEL_KINDS[kk]: ttt.scal3r_ttt_profile_read(layer.handle, kk) for kk in ttt.KERNEL_KINDS}
+                ttt.scal3r_ttt_profile_enable(layer.handle, False)
+            return statistics.mean(a.elapsed_time(b) for a, b in ev), prof
+
+        nsteps = max(3, args.steps // 2)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        layer.set_graph_mode(True)
+        for _ in range(2):
+            step()
+        ms, _ = loop(nsteps)
+        layer.set_graph_mode(False)
+        _, prof = loop(nsteps, profile=True)
+        assert layer.status() == 0
+        tot = sum(vv["ms"] for vv in prof.values())
+        leg = {"description": w.description, "tokens": T, "step": kind, "tokens_per_s": T / (ms / 1e3),
+               "ms_per_step": ms, "timing": "CUDA-graph replay, 256 MB written between steps",
+               "kernel_shares": {kk: round(vv["ms"] / tot, 4) for kk, vv in prof.items() if vv["launches"]}}
+        if tuned is not None:
+            leg["autotuned_schedule"] = tuned
+        for kk in ("fwd_sweep", "bwd_sweep"):
+            vv = prof[kk]
+            if vv["launches"] and vv["ms"] > 0:
+                tf = vv["flops"] / (vv["ms"] / 1e3) / 1e12
+                if w.dtype == "bf16":
+                    leg[kk] = {"tflops": tf, "frac_of_bf16_peak": tf / peak_tflops, "launches": vv["launches"] // nsteps,
+                               "avg_launch_ms": vv["ms"] / vv["launches"]}
+                else:
+                    fp32_peak = NUM_SMS_GB300 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                    leg[kk] = {"tflops": tf, "frac_of_fp32_fma_peak": tf / fp32_peak, "bound": "alu",
+                               "launches": vv["launches"] // nsteps, "avg_launch_ms": vv["ms"] / vv["launches"]}
+        dfs = FWD_DF + (BWD_DF if bwd else 0.0)
+        leg["step_tflops_algorithmic"] = dfs * T * H * D * F / (ms / 1e3) / 1e12
+        if w.dtype == "bf16":
+            leg["step_frac_of_bf16_peak"] = leg["step_tflops_algorithmic"] / peak_tflops
+        # the oracle on a stated part of the workload: one head, and for the
+        # long layouts the first chunks of the first sequence
+        if not args.no_cpu:
+            head_lay = lay
+            part = f"head 0 of {H}"
+            if name in ("bf16_ragged24", "bf16_long2000", "bf16_window256"):
+                nch = 2
+                c1 = min(nch, int(lay.seq_chunk_ptr[1]))
+                lens = [int(lay.chunk_offsets[c + 1] - lay.chunk_offsets[c]) for c in range(c1)]
+                head_lay = syn.layout_from_lengths([lens])
+                part = f"head 0 of {H}, the first {c1} chunks ({sum(lens)} tokens) of sequence 0"
+            Ts = head_lay.num_tokens
+            x = syn.make_inputs(Ts, H, D, F, seed=args.seed, dtype=w.dtype, heads=[0], with_grad_out=bwd)
+            t0 = time.perf_counter()
+            oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], head_lay, D, F, eps=1e-6)
+            if bwd:
+                oracle.backward(x["q"], x["k"], x["v"], x["lr"], x["w0"], head_lay, x["d_o"], D, F, eps=1e-6)
+            sec = time.perf_counter() - t0
+            tok_s = Ts / H / sec
+            leg["cpu_oracle"] = {"tokens_per_s": tok_s, "seconds": sec, "cores": cpu_threads(), "part": part,
+                                 "scaled": f"{Ts} tokens of one head in {sec:.2f} s = {Ts}/{H} full tokens",
+                                 "extrapolated": Ts != T or H != 1}
+            leg["gpu_vs_oracle"] = leg["tokens_per_s"] / tok_s
+        out[name] = leg
+        layer.close()
+        del q, k, v, lr, w0, d_o, o, ws
+        torch.cuda.empty_cache()
     return out
 
 
@@ -672,7 +815,14 @@ def run_gpu(args, rank: int, world: int):
         peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
         roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic.get(dom), "traffic_unit": "bytes/launch",
-                "peak_source": f"bf16_tflops ({pk_src})"}
+                "traffic_source": NCU_TRAFFIC_SOURCE, "peak_source": f"bf16_tflops ({pk_src})",
+                "flops_per_launch": per_launch_flops, "avg_launch_ms": avg_s * 1e3,
+                "flop_count": "forward 18 D F, backward 36 D F per (token, head): the products the kernels form, "
+                              "recompute excluded"}
+        if dom == "bwd_sweep":
+            a38 = achieved * BWD_DF_TABLE / BWD_DF
+            roof["frac_at_38DF"] = a38 / peak
+            roof["achieved_at_38DF"] = a38
     # forward sweep roofline as well (the tensor-core kernel of the forward)
     fs = fprof["fwd_sweep"]
     fwd_sweep_tflops = fs["flops"] / (fs["ms"] / 1e3) / 1e12 if fs["ms"] > 0 else 0.0
@@ -683,6 +833,10 @@ def run_gpu(args, rank: int, world: int):
         amu = amu_leg(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
         if not args.no_variants:
             amu["variants"] = amu_variants(args, dev, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+
+    configs = None
+    if not args.no_configs and rank == 0 and world == 1 and not args.fwd_only:
+        configs = config_legs(args, dev, pk, pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
 
     cpu = None
     if not args.no_cpu:
@@ -708,6 +862,7 @@ def run_gpu(args, rank: int, world: int):
                 "sweep_ms_per_step": fs["ms"] / args.steps},
         "fp32": fp32,
         "paper_amu": amu,
+        "configs": configs,
         "paper_context": {
             "note": "the paper times only its whole pipeline (VGGT backbone, 4 GCM modules, chunk alignment), "
                     "never the TTT layer alone: context, not a target",

@@ -192,7 +192,8 @@ def workload(name: str, seed: int = 0) -> Workload:
                         "1 seq x 8 frames x 128 tokens, 1 head, D=64, F=128, chunk 128 tokens, FP32")
     if name == "bf16_vggt64":
         return Workload(name, [64], TOKENS_PER_FRAME, 16, 16, 64, 128, "bf16", False,
-                        "1 seq x 64 frames x 1041 tokens, 16 heads x 64, F=128, chunk 16 frames, BF16 forward")
+                        "1 seq x 64 frames x 1041 tokens, 16 heads x 64, F=128, chunk 16 frames, BF16 q/k/v, float32 "
+                        "fast weights")
     if name == "bf16_fwdbwd_2x32":
         return Workload(name, [32, 32], TOKENS_PER_FRAME, 8, 16, 64, 128, "bf16", True,
                         "2 seqs x 32 frames x 1041 tokens, 16 heads x 64, F=128, chunk 8 frames, BF16 fwd+bwd")
