@@ -26,10 +26,11 @@
  * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
  * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
  * step as a large tcgen05 GEMM, forward and backward.  The wide path also
- * takes the squared-error loss, per-matrix learning rates (lr_per_matrix) and
- * sparse checkpoints (ckpt_every > 1); the head_dim-64 path takes the dot loss
- * with one rate per token and a checkpoint per chunk, and the autotuner is for
- * it (SCAL3R_ERR_UNSUPPORTED otherwise).  The float32 path takes either loss.
+ * takes the squared-error loss and sparse checkpoints (ckpt_every > 1); the
+ * head_dim-64 path takes the dot loss and a checkpoint per chunk, and the
+ * autotuner is for it (SCAL3R_ERR_UNSUPPORTED otherwise).  Per-matrix
+ * learning rates (lr_per_matrix) run on every path.  The float32 path takes
+ * either loss.
  *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
@@ -105,9 +106,9 @@ typedef struct scal3r_ttt_config {
                            2n-1, ... of each sequence; the backward recomputes the weights in
                            between with the forward's own gradient steps (bitwise the same) */
   int32_t lr_per_matrix; /* 0: lr [T, H], one rate per token and head for all three matrices.
-                           1 (the wide-weight path only): lr [T, H, 3], the rates of W1, W3, W2
-                           in that order, each matrix's gradient (Eq. 8) weighted by its own
-                           rate; dlr then has the same [T, H, 3] layout */
+                           1 (every path): lr [T, H, 3], the rates of W1, W3, W2 in that
+                           order, each matrix's gradient (Eq. 8) weighted by its own rate;
+                           dlr then has the same [T, H, 3] layout */
 } scal3r_ttt_config;
 
 typedef struct scal3r_ttt_handle scal3r_ttt_handle;
@@ -175,9 +176,9 @@ int scal3r_ttt_forward(scal3r_ttt_handle* handle,
  * library, held by every GPU that loads the library until the process exits.
  *  - Configurations: the float32 path at any shape it takes, either loss;
  *    the bfloat16 path at head_dim 64, hidden 128 with the dot loss.  Every
- *    normalisation, a shared or per-sequence w0.  Not: the wide-weight
- *    bfloat16 shapes, the squared-error loss in bfloat16, per-matrix rates,
- *    ckpt_every > 1 (each returns SCAL3R_ERR_UNSUPPORTED or, for a
+ *    normalisation, a shared or per-sequence w0, one rate or per-matrix
+ *    rates.  Not: the wide-weight bfloat16 shapes, the squared-error loss in
+ *    bfloat16, ckpt_every > 1 (each returns SCAL3R_ERR_UNSUPPORTED or, for a
  *    ckpt_every below 0 or above 1, SCAL3R_ERR_INVALID_ARG).
  *  - The scratch needs 2 x 4P bytes of master weights per chain (sequence x
  *    head; P = 3*F*D) plus 4P bytes per piece of the busiest chunk step (the

@@ -72,6 +72,7 @@ constexpr uint32_t QBYTES = 24 * 1024;       // weights of one quarter: 192 rows
 constexpr uint32_t WQ_OFF = 0;               // 4 quarters, 96 KB
 constexpr uint32_t XY_OFF = 96 * 1024;       // 2 stages x (X 16 KB + Y 16 KB); reused for dk/dv staging
 constexpr uint32_t ST_OFF = 160 * 1024;      // six tiles: dz1 dz3 g1 g3 dpe ue (48 KB)
+constexpr uint32_t ETA_OFF = 208 * 1024;     // half 1's dlr partials [2][3][128] float (one or three rates)
 constexpr int PB_T = 32;                     // pass B tile (tokens)
 constexpr uint32_t PB_STAGE = 32 * 1024;     // A1, A3, A2 (4 quarter blocks x 2 KB each), X 4 KB, Y 4 KB
 constexpr int PB_STAGES = 6;
@@ -81,6 +82,7 @@ constexpr uint32_t WQ_BYTES = 4 * QBYTES;
 constexpr uint32_t TILE_SCRATCH = 3 * 4 * ST_TILE;   // [factor][quarter][128 tok][32 hidden] bf16, 96 KB
 
 constexpr size_t DYN_SMEM = 1024 + tl::SMEM_BYTES;   // the apply VJP's layout is the larger
+static_assert(ETA_OFF + 2 * 3 * BT * 4 <= tl::SMEM_BYTES, "dlr partials inside the dynamic region");
 
 // TMEM columns (BKEY)
 constexpr uint32_t B_L = 0;         // L1 | L3 | L2t, 64 columns each, resident for the whole piece
@@ -102,7 +104,6 @@ struct Bars {   // BKEY
   uint64_t b_full[PB_STAGES], b_empty[PB_STAGES], bdone, wq_full;
   uint32_t tmem_base;
   int abort_flag;
-  float eta_red[2][BT];
 };
 
 // BKEY weights, quarter-major:
@@ -115,8 +116,12 @@ __device__ void load_weights_key(const float* w, const float* r, uint8_t* sm) {
 }
 
 // ---------------------------------------------------------------------------
-// BKEY: the VJP of a chunk update (two passes per sub-piece)
+// BKEY: the VJP of a chunk update (two passes per sub-piece).  PM: one rate
+// per matrix (lr [T, H, 3], dlr the same): every factor carries the rate of
+// the matrix it came from (W1: dg1 and its products, W3: dg3 and g3, W2: the
+// u terms), and dlr has three sums over the hidden units.
 // ---------------------------------------------------------------------------
+template <bool PM>
 __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem& it, uint8_t* sm, Bars& B,
                             uint32_t tb) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -137,9 +142,13 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   const int ew = warp - EPI0, half = ew >> 2;            // epilogue warps only
   const uint32_t row = 32u * (warp & 3) + lane;
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
-  // learning rate of this thread's token, one tile ahead
-  float eta_next = 0.f;
-  if (warp >= EPI0 && warp < EPI0 + 8 && t0 + (int64_t)row < t1) eta_next = p.lr[(size_t)(t0 + row) * H + h];
+  // learning rate(s) of this thread's token, one tile ahead
+  constexpr int NR = PM ? 3 : 1;
+  float eta_next[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+    eta_next[j] = (warp >= EPI0 && warp < EPI0 + 8 && t0 + (int64_t)row < t1)
+                      ? p.lr[((size_t)(t0 + row) * H + h) * NR + j] : 0.f;
 
   // pass B stage use counts (parity per stage), kept alike by the producer
   // and the MMA thread
@@ -248,16 +257,21 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       // epilogue: thread = token row of the tile; half selects hidden units
       // [16*half, 16*half + 16) of every quarter.
       uint8_t* stg = sm + ST_OFF;
-      float eta = 0.f, deta = 0.f;
+      float eta[NR], deta[NR];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) eta[j] = deta[j] = 0.f;
       for (int n = ta * NQ; n < te * NQ; ++n) {
         const int i = n / NQ, q = n % NQ;
         const int64_t tok = t0 + (int64_t)i * BT + row;
         const bool valid = tok < t1;
         if (q == 0) {
-          eta = eta_next;
-          deta = 0.f;
           const int64_t tn = tok + BT;
-          eta_next = (i + 1 < ntiles && tn < t1) ? p.lr[(size_t)tn * H + h] : 0.f;
+#pragma unroll
+          for (int j = 0; j < NR; ++j) {
+            eta[j] = eta_next[j];
+            deta[j] = 0.f;
+            eta_next[j] = (i + 1 < ntiles && tn < t1) ? p.lr[((size_t)tn * H + h) * NR + j] : 0.f;
+          }
         }
         if (!mbar_wait_spin(&B.g_full, n & 1, abort)) break;
         tc_fence_after();
@@ -275,8 +289,10 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (lane == 0) mbar_arrive(&B.g_free);
         {
           // the chain rule on pairs of hidden units (packed float32 lanes)
-          const f32x2 neta = x2(-eta), one = x2(1.f), two = x2(2.f), mtwo = x2(-2.f);
-          f32x2 dsum = x2(0.f);
+          // rates of W1, W3, W2 (all the token's one rate without PM)
+          const f32x2 neta = x2(-eta[0]), neta3 = x2(-eta[PM ? 1 : 0]), neta2 = x2(-eta[PM ? 2 : 0]);
+          const f32x2 one = x2(1.f), two = x2(2.f), mtwo = x2(-2.f);
+          f32x2 dsum = x2(0.f), dsum3 = x2(0.f), dsum2 = x2(0.f);
 #pragma unroll
           for (int sb = 0; sb < 2; ++sb) {
 #pragma unroll
@@ -292,22 +308,43 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
               const f32x2 spp = mul2(mul2(sg, oms), fma2(z1, fma2(mtwo, sg, one), two));   // silu''(z1)
               const f32x2 u = mul2(a, z3);
               const f32x2 pp = mul2(neta, praw);
-              const f32x2 du = mul2(neta, ndu);
+              const f32x2 du = mul2(neta2, ndu);
               const f32x2 z3sp = mul2(z3, sp);
-              const f32x2 dp = fma2(dg3, a, mul2(dg1, z3sp));
-              const f32x2 da = fma2(dg3, pp, mul2(du, z3));
-              const f32x2 gp = mul2(dg1, pp);
               const int w = 4 * sb + jp;
-              ob[1][w] = pack_bf16x2(fma2(gp, sp, mul2(du, a)));                  // dz3
-              ob[0][w] = pack_bf16x2(fma2(mul2(gp, z3), spp, mul2(da, sp)));      // dz1
-              ob[2][w] = pack_bf16x2(mul2(pp, z3sp));                            // g1
-              ob[3][w] = pack_bf16x2(mul2(pp, a));                               // g3
-              ob[4][w] = pack_bf16x2(mul2(neta, dp));                            // -lr dp
-              ob[5][w] = pack_bf16x2(mul2(neta, u));                             // -lr u
-              dsum = fma2(praw, dp, fma2(ndu, u, dsum));
+              if (!PM) {
+                const f32x2 dp = fma2(dg3, a, mul2(dg1, z3sp));
+                const f32x2 da = fma2(dg3, pp, mul2(du, z3));
+                const f32x2 gp = mul2(dg1, pp);
+                ob[1][w] = pack_bf16x2(fma2(gp, sp, mul2(du, a)));                  // dz3
+                ob[0][w] = pack_bf16x2(fma2(mul2(gp, z3), spp, mul2(da, sp)));      // dz1
+                ob[2][w] = pack_bf16x2(mul2(pp, z3sp));                            // g1
+                ob[3][w] = pack_bf16x2(mul2(pp, a));                               // g3
+                ob[4][w] = pack_bf16x2(mul2(neta, dp));                            // -lr dp
+                ob[5][w] = pack_bf16x2(mul2(neta, u));                             // -lr u
+                dsum = fma2(praw, dp, fma2(ndu, u, dsum));
+              } else {
+                // W1's terms with its rate, W3's with its rate, u's with W2's
+                const f32x2 pp3 = mul2(neta3, praw);
+                const f32x2 dg1z = mul2(dg1, z3sp), dg3a = mul2(dg3, a);
+                const f32x2 da = fma2(dg3, pp3, mul2(du, z3));
+                const f32x2 gp = mul2(dg1, pp);
+                ob[1][w] = pack_bf16x2(fma2(gp, sp, mul2(du, a)));                  // dz3
+                ob[0][w] = pack_bf16x2(fma2(mul2(gp, z3), spp, mul2(da, sp)));      // dz1
+                ob[2][w] = pack_bf16x2(mul2(pp, z3sp));                            // g1
+                ob[3][w] = pack_bf16x2(mul2(pp3, a));                              // g3
+                ob[4][w] = pack_bf16x2(fma2(neta, dg1z, mul2(neta3, dg3a)));      // -(e1 dg1 z3 s' + e3 dg3 a)
+                ob[5][w] = pack_bf16x2(mul2(neta2, u));                            // -e2 u
+                dsum = fma2(praw, dg1z, dsum);
+                dsum3 = fma2(praw, dg3a, dsum3);
+                dsum2 = fma2(ndu, u, dsum2);
+              }
             }
           }
-          deta -= x2_lo(dsum) + x2_hi(dsum);
+          deta[0] -= x2_lo(dsum) + x2_hi(dsum);
+          if (PM) {
+            deta[1] -= x2_lo(dsum3) + x2_hi(dsum3);
+            deta[2] -= x2_lo(dsum2) + x2_hi(dsum2);
+          }
         }
         // staging of the quarter: free once the previous quarter's products
         // and its scratch copy have read it
@@ -355,14 +392,19 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           // dlr of the token = sum of the two halves' partials (half 1 hands
           // its partial to half 0 through shared memory)
           const int e = i & 1;
+          float* eta_red = reinterpret_cast<float*>(sm + ETA_OFF) + e * 3 * BT;
           if (half == 1) {
             if (!mbar_wait_spin(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
-            B.eta_red[e][row] = deta;
+#pragma unroll
+            for (int j = 0; j < NR; ++j) eta_red[j * BT + row] = deta[j];
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.eta_full[e]);
           } else {
             if (!mbar_wait_spin(&B.eta_full[e], (i >> 1) & 1, abort)) break;
-            if (valid) p.dlr[(size_t)tok * H + h] = deta + B.eta_red[e][row];
+            if (valid) {
+#pragma unroll
+              for (int j = 0; j < NR; ++j) p.dlr[((size_t)tok * H + h) * NR + j] = deta[j] + eta_red[j * BT + row];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.eta_free[e]);
           }
@@ -508,7 +550,10 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = B.tmem_base;
-  if (key) run_key_vjp(maps, p, it, sm, B, tb);
+  if (key) {
+    if (p.lr_mat) run_key_vjp<true>(maps, p, it, sm, B, tb);
+    else run_key_vjp<false>(maps, p, it, sm, B, tb);
+  }
   else tl::token_lane_pass<true, EPI0>(&maps.x_q, &maps.y_do, &maps.s_dq, p, it, sm, TB, tb);
   tc_fence_before();
   __syncthreads();

@@ -296,7 +296,10 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   __syncthreads();
   tc_fence_after();
 
-  if (it.role == ROLE_KEY) tl::token_lane_pass<false, EPI0>(&maps.k, &maps.v, nullptr, p, it, sm, TB, tb);
+  if (it.role == ROLE_KEY) {
+    if (p.lr_mat) tl::token_lane_pass<false, EPI0, true>(&maps.k, &maps.v, nullptr, p, it, sm, TB, tb);
+    else tl::token_lane_pass<false, EPI0>(&maps.k, &maps.v, nullptr, p, it, sm, TB, tb);
+  }
   else apply_role(maps, p, it, sm, B, tb);
 
   tc_fence_before();

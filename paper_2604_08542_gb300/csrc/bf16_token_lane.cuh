@@ -191,8 +191,10 @@ __device__ void load_weights(const float* w, uint8_t* sm) {
 
 // The pass over the item's tokens.  mx, my: tensor maps of X and Y with
 // 64-token boxes; mdq: dq's (DQ only).  DQ selects the apply VJP (with dq
-// out), else the gradient (factors scaled by the token's learning rate).
-template <bool DQ, int EPI0>
+// out), else the gradient (factors scaled by the token's learning rate; PM:
+// one rate per matrix, lr [T, H, 3] = W1's, W3's, W2's, each factor scaled by
+// the rate of the matrix it updates).
+template <bool DQ, int EPI0, bool PM = false>
 __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, const CUtensorMap* mdq,
                                 const Params& p, const WorkItem& it, uint8_t* sm, Bars& B, uint32_t tb) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -306,12 +308,20 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
     // epilogue: thread = token row of the tile; half selects hidden units
     // [16*half, 16*half + 16) of every quarter.
     uint8_t* stg = sm + AST_OFF;
-    float eta = 0.f;
+    float eta = 0.f, eta3 = 0.f, eta2 = 0.f;
     for (int n = 0; n < nq; ++n) {
       const int i = n / NQ, q = n % NQ, b = n & 1;
       const int64_t tok = t0 + (int64_t)i * BT + row;
       const bool valid = tok < t1;
-      if (!DQ && q == 0) eta = valid ? p.lr[(size_t)tok * H + h] : 0.f;
+      if (!DQ && q == 0) {
+        if (PM) {
+          eta = valid ? p.lr[((size_t)tok * H + h) * 3] : 0.f;
+          eta3 = valid ? p.lr[((size_t)tok * H + h) * 3 + 1] : 0.f;
+          eta2 = valid ? p.lr[((size_t)tok * H + h) * 3 + 2] : 0.f;
+        } else {
+          eta = valid ? p.lr[(size_t)tok * H + h] : 0.f;
+        }
+      }
       if (!mbar_wait_spin(&B.ga_full[b], (n >> 1) & 1, abort)) break;
       tc_fence_after();
       const uint32_t buf = tb + lane_base + A_BUF + b * A_GBUF + 16 * half;
@@ -325,6 +335,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
         // the chain rule on pairs of hidden units (packed float32 lanes); the
         // scale is the learning rate (gradient) or the row's validity (dq)
         const f32x2 scale = x2(DQ ? (valid ? 1.f : 0.f) : eta), one = x2(1.f);
+        const f32x2 scale3 = x2(eta3), scale2 = x2(eta2);   // PM: W3's and W2's rates
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
           const int k = 2 * w;
@@ -332,10 +343,11 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
           const f32x2 sg = sigmoid2(z1);
           const f32x2 a = mul2(z1, sg);
           const f32x2 sp = fma2(a, sub2(one, sg), sg);
-          const f32x2 pk = mul2(scale, x2(r[2][k], r[2][k + 1]));
+          const f32x2 pr = x2(r[2][k], r[2][k + 1]);
+          const f32x2 pk = mul2(scale, pr);
           ob[0][w] = pack_bf16x2(mul2(mul2(pk, z3), sp));
-          ob[1][w] = pack_bf16x2(mul2(pk, a));
-          ob[2][w] = pack_bf16x2(mul2(scale, mul2(a, z3)));
+          ob[1][w] = pack_bf16x2(mul2(PM ? mul2(scale3, pr) : pk, a));
+          ob[2][w] = pack_bf16x2(mul2(PM ? scale2 : scale, mul2(a, z3)));
         }
       }
       // this thread's staging rows are free once the previous tile's L

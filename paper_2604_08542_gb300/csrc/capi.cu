@@ -415,7 +415,6 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
       (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
   if (cfg->ckpt_every > 1 && !wide) return SCAL3R_ERR_UNSUPPORTED;   // sparse checkpoints: the wide path
-  if (cfg->lr_per_matrix && !wide) return SCAL3R_ERR_UNSUPPORTED;     // per-matrix rates: the wide path
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
   int major = 0, minor = 0, sms = 0;

@@ -108,12 +108,13 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   float* Z3s = As + TT * F;
   float* SPs = Z3s + TT * F;       // SiLU'(z1), later g1
   float* Us = SPs + TT * F;
-  float* etas = Us + TT * F;
+  float* etas = Us + TT * F;       // the token's rate; with per-matrix rates three (W1, W3, W2)
 
   const WorkItem it = items[blockIdx.x];
   const int H = p.H;
   const int h = it.chain % H;
   const int chains = p.S * H;
+  const int nr = p.lr_mat ? 3 : 1;
   const float* w = p.wm + ((size_t)(step & 1) * chains + it.chain) * 3 * F * D;
   load_weights<D, F>(sm, w);
   const int tid = threadIdx.x;
@@ -169,7 +170,8 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
     __syncthreads();
     load_rows<D, F, TT, float>(Ks, kk, t, n, H, h);
     load_rows<D, F, TT, float>(Vs, vv, t, n, H, h);
-    for (int i = tid; i < TT; i += NTH) etas[i] = (i < n) ? p.lr[(size_t)(t + i) * H + h] : 0.f;
+    for (int i = tid; i < TT * nr; i += NTH)
+      etas[i] = (i / nr < n) ? p.lr[((size_t)(t + i / nr) * H + h) * nr + i % nr] : 0.f;
     __syncthreads();
     {  // z1, z3 and the SiLU pieces
       const int f = tid % F;
@@ -190,32 +192,34 @@ fp32_sweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
       }
     }
     __syncthreads();
-    {  // e~ = -lr dL/df
+    {  // e~ = -lr dL/df (one rate); with per-matrix rates -dL/df, the rates follow
       const int d = tid % D;
       for (int i = tid / D; i < TT; i += NTH / D) {
         float e;
         if (p.loss == SCAL3R_LOSS_DOT) {
-          e = etas[i] * Vs[i * D + d];
+          e = Vs[i * D + d];
         } else {
           float y = 0.f;
 #pragma unroll 16
           for (int f = 0; f < F; ++f) y = fmaf(Us[i * F + f], W2s[d * G::LD2 + f], y);
-          e = etas[i] * (Vs[i * D + d] - y);
+          e = Vs[i * D + d] - y;
         }
-        Es[i * D + d] = e;
+        Es[i * D + d] = p.lr_mat ? e : etas[i] * e;
       }
     }
     __syncthreads();
-    {  // p~ = W2^T e~, g1, g3
+    {  // p~ = W2^T e~, g1, g3 (matrix j's gradient weighted by its own rate)
       const int f = tid % F;
       for (int i = tid / F; i < TT; i += NTH / F) {
         float pp = 0.f;
 #pragma unroll 16
         for (int d = 0; d < D; ++d) pp = fmaf(Es[i * D + d], W2s[d * G::LD2 + f], pp);
-        const float g1 = pp * Z3s[i * F + f] * SPs[i * F + f];
-        const float g3 = pp * As[i * F + f];
+        const float p1 = p.lr_mat ? etas[3 * i] * pp : pp, p3 = p.lr_mat ? etas[3 * i + 1] * pp : pp;
+        const float g1 = p1 * Z3s[i * F + f] * SPs[i * F + f];
+        const float g3 = p3 * As[i * F + f];
         SPs[i * F + f] = g1;
         As[i * F + f] = g3;
+        if (p.lr_mat) Us[i * F + f] *= etas[3 * i + 2];   // W2's increment: u (e2 e~)^T
       }
     }
     __syncthreads();
@@ -277,8 +281,10 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   float* DAs = DPs + TT * F;
   float* DZ1s = DAs + TT * F;
   float* DZ3s = DZ1s + TT * F;
-  float* DHs = DZ3s + TT * F;        // per-element terms of dlr
-  float* etas = DHs + TT * D;
+  float* DHs = DZ3s + TT * F;        // per-element terms of dlr (of W2's rate with per-matrix rates)
+  float* DH1s = DHs + TT * D;        // per-matrix rates: the terms of W1's and W3's rates
+  float* DH3s = DH1s + TT * F;
+  float* etas = DH3s + TT * F;       // one rate per token, or three (W1, W3, W2)
 
   const WorkItem it = items[blockIdx.x];
   const int H = p.H;
@@ -370,13 +376,16 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
   const TIO* vv = (const TIO*)p.v;
   TIO* dk = (TIO*)p.dk;
   TIO* dv = (TIO*)p.dv;
+  const bool pm = p.lr_mat != 0;
+  const int nr = pm ? 3 : 1;
   for (int64_t t = it.t0; t < it.t1; t += TT) {
     const int n = (int)((it.t1 - t) < TT ? (it.t1 - t) : TT);
     __syncthreads();
     load_weights<D, F>(sm, w);
     load_rows<D, F, TT, TIO>(Ks, kk, t, n, H, h);
     load_rows<D, F, TT, TIO>(Vs, vv, t, n, H, h);
-    for (int i = tid; i < TT; i += NTH) etas[i] = (i < n) ? p.lr[(size_t)(t + i) * H + h] : 0.f;
+    for (int i = tid; i < TT * nr; i += NTH)
+      etas[i] = (i / nr < n) ? p.lr[((size_t)(t + i / nr) * H + h) * nr + i % nr] : 0.f;
     __syncthreads();
     // ---- recompute at W -------------------------------------------------
     {
@@ -402,14 +411,17 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
     {
       const int d = tid % D;
       for (int i = tid / D; i < TT; i += NTH / D) {
+        // e = lr (dL/df) with one rate; with per-matrix rates the residual
+        // dL/df itself (each matrix's rate enters below)
+        const float sc = pm ? 1.f : etas[i];
         if (mse) {
           float y = 0.f;
 #pragma unroll 16
           for (int f = 0; f < F; ++f) y = fmaf(Us[i * F + f], M2[d * G::LD2 + f], y);
           Ys[i * D + d] = y;
-          Es[i * D + d] = etas[i] * (y - Vs[i * D + d]);
+          Es[i * D + d] = sc * (y - Vs[i * D + d]);
         } else {
-          Es[i * D + d] = -etas[i] * Vs[i * D + d];
+          Es[i * D + d] = -sc * Vs[i * D + d];
         }
       }
     }
@@ -421,8 +433,9 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 #pragma unroll 16
         for (int d = 0; d < D; ++d) pp = fmaf(Es[i * D + d], M2[d * G::LD2 + f], pp);
         Ps[i * F + f] = pp;
-        G3s[i * F + f] = pp * As[i * F + f];
-        G1s[i * F + f] = pp * Z3s[i * F + f] * SPs[i * F + f];
+        // g1, g3 of the step (with per-matrix rates scaled by W1's, W3's rate)
+        G3s[i * F + f] = (pm ? etas[3 * i + 1] : 1.f) * pp * As[i * F + f];
+        G1s[i * F + f] = (pm ? etas[3 * i] : 1.f) * pp * Z3s[i * F + f] * SPs[i * F + f];
       }
     }
     __syncthreads();
@@ -457,6 +470,16 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
         dg1 = -dg1;
         dg3 = -dg3;
         const float a = As[i * F + f], z3 = Z3s[i * F + f], sp = SPs[i * F + f], pp = Ps[i * F + f];
+        if (pm) {
+          // per-matrix rates: the adjoints of (e1 h1), (e3 h3) scaled by their
+          // rates; dp is dL/dph (the residual's projection); the rates' terms
+          // h1 . dg1 and h3 . dg3 (h1 = ph z3 s', h3 = ph a)
+          DH1s[i * F + f] = pp * z3 * sp * dg1;
+          DH3s[i * F + f] = pp * a * dg3;
+          dg1 *= etas[3 * i];
+          dg3 *= etas[3 * i + 1];
+          du *= etas[3 * i + 2];
+        }
         DPs[i * F + f] = dg3 * a + dg1 * z3 * sp;
         DAs[i * F + f] = dg3 * pp;
         DZ3s[i * F + f] = dg1 * pp * sp;
@@ -471,12 +494,19 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
     {
       const int d = tid % D;
       for (int i = tid / D; i < TT; i += NTH / D) {
-        float de = DEs[i * D + d];
+        const float ds2 = DEs[i * D + d];
+        float de = pm ? etas[3 * i + 2] * ds2 : ds2;
 #pragma unroll 16
         for (int f = 0; f < F; ++f) de = fmaf(DPs[i * F + f], M2[d * G::LD2 + f], de);
         const float eta = etas[i];
         float dvv, dh;
-        if (mse) {
+        if (pm) {
+          // per-matrix rates: de = dL/d(residual) itself; W2's rate term is
+          // residual . ds2; dy = de for the squared error
+          DEs[i * D + d] = de;
+          dvv = -de;
+          dh = Es[i * D + d] * ds2;
+        } else if (mse) {
           DEs[i * D + d] = eta * de;                         // dy
           dvv = -eta * de;
           dh = (Ys[i * D + d] - Vs[i * D + d]) * de;
@@ -517,7 +547,19 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
       for (int i = tid; i < n; i += NTH) {
         float a = 0.f;
         for (int d2 = 0; d2 < D; ++d2) a += DHs[i * D + d2];   // fixed order
-        p.dlr[(size_t)(t + i) * H + h] = a;
+        if (pm) {
+          float a1 = 0.f, a3 = 0.f;
+          for (int f = 0; f < F; ++f) {
+            a1 += DH1s[i * F + f];
+            a3 += DH3s[i * F + f];
+          }
+          float* dl = p.dlr + ((size_t)(t + i) * H + h) * 3;
+          dl[0] = a1;
+          dl[1] = a3;
+          dl[2] = a;
+        } else {
+          p.dlr[(size_t)(t + i) * H + h] = a;
+        }
       }
     }
     {
@@ -550,11 +592,11 @@ fp32_bsweep_kernel(Params p, const WorkItem* __restrict__ items, int step) {
 
 template <int D, int F>
 constexpr size_t fwd_smem() {
-  return sizeof(float) * (Geo<D, F>::WS + 3 * 16 * D + 4 * 16 * F + 16);
+  return sizeof(float) * (Geo<D, F>::WS + 3 * 16 * D + 4 * 16 * F + 3 * 16);
 }
 template <int D, int F>
 constexpr size_t bwd_smem() {
-  return sizeof(float) * (Geo<D, F>::WS + 7 * 8 * D + 13 * 8 * F + 8);
+  return sizeof(float) * (Geo<D, F>::WS + 7 * 8 * D + 15 * 8 * F + 3 * 8);
 }
 
 template <int D, int F>

@@ -141,7 +141,6 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every > 1 || cfg->ckpt_every < 0 ||
       cfg->lr_per_matrix < 0 || cfg->lr_per_matrix > 1)
     return SCAL3R_ERR_INVALID_ARG;
-  if (cfg->lr_per_matrix) return SCAL3R_ERR_UNSUPPORTED;   // per-matrix rates: the wide-weight path
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->weight_norm < 0 || cfg->weight_norm > 2) return SCAL3R_ERR_INVALID_ARG;
@@ -205,7 +204,7 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   prm.S = pl.S;
   prm.T = pl.T;
   prm.loss = cfg->loss;
-  prm.lr_mat = 0;
+  prm.lr_mat = cfg->lr_per_matrix;
   prm.norm = cfg->weight_norm;
   prm.eps = cfg->norm_eps > 0.f ? cfg->norm_eps : 1e-6f;
   prm.status = status;

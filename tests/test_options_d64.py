@@ -1,0 +1,128 @@
+"""The layer's options at head_dim 64, hidden 128 (GPU, through the C ABI):
+per-matrix learning rates (reading A4b: matrix j's gradient of Eq. 8
+weighted by its own rate), on the float32 path and the fused bfloat16 path,
+forward and backward, against the FP64 oracle.
+
+Bars: 1e-5 normwise for float32, 2e-2 for bfloat16 (the oracle run on the
+same bfloat16-rounded inputs).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import ttt_synth as syn
+from _util import rel_inf, to_np, upload
+
+pytestmark = pytest.mark.gpu
+
+D, F = 64, 128
+TOLS = {"fp32": 1e-5, "bf16": 2e-2}
+
+
+def _run(dtype_name, lay, H, seed, loss="dot", lr=None, norm="row_w0", heads=None, **cfg):
+    """Forward + backward through the library and the oracle; returns the
+    normwise errors of every output and gradient (on `heads` only if given)."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=seed, dtype=dtype_name, with_grad_out=True)
+    if lr is not None:
+        x["lr"] = lr
+    g = upload(x, dtype)
+    layer = ttt.TTT(H, D, F, dtype=dtype, loss=loss, weight_norm=norm, **cfg)
+    o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                                  want_final=True)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    hs = list(range(H)) if heads is None else heads
+    xs = {n: x[n][:, hs] for n in ("q", "k", "v", "lr", "d_o")}
+    ref = oracle.forward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][hs], lay, D, F, loss=loss, norm=norm,
+                         eps=1e-6)
+    rb = oracle.backward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][hs], lay, xs["d_o"], D, F, loss=loss,
+                         norm=norm, eps=1e-6)
+    errs = {"o": rel_inf(to_np(o)[:, hs], ref["o"]), "w_final": rel_inf(to_np(wf)[:, hs], ref["w_final"])}
+    if layer.cfg.ckpt_every <= 1:
+        errs["w_ckpt"] = rel_inf(to_np(ck)[:, hs], ref["w_ckpt"])
+    errs["wnorm"] = rel_inf(to_np(wn)[:, hs], ref["wnorm"])
+    for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
+        a = to_np(t)
+        errs[n] = rel_inf(a[hs] if n == "dw0" else a[:, hs], rb[n])
+    return errs, (o, ck, wn, grads)
+
+
+def _assert(errs, tol, tag=""):
+    bad = {n: e for n, e in errs.items() if not e <= tol}
+    assert not bad, f"{tag} above {tol}: {bad}; all {errs}"
+
+
+# ---- per-matrix learning rates ----------------------------------------------
+
+@pytest.mark.parametrize("dtype_name,loss", [("fp32", "dot"), ("fp32", "mse"), ("bf16", "dot")])
+def test_per_matrix_rates_match_oracle(dtype_name, loss):
+    """lr [T, H, 3] (W1, W3, W2): forward outputs and every gradient, dlr
+    included in the same layout; two heads, ragged chunks with tile edges."""
+    lay = syn.layout_from_lengths([[300, 129], [77, 257]])
+    H = 2
+    lr = syn.per_matrix_lr(81, lay.num_tokens, H, lr_max=0.1)
+    errs, _ = _run(dtype_name, lay, H, seed=80, loss=loss, lr=lr, lr_per_matrix=True)
+    _assert(errs, TOLS[dtype_name], f"{dtype_name}/{loss}")
+
+
+@pytest.mark.parametrize("dtype_name", ["fp32", "bf16"])
+def test_per_matrix_rates_with_one_matrix_frozen(dtype_name):
+    """W3's rates all zero: the oracle keeps W3's update at zero while W1 and
+    W2 move, and the library matches it (which rate scales which matrix)."""
+    lay = syn.layout_from_lengths([[200, 129]])
+    H = 2
+    lr = syn.per_matrix_lr(83, lay.num_tokens, H, lr_max=0.1)
+    lr[:, :, 1] = 0.0
+    errs, _ = _run(dtype_name, lay, H, seed=82, lr=lr, norm="none", lr_per_matrix=True)
+    _assert(errs, TOLS[dtype_name])
+
+
+@pytest.mark.parametrize("dtype_name", ["fp32", "bf16"])
+def test_equal_per_matrix_rates_are_the_one_rate_layer(dtype_name):
+    """Three equal rates per token reproduce the one-rate layer, with dlr
+    split three ways (the bfloat16 forward bitwise: its gradient pieces scale
+    the same products by the same rate; the float32 one applies the rate
+    after the W2 product instead of before, so up to rounding)."""
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
+    lay = syn.layout_from_lengths([[260, 200], [128]])
+    H = 2
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=84, dtype=dtype_name, with_grad_out=True)
+    g = upload(x, dtype)
+    res = []
+    for per in (False, True):
+        layer = ttt.TTT(H, D, F, dtype=dtype, lr_per_matrix=per)
+        lr = g["lr"][..., None].expand(-1, -1, 3).contiguous() if per else g["lr"]
+        o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], lr, g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+        grads = layer.backward(g["q"], g["k"], g["v"], lr, g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        res.append((o, ck, grads))
+    (o1, ck1, g1), (o3, ck3, g3) = res
+    if dtype_name == "bf16":
+        assert torch.equal(o1, o3) and torch.equal(ck1, ck3)
+    else:
+        assert rel_inf(to_np(o3), to_np(o1)) < 1e-6 and rel_inf(to_np(ck3), to_np(ck1)) < 1e-6
+    tol = 1e-5 if dtype_name == "fp32" else 5e-3
+    for n, a, b in zip(("dq", "dk", "dv", "dw0"), (g1[0], g1[1], g1[2], g1[4]), (g3[0], g3[1], g3[2], g3[4])):
+        assert rel_inf(to_np(b), to_np(a)) < tol, n
+    assert rel_inf(to_np(g3[3]).sum(-1), to_np(g1[3])) < tol
+
+
+def test_per_matrix_rates_full_size_sampled_heads():
+    """The forward+backward workload (2 sequences x 32 frames x 1041 tokens,
+    16 heads, chunk 8 frames) with a rate per matrix; the oracle checks two
+    whole heads."""
+    w = syn.workload("bf16_fwdbwd_2x32")
+    lay = w.layout()
+    lr = syn.per_matrix_lr(86, lay.num_tokens, 16, lr_max=0.1)
+    errs, _ = _run("bf16", lay, 16, seed=85, lr=lr, heads=[4, 11], lr_per_matrix=True)
+    print("per-matrix fwdbwd_2x32 errors", errs)
+    _assert(errs, TOLS["bf16"])

@@ -20,11 +20,11 @@ from _util import rel_inf, to_np, upload
 
 pytestmark = pytest.mark.gpu
 
-CASES = [("bf16", "dot", False, 2e-2), ("fp32", "dot", False, 1e-5), ("fp32", "mse", False, 1e-5),
-         ("fp32", "dot", True, 1e-5)]
+CASES = [("bf16", "dot", False, False, 2e-2), ("fp32", "dot", False, False, 1e-5),
+         ("fp32", "mse", False, False, 1e-5), ("fp32", "dot", True, False, 1e-5), ("bf16", "dot", True, True, 2e-2)]
 
 
-def _setup(dtype_name, loss, per_seq_w0, seed=31):
+def _setup(dtype_name, loss, per_seq_w0, per_matrix=False, seed=31):
     import torch
     import paper_2604_08542_gb300 as ttt
     dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
@@ -34,17 +34,19 @@ def _setup(dtype_name, loss, per_seq_w0, seed=31):
     x = syn.make_inputs(T, H, D, F, seed=seed, dtype=dtype_name)
     if loss == "mse":
         x["lr"] = x["lr"] * 0.3   # keeps the squared-error recurrence in range
+    if per_matrix:
+        x["lr"] = syn.per_matrix_lr(seed + 2, T, H, lr_max=0.1)
     g = upload(x, dtype)
     if per_seq_w0:
         w = syn.make_inputs(1, S * H, D, F, seed=seed + 1)["w0"].reshape(S, H, 3 * F * D)
         g["w0"] = torch.from_numpy(np.ascontiguousarray(w)).cuda()
-    layer = ttt.TTT(H, D, F, dtype=dtype, loss=loss)
+    layer = ttt.TTT(H, D, F, dtype=dtype, loss=loss, lr_per_matrix=per_matrix)
     ref = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
                         want_final=True)
     torch.cuda.synchronize()
     cfg = ttt.scal3r_ttt_config(H, D, F, ttt.SCAL3R_BF16 if dtype_name == "bf16" else ttt.SCAL3R_FP32,
                                 ttt.SCAL3R_LOSS_MSE if loss == "mse" else ttt.SCAL3R_LOSS_DOT,
-                                ttt.SCAL3R_NORM_ROW_W0, 1e-6, 0)
+                                ttt.SCAL3R_NORM_ROW_W0, 1e-6, 0, lr_per_matrix=int(per_matrix))
     stride = H * 3 * F * D if per_seq_w0 else 0
     return lay, g, ref, cfg, stride, (H, D, F)
 
@@ -73,11 +75,11 @@ def _check(outs, ref, tol, tag):
         assert np.isfinite(err) and err <= tol, (tag, name, err)
 
 
-@pytest.mark.parametrize("dtype_name,loss,per_seq_w0,tol", CASES)
-def test_noalloc_forward_matches_forward_twice(dtype_name, loss, per_seq_w0, tol):
+@pytest.mark.parametrize("dtype_name,loss,per_seq_w0,per_matrix,tol", CASES)
+def test_noalloc_forward_matches_forward_twice(dtype_name, loss, per_seq_w0, per_matrix, tol):
     import torch
     import paper_2604_08542_gb300 as ttt
-    lay, g, ref, cfg, stride, shape = _setup(dtype_name, loss, per_seq_w0)
+    lay, g, ref, cfg, stride, shape = _setup(dtype_name, loss, per_seq_w0, per_matrix)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         outs = _outputs(lay, shape, g["q"])
