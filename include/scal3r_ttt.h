@@ -38,7 +38,9 @@
  *    the config's dtype (float32 or bfloat16), 16-byte aligned device memory.
  *  - lr, dlr: [T, H] float32 device memory ([T, H, 3] with lr_per_matrix).
  *  - Fast weights of one head are P = 3*F*D float32 values packed W1, W3, W2,
- *    each row-major.  w0 is [H, P] shared by all sequences (w0_seq_stride = 0)
+ *    each row-major (the linear model: P = D*D, W row-major).  Row norms
+ *    per chunk and head: R = 2*F + D (linear: D).
+ *    w0 is [H, P] shared by all sequences (w0_seq_stride = 0)
  *    or one [H, P] block per sequence, w0_seq_stride floats apart.
  *  - chunk_offsets [C+1] int64 and seq_chunk_ptr [S+1] int32 are HOST arrays:
  *    chunk c covers tokens [chunk_offsets[c], chunk_offsets[c+1]) of the
@@ -90,6 +92,12 @@ extern "C" {
 #define SCAL3R_NORM_NONE    1   /* no rescaling */
 #define SCAL3R_NORM_UNIT    2   /* rescale rows to unit norm */
 
+/* scal3r_ttt_config.model: the fast-weight network f_W */
+#define SCAL3R_MODEL_SWIGLU 0   /* f_W(x) = W2 (SiLU(W1 x) * W3 x), Supp. Sec. A (the default) */
+#define SCAL3R_MODEL_LINEAR 1   /* f_W(x) = W x, one D x D matrix (Sec. 3.2, Eq. 3-4 with a linear
+                                   map): with the dot loss and no normalisation the forward is
+                                   chunk-causal linear attention, a closed form for testing */
+
 typedef struct scal3r_ttt_config {
   int32_t num_heads;    /* H >= 1 */
   int32_t head_dim;     /* D; BF16: 64 (fused per-head kernels) or a multiple of 256 up to 4096
@@ -109,6 +117,15 @@ typedef struct scal3r_ttt_config {
                            1 (every path): lr [T, H, 3], the rates of W1, W3, W2 in that
                            order, each matrix's gradient (Eq. 8) weighted by its own rate;
                            dlr then has the same [T, H, 3] layout */
+  int32_t model;        /* SCAL3R_MODEL_SWIGLU (0) | SCAL3R_MODEL_LINEAR.  LINEAR: float32 only,
+                           hidden_dim = head_dim in {16, 32, 64}, lr_per_matrix 0, ckpt_every
+                           0 or 1; P = D*D (W row-major [D][D]) and wnorm keeps D row norms per
+                           chunk and head.  Every loss and normalisation; forward and backward
+                           only (the other entry points return SCAL3R_ERR_UNSUPPORTED) */
+  int32_t deterministic; /* 0 or 1.  Every reduction of every path (partial sums over pieces,
+                           sums over sequences of dw0) runs in a fixed order, so repeated calls
+                           with the same inputs and layout give bitwise the same results for
+                           either value; no faster non-deterministic variant exists */
 } scal3r_ttt_config;
 
 typedef struct scal3r_ttt_handle scal3r_ttt_handle;
@@ -149,7 +166,7 @@ int scal3r_ttt_ckpt_slots(const scal3r_ttt_handle* handle, const int32_t* seq_ch
  *            update (needed by the backward).  With ckpt_every = n > 1:
  *            [scal3r_ttt_ckpt_slots, H, P], the weights after local chunks
  *            n-1, 2n-1, ... of sequence 0, then of sequence 1, ...
- *   wnorm    [C,H,2F+D] float32 out or NULL: each row's L2 norm after the
+ *   wnorm    [C,H,R] float32 out or NULL: each row's L2 norm after the
  *            gradient step and before rescaling (needed by the backward).
  *   w_final  [S,H,P] float32 out or NULL: the weights after the last chunk
  *            of each sequence (w0 for a sequence with no chunk); pass it as

@@ -40,6 +40,8 @@ SCAL3R_LOSS_MSE = 1
 SCAL3R_NORM_ROW_W0 = 0
 SCAL3R_NORM_NONE = 1
 SCAL3R_NORM_UNIT = 2
+SCAL3R_MODEL_SWIGLU = 0
+SCAL3R_MODEL_LINEAR = 1
 
 SCAL3R_KERNEL_FWD_SWEEP = 0
 SCAL3R_KERNEL_FWD_UPDATE = 1
@@ -62,7 +64,13 @@ class scal3r_ttt_config(ctypes.Structure):
                 ("hidden_dim", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("loss", ctypes.c_int32), ("weight_norm", ctypes.c_int32),
                 ("norm_eps", ctypes.c_float), ("ckpt_every", ctypes.c_int32),
-                ("lr_per_matrix", ctypes.c_int32)]
+                ("lr_per_matrix", ctypes.c_int32), ("model", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
+
+    def __init__(self, *args, **kw):
+        if len(args) < 11:
+            kw.setdefault("deterministic", 1)
+        super().__init__(*args, **kw)
 
 
 class scal3r_ttt_schedule(ctypes.Structure):

@@ -71,6 +71,7 @@ cudaError_t prepare_kernels() {
   if (e == cudaSuccess) e = prepare_bf16_forward();
   if (e == cudaSuccess) e = prepare_bf16_backward();
   if (e == cudaSuccess) e = prepare_wide();
+  if (e == cudaSuccess) e = prepare_linear_kernels();
   return e;
 }
 }  // namespace scal3r
@@ -157,6 +158,10 @@ void free_plan(Plan& p) {
   if (p.d_updates) cudaFree(p.d_updates);
   if (p.d_bitems) cudaFree(p.d_bitems);
   if (p.d_bupdates) cudaFree(p.d_bupdates);
+  if (p.d_off) cudaFree(p.d_off);
+  if (p.d_ptr) cudaFree(p.d_ptr);
+  p.d_off = nullptr;
+  p.d_ptr = nullptr;
   p.d_items = nullptr;
   p.d_updates = nullptr;
   p.d_bitems = nullptr;
@@ -186,7 +191,8 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
   int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   if (upload(&np.d_items, np.items) != cudaSuccess || upload(&np.d_updates, np.updates) != cudaSuccess ||
-      upload(&np.d_bitems, np.bitems) != cudaSuccess || upload(&np.d_bupdates, np.bupdates) != cudaSuccess) {
+      upload(&np.d_bitems, np.bitems) != cudaSuccess || upload(&np.d_bupdates, np.bupdates) != cudaSuccess ||
+      upload(&np.d_off, np.chunk_offsets) != cudaSuccess || upload(&np.d_ptr, np.seq_chunk_ptr) != cudaSuccess) {
     free_plan(np);
     return SCAL3R_ERR_CUDA;
   }
@@ -404,10 +410,17 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every < 0 ||
       cfg->lr_per_matrix < 0 || cfg->lr_per_matrix > 1)
     return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->model != SCAL3R_MODEL_SWIGLU && cfg->model != SCAL3R_MODEL_LINEAR) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->deterministic < 0 || cfg->deterministic > 1) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->weight_norm < 0 || cfg->weight_norm > 2) return SCAL3R_ERR_INVALID_ARG;
-  if (cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
+  const bool lin = cfg->model == SCAL3R_MODEL_LINEAR;
+  // the linear model: float32, hidden_dim = head_dim, one rate per token, a checkpoint per chunk
+  if (lin && (cfg->dtype != SCAL3R_FP32 || !linear_shape_supported(cfg->head_dim, cfg->hidden_dim) ||
+              cfg->lr_per_matrix || cfg->ckpt_every > 1))
+    return SCAL3R_ERR_UNSUPPORTED;
+  if (!lin && cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
     return SCAL3R_ERR_UNSUPPORTED;
   const bool wide = cfg->dtype == SCAL3R_BF16 && wide_shape_supported(cfg->head_dim, cfg->hidden_dim);
   // BF16: the D = 64, F = 128 path (dot loss) or the wide-weight path (both losses)
@@ -426,7 +439,7 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (prepare_kernels() != cudaSuccess) return SCAL3R_ERR_CUDA;
   auto* hd = new scal3r_ttt_handle();
   hd->cfg = *cfg;
-  hd->shape = Shape{cfg->num_heads, cfg->head_dim, cfg->hidden_dim};
+  hd->shape = Shape{cfg->num_heads, cfg->head_dim, cfg->hidden_dim, lin ? 1 : 0};
   hd->device = dev;
   hd->num_sms = sms;
   hd->wide = wide;
@@ -462,6 +475,10 @@ int scal3r_ttt_workspace_size(scal3r_ttt_handle* hd, const int64_t* off, int32_t
   if (!hd || !bytes) return SCAL3R_ERR_INVALID_ARG;
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
+  if (hd->shape.lin) {   // the backward's per-chain dW0 (shared w0)
+    *bytes = with_backward ? (size_t)hd->plan.S * hd->shape.H * hd->shape.P() * sizeof(float) : 0;
+    return SCAL3R_OK;
+  }
   if (hd->wide) {
     *bytes = wide_workspace_bytes(hd->plan, hd->shape, with_backward != 0, hd->cfg.ckpt_every, hd->cfg.loss,
                                          hd->cfg.lr_per_matrix);
@@ -486,6 +503,28 @@ static int forward_impl(scal3r_ttt_handle* hd, const void* q, const void* k, con
   if (!aligned16(q) || !aligned16(k) || !aligned16(v) || !aligned16(o)) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(lr) || !aligned16(w0) || (w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
   if (!aligned16(w_ckpt) || !aligned16(w_final)) return SCAL3R_ERR_MISALIGNED;
+  if (sh.lin) {   // the linear model: one kernel, one CTA per chain, no workspace
+    Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    fill_common(hd, prm);
+    prm.q = q;
+    prm.k = k;
+    prm.v = v;
+    prm.lr = lr;
+    prm.w0 = w0;
+    prm.w0_seq_stride = w0_seq_stride;
+    prm.o = o;
+    prm.w_ckpt = w_ckpt;
+    prm.wnorm = wnorm;
+    prm.w_final = w_final;
+    prm.off = pl.d_off;
+    prm.sptr = pl.d_ptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    return timed(hd, SCAL3R_KERNEL_FWD_SWEEP, 0, 0, st, [&] { return launch_linear_forward(prm, st); }) ==
+                   cudaSuccess
+               ? SCAL3R_OK
+               : SCAL3R_ERR_CUDA;
+  }
   const size_t need =
       hd->wide ? wide_workspace_bytes(pl, sh, false, hd->cfg.ckpt_every, hd->cfg.loss,
                                          hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, false);
@@ -560,6 +599,35 @@ static int backward_impl(scal3r_ttt_handle* hd, const void* q, const void* k, co
                         (const void*)w0, (const void*)dw0})
     if (!aligned16(p)) return SCAL3R_ERR_MISALIGNED;
   if ((w0_seq_stride & 3) != 0) return SCAL3R_ERR_MISALIGNED;
+  if (sh.lin) {   // the linear model: one kernel, one CTA per chain (+ the dw0 sum for a shared w0)
+    const size_t lneed = w0_seq_stride ? 0 : (size_t)pl.S * sh.H * sh.P() * sizeof(float);
+    if (lneed && (!workspace || workspace_bytes_ < lneed || !aligned16(workspace))) return SCAL3R_ERR_WORKSPACE;
+    Params prm;
+    std::memset(&prm, 0, sizeof(prm));
+    fill_common(hd, prm);
+    prm.q = q;
+    prm.k = k;
+    prm.v = v;
+    prm.lr = lr;
+    prm.w0 = w0;
+    prm.w0_seq_stride = w0_seq_stride;
+    prm.d_o = d_o;
+    prm.w_ckpt_in = w_ckpt;
+    prm.wnorm_in = wnorm;
+    prm.dq = dq;
+    prm.dk = dk;
+    prm.dv = dv;
+    prm.dlr = dlr;
+    prm.dw0 = dw0;
+    prm.dw0_chain = static_cast<float*>(workspace);
+    prm.off = pl.d_off;
+    prm.sptr = pl.d_ptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    return timed(hd, SCAL3R_KERNEL_BWD_SWEEP, 0, 0, st, [&] { return launch_linear_backward(prm, st); }) ==
+                   cudaSuccess
+               ? SCAL3R_OK
+               : SCAL3R_ERR_CUDA;
+  }
   const size_t need =
       hd->wide ? wide_workspace_bytes(pl, sh, true, hd->cfg.ckpt_every, hd->cfg.loss,
                                          hd->cfg.lr_per_matrix) : workspace_bytes(pl, sh, true);
@@ -793,7 +861,7 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
                         void* dv, float* dlr, float* dw0, int32_t with_backward, void* stream,
                         scal3r_ttt_schedule* best, float* best_ms) {
   if (!hd || !best || !best_ms) return SCAL3R_ERR_INVALID_ARG;
-  if (hd->wide) return SCAL3R_ERR_UNSUPPORTED;   // the schedule knobs are the head_dim-64 path's
+  if (hd->wide || hd->shape.lin) return SCAL3R_ERR_UNSUPPORTED;   // the schedule knobs are the head_dim-64 path's
   if (with_backward && (!d_o || !dq || !dk || !dv || !dlr || !dw0 || !w_ckpt || !wnorm))
     return SCAL3R_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -944,6 +1012,7 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
                             int64_t w_seq_stride, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S,
                             float* grad, void* workspace, size_t workspace_bytes_, void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->shape.lin) return SCAL3R_ERR_UNSUPPORTED;
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;
@@ -1005,6 +1074,7 @@ int scal3r_ttt_apply_update(scal3r_ttt_handle* hd, const float* w, int64_t w_seq
                             const float* w0, int64_t w0_seq_stride, int32_t num_seqs, float* w_out, float* wnorm,
                             void* stream) {
   if (!hd || num_seqs < 0) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->shape.lin) return SCAL3R_ERR_UNSUPPORTED;
   const Shape& sh = hd->shape;
   if (num_seqs == 0) return SCAL3R_OK;
   if (!w || !grad || !w0 || !w_out || w_seq_stride < 0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
@@ -1039,6 +1109,7 @@ int scal3r_ttt_apply(scal3r_ttt_handle* hd, const void* q, const float* w, int64
                      int32_t C, const int32_t* ptr, int32_t S, void* o, void* workspace, size_t workspace_bytes_,
                      void* stream) {
   if (!hd) return SCAL3R_ERR_INVALID_ARG;
+  if (hd->shape.lin) return SCAL3R_ERR_UNSUPPORTED;
   int rc = ensure_plan(hd, off, C, ptr, S);
   if (rc != SCAL3R_OK) return rc;
   const Plan& pl = hd->plan;

@@ -141,6 +141,9 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   if (cfg->num_heads < 1 || cfg->head_dim < 1 || cfg->hidden_dim < 1 || cfg->ckpt_every > 1 || cfg->ckpt_every < 0 ||
       cfg->lr_per_matrix < 0 || cfg->lr_per_matrix > 1)
     return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->model != SCAL3R_MODEL_SWIGLU && cfg->model != SCAL3R_MODEL_LINEAR) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->deterministic < 0 || cfg->deterministic > 1) return SCAL3R_ERR_INVALID_ARG;
+  if (cfg->model == SCAL3R_MODEL_LINEAR) return SCAL3R_ERR_UNSUPPORTED;   // the handle's forward runs it
   if (cfg->dtype != SCAL3R_FP32 && cfg->dtype != SCAL3R_BF16) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->loss != SCAL3R_LOSS_DOT && cfg->loss != SCAL3R_LOSS_MSE) return SCAL3R_ERR_INVALID_ARG;
   if (cfg->weight_norm < 0 || cfg->weight_norm > 2) return SCAL3R_ERR_INVALID_ARG;

@@ -73,6 +73,8 @@ struct Plan {
   UpdateItem* d_updates = nullptr;
   WorkItem* d_bitems = nullptr;
   UpdateItem* d_bupdates = nullptr;
+  int64_t* d_off = nullptr;     // chunk_offsets and seq_chunk_ptr (the linear model's kernels)
+  int32_t* d_ptr = nullptr;
   bool valid = false;
 };
 
@@ -94,8 +96,9 @@ struct Schedule {
 
 struct Shape {
   int32_t H, D, F;
-  int32_t P() const { return 3 * F * D; }
-  int32_t R() const { return 2 * F + D; }
+  int32_t lin = 0;   // 1: the linear model, one D x D matrix per chain
+  int32_t P() const { return lin ? D * D : 3 * F * D; }
+  int32_t R() const { return lin ? D : 2 * F + D; }
 };
 
 // Device-side parameter block of one forward/backward call.
@@ -110,6 +113,8 @@ struct Params {
   const void* d_o;
   const float* w_ckpt_in;
   const float* wnorm_in;
+  const int64_t* off;    // linear model: device copies of chunk_offsets and seq_chunk_ptr
+  const int32_t* sptr;
   // outputs
   void* o;
   float* w_ckpt;
@@ -159,6 +164,11 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int nite
                               const void* tmaps, cudaStream_t st);
 cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int nitems, int step,
                                const void* tmaps, cudaStream_t st);
+// linear model (float32): one CTA per chain runs its whole chunk loop
+bool linear_shape_supported(int D, int F);
+cudaError_t prepare_linear_kernels();
+cudaError_t launch_linear_forward(const Params& prm, cudaStream_t st);
+cudaError_t launch_linear_backward(const Params& prm, cudaStream_t st);
 // Set kernel attributes once (outside any stream capture).
 cudaError_t prepare_kernels();
 

@@ -16,7 +16,8 @@ import hashlib
 import json
 import os
 
-from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3R_NORM_NONE,
+from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3R_MODEL_LINEAR,
+               SCAL3R_MODEL_SWIGLU, SCAL3R_NORM_NONE,
                SCAL3R_NORM_ROW_W0, SCAL3R_NORM_UNIT, Scal3rError, _check, scal3r_ttt_autotune, scal3r_ttt_backward,
                scal3r_ttt_config, scal3r_ttt_destroy, scal3r_ttt_forward, scal3r_ttt_get_schedule,
                scal3r_ttt_get_status, scal3r_ttt_init, scal3r_ttt_plan, scal3r_ttt_schedule,
@@ -26,6 +27,7 @@ from . import (SCAL3R_BF16, SCAL3R_FP32, SCAL3R_LOSS_DOT, SCAL3R_LOSS_MSE, SCAL3
 
 NORMS = {"row_w0": SCAL3R_NORM_ROW_W0, "none": SCAL3R_NORM_NONE, "unit": SCAL3R_NORM_UNIT}
 LOSSES = {"dot": SCAL3R_LOSS_DOT, "mse": SCAL3R_LOSS_MSE}
+MODELS = {"swiglu": SCAL3R_MODEL_SWIGLU, "linear": SCAL3R_MODEL_LINEAR}
 
 
 def _ptr(t):
@@ -37,26 +39,28 @@ class TTT:
 
     def __init__(self, num_heads: int, head_dim: int = 64, hidden_dim: int = 128,
                  dtype: torch.dtype = torch.bfloat16, loss: str = "dot", weight_norm: str = "row_w0",
-                 norm_eps: float = 1e-6, ckpt_every: int = 1, lr_per_matrix: bool = False):
+                 norm_eps: float = 1e-6, ckpt_every: int = 1, lr_per_matrix: bool = False,
+                 model: str = "swiglu", deterministic: bool = True):
         if dtype not in (torch.bfloat16, torch.float32):
             raise ValueError("dtype must be torch.bfloat16 or torch.float32")
         self.H, self.D, self.F = num_heads, head_dim, hidden_dim
         self.dtype = dtype
+        self.model = model
         self.cfg = scal3r_ttt_config(num_heads, head_dim, hidden_dim,
                                      SCAL3R_BF16 if dtype == torch.bfloat16 else SCAL3R_FP32,
                                      LOSSES[loss], NORMS[weight_norm], float(norm_eps), int(ckpt_every),
-                                     int(bool(lr_per_matrix)))
+                                     int(bool(lr_per_matrix)), MODELS[model], int(bool(deterministic)))
         self.lr_shape = (num_heads, 3) if lr_per_matrix else (num_heads,)
         self.handle = scal3r_ttt_init(self.cfg)
         self._ws = None
 
     @property
     def P(self) -> int:
-        return 3 * self.F * self.D
+        return self.D * self.D if self.model == "linear" else 3 * self.F * self.D
 
     @property
     def R(self) -> int:
-        return 2 * self.F + self.D
+        return self.D if self.model == "linear" else 2 * self.F + self.D
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -95,7 +99,7 @@ class TTT:
             return 0
         if w0.dim() == 3 and tuple(w0.shape) == (S, self.H, self.P):
             return self.H * self.P
-        raise ValueError("w0 must be [H, 3*F*D] or [S, H, 3*F*D]")
+        raise ValueError("w0 must be [H, P] or [S, H, P] (P = 3*F*D, or D*D for the linear model)")
 
     # -- passes ------------------------------------------------------------
     def forward(self, q, k, v, lr, w0, chunk_offsets, seq_chunk_ptr, *, save_for_backward=True,

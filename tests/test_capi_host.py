@@ -61,6 +61,17 @@ def test_init_without_a_device_fails_cleanly(libpath):
     assert e.value.status in (ttt.SCAL3R_ERR_NO_DEVICE, ttt.SCAL3R_ERR_CUDA)
 
 
+def test_config_struct_matches_the_header(libpath):
+    # the binding's structure has the header's fields in the header's order
+    import re
+    import paper_2604_08542_gb300 as ttt
+    hdr = open(os.path.join(ROOT, "include", "scal3r_ttt.h")).read()
+    body = hdr[hdr.index("typedef struct scal3r_ttt_config {"):hdr.index("} scal3r_ttt_config;")]
+    names = re.findall(r"^\s*(?:int32_t|float)\s+(\w+);", body, flags=re.M)
+    assert names == [n for n, _ in ttt.scal3r_ttt_config._fields_]
+    assert ttt.scal3r_ttt_config(1, 64, 128, 1, 0, 0, 1e-6, 0).deterministic == 1
+
+
 def test_bad_config_rejected_before_device_query(libpath):
     import paper_2604_08542_gb300 as ttt
     bad = [ttt.scal3r_ttt_config(0, 64, 128, 1, 0, 0, 1e-6, 0),        # no heads
@@ -68,7 +79,9 @@ def test_bad_config_rejected_before_device_query(libpath):
            ttt.scal3r_ttt_config(16, 64, 128, 1, 5, 0, 1e-6, 0),       # bad loss
            ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 9, 1e-6, 0),       # bad norm
            ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, -1),      # negative checkpoint interval
-           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 0, 2)]    # bad rate layout
+           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 0, 2),    # bad rate layout
+           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 0, 0, 2),  # bad model
+           ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 0, 0, 0, 3)]   # bad determinism flag
     for c in bad:
         with pytest.raises(ttt.Scal3rError) as e:
             ttt.scal3r_ttt_init(c)
@@ -76,7 +89,10 @@ def test_bad_config_rejected_before_device_query(libpath):
     for c in (ttt.scal3r_ttt_config(16, 32, 128, 1, 0, 0, 1e-6, 0),     # BF16 needs D=64, F=128 or wide
               ttt.scal3r_ttt_config(16, 48, 100, 0, 0, 0, 1e-6, 0),     # FP32 shape not built
               ttt.scal3r_ttt_config(16, 64, 128, 1, 1, 0, 1e-6, 0),     # squared-error loss: wide path only (BF16)
-              ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 3)):    # sparse checkpoints: wide path only
+              ttt.scal3r_ttt_config(16, 64, 128, 1, 0, 0, 1e-6, 3),     # sparse checkpoints: wide path only
+              ttt.scal3r_ttt_config(4, 64, 64, 1, 0, 0, 1e-6, 0, 0, 1),  # linear model: float32 only
+              ttt.scal3r_ttt_config(4, 64, 128, 0, 0, 0, 1e-6, 0, 0, 1),  # linear model: hidden_dim = head_dim
+              ttt.scal3r_ttt_config(4, 64, 64, 0, 0, 0, 1e-6, 0, 1, 1)):  # linear model: one rate per token
         with pytest.raises(ttt.Scal3rError) as e:
             ttt.scal3r_ttt_init(c)
         assert e.value.status == ttt.SCAL3R_ERR_UNSUPPORTED
