@@ -26,11 +26,10 @@
  * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
  * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
  * step as a large tcgen05 GEMM, forward and backward.  The wide path also
- * takes the squared-error loss and sparse checkpoints (ckpt_every > 1); the
- * head_dim-64 path takes the dot loss and a checkpoint per chunk, and the
- * autotuner is for it (SCAL3R_ERR_UNSUPPORTED otherwise).  Per-matrix
- * learning rates (lr_per_matrix) run on every path.  The float32 path takes
- * either loss.
+ * takes the squared-error loss; the head_dim-64 path takes the dot loss, and
+ * the autotuner is for it (SCAL3R_ERR_UNSUPPORTED otherwise).  Per-matrix
+ * learning rates (lr_per_matrix) and sparse checkpoints (ckpt_every > 1) run
+ * on every SwiGLU path.  The float32 path takes either loss.
  *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
@@ -109,10 +108,11 @@ typedef struct scal3r_ttt_config {
   int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 and wide-weight paths) */
   int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
   float   norm_eps;     /* clamp of the row norm; <= 0 selects 1e-6 */
-  int32_t ckpt_every;   /* chunks between stored checkpoints: 0 or 1 = every chunk.  n > 1 (the
-                           wide-weight path only) stores the weights after local chunks n-1,
-                           2n-1, ... of each sequence; the backward recomputes the weights in
-                           between with the forward's own gradient steps (bitwise the same) */
+  int32_t ckpt_every;   /* chunks between stored checkpoints: 0 or 1 = every chunk.  n > 1 (not
+                           the linear model) stores the weights after local chunks n-1, 2n-1,
+                           ... of each sequence; the backward recomputes the weights in between
+                           with the forward's own gradient steps (bitwise the same), holding
+                           n-1 weight sets per chain in its workspace */
   int32_t lr_per_matrix; /* 0: lr [T, H], one rate per token and head for all three matrices.
                            1 (every path): lr [T, H, 3], the rates of W1, W3, W2 in that
                            order, each matrix's gradient (Eq. 8) weighted by its own rate;

@@ -158,6 +158,12 @@ void free_plan(Plan& p) {
   if (p.d_updates) cudaFree(p.d_updates);
   if (p.d_bitems) cudaFree(p.d_bitems);
   if (p.d_bupdates) cudaFree(p.d_bupdates);
+  if (p.d_ritems) cudaFree(p.d_ritems);
+  if (p.d_rupdates) cudaFree(p.d_rupdates);
+  if (p.d_segsrc) cudaFree(p.d_segsrc);
+  p.d_ritems = nullptr;
+  p.d_rupdates = nullptr;
+  p.d_segsrc = nullptr;
   if (p.d_off) cudaFree(p.d_off);
   if (p.d_ptr) cudaFree(p.d_ptr);
   p.d_off = nullptr;
@@ -188,11 +194,13 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
   if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
   if (same_layout(hd->plan, off, C, ptr, S)) return SCAL3R_OK;
   Plan np;
-  int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S);
+  int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every);
   if (rc != SCAL3R_OK) return rc;
   if (upload(&np.d_items, np.items) != cudaSuccess || upload(&np.d_updates, np.updates) != cudaSuccess ||
       upload(&np.d_bitems, np.bitems) != cudaSuccess || upload(&np.d_bupdates, np.bupdates) != cudaSuccess ||
-      upload(&np.d_off, np.chunk_offsets) != cudaSuccess || upload(&np.d_ptr, np.seq_chunk_ptr) != cudaSuccess) {
+      upload(&np.d_off, np.chunk_offsets) != cudaSuccess || upload(&np.d_ptr, np.seq_chunk_ptr) != cudaSuccess ||
+      upload(&np.d_ritems, np.ritems) != cudaSuccess || upload(&np.d_rupdates, np.rupdates) != cudaSuccess ||
+      upload(&np.d_segsrc, np.segsrc) != cudaSuccess) {
     free_plan(np);
     return SCAL3R_ERR_CUDA;
   }
@@ -340,20 +348,50 @@ int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) 
   const int chains = pl.S * hd->shape.H;
   if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_bprep(prm, chains, st); }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
+  const bool bf = hd->cfg.dtype == SCAL3R_BF16;
+  const size_t wset = (size_t)chains * hd->shape.P();   // floats of one weight set of every chain
   for (size_t j = 0; j < pl.bsteps.size(); ++j) {
     const Step& s = pl.bsteps[j];
+    if (s.nrec > 0) {
+      // sparse checkpoints: W_{kn+1} .. W_{kn+nrec} into the recompute buffer,
+      // by the forward's own gradient pieces and updates from W_{kn}
+      const int k0 = s.rec0;
+      if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
+            return launch_loadw_seg(prm, chains, k0 & 1, pl.d_segsrc + (size_t)s.segk * pl.S, st);
+          }) != cudaSuccess)
+        return SCAL3R_ERR_CUDA;
+      for (int r = k0; r < k0 + s.nrec; ++r) {
+        const Step& rs = pl.rsteps[r];
+        Params pr = prm;
+        pr.w_ckpt = prm.wseg + (size_t)(r - k0) * wset;
+        pr.wnorm = nullptr;
+        pr.w_final = nullptr;
+        double fl = 0, by = 0;
+        if (hd->prof_on) sweep_work(hd, pl.ritems.data() + rs.item0, rs.nitems, fl, by);
+        if (rs.nitems > 0 && timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
+              return bf ? launch_bf16_sweep(pr, pl.d_ritems + rs.item0, rs.nitems, r, nullptr, st)
+                        : launch_fp32_sweep(pr, pl.d_ritems + rs.item0, rs.nitems, r, st);
+            }) != cudaSuccess)
+          return SCAL3R_ERR_CUDA;
+        if (rs.nupd > 0 && timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
+              return launch_update(pr, pl.d_rupdates + rs.upd0, rs.nupd, r, st);
+            }) != cudaSuccess)
+          return SCAL3R_ERR_CUDA;
+      }
+    }
+    Params pb = prm;   // the step's weights: checkpoints / w0, or the recompute buffer
+    if (s.wseg > 0) pb.w_ckpt_in = prm.wseg + (size_t)(s.wseg - 1) * wset;
     double fl = 0, by = 0;
     if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, s.nitems, fl, by);
     cudaError_t e = cudaSuccess;
     if (s.nitems > 0)
       e = timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fl, by, st, [&] {
-        return hd->cfg.dtype == SCAL3R_BF16
-                   ? launch_bf16_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
-                   : launch_fp32_bsweep(prm, pl.d_bitems + s.item0, s.nitems, (int)j, st);
+        return bf ? launch_bf16_bsweep(pb, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
+                  : launch_fp32_bsweep(pb, pl.d_bitems + s.item0, s.nitems, (int)j, st);
       });
     if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
     if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_BWD_UPDATE, 0, 0, st, [&] {
-          return launch_bupdate(prm, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
+          return launch_bupdate(pb, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
         }) != cudaSuccess)
       return SCAL3R_ERR_CUDA;
   }
@@ -427,7 +465,6 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (cfg->dtype == SCAL3R_BF16 && !wide &&
       (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
     return SCAL3R_ERR_UNSUPPORTED;
-  if (cfg->ckpt_every > 1 && !wide) return SCAL3R_ERR_UNSUPPORTED;   // sparse checkpoints: the wide path
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
   int major = 0, minor = 0, sms = 0;
@@ -592,7 +629,7 @@ static int backward_impl(scal3r_ttt_handle* hd, const void* q, const void* k, co
   const Plan& pl = hd->plan;
   const Shape& sh = hd->shape;
   if (pl.T > 0 && (!q || !k || !v || !lr || !d_o || !dq || !dk || !dv || !dlr)) return SCAL3R_ERR_INVALID_ARG;
-  if (pl.C > 0 && (!w_ckpt || !wnorm)) return SCAL3R_ERR_INVALID_ARG;
+  if (pl.C > 0 && (!wnorm || (!w_ckpt && pl.ckpt_slots > 0))) return SCAL3R_ERR_INVALID_ARG;
   if (!w0 || !dw0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;
   if (w0_seq_stride != 0 && w0_seq_stride < (int64_t)sh.H * sh.P()) return SCAL3R_ERR_INVALID_ARG;
   for (const void* p : {q, k, v, d_o, (const void*)dq, (const void*)dk, (const void*)dv, (const void*)w_ckpt,

@@ -147,7 +147,7 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
 }  // namespace
 
 int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
-               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S) {
+               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t ckpt_every) {
   if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
   if (off[0] != 0) return SCAL3R_ERR_INVALID_ARG;
   for (int32_t c = 0; c < C; ++c)
@@ -168,6 +168,21 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
   for (int32_t i = 0; i < S; ++i) maxn = std::max(maxn, ptr[i + 1] - ptr[i]);
   p.max_chunks = maxn;
   const int32_t H = s.H;
+  // checkpoints: with n = ckpt_every > 1 only the weights after local chunks
+  // n-1, 2n-1, ... are stored, sequence after sequence
+  const int32_t nck = ckpt_every > 1 ? ckpt_every : 1;
+  p.ckpt_every = nck;
+  std::vector<int64_t> cbase(S, 0);
+  for (int32_t q = 1; q < S; ++q) cbase[q] = cbase[q - 1] + (ptr[q] - ptr[q - 1]) / nck;
+  p.ckpt_slots = cbase[S - 1] + (ptr[S] - ptr[S - 1]) / nck;
+  // where the backward reads W_j of sequence q (j >= 1): its checkpoint, or
+  // (sparse, j not a multiple of n) the recompute buffer at the chain's row
+  auto wsrc = [&](int32_t q, int32_t j) -> int32_t {
+    if (j == 0) return -1;
+    if (nck == 1) return ptr[q] + j - 1;
+    if (j % nck == 0) return (int32_t)(cbase[q] + j / nck - 1);
+    return q;
+  };
 
   // ---- forward: steps j = 0 .. maxn --------------------------------------
   for (int32_t j = 0; j <= maxn; ++j) {
@@ -187,6 +202,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
           u.chunk = c;
           u.last = (j == n - 1);
           u.seq = q;
+          u.wslot = nck == 1 ? c : ((j + 1) % nck == 0 ? (int32_t)(cbase[q] + (j + 1) / nck - 1) : -1);
           upd.push_back(u);
         }
         if (j >= 1) {
@@ -199,6 +215,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
           u.chunk = -1;   // no chunk: w_final = w0
           u.last = 1;
           u.seq = q;
+          u.wslot = -1;
           upd.push_back(u);
         }
       }
@@ -218,11 +235,11 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
         if (j < n) {
           int32_t c = ptr[q] + j;
           tasks.push_back({chain, q, ROLE_BKEY, c, off[c], off[c + 1],
-                           (float)(off[c + 1] - off[c]) * sch.bkey_cost, j >= 1 ? c - 1 : -1});
+                           (float)(off[c + 1] - off[c]) * sch.bkey_cost, wsrc(q, j)});
         }
         if (j >= 1) {
           int32_t c = ptr[q] + j - 1;
-          tasks.push_back({chain, q, ROLE_BAPPLY, c, off[c], off[c + 1], (float)(off[c + 1] - off[c]), c});
+          tasks.push_back({chain, q, ROLE_BAPPLY, c, off[c], off[c + 1], (float)(off[c + 1] - off[c]), wsrc(q, j)});
         }
         UpdateItem u{};
         u.chain = chain;
@@ -230,11 +247,49 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
         u.last = (j == n);                           // no adjoint from a later chunk yet
         u.first = (j == 0);
         u.seq = q;
+        u.wslot = wsrc(q, j);
         upd.push_back(u);
       }
     }
     lay_out_step(tasks, sch, num_sms, sch.bwd_waves, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
     p.bscratch_tiles = std::max<int64_t>(p.bscratch_tiles, p.bsteps.back().scratch_tiles);
+    Step& bs = p.bsteps.back();
+    if (nck > 1 && j % nck != 0) {
+      bs.wseg = j % nck;
+      if (j == maxn || (j + 1) % nck == 0) {   // the segment's last step comes first: recompute it
+        bs.rec0 = j - j % nck;
+        bs.nrec = j % nck;
+        bs.segk = j / nck;
+      }
+    }
+  }
+
+  // ---- sparse checkpoints: forward steps to rerun, segment sources --------
+  if (nck > 1) {
+    for (int32_t j = 0; j < maxn; ++j) {
+      const Step& fs = p.steps[j];
+      Step rs{};
+      rs.item0 = (int32_t)p.ritems.size();
+      rs.upd0 = (int32_t)p.rupdates.size();
+      for (int32_t i = fs.item0; i < fs.item0 + fs.nitems; ++i)
+        if (p.items[i].role == ROLE_KEY) p.ritems.push_back(p.items[i]);
+      for (int32_t i = fs.upd0; i < fs.upd0 + fs.nupd; ++i) {
+        UpdateItem u = p.updates[i];
+        if (u.chunk < 0) continue;
+        u.wslot = u.seq;   // the recompute buffer's row of the chain
+        u.last = 0;
+        p.rupdates.push_back(u);
+      }
+      rs.nitems = (int32_t)p.ritems.size() - rs.item0;
+      rs.nupd = (int32_t)p.rupdates.size() - rs.upd0;
+      rs.nslots = fs.nslots;
+      p.rsteps.push_back(rs);
+    }
+    for (int32_t k = 0; k * nck <= maxn; ++k)
+      for (int32_t q = 0; q < S; ++q) {
+        const int32_t n = ptr[q + 1] - ptr[q];
+        p.segsrc.push_back(k * nck > n ? -2 : (k == 0 ? -1 : (int32_t)(cbase[q] + k - 1)));
+      }
   }
   p.valid = true;
   plan = std::move(p);
@@ -254,6 +309,7 @@ size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
     b += al(chains * s.R() * sizeof(float));                    // drho
     b += al(chains * s.P() * sizeof(float));                    // dw0 per chain
     b += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);   // BF16 backward scratch
+    if (p.ckpt_every > 1) b += al((size_t)(p.ckpt_every - 1) * chains * s.P() * sizeof(float));   // wseg
   }
   return b;
 }
@@ -279,7 +335,9 @@ void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws
     prm.scratch = (void*)(((uintptr_t)c + 1023) & ~(uintptr_t)1023);
     prm.scratch_tiles = p.bscratch_tiles;
     c += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);
+    prm.wseg = p.ckpt_every > 1 ? (float*)c : nullptr;
   } else {
+    prm.wseg = nullptr;
     prm.rbuf = prm.drho = prm.dw0_chain = nullptr;
     prm.scratch = nullptr;
     prm.scratch_tiles = 0;

@@ -41,7 +41,9 @@ struct UpdateItem {
   int32_t last;     // forward: 1 if chunk is the last of its sequence
   int32_t seq;
   int32_t first;    // backward: 1 if this closes chunk 0 (produces dW0)
-  int32_t pad;
+  int32_t wslot;    // forward: checkpoint slot the new weights go to (-1: none);
+                    // backward: index of the weights after `chunk` in the call's
+                    // weight source (checkpoints, or the recompute buffer by chain)
 };
 
 struct Step {
@@ -49,6 +51,11 @@ struct Step {
   int32_t upd0, nupd;     // updates after the sweep
   int32_t nslots;         // partial slots used in this step
   int32_t scratch_tiles;  // backward: 128-token scratch tiles of all pieces
+  // backward with sparse checkpoints (every n-th chunk stored):
+  int32_t wseg = 0;       // 0: the step's weights are checkpoints or w0; i > 0: recompute buffer i
+  int32_t rec0 = 0;       // before the step, rerun forward steps rec0 .. rec0 + nrec - 1
+  int32_t nrec = 0;       //   (their gradient pieces and updates) from the segment's first weights
+  int32_t segk = 0;       //   whose sources are row segk of the plan's segment table
 };
 
 struct Plan {
@@ -68,11 +75,22 @@ struct Plan {
   std::vector<Step> bsteps;
   int32_t bmax_slots = 0;
   int64_t bscratch_tiles = 0;   // max over backward steps of the 128-token tiles of all pieces
+  // sparse checkpoints (ckpt_every = n > 1): the backward recomputes W_j for j
+  // not a multiple of n from the segment's first weights W_{kn}
+  int32_t ckpt_every = 1;
+  int64_t ckpt_slots = 0;           // stored weight sets (C with a checkpoint per chunk)
+  std::vector<WorkItem> ritems;     // forward step j's gradient pieces (same slots)
+  std::vector<UpdateItem> rupdates; // forward step j's updates, wslot = sequence
+  std::vector<Step> rsteps;         // one per forward step j < max_chunks
+  std::vector<int32_t> segsrc;      // [segment][S]: checkpoint slot of W_{kn} (-1: w0; -2: not needed)
   // device copies (owned by the handle)
   WorkItem* d_items = nullptr;
   UpdateItem* d_updates = nullptr;
   WorkItem* d_bitems = nullptr;
   UpdateItem* d_bupdates = nullptr;
+  WorkItem* d_ritems = nullptr;
+  UpdateItem* d_rupdates = nullptr;
+  int32_t* d_segsrc = nullptr;
   int64_t* d_off = nullptr;     // chunk_offsets and seq_chunk_ptr (the linear model's kernels)
   int32_t* d_ptr = nullptr;
   bool valid = false;
@@ -132,6 +150,7 @@ struct Params {
   float* rbuf;      // backward: [chains][P] adjoint R of the next update
   float* drho;      // backward: [chains][R]
   float* dw0_chain; // backward: [chains][P] per-chain dW0 (shared w0 only)
+  float* wseg;      // backward, sparse checkpoints: [n-1][chains][P] recomputed weights
   void* scratch;    // backward, BF16 path: per-piece factors of the weight adjoints
   int64_t scratch_tiles;   // its size in 96 KB tiles
   int* status;      // handle-owned status word
@@ -147,7 +166,7 @@ size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward);
 void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws, Params& prm);
 int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
                const int64_t* chunk_offsets, int32_t num_chunks,
-               const int32_t* seq_chunk_ptr, int32_t num_seqs);
+               const int32_t* seq_chunk_ptr, int32_t num_seqs, int32_t ckpt_every = 1);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st);
@@ -156,6 +175,7 @@ cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, i
 cudaError_t launch_bfinal(const Params& prm, cudaStream_t st);
 cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, float* grad, cudaStream_t st);
 cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st);
+cudaError_t launch_loadw_seg(const Params& prm, int chains, int buf, const int32_t* src, cudaStream_t st);
 cudaError_t launch_gcs_update(const Params& prm, int chains, const float* w, int64_t w_stride, const float* g,
                               float* w_out, float* wnorm, cudaStream_t st);
 cudaError_t launch_fp32_sweep(const Params& prm, const WorkItem* items, int nitems, int step, cudaStream_t st);

@@ -128,7 +128,7 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
   if (p.norm != SCAL3R_NORM_NONE) scale = p.rho[(size_t)u.chain * R + s.r] / fmaxf(n, p.eps);
   const float4 w = scale4(x, scale);
   st4(wnext + s.off, w);
-  if (p.w_ckpt) st4(p.w_ckpt + ((size_t)u.chunk * p.H + h) * P + s.off, w);
+  if (p.w_ckpt && u.wslot >= 0) st4(p.w_ckpt + ((size_t)u.wslot * p.H + h) * P + s.off, w);
   if (p.w_final && u.last) st4(p.w_final + ((size_t)u.seq * p.H + h) * P + s.off, w);
   if (p.wnorm && s.c4 == 0) p.wnorm[((size_t)u.chunk * p.H + h) * R + s.r] = n;
 }
@@ -184,7 +184,7 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
   }
   const float inv_rho = rho > 0.f ? 1.f / rho : 0.f;
   float4 what = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (s.valid) what = scale4(ld4(p.w_ckpt_in + ((size_t)u.chunk * p.H + h) * P + s.off), inv_rho);
+  if (s.valid) what = scale4(ld4(p.w_ckpt_in + ((size_t)u.wslot * p.H + h) * P + s.off), inv_rho);
   const float proj = group_sum(dot4(what, lam), s.group);
   if (!s.valid) return;
   const float n = p.wnorm_in[((size_t)u.chunk * p.H + h) * R + s.r];
@@ -241,6 +241,19 @@ __global__ void loadw_kernel(Params p, int buf) {
   if (!s.valid) return;
   const int P = 3 * p.F * p.D;
   st4(p.wm + ((size_t)buf * p.S * p.H + chain) * P + s.off, ld4(chain_w0(p, chain) + s.off));
+}
+
+// Sparse checkpoints: the first weights of a backward segment into master
+// buffer `buf`, per chain from its sequence's checkpoint slot src[s] (-1: w0,
+// -2: the sequence has no step in the segment).
+__global__ void loadw_seg_kernel(Params p, int buf, const int32_t* __restrict__ src) {
+  const int chain = blockIdx.x;
+  const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
+  const int idx = src[chain / p.H];
+  if (!s.valid || idx == -2) return;
+  const int P = 3 * p.F * p.D;
+  const float* from = idx < 0 ? chain_w0(p, chain) : p.w_ckpt_in + ((size_t)idx * p.H + chain % p.H) * P;
+  st4(p.wm + ((size_t)buf * p.S * p.H + chain) * P + s.off, ld4(from + s.off));
 }
 
 // W_next = W - G with every row rescaled to its target (taken from w0, as in
@@ -311,6 +324,12 @@ cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, floa
 cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st) {
   if (chains == 0) return cudaSuccess;
   loadw_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm, buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loadw_seg(const Params& prm, int chains, int buf, const int32_t* src, cudaStream_t st) {
+  if (chains == 0) return cudaSuccess;
+  loadw_seg_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm, buf, src);
   return cudaGetLastError();
 }
 

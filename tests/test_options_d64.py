@@ -126,3 +126,76 @@ def test_per_matrix_rates_full_size_sampled_heads():
     errs, _ = _run("bf16", lay, 16, seed=85, lr=lr, heads=[4, 11], lr_per_matrix=True)
     print("per-matrix fwdbwd_2x32 errors", errs)
     _assert(errs, TOLS["bf16"])
+
+
+# ---- sparse checkpoints -----------------------------------------------------
+
+def _fwd_bwd(dtype_name, lay, H, seed, ckpt_every):
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
+    x = syn.make_inputs(lay.num_tokens, H, D, F, seed=seed, dtype=dtype_name, with_grad_out=True)
+    g = upload(x, dtype)
+    layer = ttt.TTT(H, D, F, dtype=dtype, ckpt_every=ckpt_every)
+    o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                                  want_final=True)
+    grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                           g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    return x, (o, ck, wn, wf), grads
+
+
+def _slots(lay, n):
+    """(global chunk index, slot) of every stored checkpoint with ckpt_every = n."""
+    out, slot = [], 0
+    for s in range(lay.num_seqs):
+        c0, c1 = int(lay.seq_chunk_ptr[s]), int(lay.seq_chunk_ptr[s + 1])
+        for i in range(c1 - c0):
+            if (i + 1) % n == 0:
+                out.append((c0 + i, slot))
+                slot += 1
+    return out
+
+
+@pytest.mark.parametrize("dtype_name,n", [("fp32", 2), ("fp32", 3), ("bf16", 2), ("bf16", 4)])
+def test_sparse_checkpoints_reproduce_dense_bitwise(dtype_name, n):
+    """ckpt_every = n stores the weights after local chunks n-1, 2n-1, ...;
+    the backward recomputes the others with the forward's own gradient
+    pieces and updates, so every output and gradient equals the run with a
+    checkpoint per chunk bit for bit.  Sequences of 5, 2, 3 and 1 chunks:
+    segments that end at a sequence's last chunk, sequences shorter than a
+    segment, a last step that is not a multiple of n."""
+    import torch
+    lay = syn.layout_from_lengths([[300, 129, 77, 200, 50], [130, 257], [100, 100, 100], [64]])
+    H = 2
+    x, (o1, ck1, wn1, wf1), g1 = _fwd_bwd(dtype_name, lay, H, 90, 1)
+    _, (o2, ck2, wn2, wf2), g2 = _fwd_bwd(dtype_name, lay, H, 90, n)
+    assert torch.equal(o1, o2) and torch.equal(wn1, wn2) and torch.equal(wf1, wf2)
+    pairs = _slots(lay, n)
+    assert ck2.shape[0] == len(pairs)
+    for c, slot in pairs:
+        assert torch.equal(ck2[slot], ck1[c])
+    for name, a, b in zip(("dq", "dk", "dv", "dlr", "dw0"), g1, g2):
+        assert torch.equal(a, b), name
+
+
+def test_sparse_checkpoints_full_size_fwdbwd():
+    """The forward+backward workload (2 sequences x 32 frames x 1041 tokens,
+    16 heads, chunk 8 frames: 4 chunks a sequence) with a checkpoint every
+    third chunk: bitwise the dense run, and the oracle on two whole heads."""
+    import torch
+    w = syn.workload("bf16_fwdbwd_2x32")
+    lay = w.layout()
+    x, (o1, _, _, _), g1 = _fwd_bwd("bf16", lay, 16, 91, 1)
+    _, (o3, ck3, _, _), g3 = _fwd_bwd("bf16", lay, 16, 91, 3)
+    assert ck3.shape[0] == len(_slots(lay, 3))
+    assert torch.equal(o1, o3)
+    for a, b in zip(g1, g3):
+        assert torch.equal(a, b)
+    hs = [2, 13]
+    xs = {n: x[n][:, hs] for n in ("q", "k", "v", "lr", "d_o")}
+    rb = oracle.backward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][hs], lay, xs["d_o"], D, F, eps=1e-6)
+    for name, t in zip(("dq", "dk", "dv", "dlr", "dw0"), g3):
+        a = to_np(t)
+        assert rel_inf(a[hs] if name == "dw0" else a[:, hs], rb[name]) <= TOLS["bf16"], name
