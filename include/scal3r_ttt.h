@@ -25,11 +25,13 @@
  * (the weights of a head stay on chip for a chunk); head_dim and hidden that
  * are multiples of 256 (the paper's own AMU: one head, hd 1024, hidden
  * 4 * hd, Supp. "Global Context Memory module") run every product of a chunk
- * step as a large tcgen05 GEMM, forward and backward.  The wide path also
- * takes the squared-error loss; the head_dim-64 path takes the dot loss, and
- * the autotuner is for it (SCAL3R_ERR_UNSUPPORTED otherwise).  Per-matrix
- * learning rates (lr_per_matrix) and sparse checkpoints (ckpt_every > 1) run
- * on every SwiGLU path.  The float32 path takes either loss.
+ * step as a large tcgen05 GEMM, forward and backward.  Both losses,
+ * per-matrix learning rates (lr_per_matrix) and sparse checkpoints
+ * (ckpt_every > 1) run on every SwiGLU path.  The head_dim-64 kernels take
+ * the squared-error loss by composition: residual pieces write
+ * r = v - f_W(k), the dot-loss gradient pieces take r as their values, and
+ * the backward adds the apply VJP over the keys with upstream -dr.  The
+ * autotuner is for the head_dim-64 path (SCAL3R_ERR_UNSUPPORTED otherwise).
  *
  * Conventions common to every entry point
  *  - T tokens, H heads, head dim D, hidden F, S sequences, C chunks.
@@ -105,7 +107,7 @@ typedef struct scal3r_ttt_config {
   int32_t hidden_dim;   /* F; BF16: 128 with D = 64, else a multiple of 256 up to 4096 (k * hd);
                            FP32: 32 or 128 */
   int32_t dtype;        /* SCAL3R_FP32 | SCAL3R_BF16 */
-  int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE (MSE: FP32 and wide-weight paths) */
+  int32_t loss;         /* SCAL3R_LOSS_DOT | SCAL3R_LOSS_MSE */
   int32_t weight_norm;  /* SCAL3R_NORM_ROW_W0 | SCAL3R_NORM_NONE | SCAL3R_NORM_UNIT */
   float   norm_eps;     /* clamp of the row norm; <= 0 selects 1e-6 */
   int32_t ckpt_every;   /* chunks between stored checkpoints: 0 or 1 = every chunk.  n > 1 (not

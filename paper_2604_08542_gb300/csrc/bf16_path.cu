@@ -186,6 +186,27 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     __syncwarp();
     if (lane == 0) mbar_arrive(&B.o_free[b]);
     const int64_t tok = t0 + (int64_t)i * QT + row;
+    if (tok < t1 && p.resid_v) {
+      // residual pieces: r = v - f_W(k), rounded once
+      const uint4* vv = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(p.resid_v) +
+                                                       ((size_t)tok * p.H + h) * D + 32 * half);
+      uint32_t vw[16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint4 x = vv[c];
+        vw[4 * c] = x.x;
+        vw[4 * c + 1] = x.y;
+        vw[4 * c + 2] = x.z;
+        vw[4 * c + 3] = x.w;
+      }
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        v0[2 * m] = bf16_lo(vw[m]) - v0[2 * m];
+        v0[2 * m + 1] = bf16_hi(vw[m]) - v0[2 * m + 1];
+        v1[2 * m] = bf16_lo(vw[8 + m]) - v1[2 * m];
+        v1[2 * m + 1] = bf16_hi(vw[8 + m]) - v1[2 * m + 1];
+      }
+    }
     if (tok < t1) {
       uint4* dst = reinterpret_cast<uint4*>(o + ((size_t)tok * p.H + h) * D + 32 * half);
       dst[0] = make_uint4(pack_bf16(v0[0], v0[1]), pack_bf16(v0[2], v0[3]), pack_bf16(v0[4], v0[5]), pack_bf16(v0[6], v0[7]));
@@ -257,7 +278,12 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const WorkItem it = items[blockIdx.x];
   const int chains = p.S * p.H;
-  const float* w = p.wm + ((size_t)(step & 1) * chains + it.chain) * 3 * F * D;
+  // the step's master weights, or (the backward's residual pieces) the weights
+  // the piece names, as the backward's pieces read them
+  const int hh = it.chain % p.H, ss = it.chain / p.H;
+  const float* w = !p.w_items ? p.wm + ((size_t)(step & 1) * chains + it.chain) * 3 * F * D
+                   : it.wchunk >= 0 ? p.w_ckpt_in + ((size_t)it.wchunk * p.H + hh) * 3 * F * D
+                                    : p.w0 + (size_t)ss * p.w0_seq_stride + (size_t)hh * 3 * F * D;
 
   if (threadIdx.x == 0) {
     tl::init_bars(TB);

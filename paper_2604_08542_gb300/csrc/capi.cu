@@ -159,6 +159,8 @@ void free_plan(Plan& p) {
   if (p.d_bitems) cudaFree(p.d_bitems);
   if (p.d_bupdates) cudaFree(p.d_bupdates);
   if (p.d_ritems) cudaFree(p.d_ritems);
+  if (p.d_yitems) cudaFree(p.d_yitems);
+  p.d_yitems = nullptr;
   if (p.d_rupdates) cudaFree(p.d_rupdates);
   if (p.d_segsrc) cudaFree(p.d_segsrc);
   p.d_ritems = nullptr;
@@ -194,13 +196,15 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
   if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
   if (same_layout(hd->plan, off, C, ptr, S)) return SCAL3R_OK;
   Plan np;
-  int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every);
+  const bool mse_compose = hd->cfg.dtype == SCAL3R_BF16 && !hd->wide && hd->cfg.loss == SCAL3R_LOSS_MSE;
+  int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every,
+                      mse_compose);
   if (rc != SCAL3R_OK) return rc;
   if (upload(&np.d_items, np.items) != cudaSuccess || upload(&np.d_updates, np.updates) != cudaSuccess ||
       upload(&np.d_bitems, np.bitems) != cudaSuccess || upload(&np.d_bupdates, np.bupdates) != cudaSuccess ||
       upload(&np.d_off, np.chunk_offsets) != cudaSuccess || upload(&np.d_ptr, np.seq_chunk_ptr) != cudaSuccess ||
       upload(&np.d_ritems, np.ritems) != cudaSuccess || upload(&np.d_rupdates, np.rupdates) != cudaSuccess ||
-      upload(&np.d_segsrc, np.segsrc) != cudaSuccess) {
+      upload(&np.d_segsrc, np.segsrc) != cudaSuccess || upload(&np.d_yitems, np.yitems) != cudaSuccess) {
     free_plan(np);
     return SCAL3R_ERR_CUDA;
   }
@@ -318,20 +322,51 @@ void fill_common(const scal3r_ttt_handle* hd, Params& prm) {
 }
 
 // The forward launch sequence on `st` (see the file comment).
+// Composed squared-error loss (BF16, head_dim 64): the residual pieces
+// r = v - f_W(k) into prm.rtok, at the step's master weights or (w_items) at
+// the weights each piece names.
+cudaError_t run_resid(scal3r_ttt_handle* hd, const Params& prm, const WorkItem* host_items, const WorkItem* items,
+                      int n, int step, bool w_items, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  Params py = prm;
+  py.q = prm.k;
+  py.o = prm.rtok;
+  py.resid_v = prm.v;
+  py.w_items = w_items ? 1 : 0;
+  double fl = 0, by = 0;
+  if (hd->prof_on) sweep_work(hd, host_items, n, fl, by);
+  return timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st,
+               [&] { return launch_bf16_sweep(py, items, n, step, nullptr, st); });
+}
+
 int enqueue_forward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) {
   const Plan& pl = hd->plan;
   const int chains = pl.S * hd->shape.H;
   if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
+  Params pk = prm;   // the gradient pieces see the residuals as their values
+  if (pl.mse_compose) {
+    pk.v = prm.rtok;
+    // a piece's last tile reads rows past its range (masked by a zero rate):
+    // they must hold finite values
+    if (cudaMemsetAsync(prm.rtok, 0, (size_t)pl.T * hd->shape.H * hd->shape.D * 2, st) != cudaSuccess)
+      return SCAL3R_ERR_CUDA;
+  }
   for (size_t j = 0; j < pl.steps.size(); ++j) {
     const Step& s = pl.steps[j];
+    if (pl.mse_compose) {
+      const Step& ys = pl.ysteps[j];
+      if (run_resid(hd, prm, pl.yitems.data() + ys.item0, pl.d_yitems + ys.item0, ys.nitems, (int)j, false, st) !=
+          cudaSuccess)
+        return SCAL3R_ERR_CUDA;
+    }
     double fl = 0, by = 0;
     if (hd->prof_on) sweep_work(hd, pl.items.data() + s.item0, s.nitems, fl, by);
     cudaError_t e = cudaSuccess;
     if (s.nitems > 0)
       e = timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
-        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st)
-                                            : launch_fp32_sweep(prm, pl.d_items + s.item0, s.nitems, (int)j, st);
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(pk, pl.d_items + s.item0, s.nitems, (int)j, nullptr, st)
+                                            : launch_fp32_sweep(pk, pl.d_items + s.item0, s.nitems, (int)j, st);
       });
     if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
     if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_FWD_UPDATE, 0, 0, st, [&] {
@@ -350,6 +385,9 @@ int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) 
     return SCAL3R_ERR_CUDA;
   const bool bf = hd->cfg.dtype == SCAL3R_BF16;
   const size_t wset = (size_t)chains * hd->shape.P();   // floats of one weight set of every chain
+  if (pl.mse_compose &&   // rows past a piece's range are read (and masked): keep them finite
+      cudaMemsetAsync(prm.rtok, 0, (size_t)pl.T * hd->shape.H * hd->shape.D * 2, st) != cudaSuccess)
+    return SCAL3R_ERR_CUDA;
   for (size_t j = 0; j < pl.bsteps.size(); ++j) {
     const Step& s = pl.bsteps[j];
     if (s.nrec > 0) {
@@ -366,6 +404,13 @@ int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) 
         pr.w_ckpt = prm.wseg + (size_t)(r - k0) * wset;
         pr.wnorm = nullptr;
         pr.w_final = nullptr;
+        if (pl.mse_compose) {
+          const Step& ys = pl.ysteps[r];
+          if (run_resid(hd, prm, pl.yitems.data() + ys.item0, pl.d_yitems + ys.item0, ys.nitems, r, false, st) !=
+              cudaSuccess)
+            return SCAL3R_ERR_CUDA;
+          pr.v = prm.rtok;
+        }
         double fl = 0, by = 0;
         if (hd->prof_on) sweep_work(hd, pl.ritems.data() + rs.item0, rs.nitems, fl, by);
         if (rs.nitems > 0 && timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
@@ -381,15 +426,41 @@ int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) 
     }
     Params pb = prm;   // the step's weights: checkpoints / w0, or the recompute buffer
     if (s.wseg > 0) pb.w_ckpt_in = prm.wseg + (size_t)(s.wseg - 1) * wset;
+    // composed squared-error loss: the update VJPs see r = v - f_W(k) as their
+    // values (their dv is dL/dr = dL/dv); then the apply VJP over the keys with
+    // upstream -dr adds its dk and its weight adjoint (the last npost pieces)
+    const int nmain = s.nitems - s.npost;
+    const WorkItem* post = pl.d_bitems + s.item0 + nmain;
+    Params pm = pb;
+    if (s.npost > 0) {
+      if (run_resid(hd, pb, pl.bitems.data() + s.item0 + nmain, post, s.npost, (int)j, true, st) != cudaSuccess)
+        return SCAL3R_ERR_CUDA;
+      pm.v = prm.rtok;
+    }
     double fl = 0, by = 0;
-    if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, s.nitems, fl, by);
+    if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0, nmain, fl, by);
     cudaError_t e = cudaSuccess;
-    if (s.nitems > 0)
+    if (nmain > 0)
       e = timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fl, by, st, [&] {
-        return bf ? launch_bf16_bsweep(pb, pl.d_bitems + s.item0, s.nitems, (int)j, nullptr, st)
-                  : launch_fp32_bsweep(pb, pl.d_bitems + s.item0, s.nitems, (int)j, st);
+        return bf ? launch_bf16_bsweep(pm, pl.d_bitems + s.item0, nmain, (int)j, nullptr, st)
+                  : launch_fp32_bsweep(pm, pl.d_bitems + s.item0, nmain, (int)j, st);
       });
     if (e != cudaSuccess) return SCAL3R_ERR_CUDA;
+    if (s.npost > 0) {
+      Params pp = pb;
+      pp.q = prm.k;
+      pp.d_o = prm.rtok;
+      pp.dq = prm.dk2;
+      double fp = 0, bp = 0;
+      if (hd->prof_on) sweep_work(hd, pl.bitems.data() + s.item0 + nmain, s.npost, fp, bp);
+      if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st,
+                [&] { return launch_tok_negate(pb, post, s.npost, prm.dv, prm.rtok, st); }) != cudaSuccess ||
+          timed(hd, SCAL3R_KERNEL_BWD_SWEEP, fp, bp, st,
+                [&] { return launch_bf16_bsweep(pp, post, s.npost, (int)j, nullptr, st); }) != cudaSuccess ||
+          timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st,
+                [&] { return launch_tok_add(pb, post, s.npost, prm.dk, prm.dk2, st); }) != cudaSuccess)
+        return SCAL3R_ERR_CUDA;
+    }
     if (s.nupd > 0 && timed(hd, SCAL3R_KERNEL_BWD_UPDATE, 0, 0, st, [&] {
           return launch_bupdate(pb, pl.d_bupdates + s.upd0, s.nupd, (int)j, st);
         }) != cudaSuccess)
@@ -461,9 +532,8 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   if (!lin && cfg->dtype == SCAL3R_FP32 && !fp32_shape_supported(cfg->head_dim, cfg->hidden_dim))
     return SCAL3R_ERR_UNSUPPORTED;
   const bool wide = cfg->dtype == SCAL3R_BF16 && wide_shape_supported(cfg->head_dim, cfg->hidden_dim);
-  // BF16: the D = 64, F = 128 path (dot loss) or the wide-weight path (both losses)
-  if (cfg->dtype == SCAL3R_BF16 && !wide &&
-      (!bf16_shape_supported(cfg->head_dim, cfg->hidden_dim) || cfg->loss != SCAL3R_LOSS_DOT))
+  // BF16: the D = 64, F = 128 path or the wide-weight path (both losses)
+  if (cfg->dtype == SCAL3R_BF16 && !wide && !bf16_shape_supported(cfg->head_dim, cfg->hidden_dim))
     return SCAL3R_ERR_UNSUPPORTED;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCAL3R_ERR_NO_DEVICE;
@@ -1094,11 +1164,20 @@ int scal3r_ttt_partial_grad(scal3r_ttt_handle* hd, const void* k, const void* v,
   if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] { return launch_prep(prm, chains, st); }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
   const Step& s0 = pl.steps[0];   // the gradient pieces of every sequence's chunk, at w
+  Params pk = prm;
+  if (pl.mse_compose) {   // residuals first; the gradient pieces see them as values
+    if (cudaMemsetAsync(prm.rtok, 0, (size_t)pl.T * sh.H * sh.D * 2, st) != cudaSuccess) return SCAL3R_ERR_CUDA;
+    const Step& ys = pl.ysteps[0];
+    if (run_resid(hd, prm, pl.yitems.data() + ys.item0, pl.d_yitems + ys.item0, ys.nitems, 0, false, st) !=
+        cudaSuccess)
+      return SCAL3R_ERR_CUDA;
+    pk.v = prm.rtok;
+  }
   double fl = 0, by = 0;
   if (hd->prof_on) sweep_work(hd, pl.items.data() + s0.item0, s0.nitems, fl, by);
   if (s0.nitems > 0 && timed(hd, SCAL3R_KERNEL_FWD_SWEEP, fl, by, st, [&] {
-        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(prm, pl.d_items + s0.item0, s0.nitems, 0, nullptr, st)
-                                            : launch_fp32_sweep(prm, pl.d_items + s0.item0, s0.nitems, 0, st);
+        return hd->cfg.dtype == SCAL3R_BF16 ? launch_bf16_sweep(pk, pl.d_items + s0.item0, s0.nitems, 0, nullptr, st)
+                                            : launch_fp32_sweep(pk, pl.d_items + s0.item0, s0.nitems, 0, st);
       }) != cudaSuccess)
     return SCAL3R_ERR_CUDA;
   if (timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st,

@@ -147,7 +147,8 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
 }  // namespace
 
 int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
-               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t ckpt_every) {
+               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t ckpt_every,
+               bool mse_compose) {
   if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
   if (off[0] != 0) return SCAL3R_ERR_INVALID_ARG;
   for (int32_t c = 0; c < C; ++c)
@@ -172,6 +173,7 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
   // n-1, 2n-1, ... are stored, sequence after sequence
   const int32_t nck = ckpt_every > 1 ? ckpt_every : 1;
   p.ckpt_every = nck;
+  p.mse_compose = mse_compose;
   std::vector<int64_t> cbase(S, 0);
   for (int32_t q = 1; q < S; ++q) cbase[q] = cbase[q - 1] + (ptr[q] - ptr[q - 1]) / nck;
   p.ckpt_slots = cbase[S - 1] + (ptr[S] - ptr[S - 1]) / nck;
@@ -221,6 +223,20 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
       }
     }
     lay_out_step(tasks, sch, num_sms, sch.fwd_waves, false, p.items, p.updates, p.steps, p.max_slots, upd);
+    if (mse_compose) {   // the residual pieces: the gradient pieces' ranges, as apply pieces
+      const Step& fs = p.steps.back();
+      Step ys{};
+      ys.item0 = (int32_t)p.yitems.size();
+      for (int32_t i = fs.item0; i < fs.item0 + fs.nitems; ++i)
+        if (p.items[i].role == ROLE_KEY) {
+          WorkItem y = p.items[i];
+          y.role = ROLE_APPLY;
+          y.slot = -1;
+          p.yitems.push_back(y);
+        }
+      ys.nitems = (int32_t)p.yitems.size() - ys.item0;
+      p.ysteps.push_back(ys);
+    }
   }
 
   // ---- backward: steps j = maxn .. 0 -------------------------------------
@@ -236,6 +252,9 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
           int32_t c = ptr[q] + j;
           tasks.push_back({chain, q, ROLE_BKEY, c, off[c], off[c + 1],
                            (float)(off[c + 1] - off[c]) * sch.bkey_cost, wsrc(q, j)});
+          if (mse_compose)
+            tasks.push_back({chain, q, ROLE_BAPPLY_K, c, off[c], off[c + 1], (float)(off[c + 1] - off[c]),
+                             wsrc(q, j)});
         }
         if (j >= 1) {
           int32_t c = ptr[q] + j - 1;
@@ -254,6 +273,12 @@ int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
     lay_out_step(tasks, sch, num_sms, sch.bwd_waves, true, p.bitems, p.bupdates, p.bsteps, p.bmax_slots, upd);
     p.bscratch_tiles = std::max<int64_t>(p.bscratch_tiles, p.bsteps.back().scratch_tiles);
     Step& bs = p.bsteps.back();
+    if (mse_compose) {   // the key-side apply VJPs last: they run after the update VJPs
+      auto first = p.bitems.begin() + bs.item0;
+      auto mid = std::stable_partition(first, first + bs.nitems,
+                                       [](const WorkItem& w) { return w.role != ROLE_BAPPLY_K; });
+      bs.npost = (int32_t)(first + bs.nitems - mid);
+    }
     if (nck > 1 && j % nck != 0) {
       bs.wseg = j % nck;
       if (j == maxn || (j + 1) % nck == 0) {   // the segment's last step comes first: recompute it
@@ -311,6 +336,10 @@ size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward) {
     b += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);   // BF16 backward scratch
     if (p.ckpt_every > 1) b += al((size_t)(p.ckpt_every - 1) * chains * s.P() * sizeof(float));   // wseg
   }
+  if (p.mse_compose) {   // residuals (and the backward's key-side dk), bf16 [T][H][D]
+    const size_t tok = al((size_t)p.T * s.H * s.D * 2);
+    b += tok * (with_backward ? 2 : 1);
+  }
   return b;
 }
 
@@ -336,11 +365,19 @@ void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws
     prm.scratch_tiles = p.bscratch_tiles;
     c += al((size_t)p.bscratch_tiles * kScratchTileBytes + 1024);
     prm.wseg = p.ckpt_every > 1 ? (float*)c : nullptr;
+    if (p.ckpt_every > 1) c += al((size_t)(p.ckpt_every - 1) * chains * s.P() * sizeof(float));
   } else {
     prm.wseg = nullptr;
     prm.rbuf = prm.drho = prm.dw0_chain = nullptr;
     prm.scratch = nullptr;
     prm.scratch_tiles = 0;
+  }
+  prm.rtok = prm.dk2 = nullptr;
+  if (p.mse_compose) {
+    const size_t tok = al((size_t)p.T * s.H * s.D * 2);
+    prm.rtok = (void*)c;
+    c += tok;
+    if (with_backward) prm.dk2 = (void*)c;
   }
 }
 

@@ -486,6 +486,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// The low / high bf16 of a packed pair as float (exact: bf16 is the top half
+// of a float32).
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
 // Byte offset of element (row, col) of a [rows][32] bf16 tile in the 64-byte
 // swizzled layout (tile base 512-byte aligned): the 16-byte chunk c of row r
 // sits at chunk position c ^ ((r >> 1) & 3).

@@ -18,6 +18,9 @@ enum Role : int32_t {
   ROLE_APPLY = 1,   // forward: o = f_{W_j}(q) for chunk j-1 (Eq. 4)
   ROLE_BKEY = 2,    // backward: VJP of chunk j's update at W_j
   ROLE_BAPPLY = 3,  // backward: VJP of chunk j-1's apply at W_j
+  ROLE_BAPPLY_K = 4,  // backward, squared-error loss by composition (BF16, head_dim 64): the apply
+                      // VJP over chunk j's keys at W_j with the upstream gradient -dr, where
+                      // r = v - f_W(k) is what the chunk's dot-loss gradient pieces saw as values
 };
 
 // One piece of a chunk step: a token range of one chain (sequence, head).
@@ -56,6 +59,8 @@ struct Step {
   int32_t rec0 = 0;       // before the step, rerun forward steps rec0 .. rec0 + nrec - 1
   int32_t nrec = 0;       //   (their gradient pieces and updates) from the segment's first weights
   int32_t segk = 0;       //   whose sources are row segk of the plan's segment table
+  int32_t npost = 0;      // backward, composed squared-error loss: the last npost pieces are
+                          // ROLE_BAPPLY_K, launched after the others
 };
 
 struct Plan {
@@ -83,12 +88,19 @@ struct Plan {
   std::vector<UpdateItem> rupdates; // forward step j's updates, wslot = sequence
   std::vector<Step> rsteps;         // one per forward step j < max_chunks
   std::vector<int32_t> segsrc;      // [segment][S]: checkpoint slot of W_{kn} (-1: w0; -2: not needed)
+  // composed squared-error loss (BF16, head_dim 64): per forward step, the
+  // residual pieces r = v - f_{W_j}(k) over chunk j (the gradient pieces'
+  // token ranges, as apply pieces)
+  bool mse_compose = false;
+  std::vector<WorkItem> yitems;
+  std::vector<Step> ysteps;
   // device copies (owned by the handle)
   WorkItem* d_items = nullptr;
   UpdateItem* d_updates = nullptr;
   WorkItem* d_bitems = nullptr;
   UpdateItem* d_bupdates = nullptr;
   WorkItem* d_ritems = nullptr;
+  WorkItem* d_yitems = nullptr;
   UpdateItem* d_rupdates = nullptr;
   int32_t* d_segsrc = nullptr;
   int64_t* d_off = nullptr;     // chunk_offsets and seq_chunk_ptr (the linear model's kernels)
@@ -151,6 +163,10 @@ struct Params {
   float* drho;      // backward: [chains][R]
   float* dw0_chain; // backward: [chains][P] per-chain dW0 (shared w0 only)
   float* wseg;      // backward, sparse checkpoints: [n-1][chains][P] recomputed weights
+  void* rtok;       // composed squared-error loss: [T][H][D] bf16 residuals r = v - f_W(k), then -dr
+  void* dk2;        //   backward: [T][H][D] bf16 dk of the apply VJP over the keys
+  const void* resid_v;   // apply pieces write v - f_W(x) instead of f_W(x) (values v)
+  int32_t w_items;  // 1: forward pieces read their weights as the backward does (wchunk)
   void* scratch;    // backward, BF16 path: per-piece factors of the weight adjoints
   int64_t scratch_tiles;   // its size in 96 KB tiles
   int* status;      // handle-owned status word
@@ -166,7 +182,8 @@ size_t workspace_bytes(const Plan& p, const Shape& s, bool with_backward);
 void carve_workspace(const Plan& p, const Shape& s, bool with_backward, void* ws, Params& prm);
 int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
                const int64_t* chunk_offsets, int32_t num_chunks,
-               const int32_t* seq_chunk_ptr, int32_t num_seqs, int32_t ckpt_every = 1);
+               const int32_t* seq_chunk_ptr, int32_t num_seqs, int32_t ckpt_every = 1,
+               bool mse_compose = false);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st);
@@ -175,6 +192,10 @@ cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, i
 cudaError_t launch_bfinal(const Params& prm, cudaStream_t st);
 cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, float* grad, cudaStream_t st);
 cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st);
+cudaError_t launch_tok_negate(const Params& prm, const WorkItem* items, int nitems, const void* src, void* dst,
+                              cudaStream_t st);
+cudaError_t launch_tok_add(const Params& prm, const WorkItem* items, int nitems, void* acc, const void* add,
+                           cudaStream_t st);
 cudaError_t launch_loadw_seg(const Params& prm, int chains, int buf, const int32_t* src, cudaStream_t st);
 cudaError_t launch_gcs_update(const Params& prm, int chains, const float* w, int64_t w_stride, const float* g,
                               float* w_out, float* wnorm, cudaStream_t st);

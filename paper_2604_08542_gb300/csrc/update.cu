@@ -10,6 +10,8 @@
 // row (a float4); a row's L2 norm is reduced over the D/4 (or F/4) lanes that
 // hold it with shuffles, in a fixed order.  Blocks along y cover the rows:
 // first the W1/W3 rows (1024/D per block), then the W2 rows (1024/F per block).
+#include <cuda_bf16.h>
+
 #include "ttt_internal.h"
 
 namespace scal3r {
@@ -243,6 +245,44 @@ __global__ void loadw_kernel(Params p, int buf) {
   st4(p.wm + ((size_t)buf * p.S * p.H + chain) * P + s.off, ld4(chain_w0(p, chain) + s.off));
 }
 
+// Token rows of the pieces' ranges (head of the piece's chain) of a bf16
+// [T][H][D] tensor, 16 bytes per thread step: dst = -src (sign flips, exact).
+__global__ void tok_negate_kernel(Params p, const WorkItem* __restrict__ items, const uint4* __restrict__ src,
+                                  uint4* __restrict__ dst) {
+  const WorkItem it = items[blockIdx.x];
+  const int h = it.chain % p.H, nc = p.D / 8;
+  const int64_t n = (it.t1 - it.t0) * nc;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const size_t o = (((size_t)(it.t0 + i / nc) * p.H + h) * p.D) / 8 + i % nc;
+    uint4 x = src[o];
+    x.x ^= 0x80008000u;
+    x.y ^= 0x80008000u;
+    x.z ^= 0x80008000u;
+    x.w ^= 0x80008000u;
+    dst[o] = x;
+  }
+}
+
+__device__ __forceinline__ uint32_t add_bf16x2(uint32_t a, uint32_t b) {
+  const float lo = __uint_as_float(a << 16) + __uint_as_float(b << 16);
+  const float hi = __uint_as_float(a & 0xFFFF0000u) + __uint_as_float(b & 0xFFFF0000u);
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// acc += add over the same rows (float32 sum, one rounding to bf16).
+__global__ void tok_add_kernel(Params p, const WorkItem* __restrict__ items, uint4* __restrict__ acc,
+                               const uint4* __restrict__ add) {
+  const WorkItem it = items[blockIdx.x];
+  const int h = it.chain % p.H, nc = p.D / 8;
+  const int64_t n = (it.t1 - it.t0) * nc;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const size_t o = (((size_t)(it.t0 + i / nc) * p.H + h) * p.D) / 8 + i % nc;
+    const uint4 a = acc[o], b = add[o];
+    acc[o] = make_uint4(add_bf16x2(a.x, b.x), add_bf16x2(a.y, b.y), add_bf16x2(a.z, b.z), add_bf16x2(a.w, b.w));
+  }
+}
+
 // Sparse checkpoints: the first weights of a backward segment into master
 // buffer `buf`, per chain from its sequence's checkpoint slot src[s] (-1: w0,
 // -2: the sequence has no step in the segment).
@@ -324,6 +364,20 @@ cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, floa
 cudaError_t launch_loadw(const Params& prm, int chains, int buf, cudaStream_t st) {
   if (chains == 0) return cudaSuccess;
   loadw_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm, buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tok_negate(const Params& prm, const WorkItem* items, int nitems, const void* src, void* dst,
+                              cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  tok_negate_kernel<<<nitems, kThreads, 0, st>>>(prm, items, static_cast<const uint4*>(src), static_cast<uint4*>(dst));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tok_add(const Params& prm, const WorkItem* items, int nitems, void* acc, const void* add,
+                           cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  tok_add_kernel<<<nitems, kThreads, 0, st>>>(prm, items, static_cast<uint4*>(acc), static_cast<const uint4*>(add));
   return cudaGetLastError();
 }
 

@@ -88,7 +88,6 @@ def test_bad_config_rejected_before_device_query(libpath):
         assert e.value.status == ttt.SCAL3R_ERR_INVALID_ARG
     for c in (ttt.scal3r_ttt_config(16, 32, 128, 1, 0, 0, 1e-6, 0),     # BF16 needs D=64, F=128 or wide
               ttt.scal3r_ttt_config(16, 48, 100, 0, 0, 0, 1e-6, 0),     # FP32 shape not built
-              ttt.scal3r_ttt_config(16, 64, 128, 1, 1, 0, 1e-6, 0),     # squared-error loss: wide path only (BF16)
               ttt.scal3r_ttt_config(4, 64, 64, 1, 0, 0, 1e-6, 0, 0, 1),  # linear model: float32 only
               ttt.scal3r_ttt_config(4, 64, 128, 0, 0, 0, 1e-6, 0, 0, 1),  # linear model: hidden_dim = head_dim
               ttt.scal3r_ttt_config(4, 64, 64, 0, 0, 0, 1e-6, 0, 1, 1)):  # linear model: one rate per token

@@ -166,7 +166,7 @@ def test_gcs_one_rank_is_the_forward():
 # GPU: the library's three calls
 # ---------------------------------------------------------------------------
 
-def _gpu_gcs(dtype, H, D, F, chunks, cuts, seed, per_matrix=False):
+def _gpu_gcs(dtype, H, D, F, chunks, cuts, seed, per_matrix=False, loss="dot"):
     """Two shards per chunk on one device, in the order of
     distributed.gcs_forward: returns (outputs of the loop, its weights after
     every chunk, the library's forward of the unsharded sequence (o, w_ckpt),
@@ -179,11 +179,13 @@ def _gpu_gcs(dtype, H, D, F, chunks, cuts, seed, per_matrix=False):
     x = syn.make_inputs(T, H, D, F, seed=seed, dtype="bf16" if dtype == torch.bfloat16 else "fp32")
     if per_matrix:
         x["lr"] = syn.per_matrix_lr(seed + 1, T, H, lr_max=0.1)
+    if loss == "mse":
+        x["lr"] = x["lr"] * 0.3
     g = upload(x, dtype)
-    layer = ttt.TTT(H, D, F, dtype=dtype, lr_per_matrix=per_matrix)
+    layer = ttt.TTT(H, D, F, dtype=dtype, lr_per_matrix=per_matrix, loss=loss)
     o_ref, ck_ref, _, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets,
                                         lay.seq_chunk_ptr)
-    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6)
+    ref = oracle.forward(x["q"], x["k"], x["v"], x["lr"], x["w0"], lay, D, F, eps=1e-6, loss=loss)
 
     def one_chunk(n):
         return syn.layout_from_lengths([[n]] if n > 0 else [[]])
@@ -238,6 +240,21 @@ def test_gpu_gcs_per_matrix_rates_equals_forward(dtype_name):
     import torch
     dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
     o, ck, o_ref, ck_ref, ref = _gpu_gcs(dtype, 2, 64, 128, [300, 129, 77], [137, 0, 40], 7, per_matrix=True)
+    tol = 1e-5 if dtype_name == "fp32" else 5e-3
+    assert rel_inf(o, o_ref) <= tol
+    assert rel_inf(ck, ck_ref) <= (tol if dtype_name == "fp32" else 1e-4)
+    assert rel_inf(o, ref["o"]) <= (1e-5 if dtype_name == "fp32" else 2e-2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype_name", ["fp32", "bf16"])
+def test_gpu_gcs_mse_equals_forward(dtype_name):
+    """The squared-error loss: each shard's partial gradient takes its own
+    residuals v - f_W(k) at the shared weights, so the split loop still
+    equals the unsharded forward."""
+    import torch
+    dtype = torch.bfloat16 if dtype_name == "bf16" else torch.float32
+    o, ck, o_ref, ck_ref, ref = _gpu_gcs(dtype, 2, 64, 128, [300, 129, 77], [137, 0, 40], 8, loss="mse")
     tol = 1e-5 if dtype_name == "fp32" else 5e-3
     assert rel_inf(o, o_ref) <= tol
     assert rel_inf(ck, ck_ref) <= (tol if dtype_name == "fp32" else 1e-4)

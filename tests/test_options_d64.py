@@ -199,3 +199,56 @@ def test_sparse_checkpoints_full_size_fwdbwd():
     for name, t in zip(("dq", "dk", "dv", "dlr", "dw0"), g3):
         a = to_np(t)
         assert rel_inf(a[hs] if name == "dw0" else a[:, hs], rb[name]) <= TOLS["bf16"], name
+
+
+# ---- squared-error loss on the fused bfloat16 path --------------------------
+
+@pytest.mark.parametrize("norm", ["row_w0", "none"])
+def test_mse_bf16_matches_oracle(norm):
+    """Eq. 9 with the squared-error loss (reading A10) on the fused kernels:
+    the residual pieces write r = v - f_W(k), the gradient pieces take r as
+    their values, and the backward adds the apply VJP over the keys with the
+    upstream gradient -dr.  Forward outputs and every gradient against the
+    oracle, ragged chunks with tile edges, two heads."""
+    lay = syn.layout_from_lengths([[300, 129], [77, 257, 1]])
+    x = syn.make_inputs(lay.num_tokens, 2, D, F, seed=92, dtype="bf16")
+    errs, _ = _run("bf16", lay, 2, seed=92, loss="mse", lr=x["lr"] * 0.3, norm=norm)
+    _assert(errs, TOLS["bf16"], f"mse/{norm}")
+
+
+def test_mse_bf16_with_per_matrix_rates():
+    lay = syn.layout_from_lengths([[200, 129], [64]])
+    lr = syn.per_matrix_lr(94, lay.num_tokens, 2, lr_max=0.03)
+    errs, _ = _run("bf16", lay, 2, seed=93, loss="mse", lr=lr, lr_per_matrix=True)
+    _assert(errs, TOLS["bf16"])
+
+
+def test_mse_bf16_sparse_checkpoints_reproduce_dense_bitwise():
+    import torch
+    import paper_2604_08542_gb300 as ttt
+    lay = syn.layout_from_lengths([[300, 129, 77, 200, 50], [130, 257]])
+    x = syn.make_inputs(lay.num_tokens, 2, D, F, seed=95, dtype="bf16", with_grad_out=True)
+    x["lr"] = x["lr"] * 0.3
+    g = upload(x, torch.bfloat16)
+    res = []
+    for n in (1, 2):
+        layer = ttt.TTT(2, D, F, dtype=torch.bfloat16, loss="mse", ckpt_every=n)
+        o, ck, wn, _ = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr)
+        grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+        torch.cuda.synchronize()
+        assert layer.status() == 0
+        res.append([o] + list(grads))
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
+
+
+def test_mse_bf16_full_size_sampled_heads():
+    """The forward+backward workload (2 x 32 frames x 1041 tokens, 16 heads)
+    with the squared-error loss; the oracle checks two whole heads."""
+    w = syn.workload("bf16_fwdbwd_2x32")
+    lay = w.layout()
+    x = syn.make_inputs(lay.num_tokens, 16, D, F, seed=96, dtype="bf16")
+    errs, _ = _run("bf16", lay, 16, seed=96, loss="mse", lr=x["lr"] * 0.3, heads=[1, 9])
+    print("mse fwdbwd_2x32 errors", errs)
+    _assert(errs, TOLS["bf16"])
