@@ -176,21 +176,27 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
     } else if (warp == 1) {
       // the whole warp runs the issue loop (uniform control flow); one
       // elected lane issues each MMA and commit
-      const uint32_t wq = smem_u32(sm + WQ_OFF), stg = smem_u32(sm + ST_OFF);
+      // descriptor halves: the loops add constant offsets to these bases
+      const uint32_t stg_lo = sdesc_lo(smem_u32(sm + ST_OFF), 16);      // staged factors, 64-byte swizzle
+      const uint32_t wq_lo16 = sdesc_lo(smem_u32(sm + WQ_OFF), 16);     // weights as B of G (K-major)
+      const uint32_t wq_lo1k = sdesc_lo(smem_u32(sm + WQ_OFF), 1024);   // weights as B of dk/dv (MN-major)
+      const uint32_t xy_lo = sdesc_lo(smem_u32(sm + XY_OFF), 16);
+      constexpr uint32_t HI128 = sdesc_hi(1024, kSwizzle128), HI64 = sdesc_hi(512, kSwizzle64);
       auto issue_acc = [&](int m) -> bool {
         const int i = m / NQ, q = m % NQ;
         if (!mbar_wait_spin_w(&B.st_full, m & 1, abort)) return false;
         if (q == 0 && !mbar_wait_spin_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
         tc_fence_after();
-        const uint32_t wb = wq + q * QBYTES;
+        const uint32_t wb = wq_lo1k + q * (QBYTES >> 4);
+        const uint32_t acc0 = q > 0 ? 1u : 0u;
 #pragma unroll
         for (int ks = 0; ks < KDX; ++ks)
-          mma_ss_w(tb + A_DX, sdesc_sw64(stg + (ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
-                   sdesc_sw128(wb + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+          mma_ss_h(tb + A_DX, stg_lo + (((ks / 2) * ST_TILE + (ks % 2) * 32) >> 4), HI64, wb + ((ks * 2048) >> 4),
+                   HI128, IDESC_ACC, ks > 0 ? 1u : acc0);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
-          mma_ss_w(tb + A_DY, sdesc_sw64(stg + (4 + ks / 2) * ST_TILE + (ks % 2) * 32, 16, 512),
-                   sdesc_sw128(wb + 16384 + ks * 2048, 1024, 1024), IDESC_ACC, (q > 0 || ks > 0) ? 1u : 0u);
+          mma_ss_h(tb + A_DY, stg_lo + (((4 + ks / 2) * ST_TILE + (ks % 2) * 32) >> 4), HI64,
+                   wb + ((16384 + ks * 2048) >> 4), HI128, IDESC_ACC, ks > 0 ? 1u : acc0);
         mma_commit_w(&B.st_free);
         if (q == NQ - 1) mma_commit_w(&B.acc_full);
         return true;
@@ -203,14 +209,13 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (q == 0 && !mbar_wait_spin_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
         if (!mbar_wait_spin_w(&B.g_free, (n & 1) ^ 1, abort)) break;
         tc_fence_after();
-        const uint32_t xs = smem_u32(sm + XY_OFF + (i & 1) * 32768);
-        const uint32_t wb = wq + q * QBYTES;
+        const uint32_t xs = xy_lo + (i & 1) * (32768 >> 4);
+        const uint32_t wb = wq_lo16 + q * (QBYTES >> 4);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
-          mma_ss_w(tb + A_BUF, sdesc_sw128(xs + ks * 32, 16, 1024), sdesc_sw128(wb + ks * 32, 16, 1024), IDESC_G1,
-                   ks > 0);
-          mma_ss_w(tb + A_BUF + 128, sdesc_sw128(xs + 16384 + ks * 32, 16, 1024),
-                   sdesc_sw128(wb + 16384 + ks * 32, 16, 1024), IDESC_G2, ks > 0);
+          mma_ss_h(tb + A_BUF, xs + ks * 2, HI128, wb + ks * 2, HI128, IDESC_G1, ks > 0);
+          mma_ss_h(tb + A_BUF + 128, xs + ((16384 >> 4) + ks * 2), HI128, wb + ((16384 >> 4) + ks * 2), HI128,
+                   IDESC_G2, ks > 0);
         }
         mma_commit_w(&B.g_full);
         if (n > ta * NQ) ok = issue_acc(n - 1);
@@ -224,7 +229,25 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           bulk_store(wq_image, sm + WQ_OFF, WQ_BYTES);
           bulk_commit();
         }
-        for (int n = ta * NQ; n < te * NQ; ++n) {
+        // dk / dv of tile i, staged over the tile's X/Y stage by the epilogue
+        // (after the next tile's first quarter, see there)
+        auto store_dkdv = [&](int i) -> bool {
+          if (!mbar_wait_spin(&B.out_full, i & 1, abort)) return false;
+          const int64_t tok = t0 + (int64_t)i * BT;
+          if (tok + BT <= t1) {
+            uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+            tma_store_3d(&maps.s_dk, xs, 0, h, (int32_t)tok);
+            tma_store_3d(&maps.s_dk, xs + 8192, 0, h, (int32_t)(tok + 64));
+            tma_store_3d(&maps.s_dv, xs + 16384, 0, h, (int32_t)tok);
+            tma_store_3d(&maps.s_dv, xs + 24576, 0, h, (int32_t)(tok + 64));
+            bulk_commit();
+            bulk_wait_read_all();
+          }
+          mbar_arrive(&B.xy_empty[i & 1]);
+          return true;
+        };
+        bool ok = true;
+        for (int n = ta * NQ; n < te * NQ && ok; ++n) {
           const int i = n / NQ, q = n % NQ;
           if (!mbar_wait_spin(&B.st_full, n & 1, abort)) break;
           const int32_t g = g0 + 4 * (i - ta);
@@ -234,22 +257,9 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           bulk_commit();
           bulk_wait_read_all();
           mbar_arrive(&B.stg_done);
-          if (q == NQ - 1) {
-            // dk / dv of the tile, staged over the tile's X/Y stage
-            if (!mbar_wait_spin(&B.out_full, i & 1, abort)) break;
-            const int64_t tok = t0 + (int64_t)i * BT;
-            if (tok + BT <= t1) {
-              uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
-              tma_store_3d(&maps.s_dk, xs, 0, h, (int32_t)tok);
-              tma_store_3d(&maps.s_dk, xs + 8192, 0, h, (int32_t)(tok + 64));
-              tma_store_3d(&maps.s_dv, xs + 16384, 0, h, (int32_t)tok);
-              tma_store_3d(&maps.s_dv, xs + 24576, 0, h, (int32_t)(tok + 64));
-              bulk_commit();
-              bulk_wait_read_all();
-            }
-            mbar_arrive(&B.xy_empty[i & 1]);
-          }
+          if (q == 0 && i > ta) ok = store_dkdv(i - 1);
         }
+        if (ok && !*abort) store_dkdv(te - 1);
         bulk_wait_all();   // scratch written before pass B reads it back
       }
       __syncwarp();
@@ -257,17 +267,70 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       // epilogue: thread = token row of the tile; half selects hidden units
       // [16*half, 16*half + 16) of every quarter.
       uint8_t* stg = sm + ST_OFF;
-      float eta[NR], deta[NR];
+      float eta[NR], deta[NR], dprev[NR];
 #pragma unroll
-      for (int j = 0; j < NR; ++j) eta[j] = deta[j] = 0.f;
-      for (int n = ta * NQ; n < te * NQ; ++n) {
-        const int i = n / NQ, q = n % NQ;
+      for (int j = 0; j < NR; ++j) eta[j] = deta[j] = dprev[j] = 0.f;
+      // Tile i finished: dk and dv out of TMEM into the tile's X/Y stage for
+      // the TMA store (rows of a partial tile are stored directly), and the
+      // dlr halves (dprev) combined.  Run after the next tile's first quarter
+      // is staged, so that the wait for the last products overlaps that
+      // quarter's chain rule instead of stalling the epilogue.
+      auto finish_tile = [&](int i) -> bool {
         const int64_t tok = t0 + (int64_t)i * BT + row;
         const bool valid = tok < t1;
+        if (!mbar_wait_spin(&B.acc_full, i & 1, abort)) return false;
+        tc_fence_after();
+        const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
+        uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          float v0[16], v1[16];
+          tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half, v0);
+          tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half + 16, v1);
+          if (full_tile) {
+            stage_row64(xs + m * 16384, row, half, v0, v1);
+          } else if (valid) {
+            store_row64(reinterpret_cast<__nv_bfloat16*>(m ? p.dv : p.dk) + ((size_t)tok * H + h) * D, half, v0,
+                        v1);
+          }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&B.acc_free);
+          mbar_arrive(&B.out_full);
+        }
+        // dlr of the token = sum of the two halves' partials (half 1 hands
+        // its partial to half 0 through shared memory)
+        const int e = i & 1;
+        float* eta_red = reinterpret_cast<float*>(sm + ETA_OFF) + e * 3 * BT;
+        if (half == 1) {
+          if (!mbar_wait_spin(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) return false;
+#pragma unroll
+          for (int j = 0; j < NR; ++j) eta_red[j * BT + row] = dprev[j];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&B.eta_full[e]);
+        } else {
+          if (!mbar_wait_spin(&B.eta_full[e], (i >> 1) & 1, abort)) return false;
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) p.dlr[((size_t)tok * H + h) * NR + j] = dprev[j] + eta_red[j * BT + row];
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&B.eta_free[e]);
+        }
+        return true;
+      };
+      bool ok = true;
+      for (int n = ta * NQ; n < te * NQ && ok; ++n) {
+        const int i = n / NQ, q = n % NQ;
+        const int64_t tok = t0 + (int64_t)i * BT + row;
         if (q == 0) {
           const int64_t tn = tok + BT;
 #pragma unroll
           for (int j = 0; j < NR; ++j) {
+            dprev[j] = deta[j];
             eta[j] = eta_next[j];
             deta[j] = 0.f;
             eta_next[j] = (i + 1 < ntiles && tn < t1) ? p.lr[((size_t)tn * H + h) * NR + j] : 0.f;
@@ -363,52 +426,12 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&B.st_full);
-        if (q == NQ - 1) {
-          // tile finished: dk and dv to shared memory for the TMA store
-          // (rows of a partial tile are stored directly), combine the dlr halves
-          if (!mbar_wait_spin(&B.acc_full, i & 1, abort)) break;
-          tc_fence_after();
-          const bool full_tile = (t0 + (int64_t)i * BT + BT) <= t1;
-          uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
+        if (q == 0 && i > ta) ok = finish_tile(i - 1);
+      }
+      if (ok && !*abort) {
 #pragma unroll
-          for (int m = 0; m < 2; ++m) {
-            float v0[16], v1[16];
-            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half, v0);
-            tmem_ld16(tb + lane_base + (m ? A_DY : A_DX) + 32 * half + 16, v1);
-            if (full_tile) {
-              stage_row64(xs + m * 16384, row, half, v0, v1);
-            } else if (valid) {
-              store_row64(reinterpret_cast<__nv_bfloat16*>(m ? p.dv : p.dk) + ((size_t)tok * H + h) * D, half, v0,
-                          v1);
-            }
-          }
-          fence_proxy_async_smem();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(&B.acc_free);
-            mbar_arrive(&B.out_full);
-          }
-          // dlr of the token = sum of the two halves' partials (half 1 hands
-          // its partial to half 0 through shared memory)
-          const int e = i & 1;
-          float* eta_red = reinterpret_cast<float*>(sm + ETA_OFF) + e * 3 * BT;
-          if (half == 1) {
-            if (!mbar_wait_spin(&B.eta_free[e], ((i >> 1) & 1) ^ 1, abort)) break;
-#pragma unroll
-            for (int j = 0; j < NR; ++j) eta_red[j * BT + row] = deta[j];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&B.eta_full[e]);
-          } else {
-            if (!mbar_wait_spin(&B.eta_full[e], (i >> 1) & 1, abort)) break;
-            if (valid) {
-#pragma unroll
-              for (int j = 0; j < NR; ++j) p.dlr[((size_t)tok * H + h) * NR + j] = deta[j] + eta_red[j * BT + row];
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&B.eta_free[e]);
-          }
-        }
+        for (int j = 0; j < NR; ++j) dprev[j] = deta[j];
+        finish_tile(te - 1);
       }
     }
     // pass A of the sub-piece done: its MMAs completed (the epilogue waited for
@@ -458,6 +481,9 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       __syncwarp();
     } else if (warp == 1) {
       bool ok = true;
+      const uint32_t pb_a = sdesc_lo(smem_u32(sm + PB_OFF), 2048);   // factors, MN-major, 64-byte swizzle
+      const uint32_t pb_b = sdesc_lo(smem_u32(sm + PB_OFF), 1024);   // X / Y, MN-major, 128-byte swizzle
+      constexpr uint32_t HI128 = sdesc_hi(1024, kSwizzle128), HI64 = sdesc_hi(512, kSwizzle64);
       for (int j = 0; j < nb; ++j) {
         const int s = (j + rot) % PB_STAGES;
         if (!mbar_wait_spin_w(&B.b_full[s], (pb_uses >> s) & 1, abort)) {
@@ -466,15 +492,15 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         }
         pb_uses ^= 1u << s;
         tc_fence_after();
-        const uint32_t st = smem_u32(sm + PB_OFF + s * PB_STAGE);
+        const uint32_t a = pb_a + s * (PB_STAGE >> 4), b = pb_b + s * (PB_STAGE >> 4);
+        const uint32_t acc0 = jb0 + j > 0 ? 1u : 0u;
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-          const uint32_t acc = (jb0 + j > 0 || ks > 0) ? 1u : 0u;
-          const uint64_t xd = sdesc_sw128(st + 24576 + ks * 2048, 1024, 1024);
-          const uint64_t yd = sdesc_sw128(st + 28672 + ks * 2048, 1024, 1024);
-          mma_ss_w(tb + B_L, sdesc_sw64(st + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-          mma_ss_w(tb + B_L + 64, sdesc_sw64(st + 8192 + ks * 1024, 2048, 512), xd, IDESC_LAM, acc);
-          mma_ss_w(tb + B_L + 128, sdesc_sw64(st + 16384 + ks * 1024, 2048, 512), yd, IDESC_LAM, acc);
+          const uint32_t acc = ks > 0 ? 1u : acc0;
+          const uint32_t xd = b + ((24576 + ks * 2048) >> 4), yd = b + ((28672 + ks * 2048) >> 4);
+          mma_ss_h(tb + B_L, a + ((ks * 1024) >> 4), HI64, xd, HI128, IDESC_LAM, acc);
+          mma_ss_h(tb + B_L + 64, a + ((8192 + ks * 1024) >> 4), HI64, xd, HI128, IDESC_LAM, acc);
+          mma_ss_h(tb + B_L + 128, a + ((16384 + ks * 1024) >> 4), HI64, yd, HI128, IDESC_LAM, acc);
         }
         mma_commit_w(&B.b_empty[s]);
       }

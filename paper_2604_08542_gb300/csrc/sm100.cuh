@@ -367,6 +367,33 @@ __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
+// The two 32-bit halves of a shared-memory descriptor.  lo = start address
+// >> 4 | LBO >> 4 << 16; hi = SBO >> 4 | the version bit | the swizzle mode
+// (2: 128-byte, 4: 64-byte).  The operand b bytes further on has lo + (b >> 4):
+// shared memory ends below 256 KB, so the 14-bit address field never carries
+// into LBO, and an MMA loop adds one constant per operand instead of
+// rebuilding a 64-bit descriptor.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t saddr, uint32_t lbo) {
+  return ((saddr & 0x3FFFFu) >> 4) | (((lbo >> 4) & 0x3FFFu) << 16);
+}
+__host__ __device__ constexpr uint32_t sdesc_hi(uint32_t sbo, uint32_t swizzle) {
+  return ((sbo >> 4) & 0x3FFFu) | (1u << 14) | (swizzle << 29);
+}
+constexpr uint32_t kSwizzle128 = 2, kSwizzle64 = 4;
+
+// D[tmem] (+)= A[smem] * B[smem] from descriptor halves, warp-collective like
+// mma_ss_w (one elected lane issues).
+__device__ __forceinline__ void mma_ss_h(uint32_t d_tmem, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo,
+                                         uint32_t b_hi, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred e, p;\n\t.reg .b64 da, db;\n\t"
+      "mov.b64 da, {%1, %2};\n\tmov.b64 db, {%3, %4};\n\t"
+      "elect.sync _|e, 0xffffffff;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // D[tmem] (+)= A[smem] * B[smem]
 __device__ __forceinline__ void mma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                        uint32_t accumulate) {
