@@ -301,7 +301,8 @@ typedef struct scal3r_ttt_schedule {
   int32_t fwd_waves;        /* forward: at most fwd_waves x SM count pieces per chunk step (1..8);
                                pieces are cut so that the costliest one is as cheap as possible */
   int32_t bwd_waves;        /* backward: same for the backward steps (1..8) */
-  int32_t min_piece_tokens; /* smallest piece, tokens (>= 128) */
+  int32_t min_piece_tokens; /* smallest piece, tokens (>= 128); the bfloat16 path.  The float32
+                               path cuts pieces on its 16-token tiles with no other minimum */
   float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0) */
   float   bwd_key_cost;     /* backward: cost of an update-VJP token vs an apply-VJP token (> 0) */
   int32_t reserved;         /* must be 0 */

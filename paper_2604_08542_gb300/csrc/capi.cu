@@ -197,7 +197,12 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
   if (same_layout(hd->plan, off, C, ptr, S)) return SCAL3R_OK;
   Plan np;
   const bool mse_compose = hd->cfg.dtype == SCAL3R_BF16 && !hd->wide && hd->cfg.loss == SCAL3R_LOSS_MSE;
-  int rc = build_plan(np, hd->shape, hd->sched, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every,
+  Schedule sch = hd->sched;
+  if (hd->cfg.dtype == SCAL3R_FP32) {   // the float32 kernels take 16-token tiles: short chunks spread over CTAs
+    sch.align = 16;
+    sch.min_tokens = 16;
+  }
+  int rc = build_plan(np, hd->shape, sch, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every,
                       mse_compose);
   if (rc != SCAL3R_OK) return rc;
   if (upload(&np.d_items, np.items) != cudaSuccess || upload(&np.d_updates, np.updates) != cudaSuccess ||

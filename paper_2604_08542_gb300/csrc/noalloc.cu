@@ -163,7 +163,12 @@ extern "C" int scal3r_ttt_forward_noalloc(const scal3r_ttt_config* cfg, const vo
   // schedule (host memory only)
   const Shape sh{cfg->num_heads, cfg->head_dim, cfg->hidden_dim};
   Plan pl;
-  int rc = build_plan(pl, sh, Schedule{}, sms, chunk_offsets, num_chunks, seq_chunk_ptr, num_seqs);
+  Schedule sch{};
+  if (cfg->dtype == SCAL3R_FP32) {   // as the handle's plan: 16-token pieces on the float32 path
+    sch.align = 16;
+    sch.min_tokens = 16;
+  }
+  int rc = build_plan(pl, sh, sch, sms, chunk_offsets, num_chunks, seq_chunk_ptr, num_seqs);
   if (rc != SCAL3R_OK) return rc;
   if (pl.T > 0 && (!q || !k || !v || !lr || !o)) return SCAL3R_ERR_INVALID_ARG;
   if (!w0 || w0_seq_stride < 0) return SCAL3R_ERR_INVALID_ARG;

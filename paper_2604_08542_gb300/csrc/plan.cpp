@@ -24,7 +24,6 @@ namespace scal3r {
 
 namespace {
 
-constexpr int64_t kAlign = 128;   // piece boundaries fall on 128-token tiles
 constexpr size_t kScratchTileBytes = 3 * 32 * 1024;   // BF16 backward: three 128x128 bf16 images per tile
 
 struct Task {
@@ -34,18 +33,18 @@ struct Task {
   int32_t wchunk;
 };
 
-// Cut [t0, t1) into n nearly equal pieces with boundaries on kAlign tokens
-// from t0.
-std::vector<std::pair<int64_t, int64_t>> split(int64_t t0, int64_t t1, int n) {
+// Cut [t0, t1) into n nearly equal pieces with boundaries on `align` tokens
+// from t0 (the kernels' token tile).
+std::vector<std::pair<int64_t, int64_t>> split(int64_t t0, int64_t t1, int n, int64_t align) {
   std::vector<std::pair<int64_t, int64_t>> out;
   int64_t len = t1 - t0;
-  int64_t tiles = (len + kAlign - 1) / kAlign;
+  int64_t tiles = (len + align - 1) / align;
   if (n > tiles) n = (int)std::max<int64_t>(1, tiles);
   int64_t base = tiles / n, extra = tiles % n;
   int64_t cur = t0;
   for (int i = 0; i < n; ++i) {
     int64_t nt = base + (i < extra ? 1 : 0);
-    int64_t end = std::min(t1, cur + nt * kAlign);
+    int64_t end = std::min(t1, cur + nt * align);
     if (i == n - 1) end = t1;
     out.push_back({cur, end});
     cur = end;
@@ -67,7 +66,7 @@ std::vector<int> pieces_per_task(const std::vector<Task>& tasks, const Schedule&
     const size_t i = heap.top().second;
     heap.pop();
     const int64_t len = tasks[i].t1 - tasks[i].t0;
-    const int64_t tiles = (len + kAlign - 1) / kAlign;
+    const int64_t tiles = (len + sch.align - 1) / sch.align;
     const int m = n[i] + 1;
     if (m > tiles || len / m < sch.min_tokens) continue;   // cannot be cut further
     n[i] = m;
@@ -100,7 +99,7 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
       if (t.chain != u.chain) continue;
       bool reduces = backward || t.role == ROLE_KEY;
       if (!reduces) continue;
-      for (auto& pr : split(t.t0, t.t1, npieces[ti])) {
+      for (auto& pr : split(t.t0, t.t1, npieces[ti], sch.align)) {
         WorkItem w{pr.first, pr.second, t.chain, t.role, slot++, t.seq, t.wchunk, 0};
         step_items.push_back(w);
         u.nslots++;
@@ -111,7 +110,7 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
     const Task& t = tasks[ti];
     bool reduces = backward || t.role == ROLE_KEY;
     if (reduces) continue;
-    for (auto& pr : split(t.t0, t.t1, npieces[ti])) {
+    for (auto& pr : split(t.t0, t.t1, npieces[ti], sch.align)) {
       WorkItem w{pr.first, pr.second, t.chain, t.role, -1, t.seq, t.wchunk, 0};
       step_items.push_back(w);
     }

@@ -120,6 +120,8 @@ struct Schedule {
   int32_t fwd_waves = 1;       // forward: target CTAs per step = fwd_waves * ctas_per_wave
   int32_t bwd_waves = 1;       // backward: same for the backward steps
   int32_t min_tokens = 256;    // smallest piece (tokens)
+  int32_t align = 128;         // piece boundaries: multiples of the kernels' token tile from the range start
+                               // (128 on the BF16 path; the float32 path's tiles are 16 tokens)
   float key_cost = 1.85f;      // forward: gradient token vs applied token (measured on GB300)
   float bkey_cost = 2.25f;     // backward: update-VJP token vs apply-VJP token (measured on GB300)
 };

@@ -15,27 +15,32 @@ using scal3r::Shape;
 
 extern "C" {
 
-// Build a plan.  sched = {ctas_per_wave, fwd_waves, bwd_waves, min_tokens},
-// costs = {key_cost, bkey_cost}.  Returns the plan (or null) and the
-// planner's status in *rc.
-void* ph_build(int32_t H, int32_t D, int32_t F, int32_t num_sms, const int32_t* sched, const float* costs,
-               const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t* rc) {
+// Build a plan.  sched = {ctas_per_wave, fwd_waves, bwd_waves, min_tokens,
+// align}, costs = {key_cost, bkey_cost}; ckpt_every and mse_compose as the
+// library passes them (sparse checkpoints; the composed squared-error loss of
+// the BF16 head_dim-64 path).  Returns the plan (or null) and the planner's
+// status in *rc.
+void* ph_build_opts(int32_t H, int32_t D, int32_t F, int32_t num_sms, const int32_t* sched, const float* costs,
+                    const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t ckpt_every,
+                    int32_t mse_compose, int32_t* rc) {
   Schedule sch;
   sch.ctas_per_wave = sched[0];
   sch.fwd_waves = sched[1];
   sch.bwd_waves = sched[2];
   sch.min_tokens = sched[3];
+  sch.align = sched[4];
   sch.key_cost = costs[0];
   sch.bkey_cost = costs[1];
   Shape s{H, D, F};
   Plan* p = new Plan();
-  *rc = scal3r::build_plan(*p, s, sch, num_sms, off, C, ptr, S);
+  *rc = scal3r::build_plan(*p, s, sch, num_sms, off, C, ptr, S, ckpt_every, mse_compose != 0);
   if (*rc != 0) {
     delete p;
     return nullptr;
   }
   return p;
 }
+
 
 void ph_free(void* p) { delete (Plan*)p; }
 
@@ -107,5 +112,69 @@ void ph_carve(const void* pv, int32_t H, int32_t D, int32_t F, int32_t backward,
 }
 
 int32_t ph_bwd_scratch_tiles_per_piece() { return scal3r::kBwdScratchTiles; }
+
+// out = {ritems, rupdates, rsteps, segsrc, yitems, ysteps, ckpt_slots, ckpt_every}
+void ph_counts2(const void* pv, int64_t* out) {
+  const Plan& p = *(const Plan*)pv;
+  out[0] = (int64_t)p.ritems.size();
+  out[1] = (int64_t)p.rupdates.size();
+  out[2] = (int64_t)p.rsteps.size();
+  out[3] = (int64_t)p.segsrc.size();
+  out[4] = (int64_t)p.yitems.size();
+  out[5] = (int64_t)p.ysteps.size();
+  out[6] = p.ckpt_slots;
+  out[7] = p.ckpt_every;
+}
+
+// 5 values per backward step: wseg, rec0, nrec, segk, npost
+void ph_bsteps2(const void* pv, int32_t* out) {
+  const Plan& p = *(const Plan*)pv;
+  for (size_t i = 0; i < p.bsteps.size(); ++i) {
+    const scal3r::Step& s = p.bsteps[i];
+    int32_t* o = out + 5 * i;
+    o[0] = s.wseg; o[1] = s.rec0; o[2] = s.nrec; o[3] = s.segk; o[4] = s.npost;
+  }
+}
+
+// The weight slot of every update (0: forward, 1: backward, 2: the recompute updates).
+void ph_wslots(const void* pv, int32_t which, int32_t* out) {
+  const Plan& p = *(const Plan*)pv;
+  const auto& v = which == 0 ? p.updates : which == 1 ? p.bupdates : p.rupdates;
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].wslot;
+}
+
+// The recompute and residual arrays: ritems and yitems as ph_items (8 values
+// each), rupdates as ph_updates (7), rsteps {item0, nitems, upd0, nupd, nslots},
+// ysteps {item0, nitems}, segsrc.
+void ph_rarrays(const void* pv, int64_t* ritems, int32_t* rupd, int32_t* rsteps, int32_t* segsrc, int64_t* yitems,
+                int32_t* ysteps) {
+  const Plan& p = *(const Plan*)pv;
+  auto items = [](const std::vector<scal3r::WorkItem>& v, int64_t* out) {
+    for (size_t i = 0; i < v.size(); ++i) {
+      const scal3r::WorkItem& w = v[i];
+      int64_t* o = out + 8 * i;
+      o[0] = w.t0; o[1] = w.t1; o[2] = w.chain; o[3] = w.role;
+      o[4] = w.slot; o[5] = w.seq; o[6] = w.wchunk; o[7] = w.aux;
+    }
+  };
+  items(p.ritems, ritems);
+  items(p.yitems, yitems);
+  for (size_t i = 0; i < p.rupdates.size(); ++i) {
+    const scal3r::UpdateItem& u = p.rupdates[i];
+    int32_t* o = rupd + 7 * i;
+    o[0] = u.chain; o[1] = u.chunk; o[2] = u.slot0; o[3] = u.nslots;
+    o[4] = u.last; o[5] = u.seq; o[6] = u.first;
+  }
+  for (size_t i = 0; i < p.rsteps.size(); ++i) {
+    const scal3r::Step& s = p.rsteps[i];
+    int32_t* o = rsteps + 5 * i;
+    o[0] = s.item0; o[1] = s.nitems; o[2] = s.upd0; o[3] = s.nupd; o[4] = s.nslots;
+  }
+  for (size_t i = 0; i < p.ysteps.size(); ++i) {
+    ysteps[2 * i] = p.ysteps[i].item0;
+    ysteps[2 * i + 1] = p.ysteps[i].nitems;
+  }
+  for (size_t i = 0; i < p.segsrc.size(); ++i) segsrc[i] = p.segsrc[i];
+}
 
 }  // extern "C"

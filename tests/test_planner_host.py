@@ -64,10 +64,15 @@ def lib(tmp_path_factory):
     assert r.returncode == 0, r.stderr
     L = ctypes.CDLL(out)
     P = ctypes.POINTER
-    L.ph_build.restype = ctypes.c_void_p
-    L.ph_build.argtypes = [ctypes.c_int32] * 4 + [P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_int64),
-                                                  ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32,
-                                                  P(ctypes.c_int32)]
+    L.ph_build_opts.restype = ctypes.c_void_p
+    L.ph_build_opts.argtypes = [ctypes.c_int32] * 4 + [P(ctypes.c_int32), P(ctypes.c_float), P(ctypes.c_int64),
+                                                       ctypes.c_int32, P(ctypes.c_int32), ctypes.c_int32,
+                                                       ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]
+    L.ph_counts2.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
+    L.ph_bsteps2.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
+    L.ph_wslots.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32)]
+    L.ph_rarrays.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32),
+                             P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_int32)]
     L.ph_free.argtypes = [ctypes.c_void_p]
     L.ph_counts.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
     L.ph_items.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64)]
@@ -88,18 +93,20 @@ class PlanView:
     """The plan read back into numpy arrays."""
 
     def __init__(self, lib, H, off, ptr, num_sms=152, ctas=0, fwd_waves=1, bwd_waves=1, min_tokens=256,
-                 key_cost=1.85, bkey_cost=2.25, D=64, F=128):
+                 key_cost=1.85, bkey_cost=2.25, D=64, F=128, align=ALIGN, ckpt_every=1, mse_compose=False):
         self.lib, self.H, self.D, self.F = lib, H, D, F
+        self.align, self.ckpt_every, self.mse_compose = align, ckpt_every, mse_compose
         self.off = np.ascontiguousarray(off, dtype=np.int64)
         self.ptr = np.ascontiguousarray(ptr, dtype=np.int32)
         self.sched = dict(num_sms=num_sms, ctas=ctas, fwd_waves=fwd_waves, bwd_waves=bwd_waves,
                           min_tokens=min_tokens, key_cost=np.float32(key_cost), bkey_cost=np.float32(bkey_cost))
-        sch = np.array([ctas, fwd_waves, bwd_waves, min_tokens], dtype=np.int32)
+        sch = np.array([ctas, fwd_waves, bwd_waves, min_tokens, align], dtype=np.int32)
         costs = np.array([key_cost, bkey_cost], dtype=np.float32)
         rc = ctypes.c_int32(-1)
-        self.h = lib.ph_build(H, D, F, num_sms, _ptr(sch, ctypes.c_int32), _ptr(costs, ctypes.c_float),
-                              _ptr(self.off, ctypes.c_int64), len(self.off) - 1, _ptr(self.ptr, ctypes.c_int32),
-                              len(self.ptr) - 1, ctypes.byref(rc))
+        self.h = lib.ph_build_opts(H, D, F, num_sms, _ptr(sch, ctypes.c_int32), _ptr(costs, ctypes.c_float),
+                                   _ptr(self.off, ctypes.c_int64), len(self.off) - 1,
+                                   _ptr(self.ptr, ctypes.c_int32), len(self.ptr) - 1, ckpt_every,
+                                   int(mse_compose), ctypes.byref(rc))
         self.rc = rc.value
         if not self.h:
             return
@@ -109,6 +116,30 @@ class PlanView:
          self.max_chunks) = (int(x) for x in cnt)
         self.items, self.updates, self.steps = self._read(0, n_it, n_up, n_st)
         self.bitems, self.bupdates, self.bsteps = self._read(1, n_bit, n_bup, n_bst)
+        c2 = np.zeros(8, dtype=np.int64)
+        lib.ph_counts2(self.h, _ptr(c2, ctypes.c_int64))
+        n_ri, n_ru, n_rs, n_seg, n_yi, n_ys, self.ckpt_slots, _ = (int(x) for x in c2)
+        self.bsteps2 = np.zeros((max(n_bst, 1), 5), dtype=np.int32)
+        if n_bst:
+            lib.ph_bsteps2(self.h, _ptr(self.bsteps2, ctypes.c_int32))
+        self.bsteps2 = self.bsteps2[:n_bst]
+        self.wslots = []
+        for which, n in ((0, n_up), (1, n_bup), (2, n_ru)):
+            w = np.zeros(max(n, 1), dtype=np.int32)
+            if n:
+                lib.ph_wslots(self.h, which, _ptr(w, ctypes.c_int32))
+            self.wslots.append(w[:n])
+        self.ritems = np.zeros((max(n_ri, 1), 8), dtype=np.int64)
+        self.rupdates = np.zeros((max(n_ru, 1), 7), dtype=np.int32)
+        self.rsteps = np.zeros((max(n_rs, 1), 5), dtype=np.int32)
+        self.segsrc = np.zeros(max(n_seg, 1), dtype=np.int32)
+        self.yitems = np.zeros((max(n_yi, 1), 8), dtype=np.int64)
+        self.ysteps = np.zeros((max(n_ys, 1), 2), dtype=np.int32)
+        lib.ph_rarrays(self.h, _ptr(self.ritems, ctypes.c_int64), _ptr(self.rupdates, ctypes.c_int32),
+                       _ptr(self.rsteps, ctypes.c_int32), _ptr(self.segsrc, ctypes.c_int32),
+                       _ptr(self.yitems, ctypes.c_int64), _ptr(self.ysteps, ctypes.c_int32))
+        self.ritems, self.rupdates, self.rsteps = self.ritems[:n_ri], self.rupdates[:n_ru], self.rsteps[:n_rs]
+        self.segsrc, self.yitems, self.ysteps = self.segsrc[:n_seg], self.yitems[:n_yi], self.ysteps[:n_ys]
 
     def _read(self, bwd, n_it, n_up, n_st):
         it = np.zeros((n_it, 8), dtype=np.int64)
@@ -221,7 +252,7 @@ def _check_plan(pv):
                 for a, b in zip(pcs[:-1], pcs[1:]):
                     assert a[1] == b[0]
                 for r in pcs:
-                    assert r[1] > r[0] and (r[0] - t0) % ALIGN == 0
+                    assert r[1] > r[0] and (r[0] - t0) % pv.align == 0
                     assert r[5] == chain // pv.H
                     if bwd:
                         assert r[6] == wchunk[(chain, role, c)]
@@ -317,7 +348,7 @@ def _check_minmax(pv):
             for (chain, role, c), pcs in groups.items():
                 length = int(pv.off[c + 1] - pv.off[c])
                 cost = float(np.float32(pv.cost(role, length)))
-                tiles = -(-length // ALIGN)
+                tiles = -(-length // pv.align)
                 cap = 1
                 while cap + 1 <= tiles and length // (cap + 1) >= mt:
                     cap += 1
@@ -384,7 +415,7 @@ def test_pieces_stop_at_the_tile_and_min_token_limits(lib):
                     for (_, _, c), pcs in _group_pieces(pv, pv.step_items(bwd, s)).items():
                         length = int(pv.off[c + 1] - pv.off[c])
                         m = len(pcs)
-                        tiles = -(-length // ALIGN)
+                        tiles = -(-length // pv.align)
                         assert m + 1 > tiles or length // (m + 1) < mt, (mt, length, m)
         finally:
             pv.close()
@@ -460,5 +491,153 @@ def test_workspace_regions_aligned_disjoint_and_sized(lib, H, D, F):
                 assert end <= total[bwd]
                 if i + 1 < len(regions):
                     assert end <= regions[i + 1][0]
+    finally:
+        pv.close()
+
+
+# ---- the float32 path's 16-token pieces ------------------------------------
+
+def test_float32_tiles_split_short_chunks(lib):
+    """The float32 kernels work in 16-token tiles, so their plan cuts on 16
+    tokens with no larger minimum: with CTAs free, a 128-token chunk becomes
+    eight pieces per role (the 8-chunk, 128-token workload)."""
+    lay = syn.layout_from_lengths([[128] * 8])
+    pv = PlanView(lib, 1, lay.chunk_offsets, lay.seq_chunk_ptr, align=16, min_tokens=16)
+    try:
+        _check_plan(pv)
+        for bwd in (0, 1):
+            for s in range(len(pv.bsteps if bwd else pv.steps)):
+                for pcs in _group_pieces(pv, pv.step_items(bwd, s)).values():
+                    assert len(pcs) == 8 and all(int(r[1] - r[0]) == 16 for r in pcs)
+    finally:
+        pv.close()
+
+
+# ---- sparse checkpoints ------------------------------------------------------
+
+SPARSE_LENS = [[300, 129, 77, 200, 50], [130, 257], [100, 100, 100], [64]]
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_sparse_checkpoint_plan(lib, n):
+    """ckpt_every = n: the forward writes the weights after local chunks
+    n-1, 2n-1, ... to consecutive slots, sequence after sequence; every
+    backward step reads W_j from its slot (j a multiple of n), w0 (j = 0) or
+    the recompute buffer at the sequence's row; the first backward step of a
+    segment reruns the forward steps that rebuild it, with the forward's own
+    pieces and partial slots."""
+    lay = syn.layout_from_lengths(SPARSE_LENS)
+    pv = PlanView(lib, 2, lay.chunk_offsets, lay.seq_chunk_ptr, ckpt_every=n)
+    try:
+        assert pv.rc == 0
+        nch = [len(x) for x in SPARSE_LENS]
+        base = np.concatenate([[0], np.cumsum([c // n for c in nch])])
+        assert pv.ckpt_slots == base[-1]
+        for u, w in zip(pv.updates, pv.wslots[0]):
+            chunk, q = int(u[1]), int(u[5])
+            if chunk < 0:
+                assert w == -1
+                continue
+            j = chunk - int(pv.ptr[q])
+            assert w == (base[q] + (j + 1) // n - 1 if (j + 1) % n == 0 else -1)
+        maxn = pv.max_chunks
+
+        def source(q, j):
+            return -1 if j == 0 else (q if j % n else base[q] + j // n - 1)
+
+        tops = []
+        for s in range(len(pv.bsteps)):
+            j = maxn - s
+            wseg, rec0, nrec, segk, npost = (int(x) for x in pv.bsteps2[s])
+            assert wseg == j % n and npost == 0
+            top = j % n != 0 and (j == maxn or (j + 1) % n == 0)
+            assert (nrec > 0) == top
+            if top:
+                assert rec0 == j - j % n and nrec == j % n and segk == j // n
+                tops.append(j)
+            for r in pv.step_items(1, s):
+                assert r[6] == source(int(r[5]), j)
+            st = pv.bsteps[s]
+            for u, w in zip(pv.bupdates[st[2]:st[2] + st[3]], pv.wslots[1][st[2]:st[2] + st[3]]):
+                if j >= 1:
+                    assert w == source(int(u[5]), j)
+        # every W_j read from the recompute buffer is rebuilt by its segment's first step
+        for j in range(1, maxn + 1):
+            if j % n:
+                assert any(t - t % n == j - j % n and t >= j for t in tops), j
+        assert len(pv.rsteps) == maxn
+        for j in range(maxn):
+            fi = np.array([r for r in pv.step_items(0, j) if r[3] == KEY]).reshape(-1, 8)
+            rs = pv.rsteps[j]
+            assert np.array_equal(pv.ritems[rs[0]:rs[0] + rs[1]], fi)
+            assert rs[4] == pv.steps[j][4]
+            fu = [u for u in pv.step_updates(0, j) if u[1] >= 0]
+            ru = pv.rupdates[rs[2]:rs[2] + rs[3]]
+            assert len(fu) == len(ru)
+            for a, b, w in zip(fu, ru, pv.wslots[2][rs[2]:rs[2] + rs[3]]):
+                assert tuple(a[:4]) == tuple(b[:4]) and b[4] == 0 and w == b[5]
+        nseg = maxn // n + 1
+        assert len(pv.segsrc) == nseg * pv.S
+        for k in range(nseg):
+            for q in range(pv.S):
+                want = -2 if k * n > nch[q] else (-1 if k == 0 else base[q] + k - 1)
+                assert pv.segsrc[k * pv.S + q] == want
+    finally:
+        pv.close()
+
+
+def test_dense_checkpoints_plan_no_recompute(lib):
+    lay = syn.layout_from_lengths(SPARSE_LENS)
+    pv = PlanView(lib, 2, lay.chunk_offsets, lay.seq_chunk_ptr)
+    try:
+        _check_plan(pv)
+        assert pv.ckpt_slots == len(pv.off) - 1
+        assert (pv.bsteps2 == 0).all() and len(pv.rsteps) == 0 and len(pv.segsrc) == 0
+        for u, w in zip(pv.updates, pv.wslots[0]):
+            assert w == u[1]
+    finally:
+        pv.close()
+
+
+# ---- the composed squared-error loss (BF16, head_dim 64) -------------------
+
+def test_composed_mse_plan(lib):
+    """Forward: each step's residual pieces are its gradient pieces as apply
+    pieces.  Backward: the last npost pieces of a step are the key-side apply
+    VJPs; they cover the same tokens as the step's update VJPs, read the same
+    weights, and reduce into their chain's slots like every other piece."""
+    lay = syn.layout_from_lengths([[300, 129, 77], [130, 257], [64]])
+    H = 2
+    pv = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, mse_compose=True)
+    try:
+        assert pv.rc == 0
+        maxn = pv.max_chunks
+        assert len(pv.ysteps) == maxn + 1
+        for j in range(maxn + 1):
+            fi = [r for r in pv.step_items(0, j) if r[3] == KEY]
+            ys = pv.ysteps[j]
+            yi = pv.yitems[ys[0]:ys[0] + ys[1]]
+            assert len(yi) == len(fi)
+            for a, b in zip(fi, yi):
+                assert tuple(a[:3]) == tuple(b[:3]) and b[3] == APPLY and b[4] == -1 and b[5] == a[5]
+
+        def cover(rows):
+            return {(int(r[2]), t) for r in rows for t in range(int(r[0]), int(r[1]))}
+
+        for s in range(len(pv.bsteps)):
+            items = pv.step_items(1, s)
+            npost = int(pv.bsteps2[s][4])
+            main, post = items[:len(items) - npost], items[len(items) - npost:]
+            assert (post[:, 3] == 4).all() and (main[:, 3] != 4).all()
+            bkey = main[main[:, 3] == BKEY]
+            assert cover(bkey) == cover(post)
+            w = {int(r[2]): int(r[6]) for r in bkey}
+            assert all(w[int(r[2])] == r[6] for r in post)
+            ups = pv.step_updates(1, s)
+            rng = {int(u[0]): (int(u[2]), int(u[2]) + int(u[3])) for u in ups}
+            for r in items:
+                a, b = rng[int(r[2])]
+                assert a <= r[4] < b
+            assert sorted(int(r[4]) for r in items) == list(range(int(pv.bsteps[s][4])))
     finally:
         pv.close()
