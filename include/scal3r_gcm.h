@@ -11,12 +11,21 @@
  *                                                      the predictor's form is a reading)
  *     o  = TTT layer (scal3r_ttt.h) on q, k, v, lr
  *     out = alpha o (o Wo^T) + x                      (gated residual, Eq. 5)
- * The caller runs the two projections with scal3r_ttt_gemm, the TTT layer with
- * scal3r_ttt_forward / _backward, and the row steps below, all on one stream.
+ * The caller runs, on one stream: scal3r_gcm_qkv, the TTT layer
+ * (scal3r_ttt_forward), scal3r_gcm_out; backward scal3r_gcm_out_backward, the
+ * layer's scal3r_ttt_backward, scal3r_gcm_qkv_backward.  Each projection is
+ * one tcgen05 GEMM whose epilogue does the row work (bias, the sums of squares
+ * for the per-head norms, the gate and residual), so no float32 [T, 3d] or
+ * [T, d] plane exists; the small row steps left (the per-head rescale with the
+ * learning-rate predictor, their backward, column sums) are 16-byte-wide
+ * kernels.
  *
  * Conventions: as in scal3r_ttt.h.  x, out, q, k, v, the bf16 gradients:
  * token-major, 16-byte aligned device memory.  The handle gives H and D (its
- * head_dim); H <= 16.  Every entry point returns SCAL3R_OK or an error code.
+ * head_dim); a bfloat16 handle with H <= 16 and d = H * D a multiple of 256
+ * (SCAL3R_ERR_UNSUPPORTED otherwise).  Parameters: wqkv [3d, d] and wo [d, d]
+ * bf16 (y = x W^T), bqkv [3d], w_eta [H, d], b_eta [H], alpha [d] float32.
+ * Every entry point returns SCAL3R_OK or an error code.
  */
 #ifndef SCAL3R_GCM_H
 #define SCAL3R_GCM_H
@@ -65,42 +74,51 @@ int scal3r_ttt_gemm_timeout_test(scal3r_ttt_handle* handle, int32_t enable);
 int scal3r_ttt_gemm_workspace_size(scal3r_ttt_handle* handle, int64_t M, int64_t N, int64_t K, int32_t out_fp32,
                                    size_t* bytes);
 
-/* Bytes of device scratch the two backward row steps need for T tokens. */
+/* Bytes of device scratch (16-byte aligned, caller-owned) that each of the
+ * four calls below needs for T tokens; one buffer serves all four. */
 int scal3r_gcm_workspace_size(scal3r_ttt_handle* handle, int64_t T, size_t* bytes);
 
-/* Forward row steps after the projection.
- *   qkv_raw [T, 3d] float32 (x Wqkv^T), bqkv [3d], x [T, d] bf16,
- *   w_eta [H, d] and b_eta [H] float32, base_lr > 0.
- * Writes q, k, v [T, H, D] bf16 (q and k unit-norm per head), lr [T, H], and
- * for the backward qn, kn [T, H] (the norms before scaling) and sig [T, H]
- * (the predictor's sigmoid). */
-int scal3r_gcm_prep(scal3r_ttt_handle* handle, const float* qkv_raw, const float* bqkv, const void* x,
-                    const float* w_eta, const float* b_eta, float base_lr, int64_t T, void* q, void* k, void* v,
-                    float* lr, float* qn, float* kn, float* sig, void* stream);
+/* [q | k | v] = x Wqkv^T + bqkv, q and k scaled to unit L2 norm per head,
+ * lr = base_lr * sigmoid(x w_eta^T + b_eta).
+ *   x [T, d] bf16; base_lr > 0.
+ * Writes q, k, v [T, H, D] bf16, lr [T, H], and for the backward qn, kn
+ * [T, H] (the norms before scaling, from the float32 projection) and sig
+ * [T, H] (the predictor's sigmoid).  The projection's epilogue writes bf16
+ * q, k, v and per-64-column sums of squares; a row kernel then scales q and k
+ * (so they are rounded to bf16 twice) and evaluates the predictor. */
+int scal3r_gcm_qkv(scal3r_ttt_handle* handle, const void* x, const void* wqkv, const float* bqkv, const float* w_eta,
+                   const float* b_eta, float base_lr, int64_t T, void* q, void* k, void* v, float* lr, float* qn,
+                   float* kn, float* sig, void* workspace, size_t workspace_bytes, void* stream);
 
-/* out = alpha o y + x (Eq. 5): y [T, d] float32 (o Wo^T), x [T, d] bf16,
- * alpha [d]; out [T, d] bf16. */
-int scal3r_gcm_gate(scal3r_ttt_handle* handle, const float* y, const void* x, const float* alpha, int64_t T,
-                    void* out, void* stream);
+/* out = alpha o (o Wo^T) + x (Eq. 5) in the epilogue of the output product.
+ *   o [T, d] bf16 (the layer's output), x [T, d] bf16.
+ * Writes out [T, d] bf16 and y = o Wo^T [T, d] bf16 (kept for dalpha). */
+int scal3r_gcm_out(scal3r_ttt_handle* handle, const void* o, const void* wo, const void* x, const float* alpha,
+                   int64_t T, void* out, void* y, void* stream);
 
-/* Backward of the gate: d_out [T, d] bf16 -> dy = alpha o d_out [T, d] bf16,
- * dx = d_out [T, d] float32 (the residual path; later GEMMs add to it), and
- * dalpha [d] = sum over tokens of y o d_out (fixed order). */
-int scal3r_gcm_gate_backward(scal3r_ttt_handle* handle, const void* d_out, const float* y, const float* alpha,
-                             int64_t T, void* dy, float* dx, float* dalpha, void* workspace, size_t workspace_bytes,
-                             void* stream);
+/* Backward of scal3r_gcm_out for d_out [T, d] bf16 (o, wo, y, alpha of the
+ * forward).  The gate is folded into the weights, so no gated copy of d_out
+ * is formed:  d_o = d_out diag(alpha) Wo  [T, d] bf16 (the layer's upstream
+ * gradient),  dwo = diag(alpha) d_out^T o  [d, d] float32,  dalpha [d] = the
+ * sums over tokens of y o d_out (fixed order).  The residual's gradient
+ * (d_out itself) is added to dx by scal3r_gcm_qkv_backward. */
+int scal3r_gcm_out_backward(scal3r_ttt_handle* handle, const void* d_out, const void* o, const void* wo, const void* y,
+                            const float* alpha, int64_t T, void* d_o, float* dwo, float* dalpha, void* workspace,
+                            size_t workspace_bytes, void* stream);
 
-/* Backward of the row steps after the projection: from the TTT layer's dq,
- * dk, dv [T, H, D] bf16 and dlr [T, H], with q, k, qn, kn, sig of the forward:
- *   dqkv [T, 3d] bf16 (the gradient of qkv_raw; bias gradient dbqkv [3d]),
- *   dlogit [T, 64] bf16 (the predictor's pre-sigmoid gradient, columns >= H
- *   zero; d b_eta [H] = its column sums).
- * The remaining gradients are GEMMs: dx += dqkv Wqkv, dWqkv = dqkv^T x,
- * dx += dlogit w_eta (w_eta zero-padded to [64, d]), dw_eta = dlogit^T x. */
-int scal3r_gcm_prep_backward(scal3r_ttt_handle* handle, const void* dq, const void* dk, const void* dv,
-                             const float* dlr, const void* q, const void* k, const float* qn, const float* kn,
-                             const float* sig, float base_lr, int64_t T, void* dqkv, void* dlogit, float* dbqkv,
-                             float* db_eta, void* workspace, size_t workspace_bytes, void* stream);
+/* Backward of scal3r_gcm_qkv and the residual: from the layer's dq, dk, dv
+ * [T, H, D] bf16 and dlr [T, H], with q, k, qn, kn, sig of the forward, x,
+ * wqkv, w_eta, and d_out (the module's upstream gradient):
+ *   dx [T, d] float32 = d_out + dqkv Wqkv + dlogit w_eta (one GEMM over the
+ *     concatenated 3d + 64 columns; the residual added in its epilogue),
+ *   dwqkv [3d, d], dbqkv [3d], dw_eta [H, d], db_eta [H] float32,
+ * where dqkv is the gradient of the projection before the rescale and dlogit
+ * the predictor's pre-sigmoid gradient (column sums in a fixed order). */
+int scal3r_gcm_qkv_backward(scal3r_ttt_handle* handle, const void* dq, const void* dk, const void* dv,
+                            const float* dlr, const void* q, const void* k, const float* qn, const float* kn,
+                            const float* sig, float base_lr, const void* x, const void* wqkv, const float* w_eta,
+                            const void* d_out, int64_t T, float* dx, float* dwqkv, float* dbqkv, float* dw_eta,
+                            float* db_eta, void* workspace, size_t workspace_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,7 @@ EXPORTED = ("scal3r_ttt_init", "scal3r_ttt_destroy", "scal3r_ttt_error_string", 
             "scal3r_ttt_autotune", "scal3r_ttt_profile_enable", "scal3r_ttt_profile_read",
             "scal3r_ttt_get_status", "scal3r_ttt_forward_noalloc", "scal3r_ttt_noalloc_status", "scal3r_ttt_partial_grad",
             "scal3r_ttt_apply_update", "scal3r_ttt_apply", "scal3r_ttt_ckpt_slots", "scal3r_ttt_gemm", "scal3r_ttt_gemm_workspace_size", "scal3r_ttt_gemm_timeout_test", "scal3r_ttt_set_finite_check", "scal3r_ttt_debug_bounds", "scal3r_gcm_workspace_size",
-            "scal3r_gcm_prep", "scal3r_gcm_gate", "scal3r_gcm_gate_backward", "scal3r_gcm_prep_backward")
+            "scal3r_gcm_qkv", "scal3r_gcm_out", "scal3r_gcm_out_backward", "scal3r_gcm_qkv_backward")
 
 
 class scal3r_ttt_config(ctypes.Structure):
@@ -160,15 +160,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.scal3r_ttt_gemm_workspace_size.restype = ctypes.c_int
     lib.scal3r_gcm_workspace_size.argtypes = [vp, i64, ctypes.POINTER(sz)]
     lib.scal3r_gcm_workspace_size.restype = ctypes.c_int
-    lib.scal3r_gcm_prep.argtypes = [vp, vp, vp, vp, vp, vp, f32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
-    lib.scal3r_gcm_prep.restype = ctypes.c_int
-    lib.scal3r_gcm_gate.argtypes = [vp, vp, vp, vp, i64, vp, vp]
-    lib.scal3r_gcm_gate.restype = ctypes.c_int
-    lib.scal3r_gcm_gate_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
-    lib.scal3r_gcm_gate_backward.restype = ctypes.c_int
-    lib.scal3r_gcm_prep_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, i64, vp, vp, vp, vp, vp,
-                                             sz, vp]
-    lib.scal3r_gcm_prep_backward.restype = ctypes.c_int
+    lib.scal3r_gcm_qkv.argtypes = [vp, vp, vp, vp, vp, vp, f32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    lib.scal3r_gcm_qkv.restype = ctypes.c_int
+    lib.scal3r_gcm_out.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp]
+    lib.scal3r_gcm_out.restype = ctypes.c_int
+    lib.scal3r_gcm_out_backward.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    lib.scal3r_gcm_out_backward.restype = ctypes.c_int
+    lib.scal3r_gcm_qkv_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp, vp, vp, vp, i64, vp, vp,
+                                            vp, vp, vp, vp, sz, vp]
+    lib.scal3r_gcm_qkv_backward.restype = ctypes.c_int
     _lib_handle = lib
     return lib
 
@@ -367,24 +367,27 @@ def scal3r_gcm_workspace_size(handle: int, T: int) -> int:
     return n.value
 
 
-def scal3r_gcm_prep(handle, qkv_raw, bqkv, x, w_eta, b_eta, base_lr, T, q, k, v, lr, qn, kn, sig, stream) -> int:
-    return load_library().scal3r_gcm_prep(handle, qkv_raw, bqkv, x, w_eta, b_eta, float(base_lr), T, q, k, v, lr,
-                                          qn, kn, sig, stream)
+def scal3r_gcm_qkv(handle, x, wqkv, bqkv, w_eta, b_eta, base_lr, T, q, k, v, lr, qn, kn, sig, workspace,
+                   workspace_bytes, stream) -> int:
+    return load_library().scal3r_gcm_qkv(handle, x, wqkv, bqkv, w_eta, b_eta, float(base_lr), T, q, k, v, lr, qn, kn,
+                                         sig, workspace, workspace_bytes, stream)
 
 
-def scal3r_gcm_gate(handle, y, x, alpha, T, out, stream) -> int:
-    return load_library().scal3r_gcm_gate(handle, y, x, alpha, T, out, stream)
+def scal3r_gcm_out(handle, o, wo, x, alpha, T, out, y, stream) -> int:
+    return load_library().scal3r_gcm_out(handle, o, wo, x, alpha, T, out, y, stream)
 
 
-def scal3r_gcm_gate_backward(handle, d_out, y, alpha, T, dy, dx, dalpha, workspace, workspace_bytes, stream) -> int:
-    return load_library().scal3r_gcm_gate_backward(handle, d_out, y, alpha, T, dy, dx, dalpha, workspace,
-                                                   workspace_bytes, stream)
+def scal3r_gcm_out_backward(handle, d_out, o, wo, y, alpha, T, d_o, dwo, dalpha, workspace, workspace_bytes,
+                            stream) -> int:
+    return load_library().scal3r_gcm_out_backward(handle, d_out, o, wo, y, alpha, T, d_o, dwo, dalpha, workspace,
+                                                  workspace_bytes, stream)
 
 
-def scal3r_gcm_prep_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, base_lr, T, dqkv, dlogit, dbqkv, db_eta,
-                             workspace, workspace_bytes, stream) -> int:
-    return load_library().scal3r_gcm_prep_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, float(base_lr), T,
-                                                   dqkv, dlogit, dbqkv, db_eta, workspace, workspace_bytes, stream)
+def scal3r_gcm_qkv_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, base_lr, x, wqkv, w_eta, d_out, T, dx, dwqkv,
+                            dbqkv, dw_eta, db_eta, workspace, workspace_bytes, stream) -> int:
+    return load_library().scal3r_gcm_qkv_backward(handle, dq, dk, dv, dlr, q, k, qn, kn, sig, float(base_lr), x, wqkv,
+                                                  w_eta, d_out, T, dx, dwqkv, dbqkv, dw_eta, db_eta, workspace,
+                                                  workspace_bytes, stream)
 
 
 from .layer import TTT, TTTFunction  # noqa: E402,F401

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cuda_bf16.h>
 #include <cstring>
+#include <initializer_list>
 #include <functional>
 #include <mutex>
 
@@ -24,20 +25,21 @@ cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void*
                            int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
                            size_t ws_bytes, int timeout_test, int* status, cudaStream_t st);
 size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32);
-size_t gcm_partial_bytes(int64_t T, int d, int H);
 bool gcm_heads_supported(int H);
-cudaError_t gcm_prep(const float* raw, const float* bqkv, const __nv_bfloat16* x, const float* w_eta,
-                     const float* b_eta, float base, int64_t T, int H, int D, __nv_bfloat16* q, __nv_bfloat16* k,
-                     __nv_bfloat16* v, float* lr, float* qn, float* kn, float* sig, cudaStream_t st);
-cudaError_t gcm_gate(const float* y, const __nv_bfloat16* x, const float* alpha, int64_t T, int d,
-                     __nv_bfloat16* out, cudaStream_t st);
-cudaError_t gcm_gate_backward(const __nv_bfloat16* dout, const float* y, const float* alpha, int64_t T, int d,
-                              __nv_bfloat16* dy, float* dx, float* dalpha, float* part, cudaStream_t st);
-cudaError_t gcm_prep_backward(const __nv_bfloat16* dq, const __nv_bfloat16* dk, const __nv_bfloat16* dv,
-                              const float* dlr, const __nv_bfloat16* q, const __nv_bfloat16* k, const float* qn,
-                              const float* kn, const float* sig, float base, int64_t T, int H, int D,
-                              __nv_bfloat16* dqkv, __nv_bfloat16* dlogit, float* dbqkv, float* db_eta, float* part,
-                              cudaStream_t st);
+size_t gcm_workspace_bytes(int64_t T, int H, int D);
+cudaError_t gcm_qkv(const void* x, const void* wqkv, const float* bqkv, const float* w_eta, const float* b_eta,
+                    float base, int64_t T, int H, int D, void* q, void* k, void* v, float* lr, float* qn, float* kn,
+                    float* sig, void* ws, int* status, int sms, cudaStream_t st);
+cudaError_t gcm_out(const void* o, const void* wo, const void* x, const float* alpha, int64_t T, int d, void* out,
+                    void* y, int* status, cudaStream_t st);
+cudaError_t gcm_out_backward(const void* d_out, const void* o, const void* wo, const void* y, const float* alpha,
+                             int64_t T, int d, void* d_o, float* dwo, float* dalpha, void* ws, int* status, int sms,
+                             cudaStream_t st);
+cudaError_t gcm_qkv_backward(const void* dq, const void* dk, const void* dv, const float* dlr, const void* q,
+                             const void* k, const float* qn, const float* kn, const float* sig, float base,
+                             const void* x, const void* wqkv, const float* w_eta, const void* d_out, int64_t T, int H,
+                             int D, float* dx, float* dwqkv, float* dbqkv, float* dw_eta, float* db_eta, void* ws,
+                             int* status, int sms, cudaStream_t st);
 bool fp32_shape_supported(int D, int F);
 bool bf16_shape_supported(int D, int F);
 bool update_shape_supported(int D, int F);
@@ -1328,71 +1330,100 @@ int scal3r_ttt_gemm(scal3r_ttt_handle* hd, const void* a, int64_t lda, int32_t a
   return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
 }
 
-int scal3r_gcm_workspace_size(scal3r_ttt_handle* hd, int64_t T, size_t* bytes) {
-  if (!hd || !bytes || T < 0) return SCAL3R_ERR_INVALID_ARG;
-  *bytes = gcm_partial_bytes(T, hd->shape.H * hd->shape.D, hd->shape.H);
+// The GCM module's calls need a BF16 handle, H <= 16 and d = H * D a
+// multiple of 256 (the GEMM's output tile).
+static int gcm_check(const scal3r_ttt_handle* hd) {
+  if (!gcm_heads_supported(hd->shape.H) || hd->cfg.dtype != SCAL3R_BF16 || (hd->shape.H * hd->shape.D) % 256 != 0)
+    return SCAL3R_ERR_UNSUPPORTED;
   return SCAL3R_OK;
 }
 
-int scal3r_gcm_prep(scal3r_ttt_handle* hd, const float* qkv_raw, const float* bqkv, const void* x,
-                    const float* w_eta, const float* b_eta, float base_lr, int64_t T, void* q, void* k, void* v,
-                    float* lr, float* qn, float* kn, float* sig, void* stream) {
+static bool all_aligned(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (!aligned16(p)) return false;
+  return true;
+}
+
+int scal3r_gcm_workspace_size(scal3r_ttt_handle* hd, int64_t T, size_t* bytes) {
+  if (!hd || !bytes || T < 0) return SCAL3R_ERR_INVALID_ARG;
+  *bytes = gcm_workspace_bytes(T, hd->shape.H, hd->shape.D);
+  return SCAL3R_OK;
+}
+
+int scal3r_gcm_qkv(scal3r_ttt_handle* hd, const void* x, const void* wqkv, const float* bqkv, const float* w_eta,
+                   const float* b_eta, float base_lr, int64_t T, void* q, void* k, void* v, float* lr, float* qn,
+                   float* kn, float* sig, void* workspace, size_t workspace_bytes, void* stream) {
   if (!hd || T < 0 || !(base_lr > 0.f)) return SCAL3R_ERR_INVALID_ARG;
-  if (!gcm_heads_supported(hd->shape.H) || hd->cfg.dtype != SCAL3R_BF16) return SCAL3R_ERR_UNSUPPORTED;
-  if (T > 0 && (!qkv_raw || !bqkv || !x || !w_eta || !b_eta || !q || !k || !v || !lr || !qn || !kn || !sig))
+  int rc = gcm_check(hd);
+  if (rc != SCAL3R_OK) return rc;
+  if (T == 0) return SCAL3R_OK;
+  if (!x || !wqkv || !bqkv || !w_eta || !b_eta || !q || !k || !v || !lr || !qn || !kn || !sig)
     return SCAL3R_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
-    return gcm_prep(qkv_raw, bqkv, static_cast<const __nv_bfloat16*>(x), w_eta, b_eta, base_lr, T, hd->shape.H,
-                    hd->shape.D, static_cast<__nv_bfloat16*>(q), static_cast<__nv_bfloat16*>(k),
-                    static_cast<__nv_bfloat16*>(v), lr, qn, kn, sig, st);
-  });
-  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
-}
-
-int scal3r_gcm_gate(scal3r_ttt_handle* hd, const float* y, const void* x, const float* alpha, int64_t T, void* out,
-                    void* stream) {
-  if (!hd || T < 0 || (T > 0 && (!y || !x || !alpha || !out))) return SCAL3R_ERR_INVALID_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
-    return gcm_gate(y, static_cast<const __nv_bfloat16*>(x), alpha, T, hd->shape.H * hd->shape.D,
-                    static_cast<__nv_bfloat16*>(out), st);
-  });
-  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
-}
-
-int scal3r_gcm_gate_backward(scal3r_ttt_handle* hd, const void* d_out, const float* y, const float* alpha, int64_t T,
-                             void* dy, float* dx, float* dalpha, void* workspace, size_t workspace_bytes,
-                             void* stream) {
-  if (!hd || T < 0 || !dalpha || (T > 0 && (!d_out || !y || !alpha || !dy || !dx))) return SCAL3R_ERR_INVALID_ARG;
-  const int d = hd->shape.H * hd->shape.D;
-  if (!workspace || workspace_bytes < gcm_partial_bytes(T, d, hd->shape.H) || !aligned16(workspace))
-    return SCAL3R_ERR_WORKSPACE;
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
-    return gcm_gate_backward(static_cast<const __nv_bfloat16*>(d_out), y, alpha, T, d, static_cast<__nv_bfloat16*>(dy),
-                             dx, dalpha, static_cast<float*>(workspace), st);
-  });
-  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
-}
-
-int scal3r_gcm_prep_backward(scal3r_ttt_handle* hd, const void* dq, const void* dk, const void* dv, const float* dlr,
-                             const void* q, const void* k, const float* qn, const float* kn, const float* sig,
-                             float base_lr, int64_t T, void* dqkv, void* dlogit, float* dbqkv, float* db_eta,
-                             void* workspace, size_t workspace_bytes, void* stream) {
-  if (!hd || T < 0 || !dbqkv || !db_eta) return SCAL3R_ERR_INVALID_ARG;
-  if (T > 0 && (!dq || !dk || !dv || !dlr || !q || !k || !qn || !kn || !sig || !dqkv || !dlogit))
-    return SCAL3R_ERR_INVALID_ARG;
-  if (!gcm_heads_supported(hd->shape.H) || hd->cfg.dtype != SCAL3R_BF16) return SCAL3R_ERR_UNSUPPORTED;
+  if (!all_aligned({x, wqkv, bqkv, w_eta, q, k, v})) return SCAL3R_ERR_MISALIGNED;
   const int H = hd->shape.H, D = hd->shape.D;
-  if (!workspace || workspace_bytes < gcm_partial_bytes(T, H * D, H) || !aligned16(workspace))
+  if (!workspace || workspace_bytes < gcm_workspace_bytes(T, H, D) || !aligned16(workspace))
     return SCAL3R_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream;
-  auto B = [](const void* p) { return static_cast<const __nv_bfloat16*>(p); };
-  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 0, 0, st, [&] {
-    return gcm_prep_backward(B(dq), B(dk), B(dv), dlr, B(q), B(k), qn, kn, sig, base_lr, T, H, D,
-                             static_cast<__nv_bfloat16*>(dqkv), static_cast<__nv_bfloat16*>(dlogit), dbqkv, db_eta,
-                             static_cast<float*>(workspace), st);
+  const double d = (double)H * D;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 6.0 * T * d * d, 0, st, [&] {
+    return gcm_qkv(x, wqkv, bqkv, w_eta, b_eta, base_lr, T, H, D, q, k, v, lr, qn, kn, sig, workspace, hd->d_status,
+                   hd->num_sms, st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_out(scal3r_ttt_handle* hd, const void* o, const void* wo, const void* x, const float* alpha, int64_t T,
+                   void* out, void* y, void* stream) {
+  if (!hd || T < 0) return SCAL3R_ERR_INVALID_ARG;
+  int rc = gcm_check(hd);
+  if (rc != SCAL3R_OK) return rc;
+  if (T == 0) return SCAL3R_OK;
+  if (!o || !wo || !x || !alpha || !out || !y) return SCAL3R_ERR_INVALID_ARG;
+  if (!all_aligned({o, wo, x, alpha, out, y})) return SCAL3R_ERR_MISALIGNED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = hd->shape.H * hd->shape.D;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 2.0 * T * d * d, 0, st,
+                        [&] { return gcm_out(o, wo, x, alpha, T, d, out, y, hd->d_status, st); });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_out_backward(scal3r_ttt_handle* hd, const void* d_out, const void* o, const void* wo, const void* y,
+                            const float* alpha, int64_t T, void* d_o, float* dwo, float* dalpha, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (!hd || T < 0 || !dwo || !dalpha) return SCAL3R_ERR_INVALID_ARG;
+  int rc = gcm_check(hd);
+  if (rc != SCAL3R_OK) return rc;
+  if (T > 0 && (!d_out || !o || !wo || !y || !alpha || !d_o)) return SCAL3R_ERR_INVALID_ARG;
+  if (!all_aligned({d_out, o, wo, y, d_o, dwo, dalpha})) return SCAL3R_ERR_MISALIGNED;
+  const int H = hd->shape.H, D = hd->shape.D, d = H * D;
+  if (!workspace || workspace_bytes < gcm_workspace_bytes(T, H, D) || !aligned16(workspace))
+    return SCAL3R_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 4.0 * T * d * (double)d, 0, st, [&] {
+    return gcm_out_backward(d_out, o, wo, y, alpha, T, d, d_o, dwo, dalpha, workspace, hd->d_status, hd->num_sms, st);
+  });
+  return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
+}
+
+int scal3r_gcm_qkv_backward(scal3r_ttt_handle* hd, const void* dq, const void* dk, const void* dv, const float* dlr,
+                            const void* q, const void* k, const float* qn, const float* kn, const float* sig,
+                            float base_lr, const void* x, const void* wqkv, const float* w_eta, const void* d_out,
+                            int64_t T, float* dx, float* dwqkv, float* dbqkv, float* dw_eta, float* db_eta,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+  if (!hd || T < 0 || !(base_lr > 0.f) || !dwqkv || !dbqkv || !dw_eta || !db_eta) return SCAL3R_ERR_INVALID_ARG;
+  int rc = gcm_check(hd);
+  if (rc != SCAL3R_OK) return rc;
+  if (T > 0 && (!dq || !dk || !dv || !dlr || !q || !k || !qn || !kn || !sig || !x || !wqkv || !w_eta || !d_out || !dx))
+    return SCAL3R_ERR_INVALID_ARG;
+  if (!all_aligned({dq, dk, dv, q, k, x, wqkv, w_eta, d_out, dx, dwqkv, dw_eta})) return SCAL3R_ERR_MISALIGNED;
+  const int H = hd->shape.H, D = hd->shape.D;
+  if (!workspace || workspace_bytes < gcm_workspace_bytes(T, H, D) || !aligned16(workspace))
+    return SCAL3R_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double d = (double)H * D;
+  cudaError_t e = timed(hd, SCAL3R_KERNEL_OTHER, 2.0 * T * d * (6.0 * d + 128.0), 0, st, [&] {
+    return gcm_qkv_backward(dq, dk, dv, dlr, q, k, qn, kn, sig, base_lr, x, wqkv, w_eta, d_out, T, H, D, dx, dwqkv,
+                            dbqkv, dw_eta, db_eta, workspace, hd->d_status, hd->num_sms, st);
   });
   return e == cudaSuccess ? SCAL3R_OK : SCAL3R_ERR_CUDA;
 }

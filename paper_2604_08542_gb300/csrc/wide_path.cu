@@ -65,6 +65,11 @@ enum Epi : int {
   EPI_BKEY_MSE1 = 10,  // update VJP gate, pass 1: in0 = p, in1 = -R2^T e -> dp, g1, g3, partials of d eta
   EPI_BKEY_MSE2 = 11,  // update VJP gate, pass 2: in0 = p, in1 = du -> dz1, dz3
   EPI_APPLY2 = 12,  // gate z1 | z3 -> u and eta2 u
+  // the GCM module's projections (scal3r_gcm.h):
+  EPI_GCM_QKV = 13,   // acc + colvec (bias) -> bf16 into out[0] | out[1] | out[2] (q | k | v, row stride
+                      //   ld_out = d); q and k: sum of squares of every 64 columns into out[3] (ld_part)
+  EPI_GCM_GATE = 14,  // out[0] = colvec o acc + in0 (alpha o y + x), out[1] = acc; both bf16
+  EPI_F32_ADDIN = 15, // out[0] = acc + in0 (float32 out, bf16 in0)
 };
 
 struct GemmArgs {
@@ -95,6 +100,7 @@ struct GemmArgs {
   int ksplit;              // > 1: K is cut into ksplit ranges of kb_split K blocks; range s of a tile
   int kb_split;            //   writes (EPI_F32) the partial plane out[0] + s * split_stride
   int64_t split_stride;
+  const float* colvec;     // EPI_GCM_QKV: the bias of output column n; EPI_GCM_GATE: its gate alpha
 };
 
 __device__ __forceinline__ float silu_d(float z, float& sg) {
@@ -477,6 +483,84 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
               o[j] = x0;
               o[4 + j] = x1;
             }
+          }
+        }
+      } else if (!XSET && g.epi == EPI_GCM_QKV) {
+        // the tile's 256 columns lie in one of q, k, v (d is a multiple of 256)
+        const int dm = (int)g.ld_out, part = n0 / dm, c0 = n0 - part * dm;
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(g.out[part]) + (size_t)m * dm + c0;
+        float* ssq = reinterpret_cast<float*>(g.out[3]) + (size_t)m * g.ld_part + (part * dm + c0) / 64;
+        float ss = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          float v0[16], v1[16];
+          tmem_ld16(accb + c, v0);
+          tmem_ld16(accb + c + 16, v1);
+          if (!valid) continue;
+          const float* bb = g.colvec + n0 + c;
+          if (!in_bounds(bb, 128)) continue;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            v0[i] += bb[i];
+            v1[i] += bb[16 + i];
+          }
+          st_bf16x16(dst + c, v0);
+          st_bf16x16(dst + c + 16, v1);
+          if (part < 2) {   // the norm from the float32 values
+#pragma unroll
+            for (int i = 0; i < 16; ++i) ss = fmaf(v1[i], v1[i], fmaf(v0[i], v0[i], ss));
+            if (c & 32) {
+              if (in_bounds(ssq + c / 64, 4)) ssq[c / 64] = ss;
+              ss = 0.f;
+            }
+          }
+        }
+      } else if (!XSET && (g.epi == EPI_GCM_GATE || g.epi == EPI_F32_ADDIN)) {
+        const int64_t ldi = g.ld_in ? g.ld_in : g.ld_out;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          float v0[16], v1[16];
+          tmem_ld16(accb + c, v0);
+          tmem_ld16(accb + c + 16, v1);
+          if (!valid) continue;
+          const uint4* xin = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
+          if (!in_bounds(xin, 64)) continue;
+          float xv[32];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint4 w = xin[j];
+            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              xv[8 * j + 2 * e] = bf16_lo(ww[e]);
+              xv[8 * j + 2 * e + 1] = bf16_hi(ww[e]);
+            }
+          }
+          if (g.epi == EPI_F32_ADDIN) {
+            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c);
+            if (!in_bounds(o, 128)) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              o[j] = make_float4(v0[4 * j] + xv[4 * j], v0[4 * j + 1] + xv[4 * j + 1], v0[4 * j + 2] + xv[4 * j + 2],
+                                 v0[4 * j + 3] + xv[4 * j + 3]);
+              o[4 + j] = make_float4(v1[4 * j] + xv[16 + 4 * j], v1[4 * j + 1] + xv[17 + 4 * j],
+                                     v1[4 * j + 2] + xv[18 + 4 * j], v1[4 * j + 3] + xv[19 + 4 * j]);
+            }
+          } else {
+            const size_t off = (size_t)m * g.ld_out + n0 + c;
+            __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off;
+            st_bf16x16(yo, v0);
+            st_bf16x16(yo + 16, v1);
+            const float* al = g.colvec + n0 + c;
+            if (!in_bounds(al, 128)) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              v0[i] = fmaf(al[i], v0[i], xv[i]);
+              v1[i] = fmaf(al[16 + i], v1[i], xv[16 + i]);
+            }
+            __nv_bfloat16* oo = reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off;
+            st_bf16x16(oo, v0);
+            st_bf16x16(oo + 16, v1);
           }
         }
       } else if (XSET) {   // EPI_BKEY
@@ -992,7 +1076,7 @@ cudaError_t gemm(GemmArgs& a, cudaStream_t st) {
   const int64_t units = (int64_t)((a.M + BM - 1) / BM) * (a.N / BN) * a.ksplit;
   if (units > INT32_MAX) return cudaErrorInvalidValue;
   const int grid = (int)std::min<int64_t>(units, num_sms());
-  if (a.epi >= EPI_MSE_E || a.epi == EPI_BKEY)
+  if ((a.epi >= EPI_MSE_E && a.epi <= EPI_APPLY2) || a.epi == EPI_BKEY)
     wide_gemm_kernel<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
   else
     wide_gemm_kernel<false><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(a);
@@ -1158,6 +1242,74 @@ size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32) 
 // runs in K ranges into partial planes in `ws` (when it holds them) and a
 // fixed-order sum.  Returns cudaErrorInvalidValue on a shape the kernel does
 // not take.
+// The GCM module's projections with their row steps in the epilogue
+// (scal3r_gcm.h).  [q | k | v] = x Wqkv^T + bqkv as bf16 into q, k, v [T][d],
+// and the sums of squares of every 64 columns of q and k into ssq [T][2d/64]
+// (from the float32 values, for the per-head norms).
+cudaError_t wide_gcm_qkv(const void* x, const void* wqkv, const float* bqkv, int64_t T, int d, void* q, void* k,
+                         void* v, float* ssq, int* status, cudaStream_t st) {
+  if (T <= 0) return cudaSuccess;
+  if (d <= 0 || d % BN != 0 || T > INT32_MAX) return cudaErrorInvalidValue;
+  GemmArgs g{};
+  if (!make_map(&g.a[0], x, T, 1, d, d, 128) || !make_map(&g.b[0], wqkv, 3 * (int64_t)d, 1, d, d, 256))
+    return cudaErrorInvalidValue;
+  g.M = (int)T;
+  g.N = 3 * d;
+  g.K = d;
+  g.epi = EPI_GCM_QKV;
+  g.out[0] = q;
+  g.out[1] = k;
+  g.out[2] = v;
+  g.out[3] = ssq;
+  g.ld_out = d;
+  g.ld_part = 2 * d / 64;
+  g.colvec = bqkv;
+  g.status = status;
+  return gemm(g, st);
+}
+
+// out = alpha o (o Wo^T) + x and y = o Wo^T, both bf16 [T][d] (Eq. 5).
+cudaError_t wide_gcm_gate(const void* o, const void* wo, const void* x, const float* alpha, int64_t T, int d,
+                          void* out, void* y, int* status, cudaStream_t st) {
+  if (T <= 0) return cudaSuccess;
+  if (d <= 0 || d % BN != 0 || T > INT32_MAX) return cudaErrorInvalidValue;
+  GemmArgs g{};
+  if (!make_map(&g.a[0], o, T, 1, d, d, 128) || !make_map(&g.b[0], wo, d, 1, d, d, 256))
+    return cudaErrorInvalidValue;
+  g.M = (int)T;
+  g.N = d;
+  g.K = d;
+  g.epi = EPI_GCM_GATE;
+  g.out[0] = out;
+  g.out[1] = y;
+  g.in0 = static_cast<const __nv_bfloat16*>(x);
+  g.ld_out = d;
+  g.colvec = alpha;
+  g.status = status;
+  return gemm(g, st);
+}
+
+// C = A B + add: A [M][K] bf16 (rows lda apart), B given as [K][N] bf16 (rows
+// ldb apart), add [M][N] bf16, C [M][N] float32.
+cudaError_t wide_gemm_addin(const void* a, int64_t lda, const void* b, int64_t ldb, const void* add, float* c,
+                            int64_t M, int64_t N, int64_t K, int* status, cudaStream_t st) {
+  if (M <= 0) return cudaSuccess;
+  if (N % BN != 0 || K <= 0 || M > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
+  GemmArgs g{};
+  if (!make_map(&g.a[0], a, M, 1, K, lda, 128) || !make_map(&g.b[0], b, K, 1, N, ldb, 64))
+    return cudaErrorInvalidValue;
+  g.M = (int)M;
+  g.N = (int)N;
+  g.K = (int)K;
+  g.b_mn = 1;
+  g.epi = EPI_F32_ADDIN;
+  g.out[0] = c;
+  g.ld_out = N;
+  g.in0 = static_cast<const __nv_bfloat16*>(add);
+  g.status = status;
+  return gemm(g, st);
+}
+
 cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void* b, int64_t ldb, int b_kmajor, void* c,
                            int64_t ldc, int out_fp32, int accumulate, int64_t M, int64_t N, int64_t K, void* ws,
                            size_t ws_bytes, int timeout_test, int* status, cudaStream_t st) {

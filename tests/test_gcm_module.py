@@ -1,6 +1,7 @@
 """The GCM module around the layer (Sec. 4.1, Eq. 5) through the C ABI: the
-projections on the tcgen05 GEMM, the row steps, and the layer, forward and
-backward, against the FP64 oracle on the same bf16-rounded tensors (GPU).
+projections on the tcgen05 GEMM with the row work in their epilogues, the
+remaining row steps, and the layer, forward and backward, against the FP64
+oracle on the same bf16-rounded tensors (GPU).
 
 Bar: normwise relative error <= 2e-2 (the BF16 bar) on out and on every
 gradient (x, Wqkv, bqkv, w_eta, b_eta, Wo, alpha, w0)."""
@@ -63,6 +64,11 @@ def test_gcm_module_sixteen_heads_of_64():
 def test_gcm_module_wide_heads():
     """d = 512 as 2 heads x 256 (the wide-weight layer), one sequence of two chunks."""
     _case(2, 256, 512, [[300, 200]], seed=62)
+
+
+def test_gcm_module_four_heads_one_token_chunk():
+    """d = 256 as 4 heads x 64, a one-token chunk and a ragged tail."""
+    _case(4, 64, 128, [[1], [200, 3]], seed=63)
 
 
 @pytest.mark.parametrize("M,N,K,a_kmajor,b_kmajor", [(64, 1024, 8192, 0, 0), (1024, 512, 4100, 0, 0),
