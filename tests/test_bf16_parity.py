@@ -135,3 +135,35 @@ def test_bf16_backward_full_size_sampled_heads():
     print("fwdbwd_2x32 gradient errors", errs)
     bad = {n: e for n, e in errs.items() if not e <= TOL}
     assert not bad, f"above {TOL}: {bad}; all {errs}"
+
+
+def test_bf16_vggt64_backward_in_graph_mode_sampled_heads():
+    """The benchmark's own step: 64 frames x 1041 tokens, 16 heads, 4 chunks of
+    16,656 tokens, forward + backward replayed from the library's CUDA graphs
+    (second call; the first captures).  The oracle checks every output and
+    gradient of two whole heads."""
+    import torch
+    w = syn.workload("bf16_vggt64")
+    lay = w.layout()
+    x = syn.make_inputs(lay.num_tokens, 16, 64, 128, seed=4, dtype="bf16", with_grad_out=True)
+    g = upload(x, torch.bfloat16)
+    layer = _layer(16)
+    layer.set_graph_mode(True)
+    for _ in range(2):
+        o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets,
+                                      lay.seq_chunk_ptr, want_final=True)
+        grads = layer.backward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr,
+                               g["d_o"], ck, wn)
+    torch.cuda.synchronize()
+    assert layer.status() == 0
+    heads = [5, 10]
+    xs = {n: x[n][:, heads] for n in ("q", "k", "v", "lr", "d_o")}
+    ref = oracle.forward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][heads], lay, 64, 128, eps=1e-6)
+    errs = _check((o, ck, wn, wf), ref, heads=heads)
+    rb = oracle.backward(xs["q"], xs["k"], xs["v"], xs["lr"], x["w0"][heads], lay, xs["d_o"], 64, 128, eps=1e-6)
+    for n, t in zip(("dq", "dk", "dv", "dlr", "dw0"), grads):
+        a = to_np(t)
+        errs[n] = rel_inf(a[heads] if n == "dw0" else a[:, heads], rb[n])
+    print("vggt64 graph-mode errors", errs)
+    bad = {n: e for n, e in errs.items() if not e <= TOL}
+    assert not bad, f"above {TOL}: {bad}; all {errs}"
