@@ -162,7 +162,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       if (lane == 0) {
         for (int i = ta; i < te; ++i) {
           const int s = i & 1;
-          if (!mbar_wait_spin(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
+          if (!mbar_wait(&B.xy_empty[s], ((i >> 1) & 1) ^ 1, abort)) break;
           mbar_arrive_expect_tx(&B.xy_full[s], 2 * BT * 128);
           uint8_t* xs = sm + XY_OFF + s * 32768;
           const int32_t tok = (int32_t)(t0 + (int64_t)i * BT);
@@ -184,8 +184,8 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       constexpr uint32_t HI128 = sdesc_hi(1024, kSwizzle128), HI64 = sdesc_hi(512, kSwizzle64);
       auto issue_acc = [&](int m) -> bool {
         const int i = m / NQ, q = m % NQ;
-        if (!mbar_wait_spin_w(&B.st_full, m & 1, abort)) return false;
-        if (q == 0 && !mbar_wait_spin_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
+        if (!mbar_wait_nap_w(&B.st_full, m & 1, abort)) return false;
+        if (q == 0 && !mbar_wait_nap_w(&B.acc_free, (i & 1) ^ 1, abort)) return false;
         tc_fence_after();
         const uint32_t wb = wq_lo1k + q * (QBYTES >> 4);
         const uint32_t acc0 = q > 0 ? 1u : 0u;
@@ -203,11 +203,11 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
       };
       bool ok = true;
       // pass B of the previous sub-piece overwrote the weights
-      if (sp > 0 && !mbar_wait_spin_w(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
+      if (sp > 0 && !mbar_wait_nap_w(&B.wq_full, (sp - 1) & 1, abort)) ok = false;
       for (int n = ta * NQ; n < te * NQ && ok; ++n) {
         const int i = n / NQ, q = n % NQ;
-        if (q == 0 && !mbar_wait_spin_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
-        if (!mbar_wait_spin_w(&B.g_free, (n & 1) ^ 1, abort)) break;
+        if (q == 0 && !mbar_wait_nap_w(&B.xy_full[i & 1], (i >> 1) & 1, abort)) break;
+        if (!mbar_wait_nap_w(&B.g_free, (n & 1) ^ 1, abort)) break;
         tc_fence_after();
         const uint32_t xs = xy_lo + (i & 1) * (32768 >> 4);
         const uint32_t wb = wq_lo16 + q * (QBYTES >> 4);
@@ -232,7 +232,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         // dk / dv of tile i, staged over the tile's X/Y stage by the epilogue
         // (after the next tile's first quarter, see there)
         auto store_dkdv = [&](int i) -> bool {
-          if (!mbar_wait_spin(&B.out_full, i & 1, abort)) return false;
+          if (!mbar_wait(&B.out_full, i & 1, abort)) return false;
           const int64_t tok = t0 + (int64_t)i * BT;
           if (tok + BT <= t1) {
             uint8_t* xs = sm + XY_OFF + (i & 1) * 32768;
@@ -249,7 +249,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         bool ok = true;
         for (int n = ta * NQ; n < te * NQ && ok; ++n) {
           const int i = n / NQ, q = n % NQ;
-          if (!mbar_wait_spin(&B.st_full, n & 1, abort)) break;
+          if (!mbar_wait(&B.st_full, n & 1, abort)) break;
           const int32_t g = g0 + 4 * (i - ta);
           tma_store_5d(&maps.sc_st, sm + ST_OFF + 0 * ST_TILE, 0, 0, q, 0, g);   // dz1
           tma_store_5d(&maps.sc_st, sm + ST_OFF + 1 * ST_TILE, 0, 0, q, 1, g);   // dz3
@@ -456,7 +456,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         bool ok = true;
         for (int j = 0; j < nb; ++j) {
           const int s = (j + rot) % PB_STAGES;
-          if (!mbar_wait_spin(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort)) {
+          if (!mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort)) {
             ok = false;
             break;
           }
@@ -471,7 +471,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
         if (ok && sp + 1 < nsub) {
           // the stages over the weights are read: copy the weights back
           for (int s = 0; s < PB_WQ_STAGES && ok; ++s)
-            ok = mbar_wait_spin(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort);
+            ok = mbar_wait(&B.b_empty[s], ((pb_uses >> s) & 1) ^ 1, abort);
           if (ok) {
             mbar_arrive_expect_tx(&B.wq_full, WQ_BYTES);
             bulk_load(sm + WQ_OFF, wq_image, WQ_BYTES, &B.wq_full);

@@ -115,6 +115,27 @@ __device__ __forceinline__ bool mbar_wait_spin_w(uint64_t* bar, uint32_t parity,
   return __all_sync(0xffffffffu, mbar_wait_spin(bar, parity, abort));
 }
 
+
+// Polling with a short sleep between tests (the waiting warp gives its issue
+// slots to the other warps of its scheduler while it waits).
+__device__ __forceinline__ bool mbar_wait_nap(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                              uint64_t budget_ns = 1000000000ull) {
+  if (mbar_try_wait<false>(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    __nanosleep(20);
+    if (mbar_try_wait<false>(bar, parity)) return true;
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > budget_ns) {
+      *abort = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ bool mbar_wait_nap_w(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  return __all_sync(0xffffffffu, mbar_wait_nap(bar, parity, abort));
+}
+
 // ---------------------------------------------------------------------------
 // TMA
 // ---------------------------------------------------------------------------
