@@ -130,6 +130,13 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   const int64_t t0 = it.t0, t1 = it.t1;
   const int ntiles = (int)((t1 - t0 + BT - 1) / BT);
   const int nsub = (ntiles + kBwdSubTiles - 1) / kBwdSubTiles;
+  // The pieces of a launch start together and have equal sub-pieces, so
+  // their second passes (the L2-heavy phase) would coincide.  The slack of
+  // the last sub-piece (nsub * kBwdSubTiles - ntiles tiles) is taken off the
+  // first one by a CTA-dependent amount instead, which staggers the phases
+  // without adding a sub-piece.
+  const int slack = nsub * kBwdSubTiles - ntiles;
+  const int lead = slack > 0 ? (int)(blockIdx.x % (unsigned)(slack + 1)) : 0;
   // the piece's scratch: kBwdSubTiles tiles of factor groups, then the weights
   const int32_t g0 = 4 * it.aux;   // first 32-token group of the piece
   uint8_t* wq_image = reinterpret_cast<uint8_t*>(p.scratch) + (size_t)(it.aux + kBwdSubTiles) * TILE_SCRATCH;
@@ -155,8 +162,8 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   uint32_t pb_uses = 0;
   bool aborted = false;
   for (int sp = 0; sp < nsub; ++sp) {
-    const int ta = sp * kBwdSubTiles;
-    const int te = min(ntiles, ta + kBwdSubTiles);
+    const int ta = sp == 0 ? 0 : sp * kBwdSubTiles - lead;
+    const int te = min(ntiles, (sp + 1) * kBwdSubTiles - lead);
     // ======================= pass A on tiles [ta, te) =======================
     if (warp == 0) {
       if (lane == 0) {
