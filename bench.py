@@ -45,11 +45,11 @@ NUM_SMS_GB300 = 152
 # (update VJP of chunk 1 with apply VJP of chunk 0) and forward step 3.  It
 # belongs to the kernels as they were captured: retake it when they change.
 NCU_TRAFFIC = {
-    "bf16_vggt64": {"bwd_sweep": 196_698_880 + 218_130_432, "fwd_sweep": 105_362_944 + 13_213_952},
+    # the forward sweep's kernel changed after its last capture: no figure for it
+    "bf16_vggt64": {"bwd_sweep": 206_362_880 + 210_849_280, "fwd_sweep": None},
 }
-NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: the backward sweep of commit "
-                      "aa46d8d (its kernel as of cc87ed2; profiles/bf16_bsweep_kernel_vggt64.md), the forward sweep "
-                      "of commit 8b5f4ba")
+NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the backward sweep at "
+                      "commit 1198f2e (profiles/bf16_bsweep_kernel_vggt64.md)")
 
 
 def parse():
