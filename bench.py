@@ -314,7 +314,8 @@ def amu_leg(args, dev, peak_tflops):
 
 def amu_variants(args, dev, peak_tflops):
     """Forward+backward at the paper's AMU shape (workload bf16_amu1024) for the
-    layer's options: the squared-error loss, per-matrix learning rates, sparse
+    layer's options (against the plain layer timed the same way): the
+    squared-error loss, per-matrix learning rates, sparse
     checkpoints (every 4th chunk), the state-size ablation's smaller hidden
     sizes (k = 1, 2), the GCM module around the layer, and the
     forward as the Global Context Synchronisation split loop (partial
@@ -381,7 +382,8 @@ def amu_variants(args, dev, peak_tflops):
             layer.backward(q, k, v, lr, w, off, ptr, d_o, ck, wn, workspace=ws)
         return fn
 
-    for name, kw, lr in (("mse_fwdbwd", {"loss": "mse"}, lr1), ("per_matrix_lr_fwdbwd", {"lr_per_matrix": True}, lr3),
+    for name, kw, lr in (("plain_fwdbwd", {}, lr1), ("mse_fwdbwd", {"loss": "mse"}, lr1),
+                         ("per_matrix_lr_fwdbwd", {"lr_per_matrix": True}, lr3),
                          ("ckpt_every4_fwdbwd", {"ckpt_every": 4}, lr1)):
         layer = ttt.TTT(H, D, F, dtype=torch.bfloat16, **kw)
         out[name] = timed(layer_fwd_bwd(layer, lr), layer)
@@ -418,6 +420,8 @@ def amu_variants(args, dev, peak_tflops):
                                off, ptr)
         gcm.backward(saved, d_out)
     out["gcm_fwdbwd"] = timed(gcm_step, gcm.ttt)
+    # the module's cost against the bare layer timed the same way (direct launches)
+    out["gcm_fwdbwd"]["vs_plain_fwdbwd"] = out["gcm_fwdbwd"]["tokens_per_s"] / out["plain_fwdbwd"]["tokens_per_s"]
 
     # Global Context Synchronisation split loop, forward (one shard per chunk)
     layer = ttt.TTT(H, D, F, dtype=torch.bfloat16)

@@ -49,9 +49,11 @@ extern "C" {
  * N must be a multiple of 256; M, K >= 1 (ragged edges read zeros); lda, ldb
  * multiples of 8; every pointer 16-byte aligned.  SCAL3R_ERR_UNSUPPORTED
  * otherwise.  The handle carries the status word and the profiler.
- * A float32-output product with fewer 128 x 256 output tiles than half the
- * SMs (a weight gradient: small M and N, long K) runs in K ranges into
- * float32 partial planes in `workspace`, then sums them in a fixed order:
+ * A float32-output product whose output tiles would leave SMs idle through a
+ * long K loop (a weight gradient: small M and N, long K) runs in K ranges into
+ * float32 partial planes in `workspace`, then sums them in a fixed order (the
+ * number of ranges is the one with the least estimated time, counting the
+ * rounds of work over the SMs and the planes' extra traffic):
  * give scal3r_ttt_gemm_workspace_size bytes (device memory, 16-byte aligned,
  * owned by the caller, not touched after the stream reaches the end of the
  * call).  With a smaller or NULL workspace the product runs unsplit; the

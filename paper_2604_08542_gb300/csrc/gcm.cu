@@ -77,7 +77,11 @@ __global__ void __launch_bounds__(256) gcm_norm_eta_kernel(const float* __restri
                                                            float* __restrict__ sig) {
   const int lane = threadIdx.x & 31, d = H * D, nc = d / 8, gph = D / 64;
   const int64_t step = (int64_t)gridDim.x * (blockDim.x / 32);
+  constexpr int kB = 4;   // 8-value chunks of q, k and x per lane in flight at once
   for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; t < T; t += step) {
+    uint4* qr = reinterpret_cast<uint4*>(q + (size_t)t * d);
+    uint4* kr = reinterpret_cast<uint4*>(k + (size_t)t * d);
+    const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)t * d);
     // lane h < H: the norm of q's head h; lane 16 + h: of k's head h
     float n = 0.f;
     const int hh = lane & 15, part = lane >> 4;
@@ -88,32 +92,49 @@ __global__ void __launch_bounds__(256) gcm_norm_eta_kernel(const float* __restri
       n = sqrtf(s);
       (part ? kn : qn)[(size_t)t * H + hh] = n;
     }
-    for (int pt = 0; pt < 2; ++pt) {
-      uint4* row = reinterpret_cast<uint4*>((pt ? k : q) + (size_t)t * d);
-      for (int c = lane; c < nc; c += 32) {
-        const float nn = __shfl_sync(0xffffffffu, n, pt * 16 + (8 * c) / D);
-        const float inv = 1.f / fmaxf(nn, 1e-12f);
-        float f[8];
-        unpack8(row[c], f);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] *= inv;
-        row[c] = pack8(f);
-      }
-    }
     float acc[kMaxHeads];
 #pragma unroll
     for (int h = 0; h < kMaxHeads; ++h) acc[h] = 0.f;
-    const uint4* xr = reinterpret_cast<const uint4*>(x + (size_t)t * d);
-    for (int c = lane; c < nc; c += 32) {
-      float f[8];
-      unpack8(__ldg(xr + c), f);
+    // kB chunks of q, k and x per lane are loaded before any is used, so a
+    // token costs about one memory round trip per kB * 32 chunks, not one
+    // per dependent step
+    for (int c0 = lane; c0 < nc; c0 += 32 * kB) {
+      uint4 qv[kB], kv[kB], xv[kB];
 #pragma unroll
-      for (int h = 0; h < kMaxHeads; ++h) {
-        if (h >= H) break;
-        const float4* wp = reinterpret_cast<const float4*>(w_eta + (size_t)h * d + 8 * c);
-        const float4 a = __ldg(wp), b = __ldg(wp + 1);
-        acc[h] = fmaf(f[0], a.x, fmaf(f[1], a.y, fmaf(f[2], a.z, fmaf(f[3], a.w, acc[h]))));
-        acc[h] = fmaf(f[4], b.x, fmaf(f[5], b.y, fmaf(f[6], b.z, fmaf(f[7], b.w, acc[h]))));
+      for (int b = 0; b < kB; ++b) {
+        const int c = c0 + 32 * b;
+        if (c < nc) {
+          qv[b] = qr[c];
+          kv[b] = kr[c];
+          xv[b] = __ldg(xr + c);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < kB; ++b) {
+        const int c = c0 + 32 * b;
+        const bool in = c < nc;
+        const int hc = in ? (8 * c) / D : 0;
+        const float inq = 1.f / fmaxf(__shfl_sync(0xffffffffu, n, hc), 1e-12f);
+        const float ink = 1.f / fmaxf(__shfl_sync(0xffffffffu, n, 16 + hc), 1e-12f);
+        if (!in) continue;
+        float f[8];
+        unpack8(qv[b], f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] *= inq;
+        qr[c] = pack8(f);
+        unpack8(kv[b], f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] *= ink;
+        kr[c] = pack8(f);
+        unpack8(xv[b], f);
+#pragma unroll
+        for (int h = 0; h < kMaxHeads; ++h) {
+          if (h >= H) break;
+          const float4* wp = reinterpret_cast<const float4*>(w_eta + (size_t)h * d + 8 * c);
+          const float4 a = __ldg(wp), bq = __ldg(wp + 1);
+          acc[h] = fmaf(f[0], a.x, fmaf(f[1], a.y, fmaf(f[2], a.z, fmaf(f[3], a.w, acc[h]))));
+          acc[h] = fmaf(f[4], bq.x, fmaf(f[5], bq.y, fmaf(f[6], bq.z, fmaf(f[7], bq.w, acc[h]))));
+        }
       }
     }
 #pragma unroll
@@ -135,7 +156,10 @@ __global__ void __launch_bounds__(256) gcm_norm_eta_kernel(const float* __restri
 // unit-norm q the layer saw), [2d, 3d) dv, then dlogit = dlr base s (1 - s)
 // for heads h < H and zeros to column 3d + 63.  A head's D values are G =
 // min(32, D/8) lanes' chunks; G lanes reduce its dot with xor shuffles inside
-// their aligned group, 32/G heads at a time.
+// their aligned group, 32/G heads at a time.  Block b takes the kRowBlock
+// tokens from b * kRowBlock; once its rows are written (and still in L2) it
+// sums them per column, in token order, into part[b][ld] (the partial rows of
+// dbqkv and db_eta).
 __global__ void __launch_bounds__(256) gcm_qkv_bwd_kernel(const __nv_bfloat16* __restrict__ dq,
                                                           const __nv_bfloat16* __restrict__ dk,
                                                           const __nv_bfloat16* __restrict__ dv,
@@ -144,12 +168,13 @@ __global__ void __launch_bounds__(256) gcm_qkv_bwd_kernel(const __nv_bfloat16* _
                                                           const __nv_bfloat16* __restrict__ k,
                                                           const float* __restrict__ qn, const float* __restrict__ kn,
                                                           const float* __restrict__ sig, float base, int64_t T, int H,
-                                                          int D, __nv_bfloat16* __restrict__ ext) {
+                                                          int D, __nv_bfloat16* __restrict__ ext,
+                                                          float* __restrict__ part) {
   const int lane = threadIdx.x & 31, d = H * D, nc = d / 8, cph = D / 8;
   const int G = cph < 32 ? cph : 32, hpi = 32 / G, per = cph / G;
   const size_t ld = 3 * (size_t)d + kEtaPad;
-  const int64_t step = (int64_t)gridDim.x * (blockDim.x / 32);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; t < T; t += step) {
+  const int64_t t0 = (int64_t)blockIdx.x * kRowBlock, t1 = min(T, t0 + kRowBlock);
+  for (int64_t t = t0 + threadIdx.x / 32; t < t1; t += blockDim.x / 32) {
     __nv_bfloat16* out = ext + (size_t)t * ld;
     for (int part = 0; part < 2; ++part) {
       const uint4* gg = reinterpret_cast<const uint4*>((part ? dk : dq) + (size_t)t * d);
@@ -191,6 +216,22 @@ __global__ void __launch_bounds__(256) gcm_qkv_bwd_kernel(const __nv_bfloat16* _
       out[3 * (size_t)d + col] = __float2bfloat16(g);
     }
   }
+  // the block's rows are written: their column sums, 8 columns per thread
+  __syncthreads();
+  for (int v = threadIdx.x; v < (int)(ld / 8); v += blockDim.x) {
+    float acc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int64_t t = t0; t < t1; ++t) {
+      float f[8];
+      unpack8(reinterpret_cast<const uint4*>(ext + (size_t)t * ld)[v], f);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[e] += f[e];
+    }
+    float4* o = reinterpret_cast<float4*>(part + (size_t)blockIdx.x * ld + 8 * v);
+    o[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    o[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+  }
 }
 
 // Per kRowBlock-token block, column sums of a bf16 [T][ncol] array (or of the
@@ -223,13 +264,38 @@ __global__ void colsum8_part_kernel(const __nv_bfloat16* __restrict__ a, const _
 }
 
 // Column sums of `rows` partial rows (`stride` floats apart), columns
-// 0 .. n-1, in row order.
-__global__ void colsum_kernel(const float* __restrict__ part, int64_t rows, int stride, int n, float* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// 0 .. n-1.  A block takes 32 columns (lane = column); warp w sums rows
+// w, w + 8, w + 16, ... in order, and the eight warp sums are added in warp
+// order, so the result is the same on every run.
+constexpr int kColsumWarps = 8;
+__global__ void __launch_bounds__(32 * kColsumWarps) colsum_kernel(const float* __restrict__ part, int64_t rows,
+                                                                    int stride, int n, float* __restrict__ out) {
+  __shared__ float ws[kColsumWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
   float s = 0.f;
-  for (int64_t r = 0; r < rows; ++r) s += part[(size_t)r * stride + j];
-  out[j] = s;
+  if (j < n) {
+    const float* pc = part + j;
+    int64_t r = w;
+    // four independent loads in flight, added in row order
+    for (; r + 3 * kColsumWarps < rows; r += 4 * kColsumWarps) {
+      const float a = pc[(size_t)r * stride], b = pc[(size_t)(r + kColsumWarps) * stride];
+      const float c = pc[(size_t)(r + 2 * kColsumWarps) * stride], d = pc[(size_t)(r + 3 * kColsumWarps) * stride];
+      s += a;
+      s += b;
+      s += c;
+      s += d;
+    }
+    for (; r < rows; r += kColsumWarps) s += pc[(size_t)r * stride];
+  }
+  ws[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && j < n) {
+    float t = ws[0][lane];
+#pragma unroll
+    for (int i = 1; i < kColsumWarps; ++i) t += ws[i][lane];
+    out[j] = t;
+  }
 }
 
 // Row j of a [rows][cols] matrix scaled by alpha[j]: a bf16 copy (Wo with
@@ -323,7 +389,7 @@ cudaError_t gcm_out_backward(const void* d_out, const void* o, const void* wo, c
   scale_rows_f32_kernel<<<grid_of((int64_t)d * d, 256, 4 * sms), 256, 0, st>>>(dwo, alpha, d, d);
   colsum8_part_kernel<true><<<dim3((unsigned)nb, (d / 8 + 255) / 256), 256, 0, st>>>(
       static_cast<const __nv_bfloat16*>(y), static_cast<const __nv_bfloat16*>(d_out), T, d, part);
-  colsum_kernel<<<(d + 255) / 256, 256, 0, st>>>(part, nb, d, d, dalpha);
+  colsum_kernel<<<(d + 31) / 32, 32 * kColsumWarps, 0, st>>>(part, nb, d, d, dalpha);
   return cudaGetLastError();
 }
 
@@ -359,12 +425,11 @@ cudaError_t gcm_qkv_backward(const void* dq, const void* dk, const void* dv, con
   void* gws2 = c;   // the split planes of the dw_eta product (its own region: it splits, dWqkv may not)
   const size_t gwb2 = wide_gemm_workspace_bytes(kEtaPad, d, T, 1);
   using bf = __nv_bfloat16;
-  gcm_qkv_bwd_kernel<<<grid_of(T, 8, 8 * sms), 256, 0, st>>>(
+  gcm_qkv_bwd_kernel<<<(unsigned)nb, 256, 0, st>>>(
       static_cast<const bf*>(dq), static_cast<const bf*>(dk), static_cast<const bf*>(dv), dlr,
-      static_cast<const bf*>(q), static_cast<const bf*>(k), qn, kn, sig, base, T, H, D, ext);
-  colsum8_part_kernel<false><<<dim3((unsigned)nb, (ld / 8 + 255) / 256), 256, 0, st>>>(ext, nullptr, T, ld, part);
-  colsum_kernel<<<(3 * d + 255) / 256, 256, 0, st>>>(part, nb, ld, 3 * d, dbqkv);
-  colsum_kernel<<<1, 32, 0, st>>>(part + 3 * d, nb, ld, H, db_eta);
+      static_cast<const bf*>(q), static_cast<const bf*>(k), qn, kn, sig, base, T, H, D, ext, part);
+  colsum_kernel<<<(3 * d + 31) / 32, 32 * kColsumWarps, 0, st>>>(part, nb, ld, 3 * d, dbqkv);
+  colsum_kernel<<<1, 32 * kColsumWarps, 0, st>>>(part + 3 * d, nb, ld, H, db_eta);
   cudaError_t e = cudaMemcpyAsync(bext, wqkv, (size_t)3 * d * d * 2, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
   eta_rows_kernel<<<grid_of((int64_t)kEtaPad * d, 256, 4 * sms), 256, 0, st>>>(w_eta, H, d, bext + (size_t)3 * d * d);

@@ -330,6 +330,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
     const uint32_t accb = tb + lane_base + gp * 256;
     int i = gp;
     for (int u = blockIdx.x + gp * gridDim.x; u < nunits; u += 2 * gridDim.x, i += 2) {
+      if (!XSET && (g.epi == EPI_GCM_GATE || g.epi == EPI_F32_ADDIN)) {
+        // the row's addend (x, or the residual gradient) of this group's next
+        // tile (and of its first) into L2 while products finish: the column
+        // loop below then waits on L2, not HBM
+        for (int up = (i == gp ? u : u + 2 * (int)gridDim.x); up <= u + 2 * (int)gridDim.x && up < nunits;
+             up += 2 * (int)gridDim.x) {
+          const int tp = up % ntiles;
+          const int mp = (tp / tiles_n) * BM + (int)row, np = (tp % tiles_n) * BN;
+          if (mp < g.M) {
+            const __nv_bfloat16* src = g.in0 + (size_t)mp * (g.ld_in ? g.ld_in : g.ld_out) + np;
+            if (in_bounds(src, BN * 2)) bulk_prefetch_l2(src, BN * 2);
+          }
+        }
+      }
       if (!mbar_wait(&acc_full[gp], (i >> 1) & 1, abort)) break;
       tc_fence_after();
       const int t = u % ntiles;
@@ -517,50 +531,59 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) wide_gemm_kernel(const __grid
         }
       } else if (!XSET && (g.epi == EPI_GCM_GATE || g.epi == EPI_F32_ADDIN)) {
         const int64_t ldi = g.ld_in ? g.ld_in : g.ld_out;
+        // the addend in batches of 64 columns: eight 16-byte loads in flight
+        // per thread, so a tile waits four memory round trips, not eight
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 32) {
-          float v0[16], v1[16];
-          tmem_ld16(accb + c, v0);
-          tmem_ld16(accb + c + 16, v1);
-          if (!valid) continue;
-          const uint4* xin = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c);
-          if (!in_bounds(xin, 64)) continue;
-          float xv[32];
+        for (int c0 = 0; c0 < BN; c0 += 64) {
+          const uint4* xin = reinterpret_cast<const uint4*>(g.in0 + (size_t)m * ldi + n0 + c0);
+          const bool okx = valid && in_bounds(xin, 128);
+          uint4 xw[8];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint4 w = xin[j];
-            const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+          for (int j = 0; j < 8; ++j) xw[j] = okx ? xin[j] : make_uint4(0, 0, 0, 0);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              xv[8 * j + 2 * e] = bf16_lo(ww[e]);
-              xv[8 * j + 2 * e + 1] = bf16_hi(ww[e]);
-            }
-          }
-          if (g.epi == EPI_F32_ADDIN) {
-            float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c);
-            if (!in_bounds(o, 128)) continue;
+          for (int cc = 0; cc < 64; cc += 32) {
+            const int c = c0 + cc;
+            float v0[16], v1[16];
+            tmem_ld16(accb + c, v0);
+            tmem_ld16(accb + c + 16, v1);
+            if (!okx) continue;
+            float xv[32];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              o[j] = make_float4(v0[4 * j] + xv[4 * j], v0[4 * j + 1] + xv[4 * j + 1], v0[4 * j + 2] + xv[4 * j + 2],
-                                 v0[4 * j + 3] + xv[4 * j + 3]);
-              o[4 + j] = make_float4(v1[4 * j] + xv[16 + 4 * j], v1[4 * j + 1] + xv[17 + 4 * j],
-                                     v1[4 * j + 2] + xv[18 + 4 * j], v1[4 * j + 3] + xv[19 + 4 * j]);
-            }
-          } else {
-            const size_t off = (size_t)m * g.ld_out + n0 + c;
-            __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off;
-            st_bf16x16(yo, v0);
-            st_bf16x16(yo + 16, v1);
-            const float* al = g.colvec + n0 + c;
-            if (!in_bounds(al, 128)) continue;
+              const uint4 w = xw[cc / 8 + j];
+              const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              v0[i] = fmaf(al[i], v0[i], xv[i]);
-              v1[i] = fmaf(al[16 + i], v1[i], xv[16 + i]);
+              for (int e = 0; e < 4; ++e) {
+                xv[8 * j + 2 * e] = bf16_lo(ww[e]);
+                xv[8 * j + 2 * e + 1] = bf16_hi(ww[e]);
+              }
             }
-            __nv_bfloat16* oo = reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off;
-            st_bf16x16(oo, v0);
-            st_bf16x16(oo + 16, v1);
+            if (g.epi == EPI_F32_ADDIN) {
+              float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(g.out[0]) + (size_t)m * g.ld_out + n0 + c);
+              if (!in_bounds(o, 128)) continue;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                o[j] = make_float4(v0[4 * j] + xv[4 * j], v0[4 * j + 1] + xv[4 * j + 1], v0[4 * j + 2] + xv[4 * j + 2],
+                                   v0[4 * j + 3] + xv[4 * j + 3]);
+                o[4 + j] = make_float4(v1[4 * j] + xv[16 + 4 * j], v1[4 * j + 1] + xv[17 + 4 * j],
+                                       v1[4 * j + 2] + xv[18 + 4 * j], v1[4 * j + 3] + xv[19 + 4 * j]);
+              }
+            } else {
+              const size_t off = (size_t)m * g.ld_out + n0 + c;
+              __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(g.out[1]) + off;
+              st_bf16x16(yo, v0);
+              st_bf16x16(yo + 16, v1);
+              const float* al = g.colvec + n0 + c;
+              if (!in_bounds(al, 128)) continue;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                v0[i] = fmaf(al[i], v0[i], xv[i]);
+                v1[i] = fmaf(al[16 + i], v1[i], xv[16 + i]);
+              }
+              __nv_bfloat16* oo = reinterpret_cast<__nv_bfloat16*>(g.out[0]) + off;
+              st_bf16x16(oo, v0);
+              st_bf16x16(oo + 16, v1);
+            }
           }
         }
       } else if (XSET) {   // EPI_BKEY
@@ -1229,11 +1252,43 @@ cudaError_t run_gemm_red(const Ctx& c, GemmArgs& a, double flops, float* spl) {
   });
 }
 
+// K ranges of a float32-output product of the C ABI (scal3r_ttt_gemm, and the
+// GCM module's weight gradients): the count s with the least estimated time,
+// rounds of work units (tiles x ranges over the SMs) times K blocks per range,
+// at about 0.34 us per K block of a 128 x 256 tile on one SM (four M128 N256
+// K16 MMAs at the measured rate), plus the partial planes' extra traffic
+// (written by the GEMM, read by the reduce: 8 s M N bytes at about 6.5 TB/s).
+// A larger count is taken only when it saves at least 3 %.  Unlike
+// split_count, the count may fall as K grows: these callers size the
+// workspace for the product they run (and run unsplit without it).
+int api_split_count(int64_t M, int64_t N, int64_t K, int out_fp32) {
+  if (!out_fp32) return 1;
+  const int64_t tiles = ((M + BM - 1) / BM) * (N / BN);
+  const int64_t nk = (K + BK - 1) / BK;
+  const int64_t sms = num_sms();
+  if (tiles <= 0 || nk < 8 || sms <= 0) return 1;
+  auto est_us = [&](int64_t s) {
+    const int64_t kb = (nk + s - 1) / s, ranges = (nk + kb - 1) / kb;
+    const int64_t rounds = (tiles * ranges + sms - 1) / sms;
+    return (double)(rounds * kb) * 0.34 + (ranges > 1 ? 8.0 * (double)ranges * M * N / 6.5e6 : 0.0);
+  };
+  int best = 1;
+  double bt = est_us(1);
+  for (int64_t s = 2; s <= 64 && nk / s >= 4; ++s) {
+    const double t = est_us(s);
+    if (t < 0.97 * bt) {
+      bt = t;
+      best = (int)s;
+    }
+  }
+  return best;
+}
+
 }  // namespace
 
 size_t wide_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int out_fp32) {
   if (M <= 0 || N <= 0 || K <= 0 || N % BN != 0) return 0;
-  const int s = split_count(M, N, K, out_fp32);
+  const int s = api_split_count(M, N, K, out_fp32);
   return s > 1 ? (size_t)s * M * N * sizeof(float) : 0;
 }
 
@@ -1330,7 +1385,7 @@ cudaError_t wide_gemm_bf16(const void* a, int64_t lda, int a_kmajor, const void*
   g.ld_out = ldc;
   g.status = status;
   g.timeout_test = timeout_test;
-  const int S = split_count(M, N, K, out_fp32);
+  const int S = api_split_count(M, N, K, out_fp32);
   const size_t need = S > 1 ? (size_t)S * M * N * sizeof(float) : 0;
   if (S <= 1 || !ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 15) != 0) return gemm(g, st);
   const int nk = (int)((K + BK - 1) / BK);
