@@ -575,6 +575,8 @@ bf16_bsweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const W
     tmem_alloc(&B.tmem_base, 512);
     tmem_relinquish();
   }
+  // the weights and the adjoint R come from the kernels ahead of this one
+  pdl_wait();
   if (warp >= EPI0 && warp < EPI0 + 8) {
     if (key) load_weights_key(w, r, sm);
     else tl::load_weights<EPI0>(w, sm);
@@ -657,8 +659,7 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
       !make_map(&maps.s_dk, prm.dk, prm.T, prm.H, 64) || !make_map(&maps.s_dv, prm.dv, prm.T, prm.H, 64) ||
       !make_map(&maps.s_dq, prm.dq, prm.T, prm.H, 64))
     return cudaErrorInvalidValue;
-  bf16_bsweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items);
-  return cudaGetLastError();
+  return launch_pdl(bf16_bsweep_kernel, dim3(n), dim3(NTHREADS), DYN_SMEM, st, maps, prm, items);
 }
 
 }  // namespace scal3r

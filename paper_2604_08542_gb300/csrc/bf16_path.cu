@@ -312,6 +312,8 @@ bf16_sweep_kernel(const __grid_constant__ TmaMaps maps, const Params p, const Wo
   __syncthreads();
   tc_fence_after();
   const uint32_t tb = B.tmem_base;
+  // the step's weights come from the kernel ahead of this one
+  pdl_wait();
 
   // weights
   if (warp >= 2 && warp < 10) {
@@ -378,8 +380,7 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, i
   if (!make_token_map(&maps.q, prm.q, prm.T, prm.H, QT) || !make_token_map(&maps.k, prm.k, prm.T, prm.H, 64) ||
       !make_token_map(&maps.v, prm.v, prm.T, prm.H, 64))
     return cudaErrorInvalidValue;
-  bf16_sweep_kernel<<<n, NTHREADS, DYN_SMEM, st>>>(maps, prm, items, step);
-  return cudaGetLastError();
+  return launch_pdl(bf16_sweep_kernel, dim3(n), dim3(NTHREADS), DYN_SMEM, st, maps, prm, items, step);
 }
 
 }  // namespace scal3r

@@ -95,6 +95,7 @@ __device__ __forceinline__ float row_target(const Params& p, float ss) {
 // Copy the starting weights of every chain into master buffer 0 and compute
 // the row-norm targets.
 __global__ void prep_kernel(Params p) {
+  pdl_wait();
   const int chain = blockIdx.x;
   const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
@@ -109,6 +110,7 @@ __global__ void prep_kernel(Params p) {
 //   W~ = W_step + sum_slots partial (fixed slot order),
 //   W_{step+1} row = W~ row * rho / max(||W~ row||, eps).
 __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int step) {
+  pdl_wait();
   const UpdateItem u = upd[blockIdx.x];
   const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
@@ -138,6 +140,7 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
 // Backward: zero the carried row-norm adjoints and per-chain dW0, compute
 // the row-norm targets from w0.
 __global__ void bprep_kernel(Params p) {
+  pdl_wait();
   const int chain = blockIdx.x;
   const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
@@ -159,6 +162,7 @@ __global__ void bprep_kernel(Params p) {
 //   unclamped  R = (rho / ||w~||) (lambda - w_hat (w_hat . lambda))
 //   clamped    R = (rho / eps) lambda;      drho += w_hat . lambda in both
 __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int step) {
+  pdl_wait();
   (void)step;
   const UpdateItem u = upd[blockIdx.x];
   const RowSlice s = row_slice(blockIdx.y, p.D, p.F);
@@ -205,6 +209,7 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
 // dw0 from the per-chain results: summed over sequences in order when w0 is
 // shared, copied per sequence otherwise.
 __global__ void bfinal_kernel(Params p) {
+  pdl_wait();
   const int P = 3 * p.F * p.D;
   const int h = blockIdx.y;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
@@ -332,27 +337,23 @@ bool update_shape_supported(int D, int F) {
 
 cudaError_t launch_prep(const Params& prm, int chains, cudaStream_t st) {
   if (chains == 0) return cudaSuccess;
-  prep_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm);
-  return cudaGetLastError();
+  return launch_pdl(prep_kernel, dim3(chains, row_blocks(prm)), dim3(kThreads), 0, st, prm);
 }
 
 cudaError_t launch_update(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st) {
   if (nupd == 0) return cudaSuccess;
-  update_kernel<<<dim3(nupd, row_blocks(prm)), kThreads, 0, st>>>(prm, upd, step);
-  return cudaGetLastError();
+  return launch_pdl(update_kernel, dim3(nupd, row_blocks(prm)), dim3(kThreads), 0, st, prm, upd, step);
 }
 
 cudaError_t launch_bupdate(const Params& prm, const UpdateItem* upd, int nupd, int step, cudaStream_t st) {
   if (nupd == 0) return cudaSuccess;
-  bupdate_kernel<<<dim3(nupd, row_blocks(prm)), kThreads, 0, st>>>(prm, upd, step);
-  return cudaGetLastError();
+  return launch_pdl(bupdate_kernel, dim3(nupd, row_blocks(prm)), dim3(kThreads), 0, st, prm, upd, step);
 }
 
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st);
 cudaError_t launch_bprep(const Params& prm, int chains, cudaStream_t st) {
   if (chains == 0) return cudaSuccess;
-  bprep_kernel<<<dim3(chains, row_blocks(prm)), kThreads, 0, st>>>(prm);
-  return cudaGetLastError();
+  return launch_pdl(bprep_kernel, dim3(chains, row_blocks(prm)), dim3(kThreads), 0, st, prm);
 }
 
 cudaError_t launch_gsum(const Params& prm, const UpdateItem* upd, int nupd, float* grad, cudaStream_t st) {
@@ -397,8 +398,7 @@ cudaError_t launch_gcs_update(const Params& prm, int chains, const float* w, int
 cudaError_t launch_bfinal(const Params& prm, cudaStream_t st) {
   const int P = 3 * prm.F * prm.D;
   dim3 grid((P + 255) / 256, prm.H);
-  bfinal_kernel<<<grid, 256, 0, st>>>(prm);
-  return cudaGetLastError();
+  return launch_pdl(bfinal_kernel, grid, dim3(256), 0, st, prm);
 }
 
 }  // namespace scal3r
