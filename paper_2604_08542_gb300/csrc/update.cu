@@ -123,13 +123,17 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
     return;
   }
   float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+  float rho = 1.f;
   if (s.valid) {
+    // the row target is loaded before the slot sum so that its round trip
+    // overlaps the sum's
+    if (p.norm != SCAL3R_NORM_NONE) rho = p.rho[(size_t)u.chain * R + s.r];
     x = add_slots(ld4(wcur + s.off), p.part, u.slot0, u.nslots, P, s.off);
   }
   const float n = sqrtf(group_sum(dot4(x, x), s.group));
   if (!s.valid) return;
   float scale = 1.f;
-  if (p.norm != SCAL3R_NORM_NONE) scale = p.rho[(size_t)u.chain * R + s.r] / fmaxf(n, p.eps);
+  if (p.norm != SCAL3R_NORM_NONE) scale = rho / fmaxf(n, p.eps);
   const float4 w = scale4(x, scale);
   st4(wnext + s.off, w);
   if (p.w_ckpt && u.wslot >= 0) st4(p.w_ckpt + ((size_t)u.wslot * p.H + h) * P + s.off, w);
@@ -169,17 +173,28 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
   const int P = 3 * p.F * p.D, R = 2 * p.F + p.D;
   const int h = u.chain % p.H;
   float* rb = p.rbuf + (size_t)u.chain * P;
+  // every load that does not depend on the slot sum is issued before it, so
+  // that their round trips overlap the sum's
+  const bool norm_vjp = !u.first && p.norm != SCAL3R_NORM_NONE;
+  float rho = 0.f, drho = 0.f, n = 0.f;
+  float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), wck = w0;
   float4 lam = make_float4(0.f, 0.f, 0.f, 0.f);
   if (s.valid) {
+    rho = p.rho[(size_t)u.chain * R + s.r];
+    if (u.first) {
+      if (p.norm == SCAL3R_NORM_ROW_W0) drho = p.drho[(size_t)u.chain * R + s.r];
+      w0 = ld4(chain_w0(p, u.chain) + s.off);
+    } else if (norm_vjp) {
+      wck = ld4(p.w_ckpt_in + ((size_t)u.wslot * p.H + h) * P + s.off);
+      n = p.wnorm_in[((size_t)u.chunk * p.H + h) * R + s.r];
+    }
     if (!u.last) lam = ld4(rb + s.off);
     lam = add_slots(lam, p.part, u.slot0, u.nslots, P, s.off);
   }
-  const float rho = s.valid ? p.rho[(size_t)u.chain * R + s.r] : 0.f;
   if (u.first) {
     if (!s.valid) return;
     float coef = 0.f;
-    if (p.norm == SCAL3R_NORM_ROW_W0 && rho > 0.f) coef = p.drho[(size_t)u.chain * R + s.r] / rho;
-    const float4 w0 = ld4(chain_w0(p, u.chain) + s.off);
+    if (p.norm == SCAL3R_NORM_ROW_W0 && rho > 0.f) coef = drho / rho;
     st4(p.dw0_chain + (size_t)u.chain * P + s.off,
         make_float4(lam.x + coef * w0.x, lam.y + coef * w0.y, lam.z + coef * w0.z, lam.w + coef * w0.w));
     return;
@@ -189,11 +204,9 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
     return;
   }
   const float inv_rho = rho > 0.f ? 1.f / rho : 0.f;
-  float4 what = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (s.valid) what = scale4(ld4(p.w_ckpt_in + ((size_t)u.wslot * p.H + h) * P + s.off), inv_rho);
+  const float4 what = scale4(wck, inv_rho);
   const float proj = group_sum(dot4(what, lam), s.group);
   if (!s.valid) return;
-  const float n = p.wnorm_in[((size_t)u.chunk * p.H + h) * R + s.r];
   float4 out;
   if (!(n >= p.eps)) {
     out = scale4(lam, rho / p.eps);
