@@ -72,12 +72,15 @@ def test_gcm_module_four_heads_one_token_chunk():
 
 
 @pytest.mark.parametrize("M,N,K,a_kmajor,b_kmajor", [(64, 1024, 8192, 0, 0), (1024, 512, 4100, 0, 0),
-                                                      (300, 256, 2048, 1, 1)])
+                                                      (300, 256, 2048, 1, 1), (2560, 1024, 16384, 0, 0)])
 def test_gemm_split_k_matches_reference(M, N, K, a_kmajor, b_kmajor):
     """The GEMM entry point on weight-gradient shapes (few output tiles, long K),
     where it runs in K ranges with a fixed-order sum: against an FP64 product of
     the same bf16 operands, against the unsplit run, accumulating into C, and
-    bitwise equal run to run."""
+    bitwise equal run to run.  2560 x 1024 has 80 output tiles, more than half
+    the SMs: the range count comes from the estimate of rounds of work and
+    plane traffic, which splits it (one wave of 80 tiles leaves 72 SMs idle
+    for the whole K loop)."""
     import torch
     import paper_2604_08542_gb300 as ttt
     g = torch.Generator().manual_seed(M + N + K)
@@ -92,7 +95,7 @@ def test_gemm_split_k_matches_reference(M, N, K, a_kmajor, b_kmajor):
     h = layer.handle
     st = torch.cuda.current_stream().cuda_stream
     nbytes = ttt.scal3r_ttt_gemm_workspace_size(h, M, N, K, True)
-    if M <= 128 or M * N <= 512 * 1024:
+    if M <= 128 or M * N <= 512 * 1024 or (M, N) == (2560, 1024):
         assert nbytes > 0          # these shapes take the split path
     ws = torch.empty(max(nbytes, 16), dtype=torch.uint8, device="cuda")
 
