@@ -376,12 +376,13 @@ int scal3r_ttt_set_finite_check(scal3r_ttt_handle* handle, int32_t enable);
 
 /* Bounds checking.  A library built with SCAL3R_DEBUG_BOUNDS (the build
  * script's "bounds" variant) registers, for each scal3r_ttt_forward and
- * scal3r_ttt_backward call on a wide-weight handle (head_dim and hidden
- * multiples of 256), the byte range of every tensor the call was given and of
- * its workspace.  Every plain global load and store of the wide-weight
- * kernels must then fall inside one of them; one that does not is skipped
- * (a load reads zeros) and the status word becomes SCAL3R_ERR_BOUNDS.  TMA
- * copies are bounded by their tensor maps and are not checked here.  The
+ * scal3r_ttt_backward call on a bfloat16 handle (the wide-weight path, or the
+ * fused head_dim-64 kernels), the byte range of every tensor the call was
+ * given and of its workspace.  Every plain global load and store of those
+ * kernels and of the update kernels between them must then fall inside one
+ * of them; one that does not is skipped (a load reads zeros) and the status
+ * word becomes SCAL3R_ERR_BOUNDS.  TMA copies are bounded by their tensor
+ * maps and are not checked here; nor are the float32 and linear paths.  The
  * extents registered are:
  *   q, k, v, o, d_o, dq, dk, dv: T*H*D elements of the dtype;
  *   lr, dlr: T*H (or T*H*3) floats;  w0, dw0: H*P floats, or

@@ -155,7 +155,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
 #pragma unroll
   for (int j = 0; j < NR; ++j)
     eta_next[j] = (warp >= EPI0 && warp < EPI0 + 8 && t0 + (int64_t)row < t1)
-                      ? p.lr[((size_t)(t0 + row) * H + h) * NR + j] : 0.f;
+                      ? ld_chk(p.lr + ((size_t)(t0 + row) * H + h) * NR + j) : 0.f;
 
   // pass B stage use counts (parity per stage), kept alike by the producer
   // and the MMA thread
@@ -322,7 +322,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
           if (!mbar_wait_spin(&B.eta_full[e], (i >> 1) & 1, abort)) return false;
           if (valid) {
 #pragma unroll
-            for (int j = 0; j < NR; ++j) p.dlr[((size_t)tok * H + h) * NR + j] = dprev[j] + eta_red[j * BT + row];
+            for (int j = 0; j < NR; ++j) st_chk(p.dlr + ((size_t)tok * H + h) * NR + j, dprev[j] + eta_red[j * BT + row]);
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&B.eta_free[e]);
@@ -340,7 +340,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
             dprev[j] = deta[j];
             eta[j] = eta_next[j];
             deta[j] = 0.f;
-            eta_next[j] = (i + 1 < ntiles && tn < t1) ? p.lr[((size_t)tn * H + h) * NR + j] : 0.f;
+            eta_next[j] = (i + 1 < ntiles && tn < t1) ? ld_chk(p.lr + ((size_t)tn * H + h) * NR + j) : 0.f;
           }
         }
         if (!mbar_wait_spin(&B.g_full, n & 1, abort)) break;
@@ -661,5 +661,9 @@ cudaError_t launch_bf16_bsweep(const Params& prm, const WorkItem* items, int n, 
     return cudaErrorInvalidValue;
   return launch_pdl(bf16_bsweep_kernel, dim3(n), dim3(NTHREADS), DYN_SMEM, st, maps, prm, items);
 }
+
+#ifdef SCAL3R_DEBUG_BOUNDS
+cudaError_t bf16_bwd_upload_bounds(const BoundsTable& t, cudaStream_t st) { return upload_bounds_table(t, st); }
+#endif
 
 }  // namespace scal3r

@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 
 #include "bf16_token_lane.cuh"
+#include "bounds.cuh"
 #include "sm100.cuh"
 #include "ttt_internal.h"
 
@@ -85,16 +86,16 @@ __device__ void apply_load_weights(const float* w, uint8_t* sm) {
   for (int i = 0; i < N13; ++i) {
     const int c = t + 256 * i;
     const float4* src = reinterpret_cast<const float4*>(w + (size_t)(c >> 3) * D + (c & 7) * 8);
-    v[i][0] = __ldg(src);
-    v[i][1] = __ldg(src + 1);
+    v[i][0] = ldg_chk(src);
+    v[i][1] = ldg_chk(src + 1);
   }
   const float* w2 = w + 2 * (size_t)F * D;
 #pragma unroll
   for (int i = 0; i < N2; ++i) {
     const int c = t + 256 * i;
     const float4* src = reinterpret_cast<const float4*>(w2 + (size_t)(c / (F / 8)) * F + (c % (F / 8)) * 8);
-    v[N13 + i][0] = __ldg(src);
-    v[N13 + i][1] = __ldg(src + 1);
+    v[N13 + i][0] = ldg_chk(src);
+    v[N13 + i][1] = ldg_chk(src + 1);
   }
 #pragma unroll
   for (int i = 0; i < N13 + N2; ++i) {
@@ -193,7 +194,7 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
       uint32_t vw[16];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const uint4 x = vv[c];
+        const uint4 x = ld_chk(vv + c);
         vw[4 * c] = x.x;
         vw[4 * c + 1] = x.y;
         vw[4 * c + 2] = x.z;
@@ -209,10 +210,14 @@ __device__ void apply_role(const TmaMaps& maps, const Params& p, const WorkItem&
     }
     if (tok < t1) {
       uint4* dst = reinterpret_cast<uint4*>(o + ((size_t)tok * p.H + h) * D + 32 * half);
-      dst[0] = make_uint4(pack_bf16(v0[0], v0[1]), pack_bf16(v0[2], v0[3]), pack_bf16(v0[4], v0[5]), pack_bf16(v0[6], v0[7]));
-      dst[1] = make_uint4(pack_bf16(v0[8], v0[9]), pack_bf16(v0[10], v0[11]), pack_bf16(v0[12], v0[13]), pack_bf16(v0[14], v0[15]));
-      dst[2] = make_uint4(pack_bf16(v1[0], v1[1]), pack_bf16(v1[2], v1[3]), pack_bf16(v1[4], v1[5]), pack_bf16(v1[6], v1[7]));
-      dst[3] = make_uint4(pack_bf16(v1[8], v1[9]), pack_bf16(v1[10], v1[11]), pack_bf16(v1[12], v1[13]), pack_bf16(v1[14], v1[15]));
+      st_chk(dst, make_uint4(pack_bf16(v0[0], v0[1]), pack_bf16(v0[2], v0[3]), pack_bf16(v0[4], v0[5]),
+                             pack_bf16(v0[6], v0[7])));
+      st_chk(dst + 1, make_uint4(pack_bf16(v0[8], v0[9]), pack_bf16(v0[10], v0[11]), pack_bf16(v0[12], v0[13]),
+                                 pack_bf16(v0[14], v0[15])));
+      st_chk(dst + 2, make_uint4(pack_bf16(v1[0], v1[1]), pack_bf16(v1[2], v1[3]), pack_bf16(v1[4], v1[5]),
+                                 pack_bf16(v1[6], v1[7])));
+      st_chk(dst + 3, make_uint4(pack_bf16(v1[8], v1[9]), pack_bf16(v1[10], v1[11]), pack_bf16(v1[12], v1[13]),
+                                 pack_bf16(v1[14], v1[15])));
     }
     return true;
   };
@@ -382,5 +387,9 @@ cudaError_t launch_bf16_sweep(const Params& prm, const WorkItem* items, int n, i
     return cudaErrorInvalidValue;
   return launch_pdl(bf16_sweep_kernel, dim3(n), dim3(NTHREADS), DYN_SMEM, st, maps, prm, items, step);
 }
+
+#ifdef SCAL3R_DEBUG_BOUNDS
+cudaError_t bf16_fwd_upload_bounds(const BoundsTable& t, cudaStream_t st) { return upload_bounds_table(t, st); }
+#endif
 
 }  // namespace scal3r

@@ -27,6 +27,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "bounds.cuh"
 #include "sm100.cuh"
 #include "ttt_internal.h"
 
@@ -95,10 +96,10 @@ __device__ __forceinline__ void stage_row64(uint8_t* base, uint32_t row, int hal
 
 __device__ __forceinline__ void store_row64(__nv_bfloat16* dst0, int half, const float* v0, const float* v1) {
   uint4* dst = reinterpret_cast<uint4*>(dst0 + 32 * half);
-  dst[0] = pack8(v0);
-  dst[1] = pack8(v0 + 8);
-  dst[2] = pack8(v1);
-  dst[3] = pack8(v1 + 8);
+  st_chk(dst, pack8(v0));
+  st_chk(dst + 1, pack8(v0 + 8));
+  st_chk(dst + 2, pack8(v1));
+  st_chk(dst + 3, pack8(v1 + 8));
 }
 
 // The L sums of the piece (TMEM lanes = hidden unit) -> its slot, in the
@@ -119,7 +120,7 @@ __device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
       tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
       float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
 #pragma unroll
-      for (int x = 0; x < 4; ++x) dst[x] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
+      for (int x = 0; x < 4; ++x) st_chk(dst + x, make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]));
     }
   }
   // L2t[f][d] is the W2[d][f] entry: stored in W2's orientation
@@ -128,7 +129,7 @@ __device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
     float v[16];
     tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) slot[2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row] = v[j];
+    for (int j = 0; j < 16; ++j) st_chk(slot + 2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row, v[j]);
   }
 }
 
@@ -159,13 +160,13 @@ __device__ void load_weight_chunks(const float* w, const float* r, uint8_t* dst,
       if (blk < 4) {   // W1, W3, R1, R3: row f
         const float4* src = reinterpret_cast<const float4*>(
             (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col);
-        const float4 a = __ldg(src), bq = __ldg(src + 1);
+        const float4 a = ldg_chk(src), bq = ldg_chk(src + 1);
         v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
         v[i][4] = bq.x; v[i][5] = bq.y; v[i][6] = bq.z; v[i][7] = bq.w;
       } else {         // W2, R2 [D][F]: column f
         const float* src = (blk == 4 ? w : r) + 2 * (size_t)F * D + f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[i][j] = __ldg(src + (size_t)(col + j) * F);
+        for (int j = 0; j < 8; ++j) v[i][j] = ldg_chk(src + (size_t)(col + j) * F);
       }
     }
 #pragma unroll
@@ -315,11 +316,11 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
       const bool valid = tok < t1;
       if (!DQ && q == 0) {
         if (PM) {
-          eta = valid ? p.lr[((size_t)tok * H + h) * 3] : 0.f;
-          eta3 = valid ? p.lr[((size_t)tok * H + h) * 3 + 1] : 0.f;
-          eta2 = valid ? p.lr[((size_t)tok * H + h) * 3 + 2] : 0.f;
+          eta = valid ? ld_chk(p.lr + ((size_t)tok * H + h) * 3) : 0.f;
+          eta3 = valid ? ld_chk(p.lr + ((size_t)tok * H + h) * 3 + 1) : 0.f;
+          eta2 = valid ? ld_chk(p.lr + ((size_t)tok * H + h) * 3 + 2) : 0.f;
         } else {
-          eta = valid ? p.lr[(size_t)tok * H + h] : 0.f;
+          eta = valid ? ld_chk(p.lr + (size_t)tok * H + h) : 0.f;
         }
       }
       if (!mbar_wait_spin(&B.ga_full[b], (n >> 1) & 1, abort)) break;

@@ -51,4 +51,19 @@ inline cudaError_t upload_bounds_table(const BoundsTable& t, cudaStream_t st) {
 __device__ __forceinline__ constexpr bool in_bounds(const void*, uint32_t) { return true; }
 #endif
 
+// Checked plain accesses: a skipped load reads zero.  In the normal build
+// these are the plain access.
+template <typename T>
+__device__ __forceinline__ T ld_chk(const T* p) {
+  return in_bounds(p, sizeof(T)) ? *p : T{};
+}
+template <typename T>
+__device__ __forceinline__ void st_chk(T* p, const T& v) {
+  if (in_bounds(p, sizeof(T))) *p = v;
+}
+__device__ __forceinline__ float4 ldg_chk(const float4* p) {
+  return in_bounds(p, sizeof(float4)) ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float ldg_chk(const float* p) { return in_bounds(p, sizeof(float)) ? __ldg(p) : 0.f; }
+
 }  // namespace scal3r

@@ -61,6 +61,16 @@ cudaError_t wide_apply(const Plan& pl, const Shape& sh, const Params& prm, void*
 cudaError_t prepare_wide();
 #ifdef SCAL3R_DEBUG_BOUNDS
 cudaError_t wide_upload_bounds(const BoundsTable& t, cudaStream_t st);
+cudaError_t bf16_fwd_upload_bounds(const BoundsTable& t, cudaStream_t st);
+cudaError_t bf16_bwd_upload_bounds(const BoundsTable& t, cudaStream_t st);
+cudaError_t update_upload_bounds(const BoundsTable& t, cudaStream_t st);
+// Every translation unit with checked kernels keeps its own table.
+static void upload_all_bounds(const BoundsTable& t, cudaStream_t st) {
+  wide_upload_bounds(t, st);
+  bf16_fwd_upload_bounds(t, st);
+  bf16_bwd_upload_bounds(t, st);
+  update_upload_bounds(t, st);
+}
 #endif
 cudaError_t wide_forward(const Plan& pl, const Shape& sh, const Params& prm, int ckpt_every, void* ws,
                          const std::function<cudaError_t(int, double, double, const std::function<cudaError_t()>&)>& launch,
@@ -841,10 +851,11 @@ constexpr bool kBoundsBuild = true;
 constexpr bool kBoundsBuild = false;
 #endif
 
-// A checked call: the bounds-checking build, a wide-weight handle and a
+// A checked call: the bounds-checking build, a BF16 handle (the wide-weight
+// path, or the fused head_dim-64 kernels and their update kernels) and a
 // layout its planner accepts (the tensors' extents come from the plan).
 static bool bounds_on(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int32_t* ptr, int32_t S) {
-  return kBoundsBuild && hd && hd->wide && ensure_plan(hd, off, C, ptr, S) == SCAL3R_OK;
+  return kBoundsBuild && hd && hd->cfg.dtype == SCAL3R_BF16 && ensure_plan(hd, off, C, ptr, S) == SCAL3R_OK;
 }
 
 static void bounds_begin(const scal3r_ttt_handle* hd, const CallTensors& ct, cudaStream_t st) {
@@ -859,7 +870,7 @@ static void bounds_begin(const scal3r_ttt_handle* hd, const CallTensors& ct, cud
     ++t.n;
   }
   if (t.n == 0) t.n = 1;   // nothing registered: every checked access is outside (lo = hi = 0)
-  wide_upload_bounds(t, st);
+  upload_all_bounds(t, st);
 #else
   (void)hd; (void)ct; (void)st;
 #endif
@@ -868,7 +879,7 @@ static void bounds_begin(const scal3r_ttt_handle* hd, const CallTensors& ct, cud
 static void bounds_end(cudaStream_t st) {
 #ifdef SCAL3R_DEBUG_BOUNDS
   BoundsTable t{};
-  wide_upload_bounds(t, st);
+  upload_all_bounds(t, st);
 #else
   (void)st;
 #endif

@@ -12,6 +12,7 @@
 // first the W1/W3 rows (1024/D per block), then the W2 rows (1024/F per block).
 #include <cuda_bf16.h>
 
+#include "bounds.cuh"
 #include "ttt_internal.h"
 
 namespace scal3r {
@@ -57,8 +58,10 @@ __device__ __forceinline__ float group_sum(float x, int group) {
   return x;
 }
 
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+// Every plain global access of these kernels is checked in the bounds-checking
+// build (ld4 / st4 and the scalar accesses below); plain otherwise.
+__device__ __forceinline__ float4 ld4(const float* p) { return ld_chk(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { st_chk(reinterpret_cast<float4*>(p), v); }
 __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
@@ -103,7 +106,7 @@ __global__ void prep_kernel(Params p) {
   float4 w = s.valid ? ld4(w0 + s.off) : make_float4(0.f, 0.f, 0.f, 0.f);
   if (s.valid) st4(p.wm + (size_t)chain * P + s.off, w);
   const float ss = group_sum(dot4(w, w), s.group);
-  if (s.valid && s.c4 == 0) p.rho[(size_t)chain * R + s.r] = row_target(p, ss);
+  if (s.valid && s.c4 == 0) st_chk(p.rho + (size_t)chain * R + s.r, row_target(p, ss));
 }
 
 // Forward update of one chain at step `step`:
@@ -127,7 +130,7 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
   if (s.valid) {
     // the row target is loaded before the slot sum so that its round trip
     // overlaps the sum's
-    if (p.norm != SCAL3R_NORM_NONE) rho = p.rho[(size_t)u.chain * R + s.r];
+    if (p.norm != SCAL3R_NORM_NONE) rho = ld_chk(p.rho + (size_t)u.chain * R + s.r);
     x = add_slots(ld4(wcur + s.off), p.part, u.slot0, u.nslots, P, s.off);
   }
   const float n = sqrtf(group_sum(dot4(x, x), s.group));
@@ -138,7 +141,7 @@ __global__ void update_kernel(Params p, const UpdateItem* __restrict__ upd, int 
   st4(wnext + s.off, w);
   if (p.w_ckpt && u.wslot >= 0) st4(p.w_ckpt + ((size_t)u.wslot * p.H + h) * P + s.off, w);
   if (p.w_final && u.last) st4(p.w_final + ((size_t)u.seq * p.H + h) * P + s.off, w);
-  if (p.wnorm && s.c4 == 0) p.wnorm[((size_t)u.chunk * p.H + h) * R + s.r] = n;
+  if (p.wnorm && s.c4 == 0) st_chk(p.wnorm + ((size_t)u.chunk * p.H + h) * R + s.r, n);
 }
 
 // Backward: zero the carried row-norm adjoints and per-chain dW0, compute
@@ -153,8 +156,8 @@ __global__ void bprep_kernel(Params p) {
   if (s.valid) st4(p.dw0_chain + (size_t)chain * P + s.off, make_float4(0.f, 0.f, 0.f, 0.f));
   const float ss = group_sum(dot4(w, w), s.group);
   if (s.valid && s.c4 == 0) {
-    p.rho[(size_t)chain * R + s.r] = row_target(p, ss);
-    p.drho[(size_t)chain * R + s.r] = 0.f;
+    st_chk(p.rho + (size_t)chain * R + s.r, row_target(p, ss));
+    st_chk(p.drho + (size_t)chain * R + s.r, 0.f);
   }
 }
 
@@ -180,13 +183,13 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
   float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), wck = w0;
   float4 lam = make_float4(0.f, 0.f, 0.f, 0.f);
   if (s.valid) {
-    rho = p.rho[(size_t)u.chain * R + s.r];
+    rho = ld_chk(p.rho + (size_t)u.chain * R + s.r);
     if (u.first) {
-      if (p.norm == SCAL3R_NORM_ROW_W0) drho = p.drho[(size_t)u.chain * R + s.r];
+      if (p.norm == SCAL3R_NORM_ROW_W0) drho = ld_chk(p.drho + (size_t)u.chain * R + s.r);
       w0 = ld4(chain_w0(p, u.chain) + s.off);
     } else if (norm_vjp) {
       wck = ld4(p.w_ckpt_in + ((size_t)u.wslot * p.H + h) * P + s.off);
-      n = p.wnorm_in[((size_t)u.chunk * p.H + h) * R + s.r];
+      n = ld_chk(p.wnorm_in + ((size_t)u.chunk * p.H + h) * R + s.r);
     }
     if (!u.last) lam = ld4(rb + s.off);
     lam = add_slots(lam, p.part, u.slot0, u.nslots, P, s.off);
@@ -216,7 +219,10 @@ __global__ void bupdate_kernel(Params p, const UpdateItem* __restrict__ upd, int
                       c * (lam.w - what.w * proj));
   }
   st4(rb + s.off, out);
-  if (s.c4 == 0 && p.norm == SCAL3R_NORM_ROW_W0) p.drho[(size_t)u.chain * R + s.r] += proj;
+  if (s.c4 == 0 && p.norm == SCAL3R_NORM_ROW_W0) {
+    float* dr = p.drho + (size_t)u.chain * R + s.r;
+    st_chk(dr, ld_chk(dr) + proj);
+  }
 }
 
 // dw0 from the per-chain results: summed over sequences in order when w0 is
@@ -228,11 +234,12 @@ __global__ void bfinal_kernel(Params p) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
     if (p.w0_seq_stride == 0) {
       float a = 0.f;
-      for (int s = 0; s < p.S; ++s) a += p.dw0_chain[((size_t)s * p.H + h) * P + i];
-      p.dw0[(size_t)h * P + i] = a;
+      for (int s = 0; s < p.S; ++s) a += ld_chk(p.dw0_chain + ((size_t)s * p.H + h) * P + i);
+      st_chk(p.dw0 + (size_t)h * P + i, a);
     } else {
       for (int s = 0; s < p.S; ++s)
-        p.dw0[(size_t)s * p.w0_seq_stride + (size_t)h * P + i] = p.dw0_chain[((size_t)s * p.H + h) * P + i];
+        st_chk(p.dw0 + (size_t)s * p.w0_seq_stride + (size_t)h * P + i,
+               ld_chk(p.dw0_chain + ((size_t)s * p.H + h) * P + i));
     }
   }
 }
@@ -272,12 +279,12 @@ __global__ void tok_negate_kernel(Params p, const WorkItem* __restrict__ items, 
   const int64_t n = (it.t1 - it.t0) * nc;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const size_t o = (((size_t)(it.t0 + i / nc) * p.H + h) * p.D) / 8 + i % nc;
-    uint4 x = src[o];
+    uint4 x = ld_chk(src + o);
     x.x ^= 0x80008000u;
     x.y ^= 0x80008000u;
     x.z ^= 0x80008000u;
     x.w ^= 0x80008000u;
-    dst[o] = x;
+    st_chk(dst + o, x);
   }
 }
 
@@ -296,8 +303,8 @@ __global__ void tok_add_kernel(Params p, const WorkItem* __restrict__ items, uin
   const int64_t n = (it.t1 - it.t0) * nc;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     const size_t o = (((size_t)(it.t0 + i / nc) * p.H + h) * p.D) / 8 + i % nc;
-    const uint4 a = acc[o], b = add[o];
-    acc[o] = make_uint4(add_bf16x2(a.x, b.x), add_bf16x2(a.y, b.y), add_bf16x2(a.z, b.z), add_bf16x2(a.w, b.w));
+    const uint4 a = ld_chk(acc + o), b = ld_chk(add + o);
+    st_chk(acc + o, make_uint4(add_bf16x2(a.x, b.x), add_bf16x2(a.y, b.y), add_bf16x2(a.z, b.z), add_bf16x2(a.w, b.w)));
   }
 }
 
@@ -335,7 +342,7 @@ __global__ void gcs_update_kernel(Params p, const float* w, int64_t w_stride, co
   float scale = 1.f;
   if (p.norm != SCAL3R_NORM_NONE) scale = row_target(p, ss) / fmaxf(n, p.eps);
   st4(w_out + (size_t)chain * P + s.off, scale4(x, scale));
-  if (wnorm && s.c4 == 0) wnorm[(size_t)chain * R + s.r] = n;
+  if (wnorm && s.c4 == 0) st_chk(wnorm + (size_t)chain * R + s.r, n);
 }
 
 int row_blocks(const Params& p) { return (2 * p.F * p.D + 1023) / 1024 + (p.F * p.D + 1023) / 1024; }
@@ -413,5 +420,9 @@ cudaError_t launch_bfinal(const Params& prm, cudaStream_t st) {
   dim3 grid((P + 255) / 256, prm.H);
   return launch_pdl(bfinal_kernel, grid, dim3(256), 0, st, prm);
 }
+
+#ifdef SCAL3R_DEBUG_BOUNDS
+cudaError_t update_upload_bounds(const BoundsTable& t, cudaStream_t st) { return upload_bounds_table(t, st); }
+#endif
 
 }  // namespace scal3r

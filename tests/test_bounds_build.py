@@ -71,12 +71,13 @@ def test_bounds_build_clean_runs_and_planted_violation():
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["library"] == lib
-    for case in ("dot", "dot_per_matrix", "mse"):
+    for case in ("dot", "dot_per_matrix", "mse", "d64_dot", "d64_per_matrix_ckpt2", "d64_mse"):
         res = out[case]
         assert res["status"] == 0, (case, res)
         bad = {n: e for n, e in res["errors"].items() if not e <= TOL}
         assert not bad, (case, res["errors"])
-    p = out["planted"]
-    assert p["status"] == 9, p                 # SCAL3R_ERR_BOUNDS
-    assert p["tail_untouched"] and p["before_tail_written"], p
-    assert p["status_after_restore"] == 0, p
+    for case in ("planted", "d64_planted"):
+        p = out[case]
+        assert p["status"] == 9, (case, p)     # SCAL3R_ERR_BOUNDS
+        assert p["tail_untouched"] and p["before_tail_written"], (case, p)
+        assert p["status_after_restore"] == 0, (case, p)
