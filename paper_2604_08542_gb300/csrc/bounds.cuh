@@ -51,8 +51,10 @@ inline cudaError_t upload_bounds_table(const BoundsTable& t, cudaStream_t st) {
 __device__ __forceinline__ constexpr bool in_bounds(const void*, uint32_t) { return true; }
 #endif
 
-// Checked plain accesses: a skipped load reads zero.  In the normal build
-// these are the plain access.
+// Checked plain accesses: a skipped load reads zero.  In the ordinary build
+// they are macros for the plain access itself, so that the compiler sees the
+// same expression (and the same aliasing) as unchecked code.
+#ifdef SCAL3R_DEBUG_BOUNDS
 template <typename T>
 __device__ __forceinline__ T ld_chk(const T* p) {
   return in_bounds(p, sizeof(T)) ? *p : T{};
@@ -65,5 +67,10 @@ __device__ __forceinline__ float4 ldg_chk(const float4* p) {
   return in_bounds(p, sizeof(float4)) ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 __device__ __forceinline__ float ldg_chk(const float* p) { return in_bounds(p, sizeof(float)) ? __ldg(p) : 0.f; }
+#else
+#define ld_chk(p) (*(p))
+#define st_chk(p, v) (*(p) = (v))
+#define ldg_chk(p) __ldg(p)
+#endif
 
 }  // namespace scal3r
