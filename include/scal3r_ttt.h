@@ -305,7 +305,14 @@ typedef struct scal3r_ttt_schedule {
                                path cuts pieces on its 16-token tiles with no other minimum */
   float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0) */
   float   bwd_key_cost;     /* backward: cost of an update-VJP token vs an apply-VJP token (> 0) */
-  int32_t reserved;         /* must be 0 */
+  int32_t tail_fill;        /* 0..3.  Bit 0: forward steps, bit 1: backward steps (each with one
+                               wave).  The pieces modelled to end first take extra pieces cut off
+                               the longest ones, launched behind the first wave; kept for a step
+                               only where the library's piece-time model shortens it.  BF16
+                               head_dim-64 path with the dot loss only; ignored elsewhere.
+                               Default 0 (on the 66,624-token x 16-head benchmark layout it
+                               measured neutral); the autotuner tries it.  Results match to
+                               rounding: a chunk's token sum is split at other boundaries */
 } scal3r_ttt_schedule;
 
 /* Replace / read the handle's schedule.  Setting it drops the cached plan

@@ -76,10 +76,10 @@ class scal3r_ttt_config(ctypes.Structure):
 class scal3r_ttt_schedule(ctypes.Structure):
     _fields_ = [("fwd_waves", ctypes.c_int32), ("bwd_waves", ctypes.c_int32),
                 ("min_piece_tokens", ctypes.c_int32), ("fwd_key_cost", ctypes.c_float),
-                ("bwd_key_cost", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("bwd_key_cost", ctypes.c_float), ("tail_fill", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class Scal3rError(RuntimeError):

@@ -214,6 +214,7 @@ int ensure_plan(scal3r_ttt_handle* hd, const int64_t* off, int32_t C, const int3
     sch.align = 16;
     sch.min_tokens = 16;
   }
+  if (hd->cfg.dtype != SCAL3R_BF16 || hd->wide || hd->shape.lin) sch.fill = 0;   // its model is the BF16 kernels'
   int rc = build_plan(np, hd->shape, sch, hd->num_sms, off, C, ptr, S, hd->wide ? 1 : hd->cfg.ckpt_every,
                       mse_compose);
   if (rc != SCAL3R_OK) return rc;
@@ -490,7 +491,8 @@ int enqueue_backward(scal3r_ttt_handle* hd, const Params& prm, cudaStream_t st) 
 
 bool valid_schedule(const scal3r_ttt_schedule& s) {
   return s.fwd_waves >= 1 && s.fwd_waves <= 8 && s.bwd_waves >= 1 && s.bwd_waves <= 8 &&
-         s.min_piece_tokens >= 128 && s.fwd_key_cost > 0.f && s.bwd_key_cost > 0.f && s.reserved == 0;
+         s.min_piece_tokens >= 128 && s.fwd_key_cost > 0.f && s.bwd_key_cost > 0.f && s.tail_fill >= 0 &&
+         s.tail_fill <= 3;
 }
 
 void to_internal(const scal3r_ttt_schedule& s, Schedule& o) {
@@ -499,6 +501,7 @@ void to_internal(const scal3r_ttt_schedule& s, Schedule& o) {
   o.min_tokens = s.min_piece_tokens;
   o.key_cost = s.fwd_key_cost;
   o.bkey_cost = s.bwd_key_cost;
+  o.fill = s.tail_fill;
 }
 
 void to_public(const Schedule& o, scal3r_ttt_schedule& s) {
@@ -507,7 +510,7 @@ void to_public(const Schedule& o, scal3r_ttt_schedule& s) {
   s.min_piece_tokens = o.min_tokens;
   s.fwd_key_cost = o.key_cost;
   s.bwd_key_cost = o.bkey_cost;
-  s.reserved = 0;
+  s.tail_fill = o.fill;
 }
 
 }  // namespace
@@ -1038,12 +1041,14 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
   Schedule bestc = saved;
   float bestt = 0.f;
   if (rc == SCAL3R_OK) {
-    // forward: pieces per step and the gradient/apply cost ratio
+    // forward: pieces per step (waves; one wave with or without the tail
+    // fill) and the gradient/apply cost ratio
     bool first = true;
-    for (int wv : {1, 2, 3})
-      for (float kc : {1.6f, 1.85f, 2.1f}) {
+    for (int wf : {0, 1, 2, 3})
+      for (float kc : {1.6f, 1.85f, 2.1f, 2.45f}) {
         Schedule sc = saved;
-        sc.fwd_waves = wv;
+        sc.fwd_waves = wf < 2 ? 1 : wf;
+        sc.fill = (saved.fill & 2) | (wf == 1 ? 1 : 0);
         sc.key_cost = kc;
         float t = 0.f;
         rc = trial(sc, false, t);
@@ -1059,10 +1064,11 @@ int scal3r_ttt_autotune(scal3r_ttt_handle* hd, const void* q, const void* k, con
     // backward, with the forward fixed at its best schedule
     bool first = true;
     const Schedule fb = bestc;
-    for (int wv : {1, 2, 3})
+    for (int wf : {0, 1, 2, 3})
       for (float kc : {2.25f, 2.95f, 3.6f}) {
         Schedule sc = fb;
-        sc.bwd_waves = wv;
+        sc.bwd_waves = wf < 2 ? 1 : wf;
+        sc.fill = (fb.fill & 1) | (wf == 1 ? 2 : 0);
         sc.bkey_cost = kc;
         float t = 0.f;
         rc = trial(sc, true, t);

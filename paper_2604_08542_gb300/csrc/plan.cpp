@@ -76,6 +76,133 @@ std::vector<int> pieces_per_task(const std::vector<Task>& tasks, const Schedule&
   return n;
 }
 
+// ---- tail fill ------------------------------------------------------------
+// With one wave of pieces, a task whose CTA share was rounded down keeps long
+// pieces while the SMs of shorter pieces idle until the launch ends.  The fill
+// caps every first-wave piece at a target time M and cuts the tokens that no
+// longer fit into extra pieces placed behind the first wave.  A grid's CTA k
+// starts on the first SM that frees once CTAs 0..k-1 are resident, so the
+// extra pieces are sized, earliest first, for the modelled moments at which
+// the first wave's SMs free.  M is the smallest target the model can meet
+// (bisection); the fill is kept only if M beats the one-wave plan's modelled
+// end by fill_margin.
+
+struct Cut {
+  int64_t t0, t1;
+  bool fill;      // placed behind the first wave
+  double start;   // modelled start of a fill piece
+};
+
+// A piece's modelled time.  The kernels run whole tiles (a ragged last tile
+// costs a full one), so tokens count in tiles.
+double fill_time(const Schedule& sch, int role, int64_t tokens) {
+  const int64_t tiles = (tokens + sch.align - 1) / sch.align;
+  const double t = (double)(tiles * sch.align);
+  switch (role) {
+    case ROLE_KEY: return sch.fill_ovh[0] + t * sch.key_cost;
+    case ROLE_APPLY: return sch.fill_ovh[1] + t;
+    case ROLE_BKEY:
+      return sch.fill_ovh[2] + t * sch.fill_bkey_tok +
+             (double)((tiles + kBwdSubTiles - 1) / kBwdSubTiles) * sch.fill_bkey_sub;
+    default: return sch.fill_ovh[3] + t;
+  }
+}
+
+// The largest number of tiles (at most `avail` tiles, i.e. the tokens left
+// from `t0` to `t1`) whose piece, started at `start`, ends by M; 0 if none.
+int64_t tiles_by(const Schedule& sch, int role, int64_t t0, int64_t t1, double start, double M) {
+  int64_t lo = 0, hi = (t1 - t0 + sch.align - 1) / sch.align;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    const int64_t tok = std::min(t1 - t0, mid * sch.align);
+    if (start + fill_time(sch, role, tok) <= M) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cuts of every task for target M (first-wave pieces: npieces[i] of them),
+// or false if some tokens do not fit.
+bool try_fill(const std::vector<Task>& tasks, const std::vector<int>& npieces, const Schedule& sch,
+              int64_t ctas, double M, std::vector<std::vector<Cut>>& cuts) {
+  cuts.assign(tasks.size(), {});
+  std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+  std::vector<std::pair<double, size_t>> rest;   // (cost of the tokens left, task)
+  std::vector<int64_t> next(tasks.size());
+  int64_t first = 0;
+  // The model prices each piece's fixed cost, so the fill's pieces are sized
+  // by it alone, down to one tile (min_tokens governs the one-wave split).
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const Task& t = tasks[i];
+    const int64_t tiles = (t.t1 - t.t0 + sch.align - 1) / sch.align;
+    const int64_t cap = tiles_by(sch, t.role, t.t0, t.t1, 0.0, M);
+    if (cap < 1) return false;
+    const int64_t cov = std::min(tiles, (int64_t)npieces[i] * cap);
+    const int64_t end = std::min(t.t1, t.t0 + cov * sch.align);
+    for (auto& pr : split(t.t0, end, npieces[i], sch.align)) {
+      cuts[i].push_back({pr.first, pr.second, false, 0.0});
+      free_at.push(fill_time(sch, t.role, pr.second - pr.first));
+      ++first;
+    }
+    next[i] = end;
+    if (end < t.t1) rest.push_back({fill_time(sch, t.role, t.t1 - end), i});
+  }
+  // SMs the first wave leaves empty: their pieces start with it, at time 0
+  for (int64_t k = first; k < ctas; ++k) free_at.push(-(double)sch.fill_start);
+  std::stable_sort(rest.begin(), rest.end(),
+                   [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) {
+                     return a.first > b.first;
+                   });
+  int64_t extra = 0;
+  for (const auto& r : rest) {
+    const Task& t = tasks[r.second];
+    int64_t cur = next[r.second];
+    while (cur < t.t1) {
+      if (free_at.empty() || ++extra > ctas) return false;
+      const double f = free_at.top() + sch.fill_start;
+      free_at.pop();
+      const int64_t n = tiles_by(sch, t.role, cur, t.t1, f, M);
+      if (n < 1) return false;
+      const int64_t e = std::min(t.t1, cur + n * sch.align);
+      cuts[r.second].push_back({cur, e, true, f});
+      free_at.push(f + fill_time(sch, t.role, e - cur));
+      cur = e;
+    }
+  }
+  return true;
+}
+
+// Cuts of every task: the one-wave split, or the fill when it pays.
+std::vector<std::vector<Cut>> cut_tasks(const std::vector<Task>& tasks, const std::vector<int>& npieces,
+                                        const Schedule& sch, int64_t ctas, bool fill) {
+  std::vector<std::vector<Cut>> one(tasks.size());
+  double m1 = 0.0, work = 0.0;
+  int64_t total = 0;
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    for (auto& pr : split(tasks[i].t0, tasks[i].t1, npieces[i], sch.align)) {
+      one[i].push_back({pr.first, pr.second, false, 0.0});
+      const double c = fill_time(sch, tasks[i].role, pr.second - pr.first);
+      m1 = std::max(m1, c);
+      work += c;
+    }
+    total += npieces[i];
+  }
+  if (!fill || total > ctas || tasks.empty()) return one;
+  std::vector<std::vector<Cut>> best, trial;
+  double lo = work / (double)ctas, hi = m1;
+  for (int it = 0; it < 48 && hi - lo > 0.5; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (try_fill(tasks, npieces, sch, ctas, mid, trial)) {
+      hi = mid;
+      best.swap(trial);
+    } else {
+      lo = mid;
+    }
+  }
+  if (best.empty() || hi > m1 * (1.0 - sch.fill_margin)) return one;
+  return best;
+}
+
 void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_sms, int waves,
                   bool backward, std::vector<WorkItem>& items, std::vector<UpdateItem>& upds,
                   std::vector<Step>& steps, int32_t& max_slots,
@@ -85,10 +212,13 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
   st.upd0 = (int32_t)upds.size();
   int ctas = sch.ctas_per_wave > 0 ? sch.ctas_per_wave : num_sms;
   const std::vector<int> npieces = pieces_per_task(tasks, sch, std::max<int64_t>(1, (int64_t)waves * ctas));
-  // pieces per task
+  const bool fill = waves == 1 && (sch.fill & (backward ? 2 : 1)) != 0;
+  const std::vector<std::vector<Cut>> cuts = cut_tasks(tasks, npieces, sch, ctas, fill);
+  // pieces per task; a piece's modelled start orders the fill pieces
   std::vector<WorkItem> step_items;
+  std::vector<Cut> where;
   // slots: per chain, slots are contiguous (key pieces, and in the backward
-  // also apply pieces, of the same chain).
+  // also apply pieces, of the same chain), in token order.
   std::vector<UpdateItem> upd = step_updates_template;
   int32_t slot = 0;
   for (auto& u : upd) {
@@ -99,9 +229,10 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
       if (t.chain != u.chain) continue;
       bool reduces = backward || t.role == ROLE_KEY;
       if (!reduces) continue;
-      for (auto& pr : split(t.t0, t.t1, npieces[ti], sch.align)) {
-        WorkItem w{pr.first, pr.second, t.chain, t.role, slot++, t.seq, t.wchunk, 0};
+      for (const Cut& c : cuts[ti]) {
+        WorkItem w{c.t0, c.t1, t.chain, t.role, slot++, t.seq, t.wchunk, 0};
         step_items.push_back(w);
+        where.push_back(c);
         u.nslots++;
       }
     }
@@ -110,20 +241,37 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
     const Task& t = tasks[ti];
     bool reduces = backward || t.role == ROLE_KEY;
     if (reduces) continue;
-    for (auto& pr : split(t.t0, t.t1, npieces[ti], sch.align)) {
-      WorkItem w{pr.first, pr.second, t.chain, t.role, -1, t.seq, t.wchunk, 0};
+    for (const Cut& c : cuts[ti]) {
+      WorkItem w{c.t0, c.t1, t.chain, t.role, -1, t.seq, t.wchunk, 0};
       step_items.push_back(w);
+      where.push_back(c);
     }
   }
-  // longest (costliest) pieces first
+  // the first wave, longest (costliest) pieces first; then the fill pieces by
+  // modelled start (a negative start: an SM the first wave left empty)
   auto cost_of = [&](const WorkItem& w) {
     double c = (double)(w.t1 - w.t0);
     if (w.role == ROLE_KEY) c *= sch.key_cost;
     if (w.role == ROLE_BKEY) c *= sch.bkey_cost;
     return c;
   };
-  std::stable_sort(step_items.begin(), step_items.end(),
-                   [&](const WorkItem& a, const WorkItem& b) { return cost_of(a) > cost_of(b); });
+  std::vector<size_t> order(step_items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    const bool fa = where[a].fill, fb = where[b].fill;
+    if (fa != fb) return fb;
+    if (fa) return where[a].start < where[b].start;
+    return cost_of(step_items[a]) > cost_of(step_items[b]);
+  });
+  {
+    std::vector<WorkItem> sorted;
+    sorted.reserve(order.size());
+    for (size_t i : order) {
+      sorted.push_back(step_items[i]);
+      if (where[i].fill) st.nfill++;
+    }
+    step_items.swap(sorted);
+  }
   if (backward) {
     // one sub-piece of scratch and a weight image per update-VJP piece (BF16
     // backward; the apply-VJP pieces keep their factors in shared memory)
@@ -145,9 +293,13 @@ void lay_out_step(const std::vector<Task>& tasks, const Schedule& sch, int num_s
 
 }  // namespace
 
-int build_plan(Plan& plan, const Shape& s, const Schedule& sch, int num_sms,
+int build_plan(Plan& plan, const Shape& s, const Schedule& sch_in, int num_sms,
                const int64_t* off, int32_t C, const int32_t* ptr, int32_t S, int32_t ckpt_every,
                bool mse_compose) {
+  // the composed squared-error loss launches part of each backward step
+  // separately, outside the fill's one-launch model
+  Schedule sch = sch_in;
+  if (mse_compose) sch.fill = 0;
   if (!off || !ptr || C < 0 || S < 1) return SCAL3R_ERR_INVALID_ARG;
   if (off[0] != 0) return SCAL3R_ERR_INVALID_ARG;
   for (int32_t c = 0; c < C; ++c)

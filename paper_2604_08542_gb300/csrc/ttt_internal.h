@@ -61,6 +61,8 @@ struct Step {
   int32_t segk = 0;       //   whose sources are row segk of the plan's segment table
   int32_t npost = 0;      // backward, composed squared-error loss: the last npost pieces are
                           // ROLE_BAPPLY_K, launched after the others
+  int32_t nfill = 0;      // tail fill: the last nfill pieces (before any npost) start behind
+                          // the first wave, in the order their SMs are modelled to free
 };
 
 struct Plan {
@@ -124,6 +126,19 @@ struct Schedule {
                                // (128 on the BF16 path; the float32 path's tiles are 16 tokens)
   float key_cost = 1.85f;      // forward: gradient token vs applied token (measured on GB300)
   float bkey_cost = 2.25f;     // backward: update-VJP token vs apply-VJP token (measured on GB300)
+  // Tail fill (bit 0: forward steps, bit 1: backward steps; one wave only).
+  // The pieces that end first take extra pieces cut off the longest ones,
+  // launched behind the first wave.  Its piece-time model is in units of the
+  // step's cheaper token (an applied token forward, an apply-VJP token
+  // backward): a fixed cost per piece plus a cost per token (and, for an
+  // update-VJP piece, per sub-piece).  Estimated from per-phase timestamps of
+  // the BF16 head_dim-64 kernels on GB300.
+  int32_t fill = 0;
+  float fill_ovh[4] = {200.f, 120.f, 340.f, 200.f};   // per piece: KEY, APPLY, BKEY, BAPPLY
+  float fill_bkey_tok = 2.03f;   // update-VJP token, its sub-piece costs apart
+  float fill_bkey_sub = 170.f;   // per sub-piece of kBwdSubTiles tiles
+  float fill_start = 50.f;       // a CTA's start on an SM another CTA has just left
+  float fill_margin = 0.02f;     // kept only if the modelled step gets this much shorter
 };
 
 struct Shape {

@@ -16,7 +16,7 @@ using scal3r::Shape;
 extern "C" {
 
 // Build a plan.  sched = {ctas_per_wave, fwd_waves, bwd_waves, min_tokens,
-// align}, costs = {key_cost, bkey_cost}; ckpt_every and mse_compose as the
+// align, fill}, costs = {key_cost, bkey_cost}; ckpt_every and mse_compose as the
 // library passes them (sparse checkpoints; the composed squared-error loss of
 // the BF16 head_dim-64 path).  Returns the plan (or null) and the planner's
 // status in *rc.
@@ -29,6 +29,7 @@ void* ph_build_opts(int32_t H, int32_t D, int32_t F, int32_t num_sms, const int3
   sch.bwd_waves = sched[2];
   sch.min_tokens = sched[3];
   sch.align = sched[4];
+  sch.fill = sched[5];
   sch.key_cost = costs[0];
   sch.bkey_cost = costs[1];
   Shape s{H, D, F};
@@ -124,6 +125,13 @@ void ph_counts2(const void* pv, int64_t* out) {
   out[5] = (int64_t)p.ysteps.size();
   out[6] = p.ckpt_slots;
   out[7] = p.ckpt_every;
+}
+
+// The number of tail-fill pieces of every step (0: forward, 1: backward).
+void ph_nfill(const void* pv, int32_t backward, int32_t* out) {
+  const Plan& p = *(const Plan*)pv;
+  const auto& v = backward ? p.bsteps : p.steps;
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].nfill;
 }
 
 // 5 values per backward step: wseg, rec0, nrec, segk, npost

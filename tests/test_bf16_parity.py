@@ -137,17 +137,21 @@ def test_bf16_backward_full_size_sampled_heads():
     assert not bad, f"above {TOL}: {bad}; all {errs}"
 
 
-def test_bf16_vggt64_backward_in_graph_mode_sampled_heads():
+@pytest.mark.parametrize("tail_fill", [0, 3])
+def test_bf16_vggt64_backward_in_graph_mode_sampled_heads(tail_fill):
     """The benchmark's own step: 64 frames x 1041 tokens, 16 heads, 4 chunks of
     16,656 tokens, forward + backward replayed from the library's CUDA graphs
     (second call; the first captures).  The oracle checks every output and
-    gradient of two whole heads."""
+    gradient of two whole heads.  With the tail fill on, the three steps that
+    hold both roles launch extra pieces behind the first wave in each
+    direction (the host planner tests show which)."""
     import torch
     w = syn.workload("bf16_vggt64")
     lay = w.layout()
     x = syn.make_inputs(lay.num_tokens, 16, 64, 128, seed=4, dtype="bf16", with_grad_out=True)
     g = upload(x, torch.bfloat16)
     layer = _layer(16)
+    layer.set_schedule(tail_fill=tail_fill)
     layer.set_graph_mode(True)
     for _ in range(2):
         o, ck, wn, wf = layer.forward(g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets,

@@ -61,6 +61,11 @@ def test_schedule_roundtrip_and_validation():
         layer.set_schedule(fwd_waves=0)
     with pytest.raises(ttt.Scal3rError):
         layer.set_schedule(min_piece_tokens=16)
+    assert s["tail_fill"] == 0
+    layer.set_schedule(tail_fill=3)
+    assert layer.schedule()["tail_fill"] == 3
+    with pytest.raises(ttt.Scal3rError):
+        layer.set_schedule(tail_fill=4)
 
 
 @pytest.mark.parametrize("waves", [1, 2, 3])
@@ -88,6 +93,7 @@ def test_autotune_picks_a_valid_schedule_and_caches_it(tmp_path):
                          d_o=g["d_o"], cache_path=cache)
     s = res["schedule"]
     assert 1 <= s["fwd_waves"] <= 3 and 1 <= s["bwd_waves"] <= 3 and res["ms"] > 0
+    assert 0 <= s["tail_fill"] <= 3
     assert layer.schedule() == s
     again = ttt.TTT(16, 64, 128, dtype=torch.bfloat16).autotune(
         g["q"], g["k"], g["v"], g["lr"], g["w0"], lay.chunk_offsets, lay.seq_chunk_ptr, d_o=g["d_o"],

@@ -70,6 +70,7 @@ def lib(tmp_path_factory):
                                                        ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]
     L.ph_counts2.argtypes = [ctypes.c_void_p, P(ctypes.c_int64)]
     L.ph_bsteps2.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
+    L.ph_nfill.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32)]
     L.ph_wslots.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int32)]
     L.ph_rarrays.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int32), P(ctypes.c_int32),
                              P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_int32)]
@@ -93,14 +94,16 @@ class PlanView:
     """The plan read back into numpy arrays."""
 
     def __init__(self, lib, H, off, ptr, num_sms=152, ctas=0, fwd_waves=1, bwd_waves=1, min_tokens=256,
-                 key_cost=1.85, bkey_cost=2.25, D=64, F=128, align=ALIGN, ckpt_every=1, mse_compose=False):
+                 key_cost=1.85, bkey_cost=2.25, D=64, F=128, align=ALIGN, ckpt_every=1, mse_compose=False,
+                 fill=0):
         self.lib, self.H, self.D, self.F = lib, H, D, F
         self.align, self.ckpt_every, self.mse_compose = align, ckpt_every, mse_compose
         self.off = np.ascontiguousarray(off, dtype=np.int64)
         self.ptr = np.ascontiguousarray(ptr, dtype=np.int32)
         self.sched = dict(num_sms=num_sms, ctas=ctas, fwd_waves=fwd_waves, bwd_waves=bwd_waves,
-                          min_tokens=min_tokens, key_cost=np.float32(key_cost), bkey_cost=np.float32(bkey_cost))
-        sch = np.array([ctas, fwd_waves, bwd_waves, min_tokens, align], dtype=np.int32)
+                          min_tokens=min_tokens, key_cost=np.float32(key_cost), bkey_cost=np.float32(bkey_cost),
+                          fill=fill)
+        sch = np.array([ctas, fwd_waves, bwd_waves, min_tokens, align, fill], dtype=np.int32)
         costs = np.array([key_cost, bkey_cost], dtype=np.float32)
         rc = ctypes.c_int32(-1)
         self.h = lib.ph_build_opts(H, D, F, num_sms, _ptr(sch, ctypes.c_int32), _ptr(costs, ctypes.c_float),
@@ -123,6 +126,13 @@ class PlanView:
         if n_bst:
             lib.ph_bsteps2(self.h, _ptr(self.bsteps2, ctypes.c_int32))
         self.bsteps2 = self.bsteps2[:n_bst]
+        # tail-fill pieces at the end of every step (forward, backward)
+        self.nfill = []
+        for bwd, n in ((0, n_st), (1, n_bst)):
+            nf = np.zeros(max(n, 1), dtype=np.int32)
+            if n:
+                lib.ph_nfill(self.h, bwd, _ptr(nf, ctypes.c_int32))
+            self.nfill.append(nf[:n])
         self.wslots = []
         for which, n in ((0, n_up), (1, n_bup), (2, n_ru)):
             w = np.zeros(max(n, 1), dtype=np.int32)
@@ -259,11 +269,16 @@ def _check_plan(pv):
                 key = (bwd, role, chain, c)
                 assert key not in seen
                 seen[key] = len(pcs)
-            # the costliest pieces come first
-            costs = [pv.cost(int(r[3]), int(r[1] - r[0])) for r in items]
+            # the costliest pieces come first (the first wave; tail-fill pieces
+            # follow it)
+            nf = int(pv.nfill[bwd][s])
+            first = items[:len(items) - nf]
+            costs = [pv.cost(int(r[3]), int(r[1] - r[0])) for r in first]
             assert all(costs[i] >= costs[i + 1] * (1 - 1e-6) for i in range(len(costs) - 1))
-            # no more pieces than CTAs, unless the step has more tasks than CTAs
-            assert len(items) <= max(len(want), pv.ctas(bwd))
+            # no more pieces than CTAs, unless the step has more tasks than
+            # CTAs; the fill adds at most one more wave
+            assert len(first) <= max(len(want), pv.ctas(bwd))
+            assert nf == 0 or (pv.sched["fill"] & (2 if bwd else 1) and nf <= pv.ctas(bwd))
             # updates: one per chain that closes a chunk here, in sequence-major order
             _check_updates(pv, bwd, s, items, ups)
             st = steps[s]
@@ -338,12 +353,14 @@ def _optimal_max_cost(costs, caps, ctas):
 
 
 def _check_minmax(pv):
-    """The piece counts minimise the costliest piece of every step."""
+    """The piece counts minimise the costliest piece of every step (the
+    first wave's counts, when the tail fill adds pieces behind it)."""
     mt = pv.sched["min_tokens"]
     for bwd in (0, 1):
         steps = pv.bsteps if bwd else pv.steps
         for s in range(len(steps)):
-            groups = _group_pieces(pv, pv.step_items(bwd, s))
+            items = pv.step_items(bwd, s)
+            groups = _group_pieces(pv, items[:len(items) - int(pv.nfill[bwd][s])])
             costs, caps, got = [], [], 0.0
             for (chain, role, c), pcs in groups.items():
                 length = int(pv.off[c + 1] - pv.off[c])
@@ -370,13 +387,14 @@ LAYOUTS = {
 }
 
 
+@pytest.mark.parametrize("fill", [0, 3])
 @pytest.mark.parametrize("name", list(LAYOUTS))
 @pytest.mark.parametrize("H,num_sms,ctas,waves,min_tokens", [(1, 152, 0, 1, 256), (4, 8, 0, 2, 128),
                                                             (3, 152, 20, 1, 512), (16, 4, 0, 1, 256)])
-def test_plan_invariants_on_ragged_layouts(lib, name, H, num_sms, ctas, waves, min_tokens):
+def test_plan_invariants_on_ragged_layouts(lib, name, H, num_sms, ctas, waves, min_tokens, fill):
     lay = syn.layout_from_lengths(LAYOUTS[name])
     pv = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, num_sms=num_sms, ctas=ctas, fwd_waves=waves,
-                  bwd_waves=waves, min_tokens=min_tokens)
+                  bwd_waves=waves, min_tokens=min_tokens, fill=fill)
     try:
         _check_plan(pv)
         _check_minmax(pv)
@@ -397,6 +415,103 @@ def test_plan_invariants_on_benchmark_layouts(lib, wl, H):
             # 16 chains x (key + apply) = 32 tasks; the planner fills the SMs
             full = [len(pv.step_items(0, s)) for s in range(1, len(pv.steps) - 1)]
             assert all(n == 152 for n in full), full
+    finally:
+        pv.close()
+
+
+# ---- the tail fill -----------------------------------------------------------
+# The planner's piece-time model (units of the step's cheaper token): a fixed
+# cost per piece, a cost per token of whole tiles, and for an update-VJP piece
+# a cost per sub-piece of four tiles; a CTA behind the first wave starts a
+# little after its SM frees.
+_FILL_OVH = {KEY: 200.0, APPLY: 120.0, BKEY: 340.0, BAPPLY: 200.0}
+
+
+def _fill_time(pv, role, length):
+    tiles = -(-length // pv.align)
+    t = float(tiles * pv.align)
+    if role == KEY:
+        return _FILL_OVH[KEY] + t * float(pv.sched["key_cost"])
+    if role == BKEY:
+        return _FILL_OVH[BKEY] + t * 2.03 + -(-tiles // 4) * 170.0
+    return _FILL_OVH[role] + t
+
+
+def _dispatch_end(pv, items, ctas, start_lag=50.0):
+    """When the last piece of a launch ends if the GPU starts CTA k on the
+    first SM that frees once CTAs 0..k-1 have started."""
+    import heapq
+    free, end = [], 0.0
+    for k, r in enumerate(items):
+        t = _fill_time(pv, int(r[3]), int(r[1] - r[0]))
+        if k < ctas:
+            e = t
+        else:
+            e = heapq.heappop(free) + start_lag + t
+        heapq.heappush(free, e)
+        end = max(end, e)
+    return end
+
+
+def _task_counts(pv, items):
+    return {k: len(v) for k, v in _group_pieces(pv, items).items()}
+
+
+@pytest.mark.parametrize("wl,H", [("bf16_vggt64", 16), ("bf16_window256", 16), ("bf16_fwdbwd_2x32", 16)])
+def test_tail_fill_on_benchmark_layouts(lib, wl, H):
+    """The fill leaves each task's first-wave piece count as the one-wave plan
+    has it, covers the rest behind the first wave, and shortens every launch it
+    touches under the model by at least the planner's 2 % margin, with the GPU's
+    dispatch order simulated from the item order alone."""
+    lay = syn.workload(wl).layout()
+    one = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, num_sms=152)
+    pv = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, num_sms=152, fill=3)
+    try:
+        _check_plan(pv)
+        _check_minmax(pv)
+        touched = 0
+        for bwd in (0, 1):
+            steps = pv.bsteps if bwd else pv.steps
+            for s in range(len(steps)):
+                a, b = one.step_items(bwd, s), pv.step_items(bwd, s)
+                nf = int(pv.nfill[bwd][s])
+                assert int(one.nfill[bwd][s]) == 0
+                if nf == 0:
+                    assert np.array_equal(a, b)
+                    continue
+                touched += 1
+                assert _task_counts(pv, b[:len(b) - nf]) == _task_counts(one, a)
+                # fill pieces: whole tiles, or the ragged end of their task
+                for r in b[len(b) - nf:]:
+                    c = pv.chunk_of(int(r[0]), int(r[1]))
+                    assert (r[1] - r[0]) % pv.align == 0 or r[1] == pv.off[c + 1]
+                t_one, t_fill = _dispatch_end(one, a, 152), _dispatch_end(pv, b, 152)
+                assert t_fill <= 0.98 * t_one + 1e-6, (bwd, s, t_fill, t_one)
+        if wl == "bf16_vggt64":
+            # the three steps with both roles, in each direction
+            assert [int(x) > 0 for x in pv.nfill[0]] == [False, True, True, True, False]
+            assert [int(x) > 0 for x in pv.nfill[1]] == [False, True, True, True, False]
+        assert touched > 0
+    finally:
+        pv.close()
+        one.close()
+
+
+def test_tail_fill_off_keeps_the_one_wave_plan(lib):
+    """fill = 0 never adds a piece, and neither does fill = 3 with more than
+    one wave or when the one-wave plan is already balanced."""
+    lay = syn.workload("bf16_vggt64").layout()
+    for kw in ({"fill": 0}, {"fill": 3, "fwd_waves": 2, "bwd_waves": 2}):
+        pv = PlanView(lib, 16, lay.chunk_offsets, lay.seq_chunk_ptr, num_sms=152, **kw)
+        try:
+            assert all((nf == 0).all() for nf in pv.nfill)
+        finally:
+            pv.close()
+    bal = syn.layout_from_lengths([[256 * 152]])   # every step: one task, 152 pieces of two tiles
+    pv = PlanView(lib, 1, bal.chunk_offsets, bal.seq_chunk_ptr, num_sms=152, fill=3)
+    try:
+        _check_plan(pv)
+        assert all((nf == 0).all() for nf in pv.nfill)
     finally:
         pv.close()
 
