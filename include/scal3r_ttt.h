@@ -190,7 +190,10 @@ int scal3r_ttt_forward(scal3r_ttt_handle* handle,
  * latency-critical paths that must not enter the driver's allocator.
  *   It takes the configuration instead of a handle and no workspace; every
  * other argument means what it means for scal3r_ttt_forward, and the results
- * are those of scal3r_ttt_forward.  Its scratch (schedule, master weights,
+ * are those of scal3r_ttt_forward under the schedule this call uses: waves 1,
+ * cost ratios 1.85 / 2.25, no tail fill (a bfloat16 handle's default
+ * schedule sums a chunk's tokens over other pieces, so its results differ
+ * in rounding only).  Its scratch (schedule, master weights,
  * partial sums, status word) is one fixed 32 MiB device array inside the
  * library, held by every GPU that loads the library until the process exits.
  *  - Configurations: the float32 path at any shape it takes, either loss;
@@ -303,16 +306,17 @@ typedef struct scal3r_ttt_schedule {
   int32_t bwd_waves;        /* backward: same for the backward steps (1..8) */
   int32_t min_piece_tokens; /* smallest piece, tokens (>= 128); the bfloat16 path.  The float32
                                path cuts pieces on its 16-token tiles with no other minimum */
-  float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0) */
+  float   fwd_key_cost;     /* cost of a gradient token relative to an applied token (> 0);
+                               default 2.45 for a BF16 head_dim-64 handle, else 1.85 */
   float   bwd_key_cost;     /* backward: cost of an update-VJP token vs an apply-VJP token (> 0) */
   int32_t tail_fill;        /* 0..3.  Bit 0: forward steps, bit 1: backward steps (each with one
                                wave).  The pieces modelled to end first take extra pieces cut off
                                the longest ones, launched behind the first wave; kept for a step
                                only where the library's piece-time model shortens it.  BF16
                                head_dim-64 path with the dot loss only; ignored elsewhere.
-                               Default 0 (on the 66,624-token x 16-head benchmark layout it
-                               measured neutral); the autotuner tries it.  Results match to
-                               rounding: a chunk's token sum is split at other boundaries */
+                               Default 3 for a BF16 head_dim-64 handle, else 0; the autotuner
+                               tries it on and off.  Results match to rounding: a chunk's
+                               token sum is split at other boundaries */
 } scal3r_ttt_schedule;
 
 /* Replace / read the handle's schedule.  Setting it drops the cached plan

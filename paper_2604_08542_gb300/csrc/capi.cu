@@ -570,6 +570,12 @@ int scal3r_ttt_init(const scal3r_ttt_config* cfg, scal3r_ttt_handle** out) {
   hd->device = dev;
   hd->num_sms = sms;
   hd->wide = wide;
+  if (cfg->dtype == SCAL3R_BF16 && !wide && !lin) {
+    // the head_dim-64 kernels' defaults, measured on GB300 (per-CTA timelines
+    // and a same-box A/B of the bench layout's step)
+    hd->sched.fill = 3;
+    hd->sched.key_cost = 2.45f;
+  }
   if (cudaMalloc((void**)&hd->d_status, sizeof(int)) != cudaSuccess ||
       cudaMemset(hd->d_status, 0, sizeof(int)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&hd->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -99,7 +99,7 @@ double fill_time(const Schedule& sch, int role, int64_t tokens) {
   const int64_t tiles = (tokens + sch.align - 1) / sch.align;
   const double t = (double)(tiles * sch.align);
   switch (role) {
-    case ROLE_KEY: return sch.fill_ovh[0] + t * sch.key_cost;
+    case ROLE_KEY: return sch.fill_ovh[0] + t * sch.fill_key_tok;
     case ROLE_APPLY: return sch.fill_ovh[1] + t;
     case ROLE_BKEY:
       return sch.fill_ovh[2] + t * sch.fill_bkey_tok +

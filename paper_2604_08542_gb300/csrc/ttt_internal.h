@@ -131,13 +131,16 @@ struct Schedule {
   // launched behind the first wave.  Its piece-time model is in units of the
   // step's cheaper token (an applied token forward, an apply-VJP token
   // backward): a fixed cost per piece plus a cost per token (and, for an
-  // update-VJP piece, per sub-piece).  Estimated from per-phase timestamps of
-  // the BF16 head_dim-64 kernels on GB300.
+  // update-VJP piece, per sub-piece).  Fitted to per-CTA timelines of the
+  // BF16 head_dim-64 kernels on GB300 (forward: a gradient tile 2.9 us and an
+  // apply tile 1.2 us, plus 5.1 and 4.0 us a piece; backward: an update-VJP
+  // piece of 1 / 2 / 22 tiles 22.5 / 29.3 / 175 us, an apply-VJP tile 3.3 us).
   int32_t fill = 0;
-  float fill_ovh[4] = {200.f, 120.f, 340.f, 200.f};   // per piece: KEY, APPLY, BKEY, BAPPLY
-  float fill_bkey_tok = 2.03f;   // update-VJP token, its sub-piece costs apart
-  float fill_bkey_sub = 170.f;   // per sub-piece of kBwdSubTiles tiles
-  float fill_start = 50.f;       // a CTA's start on an SM another CTA has just left
+  float fill_ovh[4] = {544.f, 427.f, 568.f, 60.f};   // per piece: KEY, APPLY, BKEY, BAPPLY
+  float fill_key_tok = 2.42f;    // gradient token
+  float fill_bkey_tok = 2.15f;   // update-VJP token, its sub-piece costs apart
+  float fill_bkey_sub = 30.f;    // per sub-piece of kBwdSubTiles tiles
+  float fill_start = 32.f;       // a CTA's start on an SM another CTA has just left
   float fill_margin = 0.02f;     // kept only if the modelled step gets this much shorter
 };
 

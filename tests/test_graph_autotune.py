@@ -54,6 +54,7 @@ def test_schedule_roundtrip_and_validation():
     layer = ttt.TTT(2, 64, 128, dtype=torch.bfloat16)
     s = layer.schedule()
     assert s["fwd_waves"] == 1 and s["bwd_waves"] == 1
+    assert s["tail_fill"] == 3 and abs(s["fwd_key_cost"] - 2.45) < 1e-6   # the BF16 head_dim-64 defaults
     layer.set_schedule(fwd_waves=3, fwd_key_cost=1.5)
     s = layer.schedule()
     assert s["fwd_waves"] == 3 and abs(s["fwd_key_cost"] - 1.5) < 1e-6
@@ -61,9 +62,8 @@ def test_schedule_roundtrip_and_validation():
         layer.set_schedule(fwd_waves=0)
     with pytest.raises(ttt.Scal3rError):
         layer.set_schedule(min_piece_tokens=16)
-    assert s["tail_fill"] == 0
-    layer.set_schedule(tail_fill=3)
-    assert layer.schedule()["tail_fill"] == 3
+    layer.set_schedule(tail_fill=0)
+    assert layer.schedule()["tail_fill"] == 0
     with pytest.raises(ttt.Scal3rError):
         layer.set_schedule(tail_fill=4)
 

@@ -424,20 +424,20 @@ def test_plan_invariants_on_benchmark_layouts(lib, wl, H):
 # cost per piece, a cost per token of whole tiles, and for an update-VJP piece
 # a cost per sub-piece of four tiles; a CTA behind the first wave starts a
 # little after its SM frees.
-_FILL_OVH = {KEY: 200.0, APPLY: 120.0, BKEY: 340.0, BAPPLY: 200.0}
+_FILL_OVH = {KEY: 544.0, APPLY: 427.0, BKEY: 568.0, BAPPLY: 60.0}
 
 
 def _fill_time(pv, role, length):
     tiles = -(-length // pv.align)
     t = float(tiles * pv.align)
     if role == KEY:
-        return _FILL_OVH[KEY] + t * float(pv.sched["key_cost"])
+        return _FILL_OVH[KEY] + t * 2.42
     if role == BKEY:
-        return _FILL_OVH[BKEY] + t * 2.03 + -(-tiles // 4) * 170.0
+        return _FILL_OVH[BKEY] + t * 2.15 + -(-tiles // 4) * 30.0
     return _FILL_OVH[role] + t
 
 
-def _dispatch_end(pv, items, ctas, start_lag=50.0):
+def _dispatch_end(pv, items, ctas, start_lag=32.0):
     """When the last piece of a launch ends if the GPU starts CTA k on the
     first SM that frees once CTAs 0..k-1 have started."""
     import heapq
