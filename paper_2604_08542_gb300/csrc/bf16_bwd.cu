@@ -526,7 +526,7 @@ __device__ void run_key_vjp(const TmaMaps& maps, const Params& p, const WorkItem
   }
   if (warp == 2 && lane == 0) bulk_wait_all();   // dk/dv stores complete
   if (aborted || warp < EPI0 || warp >= EPI0 + 8) return;
-  tl::store_lambda<EPI0>(p, it, tb);
+  tl::store_lambda<EPI0>(p, it, tb, sm + PB_OFF);   // the pass B stages: all read
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)

@@ -103,26 +103,20 @@ __device__ __forceinline__ void store_row64(__nv_bfloat16* dst0, int half, const
 }
 
 // The L sums of the piece (TMEM lanes = hidden unit) -> its slot, in the
-// layout of W: L1 [F][D], L3 [F][D], L2 [D][F].
+// layout of W: L1 [F][D], L3 [F][D], L2 [D][F].  A thread holds a row of L1
+// and L3 (256 B each), so stored directly every warp store would write 32
+// scattered 16-byte pieces; they pass through `stage` instead (64 KB of
+// shared memory the piece no longer uses), float4 index swizzled by the row,
+// and leave as whole rows, two per warp store.  L2t is stored column-wise,
+// which is already coalesced.  Run by the 8 epilogue warps only (they meet
+// at named barrier 1).
 template <int EPI0>
-__device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
+__device__ __noinline__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb, uint8_t* stage) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int half = (warp - EPI0) >> 2;
   const uint32_t row = 32u * (warp & 3) + lane;
   const uint32_t lane_base = (32u * (warp & 3)) << 16;
   float* slot = p.part + (size_t)it.slot * 3 * F * D;
-  float* out = slot + (size_t)row * D + 32 * half;
-#pragma unroll
-  for (int m = 0; m < 2; ++m) {
-    float v[16];
-#pragma unroll
-    for (int c = 0; c < 32; c += 16) {
-      tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
-      float4* dst = reinterpret_cast<float4*>(out + (size_t)m * F * D + c);
-#pragma unroll
-      for (int x = 0; x < 4; ++x) st_chk(dst + x, make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]));
-    }
-  }
   // L2t[f][d] is the W2[d][f] entry: stored in W2's orientation
 #pragma unroll
   for (int c = 0; c < 32; c += 16) {
@@ -130,6 +124,27 @@ __device__ void store_lambda(const Params& p, const WorkItem& it, uint32_t tb) {
     tmem_ld16(tb + lane_base + B_L + 128 + 32 * half + c, v);
 #pragma unroll
     for (int j = 0; j < 16; ++j) st_chk(slot + 2 * (size_t)F * D + (size_t)(32 * half + c + j) * F + row, v[j]);
+  }
+  float4* st = reinterpret_cast<float4*>(stage);   // [m][f][16 float4]
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 32; c += 16) {
+      tmem_ld16(tb + lane_base + B_L + 64 * m + 32 * half + c, v);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const uint32_t c4 = (32 * half + c) / 4 + x;
+        st[(m * F + row) * 16 + (c4 ^ (row & 15))] = make_float4(v[4 * x], v[4 * x + 1], v[4 * x + 2], v[4 * x + 3]);
+      }
+    }
+  }
+  named_bar_sync(1, 256);
+  const int t = threadIdx.x - 32 * EPI0;
+#pragma unroll 2
+  for (int k = 0; k < 2 * F * 16 / 256; ++k) {
+    const int idx = k * 256 + t, mr = idx >> 4, c4 = idx & 15, f = mr & (F - 1);
+    st_chk(reinterpret_cast<float4*>(slot + (size_t)mr * D) + c4, st[mr * 16 + (c4 ^ (f & 15))]);
   }
 }
 
@@ -400,7 +415,7 @@ __device__ void token_lane_pass(const CUtensorMap* mx, const CUtensorMap* my, co
   const int stop = __syncthreads_or(*abort);
   tc_fence_after();
   if (stop || warp < EPI0 || warp >= EPI0 + 8) return;
-  store_lambda<EPI0>(p, it, tb);
+  store_lambda<EPI0>(p, it, tb, sm + AW_OFF);   // weights and X/Y stages: no longer read
 }
 
 }  // namespace tl
