@@ -158,6 +158,26 @@ __device__ __noinline__ void store_lambda(const Params& p, const WorkItem& it, u
 //                               128..159 W2[:][32q + r] 160..191 -R2[:][32q + r]
 //   KEY = false: quarter q rows   0.. 31 W1[32q + r]   32.. 63 W3[32q + r]
 //                                64.. 95 W2[:][32q + r]
+// Chunk c = t + 256 k covers block k (quarter k / blocks, 32 rows).  In a row
+// block thread t takes row t / 8, chunk t % 8 (a warp reads 4 whole rows); in
+// a column block row t % 32, chunk t / 32, so that a warp's load of one d
+// reads 32 consecutive entries of W2's (or R2's) row d.
+template <bool KEY>
+struct ChunkAt {
+  static constexpr int BLOCKS = KEY ? 6 : 3;   // 32-row blocks per quarter
+  int q, rr, col, blk, f;
+  __device__ __forceinline__ ChunkAt(int t, int k) {
+    q = k / BLOCKS;
+    const int b = k % BLOCKS;
+    blk = KEY ? b : (b < 2 ? b : 4);            // 0 W1, 1 W3, 2 R1, 3 R3, 4 W2, 5 R2
+    const bool column = blk >= 4;
+    const int r = column ? t % 32 : t / 8;
+    col = (column ? t / 32 : t % 8) * 8;
+    rr = 32 * b + r;
+    f = 32 * q + r;
+  }
+};
+
 template <bool KEY, int BATCH, int EPI0>
 __device__ void load_weight_chunks(const float* w, const float* r, uint8_t* dst, uint32_t qbytes) {
   constexpr int QROWS = KEY ? 192 : 96;
@@ -169,31 +189,27 @@ __device__ void load_weight_chunks(const float* w, const float* r, uint8_t* dst,
     float v[BATCH][8];
 #pragma unroll
     for (int i = 0; i < BATCH; ++i) {
-      const int c = t + 256 * (b0 + i);
-      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
-      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4), f = 32 * q + rr % 32;
-      if (blk < 4) {   // W1, W3, R1, R3: row f
+      const ChunkAt<KEY> a(t, b0 + i);
+      if (a.blk < 4) {   // W1, W3, R1, R3: row f
         const float4* src = reinterpret_cast<const float4*>(
-            (blk == 0 ? w : blk == 1 ? w + F * D : blk == 2 ? r : r + F * D) + (size_t)f * D + col);
-        const float4 a = ldg_chk(src), bq = ldg_chk(src + 1);
-        v[i][0] = a.x; v[i][1] = a.y; v[i][2] = a.z; v[i][3] = a.w;
-        v[i][4] = bq.x; v[i][5] = bq.y; v[i][6] = bq.z; v[i][7] = bq.w;
-      } else {         // W2, R2 [D][F]: column f
-        const float* src = (blk == 4 ? w : r) + 2 * (size_t)F * D + f;
+            (a.blk == 0 ? w : a.blk == 1 ? w + F * D : a.blk == 2 ? r : r + F * D) + (size_t)a.f * D + a.col);
+        const float4 x = ldg_chk(src), y = ldg_chk(src + 1);
+        v[i][0] = x.x; v[i][1] = x.y; v[i][2] = x.z; v[i][3] = x.w;
+        v[i][4] = y.x; v[i][5] = y.y; v[i][6] = y.z; v[i][7] = y.w;
+      } else {           // W2, R2 [D][F]: column f
+        const float* src = (a.blk == 4 ? w : r) + 2 * (size_t)F * D + a.f;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[i][j] = ldg_chk(src + (size_t)(col + j) * F);
+        for (int j = 0; j < 8; ++j) v[i][j] = ldg_chk(src + (size_t)(a.col + j) * F);
       }
     }
 #pragma unroll
     for (int i = 0; i < BATCH; ++i) {
-      const int c = t + 256 * (b0 + i);
-      const int q = c / (QROWS * 8), rr = (c / 8) % QROWS, col = (c % 8) * 8;
-      const int blk = KEY ? rr / 32 : (rr < 64 ? rr / 32 : 4);
-      if (blk == 2 || blk == 3 || blk == 5) {   // the adjoint enters negated
+      const ChunkAt<KEY> a(t, b0 + i);
+      if (a.blk == 2 || a.blk == 3 || a.blk == 5) {   // the adjoint enters negated
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[i][j] = -v[i][j];
       }
-      *reinterpret_cast<uint4*>(dst + q * qbytes + sw128_offset(rr, col)) = pack8(v[i]);
+      *reinterpret_cast<uint4*>(dst + a.q * qbytes + sw128_offset(a.rr, a.col)) = pack8(v[i]);
     }
   }
   fence_proxy_async_smem();
