@@ -45,10 +45,10 @@ NUM_SMS_GB300 = 152
 # (update VJP of chunk 1 with apply VJP of chunk 0) and forward step 3.  It
 # belongs to the kernels as they were captured: retake it when they change.
 NCU_TRAFFIC = {
-    "bf16_vggt64": {"bwd_sweep": 210_551_808 + 217_525_248, "fwd_sweep": 106_425_088 + 14_747_904},
+    "bf16_vggt64": {"bwd_sweep": 211_384_832 + 216_748_032, "fwd_sweep": 106_385_152 + 15_150_848},
 }
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the sweep (a step with "
-                      "both roles, tail fill on) at commit 8ab4142 (profiles/bf16_bsweep_kernel_vggt64.md, "
+                      "both roles, tail fill on) at commit 9e3b98a (profiles/bf16_bsweep_kernel_vggt64.md, "
                       "profiles/bf16_sweep_kernel_vggt64.md)")
 
 
