@@ -633,16 +633,17 @@ def test_float32_tiles_split_short_chunks(lib):
 SPARSE_LENS = [[300, 129, 77, 200, 50], [130, 257], [100, 100, 100], [64]]
 
 
+@pytest.mark.parametrize("fill", [0, 3])
 @pytest.mark.parametrize("n", [2, 3, 5])
-def test_sparse_checkpoint_plan(lib, n):
+def test_sparse_checkpoint_plan(lib, n, fill):
     """ckpt_every = n: the forward writes the weights after local chunks
     n-1, 2n-1, ... to consecutive slots, sequence after sequence; every
     backward step reads W_j from its slot (j a multiple of n), w0 (j = 0) or
     the recompute buffer at the sequence's row; the first backward step of a
     segment reruns the forward steps that rebuild it, with the forward's own
-    pieces and partial slots."""
+    pieces and partial slots (tail-fill pieces included)."""
     lay = syn.layout_from_lengths(SPARSE_LENS)
-    pv = PlanView(lib, 2, lay.chunk_offsets, lay.seq_chunk_ptr, ckpt_every=n)
+    pv = PlanView(lib, 2, lay.chunk_offsets, lay.seq_chunk_ptr, ckpt_every=n, fill=fill)
     try:
         assert pv.rc == 0
         nch = [len(x) for x in SPARSE_LENS]
@@ -716,16 +717,20 @@ def test_dense_checkpoints_plan_no_recompute(lib):
 
 # ---- the composed squared-error loss (BF16, head_dim 64) -------------------
 
-def test_composed_mse_plan(lib):
+@pytest.mark.parametrize("fill", [0, 3])
+def test_composed_mse_plan(lib, fill):
     """Forward: each step's residual pieces are its gradient pieces as apply
     pieces.  Backward: the last npost pieces of a step are the key-side apply
     VJPs; they cover the same tokens as the step's update VJPs, read the same
-    weights, and reduce into their chain's slots like every other piece."""
+    weights, and reduce into their chain's slots like every other piece.  The
+    tail fill stays off: part of each backward step is launched separately,
+    outside its one-launch model."""
     lay = syn.layout_from_lengths([[300, 129, 77], [130, 257], [64]])
     H = 2
-    pv = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, mse_compose=True)
+    pv = PlanView(lib, H, lay.chunk_offsets, lay.seq_chunk_ptr, mse_compose=True, fill=fill)
     try:
         assert pv.rc == 0
+        assert all((nf == 0).all() for nf in pv.nfill)
         maxn = pv.max_chunks
         assert len(pv.ysteps) == maxn + 1
         for j in range(maxn + 1):
